@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark: Bellman node-updates/s of modified policy iteration on the
+61^4 minimum-time orbit-transfer grid (FP32 sweeps, FP64 residual).
+
+One step = one outer iteration of modified policy iteration: an improvement
+sweep (local walk from the previous optimum + golden-section refinement over
+64 tabulated angles) followed by 20 Jacobi policy-evaluation sweeps, over the
+13,845,841 grid nodes resident in HBM.  value = node updates / device time.
+The e2e figure runs the same step through the C ABI with host buffers: the
+value and policy go up from pinned host memory and come back every step.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+step (there is no reference implementation of this method to run).
+
+Multi-GPU: the grid does not shard in this build ("replicas only"): every rank
+solves its own copy, value = all ranks' node updates / the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Bellman node-updates/s; time to ‖ΔV‖∞<1e-6, plain vs NN-warm-started"
+UNIT = "node-updates/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": num(rows[0][2]),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    return world, rank, local
+
+
+def _reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _reduce_sum(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- CPU oracle --
+
+def oracle_step_rate(p, seconds_target=12.0, seed=2407):
+    """Node-updates/s of the FP64 oracle (single thread) for the step's mix of
+    one walk improvement and n_eval evaluation sweeps, measured on sampled
+    nodes of the same grid with a seeded smooth value function."""
+    import oracle
+    from paper_2407_14675_gb300 import workloads as W
+    o = oracle.Oracle(p)
+    V = W.smooth_value(p, seed)
+    V[o.target.astype(bool)] = 0
+    rng = np.random.default_rng(seed)
+    free = np.flatnonzero((o.active & ~o.target).astype(bool))
+    # previous optimum for the walk: the oracle's own full tabulation (untimed)
+    n_imp = 2000
+    nodes = np.sort(rng.choice(free, n_imp, replace=False))
+    _, start = o.bellman_nodes(V, nodes, mode=oracle.IMPROVE_FULL)
+    t0 = time.perf_counter()
+    o.bellman_nodes(V, nodes, mode=oracle.IMPROVE_WALK, codes=start)
+    t_imp = (time.perf_counter() - t0) / n_imp
+    n_ev = 50000
+    ev_nodes = np.sort(rng.choice(free, n_ev, replace=False))
+    codes = rng.integers(0, 65536, n_ev).astype(np.uint16)
+    t0 = time.perf_counter()
+    o.bellman_nodes(V, ev_nodes, mode=oracle.EVAL, codes=codes)
+    t_ev = (time.perf_counter() - t0) / n_ev
+    # scale the sample to about seconds_target of CPU work
+    per_step_node = t_imp + p.n_eval * t_ev
+    reps = max(1, int(seconds_target / max(per_step_node * (n_imp + n_ev), 1e-9)))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        o.bellman_nodes(V, nodes, mode=oracle.IMPROVE_WALK, codes=start)
+        for _e in range(p.n_eval):
+            o.bellman_nodes(V, nodes, mode=oracle.EVAL, codes=start)
+    wall = time.perf_counter() - t0
+    updates = reps * n_imp * (1 + p.n_eval)
+    return updates / wall, {"nodes": n_imp, "reps": reps, "seconds": wall, "updates": updates}
+
+
+def run_reference(args, world, rank):
+    from paper_2407_14675_gb300 import workloads as W
+    if rank != 0:
+        return 0
+    p = W.config1()
+    steps = []
+    for _ in range(args.warmup):
+        oracle_step_rate(p, seconds_target=2.0)
+    for _ in range(args.steps):
+        r, info = oracle_step_rate(p, seconds_target=max(2.0, 20.0 / max(args.steps, 1)))
+        steps.append((r, info))
+    rate = float(np.mean([s[0] for s in steps]))
+    nodes = p.nodes
+    ms_step = (1 + p.n_eval) * nodes / rate * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(p),
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "per step: %d sampled nodes x (1 walk improvement + %d evaluations), "
+                                   "repeated to ~%.0f s, FP64 single thread" %
+                                   (steps[0][1]["nodes"], p.n_eval, steps[0][1]["seconds"])},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(p):
+    return {"workload": "61^4 minimum-time orbit transfer (r, v_r, v_t, m), FP32 modified policy iteration: "
+                        "1 walk+golden improvement (64 angles) + 20 evaluation sweeps per step",
+            "grid": list(p.n), "nodes": p.nodes, "n_angles": p.n_angles, "n_eval": p.n_eval,
+            "accel": p.accel, "dt": p.dt, "beta": p.beta,
+            "l2": "flushed between steps (256 MiB write); per-sweep working set 138 MB > 129 MB L2"}
+
+
+# ------------------------------------------------------------------ GPU arm --
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2407_14675_gb300 import build, dp
+    from paper_2407_14675_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    dp.load()
+    p = W.config1()
+    stream = torch.cuda.current_stream()
+    g = dp.Grid(p, stream=int(stream.cuda_stream))
+    n_upd = g.info["n_active"] - g.info["n_target"]
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+
+    # prepare a realistic state: cold start (full tabulation) + a few steps
+    g.policy_iterate(tol=0.0, max_sweeps=3, n_eval=p.n_eval, polish=0, warm=0)
+    for _ in range(args.warmup):
+        g.policy_iterate(tol=0.0, max_sweeps=1, n_eval=p.n_eval, polish=0, warm=1)
+    torch.cuda.synchronize()
+
+    # --- timed device-resident steps ---
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    _barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            rc, st = g.policy_iterate(tol=0.0, max_sweeps=1, n_eval=p.n_eval, polish=0, warm=1, time_kernels=1)
+            ev[k][1].record(stream)
+            stats.append(st)
+        torch.cuda.synchronize()
+    _barrier(world)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms_max = _reduce_max(ms, world)
+    updates = sum(s.node_updates for s in stats)
+    total_updates = _reduce_sum(float(updates), world)
+    value = total_updates / (ms_max / 1e3)
+    ms_eval = sum(s.ms_eval for s in stats)
+    n_eval = sum(s.sweeps_eval for s in stats)
+    ms_imp = sum(s.ms_improve for s in stats)
+    n_imp = sum(s.sweeps_improve for s in stats)
+    launches = sum(s.launches for s in stats)
+
+    # --- end to end through the C ABI with host buffers ---
+    V_host = torch.empty(g.n, dtype=torch.float64, pin_memory=True)
+    C_host = torch.empty(g.n, dtype=torch.int16, pin_memory=True)
+    C_view = C_host.numpy().view(np.uint16)
+    dp.dp_get_value(g.h, g.n, out=V_host.numpy())
+    C_view[:] = g.get_policy()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    _barrier(world)
+    t0 = time.perf_counter()
+    e2e_updates = 0
+    for _ in range(e2e_steps):
+        dp.dp_set_value(g.h, V_host)
+        dp.dp_set_policy(g.h, C_view)
+        rc, st = g.policy_iterate(tol=0.0, max_sweeps=1, n_eval=p.n_eval, polish=0, warm=1)
+        dp.dp_get_value(g.h, g.n, out=V_host.numpy())
+        C_view[:] = dp.dp_get_policy(g.h, g.n)
+        e2e_updates += st.node_updates
+    torch.cuda.synchronize()
+    e2e_s = _reduce_max(time.perf_counter() - t0, world)
+    e2e_value = _reduce_sum(float(e2e_updates), world) / e2e_s
+
+    # --- time to ||dV|| < 1e-6 (plain cold start, FP32 + FP64 polish) ---
+    solve = None
+    if args.solve:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = g.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=p.n_eval, polish=1, warm=0)
+        torch.cuda.synchronize()
+        solve = {"seconds": time.perf_counter() - t0, "converged": bool(st.converged), "residual": st.residual,
+                 "sweeps_improve": st.sweeps_improve, "sweeps_eval": st.sweeps_eval,
+                 "sweeps_improve_fp64": st.sweeps_improve_fp64, "sweeps_eval_fp64": st.sweeps_eval_fp64,
+                 "start": "cold (V = 0, full tabulation first)"}
+    g.close()
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    peaks, peak_src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    eval_ms = ms_eval / max(n_eval, 1)
+    eval_bytes = 10.0 * n_upd        # V read 4 B + policy 2 B + V write 4 B per node
+    ach = eval_bytes / (eval_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "sweep_kernel<float,float,EVAL> (policy evaluation)",
+            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+            "traffic": None, "algorithmic_bytes_per_launch": eval_bytes, "avg_launch_ms": eval_ms,
+            "share_of_step": ms_eval / max(ms, 1e-9)}
+    imp_ms = ms_imp / max(n_imp, 1)
+
+    cpu_rate, cpu_info = oracle_step_rate(p, seconds_target=args.cpu_seconds) if args.cpu_seconds > 0 else (None, {})
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(_config(p), parallelism="replicas" if world > 1 else "single"),
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
+                "h2d_bytes_per_step": g.n * (8 + 2), "d2h_bytes_per_step": g.n * (8 + 2)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "improve_sweep": {"avg_launch_ms": imp_ms, "share_of_step": ms_imp / max(ms, 1e-9),
+                          "node_updates_per_s": n_upd / (imp_ms / 1e3)},
+        "eval_sweep_node_updates_per_s": n_upd / (eval_ms / 1e3),
+        "cpu_baseline": None if cpu_rate is None else {
+            "value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d sampled nodes of the 61^4 grid x (1 walk improvement + %d evaluations), %d reps, "
+                      "%.1f s FP64 single thread" % (cpu_info["nodes"], p.n_eval, cpu_info["reps"],
+                                                      cpu_info["seconds"])},
+        "time_to_tol": solve,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--solve", type=int, default=1, help="also time a cold solve to 1e-6")
+    ap.add_argument("--solve-max", type=int, default=3000, help="improvement-sweep budget of that solve")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,207 @@
+/*
+ * dp.h -- C ABI of the GB300 semi-Lagrangian Bellman solver for planar
+ * low-thrust orbit transfer (Ciancarelli, Ferretti, Intelisano, Villani,
+ * "Dynamic Programming Techniques for Planar Orbital Transfer of Low Earth
+ * Orbit Satellites", arXiv 2407.14675).
+ *
+ * The library solves the fixed-point scheme of §3, Eq. (10),
+ *
+ *     v_j = min_f { dt l(x_j, f) + beta I[V](x_j + dt Phi(x_j, f)) },
+ *
+ * on a 4-D grid of states x = (r, v_r, v_t, m) with running cost l = 1
+ * (minimum time), beta = exp(-lambda dt), Phi a second-order Runge-Kutta
+ * (Heun) step of the polar two-body dynamics with thrust (§3 "Grid and polar
+ * coordinates", angle coordinate dropped, mass added with m' = -a/c), I[V]
+ * the multilinear (Q1) interpolation, and I[V] = M for a foot outside the box
+ * or the reduced node set.  The control is the thrust angle alpha (sin alpha
+ * radial, cos alpha tangential); every policy is stored as a 16-bit angle
+ * code, alpha = 2 pi code / 65536.
+ *
+ * Conventions for every call:
+ *   - Return value: a DP_* status code.  On failure dp_last_error() gives a
+ *     message (thread-local, valid until the next call on that thread).
+ *   - Host pointers are owned by the caller and only read or written during
+ *     the call; the library copies in and out and keeps no reference.
+ *   - The library owns all device memory of a grid (allocated by
+ *     dp_grid_create and by the first FP64 polish, freed by dp_grid_destroy).
+ *   - All GPU work of a grid is issued on desc.stream (NULL: the legacy
+ *     default stream) on the device that was current at dp_grid_create; calls
+ *     that return host data synchronise that stream.
+ *   - One grid handle must not be used by two threads at the same time.
+ *
+ * Node order: a box node (i_r, i_vr, i_vt, i_m) has box index
+ * ((i_r n1 + i_vr) n2 + i_vt) n3 + i_m (mass fastest), coordinates
+ * x_d = lo_d + i_d (hi_d - lo_d)/(n_d - 1).  Values and policies are exchanged
+ * in "compact order": the stored nodes in ascending box index.  Without the
+ * reduced grid every box node is stored and compact order is box order.
+ */
+#ifndef DP_H
+#define DP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define DP_OK         0
+#define DP_EINVAL     1  /* invalid argument or descriptor                     */
+#define DP_ENOMEM     2  /* device or host allocation failed                   */
+#define DP_ECUDA      3  /* a CUDA call failed                                 */
+#define DP_ENOCONV    4  /* sweep budget reached before the tolerance; results
+                            and statistics are valid                           */
+#define DP_ETIMEOUT   5  /* a bounded device-side wait expired                 */
+#define DP_ENONFINITE 6  /* a non-finite value met (input or iterate)          */
+
+/* ---- enums ---- */
+#define DP_FP64 0            /* FP64 geometry and FP64 values                     */
+#define DP_FP32 1            /* FP32 geometry and values, FP64 residual / polish  */
+
+#define DP_DYN_ORBIT      0  /* planar orbit (r, v_r, v_t, m), §3 polar dynamics   */
+#define DP_DYN_UNIT_SPEED 1  /* test dynamics x' = (cos a, sin a, 0, 0); components
+                                below 1e-12 in magnitude are taken as exact zeros  */
+
+#define DP_SWEEP_VI           0  /* Eq. (12): min over the tabulated angles        */
+#define DP_SWEEP_IMPROVE_FULL 1  /* Eq. (14): full tabulation (+ refinement)       */
+#define DP_SWEEP_IMPROVE_WALK 2  /* Eq. (14): walk from the previous optimum
+                                    (+ refinement), §3 "Efficient computation of
+                                    the minimum"                                   */
+#define DP_SWEEP_EVAL         3  /* Eq. (13): one Jacobi sweep at the frozen policy */
+
+typedef struct dp_grid dp_grid;
+
+/* Grid, dynamics, target and control-set description (§3, §4). */
+typedef struct dp_grid_desc {
+    int32_t n[4];          /* nodes per dimension (r, v_r, v_t, m), each in [2, 1024] */
+    double  lo[4], hi[4];  /* box, lo < hi; r > 0 and m > 0 on the box for ORBIT     */
+    int32_t dynamics;      /* DP_DYN_*                                               */
+    double  mu;            /* gravitational parameter (nondimensional 1)             */
+    double  accel;         /* thrust acceleration a at unit mass (>= 0)              */
+    double  exhaust_c;     /* exhaust speed c (> 0), m' = -a/c                       */
+    double  dt;            /* pseudo-time step of the scheme (> 0)                   */
+    double  beta;          /* discount exp(-lambda dt), in (0, 1)                    */
+    double  penalty_M;     /* I[V] outside the domain; <= 0 means dt / (1 - beta)    */
+    double  target_c[4];   /* target: open box |x_d - c_d| < w_d over the d with     */
+    double  target_w[4];   /*   w_d > 0; V = 0 there and those nodes are not updated */
+    int32_t n_angles;      /* K tabulated angles 2 pi k / K, K in [2, 4096]          */
+    int32_t refine;        /* 1: golden-section refinement in improvement sweeps     */
+    double  refine_tol;    /* refinement bracket width, rad (> 0)                    */
+    int32_t reduced;       /* 1: keep only nodes with energy in [energy_lo, hi]      */
+    double  energy_lo, energy_hi; /* specific energy (v_r^2 + v_t^2)/2 - mu/r band   */
+    int32_t precision;     /* DP_FP64 or DP_FP32                                     */
+    void*   stream;        /* cudaStream_t for all work of this grid (may be NULL)   */
+} dp_grid_desc;
+
+/* Solver options. */
+typedef struct dp_solve_opts {
+    double  tol;           /* stop when an improvement (PI) or VI sweep moves V by
+                              less than tol in the sup norm                         */
+    int64_t max_sweeps;    /* VI: sweep budget; PI: improvement-sweep budget        */
+    int32_t n_eval;        /* PI: evaluation sweeps per improvement (>= 0)          */
+    int32_t walk;          /* PI: 1 = local walk from the previous optimum after the
+                              first improvement, 0 = full tabulation every time     */
+    int32_t warm;          /* 0: start from V = 0 (PI: full tabulation first);
+                              1: start from the resident V and policy               */
+    int32_t polish;        /* FP32 grids: 1 = finish with FP64 values once FP32
+                              stalls; 0 = stay FP32                                 */
+    double  switch_tol;    /* FP32 -> FP64 switch when the improvement residual is
+                              below this (<= 0: 32 ulp of max V, automatic)         */
+    int32_t time_kernels;  /* 1: time every sweep with CUDA events (small overhead) */
+} dp_solve_opts;
+
+/* Solver statistics (filled on DP_OK and on DP_ENOCONV). */
+typedef struct dp_solve_stats {
+    int64_t sweeps_vi;
+    int64_t sweeps_improve;       /* storage-precision improvement sweeps            */
+    int64_t sweeps_eval;          /* storage-precision evaluation sweeps             */
+    int64_t sweeps_improve_fp64;  /* FP64-value improvement sweeps (polish)          */
+    int64_t sweeps_eval_fp64;     /* FP64-value evaluation sweeps (polish)           */
+    double  residual;             /* last stopping-test sup norm                     */
+    int32_t converged;
+    double  ms_wall;              /* host wall time of the call                      */
+    double  ms_vi, ms_improve, ms_eval, ms_improve_fp64, ms_eval_fp64; /* GPU time by
+                                     sweep type when time_kernels = 1               */
+    int64_t node_updates;         /* stored non-target nodes x sweeps               */
+    int64_t launches;             /* kernels launched by the call                    */
+} dp_solve_stats;
+
+/* Sizes of a grid. */
+typedef struct dp_grid_info {
+    int64_t n_box;      /* n0 n1 n2 n3                                             */
+    int64_t n_active;   /* stored nodes                                            */
+    int64_t n_target;   /* stored nodes inside the target                          */
+    double  penalty_M;  /* the M in use                                            */
+    int32_t fp64_values;/* 1 when the resident value is held in FP64               */
+    int64_t device_bytes;
+} dp_grid_info;
+
+/* Validates desc, builds the node set (the energy-band reduction of §3 "Grid
+ * and polar coordinates" when desc->reduced), the target set and the angle
+ * tables, and allocates double-buffered V (= 0) and the policy (code 0).
+ * Errors: DP_EINVAL (bad descriptor; empty node set; reduced grid needs v_t > 0
+ * on the box), DP_ENOMEM, DP_ECUDA.  *out is NULL on failure. */
+int dp_grid_create(const dp_grid_desc* desc, dp_grid** out);
+
+/* Frees all device memory of the grid (synchronises its stream).  NULL is a
+ * no-op. */
+int dp_grid_destroy(dp_grid* grid);
+
+int dp_grid_get_info(const dp_grid* grid, dp_grid_info* info);
+
+/* Box index of every stored node, compact order (count == n_active). */
+int dp_get_active_index(const dp_grid* grid, int64_t* box_index, int64_t count);
+
+/* Copy V in / out, compact order, count == n_active.  dp_set_value rejects
+ * non-finite input (DP_ENONFINITE) and forces target nodes to 0; it loads the
+ * storage precision of the grid (FP32 grids round to nearest). */
+int dp_set_value(dp_grid* grid, const double* host_V, int64_t count);
+int dp_get_value(const dp_grid* grid, double* host_V, int64_t count);
+
+/* Copy the policy (16-bit angle codes) in / out, compact order. */
+int dp_set_policy(dp_grid* grid, const uint16_t* host_codes, int64_t count);
+int dp_get_policy(const dp_grid* grid, uint16_t* host_codes, int64_t count);
+
+/* One Jacobi sweep of the scheme on the resident V and policy (mode =
+ * DP_SWEEP_*): Eq. (12), (13) or (14).  Improvement modes rewrite the policy;
+ * EVAL reads it.  On FP32 grids whose value has moved to FP64 (after a
+ * polish) the sweep runs with FP64 values.  *residual (nullable) receives
+ * max_j |V'_j - V_j| over the stored nodes, accumulated in FP64. */
+int dp_bellman_sweep(dp_grid* grid, int32_t mode, double* residual);
+
+/* Value iteration, §3 Eq. (12): sweeps until the residual < opts->tol or
+ * opts->max_sweeps (DP_ENOCONV).  stats nullable. */
+int dp_value_iterate(dp_grid* grid, const dp_solve_opts* opts, dp_solve_stats* stats);
+
+/* Modified policy iteration, §3 Eq. (13)-(14): an improvement sweep (full
+ * tabulation first, then the local walk, each followed by golden-section
+ * refinement when desc.refine) and opts->n_eval Jacobi evaluation sweeps at
+ * the frozen policy, repeated until an improvement sweep moves V by less than
+ * opts->tol.  FP32 grids with opts->polish switch to FP64 values once the FP32
+ * residual stalls and finish there.  stats nullable. */
+int dp_policy_iterate(dp_grid* grid, const dp_solve_opts* opts, dp_solve_stats* stats);
+
+/* Approximate optimal feedback, §3 Eq. (15), at n arbitrary states
+ * (host, n x 4 row-major) with step tau > 0: full tabulation then refinement
+ * (when desc.refine) of tau + beta^(tau/dt) I[V](y + tau Phi(y, alpha)).
+ * alpha_out (n, rad in [0, 2 pi)) required, q_out (n) nullable. */
+int dp_feedback_control(const dp_grid* grid, const double* states, int32_t n, double tau,
+                        double* alpha_out, double* q_out);
+
+/* Closed loop, §3 "Computation of the approximate optimal solution": per
+ * trajectory, the feedback of Eq. (15) with step tau is recomputed every
+ * h_rk4 and held over one classical RK4 step of the dynamics, until the state
+ * enters the target (t_arrive = end of that step) or t_max (t_arrive = -1).
+ * x0 and x_final are n x 4 row-major host arrays. */
+int dp_simulate_closed_loop(const dp_grid* grid, const double* x0, int32_t n, double tau,
+                            double h_rk4, double t_max, double* t_arrive, double* x_final);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* dp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DP_H */

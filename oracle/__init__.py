@@ -67,6 +67,7 @@ def lib():
             "orc_interp": (C.c_int, [P, _dp, _u8, _dp, _dp]),
             "orc_q_node": (C.c_double, [P, _dp, _u8, C.POINTER(C.c_int), C.c_double]),
             "orc_q_state": (C.c_double, [P, _dp, _u8, _dp, C.c_double, C.c_double]),
+            "orc_foot_node": (None, [P, C.POINTER(C.c_int), C.c_double, _dp]),
             "orc_sweep": (C.c_double, [P, _dp, _dp, _u8, _u8, C.c_int, _u16, _u16, _l]),
             "orc_bellman_nodes": (None, [P, _dp, _u8, _u8, _l, C.c_long, C.c_int, _u16, _dp, _u16]),
             "orc_q_nodes": (None, [P, _dp, _u8, _l, _u16, C.c_long, _dp]),
@@ -157,6 +158,13 @@ class Oracle:
         V = np.ascontiguousarray(V, np.float64)
         i = (C.c_int * 4)(*idx)
         return lib().orc_q_node(C.byref(self.s), _ptr(V, _dp), _ptr(self.active, _u8), i, alpha)
+
+    def foot_node(self, idx, alpha):
+        """Foot of the Heun step from node idx, in grid units."""
+        i = (C.c_int * 4)(*[int(v) for v in idx])
+        s = np.zeros(4)
+        lib().orc_foot_node(C.byref(self.s), i, alpha, _ptr(s, _dp))
+        return s
 
     def q_state(self, V, y, alpha, tau):
         V = np.ascontiguousarray(V, np.float64)

@@ -249,6 +249,16 @@ double orc_q_node(const orc_problem* p, const double* V, const unsigned char* ac
     return p->dt + p->beta * I;
 }
 
+/* Foot of the one-step map from grid node idx in grid units (test helper:
+ * tells how close a foot lies to a cell face). */
+void orc_foot_node(const orc_problem* p, const int idx[4], double alpha, double s[4])
+{
+    double x[4], delta[4];
+    node_state(p, idx, x);
+    orc_heun_displacement(p, x, alpha, p->dt, delta);
+    for (int d = 0; d < 4; ++d) s[d] = idx[d] + delta[d] / spacing(p, d);
+}
+
 /* Term of Eq. (15) at an arbitrary state y with feedback step tau: the
  * discount over tau is beta^(tau/dt) = exp(-lambda tau). */
 double orc_q_state(const orc_problem* p, const double* V, const unsigned char* active,

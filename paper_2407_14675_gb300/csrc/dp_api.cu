@@ -1,0 +1,881 @@
+// dp_api.cu -- host side of the C ABI declared in include/dp.h.
+//
+// A dp_grid owns every device buffer of one problem: the row and line tables
+// of the node set, double-buffered V in the grid's storage precision (plus
+// FP64 buffers once a polish starts), the 16-bit policy, the angle tables, a
+// control block and a ring of FP64 residual slots (one per sweep).  Solvers
+// enqueue Jacobi sweeps in chunks on the grid's stream; each sweep can check
+// the previous sweep's residual on the device and turn the rest of the queue
+// into no-ops, so the host only synchronises once per chunk.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dp.h"
+#include "dp_host.h"
+
+using namespace dpk;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) return fail(DP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int kRing = 8192;        // residual slots (power of two)
+constexpr int kMaxChunk = 2048;    // sweeps enqueued between host checks (< kRing / 2)
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+}  // namespace
+
+struct dp_grid {
+    dp_grid_desc d;
+    int device = 0;
+    cudaStream_t st = nullptr;
+    int sm_count = 0;
+    int fp32 = 0;
+    long long n_box = 0, n_active = 0, n_target = 0;
+    int n_rows = 0;
+    double h[4] = {0, 0, 0, 0};
+    double M = 0;
+    int tlo[4], thi[4];
+
+    int4* rows = nullptr;
+    unsigned* lines = nullptr;
+    double2 *hi64 = nullptr, *lo64 = nullptr;
+    float2 *hi32 = nullptr, *lo32 = nullptr;
+    void* V[2] = {nullptr, nullptr};     // storage precision
+    int cur = 0;
+    double* V64[2] = {nullptr, nullptr}; // FP64 values after a polish (FP32 grids)
+    int cur64 = 0;
+    bool fp64_values = false;
+    uint16_t* code = nullptr;
+    Ctl* ctl = nullptr;
+    unsigned long long* ring = nullptr;
+    double* staging = nullptr;           // n_active doubles
+    long long* scratch64 = nullptr;      // n_active int64 (index export)
+    Ctl* h_ctl = nullptr;                // pinned
+    unsigned long long* h_ring = nullptr;// pinned, kRing
+    long long device_bytes = 0;
+
+    Geo<double> g64;
+    Geo<float> g32;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(dp_grid* g, T** p, size_t count)
+{
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? DP_ENOMEM : DP_ECUDA, "cudaMalloc(%zu bytes): %s",
+                    count * sizeof(T), cudaGetErrorString(e));
+    }
+    g->device_bytes += (long long)(count * sizeof(T));
+    return DP_OK;
+}
+
+void free_grid(dp_grid* g)
+{
+    if (!g) return;
+    cudaSetDevice(g->device);
+    if (g->st) cudaStreamSynchronize(g->st);
+    void* ps[] = {g->rows, g->lines, g->hi64, g->lo64, g->hi32, g->lo32, g->V[0], g->V[1], g->V64[0],
+                  g->V64[1], g->code, g->ctl, g->ring, g->staging, g->scratch64};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    if (g->h_ctl) cudaFreeHost(g->h_ctl);
+    if (g->h_ring) cudaFreeHost(g->h_ring);
+    delete g;
+}
+
+int validate(const dp_grid_desc* d)
+{
+    if (!d) return fail(DP_EINVAL, "desc is NULL");
+    long long box = 1;
+    for (int k = 0; k < 4; ++k) {
+        if (d->n[k] < 2 || d->n[k] > 1024) return fail(DP_EINVAL, "n[%d] = %d outside [2, 1024]", k, d->n[k]);
+        if (!(d->lo[k] < d->hi[k]) || !std::isfinite(d->lo[k]) || !std::isfinite(d->hi[k]))
+            return fail(DP_EINVAL, "box dimension %d needs finite lo < hi", k);
+        box *= d->n[k];
+    }
+    if (box > 2147483647LL) return fail(DP_EINVAL, "box of %lld nodes exceeds 2^31 - 1", box);
+    if (d->dynamics != DP_DYN_ORBIT && d->dynamics != DP_DYN_UNIT_SPEED)
+        return fail(DP_EINVAL, "unknown dynamics %d", d->dynamics);
+    if (!(d->dt > 0) || !std::isfinite(d->dt)) return fail(DP_EINVAL, "dt must be > 0");
+    if (!(d->beta > 0 && d->beta < 1)) return fail(DP_EINVAL, "beta must lie in (0, 1)");
+    if (d->n_angles < 2 || d->n_angles > 4096) return fail(DP_EINVAL, "n_angles must lie in [2, 4096]");
+    if (d->refine && !(d->refine_tol > 0)) return fail(DP_EINVAL, "refine_tol must be > 0");
+    if (d->precision != DP_FP64 && d->precision != DP_FP32) return fail(DP_EINVAL, "unknown precision");
+    if (!std::isfinite(d->penalty_M)) return fail(DP_EINVAL, "penalty_M must be finite");
+    if (d->dynamics == DP_DYN_ORBIT) {
+        if (!(d->mu > 0) || !(d->accel >= 0) || !(d->exhaust_c > 0))
+            return fail(DP_EINVAL, "orbit dynamics need mu > 0, accel >= 0, exhaust_c > 0");
+        if (!(d->lo[0] > 0) || !(d->lo[3] > 0)) return fail(DP_EINVAL, "orbit box needs r > 0 and m > 0");
+        double r2 = d->lo[0] + d->dt * std::fmin(d->lo[1], 0.0);
+        double m2 = d->lo[3] - d->dt * d->accel / d->exhaust_c;
+        if (!(r2 > 0) || !(m2 > 0)) return fail(DP_EINVAL, "Heun predictor leaves r > 0 or m > 0 on the box");
+    }
+    if (d->reduced) {
+        if (d->dynamics != DP_DYN_ORBIT) return fail(DP_EINVAL, "the energy-band grid needs orbit dynamics");
+        if (!(d->lo[2] > 0)) return fail(DP_EINVAL, "the energy-band grid needs v_t > 0 on the box");
+        if (!(d->energy_lo <= d->energy_hi)) return fail(DP_EINVAL, "energy_lo > energy_hi");
+    }
+    for (int k = 0; k < 4; ++k)
+        if (!std::isfinite(d->target_c[k]) || !std::isfinite(d->target_w[k]))
+            return fail(DP_EINVAL, "target box must be finite");
+    return DP_OK;
+}
+
+template <typename G>
+void fill_geo(const dp_grid* gr, Geo<G>& g)
+{
+    const dp_grid_desc& d = gr->d;
+    for (int k = 0; k < 4; ++k) {
+        g.n[k] = d.n[k];
+        g.lo[k] = (G)d.lo[k];
+        g.h[k] = (G)gr->h[k];
+        g.ih[k] = (G)(1.0 / gr->h[k]);
+        g.tlo[k] = gr->tlo[k];
+        g.thi[k] = gr->thi[k];
+    }
+    g.stride[3] = 1;
+    g.stride[2] = d.n[3];
+    g.stride[1] = d.n[2] * d.n[3];
+    g.stride[0] = d.n[1] * d.n[2] * d.n[3];
+    double mdot = d.dynamics == DP_DYN_ORBIT ? -d.accel / d.exhaust_c : 0.0;
+    g.mu = (G)d.mu;
+    g.accel = (G)d.accel;
+    g.mdot = (G)mdot;
+    g.dt = (G)d.dt;
+    g.hdt = (G)(0.5 * d.dt);
+    g.beta = (G)d.beta;
+    g.M = (G)gr->M;
+    g.beta_hi = (G)d.beta;
+    g.beta_lo = (G)(d.beta - (double)g.beta_hi);
+    g.dt64 = d.dt;
+    g.beta64 = d.beta;
+    g.M64 = gr->M;
+    g.um = (G)(d.dt * mdot / gr->h[3]);
+    g.dyn = d.dynamics;
+    g.K = d.n_angles;
+    g.refine = d.refine;
+    double tc = d.refine ? std::floor(d.refine_tol / (kTwoPi / kCodes)) : 0.0;
+    g.fib_stop = (int)std::fmin(tc, 1e9);
+    g.n_m = d.n[3];
+    g.magic_m = ((1ULL << 40) + (unsigned long long)d.n[3] - 1) / (unsigned long long)d.n[3];
+    g.n_nodes = (int)gr->n_active;
+    g.rows = gr->rows;
+    g.lines = gr->lines;
+}
+
+template <typename G, typename S>
+SweepLaunch<G, S> sweep_launch(dp_grid* g, const Geo<G>& geo, const S* Vin, S* Vout, int mode, long long sweep,
+                               int check_prev, double tol)
+{
+    SweepLaunch<G, S> L;
+    L.g = geo;
+    L.Vin = Vin;
+    L.Vout = Vout;
+    L.code = g->code;
+    L.ctl = g->ctl;
+    L.ring = g->ring;
+    L.ring_mask = kRing - 1;
+    L.sweep = sweep;
+    L.check_prev = check_prev;
+    L.tol = tol;
+    L.mode = mode;
+    L.dyn = g->d.dynamics;
+    L.reduced = g->d.reduced;
+    L.stream = g->st;
+    L.sm_count = g->sm_count;
+    return L;
+}
+
+// Value storage of the grid for the sweep kernels.
+enum Store { kStoreF64, kStoreF32, kStoreMix };
+
+Store store_of(const dp_grid* g)
+{
+    if (!g->fp32) return kStoreF64;
+    return g->fp64_values ? kStoreMix : kStoreF32;
+}
+
+// Enqueue sweep number `t` (relative to the solve start, buffers alternate
+// from the current one).
+cudaError_t enqueue_sweep(dp_grid* g, int mode, long long t, int check_prev, double tol)
+{
+    int a = (int)(t & 1);
+    switch (store_of(g)) {
+    case kStoreF64: {
+        const double* in = (const double*)g->V[(g->cur + a) & 1];
+        double* out = (double*)g->V[(g->cur + a + 1) & 1];
+        return launch_sweep(sweep_launch<double, double>(g, g->g64, in, out, mode, t, check_prev, tol));
+    }
+    case kStoreF32: {
+        const float* in = (const float*)g->V[(g->cur + a) & 1];
+        float* out = (float*)g->V[(g->cur + a + 1) & 1];
+        return launch_sweep(sweep_launch<float, float>(g, g->g32, in, out, mode, t, check_prev, tol));
+    }
+    default: {
+        const double* in = g->V64[(g->cur64 + a) & 1];
+        double* out = g->V64[(g->cur64 + a + 1) & 1];
+        return launch_sweep(sweep_launch<float, double>(g, g->g32, in, out, mode, t, check_prev, tol));
+    }
+    }
+}
+
+void advance(dp_grid* g, long long done)
+{
+    if (store_of(g) == kStoreMix) g->cur64 = (int)((g->cur64 + done) & 1);
+    else g->cur = (int)((g->cur + done) & 1);
+}
+
+double ring_value(const dp_grid* g, long long t)
+{
+    unsigned long long b = g->h_ring[t & (kRing - 1)];
+    double v;
+    memcpy(&v, &b, sizeof v);
+    return v;
+}
+
+int reset_ctl(dp_grid* g)
+{
+    CK(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), g->st));
+    return DP_OK;
+}
+
+// Zero the ring slots of sweeps [t0, t0 + n).
+int clear_ring(dp_grid* g, long long t0, long long n)
+{
+    long long a = t0 & (kRing - 1);
+    long long first = n < kRing - a ? n : kRing - a;
+    CK(cudaMemsetAsync(g->ring + a, 0, first * sizeof(unsigned long long), g->st));
+    if (n > first) CK(cudaMemsetAsync(g->ring, 0, (n - first) * sizeof(unsigned long long), g->st));
+    return DP_OK;
+}
+
+// Copy ring slots of sweeps [t0, t0 + n) and the control block to the host.
+int fetch(dp_grid* g, long long t0, long long n)
+{
+    long long a = t0 & (kRing - 1);
+    long long first = n < kRing - a ? n : kRing - a;
+    CK(cudaMemcpyAsync(g->h_ring + a, g->ring + a, first * sizeof(unsigned long long), cudaMemcpyDeviceToHost, g->st));
+    if (n > first)
+        CK(cudaMemcpyAsync(g->h_ring, g->ring, (n - first) * sizeof(unsigned long long), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    return DP_OK;
+}
+
+// Optional per-sweep CUDA-event timing.
+struct SweepTimer {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;
+    int used = 0;
+    double ms[5] = {0, 0, 0, 0, 0};
+
+    ~SweepTimer()
+    {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+    cudaError_t begin(int k)
+    {
+        if (!on) return cudaSuccess;
+        if (used + 2 > (int)ev.size()) {
+            for (int i = 0; i < 2; ++i) {
+                cudaEvent_t e;
+                cudaError_t r = cudaEventCreate(&e);
+                if (r != cudaSuccess) return r;
+                ev.push_back(e);
+            }
+            kind.resize(ev.size() / 2);
+        }
+        kind[used / 2] = k;
+        return cudaEventRecord(ev[used], st);
+    }
+    cudaError_t end()
+    {
+        if (!on) return cudaSuccess;
+        cudaError_t r = cudaEventRecord(ev[used + 1], st);
+        used += 2;
+        return r;
+    }
+    // after a stream synchronisation: accumulate and recycle
+    cudaError_t collect()
+    {
+        if (!on) return cudaSuccess;
+        for (int i = 0; i + 1 < used; i += 2) {
+            float m = 0;
+            cudaError_t r = cudaEventElapsedTime(&m, ev[i], ev[i + 1]);
+            if (r != cudaSuccess) return r;
+            ms[kind[i / 2]] += m;
+        }
+        used = 0;
+        return cudaSuccess;
+    }
+};
+
+enum { kTVI = 0, kTImp = 1, kTEval = 2, kTImp64 = 3, kTEval64 = 4 };
+
+int finish_nonfinite(dp_grid* g)
+{
+    if (g->h_ctl->nonfinite) return fail(DP_ENONFINITE, "a sweep produced a non-finite value");
+    return DP_OK;
+}
+
+long long updates_per_sweep(const dp_grid* g) { return g->n_active - g->n_target; }
+
+double now_ms()
+{
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int ensure_fp64(dp_grid* g)
+{
+    if (g->V64[0]) return DP_OK;
+    int rc = dalloc(g, &g->V64[0], g->n_active);
+    if (rc) return rc;
+    return dalloc(g, &g->V64[1], g->n_active);
+}
+
+int zero_value(dp_grid* g)
+{
+    size_t es = g->fp32 ? sizeof(float) : sizeof(double);
+    CK(cudaMemsetAsync(g->V[g->cur], 0, es * g->n_active, g->st));
+    g->fp64_values = false;
+    return DP_OK;
+}
+
+}  // namespace
+
+namespace {
+
+template <typename G, typename S>
+int run_loop(dp_grid* g, const Geo<G>& geo, const S* V, const double* x0, int n, double tau, double h,
+                    long long steps, double* alpha, double* q, double* t_arrive, double* x_final)
+{
+    LoopLaunch<G, S> L;
+    L.g = geo;
+    L.V = V;
+    L.x0 = x0;
+    L.n = n;
+    L.tau = tau;
+    L.beta_tau = std::pow(g->d.beta, tau / g->d.dt);
+    L.h = h;
+    L.steps = steps;
+    for (int k = 0; k < 4; ++k) {
+        L.tgt_c[k] = g->d.target_c[k];
+        L.tgt_w[k] = g->d.target_w[k];
+    }
+    L.mu = g->d.mu;
+    L.accel = g->d.accel;
+    L.mdot = g->d.dynamics == DP_DYN_ORBIT ? -g->d.accel / g->d.exhaust_c : 0.0;
+    L.lo_m = g->d.lo[3];
+    L.tab_hi64 = g->hi64;
+    L.tab_lo64 = g->lo64;
+    L.alpha = alpha;
+    L.q = q;
+    L.t_arrive = t_arrive;
+    L.x_final = x_final;
+    L.dyn = g->d.dynamics;
+    L.reduced = g->d.reduced;
+    L.stream = g->st;
+    CK(launch_loop(L));
+    return DP_OK;
+}
+
+int loop_common(const dp_grid* cg, const double* states, int n, double tau, double h, double t_max,
+                       double* alpha_out, double* q_out, double* t_arrive, double* x_final)
+{
+    dp_grid* g = const_cast<dp_grid*>(cg);
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
+    for (long long k = 0; k < 4LL * n; ++k)
+        if (!std::isfinite(states[k])) return fail(DP_ENONFINITE, "state %lld is not finite", k / 4);
+    long long steps = 0;
+    if (t_arrive) steps = (long long)std::ceil(t_max / h - 1e-9);
+    if (t_arrive && steps < 1) steps = 1;
+    double* d_buf = nullptr;
+    size_t nb = (size_t)n * (4 + 1 + 1 + 4);
+    CK(cudaMallocAsync(&d_buf, nb * sizeof(double), g->st));
+    double* d_x0 = d_buf;
+    double* d_a = d_buf + 4 * (size_t)n;
+    double* d_q = d_a + n;
+    double* d_xf = d_q + n;
+    int rc = DP_OK;
+    cudaError_t e = cudaMemcpyAsync(d_x0, states, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess) {
+        switch (store_of(g)) {
+        case kStoreF64:
+            rc = run_loop<double, double>(g, g->g64, (const double*)g->V[g->cur], d_x0, n, tau, h, steps, d_a, d_q,
+                                          d_a, d_xf);
+            break;
+        case kStoreF32:
+            rc = run_loop<float, float>(g, g->g32, (const float*)g->V[g->cur], d_x0, n, tau, h, steps, d_a, d_q, d_a,
+                                        d_xf);
+            break;
+        default:
+            rc = run_loop<float, double>(g, g->g32, g->V64[g->cur64], d_x0, n, tau, h, steps, d_a, d_q, d_a, d_xf);
+        }
+        if (rc == DP_OK) {
+            if (t_arrive) {
+                e = cudaMemcpyAsync(t_arrive, d_a, sizeof(double) * n, cudaMemcpyDeviceToHost, g->st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(x_final, d_xf, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, g->st);
+            } else {
+                e = cudaMemcpyAsync(alpha_out, d_a, sizeof(double) * n, cudaMemcpyDeviceToHost, g->st);
+                if (e == cudaSuccess && q_out)
+                    e = cudaMemcpyAsync(q_out, d_q, sizeof(double) * n, cudaMemcpyDeviceToHost, g->st);
+            }
+        }
+    }
+    cudaError_t e2 = cudaFreeAsync(d_buf, g->st);
+    cudaError_t e3 = cudaStreamSynchronize(g->st);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(DP_ECUDA, "closed loop: %s", cudaGetErrorString(e));
+    if (e2 != cudaSuccess || e3 != cudaSuccess)
+        return fail(DP_ECUDA, "closed loop: %s", cudaGetErrorString(e2 != cudaSuccess ? e2 : e3));
+    return DP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dp_last_error(void) { return g_err; }
+
+int dp_grid_create(const dp_grid_desc* desc, dp_grid** out)
+{
+    if (!out) return fail(DP_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(desc);
+    if (rc) return rc;
+    dp_grid* g = new (std::nothrow) dp_grid();
+    if (!g) return fail(DP_ENOMEM, "host allocation failed");
+    g->d = *desc;
+    const dp_grid_desc& d = g->d;
+    g->st = (cudaStream_t)d.stream;
+    g->fp32 = d.precision == DP_FP32;
+    g->M = d.penalty_M > 0 ? d.penalty_M : d.dt / (1.0 - d.beta);
+    g->n_box = (long long)d.n[0] * d.n[1] * d.n[2] * d.n[3];
+    g->n_rows = d.n[0] * d.n[1];
+    auto bail = [&](int code) {
+        free_grid(g);
+        return code;
+    };
+    if (cudaGetDevice(&g->device) != cudaSuccess) return bail(fail(DP_ECUDA, "no CUDA device"));
+    if (cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
+        return bail(fail(DP_ECUDA, "cannot query the device"));
+
+    // target index box (FP64, node coordinates lo + i h)
+    for (int k = 0; k < 4; ++k) {
+        g->h[k] = (d.hi[k] - d.lo[k]) / (double)(d.n[k] - 1);
+        int a = -1, b = -2;
+        for (int i = 0; i < d.n[k]; ++i) {
+            volatile double x = d.lo[k] + (double)i * g->h[k];
+            bool in = !(d.target_w[k] > 0) || std::fabs(x - d.target_c[k]) < d.target_w[k];
+            if (in) {
+                if (a < 0) a = i;
+                b = i;
+            }
+        }
+        if (a < 0) { a = 1; b = 0; }
+        g->tlo[k] = a;
+        g->thi[k] = b;
+    }
+
+    // node set
+    if ((rc = dalloc(g, &g->rows, g->n_rows))) return bail(rc);
+    int* d_err = nullptr;
+    long long* d_total = nullptr;
+    if ((rc = dalloc(g, &d_err, 1))) return bail(rc);
+    if ((rc = dalloc(g, &d_total, 1))) { cudaFree(d_err); return bail(rc); }
+    auto tidy = [&]() {
+        cudaFree(d_err);
+        cudaFree(d_total);
+        g->device_bytes -= sizeof(int) + sizeof(long long);
+    };
+    int h_err = 0;
+    long long h_total = 0;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(d_err, 0, sizeof(int), g->st)) != cudaSuccess ||
+        (e = launch_rows(g->rows, d_err, d.n[0], d.n[1], d.n[2], d.n[3], d.lo, g->h, d.mu, d.reduced, d.energy_lo,
+                         d.energy_hi, g->st)) != cudaSuccess ||
+        (e = launch_row_offsets(g->rows, g->n_rows, d.n[3], d_total, g->st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, g->st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&h_total, d_total, sizeof(long long), cudaMemcpyDeviceToHost, g->st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(g->st)) != cudaSuccess) {
+        tidy();
+        return bail(fail(DP_ECUDA, "node-set construction: %s", cudaGetErrorString(e)));
+    }
+    tidy();
+    if (h_err) return bail(fail(DP_EINVAL, "energy band is not one v_t interval per (r, v_r) row"));
+    if (h_total <= 0) return bail(fail(DP_EINVAL, "empty node set"));
+    if (h_total > 2147483647LL || (unsigned long long)h_total * (unsigned long long)(d.n[3] - 1) >= (1ULL << 40))
+        return bail(fail(DP_EINVAL, "too many stored nodes"));
+    g->n_active = h_total;
+
+    // target count from the row table
+    {
+        std::vector<int4> rows(g->n_rows);
+        if (cudaMemcpy(rows.data(), g->rows, sizeof(int4) * g->n_rows, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bail(fail(DP_ECUDA, "row table copy failed"));
+        long long nt = 0;
+        for (int ir = g->tlo[0]; ir <= g->thi[0]; ++ir)
+            for (int iv = g->tlo[1]; iv <= g->thi[1]; ++iv) {
+                const int4& R = rows[ir * d.n[1] + iv];
+                int a = std::max(R.y, g->tlo[2]), b = std::min(R.y + R.z - 1, g->thi[2]);
+                if (b >= a) nt += (long long)(b - a + 1) * (g->thi[3] - g->tlo[3] + 1);
+            }
+        g->n_target = nt;
+    }
+
+    long long n_lines = g->n_active / d.n[3];
+    if ((rc = dalloc(g, &g->lines, n_lines))) return bail(rc);
+    if ((e = launch_lines(g->rows, g->lines, d.n[0], d.n[1], d.n[2], d.n[3], g->st)) != cudaSuccess)
+        return bail(fail(DP_ECUDA, "line table: %s", cudaGetErrorString(e)));
+
+    if ((rc = dalloc(g, &g->hi64, 256)) || (rc = dalloc(g, &g->lo64, 256)) || (rc = dalloc(g, &g->hi32, 256)) ||
+        (rc = dalloc(g, &g->lo32, 256)))
+        return bail(rc);
+    if ((e = launch_trig_tables(g->hi64, g->lo64, g->hi32, g->lo32, g->st)) != cudaSuccess)
+        return bail(fail(DP_ECUDA, "angle tables: %s", cudaGetErrorString(e)));
+
+    size_t es = g->fp32 ? sizeof(float) : sizeof(double);
+    for (int b = 0; b < 2; ++b) {
+        if ((e = cudaMalloc(&g->V[b], es * g->n_active)) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(e == cudaErrorMemoryAllocation ? DP_ENOMEM : DP_ECUDA, "value buffer: %s",
+                             cudaGetErrorString(e)));
+        }
+        g->device_bytes += (long long)(es * g->n_active);
+        if (cudaMemsetAsync(g->V[b], 0, es * g->n_active, g->st) != cudaSuccess)
+            return bail(fail(DP_ECUDA, "memset failed"));
+    }
+    if ((rc = dalloc(g, &g->code, g->n_active))) return bail(rc);
+    if ((rc = dalloc(g, &g->ctl, 1))) return bail(rc);
+    if ((rc = dalloc(g, &g->ring, kRing))) return bail(rc);
+    if (cudaMemsetAsync(g->code, 0, sizeof(uint16_t) * g->n_active, g->st) != cudaSuccess ||
+        cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), g->st) != cudaSuccess)
+        return bail(fail(DP_ECUDA, "memset failed"));
+    if (cudaMallocHost(&g->h_ctl, sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost(&g->h_ring, sizeof(unsigned long long) * kRing) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(DP_ENOMEM, "pinned host allocation failed"));
+    }
+
+    fill_geo(g, g->g64);
+    fill_geo(g, g->g32);
+    g->g64.tab_hi = g->hi64;
+    g->g64.tab_lo = g->lo64;
+    g->g32.tab_hi = g->hi32;
+    g->g32.tab_lo = g->lo32;
+    if ((e = cudaStreamSynchronize(g->st)) != cudaSuccess)
+        return bail(fail(DP_ECUDA, "grid setup: %s", cudaGetErrorString(e)));
+    *out = g;
+    return DP_OK;
+}
+
+int dp_grid_destroy(dp_grid* grid)
+{
+    free_grid(grid);
+    return DP_OK;
+}
+
+int dp_grid_get_info(const dp_grid* g, dp_grid_info* info)
+{
+    if (!g || !info) return fail(DP_EINVAL, "NULL argument");
+    info->n_box = g->n_box;
+    info->n_active = g->n_active;
+    info->n_target = g->n_target;
+    info->penalty_M = g->M;
+    info->fp64_values = (g->fp32 && g->fp64_values) || !g->fp32;
+    info->device_bytes = g->device_bytes;
+    return DP_OK;
+}
+
+int dp_get_active_index(const dp_grid* cg, int64_t* box_index, int64_t count)
+{
+    dp_grid* g = const_cast<dp_grid*>(cg);
+    if (!g || !box_index) return fail(DP_EINVAL, "NULL argument");
+    if (count != g->n_active) return fail(DP_EINVAL, "count %lld != stored nodes %lld", (long long)count, g->n_active);
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
+    if (!g->scratch64) {
+        int rc = dalloc(g, &g->scratch64, g->n_active);
+        if (rc) return rc;
+    }
+    CK(launch_box_index(g->g64, g->scratch64, g->st));
+    CK(cudaMemcpyAsync(box_index, g->scratch64, sizeof(int64_t) * count, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    return DP_OK;
+}
+
+static int ensure_staging(dp_grid* g)
+{
+    if (g->staging) return DP_OK;
+    return dalloc(g, &g->staging, g->n_active);
+}
+
+int dp_set_value(dp_grid* g, const double* host_V, int64_t count)
+{
+    if (!g || !host_V) return fail(DP_EINVAL, "NULL argument");
+    if (count != g->n_active) return fail(DP_EINVAL, "count %lld != stored nodes %lld", (long long)count, g->n_active);
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
+    int rc = ensure_staging(g);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(g->staging, host_V, sizeof(double) * count, cudaMemcpyHostToDevice, g->st));
+    CK(launch_store_value(g->staging, g->V[g->cur], g->fp32, (int)count, g->g64, &g->ctl->nonfinite, g->st));
+    CK(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    if (g->h_ctl->nonfinite) return fail(DP_ENONFINITE, "V holds a non-finite value; the resident V is unchanged");
+    g->fp64_values = false;
+    return DP_OK;
+}
+
+int dp_get_value(const dp_grid* cg, double* host_V, int64_t count)
+{
+    dp_grid* g = const_cast<dp_grid*>(cg);
+    if (!g || !host_V) return fail(DP_EINVAL, "NULL argument");
+    if (count != g->n_active) return fail(DP_EINVAL, "count %lld != stored nodes %lld", (long long)count, g->n_active);
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
+    if (!g->fp32 || g->fp64_values) {
+        const double* src = g->fp32 ? g->V64[g->cur64] : (const double*)g->V[g->cur];
+        CK(cudaMemcpyAsync(host_V, src, sizeof(double) * count, cudaMemcpyDeviceToHost, g->st));
+    } else {
+        int rc = ensure_staging(g);
+        if (rc) return rc;
+        CK(launch_load_value(g->V[g->cur], g->staging, 1, (int)count, g->st));
+        CK(cudaMemcpyAsync(host_V, g->staging, sizeof(double) * count, cudaMemcpyDeviceToHost, g->st));
+    }
+    CK(cudaStreamSynchronize(g->st));
+    return DP_OK;
+}
+
+int dp_set_policy(dp_grid* g, const uint16_t* host_codes, int64_t count)
+{
+    if (!g || !host_codes) return fail(DP_EINVAL, "NULL argument");
+    if (count != g->n_active) return fail(DP_EINVAL, "count %lld != stored nodes %lld", (long long)count, g->n_active);
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
+    CK(cudaMemcpyAsync(g->code, host_codes, sizeof(uint16_t) * count, cudaMemcpyHostToDevice, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    return DP_OK;
+}
+
+int dp_get_policy(const dp_grid* g, uint16_t* host_codes, int64_t count)
+{
+    if (!g || !host_codes) return fail(DP_EINVAL, "NULL argument");
+    if (count != g->n_active) return fail(DP_EINVAL, "count %lld != stored nodes %lld", (long long)count, g->n_active);
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
+    CK(cudaMemcpyAsync(host_codes, g->code, sizeof(uint16_t) * count, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    return DP_OK;
+}
+
+int dp_bellman_sweep(dp_grid* g, int32_t mode, double* residual)
+{
+    if (!g) return fail(DP_EINVAL, "grid is NULL");
+    if (mode < DP_SWEEP_VI || mode > DP_SWEEP_EVAL) return fail(DP_EINVAL, "unknown sweep mode %d", mode);
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
+    int rc;
+    if ((rc = reset_ctl(g)) || (rc = clear_ring(g, 0, 1))) return rc;
+    CK(enqueue_sweep(g, mode, 0, 0, 0.0));
+    if ((rc = fetch(g, 0, 1))) return rc;
+    advance(g, 1);
+    if (residual) *residual = ring_value(g, 0);
+    return finish_nonfinite(g);
+}
+
+int dp_value_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
+{
+    if (!g || !o) return fail(DP_EINVAL, "NULL argument");
+    if (o->max_sweeps < 0 || !(o->tol >= 0)) return fail(DP_EINVAL, "bad tol or max_sweeps");
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
+    double t0 = now_ms();
+    dp_solve_stats S;
+    memset(&S, 0, sizeof S);
+    SweepTimer T;
+    T.on = o->time_kernels != 0;
+    T.st = g->st;
+    int rc;
+    if (!o->warm && (rc = zero_value(g))) return rc;
+    if ((rc = reset_ctl(g))) return rc;
+    const int tk = store_of(g) == kStoreMix ? kTImp64 : kTVI;
+    long long s = 0, done = -1, chunk = 8;
+    double res = INFINITY;
+    while (s < o->max_sweeps) {
+        long long c = std::min<long long>(chunk, o->max_sweeps - s);
+        if ((rc = clear_ring(g, s, c))) return rc;
+        for (long long k = 0; k < c; ++k) {
+            CK(T.begin(tk));
+            CK(enqueue_sweep(g, DP_SWEEP_VI, s + k, s + k > 0, o->tol));
+            CK(T.end());
+            S.launches++;
+        }
+        if ((rc = fetch(g, s, c))) return rc;
+        CK(T.collect());
+        if (g->h_ctl->stop) {
+            done = g->h_ctl->stop_sweep;
+            res = ring_value(g, done - 1);
+            break;
+        }
+        res = ring_value(g, s + c - 1);
+        s += c;
+        if (g->h_ctl->nonfinite) { done = s; break; }
+        if (res < o->tol) { done = s; break; }
+        chunk = std::min<long long>(chunk * 2, kMaxChunk);
+    }
+    bool conv = done >= 0 && !g->h_ctl->nonfinite;
+    if (done < 0) done = s;
+    advance(g, done);
+    S.sweeps_vi = done;
+    S.residual = res;
+    S.converged = conv;
+    S.node_updates = done * updates_per_sweep(g);
+    S.ms_vi = T.ms[kTVI] + T.ms[kTImp64];
+    S.ms_wall = now_ms() - t0;
+    if (stats) *stats = S;
+    if ((rc = finish_nonfinite(g))) return rc;
+    if (!conv) return fail(DP_ENOCONV, "no convergence within %lld sweeps (residual %g)", (long long)o->max_sweeps, res);
+    return DP_OK;
+}
+
+int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
+{
+    if (!g || !o) return fail(DP_EINVAL, "NULL argument");
+    if (o->max_sweeps < 0 || o->n_eval < 0 || !(o->tol >= 0)) return fail(DP_EINVAL, "bad options");
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
+    double t0 = now_ms();
+    dp_solve_stats S;
+    memset(&S, 0, sizeof S);
+    SweepTimer T;
+    T.on = o->time_kernels != 0;
+    T.st = g->st;
+    int rc;
+    if (!o->warm && (rc = zero_value(g))) return rc;
+    if ((rc = reset_ctl(g))) return rc;
+
+    const long long per = 1 + o->n_eval;                 // sweeps per outer iteration
+    const long long per_chunk = std::max<long long>(1, kMaxChunk / per / 4);
+    double switch_tol = o->switch_tol > 0 ? o->switch_tol : 16.0 * 1.1920928955078125e-07 * g->M;
+    long long outer = 0, t = 0;    // outer iterations and sweeps of the current phase
+    double res = INFINITY, best = INFINITY;
+    int stall = 0;
+    bool conv = false, first_full = !o->warm;
+    while (outer < o->max_sweeps) {
+        const bool mix = store_of(g) == kStoreMix;
+        long long n_out = std::min<long long>(per_chunk, o->max_sweeps - outer);
+        if (g->fp32 && !mix && o->polish) n_out = 1;     // watch for the FP32 stall each step
+        if ((rc = clear_ring(g, t, n_out * per))) return rc;
+        for (long long q = 0; q < n_out; ++q) {
+            long long ti = t + q * per;
+            int mode = (first_full && q == 0) || !o->walk ? DP_SWEEP_IMPROVE_FULL : DP_SWEEP_IMPROVE_WALK;
+            CK(T.begin(mix ? kTImp64 : kTImp));
+            // without evaluation sweeps each improvement checks the previous one
+            CK(enqueue_sweep(g, mode, ti, o->n_eval == 0 && ti > 0, o->tol));
+            CK(T.end());
+            for (int e = 0; e < o->n_eval; ++e) {
+                CK(T.begin(mix ? kTEval64 : kTEval));
+                CK(enqueue_sweep(g, DP_SWEEP_EVAL, ti + 1 + e, e == 0, o->tol));
+                CK(T.end());
+            }
+            S.launches += per;
+        }
+        first_full = false;
+        if ((rc = fetch(g, t, n_out * per))) return rc;
+        CK(T.collect());
+        long long ran = n_out * per;
+        long long imp_done = n_out;
+        if (g->h_ctl->stop) {
+            // stop_sweep is the first evaluation sweep after the converged improvement
+            ran = g->h_ctl->stop_sweep - t;
+            imp_done = (ran + per - 1) / per;
+            res = ring_value(g, g->h_ctl->stop_sweep - 1);
+            conv = true;
+        } else {
+            res = ring_value(g, t + (n_out - 1) * per);
+            // an evaluation sweep checks its improvement on the device; only a
+            // chunk-final improvement without evaluations is checked here
+            if (o->n_eval == 0 && res < o->tol) conv = true;
+        }
+        long long evals = ran - imp_done;
+        if (mix) { S.sweeps_improve_fp64 += imp_done; S.sweeps_eval_fp64 += evals; }
+        else { S.sweeps_improve += imp_done; S.sweeps_eval += evals; }
+        outer += imp_done;
+        t += ran;
+        if (g->h_ctl->nonfinite) break;
+        if (conv) break;
+        // FP32 -> FP64 switch once the FP32 residual is small or stalls
+        if (g->fp32 && !mix && o->polish) {
+            if (res < best * 0.999) { best = res; stall = 0; } else ++stall;
+            if (res < switch_tol || stall >= 3) {
+                advance(g, t);
+                t = 0;
+                if ((rc = ensure_fp64(g))) return rc;
+                CK(launch_widen((const float*)g->V[g->cur], g->V64[g->cur64], (int)g->n_active, g->st));
+                g->fp64_values = true;
+                if ((rc = reset_ctl(g))) return rc;
+            }
+        }
+    }
+    advance(g, t);
+    S.residual = res;
+    S.converged = conv && !g->h_ctl->nonfinite;
+    S.node_updates = (S.sweeps_improve + S.sweeps_eval + S.sweeps_improve_fp64 + S.sweeps_eval_fp64) *
+                     updates_per_sweep(g);
+    S.ms_improve = T.ms[kTImp];
+    S.ms_eval = T.ms[kTEval];
+    S.ms_improve_fp64 = T.ms[kTImp64];
+    S.ms_eval_fp64 = T.ms[kTEval64];
+    S.ms_wall = now_ms() - t0;
+    if (stats) *stats = S;
+    if ((rc = finish_nonfinite(g))) return rc;
+    if (!S.converged)
+        return fail(DP_ENOCONV, "no convergence within %lld improvement sweeps (residual %g)",
+                    (long long)o->max_sweeps, res);
+    return DP_OK;
+}
+
+int dp_feedback_control(const dp_grid* g, const double* states, int32_t n, double tau, double* alpha_out,
+                        double* q_out)
+{
+    if (!g || (n > 0 && (!states || !alpha_out))) return fail(DP_EINVAL, "NULL argument");
+    if (n < 0 || !(tau > 0) || !std::isfinite(tau)) return fail(DP_EINVAL, "bad n or tau");
+    if (n == 0) return DP_OK;
+    return loop_common(g, states, n, tau, tau, 0.0, alpha_out, q_out, nullptr, nullptr);
+}
+
+int dp_simulate_closed_loop(const dp_grid* g, const double* x0, int32_t n, double tau, double h_rk4, double t_max,
+                            double* t_arrive, double* x_final)
+{
+    if (!g || (n > 0 && (!x0 || !t_arrive || !x_final))) return fail(DP_EINVAL, "NULL argument");
+    if (n < 0 || !(tau > 0) || !(h_rk4 > 0) || !(t_max > 0) || !std::isfinite(t_max))
+        return fail(DP_EINVAL, "bad n, tau, h_rk4 or t_max");
+    if (n == 0) return DP_OK;
+    return loop_common(g, x0, n, tau, h_rk4, t_max, nullptr, nullptr, t_arrive, x_final);
+}
+
+}  // extern "C"

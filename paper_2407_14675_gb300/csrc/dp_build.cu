@@ -1,0 +1,203 @@
+// dp_build.cu -- grid construction kernels: angle tables, the (energy-band
+// reduced) node set as per-row v_t intervals with compact offsets, the line
+// table used to decode a compact index, and value conversions.
+//
+// Reduced grid (§3 "Grid and polar coordinates": the computational domain is
+// cut down to where optimal trajectories stay): a node is stored iff its
+// specific energy (v_r^2 + v_t^2)/2 - mu/r lies in [e_lo, e_hi].  For v_t > 0
+// the energy rises with v_t, so each (i_r, i_vr) row keeps one contiguous run
+// of v_t nodes and all masses; the row table stores its first compact index,
+// first v_t index and length.  The energy is evaluated in FP64 with
+// explicitly rounded operations (no contraction), the same operation order as
+// the CPU oracle, so both sides decide membership identically.
+#include "dp_host.h"
+
+namespace dpk {
+
+__global__ void trig_tables_kernel(double2* hi64, double2* lo64, float2* hi32, float2* lo32)
+{
+    int k = threadIdx.x;   // 256 threads
+    double s, c;
+    sincospi((double)k / 128.0, &s, &c);      // 2 pi (k * 256) / 65536
+    hi64[k] = make_double2(s, c);
+    hi32[k] = make_float2((float)s, (float)c);
+    sincospi((double)k / 32768.0, &s, &c);    // 2 pi k / 65536
+    lo64[k] = make_double2(s, c);
+    lo32[k] = make_float2((float)s, (float)c);
+}
+
+cudaError_t launch_trig_tables(double2* hi64, double2* lo64, float2* hi32, float2* lo32, cudaStream_t st)
+{
+    trig_tables_kernel<<<1, 256, 0, st>>>(hi64, lo64, hi32, lo32);
+    return cudaGetLastError();
+}
+
+struct BoxGeom {
+    int n[4];
+    double lo[4], h[4];
+};
+
+__device__ __forceinline__ double node_coord(const BoxGeom& b, int d, int i)
+{
+    return __dadd_rn(b.lo[d], __dmul_rn((double)i, b.h[d]));
+}
+
+// One thread per (i_r, i_vr) row: the contiguous v_t run of stored nodes.
+__global__ void rows_kernel(int4* rows, int* err, BoxGeom b, double mu, int reduced, double e_lo, double e_hi)
+{
+    int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= b.n[0] * b.n[1]) return;
+    int ir = row / b.n[1], iv = row % b.n[1];
+    if (!reduced) {
+        rows[row] = make_int4(0, 0, b.n[2], 0);
+        return;
+    }
+    double r = node_coord(b, 0, ir), vr = node_coord(b, 1, iv);
+    int first = -1, last = -1, count = 0;
+    for (int it = 0; it < b.n[2]; ++it) {
+        double vt = node_coord(b, 2, it);
+        double e = __dsub_rn(__dmul_rn(0.5, __dadd_rn(__dmul_rn(vr, vr), __dmul_rn(vt, vt))), __ddiv_rn(mu, r));
+        if (e >= e_lo && e <= e_hi) {
+            if (first < 0) first = it;
+            last = it;
+            ++count;
+        }
+    }
+    if (count > 0 && last - first + 1 != count) atomicOr(err, 1);
+    rows[row] = make_int4(0, count > 0 ? first : 0, count, 0);
+}
+
+cudaError_t launch_rows(int4* rows, int* err, int n0, int n1, int n2, int n3, const double* lo,
+                        const double* h, double mu, int reduced, double e_lo, double e_hi, cudaStream_t st)
+{
+    BoxGeom b;
+    b.n[0] = n0; b.n[1] = n1; b.n[2] = n2; b.n[3] = n3;
+    for (int d = 0; d < 4; ++d) { b.lo[d] = lo[d]; b.h[d] = h[d]; }
+    int n_rows = n0 * n1;
+    rows_kernel<<<(n_rows + 255) / 256, 256, 0, st>>>(rows, err, b, mu, reduced, e_lo, e_hi);
+    return cudaGetLastError();
+}
+
+// Exclusive prefix sum of len * n_m over rows (one block, chunked): the
+// compact index of each row's first node.  total receives the node count.
+__global__ void row_offsets_kernel(int4* rows, int n_rows, int n_m, long long* total)
+{
+    __shared__ long long part[1024];
+    const int T = blockDim.x, t = threadIdx.x;
+    const int chunk = (n_rows + T - 1) / T;
+    const int a = t * chunk, b = min(a + chunk, n_rows);
+    long long s = 0;
+    for (int r = a; r < b; ++r) s += (long long)rows[r].z * n_m;
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < T; o <<= 1) {       // inclusive Hillis-Steele scan
+        long long v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    long long run = part[t] - s;
+    for (int r = a; r < b; ++r) {
+        rows[r].x = (int)run;
+        run += (long long)rows[r].z * n_m;
+    }
+    if (t == T - 1) *total = part[t];
+}
+
+cudaError_t launch_row_offsets(int4* rows, int n_rows, int n_m, long long* total, cudaStream_t st)
+{
+    row_offsets_kernel<<<1, 1024, 0, st>>>(rows, n_rows, n_m, total);
+    return cudaGetLastError();
+}
+
+// One thread per (row, i_vt): the packed line table.
+__global__ void lines_kernel(const int4* rows, unsigned* lines, int n0, int n1, int n2, int n_m)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n0 * n1 * n2) return;
+    int row = (int)(t / n2), it = (int)(t % n2);
+    int4 R = rows[row];
+    if (it < R.y || it >= R.y + R.z) return;
+    int ir = row / n1, iv = row % n1;
+    int line = R.x / n_m + (it - R.y);
+    lines[line] = (unsigned)ir | ((unsigned)iv << 10) | ((unsigned)it << 20);
+}
+
+cudaError_t launch_lines(const int4* rows, unsigned* lines, int n0, int n1, int n2, int n_m, cudaStream_t st)
+{
+    long long n = (long long)n0 * n1 * n2;
+    lines_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rows, lines, n0, n1, n2, n_m);
+    return cudaGetLastError();
+}
+
+// Host values (FP64, compact order) into storage precision; target nodes 0.
+// A first pass flags non-finite input; the store pass then leaves V untouched.
+__global__ void check_finite_kernel(const double* src, int n, int* bad)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n && !isfinite(src[j])) atomicOr(bad, 1);
+}
+
+__global__ void store_value_kernel(const double* src, void* dst, int fp32, Geo<double> g, const int* bad)
+{
+    if (*bad) return;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.n_nodes) return;
+    int i[4];
+    decode_node(g, j, i);
+    double v = in_target(g, i) ? 0.0 : src[j];
+    if (fp32) ((float*)dst)[j] = (float)v;
+    else ((double*)dst)[j] = v;
+}
+
+cudaError_t launch_store_value(const double* src, void* dst, int fp32, int n, const Geo<double>& g, int* bad,
+                               cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    check_finite_kernel<<<(n + 255) / 256, 256, 0, st>>>(src, n, bad);
+    store_value_kernel<<<(n + 255) / 256, 256, 0, st>>>(src, dst, fp32, g, bad);
+    return cudaGetLastError();
+}
+
+__global__ void load_value_kernel(const void* src, double* dst, int fp32, int n)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    dst[j] = fp32 ? (double)((const float*)src)[j] : ((const double*)src)[j];
+}
+
+cudaError_t launch_load_value(const void* src, double* dst, int fp32, int n, cudaStream_t st)
+{
+    load_value_kernel<<<(n + 255) / 256, 256, 0, st>>>(src, dst, fp32, n);
+    return cudaGetLastError();
+}
+
+__global__ void widen_kernel(const float* src, double* dst, int n)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) dst[j] = (double)src[j];
+}
+
+cudaError_t launch_widen(const float* src, double* dst, int n, cudaStream_t st)
+{
+    widen_kernel<<<(n + 255) / 256, 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+__global__ void box_index_kernel(Geo<double> g, long long* out)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.n_nodes) return;
+    int i[4];
+    decode_node(g, j, i);
+    out[j] = (((long long)i[0] * g.n[1] + i[1]) * g.n[2] + i[2]) * g.n[3] + i[3];
+}
+
+cudaError_t launch_box_index(const Geo<double>& g, long long* out, cudaStream_t st)
+{
+    box_index_kernel<<<(g.n_nodes + 255) / 256, 256, 0, st>>>(g, out);
+    return cudaGetLastError();
+}
+
+}  // namespace dpk

@@ -1,0 +1,76 @@
+// dp_host.h -- launch descriptors shared by the host driver and the kernel
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dp_device.cuh"
+
+namespace dpk {
+
+template <typename G, typename S>
+struct SweepLaunch {
+    Geo<G> g;
+    const S* Vin;
+    S* Vout;
+    uint16_t* code;
+    Ctl* ctl;
+    unsigned long long* ring;   // FP64 residual bits, one slot per sweep
+    int ring_mask;
+    long long sweep;            // sweep index within the solve (ring slot)
+    int check_prev;             // 1: stop if the previous sweep's residual < tol
+    double tol;
+    int mode;                   // kVI, kImproveFull, kImproveWalk, kEval
+    int dyn;
+    int reduced;
+    cudaStream_t stream;
+    int sm_count;
+};
+
+cudaError_t launch_sweep(const SweepLaunch<double, double>& L);
+cudaError_t launch_sweep(const SweepLaunch<float, float>& L);
+cudaError_t launch_sweep(const SweepLaunch<float, double>& L);
+
+// Feedback (steps == 0) or closed loop (steps > 0) over n states.
+template <typename G, typename S>
+struct LoopLaunch {
+    Geo<G> g;
+    const S* V;
+    const double* x0;        // n x 4 (device)
+    int n;
+    double tau, beta_tau;    // feedback step and its discount beta^(tau/dt)
+    double h;                // RK4 step
+    long long steps;
+    double tgt_c[4], tgt_w[4];
+    double mu, accel, mdot, lo_m;
+    const double2* tab_hi64;
+    const double2* tab_lo64;
+    double* alpha;           // n (feedback)
+    double* q;               // n (feedback)
+    double* t_arrive;        // n (closed loop)
+    double* x_final;         // n x 4 (closed loop)
+    int dyn;
+    int reduced;
+    cudaStream_t stream;
+};
+
+cudaError_t launch_loop(const LoopLaunch<double, double>& L);
+cudaError_t launch_loop(const LoopLaunch<float, float>& L);
+cudaError_t launch_loop(const LoopLaunch<float, double>& L);
+
+// Grid construction (node set, tables) and value conversions.
+cudaError_t launch_trig_tables(double2* hi64, double2* lo64, float2* hi32, float2* lo32, cudaStream_t st);
+cudaError_t launch_rows(int4* rows, int* err, int n0, int n1, int n2, int n3, const double* lo,
+                        const double* h, double mu, int reduced, double e_lo, double e_hi,
+                        cudaStream_t st);
+cudaError_t launch_row_offsets(int4* rows, int n_rows, int n_m, long long* total, cudaStream_t st);
+cudaError_t launch_lines(const int4* rows, unsigned* lines, int n0, int n1, int n2, int n_m,
+                         cudaStream_t st);
+cudaError_t launch_store_value(const double* src, void* dst, int fp32, int n, const Geo<double>& g, int* bad,
+                               cudaStream_t st);
+cudaError_t launch_load_value(const void* src, double* dst, int fp32, int n, cudaStream_t st);
+cudaError_t launch_widen(const float* src, double* dst, int n, cudaStream_t st);
+cudaError_t launch_box_index(const Geo<double>& g, long long* out, cudaStream_t st);
+
+}  // namespace dpk

@@ -1,0 +1,337 @@
+"""Python binding of the C ABI in include/dp.h (argument marshalling only).
+
+Every function here has the name of the C call it wraps and does nothing but
+convert arguments: all computation runs in libdp.so's CUDA kernels.  Host
+arrays may be numpy arrays or (pinned) CPU torch tensors; they are passed by
+pointer.  ``load()`` raises if the library has not been built: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import workloads as W
+
+DP_OK, DP_EINVAL, DP_ENOMEM, DP_ECUDA, DP_ENOCONV, DP_ETIMEOUT, DP_ENONFINITE = range(7)
+DP_FP64, DP_FP32 = 0, 1
+DP_DYN_ORBIT, DP_DYN_UNIT_SPEED = 0, 1
+DP_SWEEP_VI, DP_SWEEP_IMPROVE_FULL, DP_SWEEP_IMPROVE_WALK, DP_SWEEP_EVAL = 0, 1, 2, 3
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdp.so")
+
+
+class dp_grid_desc(C.Structure):
+    _fields_ = [
+        ("n", C.c_int32 * 4),
+        ("lo", C.c_double * 4),
+        ("hi", C.c_double * 4),
+        ("dynamics", C.c_int32),
+        ("mu", C.c_double),
+        ("accel", C.c_double),
+        ("exhaust_c", C.c_double),
+        ("dt", C.c_double),
+        ("beta", C.c_double),
+        ("penalty_M", C.c_double),
+        ("target_c", C.c_double * 4),
+        ("target_w", C.c_double * 4),
+        ("n_angles", C.c_int32),
+        ("refine", C.c_int32),
+        ("refine_tol", C.c_double),
+        ("reduced", C.c_int32),
+        ("energy_lo", C.c_double),
+        ("energy_hi", C.c_double),
+        ("precision", C.c_int32),
+        ("stream", C.c_void_p),
+    ]
+
+
+class dp_solve_opts(C.Structure):
+    _fields_ = [
+        ("tol", C.c_double),
+        ("max_sweeps", C.c_int64),
+        ("n_eval", C.c_int32),
+        ("walk", C.c_int32),
+        ("warm", C.c_int32),
+        ("polish", C.c_int32),
+        ("switch_tol", C.c_double),
+        ("time_kernels", C.c_int32),
+    ]
+
+
+class dp_solve_stats(C.Structure):
+    _fields_ = [
+        ("sweeps_vi", C.c_int64),
+        ("sweeps_improve", C.c_int64),
+        ("sweeps_eval", C.c_int64),
+        ("sweeps_improve_fp64", C.c_int64),
+        ("sweeps_eval_fp64", C.c_int64),
+        ("residual", C.c_double),
+        ("converged", C.c_int32),
+        ("ms_wall", C.c_double),
+        ("ms_vi", C.c_double),
+        ("ms_improve", C.c_double),
+        ("ms_eval", C.c_double),
+        ("ms_improve_fp64", C.c_double),
+        ("ms_eval_fp64", C.c_double),
+        ("node_updates", C.c_int64),
+        ("launches", C.c_int64),
+    ]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class dp_grid_info(C.Structure):
+    _fields_ = [
+        ("n_box", C.c_int64),
+        ("n_active", C.c_int64),
+        ("n_target", C.c_int64),
+        ("penalty_M", C.c_double),
+        ("fp64_values", C.c_int32),
+        ("device_bytes", C.c_int64),
+    ]
+
+
+class DPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("dp error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+_P = C.c_void_p
+_dp = C.POINTER(C.c_double)
+
+
+def load(path: Optional[str] = None):
+    """Load libdp.so (built by paper_2407_14675_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libdp.so is not built (%s): run __graft_entry__.build()" % path)
+    L = C.CDLL(path)
+    sigs = {
+        "dp_grid_create": [C.POINTER(dp_grid_desc), C.POINTER(_P)],
+        "dp_grid_destroy": [_P],
+        "dp_grid_get_info": [_P, C.POINTER(dp_grid_info)],
+        "dp_get_active_index": [_P, _P, C.c_int64],
+        "dp_set_value": [_P, _P, C.c_int64],
+        "dp_get_value": [_P, _P, C.c_int64],
+        "dp_set_policy": [_P, _P, C.c_int64],
+        "dp_get_policy": [_P, _P, C.c_int64],
+        "dp_bellman_sweep": [_P, C.c_int32, _dp],
+        "dp_value_iterate": [_P, C.POINTER(dp_solve_opts), C.POINTER(dp_solve_stats)],
+        "dp_policy_iterate": [_P, C.POINTER(dp_solve_opts), C.POINTER(dp_solve_stats)],
+        "dp_feedback_control": [_P, _P, C.c_int32, C.c_double, _P, _P],
+        "dp_simulate_closed_loop": [_P, _P, C.c_int32, C.c_double, C.c_double, C.c_double, _P, _P],
+    }
+    for name, args in sigs.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.dp_last_error.argtypes = []
+    L.dp_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def dp_last_error() -> str:
+    return load().dp_last_error().decode()
+
+
+def _check(rc: int, allow=(DP_OK,)) -> int:
+    if rc not in allow:
+        raise DPError(rc, dp_last_error())
+    return rc
+
+
+def _host_ptr(a, dtype):
+    """Pointer to a contiguous host buffer (numpy array or CPU torch tensor)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("expected a contiguous %s array" % np.dtype(dtype))
+        return C.c_void_p(a.ctypes.data)
+    # torch tensor on the host
+    if getattr(a, "is_cuda", False):
+        raise TypeError("host buffer expected")
+    return C.c_void_p(a.data_ptr())
+
+
+def current_stream() -> int:
+    """The current torch CUDA stream handle (0 without CUDA)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return 0
+
+
+def desc_from_problem(p: "W.Problem", stream: Optional[int] = None) -> dp_grid_desc:
+    d = dp_grid_desc()
+    d.n[:] = list(p.n)
+    d.lo[:] = list(p.lo)
+    d.hi[:] = list(p.hi)
+    d.dynamics = p.dynamics
+    d.mu, d.accel, d.exhaust_c = p.mu, p.accel, p.exhaust_c
+    d.dt, d.beta, d.penalty_M = p.dt, p.beta, p.penalty_M
+    d.target_c[:] = list(p.target_c)
+    d.target_w[:] = list(p.target_w)
+    d.n_angles, d.refine, d.refine_tol = p.n_angles, p.refine, p.refine_tol
+    d.reduced, d.energy_lo, d.energy_hi = p.reduced, p.energy_lo, p.energy_hi
+    d.precision = p.precision
+    d.stream = current_stream() if stream is None else stream
+    return d
+
+
+def dp_grid_create(desc: dp_grid_desc) -> int:
+    h = _P()
+    _check(load().dp_grid_create(C.byref(desc), C.byref(h)))
+    return h.value
+
+
+def dp_grid_destroy(grid: int) -> None:
+    _check(load().dp_grid_destroy(grid))
+
+
+def dp_grid_get_info(grid: int) -> dict:
+    info = dp_grid_info()
+    _check(load().dp_grid_get_info(grid, C.byref(info)))
+    return {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def dp_get_active_index(grid: int, count: int) -> np.ndarray:
+    out = np.empty(count, np.int64)
+    _check(load().dp_get_active_index(grid, _host_ptr(out, np.int64), count))
+    return out
+
+
+def dp_set_value(grid: int, V) -> None:
+    _check(load().dp_set_value(grid, _host_ptr(V, np.float64), len(V)))
+
+
+def dp_get_value(grid: int, count: int, out=None):
+    out = np.empty(count, np.float64) if out is None else out
+    _check(load().dp_get_value(grid, _host_ptr(out, np.float64), count))
+    return out
+
+
+def dp_set_policy(grid: int, codes) -> None:
+    _check(load().dp_set_policy(grid, _host_ptr(codes, np.uint16), len(codes)))
+
+
+def dp_get_policy(grid: int, count: int) -> np.ndarray:
+    out = np.empty(count, np.uint16)
+    _check(load().dp_get_policy(grid, _host_ptr(out, np.uint16), count))
+    return out
+
+
+def dp_bellman_sweep(grid: int, mode: int) -> float:
+    r = C.c_double(0)
+    _check(load().dp_bellman_sweep(grid, mode, C.byref(r)))
+    return r.value
+
+
+def make_opts(tol=1e-6, max_sweeps=100000, n_eval=20, walk=1, warm=0, polish=1, switch_tol=0.0,
+              time_kernels=0) -> dp_solve_opts:
+    o = dp_solve_opts()
+    o.tol, o.max_sweeps, o.n_eval, o.walk, o.warm = tol, max_sweeps, n_eval, walk, warm
+    o.polish, o.switch_tol, o.time_kernels = polish, switch_tol, time_kernels
+    return o
+
+
+def dp_value_iterate(grid: int, opts: dp_solve_opts):
+    s = dp_solve_stats()
+    rc = _check(load().dp_value_iterate(grid, C.byref(opts), C.byref(s)), allow=(DP_OK, DP_ENOCONV))
+    return rc, s
+
+
+def dp_policy_iterate(grid: int, opts: dp_solve_opts):
+    s = dp_solve_stats()
+    rc = _check(load().dp_policy_iterate(grid, C.byref(opts), C.byref(s)), allow=(DP_OK, DP_ENOCONV))
+    return rc, s
+
+
+def dp_feedback_control(grid: int, states, tau: float):
+    st = np.ascontiguousarray(states, np.float64).reshape(-1, 4)
+    n = len(st)
+    alpha = np.empty(n)
+    q = np.empty(n)
+    _check(load().dp_feedback_control(grid, _host_ptr(st, np.float64), n, tau, _host_ptr(alpha, np.float64),
+                                      _host_ptr(q, np.float64)))
+    return alpha, q
+
+
+def dp_simulate_closed_loop(grid: int, x0, tau: float, h_rk4: float, t_max: float):
+    x = np.ascontiguousarray(x0, np.float64).reshape(-1, 4)
+    n = len(x)
+    ta = np.empty(n)
+    xf = np.empty((n, 4))
+    _check(load().dp_simulate_closed_loop(grid, _host_ptr(x, np.float64), n, tau, h_rk4, t_max,
+                                          _host_ptr(ta, np.float64), _host_ptr(xf, np.float64)))
+    return ta, xf
+
+
+class Grid:
+    """Owning wrapper of a dp_grid handle (destroyed on close / exit)."""
+
+    def __init__(self, p: "W.Problem", stream: Optional[int] = None):
+        self.p = p
+        self.h = dp_grid_create(desc_from_problem(p, stream))
+        self.info = dp_grid_get_info(self.h)
+        self.n = self.info["n_active"]
+
+    def close(self):
+        if self.h:
+            dp_grid_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def active_index(self):
+        return dp_get_active_index(self.h, self.n)
+
+    def set_value(self, V):
+        dp_set_value(self.h, V)
+
+    def get_value(self):
+        return dp_get_value(self.h, self.n)
+
+    def set_policy(self, codes):
+        dp_set_policy(self.h, codes)
+
+    def get_policy(self):
+        return dp_get_policy(self.h, self.n)
+
+    def sweep(self, mode):
+        return dp_bellman_sweep(self.h, mode)
+
+    def value_iterate(self, **kw):
+        return dp_value_iterate(self.h, make_opts(**kw))
+
+    def policy_iterate(self, **kw):
+        return dp_policy_iterate(self.h, make_opts(**kw))
+
+    def feedback(self, states, tau):
+        return dp_feedback_control(self.h, states, tau)
+
+    def simulate(self, x0, tau, h_rk4, t_max):
+        return dp_simulate_closed_loop(self.h, x0, tau, h_rk4, t_max)

@@ -1,0 +1,69 @@
+"""The C-ABI library loads and exports every entry point include/dp.h declares
+(no GPU needed: nothing here launches a kernel)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:int|const char\*)\s+(dp_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2407_14675_gb300 import build, dp
+    build.build()
+    return dp.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ["dp_grid_create", "dp_grid_destroy", "dp_value_iterate", "dp_policy_iterate",
+              "dp_feedback_control", "dp_simulate_closed_loop", "dp_get_value", "dp_get_policy",
+              "dp_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_uses_the_same_names(lib):
+    from paper_2407_14675_gb300 import dp
+    for n in _declared():
+        assert hasattr(dp, n), n
+
+
+def test_struct_layouts_match_header():
+    # field names of the ctypes mirrors appear in the header in the same order
+    from paper_2407_14675_gb300 import dp
+    src = open(os.path.join(ROOT, "include", "dp.h")).read()
+    for struct in (dp.dp_grid_desc, dp.dp_solve_opts, dp.dp_solve_stats, dp.dp_grid_info):
+        name = struct.__name__
+        body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), src, flags=re.S).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        fields = re.findall(r"(\w+)(?:\[\d\])?\s*[,;]", body)
+        assert fields == [f for f, _ in struct._fields_], name
+
+
+def test_invalid_descriptor_is_rejected_without_gpu_work(lib):
+    # validation runs before any CUDA call
+    from paper_2407_14675_gb300 import dp
+    from paper_2407_14675_gb300 import workloads as W
+    d = dp.desc_from_problem(W.config0(), stream=0)
+    d.beta = 1.5
+    import ctypes as C
+    h = C.c_void_p()
+    rc = lib.dp_grid_create(C.byref(d), C.byref(h))
+    assert rc == dp.DP_EINVAL and not h.value
+    assert "beta" in dp.dp_last_error()
