@@ -197,6 +197,46 @@ int dp_feedback_control(const dp_grid* grid, const double* states, int32_t n, do
 int dp_simulate_closed_loop(const dp_grid* grid, const double* x0, int32_t n, double tau,
                             double h_rk4, double t_max, double* t_arrive, double* x_final);
 
+/* One Jacobi sweep that allocates nothing (the paper has no counterpart: this
+ * call exists for callers that cannot allocate device memory).
+ *
+ * Who needs it: software that may not call cudaMalloc once it is running --
+ * flight or other real-time code that forbids allocation after start-up, or a
+ * host whose device memory belongs to another allocator (a framework's
+ * caching allocator, a fixed pool that accounts for every byte), where an
+ * extra cudaMalloc can fail or fragment that pool.  dp_grid_create allocates,
+ * so such callers cannot hold a grid; this call needs none.
+ *
+ * It runs the same sweep as dp_bellman_sweep (mode = DP_SWEEP_*) for the
+ * full-box grid that desc describes (desc->reduced must be 0), on buffers the
+ * caller owns, in desc->stream on the current device:
+ *   V_in   device, n0 n1 n2 n3 values in box order, double (DP_FP64) or float
+ *          (DP_FP32); target nodes should hold 0
+ *   V_out  device, same size and type, distinct from V_in; receives T(V_in)
+ *   codes  device, n0 n1 n2 n3 16-bit angle codes: read by EVAL and WALK,
+ *          written by the improvement modes; may be NULL for DP_SWEEP_VI
+ *   residual  host, nullable: max |V_out - V_in| (FP64)
+ * The call synchronises desc->stream before it returns.
+ *
+ * Scratch: the node-set and angle tables, the residual slot and the control
+ * block live in one file-scope __device__ array of 1,127,168 bytes, which every
+ * GPU that loads this library holds until the process exits.  That bounds the
+ * grid: n0 n1 <= 4096 and n0 n1 n2 <= 262144, else DP_EINVAL with a message.
+ * Every call shares the array and leaves its contents behind; the call rebuilds
+ * the tables and clears the residual slot and control block itself.  Calls
+ * that overlap on the GPU (two streams, two threads) race on the array and give
+ * wrong results: issue them one after another.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  The call itself never calls cudaMalloc,
+ * cudaFree or any allocating library routine.
+ *
+ * Errors: DP_EINVAL (descriptor, mode, NULL or aliased buffers, grid beyond
+ * the scratch bound), DP_ECUDA, DP_ENONFINITE (V_out holds a non-finite value). */
+int dp_bellman_sweep_noalloc(const dp_grid_desc* desc, int32_t mode, const void* V_in, void* V_out,
+                             uint16_t* codes, double* residual);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* dp_last_error(void);
 

@@ -464,6 +464,48 @@ int loop_common(const dp_grid* cg, const double* states, int n, double tau, doub
 
 }  // namespace
 
+namespace dpk {
+
+// Records an error message for dp_last_error() and returns code (used by the
+// allocation-free entry point in dp_noalloc.cu).
+int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+// Validation and sweep geometry of a full-box grid described by desc, without
+// building a grid: the same checks and target box as dp_grid_create, the
+// same Geo fields as a grid's.  Table pointers are left NULL for the caller.
+int describe_full_grid(const dp_grid_desc* desc, Geo<double>* g64, Geo<float>* g32, long long* n_nodes)
+{
+    int rc = validate(desc);
+    if (rc) return rc;
+    if (desc->reduced) return fail(DP_EINVAL, "this call takes full-box grids only (reduced = 0)");
+    dp_grid g;
+    g.d = *desc;
+    g.M = desc->penalty_M > 0 ? desc->penalty_M : desc->dt / (1.0 - desc->beta);
+    g.n_box = (long long)desc->n[0] * desc->n[1] * desc->n[2] * desc->n[3];
+    g.n_active = g.n_box;
+    for (int k = 0; k < 4; ++k) {
+        g.h[k] = (desc->hi[k] - desc->lo[k]) / (double)(desc->n[k] - 1);
+        int a = -1, b = -2;
+        for (int i = 0; i < desc->n[k]; ++i) {
+            volatile double x = desc->lo[k] + (double)i * g.h[k];
+            bool in = !(desc->target_w[k] > 0) || std::fabs(x - desc->target_c[k]) < desc->target_w[k];
+            if (in) {
+                if (a < 0) a = i;
+                b = i;
+            }
+        }
+        if (a < 0) { a = 1; b = 0; }
+        g.tlo[k] = a;
+        g.thi[k] = b;
+    }
+    fill_geo(&g, *g64);
+    fill_geo(&g, *g32);
+    *n_nodes = g.n_box;
+    return DP_OK;
+}
+
+}  // namespace dpk
+
 extern "C" {
 
 const char* dp_last_error(void) { return g_err; }

@@ -131,6 +131,7 @@ def load(path: Optional[str] = None):
         "dp_policy_iterate": [_P, C.POINTER(dp_solve_opts), C.POINTER(dp_solve_stats)],
         "dp_feedback_control": [_P, _P, C.c_int32, C.c_double, _P, _P],
         "dp_simulate_closed_loop": [_P, _P, C.c_int32, C.c_double, C.c_double, C.c_double, _P, _P],
+        "dp_bellman_sweep_noalloc": [C.POINTER(dp_grid_desc), C.c_int32, _P, _P, _P, _dp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -237,6 +238,15 @@ def dp_get_policy(grid: int, count: int) -> np.ndarray:
 def dp_bellman_sweep(grid: int, mode: int) -> float:
     r = C.c_double(0)
     _check(load().dp_bellman_sweep(grid, mode, C.byref(r)))
+    return r.value
+
+
+def dp_bellman_sweep_noalloc(desc: dp_grid_desc, mode: int, V_in: int, V_out: int, codes: int = 0) -> float:
+    """One sweep on caller-owned device buffers (raw device pointers); the
+    library allocates nothing.  Returns the residual."""
+    r = C.c_double(0)
+    _check(load().dp_bellman_sweep_noalloc(C.byref(desc), mode, C.c_void_p(V_in), C.c_void_p(V_out),
+                                           C.c_void_p(codes or None), C.byref(r)))
     return r.value
 
 
