@@ -85,7 +85,7 @@ typedef struct dp_grid_desc {
     double  penalty_M;     /* I[V] outside the domain; <= 0 means dt / (1 - beta)    */
     double  target_c[4];   /* target: open box |x_d - c_d| < w_d over the d with     */
     double  target_w[4];   /*   w_d > 0; V = 0 there and those nodes are not updated */
-    int32_t n_angles;      /* K tabulated angles 2 pi k / K, K in [2, 4096]          */
+    int32_t n_angles;      /* K tabulated angles 2 pi k / K, K in [2, 1024]          */
     int32_t refine;        /* 1: golden-section refinement in improvement sweeps     */
     double  refine_tol;    /* refinement bracket width, rad (> 0)                    */
     int32_t reduced;       /* 1: keep only nodes with energy in [energy_lo, hi]      */

@@ -67,6 +67,8 @@ struct dp_grid {
     int cur64 = 0;
     bool fp64_values = false;
     uint16_t* code = nullptr;
+    unsigned long long* feet = nullptr;  // frozen feet of the current policy (FP32 grids)
+    bool feet_valid = false;
     Ctl* ctl = nullptr;
     unsigned long long* ring = nullptr;
     double* staging = nullptr;           // n_active doubles
@@ -102,7 +104,7 @@ void free_grid(dp_grid* g)
     cudaSetDevice(g->device);
     if (g->st) cudaStreamSynchronize(g->st);
     void* ps[] = {g->rows, g->lines, g->hi64, g->lo64, g->hi32, g->lo32, g->V[0], g->V[1], g->V64[0],
-                  g->V64[1], g->code, g->ctl, g->ring, g->staging, g->scratch64};
+                  g->V64[1], g->code, g->feet, g->ctl, g->ring, g->staging, g->scratch64};
     for (void* p : ps)
         if (p) cudaFree(p);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
@@ -125,7 +127,7 @@ int validate(const dp_grid_desc* d)
         return fail(DP_EINVAL, "unknown dynamics %d", d->dynamics);
     if (!(d->dt > 0) || !std::isfinite(d->dt)) return fail(DP_EINVAL, "dt must be > 0");
     if (!(d->beta > 0 && d->beta < 1)) return fail(DP_EINVAL, "beta must lie in (0, 1)");
-    if (d->n_angles < 2 || d->n_angles > 4096) return fail(DP_EINVAL, "n_angles must lie in [2, 4096]");
+    if (d->n_angles < 2 || d->n_angles > kMaxAngles) return fail(DP_EINVAL, "n_angles must lie in [2, 1024]");
     if (d->refine && !(d->refine_tol > 0)) return fail(DP_EINVAL, "refine_tol must be > 0");
     if (d->precision != DP_FP64 && d->precision != DP_FP32) return fail(DP_EINVAL, "unknown precision");
     if (!std::isfinite(d->penalty_M)) return fail(DP_EINVAL, "penalty_M must be finite");
@@ -178,11 +180,30 @@ void fill_geo(const dp_grid* gr, Geo<G>& g)
     g.beta64 = d.beta;
     g.M64 = gr->M;
     g.um = (G)(d.dt * mdot / gr->h[3]);
+    {
+        float um = (float)(d.dt * mdot / gr->h[3]);
+        float fl = std::floor(um);
+        g.foot_dm = (int)fl;
+        g.foot_tm = um - fl;
+    }
     g.dyn = d.dynamics;
     g.K = d.n_angles;
     g.refine = d.refine;
     double tc = d.refine ? std::floor(d.refine_tol / (kTwoPi / kCodes)) : 0.0;
     g.fib_stop = (int)std::fmin(tc, 1e9);
+    // shortest bracket between tabulated neighbours, and its Fibonacci index
+    const int K = d.n_angles;
+    long long Lmin = 1LL << 40;
+    for (int k = 0; k < K; ++k) {
+        long long prev = k == 0 ? (((long long)(K - 1) * kCodes + K / 2) / K) - kCodes
+                                : (((long long)(k - 1) * kCodes + K / 2) / K);
+        long long next = ((long long)(k + 1) * kCodes + K / 2) / K;
+        Lmin = std::min(Lmin, next - prev);
+    }
+    long long F1 = 1, F2 = 1;
+    int n = 2;
+    while (F2 < Lmin) { long long F3 = F1 + F2; F1 = F2; F2 = F3; ++n; }
+    g.fib_n0 = n;
     g.n_m = d.n[3];
     g.magic_m = ((1ULL << 40) + (unsigned long long)d.n[3] - 1) / (unsigned long long)d.n[3];
     g.n_nodes = (int)gr->n_active;
@@ -199,6 +220,7 @@ SweepLaunch<G, S> sweep_launch(dp_grid* g, const Geo<G>& geo, const S* Vin, S* V
     L.Vin = Vin;
     L.Vout = Vout;
     L.code = g->code;
+    L.feet = g->feet;
     L.ctl = g->ctl;
     L.ring = g->ring;
     L.ring_mask = kRing - 1;
@@ -236,6 +258,10 @@ cudaError_t enqueue_sweep(dp_grid* g, int mode, long long t, int check_prev, dou
     case kStoreF32: {
         const float* in = (const float*)g->V[(g->cur + a) & 1];
         float* out = (float*)g->V[(g->cur + a + 1) & 1];
+        // improvement sweeps store the frozen feet of the new policy; the
+        // evaluation sweeps after them read those instead of recomputing
+        if (mode == DP_SWEEP_IMPROVE_FULL || mode == DP_SWEEP_IMPROVE_WALK) g->feet_valid = g->feet != nullptr;
+        if (mode == DP_SWEEP_EVAL && g->feet_valid) mode = kEvalFeet;
         return launch_sweep(sweep_launch<float, float>(g, g->g32, in, out, mode, t, check_prev, tol));
     }
     default: {
@@ -619,6 +645,7 @@ int dp_grid_create(const dp_grid_desc* desc, dp_grid** out)
             return bail(fail(DP_ECUDA, "memset failed"));
     }
     if ((rc = dalloc(g, &g->code, g->n_active))) return bail(rc);
+    if (g->fp32 && (rc = dalloc(g, &g->feet, g->n_active))) return bail(rc);
     if ((rc = dalloc(g, &g->ctl, 1))) return bail(rc);
     if ((rc = dalloc(g, &g->ring, kRing))) return bail(rc);
     if (cudaMemsetAsync(g->code, 0, sizeof(uint16_t) * g->n_active, g->st) != cudaSuccess ||
@@ -723,6 +750,7 @@ int dp_set_policy(dp_grid* g, const uint16_t* host_codes, int64_t count)
     if (count != g->n_active) return fail(DP_EINVAL, "count %lld != stored nodes %lld", (long long)count, g->n_active);
     if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
     CK(cudaMemcpyAsync(g->code, host_codes, sizeof(uint16_t) * count, cudaMemcpyHostToDevice, g->st));
+    g->feet_valid = false;   // the stored feet belong to the previous policy
     CK(cudaStreamSynchronize(g->st));
     return DP_OK;
 }

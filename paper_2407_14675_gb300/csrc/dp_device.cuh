@@ -22,8 +22,9 @@ namespace dpk {
 constexpr int kCodes = 65536;       // 16-bit angle lattice, alpha = 2 pi c / 65536
 constexpr int kBlock = 256;         // threads per block of the sweep kernels
 constexpr int kMaxFib = 30;
+constexpr int kMaxAngles = 1024;   // tabulated angles per grid (shared-memory table)
 
-enum { kVI = 0, kImproveFull = 1, kImproveWalk = 2, kEval = 3 };
+enum { kVI = 0, kImproveFull = 1, kImproveWalk = 2, kEval = 3, kEvalFeet = 4 };
 enum { kDynOrbit = 0, kDynUnitSpeed = 1 };
 
 // Fibonacci numbers F[1] = F[2] = 1 (index 0 unused).
@@ -53,8 +54,11 @@ struct Geo {
     G beta_hi, beta_lo;        // beta = beta_hi + beta_lo (FP32 value update)
     double dt64, beta64, M64;  // exact parameters for FP64 value updates
     G um;                      // mass displacement in cells, identical at every node
+    int foot_dm;               // its cell offset floor(um) and fraction um - floor(um)
+    float foot_tm;             //   (grid constants of every frozen foot)
     int dyn;
     int K, refine, fib_stop;   // refinement stops once the bracket is <= fib_stop codes
+    int fib_n0;                // Fibonacci index of the shortest refinement bracket
     int tlo[4], thi[4];        // target index box, inclusive (tlo > thi: no target)
     int n_m;
     unsigned long long magic_m;    // ceil(2^40 / n_m): j / n_m for j < 2^40 / (n_m - 1)
@@ -69,17 +73,13 @@ template <typename G> __device__ __forceinline__ G ginf();
 template <> __device__ __forceinline__ float ginf<float>() { return CUDART_INF_F; }
 template <> __device__ __forceinline__ double ginf<double>() { return CUDART_INF; }
 
-__device__ __forceinline__ float grcp(float x) { return __frcp_rn(x); }
+// Reciprocal for the geometry: FP32 uses the hardware approximation (about
+// 1 ulp); its error moves a foot by ~1e-9 cells, far below FP32 grid noise.
+__device__ __forceinline__ float grcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double grcp(double x) { return __drcp_rn(x); }
 
 // Code of the k-th tabulated angle 2 pi k / K on the lattice (round half up).
 __device__ __forceinline__ int table_code(int K, int k) { return (k * kCodes + K / 2) / K; }
-
-// Nearest tabulated index to a code (start of the local walk).
-__device__ __forceinline__ int nearest_table_index(int K, int code)
-{
-    return (int)((((long long)code * K + kCodes / 2) / kCodes) % K);
-}
 
 __device__ __forceinline__ int wrap_code(int c) { return c & (kCodes - 1); }
 
@@ -180,6 +180,200 @@ __device__ __forceinline__ void heun_cells(const Geo<G>& g, const StepP<G>& sp, 
     }
 }
 
+// Cell of the foot i + u (grid units): c = i + floor(u), t = u - floor(u).
+// A foot exactly on an upper face uses the last cell with t = 1.  Returns
+// true when the foot is outside the box (strictly) or not finite.
+template <typename G>
+__device__ __forceinline__ bool foot_cell(const Geo<G>& g, const int i[4], const G u[4], int c[4], G t[4])
+{
+    bool out = false;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        G fl = floor(u[d]);
+        t[d] = u[d] - fl;
+        c[d] = i[d] + (int)fl;
+        out = out || !(t[d] >= (G)0);
+        if ((unsigned)c[d] > (unsigned)(g.n[d] - 2)) {   // outside, or on the upper face
+            out = out || c[d] != g.n[d] - 1 || t[d] > (G)0;
+            c[d] = g.n[d] - 2;
+            t[d] = (G)1;
+        }
+    }
+    return out;
+}
+
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// Paired FP32 arithmetic (two IEEE round-to-nearest results per instruction).
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// The 16 corner values of a cell as differences to the node's value, ready
+// for the blend.  Corner x = 4 r + 2 v_r + v_t (bits of the cell corner) has
+// e0[x] at the lower mass node and de[x] = step to the upper mass node.
+// blend(t) lerps along m, v_t, v_r, r in that order; the FP32 version does
+// the same lerps two at a time (pairs x and x + 4), with identical rounding.
+template <typename G> struct Corners;
+
+template <> struct Corners<double> {
+    double e0[8], de[8];
+    __device__ __forceinline__ void set(const double a[8], const double d[8])
+    {
+#pragma unroll
+        for (int x = 0; x < 8; ++x) { e0[x] = a[x]; de[x] = d[x]; }
+    }
+    __device__ __forceinline__ double blend(const double t[4]) const
+    {
+        double e[8], f[4];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) e[x] = e0[x] + t[3] * de[x];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) f[y] = e[2 * y] + t[2] * (e[2 * y + 1] - e[2 * y]);
+        double h0 = f[0] + t[1] * (f[1] - f[0]);
+        double h1 = f[2] + t[1] * (f[3] - f[2]);
+        return h0 + t[0] * (h1 - h0);
+    }
+};
+
+template <> struct Corners<float> {
+    unsigned long long q0[4], qd[4];   // (e0[x], e0[x + 4]), (de[x], de[x + 4])
+    __device__ __forceinline__ void set(const float a[8], const float d[8])
+    {
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            q0[x] = pack2(a[x], a[x + 4]);
+            qd[x] = pack2(d[x], d[x + 4]);
+        }
+    }
+    __device__ __forceinline__ float blend(const float t[4]) const
+    {
+        const unsigned long long t3 = pack2(t[3], t[3]), t2 = pack2(t[2], t[2]), t1 = pack2(t[1], t[1]);
+        unsigned long long Q[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) Q[x] = fma2(qd[x], t3, q0[x]);              // along m
+        unsigned long long R0 = fma2(sub2(Q[1], Q[0]), t2, Q[0]);               // along v_t
+        unsigned long long R1 = fma2(sub2(Q[3], Q[2]), t2, Q[2]);
+        unsigned long long S = fma2(sub2(R1, R0), t1, R0);                      // along v_r
+        float h0, h1;
+        unpack2(S, h0, h1);
+        return h0 + t[0] * (h1 - h0);                                            // along r
+    }
+};
+
+// Gathers the corners of cell c.  Returns true when a corner lies outside
+// the node set (reduced grids: the cell's four (r, v_r) rows must each hold
+// both v_t corners); the corners are then not loaded.
+template <typename G, bool REDUCED>
+__device__ __forceinline__ bool cell_rows(const Geo<G>& g, const int c[4], int base[4])
+{
+    // per (r, v_r) corner row rb = 2 r + v_r: index of corner (c_vt, c_m)
+    if (!REDUCED) {
+        const int b0 = c[0] * g.stride[0] + c[1] * g.stride[1] + c[2] * g.stride[2] + c[3];
+        base[0] = b0;
+        base[1] = b0 + g.stride[1];
+        base[2] = b0 + g.stride[0];
+        base[3] = b0 + g.stride[0] + g.stride[1];
+        return false;
+    }
+    bool out = false;
+#pragma unroll
+    for (int rb = 0; rb < 4; ++rb) {
+        int row = (c[0] + (rb >> 1)) * g.n[1] + c[1] + (rb & 1);
+        int4 R = __ldg(&g.rows[row]);
+        out = out || c[2] < R.y || c[2] + 1 > R.y + R.z - 1;
+        base[rb] = R.x + (c[2] - R.y) * g.n_m + c[3];
+    }
+    return out;
+}
+
+// Loads the 16 corners given the index of corner (c_vt, c_m) in each of the
+// four (r, v_r) rows (n_m: stride of v_t).
+template <typename G, typename S>
+__device__ __forceinline__ void load_rows(const S* __restrict__ V, const int base[4], int n_m, S vj, Corners<G>& K)
+{
+    G a[8], d[8];
+#pragma unroll
+    for (int rb = 0; rb < 4; ++rb) {
+        const S* p = V + base[rb];
+        S v00 = __ldg(p), v01 = __ldg(p + 1), v10 = __ldg(p + n_m), v11 = __ldg(p + n_m + 1);
+        a[2 * rb] = (G)(v00 - vj);
+        d[2 * rb] = (G)(v01 - vj) - a[2 * rb];
+        a[2 * rb + 1] = (G)(v10 - vj);
+        d[2 * rb + 1] = (G)(v11 - vj) - a[2 * rb + 1];
+    }
+    K.set(a, d);
+}
+
+template <typename G, typename S, bool REDUCED>
+__device__ __forceinline__ bool load_corners(const Geo<G>& g, const S* __restrict__ V, const int c[4], S vj,
+                                             Corners<G>& K)
+{
+    int base[4];
+    if (cell_rows<G, REDUCED>(g, c, base)) return true;
+    load_rows<G, S>(V, base, g.n_m, vj, K);
+    return false;
+}
+
+// Frozen foot of a node under a fixed policy (FP32 grids).  Policy
+// evaluation sweeps repeat the same foot ~20 times, so the improvement sweep
+// stores it in one 64-bit word and the evaluation sweep only gathers and
+// blends:
+//   bits  0-17, 18-35, 36-53  cell fractions t_r, t_vr, t_vt in 18-bit fixed
+//                             point (q / (2^18 - 1); error <= 1.9e-6 of a cell)
+//   bits 54-55, 56-59, 60-61  cell offset from the node in r (-2..1),
+//                             v_r (-8..7), v_t (-2..1)
+//   bits 62-63                kind: inside, outside (penalty M), target node,
+//                             or "recompute from the policy code"
+// The mass coordinate needs no storage: m' = -a/c is the same at every node,
+// so its offset and fraction are grid constants (a node where they differ, at
+// the upper mass face, is marked "recompute").
+enum { kFootInside = 0, kFootOut = 1, kFootTarget = 2, kFootRecompute = 3 };
+constexpr float kFootQ = 262143.0f;   // 2^18 - 1
+
+__device__ __forceinline__ unsigned long long foot_word_kind(int kind)
+{
+    return (unsigned long long)kind << 62;
+}
+
+// Encodes cell c and fractions t of a foot from node i; dm, tm: the grid's
+// mass offset and fraction.
+__device__ __forceinline__ unsigned long long encode_foot(const int i[4], const int c[4], const float t[4], int dm,
+                                                          float tm)
+{
+    const int dr = c[0] - i[0], dv = c[1] - i[1], dt = c[2] - i[2];
+    if (dr < -2 || dr > 1 || dv < -8 || dv > 7 || dt < -2 || dt > 1 || c[3] - i[3] != dm || t[3] != tm)
+        return foot_word_kind(kFootRecompute);
+    unsigned long long w = 0;
+    w |= (unsigned long long)__float2uint_rn(t[0] * kFootQ);
+    w |= (unsigned long long)__float2uint_rn(t[1] * kFootQ) << 18;
+    w |= (unsigned long long)__float2uint_rn(t[2] * kFootQ) << 36;
+    w |= (unsigned long long)(dr + 2) << 54;
+    w |= (unsigned long long)(dv + 8) << 56;
+    w |= (unsigned long long)(dt + 2) << 60;
+    return w;
+}
+
 // Q1 interpolation at the foot i + u (grid units), returned as the difference
 // D = I[V] - vj; M - vj when the foot is outside the box or the node set.
 template <typename G, typename S, bool REDUCED>
@@ -188,64 +382,13 @@ __device__ __forceinline__ G interp_delta(const Geo<G>& g, const S* __restrict__
 {
     int c[4];
     G t[4];
-    bool out = false;
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-        G fl = floor(u[d]);
-        t[d] = u[d] - fl;
-        c[d] = i[d] + (int)fl;
-        out = out || !(t[d] >= (G)0) || c[d] < 0 || c[d] > g.n[d] - 1;
-        if (c[d] == g.n[d] - 1) {     // foot exactly on the upper face
-            out = out || t[d] > (G)0;
-            c[d] = g.n[d] - 2;
-            t[d] = (G)1;
-        }
-    }
-    if (out) return (G)((S)g.M64 - vj);
-
-    S v[16];
-    if (!REDUCED) {
-        int base = c[0] * g.stride[0] + c[1] * g.stride[1] + c[2] * g.stride[2] + c[3];
-#pragma unroll
-        for (int b = 0; b < 16; ++b) {
-            int off = ((b >> 3) & 1) * g.stride[0] + ((b >> 2) & 1) * g.stride[1] +
-                      ((b >> 1) & 1) * g.stride[2] + (b & 1);
-            v[b] = __ldg(&V[base + off]);
-        }
-    } else {
-        // the cell's four (r, v_r) rows must each hold both v_t corners
-        int base[4];
-#pragma unroll
-        for (int rb = 0; rb < 4; ++rb) {
-            int row = (c[0] + (rb >> 1)) * g.n[1] + c[1] + (rb & 1);
-            int4 R = __ldg(&g.rows[row]);
-            out = out || c[2] < R.y || c[2] + 1 > R.y + R.z - 1;
-            base[rb] = R.x + (c[2] - R.y) * g.n_m + c[3];
-        }
-        if (out) return (G)((S)g.M64 - vj);
-#pragma unroll
-        for (int rb = 0; rb < 4; ++rb) {
-            v[rb * 4 + 0] = __ldg(&V[base[rb]]);
-            v[rb * 4 + 1] = __ldg(&V[base[rb] + 1]);
-            v[rb * 4 + 2] = __ldg(&V[base[rb] + g.n_m]);
-            v[rb * 4 + 3] = __ldg(&V[base[rb] + g.n_m + 1]);
-        }
-    }
-    // differences to the node's own value, then 15 lerps: m, v_t, v_r, r
-    G e[16];
-#pragma unroll
-    for (int b = 0; b < 16; ++b) e[b] = (G)(v[b] - vj);
-#pragma unroll
-    for (int b = 0; b < 8; ++b) e[b] = e[2 * b] + t[3] * (e[2 * b + 1] - e[2 * b]);
-#pragma unroll
-    for (int b = 0; b < 4; ++b) e[b] = e[2 * b] + t[2] * (e[2 * b + 1] - e[2 * b]);
-#pragma unroll
-    for (int b = 0; b < 2; ++b) e[b] = e[2 * b] + t[1] * (e[2 * b + 1] - e[2 * b]);
-    return e[0] + t[0] * (e[1] - e[0]);
+    Corners<G> K;
+    if (foot_cell(g, i, u, c, t) || load_corners<G, S, REDUCED>(g, V, c, vj, K)) return (G)((S)g.M64 - vj);
+    return K.blend(t);
 }
 
 // Control-dependent evaluation at one state: node i plus the offset u0 (both
-// in grid units; u0 = 0 at a grid node).
+// in grid units; u0 = 0 at a grid node).  One interpolation per call.
 template <typename G, typename S, bool REDUCED, int DYN>
 struct NodeEval {
     const Geo<G>* g;
@@ -256,25 +399,123 @@ struct NodeEval {
     S vj;
     NodeDyn<G> nd;
 
-    __device__ __forceinline__ G at_code(int code) const
+    __device__ __forceinline__ G at_sc(G s, G c)
     {
-        G s, c, u[4];
-        code_sincos(*g, code, s, c);
+        G u[4];
         heun_cells<G, DYN>(*g, sp, nd, s, c, u);
 #pragma unroll
         for (int d = 0; d < 4; ++d) u[d] += u0[d];
         return interp_delta<G, S, REDUCED>(*g, V, i, u, vj);
     }
+
+    __device__ __forceinline__ G at_code(int code)
+    {
+        G s, c;
+        code_sincos(*g, code, s, c);
+        return at_sc(s, c);
+    }
 };
 
-// Full tabulation; ties go to the lowest index.
-template <class E>
-__device__ __forceinline__ int enumerate_table(const E& ev, int K, decltype(ev.at_code(0))& Dbest)
+// The same evaluation for searches over many angles at one state: the
+// corners of the last cell used stay in registers.  Thrust moves the foot by
+// about 1e-3 cells across all angles, so nearly every angle after the first
+// costs the Heun step and the blend, with no memory access.  Results are
+// bit-identical to NodeEval.
+template <typename G, typename S, bool REDUCED, int DYN>
+struct CachedEval {
+    const Geo<G>* g;
+    const S* __restrict__ V;
+    StepP<G> sp;
+    int i[4];
+    G u0[4];
+    S vj;
+    NodeDyn<G> nd;
+    int cc[4];        // cached cell; cc[0] = -1: none
+    bool cout;        // the cached cell has a corner outside the node set
+    Corners<G> K;
+
+    __device__ __forceinline__ void reset() { cc[0] = -1; }
+
+    __device__ __forceinline__ G at_code(int code)
+    {
+        G s, c;
+        code_sincos(*g, code, s, c);
+        return at_sc(s, c);
+    }
+
+    __device__ __forceinline__ G at_sc(G s, G c)
+    {
+        G u[4], t[4];
+        int cl[4];
+        heun_cells<G, DYN>(*g, sp, nd, s, c, u);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) u[d] += u0[d];
+        if (foot_cell(*g, i, u, cl, t)) return (G)((S)g->M64 - vj);
+        if (cl[0] != cc[0] || cl[1] != cc[1] || cl[2] != cc[2] || cl[3] != cc[3]) {
+            cout = load_corners<G, S, REDUCED>(*g, V, cl, vj, K);
+#pragma unroll
+            for (int d = 0; d < 4; ++d) cc[d] = cl[d];
+        }
+        if (cout) return (G)((S)g->M64 - vj);
+        return K.blend(t);
+    }
+
+    // Frozen-foot word of this node for a code (FP32 geometry only).
+    __device__ __forceinline__ unsigned long long foot_of(int code) const
+    {
+        G s, c, u[4], t[4];
+        int cl[4], base[4];
+        code_sincos(*g, code, s, c);
+        heun_cells<G, DYN>(*g, sp, nd, s, c, u);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) u[d] += u0[d];
+        if (foot_cell(*g, i, u, cl, t)) return foot_word_kind(kFootOut);
+        if (REDUCED && cell_rows<G, REDUCED>(*g, cl, base)) return foot_word_kind(kFootOut);
+        return encode_foot(i, cl, t, g->foot_dm, g->foot_tm);
+    }
+};
+
+// Tabulated angles: codes c_k of 2 pi k / K for k = 0..K (c_K = 65536) and
+// (sin, cos) of c_k for k < K.  Kernels that search over angles build it
+// once per block in shared memory (build_table), so the searches do no
+// integer division and no trig lookup for tabulated angles.
+template <typename G>
+struct Table {
+    const int* code;
+    const typename V2<G>::type* sc;
+    int K;
+};
+
+template <typename G>
+__device__ __forceinline__ void build_table(const Geo<G>& g, int* code, typename V2<G>::type* sc)
 {
-    auto Db = ev.at_code(table_code(K, 0));
+    for (int k = threadIdx.x; k <= g.K; k += blockDim.x) {
+        int c = table_code(g.K, k);
+        code[k] = c;
+        if (k < g.K) {
+            G s, cs;
+            code_sincos(g, c, s, cs);
+            sc[k].x = s;
+            sc[k].y = cs;
+        }
+    }
+}
+
+// Nearest tabulated index to a code (start of the local walk).
+__device__ __forceinline__ int nearest_index(int K, int code)
+{
+    int k = (code * K + kCodes / 2) >> 16;
+    return k >= K ? k - K : k;
+}
+
+// Full tabulation; ties go to the lowest index.
+template <class E, typename G>
+__device__ __forceinline__ int enumerate_table(E& ev, const Table<G>& T, G& Dbest)
+{
+    G Db = ev.at_sc(T.sc[0].x, T.sc[0].y);
     int kb = 0;
-    for (int k = 1; k < K; ++k) {
-        auto D = ev.at_code(table_code(K, k));
+    for (int k = 1; k < T.K; ++k) {
+        G D = ev.at_sc(T.sc[k].x, T.sc[k].y);
         if (D < Db) { Db = D; kb = k; }
     }
     Dbest = Db;
@@ -283,23 +524,33 @@ __device__ __forceinline__ int enumerate_table(const E& ev, int K, decltype(ev.a
 
 // Local walk from k0 towards the strictly lower tabulated neighbour (left
 // wins a tie between neighbours) until neither neighbour is lower.
-template <class E>
-__device__ __forceinline__ int walk_table(const E& ev, int K, int k0, decltype(ev.at_code(0))& Dbest)
+template <class E, typename G>
+__device__ __forceinline__ int walk_table(E& ev, const Table<G>& T, int k0, G& Dbest)
 {
+    const int K = T.K;
     int k = k0;
-    auto Dk = ev.at_code(table_code(K, k));
-    auto Dl = ev.at_code(table_code(K, k == 0 ? K - 1 : k - 1));
-    auto Dr = ev.at_code(table_code(K, k == K - 1 ? 0 : k + 1));
+    int kl = k == 0 ? K - 1 : k - 1, kr = k == K - 1 ? 0 : k + 1;
+    G Dk = ev.at_sc(T.sc[k].x, T.sc[k].y);
+    G Dl = ev.at_sc(T.sc[kl].x, T.sc[kl].y);
+    G Dr = ev.at_sc(T.sc[kr].x, T.sc[kr].y);
+    // one evaluation per step, outside the branch, so that lanes of a warp that
+    // walk in different directions share it
     for (int step = 0; step < K; ++step) {
-        if (Dl < Dk && Dl <= Dr) {
-            Dr = Dk; Dk = Dl; k = (k == 0) ? K - 1 : k - 1;
-            Dl = ev.at_code(table_code(K, k == 0 ? K - 1 : k - 1));
-        } else if (Dr < Dk) {
-            Dl = Dk; Dk = Dr; k = (k == K - 1) ? 0 : k + 1;
-            Dr = ev.at_code(table_code(K, k == K - 1 ? 0 : k + 1));
+        const bool go_l = Dl < Dk && Dl <= Dr;
+        if (!go_l && !(Dr < Dk)) break;
+        int kn;
+        if (go_l) {
+            Dr = Dk; Dk = Dl; k = kl;
+            kl = k == 0 ? K - 1 : k - 1;
+            kn = kl;
         } else {
-            break;
+            Dl = Dk; Dk = Dr; k = kr;
+            kr = k == K - 1 ? 0 : k + 1;
+            kn = kr;
         }
+        const G Dn = ev.at_sc(T.sc[kn].x, T.sc[kn].y);
+        if (go_l) Dl = Dn;
+        else Dr = Dn;
     }
     Dbest = Dk;
     return k;
@@ -308,18 +559,17 @@ __device__ __forceinline__ int walk_table(const E& ev, int K, int k0, decltype(e
 // Golden-section refinement in its discrete (Fibonacci) form on the angle
 // lattice inside the bracket of the two tabulated neighbours of k, extended
 // to a Fibonacci length with +inf past the upper neighbour.  Returns the best
-// evaluated code (the tabulated minimiser included).
-template <class E>
-__device__ __forceinline__ int fibonacci_refine(const E& ev, int K, int fib_stop, int k,
-                                                decltype(ev.at_code(0)) Dk,
-                                                decltype(ev.at_code(0))& Dbest)
+// evaluated code (the tabulated minimiser included).  n0 is a lower bound of
+// the Fibonacci index of the bracket length.
+template <class E, typename G>
+__device__ __forceinline__ int fibonacci_refine(E& ev, const Table<G>& T, int n0, int fib_stop, int k, G Dk,
+                                                G& Dbest)
 {
-    typedef decltype(ev.at_code(0)) G;
-    const int ck = table_code(K, k);
-    const int cl = (k == 0) ? table_code(K, K - 1) - kCodes : table_code(K, k - 1);
-    const int cr = (k == K - 1) ? kCodes : table_code(K, k + 1);
+    const int ck = T.code[k];
+    const int cl = (k == 0) ? T.code[T.K - 1] - kCodes : T.code[k - 1];
+    const int cr = T.code[k + 1];
     const int lo_off = cl - ck, hi_off = cr - ck, L = hi_off - lo_off;
-    int n = 2;
+    int n = n0;
     while (kFib[n] < L) ++n;
     int best = ck;
     G qb = Dk;
@@ -330,18 +580,24 @@ __device__ __forceinline__ int fibonacci_refine(const E& ev, int K, int fib_stop
     if (f1 < qb) { qb = f1; best = ck + x1; }
     if (f2 < qb) { qb = f2; best = ck + x2; }
     for (int kk = n; kk > 4 && kFib[kk] > fib_stop; --kk) {
-        if (f1 <= f2) {
+        // keep [a, x2] (new point a + F[kk-3]) or [x1, a + F[kk]] (new point
+        // x1 + F[kk-2]); one evaluation per step, outside the branch
+        const bool left = f1 <= f2;
+        int xn;
+        if (left) {
             x2 = x1; f2 = f1;
             x1 = a + kFib[kk - 3];
-            f1 = (x1 >= hi_off) ? ginf<G>() : ev.at_code(ck + x1);
-            if (f1 < qb) { qb = f1; best = ck + x1; }
+            xn = x1;
         } else {
             a = x1;
             x1 = x2; f1 = f2;
             x2 = a + kFib[kk - 2];
-            f2 = (x2 >= hi_off) ? ginf<G>() : ev.at_code(ck + x2);
-            if (f2 < qb) { qb = f2; best = ck + x2; }
+            xn = x2;
         }
+        const G fn = (xn >= hi_off) ? ginf<G>() : ev.at_code(ck + xn);
+        if (left) f1 = fn;
+        else f2 = fn;
+        if (fn < qb) { qb = fn; best = ck + xn; }
     }
     Dbest = qb;
     return wrap_code(best);

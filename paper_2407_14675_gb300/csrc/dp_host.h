@@ -15,6 +15,7 @@ struct SweepLaunch {
     const S* Vin;
     S* Vout;
     uint16_t* code;
+    unsigned long long* feet;   // frozen feet (FP32 grids) or NULL
     Ctl* ctl;
     unsigned long long* ring;   // FP64 residual bits, one slot per sweep
     int ring_mask;

@@ -40,6 +40,12 @@ template <typename G, typename S, bool REDUCED, int DYN>
 __global__ void __launch_bounds__(128)
 loop_kernel(const __grid_constant__ Geo<G> g, const __grid_constant__ LoopLaunch<G, S> a)
 {
+    __shared__ int s_code[kMaxAngles + 1];
+    __shared__ typename V2<G>::type s_sc[kMaxAngles];
+    build_table(g, s_code, s_sc);
+    __syncthreads();
+    const Table<G> T{s_code, s_sc, g.K};
+
     const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (w >= a.n) return;
@@ -48,7 +54,7 @@ loop_kernel(const __grid_constant__ Geo<G> g, const __grid_constant__ LoopLaunch
 #pragma unroll
     for (int d = 0; d < 4; ++d) y[d] = a.x0[4 * w + d];
 
-    NodeEval<G, S, REDUCED, DYN> ev;
+    CachedEval<G, S, REDUCED, DYN> ev;
     ev.g = &g;
     ev.V = a.V;
     ev.sp.dt = (G)a.tau;
@@ -70,14 +76,16 @@ loop_kernel(const __grid_constant__ Geo<G> g, const __grid_constant__ LoopLaunch
             ev.u0[d] = (G)(sd - fl);
         }
         ev.nd = node_dyn<G, DYN>(g, ev.sp, x);
+        ev.reset();
         // compensation reference: the plain interpolated value at angle 0
         ev.vj = (S)0;
         ev.vj = (S)ev.at_code(0);
+        ev.reset();          // cached corners are differences to the old vj
 
         G Db = ginf<G>();
         int kb = 0x7fffffff;
         for (int k = lane; k < g.K; k += 32) {
-            G D = ev.at_code(table_code(g.K, k));
+            G D = ev.at_sc(T.sc[k].x, T.sc[k].y);
             if (better<G, S>(D, k, Db, kb)) { Db = D; kb = k; }
         }
 #pragma unroll
@@ -86,8 +94,8 @@ loop_kernel(const __grid_constant__ Geo<G> g, const __grid_constant__ LoopLaunch
             int ko = __shfl_xor_sync(0xffffffffu, kb, o);
             if (better<G, S>(Do, ko, Db, kb)) { Db = Do; kb = ko; }
         }
-        int code = wrap_code(table_code(g.K, kb));
-        if (g.refine) code = fibonacci_refine(ev, g.K, g.fib_stop, kb, Db, Db);
+        int code = T.code[kb] & (kCodes - 1);
+        if (g.refine) code = fibonacci_refine(ev, T, g.fib_n0, g.fib_stop, kb, Db, Db);
 
         double2 hi = a.tab_hi64[code >> 8], lo = a.tab_lo64[code & 255];
         double s = hi.x * lo.y + hi.y * lo.x;

@@ -86,6 +86,7 @@ int run(const Geo<G>& geo, unsigned char* scr, int mode, const void* V_in, void*
     L.Vin = (const S*)V_in;
     L.Vout = (S*)V_out;
     L.code = codes;
+    L.feet = nullptr;
     L.ctl = (Ctl*)(scr + kCtlOff);
     L.ring = (unsigned long long*)(scr + kRingOff);
     L.ring_mask = 0;

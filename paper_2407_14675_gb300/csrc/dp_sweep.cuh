@@ -9,7 +9,13 @@
 // their bits).  A sweep first looks at the previous sweep's residual when the
 // host asks it to: if the stopping test passed, it records that and returns
 // without touching V, so a queue of sweeps ends at the first converged one.
+//
+// On FP32 grids the improvement sweep also stores each node's frozen foot
+// (cell offsets and fractions of the chosen control, 8 bytes); the
+// evaluation sweeps that follow (kEvalFeet) then only gather and blend.
 #pragma once
+
+#include <type_traits>
 
 #include "dp_device.cuh"
 #include "dp_host.h"
@@ -46,12 +52,67 @@ __device__ __forceinline__ S warp_max(S v)
     return v;
 }
 
+// Fills the common fields of an evaluator for grid node ev.i with value vj.
+template <typename G, typename S, int DYN, class E>
+__device__ __forceinline__ void setup_node(E& ev, const Geo<G>& g, const S* __restrict__ V, S vj)
+{
+    G x[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) x[d] = g.lo[d] + (G)ev.i[d] * g.h[d];
+    ev.g = &g;
+    ev.V = V;
+    ev.vj = vj;
+    ev.sp.dt = g.dt;
+    ev.sp.hdt = g.hdt;
+    ev.sp.um = g.um;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) ev.u0[d] = (G)0;
+    ev.nd = node_dyn<G, DYN>(g, ev.sp, x);
+}
+
+// Evaluation at a frozen foot word of kind kFootInside: gather and blend.
+template <bool REDUCED>
+__device__ __forceinline__ float eval_foot(const Geo<float>& g, const float* __restrict__ V, int j,
+                                           unsigned long long w, float vj)
+{
+    const int dr = (int)((w >> 54) & 3u) - 2;
+    const int dv = (int)((w >> 56) & 15u) - 8;
+    const int dt = (int)((w >> 60) & 3u) - 2;
+    float t[4];
+    t[0] = (float)(unsigned)(w & 0x3ffffu) * (1.0f / kFootQ);
+    t[1] = (float)(unsigned)((w >> 18) & 0x3ffffu) * (1.0f / kFootQ);
+    t[2] = (float)(unsigned)((w >> 36) & 0x3ffffu) * (1.0f / kFootQ);
+    t[3] = g.foot_tm;
+    int base[4];
+    if (!REDUCED) {
+        // full box: the cell's corner index is the node's own index plus offsets
+        const int b0 = j + dr * g.stride[0] + dv * g.stride[1] + dt * g.stride[2] + g.foot_dm;
+        base[0] = b0;
+        base[1] = b0 + g.stride[1];
+        base[2] = b0 + g.stride[0];
+        base[3] = b0 + g.stride[0] + g.stride[1];
+    } else {
+        int i[4], c[4];
+        decode_node(g, j, i);
+        c[0] = i[0] + dr;
+        c[1] = i[1] + dv;
+        c[2] = i[2] + dt;
+        c[3] = i[3] + g.foot_dm;
+        cell_rows<float, true>(g, c, base);   // membership was checked when the foot was stored
+    }
+    Corners<float> K;
+    load_rows<float, float>(V, base, g.n_m, vj, K);
+    return K.blend(t);
+}
+
 template <typename G, typename S, int MODE, bool REDUCED, int DYN>
 __global__ void __launch_bounds__(kBlock)
-sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __restrict__ Vout, uint16_t* __restrict__ code,
-             Ctl* __restrict__ ctl, unsigned long long* __restrict__ ring, int ring_mask,
-             long long sweep, int check_prev, double tol)
+sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __restrict__ Vout,
+             uint16_t* __restrict__ code, unsigned long long* __restrict__ feet, Ctl* __restrict__ ctl,
+             unsigned long long* __restrict__ ring, int ring_mask, long long sweep, int check_prev, double tol)
 {
+    constexpr bool kSearch = MODE == kVI || MODE == kImproveFull || MODE == kImproveWalk;
+    constexpr bool kFP32 = std::is_same<G, float>::value && std::is_same<S, float>::value;
     if (*(volatile int*)&ctl->stop) return;
     if (check_prev) {
         unsigned long long bits = *(volatile unsigned long long*)&ring[(sweep - 1) & ring_mask];
@@ -64,41 +125,85 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
         }
     }
 
+    // angle searches read the tabulated codes and (sin, cos) from shared memory
+    __shared__ int s_code[kSearch ? kMaxAngles + 1 : 1];
+    __shared__ typename V2<G>::type s_sc[kSearch ? kMaxAngles : 1];
+    if constexpr (kSearch) {
+        build_table(g, s_code, s_sc);
+        __syncthreads();
+    }
+    const Table<G> T{s_code, s_sc, g.K};
+
     S resid = (S)0;
     bool bad = false;
     const int stride = gridDim.x * kBlock;
-    for (int j = blockIdx.x * kBlock + threadIdx.x; j < g.n_nodes; j += stride) {
-        NodeEval<G, S, REDUCED, DYN> ev;
-        decode_node(g, j, ev.i);
+    // evaluation sweeps interpolate once per node; searches keep the cell's
+    // corners in registers across angles
+    typedef typename std::conditional<kSearch, CachedEval<G, S, REDUCED, DYN>, NodeEval<G, S, REDUCED, DYN>>::type
+        Eval;
+    if constexpr (MODE == kEvalFeet) {
+        // frozen feet: gather-bound, so the next node's foot word and value are
+        // fetched while this node's corners are in flight
+        int j = blockIdx.x * kBlock + threadIdx.x;
+        unsigned long long w_next = 0;
+        S v_next = (S)0;
+        if (j < g.n_nodes) {
+            w_next = feet[j];
+            v_next = Vin[j];
+        }
+        for (; j < g.n_nodes; j += stride) {
+            const unsigned long long w = w_next;
+            const S vj = v_next;
+            if (j + stride < g.n_nodes) {
+                w_next = feet[j + stride];
+                v_next = Vin[j + stride];
+            }
+            const int kind = (int)(w >> 62);
+            S vnew = (S)0;
+            if (kind == kFootInside) {
+                vnew = bellman_value<G, S>(g, vj, eval_foot<REDUCED>(g, Vin, j, w, vj));
+            } else if (kind == kFootOut) {
+                vnew = bellman_value<G, S>(g, vj, (G)((S)g.M64 - vj));
+            } else if (kind == kFootRecompute) {
+                NodeEval<G, S, REDUCED, DYN> ev;
+                decode_node(g, j, ev.i);
+                setup_node<G, S, DYN>(ev, g, Vin, vj);
+                vnew = bellman_value<G, S>(g, vj, ev.at_code(code[j]));
+            }
+            Vout[j] = vnew;
+            resid = fmax(resid, (S)fabs(vnew - vj));
+            bad = bad || !isfinite(vnew);
+        }
+    }
+    if constexpr (MODE != kEvalFeet) for (int j = blockIdx.x * kBlock + threadIdx.x; j < g.n_nodes; j += stride) {
         const S vj = Vin[j];
         S vnew = (S)0;
-        if (!in_target(g, ev.i)) {
-            G x[4];
-#pragma unroll
-            for (int d = 0; d < 4; ++d) x[d] = g.lo[d] + (G)ev.i[d] * g.h[d];
-            ev.g = &g;
-            ev.V = Vin;
-            ev.vj = vj;
-            ev.sp.dt = g.dt;
-            ev.sp.hdt = g.hdt;
-            ev.sp.um = g.um;
-#pragma unroll
-            for (int d = 0; d < 4; ++d) ev.u0[d] = (G)0;
-            ev.nd = node_dyn<G, DYN>(g, ev.sp, x);
-            G D;
-            if (MODE == kEval) {
-                D = ev.at_code(code[j]);
-            } else {
-                int k;
-                if (MODE == kImproveWalk)
-                    k = walk_table(ev, g.K, nearest_table_index(g.K, code[j]), D);
-                else
-                    k = enumerate_table(ev, g.K, D);
-                int c = wrap_code(table_code(g.K, k));
-                if (MODE != kVI && g.refine) c = fibonacci_refine(ev, g.K, g.fib_stop, k, D, D);
-                if (MODE != kVI) code[j] = (uint16_t)c;
+        {
+            Eval ev;
+            decode_node(g, j, ev.i);
+            if (!in_target(g, ev.i)) {
+                setup_node<G, S, DYN>(ev, g, Vin, vj);
+                G D;
+                if constexpr (MODE == kEval) {
+                    D = ev.at_code(code[j]);
+                } else {
+                    ev.reset();
+                    int k;
+                    if (MODE == kImproveWalk)
+                        k = walk_table(ev, T, nearest_index(g.K, code[j]), D);
+                    else
+                        k = enumerate_table(ev, T, D);
+                    int c = T.code[k] & (kCodes - 1);
+                    if (MODE != kVI && g.refine) c = fibonacci_refine(ev, T, g.fib_n0, g.fib_stop, k, D, D);
+                    if (MODE != kVI) code[j] = (uint16_t)c;
+                    if constexpr (kFP32 && MODE != kVI) {
+                        if (feet) feet[j] = ev.foot_of(c);
+                    }
+                }
+                vnew = bellman_value<G, S>(g, vj, D);
+            } else if constexpr (kFP32 && MODE != kVI && MODE != kEval) {
+                if (feet) feet[j] = foot_word_kind(kFootTarget);
             }
-            vnew = bellman_value<G, S>(g, vj, D);
         }
         Vout[j] = vnew;
         resid = fmax(resid, (S)fabs(vnew - vj));
@@ -131,8 +236,8 @@ cudaError_t launch_one(const SweepLaunch<G, S>& L)
     long long cap = (long long)per_sm * L.sm_count;
     int blocks = (int)(need < cap ? need : cap);
     if (blocks < 1) blocks = 1;
-    kern<<<blocks, kBlock, 0, L.stream>>>(L.g, L.Vin, L.Vout, L.code, L.ctl, L.ring, L.ring_mask,
-                                          L.sweep, L.check_prev, L.tol);
+    kern<<<blocks, kBlock, 0, L.stream>>>(L.g, L.Vin, L.Vout, L.code, L.feet, L.ctl, L.ring, L.ring_mask, L.sweep,
+                                          L.check_prev, L.tol);
     return cudaGetLastError();
 }
 
@@ -144,6 +249,10 @@ cudaError_t launch_mode(const SweepLaunch<G, S>& L)
     case kImproveFull: return launch_one<G, S, kImproveFull, REDUCED, DYN>(L);
     case kImproveWalk: return launch_one<G, S, kImproveWalk, REDUCED, DYN>(L);
     case kEval: return launch_one<G, S, kEval, REDUCED, DYN>(L);
+    case kEvalFeet:
+        if constexpr (std::is_same<G, float>::value && std::is_same<S, float>::value)
+            return L.feet ? launch_one<G, S, kEvalFeet, REDUCED, DYN>(L) : cudaErrorInvalidValue;
+        return cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;
 }

