@@ -163,7 +163,7 @@ def oracle_step_rate(p, seconds_target=12.0, seed=2407):
     t_ev = (time.perf_counter() - t0) / n_ev
     # scale the sample to about seconds_target of CPU work
     per_step_node = t_imp + p.n_eval * t_ev
-    reps = max(1, int(seconds_target / max(per_step_node * (n_imp + n_ev), 1e-9)))
+    reps = max(1, int(seconds_target / max(per_step_node * n_imp, 1e-9)))
     t0 = time.perf_counter()
     for _ in range(reps):
         o.bellman_nodes(V, nodes, mode=oracle.IMPROVE_WALK, codes=start)
@@ -287,12 +287,20 @@ def run_ours(args, world, rank, local):
     solve = None
     if args.solve:
         torch.cuda.synchronize()
+        hist = np.zeros(args.solve_max)
         t0 = time.perf_counter()
-        rc, st = g.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=p.n_eval, polish=1, warm=0)
+        rc, st = g.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=p.n_eval, polish=1, warm=0,
+                                  time_kernels=1, history=hist)
         torch.cuda.synchronize()
+        h = hist[:st.history_count]
+        marks = sorted(set([0, 1, 2, 5, 10, 20, 50, 100, 200, 400, 800, 1600, 3200, len(h) - 1]))
         solve = {"seconds": time.perf_counter() - t0, "converged": bool(st.converged), "residual": st.residual,
                  "sweeps_improve": st.sweeps_improve, "sweeps_eval": st.sweeps_eval,
                  "sweeps_improve_fp64": st.sweeps_improve_fp64, "sweeps_eval_fp64": st.sweeps_eval_fp64,
+                 "switch_outer": st.switch_outer,
+                 "gpu_ms": {"improve": st.ms_improve, "eval": st.ms_eval, "improve_fp64": st.ms_improve_fp64,
+                            "eval_increments": st.ms_eval_fp64},
+                 "residual_trace": {int(k): float(h[k]) for k in marks if 0 <= k < len(h)},
                  "start": "cold (V = 0, full tabulation first)"}
     g.close()
 
@@ -350,7 +358,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--solve", type=int, default=1, help="also time a cold solve to 1e-6")
     ap.add_argument("--solve-max", type=int, default=3000, help="improvement-sweep budget of that solve")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.impl == "reference":

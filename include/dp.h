@@ -109,6 +109,10 @@ typedef struct dp_solve_opts {
     double  switch_tol;    /* FP32 -> FP64 switch when the improvement residual is
                               below this (<= 0: 32 ulp of max V, automatic)         */
     int32_t time_kernels;  /* 1: time every sweep with CUDA events (small overhead) */
+    double* history;       /* nullable host array: the residual of every stopping
+                              test (VI: every sweep; PI: every improvement sweep),
+                              in order, up to history_capacity entries          */
+    int64_t history_capacity;
 } dp_solve_opts;
 
 /* Solver statistics (filled on DP_OK and on DP_ENOCONV). */
@@ -125,6 +129,9 @@ typedef struct dp_solve_stats {
                                      sweep type when time_kernels = 1               */
     int64_t node_updates;         /* stored non-target nodes x sweeps               */
     int64_t launches;             /* kernels launched by the call                    */
+    int64_t history_count;        /* entries written to opts->history                */
+    int64_t switch_outer;         /* PI: improvement sweeps before the FP64 switch
+                                     (-1: no switch)                                 */
 } dp_solve_stats;
 
 /* Sizes of a grid. */

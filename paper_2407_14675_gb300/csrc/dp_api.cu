@@ -67,8 +67,10 @@ struct dp_grid {
     int cur64 = 0;
     bool fp64_values = false;
     uint16_t* code = nullptr;
-    unsigned long long* feet = nullptr;  // frozen feet of the current policy (FP32 grids)
+    unsigned long long* feet_lo = nullptr;  // frozen feet of the current policy (FP32 grids)
+    unsigned* feet_hi = nullptr;
     bool feet_valid = false;
+    float* acc = nullptr;                   // FP64-value polish: running sum of increments
     Ctl* ctl = nullptr;
     unsigned long long* ring = nullptr;
     double* staging = nullptr;           // n_active doubles
@@ -104,7 +106,8 @@ void free_grid(dp_grid* g)
     cudaSetDevice(g->device);
     if (g->st) cudaStreamSynchronize(g->st);
     void* ps[] = {g->rows, g->lines, g->hi64, g->lo64, g->hi32, g->lo32, g->V[0], g->V[1], g->V64[0],
-                  g->V64[1], g->code, g->feet, g->ctl, g->ring, g->staging, g->scratch64};
+                  g->V64[1], g->code, g->feet_lo, g->feet_hi, g->acc, g->ctl, g->ring, g->staging,
+                  g->scratch64};
     for (void* p : ps)
         if (p) cudaFree(p);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
@@ -220,7 +223,12 @@ SweepLaunch<G, S> sweep_launch(dp_grid* g, const Geo<G>& geo, const S* Vin, S* V
     L.Vin = Vin;
     L.Vout = Vout;
     L.code = g->code;
-    L.feet = g->feet;
+    L.feet_lo = g->feet_lo;
+    L.feet_hi = g->feet_hi;
+    L.inc = nullptr;
+    L.acc = nullptr;
+    L.V64 = nullptr;
+    L.incr_flags = 0;
     L.ctl = g->ctl;
     L.ring = g->ring;
     L.ring_mask = kRing - 1;
@@ -260,7 +268,7 @@ cudaError_t enqueue_sweep(dp_grid* g, int mode, long long t, int check_prev, dou
         float* out = (float*)g->V[(g->cur + a + 1) & 1];
         // improvement sweeps store the frozen feet of the new policy; the
         // evaluation sweeps after them read those instead of recomputing
-        if (mode == DP_SWEEP_IMPROVE_FULL || mode == DP_SWEEP_IMPROVE_WALK) g->feet_valid = g->feet != nullptr;
+        if (mode == DP_SWEEP_IMPROVE_FULL || mode == DP_SWEEP_IMPROVE_WALK) g->feet_valid = g->feet_lo != nullptr;
         if (mode == DP_SWEEP_EVAL && g->feet_valid) mode = kEvalFeet;
         return launch_sweep(sweep_launch<float, float>(g, g->g32, in, out, mode, t, check_prev, tol));
     }
@@ -270,6 +278,31 @@ cudaError_t enqueue_sweep(dp_grid* g, int mode, long long t, int check_prev, dou
         return launch_sweep(sweep_launch<float, double>(g, g->g32, in, out, mode, t, check_prev, tol));
     }
     }
+}
+
+// FP64-value policy iteration (FP32 grids after the switch).  The improvement
+// maps V64[c] to V64[c ^ 1] with FP64 values and writes the first increment
+// (float) and the frozen feet; the n evaluation sweeps then run on increments
+// d' = beta W d in FP32 (scratch = the grid's FP32 value buffers) and the
+// last one adds their sum to V64[c ^ 1].  Same iterates as n FP64 evaluation
+// sweeps, to FP32 rounding of the increments.
+cudaError_t enqueue_polish_improve(dp_grid* g, int mode, int c, long long t, int check_prev, double tol)
+{
+    SweepLaunch<float, double> L =
+        sweep_launch<float, double>(g, g->g32, g->V64[c], g->V64[c ^ 1], mode, t, check_prev, tol);
+    L.inc = (float*)g->V[0];
+    g->feet_valid = g->feet_lo != nullptr;
+    return launch_sweep(L);
+}
+
+cudaError_t enqueue_increment(dp_grid* g, int c, int e, int n, long long t, int check_prev, double tol)
+{
+    SweepLaunch<float, float> L = sweep_launch<float, float>(g, g->g32, (const float*)g->V[e & 1],
+                                                             (float*)g->V[(e + 1) & 1], kIncr, t, check_prev, tol);
+    L.acc = g->acc;
+    L.V64 = g->V64[c];
+    L.incr_flags = (e == 0 ? 1 : 0) | (e == n - 1 ? 2 : 0);
+    return launch_sweep(L);
 }
 
 void advance(dp_grid* g, long long done)
@@ -383,10 +416,11 @@ double now_ms()
 
 int ensure_fp64(dp_grid* g)
 {
-    if (g->V64[0]) return DP_OK;
-    int rc = dalloc(g, &g->V64[0], g->n_active);
-    if (rc) return rc;
-    return dalloc(g, &g->V64[1], g->n_active);
+    int rc;
+    if (!g->V64[0] && (rc = dalloc(g, &g->V64[0], g->n_active))) return rc;
+    if (!g->V64[1] && (rc = dalloc(g, &g->V64[1], g->n_active))) return rc;
+    if (g->fp32 && !g->acc && (rc = dalloc(g, &g->acc, g->n_active))) return rc;
+    return DP_OK;
 }
 
 int zero_value(dp_grid* g)
@@ -645,7 +679,8 @@ int dp_grid_create(const dp_grid_desc* desc, dp_grid** out)
             return bail(fail(DP_ECUDA, "memset failed"));
     }
     if ((rc = dalloc(g, &g->code, g->n_active))) return bail(rc);
-    if (g->fp32 && (rc = dalloc(g, &g->feet, g->n_active))) return bail(rc);
+    if (g->fp32 && ((rc = dalloc(g, &g->feet_lo, g->n_active)) || (rc = dalloc(g, &g->feet_hi, g->n_active))))
+        return bail(rc);
     if ((rc = dalloc(g, &g->ctl, 1))) return bail(rc);
     if ((rc = dalloc(g, &g->ring, kRing))) return bail(rc);
     if (cudaMemsetAsync(g->code, 0, sizeof(uint16_t) * g->n_active, g->st) != cudaSuccess ||
@@ -855,23 +890,33 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
     double res = INFINITY, best = INFINITY;
     int stall = 0;
     bool conv = false, first_full = !o->warm;
+    long long hist_n = 0;
+    S.switch_outer = -1;
+    auto record = [&](long long t0, long long n_imp) {
+        for (long long q = 0; q < n_imp; ++q, ++hist_n)
+            if (o->history && hist_n < o->history_capacity) o->history[hist_n] = ring_value(g, t0 + q * per);
+    };
     while (outer < o->max_sweeps) {
         const bool mix = store_of(g) == kStoreMix;
         long long n_out = std::min<long long>(per_chunk, o->max_sweeps - outer);
         if (g->fp32 && !mix && o->polish) n_out = 1;     // watch for the FP32 stall each step
         if ((rc = clear_ring(g, t, n_out * per))) return rc;
+        int c64 = g->cur64;
         for (long long q = 0; q < n_out; ++q) {
             long long ti = t + q * per;
             int mode = (first_full && q == 0) || !o->walk ? DP_SWEEP_IMPROVE_FULL : DP_SWEEP_IMPROVE_WALK;
             CK(T.begin(mix ? kTImp64 : kTImp));
             // without evaluation sweeps each improvement checks the previous one
-            CK(enqueue_sweep(g, mode, ti, o->n_eval == 0 && ti > 0, o->tol));
+            if (mix) CK(enqueue_polish_improve(g, mode, c64, ti, o->n_eval == 0 && ti > 0, o->tol));
+            else CK(enqueue_sweep(g, mode, ti, o->n_eval == 0 && ti > 0, o->tol));
             CK(T.end());
             for (int e = 0; e < o->n_eval; ++e) {
                 CK(T.begin(mix ? kTEval64 : kTEval));
-                CK(enqueue_sweep(g, DP_SWEEP_EVAL, ti + 1 + e, e == 0, o->tol));
+                if (mix) CK(enqueue_increment(g, c64 ^ 1, e, o->n_eval, ti + 1 + e, e == 0, o->tol));
+                else CK(enqueue_sweep(g, DP_SWEEP_EVAL, ti + 1 + e, e == 0, o->tol));
                 CK(T.end());
             }
+            c64 ^= 1;
             S.launches += per;
         }
         first_full = false;
@@ -891,11 +936,19 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
             // chunk-final improvement without evaluations is checked here
             if (o->n_eval == 0 && res < o->tol) conv = true;
         }
+        record(t, imp_done);
         long long evals = ran - imp_done;
         if (mix) { S.sweeps_improve_fp64 += imp_done; S.sweeps_eval_fp64 += evals; }
         else { S.sweeps_improve += imp_done; S.sweeps_eval += evals; }
         outer += imp_done;
-        t += ran;
+        if (mix) {
+            // the FP64 value moves once per improvement; the increments alternate
+            // the scratch buffers but always land in that value
+            g->cur64 = (int)((g->cur64 + imp_done) & 1);
+            t += ran;
+        } else {
+            t += ran;
+        }
         if (g->h_ctl->nonfinite) break;
         if (conv) break;
         // FP32 -> FP64 switch once the FP32 residual is small or stalls
@@ -907,11 +960,13 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
                 if ((rc = ensure_fp64(g))) return rc;
                 CK(launch_widen((const float*)g->V[g->cur], g->V64[g->cur64], (int)g->n_active, g->st));
                 g->fp64_values = true;
+                S.switch_outer = outer;
                 if ((rc = reset_ctl(g))) return rc;
             }
         }
     }
-    advance(g, t);
+    if (store_of(g) != kStoreMix) advance(g, t);
+    S.history_count = std::min<long long>(hist_n, o->history ? o->history_capacity : 0);
     S.residual = res;
     S.converged = conv && !g->h_ctl->nonfinite;
     S.node_updates = (S.sweeps_improve + S.sweeps_eval + S.sweeps_improve_fp64 + S.sweeps_eval_fp64) *

@@ -24,7 +24,7 @@ constexpr int kBlock = 256;         // threads per block of the sweep kernels
 constexpr int kMaxFib = 30;
 constexpr int kMaxAngles = 1024;   // tabulated angles per grid (shared-memory table)
 
-enum { kVI = 0, kImproveFull = 1, kImproveWalk = 2, kEval = 3, kEvalFeet = 4 };
+enum { kVI = 0, kImproveFull = 1, kImproveWalk = 2, kEval = 3, kEvalFeet = 4, kIncr = 5 };
 enum { kDynOrbit = 0, kDynUnitSpeed = 1 };
 
 // Fibonacci numbers F[1] = F[2] = 1 (index 0 unused).
@@ -335,42 +335,45 @@ __device__ __forceinline__ bool load_corners(const Geo<G>& g, const S* __restric
     return false;
 }
 
-// Frozen foot of a node under a fixed policy (FP32 grids).  Policy
+// Frozen foot of a node under a fixed policy (FP32 geometry).  Policy
 // evaluation sweeps repeat the same foot ~20 times, so the improvement sweep
-// stores it in one 64-bit word and the evaluation sweep only gathers and
-// blends:
-//   bits  0-17, 18-35, 36-53  cell fractions t_r, t_vr, t_vt in 18-bit fixed
-//                             point (q / (2^18 - 1); error <= 1.9e-6 of a cell)
-//   bits 54-55, 56-59, 60-61  cell offset from the node in r (-2..1),
-//                             v_r (-8..7), v_t (-2..1)
-//   bits 62-63                kind: inside, outside (penalty M), target node,
-//                             or "recompute from the policy code"
-// The mass coordinate needs no storage: m' = -a/c is the same at every node,
-// so its offset and fraction are grid constants (a node where they differ, at
-// the upper mass face, is marked "recompute").
+// stores it (12 bytes) and the evaluation sweep only gathers and blends:
+//   lo (64 bits): t_r bits 0-23, t_vr bits 24-47, low 16 bits of t_vt 48-63
+//   hi (32 bits): high 8 bits of t_vt 0-7, cell offset from the node in r
+//                 (-2..1) bits 8-9, v_r (-8..7) bits 10-13, v_t (-2..1) bits
+//                 14-15, kind bits 16-17 (inside, outside -> penalty M, target
+//                 node, or "recompute from the policy code")
+// Fractions are 24-bit fixed point q / (2^24 - 1), about FP32 resolution, so
+// repeated evaluation does not drift from the recomputed operator.  The mass
+// coordinate needs no storage: m' = -a/c is the same at every node, so its
+// offset and fraction are grid constants (a node where they differ, at the
+// upper mass face, is marked "recompute").
 enum { kFootInside = 0, kFootOut = 1, kFootTarget = 2, kFootRecompute = 3 };
-constexpr float kFootQ = 262143.0f;   // 2^18 - 1
+constexpr float kFootQ = 16777215.0f;   // 2^24 - 1
 
-__device__ __forceinline__ unsigned long long foot_word_kind(int kind)
+struct FootWord {
+    unsigned long long lo;
+    unsigned hi;
+};
+
+__device__ __forceinline__ FootWord foot_word_kind(int kind)
 {
-    return (unsigned long long)kind << 62;
+    return FootWord{0ull, (unsigned)kind << 16};
 }
 
 // Encodes cell c and fractions t of a foot from node i; dm, tm: the grid's
 // mass offset and fraction.
-__device__ __forceinline__ unsigned long long encode_foot(const int i[4], const int c[4], const float t[4], int dm,
-                                                          float tm)
+__device__ __forceinline__ FootWord encode_foot(const int i[4], const int c[4], const float t[4], int dm, float tm)
 {
     const int dr = c[0] - i[0], dv = c[1] - i[1], dt = c[2] - i[2];
     if (dr < -2 || dr > 1 || dv < -8 || dv > 7 || dt < -2 || dt > 1 || c[3] - i[3] != dm || t[3] != tm)
         return foot_word_kind(kFootRecompute);
-    unsigned long long w = 0;
-    w |= (unsigned long long)__float2uint_rn(t[0] * kFootQ);
-    w |= (unsigned long long)__float2uint_rn(t[1] * kFootQ) << 18;
-    w |= (unsigned long long)__float2uint_rn(t[2] * kFootQ) << 36;
-    w |= (unsigned long long)(dr + 2) << 54;
-    w |= (unsigned long long)(dv + 8) << 56;
-    w |= (unsigned long long)(dt + 2) << 60;
+    const unsigned q0 = __float2uint_rn(t[0] * kFootQ);
+    const unsigned q1 = __float2uint_rn(t[1] * kFootQ);
+    const unsigned q2 = __float2uint_rn(t[2] * kFootQ);
+    FootWord w;
+    w.lo = (unsigned long long)q0 | ((unsigned long long)q1 << 24) | ((unsigned long long)(q2 & 0xffffu) << 48);
+    w.hi = (q2 >> 16) | ((unsigned)(dr + 2) << 8) | ((unsigned)(dv + 8) << 10) | ((unsigned)(dt + 2) << 14);
     return w;
 }
 
@@ -460,8 +463,26 @@ struct CachedEval {
         return K.blend(t);
     }
 
+    // D = I[V] - vj at the foot of a code with the blend in FP64 (FP64 values):
+    // the FP32 blend has the resolution of |D|, which reaches V itself at
+    // steep fronts of V.
+    __device__ __forceinline__ double value64(int code) const
+    {
+        G s, c, u[4], t[4];
+        int cl[4], base[4];
+        code_sincos(*g, code, s, c);
+        heun_cells<G, DYN>(*g, sp, nd, s, c, u);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) u[d] += u0[d];
+        if (foot_cell(*g, i, u, cl, t) || cell_rows<G, REDUCED>(*g, cl, base)) return g->M64 - (double)vj;
+        Corners<double> K64;
+        load_rows<double, S>(V, base, g->n_m, vj, K64);
+        const double td[4] = {(double)t[0], (double)t[1], (double)t[2], (double)t[3]};
+        return K64.blend(td);
+    }
+
     // Frozen-foot word of this node for a code (FP32 geometry only).
-    __device__ __forceinline__ unsigned long long foot_of(int code) const
+    __device__ __forceinline__ FootWord foot_of(int code) const
     {
         G s, c, u[4], t[4];
         int cl[4], base[4];

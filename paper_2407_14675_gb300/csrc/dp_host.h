@@ -15,7 +15,12 @@ struct SweepLaunch {
     const S* Vin;
     S* Vout;
     uint16_t* code;
-    unsigned long long* feet;   // frozen feet (FP32 grids) or NULL
+    unsigned long long* feet_lo;   // frozen feet (FP32 geometry) or NULL
+    unsigned* feet_hi;
+    float* inc;                    // improvement: V_out - V_in (FP64-value polish) or NULL
+    float* acc;                    // kIncr: running sum of increments
+    double* V64;                   // kIncr: FP64 value that receives the sum
+    int incr_flags;                // kIncr: 1 = first sweep of the chain, 2 = last
     Ctl* ctl;
     unsigned long long* ring;   // FP64 residual bits, one slot per sweep
     int ring_mask;

@@ -86,7 +86,12 @@ int run(const Geo<G>& geo, unsigned char* scr, int mode, const void* V_in, void*
     L.Vin = (const S*)V_in;
     L.Vout = (S*)V_out;
     L.code = codes;
-    L.feet = nullptr;
+    L.feet_lo = nullptr;
+    L.feet_hi = nullptr;
+    L.inc = nullptr;
+    L.acc = nullptr;
+    L.V64 = nullptr;
+    L.incr_flags = 0;
     L.ctl = (Ctl*)(scr + kCtlOff);
     L.ring = (unsigned long long*)(scr + kRingOff);
     L.ring_mask = 0;

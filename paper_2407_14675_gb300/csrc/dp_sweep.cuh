@@ -10,9 +10,12 @@
 // host asks it to: if the stopping test passed, it records that and returns
 // without touching V, so a queue of sweeps ends at the first converged one.
 //
-// On FP32 grids the improvement sweep also stores each node's frozen foot
-// (cell offsets and fractions of the chosen control, 8 bytes); the
-// evaluation sweeps that follow (kEvalFeet) then only gather and blend.
+// Improvement sweeps with FP32 geometry also store each node's frozen foot
+// (cell offsets and fractions of the chosen control, 12 bytes).  The
+// evaluation sweeps that follow read it (kEvalFeet) and only gather and
+// blend.  With FP64 values the evaluation sweeps run on increments instead
+// (kIncr): V_{k+1} - V_k = beta W (V_k - V_{k-1}) at a frozen policy, so the
+// increments are swept in FP32 and summed into the FP64 value once.
 #pragma once
 
 #include <type_traits>
@@ -70,18 +73,19 @@ __device__ __forceinline__ void setup_node(E& ev, const Geo<G>& g, const S* __re
     ev.nd = node_dyn<G, DYN>(g, ev.sp, x);
 }
 
-// Evaluation at a frozen foot word of kind kFootInside: gather and blend.
+// Blend at a frozen foot of kind kFootInside: D = I[V] - vj.
 template <bool REDUCED>
-__device__ __forceinline__ float eval_foot(const Geo<float>& g, const float* __restrict__ V, int j,
-                                           unsigned long long w, float vj)
+__device__ __forceinline__ float eval_foot(const Geo<float>& g, const float* __restrict__ V, int j, FootWord w,
+                                           float vj)
 {
-    const int dr = (int)((w >> 54) & 3u) - 2;
-    const int dv = (int)((w >> 56) & 15u) - 8;
-    const int dt = (int)((w >> 60) & 3u) - 2;
+    const int dr = (int)((w.hi >> 8) & 3u) - 2;
+    const int dv = (int)((w.hi >> 10) & 15u) - 8;
+    const int dt = (int)((w.hi >> 14) & 3u) - 2;
+    const unsigned q2 = (unsigned)(w.lo >> 48) | ((w.hi & 0xffu) << 16);
     float t[4];
-    t[0] = (float)(unsigned)(w & 0x3ffffu) * (1.0f / kFootQ);
-    t[1] = (float)(unsigned)((w >> 18) & 0x3ffffu) * (1.0f / kFootQ);
-    t[2] = (float)(unsigned)((w >> 36) & 0x3ffffu) * (1.0f / kFootQ);
+    t[0] = (float)(unsigned)(w.lo & 0xffffffu) * (1.0f / kFootQ);
+    t[1] = (float)(unsigned)((w.lo >> 24) & 0xffffffu) * (1.0f / kFootQ);
+    t[2] = (float)q2 * (1.0f / kFootQ);
     t[3] = g.foot_tm;
     int base[4];
     if (!REDUCED) {
@@ -105,14 +109,36 @@ __device__ __forceinline__ float eval_foot(const Geo<float>& g, const float* __r
     return K.blend(t);
 }
 
+// Blend of increments d at node j's recomputed foot for a policy code: the
+// foot of an outside or target node carries no increment.
+template <bool REDUCED, int DYN>
+__device__ __forceinline__ float incr_recompute(const Geo<float>& g, const float* __restrict__ d, int j, int code)
+{
+    NodeEval<float, float, REDUCED, DYN> ev;
+    decode_node(g, j, ev.i);
+    if (in_target(g, ev.i)) return 0.0f;
+    setup_node<float, float, DYN>(ev, g, d, 0.0f);
+    float s, c, u[4], t[4];
+    int cl[4];
+    code_sincos(g, code, s, c);
+    heun_cells<float, DYN>(g, ev.sp, ev.nd, s, c, u);
+    Corners<float> K;
+    if (foot_cell(g, ev.i, u, cl, t) || load_corners<float, float, REDUCED>(g, d, cl, 0.0f, K)) return 0.0f;
+    return K.blend(t);
+}
+
 template <typename G, typename S, int MODE, bool REDUCED, int DYN>
 __global__ void __launch_bounds__(kBlock)
 sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __restrict__ Vout,
-             uint16_t* __restrict__ code, unsigned long long* __restrict__ feet, Ctl* __restrict__ ctl,
-             unsigned long long* __restrict__ ring, int ring_mask, long long sweep, int check_prev, double tol)
+             uint16_t* __restrict__ code, unsigned long long* __restrict__ feet_lo, unsigned* __restrict__ feet_hi,
+             float* __restrict__ inc, float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
+             Ctl* __restrict__ ctl, unsigned long long* __restrict__ ring, int ring_mask, long long sweep,
+             int check_prev, double tol)
 {
     constexpr bool kSearch = MODE == kVI || MODE == kImproveFull || MODE == kImproveWalk;
-    constexpr bool kFP32 = std::is_same<G, float>::value && std::is_same<S, float>::value;
+    constexpr bool kImprove = MODE == kImproveFull || MODE == kImproveWalk;
+    constexpr bool kGeo32 = std::is_same<G, float>::value;
+    constexpr bool kPolish = kGeo32 && std::is_same<S, double>::value;   // FP32 geometry, FP64 values
     if (*(volatile int*)&ctl->stop) return;
     if (check_prev) {
         unsigned long long bits = *(volatile unsigned long long*)&ring[(sweep - 1) & ring_mask];
@@ -137,48 +163,67 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
     S resid = (S)0;
     bool bad = false;
     const int stride = gridDim.x * kBlock;
-    // evaluation sweeps interpolate once per node; searches keep the cell's
-    // corners in registers across angles
-    typedef typename std::conditional<kSearch, CachedEval<G, S, REDUCED, DYN>, NodeEval<G, S, REDUCED, DYN>>::type
-        Eval;
-    if constexpr (MODE == kEvalFeet) {
-        // frozen feet: gather-bound, so the next node's foot word and value are
+
+    if constexpr (MODE == kEvalFeet || MODE == kIncr) {
+        // frozen feet: gather-bound, so the next node's foot and value are
         // fetched while this node's corners are in flight
+        const bool first = incr_flags & 1, last = incr_flags & 2;
         int j = blockIdx.x * kBlock + threadIdx.x;
-        unsigned long long w_next = 0;
+        FootWord w_next{0ull, 0u};
         S v_next = (S)0;
         if (j < g.n_nodes) {
-            w_next = feet[j];
+            w_next.lo = feet_lo[j];
+            w_next.hi = feet_hi[j];
             v_next = Vin[j];
         }
         for (; j < g.n_nodes; j += stride) {
-            const unsigned long long w = w_next;
+            const FootWord w = w_next;
             const S vj = v_next;
             if (j + stride < g.n_nodes) {
-                w_next = feet[j + stride];
+                w_next.lo = feet_lo[j + stride];
+                w_next.hi = feet_hi[j + stride];
                 v_next = Vin[j + stride];
             }
-            const int kind = (int)(w >> 62);
+            const int kind = (int)((w.hi >> 16) & 3u);
             S vnew = (S)0;
-            if (kind == kFootInside) {
-                vnew = bellman_value<G, S>(g, vj, eval_foot<REDUCED>(g, Vin, j, w, vj));
-            } else if (kind == kFootOut) {
-                vnew = bellman_value<G, S>(g, vj, (G)((S)g.M64 - vj));
-            } else if (kind == kFootRecompute) {
-                NodeEval<G, S, REDUCED, DYN> ev;
-                decode_node(g, j, ev.i);
-                setup_node<G, S, DYN>(ev, g, Vin, vj);
-                vnew = bellman_value<G, S>(g, vj, ev.at_code(code[j]));
+            if constexpr (MODE == kEvalFeet) {
+                if (kind == kFootInside) {
+                    vnew = bellman_value<G, S>(g, vj, eval_foot<REDUCED>(g, Vin, j, w, vj));
+                } else if (kind == kFootOut) {
+                    vnew = bellman_value<G, S>(g, vj, (G)((S)g.M64 - vj));
+                } else if (kind == kFootRecompute) {
+                    NodeEval<G, S, REDUCED, DYN> ev;
+                    decode_node(g, j, ev.i);
+                    setup_node<G, S, DYN>(ev, g, Vin, vj);
+                    vnew = bellman_value<G, S>(g, vj, ev.at_code(code[j]));
+                }
+                Vout[j] = vnew;
+                resid = fmax(resid, (S)fabs(vnew - vj));
+            } else {
+                // increment: d' = beta W d at the frozen policy (no running cost,
+                // no penalty: both cancel between consecutive sweeps)
+                float D = 0.0f;
+                if (kind == kFootInside) D = eval_foot<REDUCED>(g, Vin, j, w, 0.0f);
+                else if (kind == kFootRecompute) D = incr_recompute<REDUCED, DYN>(g, Vin, j, code[j]);
+                vnew = fmaf(g.beta_hi, D, g.beta_lo * D);
+                Vout[j] = vnew;
+                const float sum = (first ? 0.0f : acc[j]) + vnew;
+                if (last) V64[j] += (double)sum;
+                else acc[j] = sum;
+                resid = fmax(resid, (S)fabs(vnew));
             }
-            Vout[j] = vnew;
-            resid = fmax(resid, (S)fabs(vnew - vj));
             bad = bad || !isfinite(vnew);
         }
-    }
-    if constexpr (MODE != kEvalFeet) for (int j = blockIdx.x * kBlock + threadIdx.x; j < g.n_nodes; j += stride) {
-        const S vj = Vin[j];
-        S vnew = (S)0;
-        {
+    } else {
+        // evaluation sweeps interpolate once per node; searches keep the cell's
+        // corners in registers across angles
+        typedef typename std::conditional<kSearch, CachedEval<G, S, REDUCED, DYN>,
+                                          NodeEval<G, S, REDUCED, DYN>>::type Eval;
+        for (int j = blockIdx.x * kBlock + threadIdx.x; j < g.n_nodes; j += stride) {
+            const S vj = Vin[j];
+            S vnew = (S)0;
+            double vnew64 = 0.0;
+            (void)vnew64;
             Eval ev;
             decode_node(g, j, ev.i);
             if (!in_target(g, ev.i)) {
@@ -189,25 +234,53 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
                 } else {
                     ev.reset();
                     int k;
+                    const int c_old = MODE == kImproveWalk ? (int)code[j] : 0;
                     if (MODE == kImproveWalk)
-                        k = walk_table(ev, T, nearest_index(g.K, code[j]), D);
+                        k = walk_table(ev, T, nearest_index(g.K, c_old), D);
                     else
                         k = enumerate_table(ev, T, D);
                     int c = T.code[k] & (kCodes - 1);
                     if (MODE != kVI && g.refine) c = fibonacci_refine(ev, T, g.fib_n0, g.fib_stop, k, D, D);
+                    if constexpr (kImprove && kPolish) {
+                        // FP64 values: the FP32 search proposes, FP64 blends decide.
+                        // The policy changes only where the new code is strictly
+                        // better, so near-ties cannot flip back and forth, and the
+                        // new value is exact in FP64.
+                        double d64 = ev.value64(c);
+                        if (MODE == kImproveWalk && c != c_old) {
+                            const double d_old = ev.value64(c_old);
+                            if (!(d64 < d_old)) {
+                                c = c_old;
+                                d64 = d_old;
+                            }
+                        }
+                        vnew64 = g.dt64 + g.beta64 * ((double)vj + d64);
+                    }
                     if (MODE != kVI) code[j] = (uint16_t)c;
-                    if constexpr (kFP32 && MODE != kVI) {
-                        if (feet) feet[j] = ev.foot_of(c);
+                    if constexpr (kGeo32 && kImprove) {
+                        if (feet_lo) {
+                            const FootWord w = ev.foot_of(c);
+                            feet_lo[j] = w.lo;
+                            feet_hi[j] = w.hi;
+                        }
                     }
                 }
                 vnew = bellman_value<G, S>(g, vj, D);
-            } else if constexpr (kFP32 && MODE != kVI && MODE != kEval) {
-                if (feet) feet[j] = foot_word_kind(kFootTarget);
+                if constexpr (kImprove && kPolish) vnew = (S)vnew64;
+            } else if constexpr (kGeo32 && kImprove) {
+                if (feet_lo) {
+                    const FootWord w = foot_word_kind(kFootTarget);
+                    feet_lo[j] = w.lo;
+                    feet_hi[j] = w.hi;
+                }
             }
+            if constexpr (kImprove) {
+                if (inc) inc[j] = (float)(vnew - vj);   // first increment of the evaluation sweeps
+            }
+            Vout[j] = vnew;
+            resid = fmax(resid, (S)fabs(vnew - vj));
+            bad = bad || !isfinite(vnew);
         }
-        Vout[j] = vnew;
-        resid = fmax(resid, (S)fabs(vnew - vj));
-        bad = bad || !isfinite(vnew);
     }
 
     __shared__ S red[kBlock / 32];
@@ -236,22 +309,26 @@ cudaError_t launch_one(const SweepLaunch<G, S>& L)
     long long cap = (long long)per_sm * L.sm_count;
     int blocks = (int)(need < cap ? need : cap);
     if (blocks < 1) blocks = 1;
-    kern<<<blocks, kBlock, 0, L.stream>>>(L.g, L.Vin, L.Vout, L.code, L.feet, L.ctl, L.ring, L.ring_mask, L.sweep,
-                                          L.check_prev, L.tol);
+    kern<<<blocks, kBlock, 0, L.stream>>>(L.g, L.Vin, L.Vout, L.code, L.feet_lo, L.feet_hi, L.inc, L.acc, L.V64,
+                                          L.incr_flags, L.ctl, L.ring, L.ring_mask, L.sweep, L.check_prev, L.tol);
     return cudaGetLastError();
 }
 
 template <typename G, typename S, int DYN, bool REDUCED>
 cudaError_t launch_mode(const SweepLaunch<G, S>& L)
 {
+    constexpr bool f32 = std::is_same<G, float>::value && std::is_same<S, float>::value;
     switch (L.mode) {
     case kVI: return launch_one<G, S, kVI, REDUCED, DYN>(L);
     case kImproveFull: return launch_one<G, S, kImproveFull, REDUCED, DYN>(L);
     case kImproveWalk: return launch_one<G, S, kImproveWalk, REDUCED, DYN>(L);
     case kEval: return launch_one<G, S, kEval, REDUCED, DYN>(L);
     case kEvalFeet:
-        if constexpr (std::is_same<G, float>::value && std::is_same<S, float>::value)
-            return L.feet ? launch_one<G, S, kEvalFeet, REDUCED, DYN>(L) : cudaErrorInvalidValue;
+        if constexpr (f32) return L.feet_lo ? launch_one<G, S, kEvalFeet, REDUCED, DYN>(L) : cudaErrorInvalidValue;
+        return cudaErrorInvalidValue;
+    case kIncr:
+        if constexpr (f32)
+            return (L.feet_lo && L.acc && L.V64) ? launch_one<G, S, kIncr, REDUCED, DYN>(L) : cudaErrorInvalidValue;
         return cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;

@@ -60,6 +60,8 @@ class dp_solve_opts(C.Structure):
         ("polish", C.c_int32),
         ("switch_tol", C.c_double),
         ("time_kernels", C.c_int32),
+        ("history", C.POINTER(C.c_double)),
+        ("history_capacity", C.c_int64),
     ]
 
 
@@ -80,6 +82,8 @@ class dp_solve_stats(C.Structure):
         ("ms_eval_fp64", C.c_double),
         ("node_updates", C.c_int64),
         ("launches", C.c_int64),
+        ("history_count", C.c_int64),
+        ("switch_outer", C.c_int64),
     ]
 
     def asdict(self):
@@ -251,10 +255,15 @@ def dp_bellman_sweep_noalloc(desc: dp_grid_desc, mode: int, V_in: int, V_out: in
 
 
 def make_opts(tol=1e-6, max_sweeps=100000, n_eval=20, walk=1, warm=0, polish=1, switch_tol=0.0,
-              time_kernels=0) -> dp_solve_opts:
+              time_kernels=0, history=None) -> dp_solve_opts:
+    """Solver options; history: optional float64 numpy array that receives the
+    residual of every stopping test (kept alive by the caller)."""
     o = dp_solve_opts()
     o.tol, o.max_sweeps, o.n_eval, o.walk, o.warm = tol, max_sweeps, n_eval, walk, warm
     o.polish, o.switch_tol, o.time_kernels = polish, switch_tol, time_kernels
+    if history is not None:
+        o.history = history.ctypes.data_as(C.POINTER(C.c_double))
+        o.history_capacity = len(history)
     return o
 
 
