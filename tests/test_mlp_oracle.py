@@ -1,0 +1,72 @@
+"""Pins of the FP64 warm-start network reference (oracle/mlp.py)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+
+def test_gelu_values_and_derivative():
+    # GELU(z) = z Phi(z): Phi(1) = 0.841344746068543, Phi(0) = 1/2
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0
+    assert mlp.gelu(np.array([1.0]))[0] == pytest.approx(0.841344746068543, abs=1e-15)
+    assert mlp.gelu(np.array([-1.0]))[0] == pytest.approx(-(1 - 0.841344746068543), abs=1e-15)
+    assert mlp.gelu(np.array([8.0]))[0] == pytest.approx(8.0, abs=1e-12)
+    z = np.linspace(-4, 4, 81)
+    h = 1e-6
+    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
+    assert np.abs(fd - mlp.gelu_grad(z)).max() < 1e-8
+    assert mlp.gelu_grad(np.array([0.0]))[0] == 0.5
+
+
+@pytest.mark.parametrize("sizes", [(4, 5, 6, 7, 3), (4, 256, 256, 256, 3)])
+def test_backward_matches_central_differences(sizes):
+    rng = np.random.default_rng(3)
+    params = mlp.init_params(seed=5, sizes=sizes)
+    X = rng.uniform(-1, 1, size=(6, 4))
+    T = rng.uniform(-1, 1, size=(6, 3))
+    Y, cache = mlp.forward(params, X)
+    grads = mlp.backward(params, cache, Y, T)
+    h = 1e-6
+    for li, layer in enumerate(params):
+        for pi, P in enumerate(layer):
+            flat = P.reshape(-1)
+            idx = rng.choice(flat.size, size=min(6, flat.size), replace=False)
+            for k in idx:
+                old = flat[k]
+                flat[k] = old + h
+                lp = mlp.loss(mlp.forward(params, X)[0], T)
+                flat[k] = old - h
+                lm = mlp.loss(mlp.forward(params, X)[0], T)
+                flat[k] = old
+                fd = (lp - lm) / (2 * h)
+                an = grads[li][pi].reshape(-1)[k]
+                assert an == pytest.approx(fd, rel=1e-5, abs=1e-9), (li, pi, k)
+
+
+def test_output_layer_is_linear_and_shapes():
+    params = mlp.init_params(seed=1)
+    X = np.zeros((3, 4))
+    Y, cache = mlp.forward(params, X)
+    assert Y.shape == (3, 3)
+    assert [c[1].shape[1] for c in cache] == [256, 256, 256, 3]
+    # the output is affine in the last hidden layer
+    a3 = cache[3][0]
+    assert np.allclose(Y, a3 @ params[3][0].T + params[3][1], atol=1e-14)
+
+
+def test_adam_first_step_is_lr_times_sign():
+    params = [[np.array([[1.0, -2.0]]), np.array([0.5])]]
+    grads = [[np.array([[3.0, -0.25]]), np.array([-7.0])]]
+    state = {}
+    mlp.adam_step(params, grads, state, lr=1e-3)
+    assert params[0][0] == pytest.approx(np.array([[1.0 - 1e-3, -2.0 + 1e-3]]), abs=1e-9)
+    assert params[0][1] == pytest.approx(np.array([0.5 + 1e-3]), abs=1e-9)
+
+
+def test_normalisation_maps_box_to_unit_cube():
+    lo, hi = (0.95, -0.1, 0.85, 0.9), (1.15, 0.1, 1.1, 1.0)
+    X = np.array([lo, hi, [(a + b) / 2 for a, b in zip(lo, hi)]])
+    N = mlp.normalise_states(X, lo, hi)
+    assert np.allclose(N, [[-1] * 4, [1] * 4, [0] * 4], atol=1e-12)
