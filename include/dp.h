@@ -204,6 +204,61 @@ int dp_feedback_control(const dp_grid* grid, const double* states, int32_t n, do
 int dp_simulate_closed_loop(const dp_grid* grid, const double* x0, int32_t n, double tau,
                             double h_rk4, double t_max, double* t_arrive, double* x_final);
 
+/* ---- learned warm start (not in the paper) ----
+ *
+ * A multilayer perceptron 4 -> 256 -> 256 -> 256 -> 3 (GELU, exact erf form,
+ * after each hidden layer; linear output) maps a state, normalised to [-1, 1]^4
+ * over the network's input box, to (V / M, cos alpha, sin alpha).  Weights are
+ * FP32 master copies; the two 256 x 256 layers run as BF16 x BF16 -> FP32
+ * tensor-core GEMMs (tcgen05).  Training minimises the mean squared error over
+ * the three outputs with Adam (beta1 0.9, beta2 0.999, eps 1e-8) on every node
+ * of a solved grid; the trained network then initialises V and the policy of
+ * another grid for policy iteration (dp_solve_opts.warm = 1).  The sweeps stay
+ * the judge: the warm start only changes where policy iteration starts.
+ *
+ * Parameter order of the flat FP32 vector (dp_mlp_param_count() floats):
+ * W1 (256 x 4, row = output), b1 (256), W2 (256 x 256), b2, W3 (256 x 256), b3,
+ * W4 (3 x 256), b4 (3). */
+typedef struct dp_mlp dp_mlp;
+
+typedef struct dp_mlp_train_opts {
+    int32_t  epochs;       /* passes over the grid's nodes                          */
+    int32_t  batch;        /* samples per step, multiple of 512, <= capacity        */
+    double   lr;           /* Adam step size                                        */
+    uint64_t seed;         /* permutation seeds (0: 14675)                          */
+} dp_mlp_train_opts;
+
+typedef struct dp_mlp_train_stats {
+    int64_t epochs, steps, samples;
+    double  first_epoch_loss, last_epoch_loss;   /* mean squared error per output */
+    double  ms;                                  /* GPU time of the training       */
+    double  flops;                               /* nominal forward + backward FLOPs */
+} dp_mlp_train_stats;
+
+int64_t dp_mlp_param_count(void);
+
+/* Creates a network with zeroed parameters (set them with dp_mlp_set_params)
+ * for inputs in the box [lo, hi] (4 each), processing up to batch_capacity
+ * (multiple of 512) samples per launch on `stream`. */
+int dp_mlp_create(const double* lo, const double* hi, int32_t batch_capacity, void* stream, dp_mlp** out);
+int dp_mlp_destroy(dp_mlp* mlp);
+/* Host copies of the flat FP32 parameter vector (resets Adam's moments). */
+int dp_mlp_set_params(dp_mlp* mlp, const float* params, int64_t count);
+int dp_mlp_get_params(const dp_mlp* mlp, float* params, int64_t count);
+/* Outputs (n x 3: V / M, cos, sin) at n host states (n x 4). */
+int dp_mlp_forward(dp_mlp* mlp, const double* states, int32_t n, float* out);
+/* Gradient of the mean squared error of one batch (n a multiple of 512, <=
+ * capacity) with respect to every parameter, and the loss; no update. */
+int dp_mlp_gradients(dp_mlp* mlp, const double* states, const float* targets, int32_t n, float* grads,
+                     float* loss);
+/* Trains on every stored node of a grid: targets V / M and the (cos, sin) of
+ * the grid's resident value and policy.  stats nullable. */
+int dp_mlp_train_grid(dp_mlp* mlp, dp_grid* grid, const dp_mlp_train_opts* opts, dp_mlp_train_stats* stats);
+/* Writes V = M clamp(V/M-hat, 0, 1) (0 on target nodes) and the policy code of
+ * atan2(sin-hat, cos-hat) at every stored node of a grid.  *ms (nullable):
+ * GPU time. */
+int dp_warm_start(dp_mlp* mlp, dp_grid* grid, double* ms);
+
 /* One Jacobi sweep that allocates nothing (the paper has no counterpart: this
  * call exists for callers that cannot allocate device memory).
  *

@@ -527,8 +527,51 @@ int loop_common(const dp_grid* cg, const double* states, int n, double tau, doub
 namespace dpk {
 
 // Records an error message for dp_last_error() and returns code (used by the
-// allocation-free entry point in dp_noalloc.cu).
+// allocation-free entry point in dp_noalloc.cu and the network in dp_mlp.cu).
 int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+// Resident state of a grid for the warm-start network (dp_mlp.cu).
+struct GridView {
+    Geo<double> g64;
+    int fp32;
+    const void* V;
+    double* V64;
+    uint16_t* code;
+    long long n;
+    double M;
+    double lo[4], hi[4];
+    cudaStream_t st;
+    const double2* tab_hi64;
+    const double2* tab_lo64;
+};
+
+int grid_view(dp_grid* g, GridView* v)
+{
+    if (!g || !v) return fail(DP_EINVAL, "NULL argument");
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
+    v->g64 = g->g64;
+    v->fp32 = g->fp32;
+    v->V = g->V[g->cur];
+    v->V64 = g->fp32 ? (g->fp64_values ? g->V64[g->cur64] : nullptr) : (double*)g->V[g->cur];
+    v->code = g->code;
+    v->n = g->n_active;
+    v->M = g->M;
+    for (int k = 0; k < 4; ++k) {
+        v->lo[k] = g->d.lo[k];
+        v->hi[k] = g->d.hi[k];
+    }
+    v->st = g->st;
+    v->tab_hi64 = g->hi64;
+    v->tab_lo64 = g->lo64;
+    return DP_OK;
+}
+
+// After a warm start wrote V (storage precision) and the policy.
+void grid_after_warm_start(dp_grid* g)
+{
+    g->fp64_values = false;
+    g->feet_valid = false;
+}
 
 // Validation and sweep geometry of a full-box grid described by desc, without
 // building a grid: the same checks and target box as dp_grid_create, the
@@ -902,6 +945,8 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
         if (g->fp32 && !mix && o->polish) n_out = 1;     // watch for the FP32 stall each step
         if ((rc = clear_ring(g, t, n_out * per))) return rc;
         int c64 = g->cur64;
+        const bool first_full_chunk = first_full;
+        bool confirm_next = false;
         for (long long q = 0; q < n_out; ++q) {
             long long ti = t + q * per;
             int mode = (first_full && q == 0) || !o->walk ? DP_SWEEP_IMPROVE_FULL : DP_SWEEP_IMPROVE_WALK;
@@ -936,6 +981,14 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
             // chunk-final improvement without evaluations is checked here
             if (o->n_eval == 0 && res < o->tol) conv = true;
         }
+        // The local walk stops at a local minimum of the tabulated angles, so a
+        // converged walk is confirmed by one full-tabulation improvement: the
+        // solve ends only when that sweep also moves V by less than tol.
+        const bool last_was_walk = !(first_full_chunk && imp_done == 1) && o->walk;
+        if (conv && last_was_walk) {
+            conv = false;
+            confirm_next = true;
+        }
         record(t, imp_done);
         long long evals = ran - imp_done;
         if (mix) { S.sweeps_improve_fp64 += imp_done; S.sweeps_eval_fp64 += evals; }
@@ -951,6 +1004,11 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
         }
         if (g->h_ctl->nonfinite) break;
         if (conv) break;
+        if (confirm_next) {
+            first_full = true;
+            if ((rc = reset_ctl(g))) return rc;
+            continue;
+        }
         // FP32 -> FP64 switch once the FP32 residual is small or stalls
         if (g->fp32 && !mix && o->polish) {
             if (res < best * 0.999) { best = res; stall = 0; } else ++stall;

@@ -17,6 +17,8 @@
 #include <math_constants.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace dpk {
 
 constexpr int kCodes = 65536;       // 16-bit angle lattice, alpha = 2 pi c / 65536
@@ -325,13 +327,21 @@ __device__ __forceinline__ void load_rows(const S* __restrict__ V, const int bas
     K.set(a, d);
 }
 
-template <typename G, typename S, bool REDUCED>
+// Type in which D = I[V] - V_j is blended and compared: FP64 when the values
+// are FP64 (so that decisions resolve differences far below V), else the
+// geometry type.
+template <typename G, typename S>
+struct BlendType {
+    typedef typename std::conditional<std::is_same<S, double>::value, double, G>::type type;
+};
+
+template <typename R, typename G, typename S, bool REDUCED>
 __device__ __forceinline__ bool load_corners(const Geo<G>& g, const S* __restrict__ V, const int c[4], S vj,
-                                             Corners<G>& K)
+                                             Corners<R>& K)
 {
     int base[4];
     if (cell_rows<G, REDUCED>(g, c, base)) return true;
-    load_rows<G, S>(V, base, g.n_m, vj, K);
+    load_rows<R, S>(V, base, g.n_m, vj, K);
     return false;
 }
 
@@ -380,20 +390,23 @@ __device__ __forceinline__ FootWord encode_foot(const int i[4], const int c[4], 
 // Q1 interpolation at the foot i + u (grid units), returned as the difference
 // D = I[V] - vj; M - vj when the foot is outside the box or the node set.
 template <typename G, typename S, bool REDUCED>
-__device__ __forceinline__ G interp_delta(const Geo<G>& g, const S* __restrict__ V, const int i[4],
-                                          const G u[4], S vj)
+__device__ __forceinline__ typename BlendType<G, S>::type interp_delta(const Geo<G>& g, const S* __restrict__ V,
+                                                                       const int i[4], const G u[4], S vj)
 {
+    typedef typename BlendType<G, S>::type R;
     int c[4];
     G t[4];
-    Corners<G> K;
-    if (foot_cell(g, i, u, c, t) || load_corners<G, S, REDUCED>(g, V, c, vj, K)) return (G)((S)g.M64 - vj);
-    return K.blend(t);
+    Corners<R> K;
+    if (foot_cell(g, i, u, c, t) || load_corners<R, G, S, REDUCED>(g, V, c, vj, K)) return (R)((S)g.M64 - vj);
+    const R tr[4] = {(R)t[0], (R)t[1], (R)t[2], (R)t[3]};
+    return K.blend(tr);
 }
 
 // Control-dependent evaluation at one state: node i plus the offset u0 (both
 // in grid units; u0 = 0 at a grid node).  One interpolation per call.
 template <typename G, typename S, bool REDUCED, int DYN>
 struct NodeEval {
+    typedef typename BlendType<G, S>::type R;
     const Geo<G>* g;
     const S* __restrict__ V;
     StepP<G> sp;
@@ -402,7 +415,7 @@ struct NodeEval {
     S vj;
     NodeDyn<G> nd;
 
-    __device__ __forceinline__ G at_sc(G s, G c)
+    __device__ __forceinline__ R at_sc(G s, G c)
     {
         G u[4];
         heun_cells<G, DYN>(*g, sp, nd, s, c, u);
@@ -411,7 +424,7 @@ struct NodeEval {
         return interp_delta<G, S, REDUCED>(*g, V, i, u, vj);
     }
 
-    __device__ __forceinline__ G at_code(int code)
+    __device__ __forceinline__ R at_code(int code)
     {
         G s, c;
         code_sincos(*g, code, s, c);
@@ -426,6 +439,7 @@ struct NodeEval {
 // bit-identical to NodeEval.
 template <typename G, typename S, bool REDUCED, int DYN>
 struct CachedEval {
+    typedef typename BlendType<G, S>::type R;
     const Geo<G>* g;
     const S* __restrict__ V;
     StepP<G> sp;
@@ -435,50 +449,33 @@ struct CachedEval {
     NodeDyn<G> nd;
     int cc[4];        // cached cell; cc[0] = -1: none
     bool cout;        // the cached cell has a corner outside the node set
-    Corners<G> K;
+    Corners<R> K;
 
     __device__ __forceinline__ void reset() { cc[0] = -1; }
 
-    __device__ __forceinline__ G at_code(int code)
+    __device__ __forceinline__ R at_code(int code)
     {
         G s, c;
         code_sincos(*g, code, s, c);
         return at_sc(s, c);
     }
 
-    __device__ __forceinline__ G at_sc(G s, G c)
+    __device__ __forceinline__ R at_sc(G s, G c)
     {
         G u[4], t[4];
         int cl[4];
         heun_cells<G, DYN>(*g, sp, nd, s, c, u);
 #pragma unroll
         for (int d = 0; d < 4; ++d) u[d] += u0[d];
-        if (foot_cell(*g, i, u, cl, t)) return (G)((S)g->M64 - vj);
+        if (foot_cell(*g, i, u, cl, t)) return (R)((S)g->M64 - vj);
         if (cl[0] != cc[0] || cl[1] != cc[1] || cl[2] != cc[2] || cl[3] != cc[3]) {
-            cout = load_corners<G, S, REDUCED>(*g, V, cl, vj, K);
+            cout = load_corners<R, G, S, REDUCED>(*g, V, cl, vj, K);
 #pragma unroll
             for (int d = 0; d < 4; ++d) cc[d] = cl[d];
         }
-        if (cout) return (G)((S)g->M64 - vj);
-        return K.blend(t);
-    }
-
-    // D = I[V] - vj at the foot of a code with the blend in FP64 (FP64 values):
-    // the FP32 blend has the resolution of |D|, which reaches V itself at
-    // steep fronts of V.
-    __device__ __forceinline__ double value64(int code) const
-    {
-        G s, c, u[4], t[4];
-        int cl[4], base[4];
-        code_sincos(*g, code, s, c);
-        heun_cells<G, DYN>(*g, sp, nd, s, c, u);
-#pragma unroll
-        for (int d = 0; d < 4; ++d) u[d] += u0[d];
-        if (foot_cell(*g, i, u, cl, t) || cell_rows<G, REDUCED>(*g, cl, base)) return g->M64 - (double)vj;
-        Corners<double> K64;
-        load_rows<double, S>(V, base, g->n_m, vj, K64);
-        const double td[4] = {(double)t[0], (double)t[1], (double)t[2], (double)t[3]};
-        return K64.blend(td);
+        if (cout) return (R)((S)g->M64 - vj);
+        const R tr[4] = {(R)t[0], (R)t[1], (R)t[2], (R)t[3]};
+        return K.blend(tr);
     }
 
     // Frozen-foot word of this node for a code (FP32 geometry only).
@@ -531,12 +528,13 @@ __device__ __forceinline__ int nearest_index(int K, int code)
 
 // Full tabulation; ties go to the lowest index.
 template <class E, typename G>
-__device__ __forceinline__ int enumerate_table(E& ev, const Table<G>& T, G& Dbest)
+__device__ __forceinline__ int enumerate_table(E& ev, const Table<G>& T, typename E::R& Dbest)
 {
-    G Db = ev.at_sc(T.sc[0].x, T.sc[0].y);
+    typedef typename E::R R;
+    R Db = ev.at_sc(T.sc[0].x, T.sc[0].y);
     int kb = 0;
     for (int k = 1; k < T.K; ++k) {
-        G D = ev.at_sc(T.sc[k].x, T.sc[k].y);
+        R D = ev.at_sc(T.sc[k].x, T.sc[k].y);
         if (D < Db) { Db = D; kb = k; }
     }
     Dbest = Db;
@@ -546,14 +544,15 @@ __device__ __forceinline__ int enumerate_table(E& ev, const Table<G>& T, G& Dbes
 // Local walk from k0 towards the strictly lower tabulated neighbour (left
 // wins a tie between neighbours) until neither neighbour is lower.
 template <class E, typename G>
-__device__ __forceinline__ int walk_table(E& ev, const Table<G>& T, int k0, G& Dbest)
+__device__ __forceinline__ int walk_table(E& ev, const Table<G>& T, int k0, typename E::R& Dbest)
 {
+    typedef typename E::R R;
     const int K = T.K;
     int k = k0;
     int kl = k == 0 ? K - 1 : k - 1, kr = k == K - 1 ? 0 : k + 1;
-    G Dk = ev.at_sc(T.sc[k].x, T.sc[k].y);
-    G Dl = ev.at_sc(T.sc[kl].x, T.sc[kl].y);
-    G Dr = ev.at_sc(T.sc[kr].x, T.sc[kr].y);
+    R Dk = ev.at_sc(T.sc[k].x, T.sc[k].y);
+    R Dl = ev.at_sc(T.sc[kl].x, T.sc[kl].y);
+    R Dr = ev.at_sc(T.sc[kr].x, T.sc[kr].y);
     // one evaluation per step, outside the branch, so that lanes of a warp that
     // walk in different directions share it
     for (int step = 0; step < K; ++step) {
@@ -569,7 +568,7 @@ __device__ __forceinline__ int walk_table(E& ev, const Table<G>& T, int k0, G& D
             kr = k == K - 1 ? 0 : k + 1;
             kn = kr;
         }
-        const G Dn = ev.at_sc(T.sc[kn].x, T.sc[kn].y);
+        const R Dn = ev.at_sc(T.sc[kn].x, T.sc[kn].y);
         if (go_l) Dl = Dn;
         else Dr = Dn;
     }
@@ -583,9 +582,10 @@ __device__ __forceinline__ int walk_table(E& ev, const Table<G>& T, int k0, G& D
 // evaluated code (the tabulated minimiser included).  n0 is a lower bound of
 // the Fibonacci index of the bracket length.
 template <class E, typename G>
-__device__ __forceinline__ int fibonacci_refine(E& ev, const Table<G>& T, int n0, int fib_stop, int k, G Dk,
-                                                G& Dbest)
+__device__ __forceinline__ int fibonacci_refine(E& ev, const Table<G>& T, int n0, int fib_stop, int k,
+                                                typename E::R Dk, typename E::R& Dbest)
 {
+    typedef typename E::R R;
     const int ck = T.code[k];
     const int cl = (k == 0) ? T.code[T.K - 1] - kCodes : T.code[k - 1];
     const int cr = T.code[k + 1];
@@ -593,11 +593,11 @@ __device__ __forceinline__ int fibonacci_refine(E& ev, const Table<G>& T, int n0
     int n = n0;
     while (kFib[n] < L) ++n;
     int best = ck;
-    G qb = Dk;
+    R qb = Dk;
     int a = lo_off;
     int x1 = a + kFib[n - 2], x2 = a + kFib[n - 1];
-    G f1 = (x1 >= hi_off) ? ginf<G>() : ev.at_code(ck + x1);
-    G f2 = (x2 >= hi_off) ? ginf<G>() : ev.at_code(ck + x2);
+    R f1 = (x1 >= hi_off) ? ginf<R>() : ev.at_code(ck + x1);
+    R f2 = (x2 >= hi_off) ? ginf<R>() : ev.at_code(ck + x2);
     if (f1 < qb) { qb = f1; best = ck + x1; }
     if (f2 < qb) { qb = f2; best = ck + x2; }
     for (int kk = n; kk > 4 && kFib[kk] > fib_stop; --kk) {
@@ -615,7 +615,7 @@ __device__ __forceinline__ int fibonacci_refine(E& ev, const Table<G>& T, int n0
             x2 = a + kFib[kk - 2];
             xn = x2;
         }
-        const G fn = (xn >= hi_off) ? ginf<G>() : ev.at_code(ck + xn);
+        const R fn = (xn >= hi_off) ? ginf<R>() : ev.at_code(ck + xn);
         if (left) f1 = fn;
         else f2 = fn;
         if (fn < qb) { qb = fn; best = ck + xn; }

@@ -82,17 +82,18 @@ loop_kernel(const __grid_constant__ Geo<G> g, const __grid_constant__ LoopLaunch
         ev.vj = (S)ev.at_code(0);
         ev.reset();          // cached corners are differences to the old vj
 
-        G Db = ginf<G>();
+        typedef typename CachedEval<G, S, REDUCED, DYN>::R R;
+        R Db = ginf<R>();
         int kb = 0x7fffffff;
         for (int k = lane; k < g.K; k += 32) {
-            G D = ev.at_sc(T.sc[k].x, T.sc[k].y);
-            if (better<G, S>(D, k, Db, kb)) { Db = D; kb = k; }
+            R D = ev.at_sc(T.sc[k].x, T.sc[k].y);
+            if (better<R, S>(D, k, Db, kb)) { Db = D; kb = k; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            G Do = __shfl_xor_sync(0xffffffffu, Db, o);
+            R Do = __shfl_xor_sync(0xffffffffu, Db, o);
             int ko = __shfl_xor_sync(0xffffffffu, kb, o);
-            if (better<G, S>(Do, ko, Db, kb)) { Db = Do; kb = ko; }
+            if (better<R, S>(Do, ko, Db, kb)) { Db = Do; kb = ko; }
         }
         int code = T.code[kb] & (kCodes - 1);
         if (g.refine) code = fibonacci_refine(ev, T, g.fib_n0, g.fib_stop, kb, Db, Db);

@@ -1,0 +1,726 @@
+// dp_mlp.cu -- the learned warm start: a 4 -> 256 -> 256 -> 256 -> 3 BF16 MLP
+// (exact-erf GELU, FP32 accumulation) trained on the GPU on (state, V / M,
+// cos alpha*, sin alpha*) samples of a solved grid, then evaluated on every
+// node of another grid to initialise V and the policy of policy iteration.
+// Not part of the paper: the network only supplies the starting point, and
+// the Bellman sweeps remain the judge of the result.
+//
+// The two 256 x 256 layers (98.6 % of the FLOPs) run on the fifth-generation
+// tensor cores: tcgen05.mma kind::f16, BF16 operands staged in shared memory,
+// FP32 accumulators in TMEM, fused epilogues (bias + GELU forward, GELU'
+// backward, split-K atomic accumulation for weight gradients).  The 4-wide
+// input layer, the 3-wide output layer, the reductions and Adam run on the
+// CUDA cores.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "dp.h"
+#include "dp_host.h"
+#include "dp_umma.cuh"
+
+namespace dpk {
+int record_error(int code, const char* msg);
+
+// View of a grid's resident state (defined in dp_api.cu).
+struct GridView {
+    Geo<double> g64;
+    int fp32;
+    const void* V;       // storage precision (FP32 or FP64), compact order
+    double* V64;         // FP64 value when the grid holds one (else NULL)
+    uint16_t* code;
+    long long n;
+    double M;
+    double lo[4], hi[4];
+    cudaStream_t st;
+    const double2* tab_hi64;
+    const double2* tab_lo64;
+};
+int grid_view(dp_grid* g, GridView* v);
+void grid_after_warm_start(dp_grid* g);
+}  // namespace dpk
+
+using namespace dpk;
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int kH = 256;                       // hidden width
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kH * 4, kOffW2 = kOffB1 + kH, kOffB2 = kOffW2 + kH * kH;
+constexpr int kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH * kH, kOffW4 = kOffB3 + kH, kOffB4 = kOffW4 + 3 * kH;
+constexpr int kParams = kOffB4 + 3;           // 133,635
+constexpr int kTileM = 128, kKC = 64;
+constexpr int kGemmSmem = 80 * 1024;          // 48 KB of tiles; 80 KB keeps <= 2 CTAs (TMEM 2 x 256) per SM
+constexpr int kWaitPolls = 1 << 22;
+constexpr float kInvSqrt2 = 0.70710678118654752f, kInvSqrt2Pi = 0.39894228040143268f;
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * kInvSqrt2)); }
+__device__ __forceinline__ float gelu_grad(float z)
+{
+    return 0.5f * (1.0f + erff(z * kInvSqrt2)) + z * kInvSqrt2Pi * expf(-0.5f * z * z);
+}
+
+enum { kEpiFwd = 0, kEpiBwd = 1, kEpiAtomic = 2 };
+
+// C[128 x 256 tile] = A[rows, K range] * B[256, K range]^T on tcgen05.
+//   A: bf16 [*, lda] row-major (K contiguous); B: bf16 [256, ldb] row-major.
+//   Tile rows start at 128 blockIdx.x; K range [k_per_cta blockIdx.y, +k_per_cta).
+//   kEpiFwd:    z = acc + bias -> zout (optional, FP32), h = GELU(z) -> hout (bf16)
+//   kEpiBwd:    dz = acc * GELU'(zin) -> hout (bf16)
+//   kEpiAtomic: cacc += acc (FP32, split-K weight gradients)
+template <int EPI>
+__global__ void __launch_bounds__(128)
+mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb, int k_per_cta,
+                const float* __restrict__ bias, float* __restrict__ zout, const float* __restrict__ zin,
+                bf16* __restrict__ hout, float* __restrict__ cacc, int* __restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;                       // 128 x 64 bf16 = 16 KB
+    unsigned char* sB = smem + kTileM * kKC * 2;    // 256 x 64 bf16 = 32 KB
+    __shared__ unsigned tmem_slot;
+    __shared__ __align__(8) unsigned long long mbar;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tmem_alloc(&tmem_slot, kH);
+    if (tid == 0) mbar_init(&mbar);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const unsigned tmem = tmem_slot;
+    const size_t row0 = (size_t)blockIdx.x * kTileM;
+    const int kbeg = blockIdx.y * k_per_cta;
+    constexpr unsigned idesc = umma_idesc_bf16(kTileM, kH);
+
+    int phase = 0;
+    bool ok = true;
+    for (int k0 = kbeg; k0 < kbeg + k_per_cta; k0 += kKC) {
+        // core-matrix staging: (row, kb) -> ((row / 8) * 8 + kb) * 128 + (row % 8) * 16
+        for (int v = tid; v < kTileM * (kKC / 8); v += 128) {
+            const int row = v >> 3, kb = v & 7;
+            const int4 val = *(const int4*)(A + (row0 + row) * (size_t)lda + k0 + kb * 8);
+            *(int4*)(sA + ((row >> 3) * 8 + kb) * 128 + (row & 7) * 16) = val;
+        }
+        for (int v = tid; v < kH * (kKC / 8); v += 128) {
+            const int row = v >> 3, kb = v & 7;
+            const int4 val = *(const int4*)(B + (size_t)row * ldb + k0 + kb * 8);
+            *(int4*)(sB + ((row >> 3) * 8 + kb) * 128 + (row & 7) * 16) = val;
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after_sync();
+#pragma unroll
+            for (int s = 0; s < kKC / 16; ++s) {
+                const unsigned long long ad = umma_desc(smem_u32(sA) + s * 256, 128, (kKC / 8) * 128);
+                const unsigned long long bd = umma_desc(smem_u32(sB) + s * 256, 128, (kKC / 8) * 128);
+                umma_bf16(tmem, ad, bd, idesc, (k0 > kbeg || s > 0) ? 1u : 0u);
+            }
+            umma_commit(&mbar);
+        }
+        if (!mbar_wait(&mbar, phase, kWaitPolls)) {
+            ok = false;
+            if (lane == 0) atomicOr(err, 1);
+        }
+        phase ^= 1;
+        __syncthreads();
+        if (!__syncthreads_and(ok)) break;
+    }
+    fence_after_sync();
+    if (ok) {
+        const size_t r = row0 + warp * 32 + lane;   // TMEM lane = tile row
+        for (int c0 = 0; c0 < kH; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + c0, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int c = c0 + q;
+                if (EPI == kEpiFwd) {
+                    const float z = v[q] + bias[c];
+                    if (zout) zout[r * kH + c] = z;
+                    hout[r * kH + c] = __float2bfloat16(gelu(z));
+                } else if (EPI == kEpiBwd) {
+                    hout[r * kH + c] = __float2bfloat16(v[q] * gelu_grad(zin[r * kH + c]));
+                } else {
+                    atomicAdd(&cacc[r * kH + c], v[q]);
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kH);
+}
+
+// Inputs (normalised to [-1, 1]^4) and targets (V / M, cos, sin) of nodes
+// idx = (mult * (start + i) + offset) mod n of a grid (a seeded permutation).
+// Without V only the inputs are written.  Inputs are normalised to the
+// network's box (nlo, nhi).
+template <typename S>
+__global__ void batch_from_grid_kernel(Geo<double> g, const S* __restrict__ V, const uint16_t* __restrict__ code,
+                                       const double2* __restrict__ thi, const double2* __restrict__ tlo,
+                                       long long n, long long mult, long long offset, long long start, int count,
+                                       double invM, double4 nlo, double4 nhi, float* __restrict__ x,
+                                       float* __restrict__ t)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const long long j = (long long)(((unsigned long long)mult * (unsigned long long)(start + i) +
+                                     (unsigned long long)offset) % (unsigned long long)n);
+    int id[4];
+    decode_node(g, (int)j, id);
+    const double lo[4] = {nlo.x, nlo.y, nlo.z, nlo.w}, hi[4] = {nhi.x, nhi.y, nhi.z, nhi.w};
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const double xd = g.lo[d] + (double)id[d] * g.h[d];
+        x[4 * i + d] = (float)(2.0 * (xd - lo[d]) / (hi[d] - lo[d]) - 1.0);
+    }
+    if (!V) return;
+    const int c = code[j];
+    const double2 a = thi[c >> 8], b = tlo[c & 255];
+    t[3 * i + 0] = (float)((double)V[j] * invM);
+    t[3 * i + 1] = (float)(a.y * b.y - a.x * b.x);   // cos
+    t[3 * i + 2] = (float)(a.x * b.y + a.y * b.x);   // sin
+}
+
+// Arbitrary states (device, n x 4 double) normalised to [-1, 1]^4.
+__global__ void states_in_kernel(const double* __restrict__ s, int count, double4 lo, double4 hi,
+                                 float* __restrict__ x)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    x[4 * i + 0] = (float)(2.0 * (s[4 * i + 0] - lo.x) / (hi.x - lo.x) - 1.0);
+    x[4 * i + 1] = (float)(2.0 * (s[4 * i + 1] - lo.y) / (hi.y - lo.y) - 1.0);
+    x[4 * i + 2] = (float)(2.0 * (s[4 * i + 2] - lo.z) / (hi.z - lo.z) - 1.0);
+    x[4 * i + 3] = (float)(2.0 * (s[4 * i + 3] - lo.w) / (hi.w - lo.w) - 1.0);
+}
+
+// Layer 1 (4 -> 256): z1 = W1 x + b1, h1 = GELU(z1); rows >= count are zero.
+__global__ void l1_fwd_kernel(const float* __restrict__ x, const float* __restrict__ P, int count, int rows,
+                              float* __restrict__ z1, bf16* __restrict__ h1)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)rows * kH) return;
+    const int s = (int)(e / kH), o = (int)(e % kH);
+    float z = 0.0f;
+    if (s < count) {
+        const float* W = P + kOffW1 + o * 4;
+        z = P[kOffB1 + o] + W[0] * x[4 * s] + W[1] * x[4 * s + 1] + W[2] * x[4 * s + 2] + W[3] * x[4 * s + 3];
+    }
+    if (z1) z1[e] = z;
+    h1[e] = __float2bfloat16(s < count ? gelu(z) : 0.0f);
+}
+
+// Output layer (256 -> 3), one thread per sample; with targets also the loss
+// gradient dy = 2 (y - t) / (3 B) and the loss sum.
+__global__ void out_kernel(const bf16* __restrict__ h3, const float* __restrict__ P, const float* __restrict__ t,
+                           int count, float inv_n, float* __restrict__ y, float* __restrict__ dy,
+                           float* __restrict__ loss)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (s < count) {
+        float acc[3] = {P[kOffB4], P[kOffB4 + 1], P[kOffB4 + 2]};
+        const bf16* h = h3 + (size_t)s * kH;
+        for (int i = 0; i < kH; ++i) {
+            const float a = __bfloat162float(h[i]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc[k] += P[kOffW4 + k * kH + i] * a;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (y) y[3 * s + k] = acc[k];
+            if (t) {
+                const float r = acc[k] - t[3 * s + k];
+                l += r * r;
+                dy[3 * s + k] = 2.0f * r * inv_n;
+            }
+        }
+    }
+    if (loss) {
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(loss, l);
+    }
+}
+
+// dz3 = (dy W4) * GELU'(z3), one thread per (sample, feature).
+__global__ void dz3_kernel(const float* __restrict__ dy, const float* __restrict__ P, const float* __restrict__ z3,
+                           int rows, bf16* __restrict__ dz3)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)rows * kH) return;
+    const int s = (int)(e / kH), i = (int)(e % kH);
+    const float g = dy[3 * s] * P[kOffW4 + i] + dy[3 * s + 1] * P[kOffW4 + kH + i] + dy[3 * s + 2] * P[kOffW4 + 2 * kH + i];
+    dz3[e] = __float2bfloat16(g * gelu_grad(z3[e]));
+}
+
+// Per-feature reductions over a chunk of samples (thread = feature):
+//   db[o] += sum_s dz[s][o];  with X > 0 also dW[o][d] += sum_s dz[s][o] x[s][d]
+__global__ void feat_reduce_kernel(const bf16* __restrict__ dz, const float* __restrict__ x, int X, int rows,
+                                   int chunk, float* __restrict__ dW, float* __restrict__ db)
+{
+    const int o = threadIdx.x;   // 256 threads
+    const int s0 = blockIdx.x * chunk, s1 = min(rows, s0 + chunk);
+    float b = 0.0f, w[4] = {0, 0, 0, 0};
+    for (int s = s0; s < s1; ++s) {
+        const float g = __bfloat162float(dz[(size_t)s * kH + o]);
+        b += g;
+        for (int d = 0; d < X; ++d) w[d] += g * x[(size_t)s * X + d];
+    }
+    atomicAdd(&db[o], b);
+    for (int d = 0; d < X; ++d) atomicAdd(&dW[o * X + d], w[d]);
+}
+
+// Output-layer gradients: dW4[k][i] += sum_s dy[s][k] h3[s][i]; db4[k] += sum_s dy[s][k].
+__global__ void out_wgrad_kernel(const float* __restrict__ dy, const bf16* __restrict__ h3, int rows, int chunk,
+                                 float* __restrict__ dW4, float* __restrict__ db4)
+{
+    const int i = threadIdx.x;   // 256 threads
+    const int s0 = blockIdx.x * chunk, s1 = min(rows, s0 + chunk);
+    float w[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+    for (int s = s0; s < s1; ++s) {
+        const float a = __bfloat162float(h3[(size_t)s * kH + i]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            w[k] += dy[3 * s + k] * a;
+            b[k] += dy[3 * s + k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) atomicAdd(&dW4[k * kH + i], w[k]);
+    if (i < 3) atomicAdd(&db4[i], b[i]);
+}
+
+// bf16 [rows][256] -> [256][rows] (32 x 32 tiles).
+__global__ void transpose_kernel(const bf16* __restrict__ src, int rows, bf16* __restrict__ dst)
+{
+    __shared__ bf16 tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) tile[k][threadIdx.x] = src[(size_t)(r0 + k) * kH + c0 + threadIdx.x];
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) dst[(size_t)(c0 + k) * rows + r0 + threadIdx.x] = tile[threadIdx.x][k];
+}
+
+// Adam on the FP32 master parameters, then the BF16 copies of W2, W3 and
+// their transposes used by the tensor-core GEMMs.
+__global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
+                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float bc1, float bc2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = G[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * g;
+    const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    P[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+__global__ void bf16_weights_kernel(const float* __restrict__ P, bf16* __restrict__ W2, bf16* __restrict__ W3,
+                                    bf16* __restrict__ W2T, bf16* __restrict__ W3T)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;   // kH * kH threads
+    if (e >= kH * kH) return;
+    const int o = e / kH, i = e % kH;
+    W2[e] = __float2bfloat16(P[kOffW2 + e]);
+    W3[e] = __float2bfloat16(P[kOffW3 + e]);
+    W2T[i * kH + o] = __float2bfloat16(P[kOffW2 + e]);
+    W3T[i * kH + o] = __float2bfloat16(P[kOffW3 + e]);
+}
+
+// Warm start: V = M clamp(V/M-hat, 0, 1) (target nodes 0) and the code of
+// atan2(sin-hat, cos-hat), for compact nodes [start, start + count).
+template <typename S>
+__global__ void warm_write_kernel(Geo<double> g, const float* __restrict__ y, long long start, int count, double M,
+                                  S* __restrict__ V, uint16_t* __restrict__ code)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const long long j = start + i;
+    int id[4];
+    decode_node(g, (int)j, id);
+    const double v = fmin(fmax((double)y[3 * i], 0.0), 1.0) * M;
+    V[j] = in_target(g, id) ? (S)0 : (S)v;
+    const double a = atan2((double)y[3 * i + 2], (double)y[3 * i + 1]);   // (-pi, pi]
+    long long c = llrint(a * (65536.0 / 6.283185307179586476925286766559));
+    code[j] = (uint16_t)(c & 65535);
+}
+
+int fail_cuda(const char* what, cudaError_t e)
+{
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    return record_error(DP_ECUDA, buf);
+}
+
+#define MCK(call)                                                 \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return fail_cuda(#call, e_);       \
+    } while (0)
+
+}  // namespace
+
+struct dp_mlp {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    int cap = 0;                       // activation rows (multiple of 512)
+    double lo[4], hi[4];               // input box (normalisation)
+    long long step = 0;
+    float *P = nullptr, *G = nullptr, *Am = nullptr, *Av = nullptr;
+    bf16 *W2b = nullptr, *W3b = nullptr, *W2T = nullptr, *W3T = nullptr;
+    float *x = nullptr, *t = nullptr, *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *y = nullptr, *dy = nullptr;
+    bf16 *h1 = nullptr, *h2 = nullptr, *h3 = nullptr, *dz1 = nullptr, *dz2 = nullptr, *dz3 = nullptr;
+    bf16 *T1 = nullptr, *T2 = nullptr;
+    double* states = nullptr;
+    float* loss = nullptr;
+    int* err = nullptr;
+    float* h_loss = nullptr;           // pinned
+    int* h_err = nullptr;
+};
+
+namespace {
+
+void free_mlp(dp_mlp* m)
+{
+    if (!m) return;
+    cudaSetDevice(m->device);
+    if (m->st) cudaStreamSynchronize(m->st);
+    void* ps[] = {m->P, m->G, m->Am, m->Av, m->W2b, m->W3b, m->W2T, m->W3T, m->x, m->t, m->z1, m->z2, m->z3, m->y,
+                  m->dy, m->h1, m->h2, m->h3, m->dz1, m->dz2, m->dz3, m->T1, m->T2, m->states, m->loss, m->err};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    if (m->h_loss) cudaFreeHost(m->h_loss);
+    if (m->h_err) cudaFreeHost(m->h_err);
+    delete m;
+}
+
+template <typename T>
+cudaError_t malloc_n(T** p, size_t n)
+{
+    return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+int refresh_bf16(dp_mlp* m)
+{
+    bf16_weights_kernel<<<kH * kH / 256, 256, 0, m->st>>>(m->P, m->W2b, m->W3b, m->W2T, m->W3T);
+    MCK(cudaGetLastError());
+    return DP_OK;
+}
+
+template <int EPI>
+cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int rows, int k_total, int k_split,
+                 const float* bias, float* zout, const float* zin, bf16* hout, float* cacc)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(mlp_gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kGemmSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid(rows / kTileM, k_split);
+    mlp_gemm_kernel<EPI><<<grid, 128, kGemmSmem, m->st>>>(A, lda, B, ldb, k_total / k_split, bias, zout, zin, hout,
+                                                           cacc, m->err);
+    return cudaGetLastError();
+}
+
+// Forward of `count` rows held in m->x (rows padded to a multiple of 128).
+// save: keep z1..z3 for a backward pass.
+int forward(dp_mlp* m, int count, bool save, const float* targets, float inv_n)
+{
+    const int rows = (count + kTileM - 1) / kTileM * kTileM;
+    const long long e = (long long)rows * kH;
+    l1_fwd_kernel<<<(unsigned)((e + 255) / 256), 256, 0, m->st>>>(m->x, m->P, count, rows, save ? m->z1 : nullptr,
+                                                                    m->h1);
+    MCK(cudaGetLastError());
+    MCK(gemm<kEpiFwd>(m, m->h1, kH, m->W2b, kH, rows, kH, 1, m->P + kOffB2, save ? m->z2 : nullptr, nullptr, m->h2,
+                      nullptr));
+    MCK(gemm<kEpiFwd>(m, m->h2, kH, m->W3b, kH, rows, kH, 1, m->P + kOffB3, save ? m->z3 : nullptr, nullptr, m->h3,
+                      nullptr));
+    out_kernel<<<(count + 127) / 128, 128, 0, m->st>>>(m->h3, m->P, targets, count, inv_n, m->y, m->dy,
+                                                        targets ? m->loss : nullptr);
+    MCK(cudaGetLastError());
+    return DP_OK;
+}
+
+// Gradients of the mean squared error over a batch of `count` rows (count a
+// multiple of 512) into m->G; m->x / m->t hold the batch.
+int backward(dp_mlp* m, int count)
+{
+    const int rows = count;
+    const long long e = (long long)rows * kH;
+    const unsigned eb = (unsigned)((e + 255) / 256);
+    MCK(cudaMemsetAsync(m->G, 0, sizeof(float) * kParams, m->st));
+    dz3_kernel<<<eb, 256, 0, m->st>>>(m->dy, m->P, m->z3, rows, m->dz3);
+    MCK(cudaGetLastError());
+    const int chunk = 256;
+    out_wgrad_kernel<<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dy, m->h3, rows, chunk, m->G + kOffW4,
+                                                                     m->G + kOffB4);
+    MCK(cudaGetLastError());
+    // layer 3: dz2 = (dz3 W3) * GELU'(z2); dW3 = dz3^T h2; db3 = sum dz3
+    MCK(gemm<kEpiBwd>(m, m->dz3, kH, m->W3T, kH, rows, kH, 1, nullptr, nullptr, m->z2, m->dz2, nullptr));
+    dim3 tb(32, 8), tg(kH / 32, rows / 32);
+    transpose_kernel<<<tg, tb, 0, m->st>>>(m->dz3, rows, m->T1);
+    transpose_kernel<<<tg, tb, 0, m->st>>>(m->h2, rows, m->T2);
+    MCK(cudaGetLastError());
+    MCK(gemm<kEpiAtomic>(m, m->T1, rows, m->T2, rows, kH, rows, rows / 512, nullptr, nullptr, nullptr, nullptr,
+                         m->G + kOffW3));
+    feat_reduce_kernel<<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz3, nullptr, 0, rows, chunk, nullptr,
+                                                                       m->G + kOffB3);
+    MCK(cudaGetLastError());
+    // layer 2: dz1 = (dz2 W2) * GELU'(z1); dW2 = dz2^T h1; db2 = sum dz2
+    MCK(gemm<kEpiBwd>(m, m->dz2, kH, m->W2T, kH, rows, kH, 1, nullptr, nullptr, m->z1, m->dz1, nullptr));
+    transpose_kernel<<<tg, tb, 0, m->st>>>(m->dz2, rows, m->T1);
+    transpose_kernel<<<tg, tb, 0, m->st>>>(m->h1, rows, m->T2);
+    MCK(cudaGetLastError());
+    MCK(gemm<kEpiAtomic>(m, m->T1, rows, m->T2, rows, kH, rows, rows / 512, nullptr, nullptr, nullptr, nullptr,
+                         m->G + kOffW2));
+    feat_reduce_kernel<<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz2, nullptr, 0, rows, chunk, nullptr,
+                                                                       m->G + kOffB2);
+    // layer 1: dW1 = dz1^T x, db1 = sum dz1
+    feat_reduce_kernel<<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz1, m->x, 4, rows, chunk, m->G + kOffW1,
+                                                                       m->G + kOffB1);
+    MCK(cudaGetLastError());
+    return DP_OK;
+}
+
+int check_err(dp_mlp* m)
+{
+    MCK(cudaMemcpyAsync(m->h_err, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+    MCK(cudaStreamSynchronize(m->st));
+    if (*m->h_err) return record_error(DP_ETIMEOUT, "a tensor-core GEMM gave up waiting for its MMAs");
+    return DP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t dp_mlp_param_count(void) { return kParams; }
+
+int dp_mlp_create(const double* lo, const double* hi, int32_t batch_capacity, void* stream, dp_mlp** out)
+{
+    if (!out || !lo || !hi) return record_error(DP_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (batch_capacity < 512 || batch_capacity % 512 != 0 || batch_capacity > (1 << 20))
+        return record_error(DP_EINVAL, "batch_capacity must be a multiple of 512 in [512, 2^20]");
+    for (int d = 0; d < 4; ++d)
+        if (!(lo[d] < hi[d])) return record_error(DP_EINVAL, "input box needs lo < hi");
+    dp_mlp* m = new (std::nothrow) dp_mlp();
+    if (!m) return record_error(DP_ENOMEM, "host allocation failed");
+    m->st = (cudaStream_t)stream;
+    m->cap = batch_capacity;
+    for (int d = 0; d < 4; ++d) { m->lo[d] = lo[d]; m->hi[d] = hi[d]; }
+    cudaGetDevice(&m->device);
+    const size_t C = (size_t)m->cap, CH = C * kH;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, size_t n) { if (e == cudaSuccess) e = malloc_n(p, n); };
+    A(&m->P, kParams); A(&m->G, kParams); A(&m->Am, kParams); A(&m->Av, kParams);
+    A(&m->W2b, kH * kH); A(&m->W3b, kH * kH); A(&m->W2T, kH * kH); A(&m->W3T, kH * kH);
+    A(&m->x, C * 4); A(&m->t, C * 3); A(&m->y, C * 3); A(&m->dy, C * 3);
+    A(&m->z1, CH); A(&m->z2, CH); A(&m->z3, CH);
+    A(&m->h1, CH); A(&m->h2, CH); A(&m->h3, CH); A(&m->dz1, CH); A(&m->dz2, CH); A(&m->dz3, CH);
+    A(&m->T1, CH); A(&m->T2, CH);
+    A(&m->states, C * 4); A(&m->loss, 1); A(&m->err, 1);
+    if (e == cudaSuccess) e = cudaMallocHost(&m->h_loss, sizeof(float));
+    if (e == cudaSuccess) e = cudaMallocHost(&m->h_err, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_mlp(m);
+        return record_error(DP_ENOMEM, "device allocation of the network failed");
+    }
+    cudaMemsetAsync(m->Am, 0, sizeof(float) * kParams, m->st);
+    cudaMemsetAsync(m->Av, 0, sizeof(float) * kParams, m->st);
+    cudaMemsetAsync(m->err, 0, sizeof(int), m->st);
+    *out = m;
+    return DP_OK;
+}
+
+int dp_mlp_destroy(dp_mlp* m)
+{
+    free_mlp(m);
+    return DP_OK;
+}
+
+int dp_mlp_set_params(dp_mlp* m, const float* params, int64_t count)
+{
+    if (!m || !params) return record_error(DP_EINVAL, "NULL argument");
+    if (count != kParams) return record_error(DP_EINVAL, "parameter count mismatch");
+    MCK(cudaMemcpyAsync(m->P, params, sizeof(float) * kParams, cudaMemcpyHostToDevice, m->st));
+    MCK(cudaMemsetAsync(m->Am, 0, sizeof(float) * kParams, m->st));
+    MCK(cudaMemsetAsync(m->Av, 0, sizeof(float) * kParams, m->st));
+    m->step = 0;
+    int rc = refresh_bf16(m);
+    if (rc) return rc;
+    MCK(cudaStreamSynchronize(m->st));
+    return DP_OK;
+}
+
+int dp_mlp_get_params(const dp_mlp* m, float* params, int64_t count)
+{
+    if (!m || !params) return record_error(DP_EINVAL, "NULL argument");
+    if (count != kParams) return record_error(DP_EINVAL, "parameter count mismatch");
+    MCK(cudaMemcpyAsync(params, m->P, sizeof(float) * kParams, cudaMemcpyDeviceToHost, m->st));
+    MCK(cudaStreamSynchronize(m->st));
+    return DP_OK;
+}
+
+int dp_mlp_forward(dp_mlp* m, const double* states, int32_t n, float* out)
+{
+    if (!m || (n > 0 && (!states || !out))) return record_error(DP_EINVAL, "NULL argument");
+    if (n < 0) return record_error(DP_EINVAL, "n < 0");
+    const double4 lo = make_double4(m->lo[0], m->lo[1], m->lo[2], m->lo[3]);
+    const double4 hi = make_double4(m->hi[0], m->hi[1], m->hi[2], m->hi[3]);
+    for (int s0 = 0; s0 < n; s0 += m->cap) {
+        const int cnt = std::min(m->cap, n - s0);
+        MCK(cudaMemcpyAsync(m->states, states + 4 * (size_t)s0, sizeof(double) * 4 * cnt, cudaMemcpyHostToDevice,
+                            m->st));
+        states_in_kernel<<<(cnt + 255) / 256, 256, 0, m->st>>>(m->states, cnt, lo, hi, m->x);
+        MCK(cudaGetLastError());
+        int rc = forward(m, cnt, false, nullptr, 0.0f);
+        if (rc) return rc;
+        MCK(cudaMemcpyAsync(out + 3 * (size_t)s0, m->y, sizeof(float) * 3 * cnt, cudaMemcpyDeviceToHost, m->st));
+    }
+    return check_err(m);
+}
+
+int dp_mlp_gradients(dp_mlp* m, const double* states, const float* targets, int32_t n, float* grads, float* loss)
+{
+    if (!m || !states || !targets || !grads) return record_error(DP_EINVAL, "NULL argument");
+    if (n < 512 || n % 512 != 0 || n > m->cap) return record_error(DP_EINVAL, "n must be a multiple of 512 <= capacity");
+    const double4 lo = make_double4(m->lo[0], m->lo[1], m->lo[2], m->lo[3]);
+    const double4 hi = make_double4(m->hi[0], m->hi[1], m->hi[2], m->hi[3]);
+    MCK(cudaMemcpyAsync(m->states, states, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, m->st));
+    MCK(cudaMemcpyAsync(m->t, targets, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->st));
+    states_in_kernel<<<(n + 255) / 256, 256, 0, m->st>>>(m->states, n, lo, hi, m->x);
+    MCK(cudaMemsetAsync(m->loss, 0, sizeof(float), m->st));
+    int rc = forward(m, n, true, m->t, 1.0f / (3.0f * n));
+    if (rc) return rc;
+    if ((rc = backward(m, n))) return rc;
+    MCK(cudaMemcpyAsync(grads, m->G, sizeof(float) * kParams, cudaMemcpyDeviceToHost, m->st));
+    MCK(cudaMemcpyAsync(m->h_loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->st));
+    if ((rc = check_err(m))) return rc;
+    if (loss) *loss = *m->h_loss / (3.0f * n);
+    return DP_OK;
+}
+
+int dp_mlp_train_grid(dp_mlp* m, dp_grid* grid, const dp_mlp_train_opts* o, dp_mlp_train_stats* stats)
+{
+    if (!m || !grid || !o) return record_error(DP_EINVAL, "NULL argument");
+    if (o->batch < 512 || o->batch % 512 != 0 || o->batch > m->cap || o->epochs < 0 || !(o->lr > 0))
+        return record_error(DP_EINVAL, "bad training options");
+    GridView gv;
+    int rc = grid_view(grid, &gv);
+    if (rc) return rc;
+    const long long n = gv.n;
+    if (n < o->batch) return record_error(DP_EINVAL, "grid smaller than one batch");
+    cudaEvent_t e0, e1;
+    MCK(cudaEventCreate(&e0));
+    MCK(cudaEventCreate(&e1));
+    MCK(cudaEventRecord(e0, m->st));
+    const int B = o->batch;
+    const long long steps_per_epoch = n / B;
+    const double4 nlo = make_double4(m->lo[0], m->lo[1], m->lo[2], m->lo[3]);
+    const double4 nhi = make_double4(m->hi[0], m->hi[1], m->hi[2], m->hi[3]);
+    double last_loss = 0.0, first_loss = -1.0;
+    unsigned long long rng = o->seed ? o->seed : 14675ull;
+    auto next = [&]() {   // splitmix64: seeds of the per-epoch permutation
+        rng += 0x9E3779B97F4A7C15ull;
+        unsigned long long z = rng;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto gcd = [](unsigned long long a, unsigned long long b) { while (b) { unsigned long long t = a % b; a = b; b = t; } return a; };
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int ep = 0; ep < o->epochs; ++ep) {
+        unsigned long long mult = (next() % (unsigned long long)n) | 1ull;
+        while (gcd(mult, (unsigned long long)n) != 1) mult = (mult + 2) % (unsigned long long)n;
+        const unsigned long long off = next() % (unsigned long long)n;
+        MCK(cudaMemsetAsync(m->loss, 0, sizeof(float), m->st));
+        for (long long s = 0; s < steps_per_epoch; ++s) {
+            if (gv.fp32 && !gv.V64)
+                batch_from_grid_kernel<float><<<(B + 255) / 256, 256, 0, m->st>>>(
+                    gv.g64, (const float*)gv.V, gv.code, gv.tab_hi64, gv.tab_lo64, n, (long long)mult, (long long)off,
+                    s * B, B, 1.0 / gv.M, nlo, nhi, m->x, m->t);
+            else
+                batch_from_grid_kernel<double><<<(B + 255) / 256, 256, 0, m->st>>>(
+                    gv.g64, gv.V64 ? gv.V64 : (const double*)gv.V, gv.code, gv.tab_hi64, gv.tab_lo64, n,
+                    (long long)mult, (long long)off, s * B, B, 1.0 / gv.M, nlo, nhi, m->x, m->t);
+            MCK(cudaGetLastError());
+            if ((rc = forward(m, B, true, m->t, 1.0f / (3.0f * B)))) return rc;
+            if ((rc = backward(m, B))) return rc;
+            ++m->step;
+            const float bc1 = 1.0f - powf(b1, (float)m->step), bc2 = 1.0f - powf(b2, (float)m->step);
+            adam_kernel<<<(kParams + 255) / 256, 256, 0, m->st>>>(m->P, m->G, m->Am, m->Av, kParams, (float)o->lr, b1,
+                                                                  b2, eps, bc1, bc2);
+            MCK(cudaGetLastError());
+            if ((rc = refresh_bf16(m))) return rc;
+        }
+        MCK(cudaMemcpyAsync(m->h_loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->st));
+        if ((rc = check_err(m))) return rc;
+        last_loss = *m->h_loss / (3.0 * B * (double)steps_per_epoch);
+        if (first_loss < 0) first_loss = last_loss;
+    }
+    MCK(cudaEventRecord(e1, m->st));
+    MCK(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (stats) {
+        stats->epochs = o->epochs;
+        stats->steps = steps_per_epoch * o->epochs;
+        stats->samples = (int64_t)B * steps_per_epoch * o->epochs;
+        stats->first_epoch_loss = first_loss;
+        stats->last_epoch_loss = last_loss;
+        stats->ms = ms;
+        stats->flops = 3.0 * 2.0 * 132864.0 * (double)stats->samples;   // forward + 2x backward
+    }
+    return DP_OK;
+}
+
+int dp_warm_start(dp_mlp* m, dp_grid* grid, double* ms_out)
+{
+    if (!m || !grid) return record_error(DP_EINVAL, "NULL argument");
+    GridView gv;
+    int rc = grid_view(grid, &gv);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    MCK(cudaEventCreate(&e0));
+    MCK(cudaEventCreate(&e1));
+    MCK(cudaEventRecord(e0, m->st));
+    // node coordinates of this grid, normalised to the network's own box
+    Geo<double> g = gv.g64;
+    const double4 nlo = make_double4(m->lo[0], m->lo[1], m->lo[2], m->lo[3]);
+    const double4 nhi = make_double4(m->hi[0], m->hi[1], m->hi[2], m->hi[3]);
+    for (long long s0 = 0; s0 < gv.n; s0 += m->cap) {
+        const int cnt = (int)std::min<long long>(m->cap, gv.n - s0);
+        batch_from_grid_kernel<double><<<(cnt + 255) / 256, 256, 0, m->st>>>(
+            g, (const double*)nullptr, gv.code, gv.tab_hi64, gv.tab_lo64, gv.n, 1, 0, s0, cnt, 0.0, nlo, nhi, m->x,
+            nullptr);
+        MCK(cudaGetLastError());
+        if ((rc = forward(m, cnt, false, nullptr, 0.0f))) return rc;
+        if (gv.fp32 && !gv.V64)
+            warm_write_kernel<float><<<(cnt + 255) / 256, 256, 0, m->st>>>(g, m->y, s0, cnt, gv.M, (float*)gv.V,
+                                                                         gv.code);
+        else
+            warm_write_kernel<double><<<(cnt + 255) / 256, 256, 0, m->st>>>(g, m->y, s0, cnt, gv.M, (double*)gv.V,
+                                                                          gv.code);
+        MCK(cudaGetLastError());
+    }
+    MCK(cudaEventRecord(e1, m->st));
+    if ((rc = check_err(m))) return rc;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ms_out) *ms_out = ms;
+    grid_after_warm_start(grid);
+    return DP_OK;
+}
+
+}  // extern "C"

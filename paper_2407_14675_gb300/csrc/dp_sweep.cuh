@@ -46,6 +46,11 @@ __device__ __forceinline__ double bellman_value<double, double>(const Geo<double
 {
     return g.dt64 + g.beta64 * (vj + D);
 }
+// FP32 geometry with FP64 values: D is blended in FP64.
+__device__ __forceinline__ double bellman_value(const Geo<float>& g, double vj, double D)
+{
+    return g.dt64 + g.beta64 * (vj + D);
+}
 
 template <typename S>
 __device__ __forceinline__ S warp_max(S v)
@@ -123,7 +128,7 @@ __device__ __forceinline__ float incr_recompute(const Geo<float>& g, const float
     code_sincos(g, code, s, c);
     heun_cells<float, DYN>(g, ev.sp, ev.nd, s, c, u);
     Corners<float> K;
-    if (foot_cell(g, ev.i, u, cl, t) || load_corners<float, float, REDUCED>(g, d, cl, 0.0f, K)) return 0.0f;
+    if (foot_cell(g, ev.i, u, cl, t) || load_corners<float, float, float, REDUCED>(g, d, cl, 0.0f, K)) return 0.0f;
     return K.blend(t);
 }
 
@@ -228,7 +233,7 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
             decode_node(g, j, ev.i);
             if (!in_target(g, ev.i)) {
                 setup_node<G, S, DYN>(ev, g, Vin, vj);
-                G D;
+                typename Eval::R D;
                 if constexpr (MODE == kEval) {
                     D = ev.at_code(code[j]);
                 } else {
@@ -242,19 +247,17 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
                     int c = T.code[k] & (kCodes - 1);
                     if (MODE != kVI && g.refine) c = fibonacci_refine(ev, T, g.fib_n0, g.fib_stop, k, D, D);
                     if constexpr (kImprove && kPolish) {
-                        // FP64 values: the FP32 search proposes, FP64 blends decide.
-                        // The policy changes only where the new code is strictly
-                        // better, so near-ties cannot flip back and forth, and the
-                        // new value is exact in FP64.
-                        double d64 = ev.value64(c);
+                        // FP64 values: the search blends in FP64; the policy
+                        // changes only where the new code is strictly better than
+                        // the previous one, so exact ties cannot flip back and forth
                         if (MODE == kImproveWalk && c != c_old) {
-                            const double d_old = ev.value64(c_old);
-                            if (!(d64 < d_old)) {
+                            const double d_old = ev.at_code(c_old);
+                            if (!(D < d_old)) {
                                 c = c_old;
-                                d64 = d_old;
+                                D = d_old;
                             }
                         }
-                        vnew64 = g.dt64 + g.beta64 * ((double)vj + d64);
+                        vnew64 = g.dt64 + g.beta64 * ((double)vj + (double)D);
                     }
                     if (MODE != kVI) code[j] = (uint16_t)c;
                     if constexpr (kGeo32 && kImprove) {
@@ -265,7 +268,8 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
                         }
                     }
                 }
-                vnew = bellman_value<G, S>(g, vj, D);
+                if constexpr (kPolish) vnew = (S)bellman_value(g, (double)vj, (double)D);
+                else vnew = bellman_value<G, S>(g, vj, D);
                 if constexpr (kImprove && kPolish) vnew = (S)vnew64;
             } else if constexpr (kGeo32 && kImprove) {
                 if (feet_lo) {

@@ -101,6 +101,30 @@ class dp_grid_info(C.Structure):
     ]
 
 
+class dp_mlp_train_opts(C.Structure):
+    _fields_ = [
+        ("epochs", C.c_int32),
+        ("batch", C.c_int32),
+        ("lr", C.c_double),
+        ("seed", C.c_uint64),
+    ]
+
+
+class dp_mlp_train_stats(C.Structure):
+    _fields_ = [
+        ("epochs", C.c_int64),
+        ("steps", C.c_int64),
+        ("samples", C.c_int64),
+        ("first_epoch_loss", C.c_double),
+        ("last_epoch_loss", C.c_double),
+        ("ms", C.c_double),
+        ("flops", C.c_double),
+    ]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class DPError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("dp error %d: %s" % (code, msg))
@@ -136,11 +160,21 @@ def load(path: Optional[str] = None):
         "dp_feedback_control": [_P, _P, C.c_int32, C.c_double, _P, _P],
         "dp_simulate_closed_loop": [_P, _P, C.c_int32, C.c_double, C.c_double, C.c_double, _P, _P],
         "dp_bellman_sweep_noalloc": [C.POINTER(dp_grid_desc), C.c_int32, _P, _P, _P, _dp],
+        "dp_mlp_create": [_P, _P, C.c_int32, _P, C.POINTER(_P)],
+        "dp_mlp_destroy": [_P],
+        "dp_mlp_set_params": [_P, _P, C.c_int64],
+        "dp_mlp_get_params": [_P, _P, C.c_int64],
+        "dp_mlp_forward": [_P, _P, C.c_int32, _P],
+        "dp_mlp_gradients": [_P, _P, _P, C.c_int32, _P, C.POINTER(C.c_float)],
+        "dp_mlp_train_grid": [_P, _P, C.POINTER(dp_mlp_train_opts), C.POINTER(dp_mlp_train_stats)],
+        "dp_warm_start": [_P, _P, _dp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = C.c_int
+    L.dp_mlp_param_count.argtypes = []
+    L.dp_mlp_param_count.restype = C.c_int64
     L.dp_last_error.argtypes = []
     L.dp_last_error.restype = C.c_char_p
     _lib = L
@@ -354,3 +388,104 @@ class Grid:
 
     def simulate(self, x0, tau, h_rk4, t_max):
         return dp_simulate_closed_loop(self.h, x0, tau, h_rk4, t_max)
+
+
+# ---- learned warm start --------------------------------------------------------
+
+def dp_mlp_param_count() -> int:
+    return int(load().dp_mlp_param_count())
+
+
+def dp_mlp_create(lo, hi, batch_capacity: int, stream: Optional[int] = None) -> int:
+    lo = np.ascontiguousarray(lo, np.float64)
+    hi = np.ascontiguousarray(hi, np.float64)
+    h = _P()
+    _check(load().dp_mlp_create(_host_ptr(lo, np.float64), _host_ptr(hi, np.float64), batch_capacity,
+                                current_stream() if stream is None else stream, C.byref(h)))
+    return h.value
+
+
+def dp_mlp_destroy(mlp: int) -> None:
+    _check(load().dp_mlp_destroy(mlp))
+
+
+def dp_mlp_set_params(mlp: int, params) -> None:
+    p = np.ascontiguousarray(params, np.float32)
+    _check(load().dp_mlp_set_params(mlp, _host_ptr(p, np.float32), len(p)))
+
+
+def dp_mlp_get_params(mlp: int) -> np.ndarray:
+    out = np.empty(dp_mlp_param_count(), np.float32)
+    _check(load().dp_mlp_get_params(mlp, _host_ptr(out, np.float32), len(out)))
+    return out
+
+
+def dp_mlp_forward(mlp: int, states) -> np.ndarray:
+    st = np.ascontiguousarray(states, np.float64).reshape(-1, 4)
+    out = np.empty((len(st), 3), np.float32)
+    _check(load().dp_mlp_forward(mlp, _host_ptr(st, np.float64), len(st), _host_ptr(out, np.float32)))
+    return out
+
+
+def dp_mlp_gradients(mlp: int, states, targets):
+    st = np.ascontiguousarray(states, np.float64).reshape(-1, 4)
+    tg = np.ascontiguousarray(targets, np.float32).reshape(-1, 3)
+    g = np.empty(dp_mlp_param_count(), np.float32)
+    loss = C.c_float(0)
+    _check(load().dp_mlp_gradients(mlp, _host_ptr(st, np.float64), _host_ptr(tg, np.float32), len(st),
+                                   _host_ptr(g, np.float32), C.byref(loss)))
+    return g, loss.value
+
+
+def dp_mlp_train_grid(mlp: int, grid: int, epochs=4, batch=4096, lr=1e-3, seed=14675):
+    o = dp_mlp_train_opts()
+    o.epochs, o.batch, o.lr, o.seed = epochs, batch, lr, seed
+    s = dp_mlp_train_stats()
+    _check(load().dp_mlp_train_grid(mlp, grid, C.byref(o), C.byref(s)))
+    return s
+
+
+def dp_warm_start(mlp: int, grid: int) -> float:
+    ms = C.c_double(0)
+    _check(load().dp_warm_start(mlp, grid, C.byref(ms)))
+    return ms.value
+
+
+def flatten_params(params) -> np.ndarray:
+    """[[W1, b1], ..., [W4, b4]] -> the flat FP32 parameter vector of dp.h."""
+    return np.concatenate([np.asarray(a, np.float64).reshape(-1) for layer in params for a in layer]).astype(np.float32)
+
+
+def unflatten_params(flat, sizes=(4, 256, 256, 256, 3)):
+    out, k = [], 0
+    for fi, fo in zip(sizes[:-1], sizes[1:]):
+        W = np.asarray(flat[k:k + fi * fo], np.float64).reshape(fo, fi)
+        k += fi * fo
+        b = np.asarray(flat[k:k + fo], np.float64)
+        k += fo
+        out.append([W, b])
+    return out
+
+
+class Mlp:
+    """Owning wrapper of a dp_mlp handle."""
+
+    def __init__(self, lo, hi, batch_capacity=65536, stream: Optional[int] = None):
+        self.h = dp_mlp_create(lo, hi, batch_capacity, stream)
+
+    def close(self):
+        if self.h:
+            dp_mlp_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

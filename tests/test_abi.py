@@ -14,7 +14,7 @@ def _declared():
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names |= set(re.findall(r"^\s*(?:int|const char\*)\s+(dp_\w+)\s*\(", src, flags=re.M))
+            names |= set(re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(dp_\w+)\s*\(", src, flags=re.M))
     return names
 
 
@@ -48,7 +48,8 @@ def test_struct_layouts_match_header():
     # field names of the ctypes mirrors appear in the header in the same order
     from paper_2407_14675_gb300 import dp
     src = open(os.path.join(ROOT, "include", "dp.h")).read()
-    for struct in (dp.dp_grid_desc, dp.dp_solve_opts, dp.dp_solve_stats, dp.dp_grid_info):
+    for struct in (dp.dp_grid_desc, dp.dp_solve_opts, dp.dp_solve_stats, dp.dp_grid_info, dp.dp_mlp_train_opts,
+                   dp.dp_mlp_train_stats):
         name = struct.__name__
         body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), src, flags=re.S).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
