@@ -213,6 +213,112 @@ def _config(p):
 
 # ------------------------------------------------------------------ GPU arm --
 
+def batch_leg(args, dp, W, torch):
+    """Batched transfers: the 256-transfer batch solved to 1e-6 in one set of
+    graph-replayed persistent launches, the evaluation sweep's HBM roofline,
+    and, on a sample of the same transfers, the batched FP32 solve against
+    plain FP64 policy iteration of each transfer on its own grid."""
+    probs = W.batch_transfers(count=args.batch_count)
+    out = {"transfers": len(probs)}
+    peaks, _ = _peaks()
+    with dp.Batch(probs) as b:
+        info = b.info()
+        out["nodes"] = info["nodes_total"]
+        ie, ii = b.autotune()
+        out["items"] = {"eval": ie, "improve": ii}
+        b.sweep(dp.DP_SWEEP_IMPROVE_FULL)
+        b.sweep(dp.DP_SWEEP_IMPROVE_WALK)
+        ms_e = []
+        flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+        for _ in range(6):
+            flush.zero_()
+            ms_e.append(b.sweep(dp.DP_SWEEP_EVAL)[1])
+        r, ms_w = b.sweep(dp.DP_SWEEP_IMPROVE_WALK)
+        n_upd = info["nodes_total"] - info["nodes_target"]
+        ms_eval = float(np.median(ms_e[1:]))
+        ach = 10.0 * n_upd / (ms_eval / 1e3) / 1e9
+        out["eval_sweep"] = {"ms": ms_eval, "node_updates_per_s": n_upd / (ms_eval / 1e3),
+                             "achieved_gbs": ach, "frac_of_hbm": ach / float(peaks.get("hbm_gbs", 6800.0))}
+        out["walk_sweep"] = {"ms": ms_w, "node_updates_per_s": n_upd / (ms_w / 1e3)}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, tot, per = b.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=20, polish=1)
+        secs = time.perf_counter() - t0
+        imp = np.array([q["sweeps_improve"] + q["sweeps_improve_fp64"] for q in per])
+        out["solve"] = {"seconds": secs, "converged": int(sum(q["converged"] for q in per)),
+                        "node_updates": tot.node_updates, "node_updates_per_s": tot.node_updates / secs,
+                        "launches": tot.launches, "max_residual": tot.residual,
+                        "improvements_per_transfer": {"min": int(imp.min()), "median": float(np.median(imp)),
+                                                      "max": int(imp.max())}}
+    # the same transfers, sampled: batched FP32 vs plain FP64 per grid
+    pick = [int(i) for i in np.linspace(0, len(probs) - 1, args.batch_fp64_sample)]
+    sample = [probs[i] for i in pick]
+    with dp.Batch(sample) as b:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, tot, per = b.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=20, polish=1)
+        t_b = time.perf_counter() - t0
+    t_64, conv64 = 0.0, 0
+    for q in sample:
+        with dp.Grid(q.replace(precision=W.FP64), stream=int(torch.cuda.current_stream().cuda_stream)) as g:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, s = g.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=20)
+            torch.cuda.synchronize()
+            t_64 += time.perf_counter() - t0
+            conv64 += int(s.converged)
+    out["vs_fp64_sample"] = {"transfers": pick, "batched_fp32_seconds": t_b,
+                             "batched_fp32_converged": int(tot.converged),
+                             "plain_fp64_seconds": t_64, "plain_fp64_converged": conv64,
+                             "speedup": t_64 / max(t_b, 1e-9)}
+    return out
+
+
+def warm_start_leg(args, dp, W, torch, g1, p1):
+    """Learned warm start: train the network on the converged 61^4 solve
+    (every stored node), then solve the 121^4 energy-band grid to 1e-6 from
+    V = 0 and from the network's V and policy; closed loop from 1024 seeded
+    states on the warm-started solution."""
+    p2 = W.config2()
+    out = {"grid": "121^4 box, energy band [%.4f, %.4f]" % (p2.energy_lo, p2.energy_hi)}
+    with dp.Mlp(p1.lo, p1.hi, batch_capacity=4096) as net:
+        dp.dp_mlp_set_params(net.h, dp.flatten_params(W.mlp_init_params()))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = dp.dp_mlp_train_grid(net.h, g1.h, epochs=args.mlp_epochs, batch=4096, lr=1e-3)
+        torch.cuda.synchronize()
+        tr = st.asdict()
+        tr["wall_s"] = time.perf_counter() - t0
+        tr["tflops_nominal"] = st.flops / max(st.ms, 1e-9) / 1e9
+        out["train"] = tr
+        with dp.Grid(p2, stream=int(torch.cuda.current_stream().cuda_stream)) as g2:
+            out["nodes_active"] = g2.info["n_active"]
+            for start in ("cold", "warm"):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ws_ms = 0.0
+                if start == "warm":
+                    ws_ms = dp.dp_warm_start(net.h, g2.h)
+                rc, s2 = g2.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=p2.n_eval, polish=1,
+                                           warm=int(start == "warm"))
+                torch.cuda.synchronize()
+                out[start] = {"seconds": time.perf_counter() - t0, "converged": bool(s2.converged),
+                              "residual": s2.residual, "warm_start_ms": ws_ms,
+                              "sweeps_improve": s2.sweeps_improve, "sweeps_eval": s2.sweeps_eval,
+                              "sweeps_improve_fp64": s2.sweeps_improve_fp64,
+                              "sweeps_eval_fp64": s2.sweeps_eval_fp64, "node_updates": s2.node_updates}
+            x0 = W.closed_loop_states(p2, 1024, band=(p2.energy_lo, p2.energy_hi))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ta, xf = g2.simulate(x0, p2.dt, p2.dt, 200.0)
+            out["closed_loop"] = {"states": len(x0), "seconds": time.perf_counter() - t0,
+                                  "arrived": int((ta >= 0).sum()),
+                                  "median_time": float(np.median(ta[ta >= 0])) if (ta >= 0).any() else None}
+    c, w = out["cold"], out["warm"]
+    out["speedup_wall"] = c["seconds"] / max(w["seconds"], 1e-9)
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2407_14675_gb300 import build, dp
@@ -302,7 +408,9 @@ def run_ours(args, world, rank, local):
                             "eval_increments": st.ms_eval_fp64},
                  "residual_trace": {int(k): float(h[k]) for k in marks if 0 <= k < len(h)},
                  "start": "cold (V = 0, full tabulation first)"}
+    warm = warm_start_leg(args, dp, W, torch, g, p) if (args.warm_start and args.solve and rank == 0) else None
     g.close()
+    batch = batch_leg(args, dp, W, torch) if (args.batch and rank == 0) else None
 
     if rank != 0:
         if world > 1:
@@ -342,6 +450,8 @@ def run_ours(args, world, rank, local):
                       "%.1f s FP64 single thread" % (cpu_info["nodes"], p.n_eval, cpu_info["reps"],
                                                       cpu_info["seconds"])},
         "time_to_tol": solve,
+        "warm_start": warm,
+        "batch": batch,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -359,6 +469,11 @@ def main():
     ap.add_argument("--solve", type=int, default=1, help="also time a cold solve to 1e-6")
     ap.add_argument("--solve-max", type=int, default=3000, help="improvement-sweep budget of that solve")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--warm-start", type=int, default=1, help="train the network, compare cold/warm 121^4 solves")
+    ap.add_argument("--mlp-epochs", type=int, default=2)
+    ap.add_argument("--batch", type=int, default=1, help="time the 256-transfer batch")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-fp64-sample", type=int, default=4)
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.impl == "reference":

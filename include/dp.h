@@ -107,7 +107,9 @@ typedef struct dp_solve_opts {
     int32_t polish;        /* FP32 grids: 1 = finish with FP64 values once FP32
                               stalls; 0 = stay FP32                                 */
     double  switch_tol;    /* FP32 -> FP64 switch when the improvement residual is
-                              below this (<= 0: 32 ulp of max V, automatic)         */
+                              below this (<= 0: 16 FP32 epsilons of M, automatic);
+                              the switch also happens after 3 improvements without
+                              a 0.1 % gain over the best FP32 residual              */
     int32_t time_kernels;  /* 1: time every sweep with CUDA events (small overhead) */
     double* history;       /* nullable host array: the residual of every stopping
                               test (VI: every sweep; PI: every improvement sweep),
@@ -258,6 +260,79 @@ int dp_mlp_train_grid(dp_mlp* mlp, dp_grid* grid, const dp_mlp_train_opts* opts,
  * atan2(sin-hat, cos-hat) at every stored node of a grid.  *ms (nullable):
  * GPU time. */
 int dp_warm_start(dp_mlp* mlp, dp_grid* grid, double* ms);
+
+/* ---- batched transfers ----
+ *
+ * Many independent transfers (each its own full-box grid: sizes, thrust,
+ * target, box) solved by modified policy iteration (§3, Eq. (13)/(14)) at
+ * once.  Every sweep kind is one persistent launch over all live transfers,
+ * and the outer steps are replayed from a CUDA graph; the decisions a single
+ * grid's dp_policy_iterate takes on the host (stopping test, the confirming
+ * full-table improvement after a converged walk, the FP32 -> FP64 switch)
+ * are taken per transfer on the device, so each transfer runs the same sweep
+ * sequence as dp_policy_iterate on a grid of its own.
+ *
+ * Device memory per node: 2 x 4 (FP32 V) + 2 x 8 (FP64 V) + 2 (policy) + 12
+ * (frozen foot) + 4 (increment sum) = 42 bytes, plus the line tables.
+ * Node and value order inside a transfer: box order, as for a grid. */
+typedef struct dp_batch dp_batch;
+
+/* Per-transfer results of dp_batch_policy_iterate. */
+typedef struct dp_batch_stats {
+    int64_t sweeps_improve;       /* FP32 improvement sweeps                          */
+    int64_t sweeps_eval;          /* FP32 evaluation sweeps                           */
+    int64_t sweeps_improve_fp64;  /* FP64-value improvement sweeps                    */
+    int64_t sweeps_eval_fp64;     /* FP32 increment sweeps of the FP64-value phase    */
+    double  residual;             /* last improvement residual (sup norm, FP64)      */
+    int32_t converged;
+    int32_t nonfinite;
+    int64_t switch_outer;         /* improvements before the FP64 switch (-1: none)  */
+    int64_t nodes;                /* nodes of the transfer                            */
+} dp_batch_stats;
+
+/* Builds a batch of `count` (1 .. 65536) transfers from descs[0 .. count-1]:
+ * each must be valid for dp_grid_create, full-box (reduced = 0) and FP32, and
+ * all must share one dynamics.  V = 0, policy code 0.  GPU work is issued on
+ * `stream` (NULL: a stream the batch creates; the legacy default stream cannot
+ * be captured into a graph).  Errors: DP_EINVAL (the message names the
+ * transfer), DP_ENOMEM, DP_ECUDA. */
+int dp_batch_create(const dp_grid_desc* descs, int32_t count, void* stream, dp_batch** out);
+int dp_batch_destroy(dp_batch* batch);
+/* Sizes and tuning of a batch; every output pointer is nullable.
+ * nodes_target: nodes inside the targets (never updated).  item_eval /
+ * item_improve: nodes per work item of the evaluation and improvement
+ * launches. */
+int dp_batch_get_info(const dp_batch* batch, int32_t* count, int64_t* nodes_total, int64_t* nodes_target,
+                      int32_t* item_eval, int32_t* item_improve, int64_t* device_bytes);
+/* Sets the work-item sizes (multiples of 256 in [256, 2^20]). */
+int dp_batch_set_items(dp_batch* batch, int32_t item_eval, int32_t item_improve);
+/* Times the candidate work-item sizes (512 .. 32768 nodes) of the evaluation
+ * and walk-improvement launches on this batch with CUDA events and keeps the
+ * fastest of each (returned through the nullable outputs).  It runs sweeps,
+ * so it leaves every transfer at V = 0 and policy code 0: call it before
+ * setting a warm start. */
+int dp_batch_autotune(dp_batch* batch, int32_t* item_eval, int32_t* item_improve);
+/* Modified policy iteration of every transfer with the options of
+ * dp_policy_iterate (tol, max_sweeps = improvement budget per transfer,
+ * n_eval <= 1024, walk, warm, polish, switch_tol; time_kernels and history are
+ * ignored).  total (nullable): sums of the sweep counts, node_updates,
+ * launches, the largest residual and switch_outer, converged = all converged.
+ * per (nullable): count entries.  Returns DP_ENOCONV if some transfer missed
+ * the tolerance (statistics valid), DP_ENONFINITE if one produced a non-finite
+ * value. */
+int dp_batch_policy_iterate(dp_batch* batch, const dp_solve_opts* opts, dp_solve_stats* total,
+                            dp_batch_stats* per);
+/* One Jacobi sweep of every transfer on its FP32 values (a transfer whose
+ * value is held in FP64 after a polished solve is first rounded to FP32):
+ * DP_SWEEP_IMPROVE_FULL, DP_SWEEP_IMPROVE_WALK or DP_SWEEP_EVAL (at the
+ * resident policy).  residual (nullable): count entries, max |V_out - V_in|
+ * per transfer.  ms (nullable): GPU time of the sweep launch. */
+int dp_batch_sweep(dp_batch* batch, int32_t mode, double* residual, double* ms);
+/* Value and policy of transfer `index` (count = its n0 n1 n2 n3 nodes). */
+int dp_batch_set_value(dp_batch* batch, int32_t index, const double* host_V, int64_t count);
+int dp_batch_get_value(const dp_batch* batch, int32_t index, double* host_V, int64_t count);
+int dp_batch_set_policy(dp_batch* batch, int32_t index, const uint16_t* host_codes, int64_t count);
+int dp_batch_get_policy(const dp_batch* batch, int32_t index, uint16_t* host_codes, int64_t count);
 
 /* One Jacobi sweep that allocates nothing (the paper has no counterpart: this
  * call exists for callers that cannot allocate device memory).

@@ -19,17 +19,6 @@ from scipy.special import erf
 SIZES = (4, 256, 256, 256, 3)
 
 
-def init_params(seed: int = 14675, sizes=SIZES):
-    """W_l ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)), b_l likewise; W_l is
-    (fan_out, fan_in)."""
-    rng = np.random.default_rng(seed)
-    params = []
-    for fi, fo in zip(sizes[:-1], sizes[1:]):
-        bound = 1.0 / math.sqrt(fi)
-        params.append([rng.uniform(-bound, bound, size=(fo, fi)), rng.uniform(-bound, bound, size=fo)])
-    return params
-
-
 def gelu(z):
     return 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))
 

@@ -435,11 +435,12 @@ struct NodeEval {
 // The same evaluation for searches over many angles at one state: the
 // corners of the last cell used stay in registers.  Thrust moves the foot by
 // about 1e-3 cells across all angles, so nearly every angle after the first
-// costs the Heun step and the blend, with no memory access.  Results are
-// bit-identical to NodeEval.
-template <typename G, typename S, bool REDUCED, int DYN>
+// costs the Heun step and the blend, with no memory access.  With the default
+// blend type the results are bit-identical to NodeEval; BLEND = float with
+// FP64 values blends the FP64 corner differences V_c - V_j rounded to FP32.
+template <typename G, typename S, bool REDUCED, int DYN, typename BLEND = typename BlendType<G, S>::type>
 struct CachedEval {
-    typedef typename BlendType<G, S>::type R;
+    typedef BLEND R;
     const Geo<G>* g;
     const S* __restrict__ V;
     StepP<G> sp;

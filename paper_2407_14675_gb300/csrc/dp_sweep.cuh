@@ -132,59 +132,39 @@ __device__ __forceinline__ float incr_recompute(const Geo<float>& g, const float
     return K.blend(t);
 }
 
+// Sweeps nodes j0, j0 + stride, ... < end of one grid: the per-node work of
+// every sweep mode.  Folds max |V_out - V_in| into resid and non-finite
+// results into bad.
 template <typename G, typename S, int MODE, bool REDUCED, int DYN>
-__global__ void __launch_bounds__(kBlock)
-sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __restrict__ Vout,
-             uint16_t* __restrict__ code, unsigned long long* __restrict__ feet_lo, unsigned* __restrict__ feet_hi,
-             float* __restrict__ inc, float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
-             Ctl* __restrict__ ctl, unsigned long long* __restrict__ ring, int ring_mask, long long sweep,
-             int check_prev, double tol)
+__device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, const S* __restrict__ Vin,
+                                            S* __restrict__ Vout, uint16_t* __restrict__ code,
+                                            unsigned long long* __restrict__ feet_lo,
+                                            unsigned* __restrict__ feet_hi, float* __restrict__ inc,
+                                            float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
+                                            int j0, int end, int stride, S& resid, bool& bad)
 {
     constexpr bool kSearch = MODE == kVI || MODE == kImproveFull || MODE == kImproveWalk;
     constexpr bool kImprove = MODE == kImproveFull || MODE == kImproveWalk;
     constexpr bool kGeo32 = std::is_same<G, float>::value;
     constexpr bool kPolish = kGeo32 && std::is_same<S, double>::value;   // FP32 geometry, FP64 values
-    if (*(volatile int*)&ctl->stop) return;
-    if (check_prev) {
-        unsigned long long bits = *(volatile unsigned long long*)&ring[(sweep - 1) & ring_mask];
-        if (__longlong_as_double((long long)bits) < tol) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                ctl->stop_sweep = (int)sweep;
-                ctl->stop = 1;
-            }
-            return;
-        }
-    }
-
-    // angle searches read the tabulated codes and (sin, cos) from shared memory
-    __shared__ int s_code[kSearch ? kMaxAngles + 1 : 1];
-    __shared__ typename V2<G>::type s_sc[kSearch ? kMaxAngles : 1];
-    if constexpr (kSearch) {
-        build_table(g, s_code, s_sc);
-        __syncthreads();
-    }
-    const Table<G> T{s_code, s_sc, g.K};
-
-    S resid = (S)0;
-    bool bad = false;
-    const int stride = gridDim.x * kBlock;
-
+    (void)T;
+    (void)kSearch;
     if constexpr (MODE == kEvalFeet || MODE == kIncr) {
         // frozen feet: gather-bound, so the next node's foot and value are
         // fetched while this node's corners are in flight
         const bool first = incr_flags & 1, last = incr_flags & 2;
-        int j = blockIdx.x * kBlock + threadIdx.x;
+        int j = j0;
         FootWord w_next{0ull, 0u};
         S v_next = (S)0;
-        if (j < g.n_nodes) {
+        if (j < end) {
             w_next.lo = feet_lo[j];
             w_next.hi = feet_hi[j];
             v_next = Vin[j];
         }
-        for (; j < g.n_nodes; j += stride) {
+        for (; j < end; j += stride) {
             const FootWord w = w_next;
             const S vj = v_next;
-            if (j + stride < g.n_nodes) {
+            if (j + stride < end) {
                 w_next.lo = feet_lo[j + stride];
                 w_next.hi = feet_hi[j + stride];
                 v_next = Vin[j + stride];
@@ -222,9 +202,13 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
     } else {
         // evaluation sweeps interpolate once per node; searches keep the cell's
         // corners in registers across angles
-        typedef typename std::conditional<kSearch, CachedEval<G, S, REDUCED, DYN>,
+        // FP64 values: the search blends FP32-rounded FP64 differences (about
+        // 1e-9 of a cell's value spread, far below the FP32 geometry's own
+        // noise), and the chosen code is then re-evaluated in FP64
+        typedef typename std::conditional<kPolish, float, typename BlendType<G, S>::type>::type SearchR;
+        typedef typename std::conditional<kSearch, CachedEval<G, S, REDUCED, DYN, SearchR>,
                                           NodeEval<G, S, REDUCED, DYN>>::type Eval;
-        for (int j = blockIdx.x * kBlock + threadIdx.x; j < g.n_nodes; j += stride) {
+        for (int j = j0; j < end; j += stride) {
             const S vj = Vin[j];
             S vnew = (S)0;
             double vnew64 = 0.0;
@@ -239,7 +223,7 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
                 } else {
                     ev.reset();
                     int k;
-                    const int c_old = MODE == kImproveWalk ? (int)code[j] : 0;
+                    const int c_old = (MODE == kImproveWalk || kPolish) ? (int)code[j] : 0;
                     if (MODE == kImproveWalk)
                         k = walk_table(ev, T, nearest_index(g.K, c_old), D);
                     else
@@ -247,17 +231,31 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
                     int c = T.code[k] & (kCodes - 1);
                     if (MODE != kVI && g.refine) c = fibonacci_refine(ev, T, g.fib_n0, g.fib_stop, k, D, D);
                     if constexpr (kImprove && kPolish) {
-                        // FP64 values: the search blends in FP64; the policy
-                        // changes only where the new code is strictly better than
-                        // the previous one, so exact ties cannot flip back and forth
-                        if (MODE == kImproveWalk && c != c_old) {
-                            const double d_old = ev.at_code(c_old);
-                            if (!(D < d_old)) {
+                        // FP64 blend of the chosen code.  Both the walk and the
+                        // full tabulation keep the node's current code unless the
+                        // new one is strictly better in FP64 (policy iteration's
+                        // rule for termination): otherwise the two searches, which
+                        // can stop in different local minima, undo each other
+                        NodeEval<G, S, REDUCED, DYN> e64;
+                        e64.g = ev.g;
+                        e64.V = ev.V;
+                        e64.sp = ev.sp;
+                        e64.vj = ev.vj;
+                        e64.nd = ev.nd;
+#pragma unroll
+                        for (int d = 0; d < 4; ++d) {
+                            e64.i[d] = ev.i[d];
+                            e64.u0[d] = ev.u0[d];
+                        }
+                        double d_new = e64.at_code(c);
+                        if (c != c_old) {
+                            const double d_old = e64.at_code(c_old);
+                            if (!(d_new < d_old)) {
                                 c = c_old;
-                                D = d_old;
+                                d_new = d_old;
                             }
                         }
-                        vnew64 = g.dt64 + g.beta64 * ((double)vj + (double)D);
+                        vnew64 = g.dt64 + g.beta64 * ((double)vj + d_new);
                     }
                     if (MODE != kVI) code[j] = (uint16_t)c;
                     if constexpr (kGeo32 && kImprove) {
@@ -287,16 +285,60 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
         }
     }
 
+}
+
+// Block-wide max of resid folded into *slot (FP64 bits) and the non-finite
+// flag into *nonfinite.  Every thread of the block calls it.
+template <typename S>
+__device__ __forceinline__ void block_fold(S resid, bool bad, unsigned long long* slot, int* nonfinite)
+{
     __shared__ S red[kBlock / 32];
     resid = warp_max(resid);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = resid;
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->nonfinite, 1);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(nonfinite, 1);
     if (threadIdx.x < 32) {
         S r = threadIdx.x < kBlock / 32 ? red[threadIdx.x] : (S)0;
         r = warp_max(r);
-        if (threadIdx.x == 0)
-            atomicMax(&ring[sweep & ring_mask], (unsigned long long)__double_as_longlong((double)r));
+        if (threadIdx.x == 0) atomicMax(slot, (unsigned long long)__double_as_longlong((double)r));
     }
+}
+
+template <typename G, typename S, int MODE, bool REDUCED, int DYN>
+__global__ void __launch_bounds__(kBlock)
+sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __restrict__ Vout,
+             uint16_t* __restrict__ code, unsigned long long* __restrict__ feet_lo, unsigned* __restrict__ feet_hi,
+             float* __restrict__ inc, float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
+             Ctl* __restrict__ ctl, unsigned long long* __restrict__ ring, int ring_mask, long long sweep,
+             int check_prev, double tol)
+{
+    constexpr bool kSearch = MODE == kVI || MODE == kImproveFull || MODE == kImproveWalk;
+    if (*(volatile int*)&ctl->stop) return;
+    if (check_prev) {
+        unsigned long long bits = *(volatile unsigned long long*)&ring[(sweep - 1) & ring_mask];
+        if (__longlong_as_double((long long)bits) < tol) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                ctl->stop_sweep = (int)sweep;
+                ctl->stop = 1;
+            }
+            return;
+        }
+    }
+
+    // angle searches read the tabulated codes and (sin, cos) from shared memory
+    __shared__ int s_code[kSearch ? kMaxAngles + 1 : 1];
+    __shared__ typename V2<G>::type s_sc[kSearch ? kMaxAngles : 1];
+    if constexpr (kSearch) {
+        build_table(g, s_code, s_sc);
+        __syncthreads();
+    }
+    const Table<G> T{s_code, s_sc, g.K};
+
+    S resid = (S)0;
+    bool bad = false;
+    sweep_nodes<G, S, MODE, REDUCED, DYN>(g, T, Vin, Vout, code, feet_lo, feet_hi, inc, acc, V64, incr_flags,
+                                          blockIdx.x * kBlock + threadIdx.x, g.n_nodes, gridDim.x * kBlock,
+                                          resid, bad);
+    block_fold(resid, bad, &ring[sweep & ring_mask], &ctl->nonfinite);
 }
 
 template <typename G, typename S, int MODE, bool REDUCED, int DYN>

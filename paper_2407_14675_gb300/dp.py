@@ -125,6 +125,23 @@ class dp_mlp_train_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class dp_batch_stats(C.Structure):
+    _fields_ = [
+        ("sweeps_improve", C.c_int64),
+        ("sweeps_eval", C.c_int64),
+        ("sweeps_improve_fp64", C.c_int64),
+        ("sweeps_eval_fp64", C.c_int64),
+        ("residual", C.c_double),
+        ("converged", C.c_int32),
+        ("nonfinite", C.c_int32),
+        ("switch_outer", C.c_int64),
+        ("nodes", C.c_int64),
+    ]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class DPError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("dp error %d: %s" % (code, msg))
@@ -168,6 +185,17 @@ def load(path: Optional[str] = None):
         "dp_mlp_gradients": [_P, _P, _P, C.c_int32, _P, C.POINTER(C.c_float)],
         "dp_mlp_train_grid": [_P, _P, C.POINTER(dp_mlp_train_opts), C.POINTER(dp_mlp_train_stats)],
         "dp_warm_start": [_P, _P, _dp],
+        "dp_batch_create": [_P, C.c_int32, _P, C.POINTER(_P)],
+        "dp_batch_destroy": [_P],
+        "dp_batch_get_info": [_P, _P, _P, _P, _P, _P, _P],
+        "dp_batch_set_items": [_P, C.c_int32, C.c_int32],
+        "dp_batch_autotune": [_P, _P, _P],
+        "dp_batch_policy_iterate": [_P, C.POINTER(dp_solve_opts), C.POINTER(dp_solve_stats), _P],
+        "dp_batch_sweep": [_P, C.c_int32, _P, _dp],
+        "dp_batch_set_value": [_P, C.c_int32, _P, C.c_int64],
+        "dp_batch_get_value": [_P, C.c_int32, _P, C.c_int64],
+        "dp_batch_set_policy": [_P, C.c_int32, _P, C.c_int64],
+        "dp_batch_get_policy": [_P, C.c_int32, _P, C.c_int64],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -388,6 +416,128 @@ class Grid:
 
     def simulate(self, x0, tau, h_rk4, t_max):
         return dp_simulate_closed_loop(self.h, x0, tau, h_rk4, t_max)
+
+
+# ---- batched transfers ---------------------------------------------------------
+
+def dp_batch_create(descs, stream: Optional[int] = 0) -> int:
+    """descs: a list of dp_grid_desc; stream 0: the batch makes its own."""
+    arr = (dp_grid_desc * len(descs))(*descs)
+    h = _P()
+    _check(load().dp_batch_create(arr, len(descs), C.c_void_p(stream or None), C.byref(h)))
+    return h.value
+
+
+def dp_batch_destroy(batch: int) -> None:
+    _check(load().dp_batch_destroy(batch))
+
+
+def dp_batch_get_info(batch: int) -> dict:
+    c, ie, ii = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+    n, nt, b = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    _check(load().dp_batch_get_info(batch, C.byref(c), C.byref(n), C.byref(nt), C.byref(ie), C.byref(ii),
+                                    C.byref(b)))
+    return {"count": c.value, "nodes_total": n.value, "nodes_target": nt.value, "item_eval": ie.value,
+            "item_improve": ii.value, "device_bytes": b.value}
+
+
+def dp_batch_set_items(batch: int, item_eval: int, item_improve: int) -> None:
+    _check(load().dp_batch_set_items(batch, item_eval, item_improve))
+
+
+def dp_batch_autotune(batch: int):
+    ie, ii = C.c_int32(0), C.c_int32(0)
+    _check(load().dp_batch_autotune(batch, C.byref(ie), C.byref(ii)))
+    return ie.value, ii.value
+
+
+def dp_batch_policy_iterate(batch: int, count: int, opts: dp_solve_opts):
+    s = dp_solve_stats()
+    per = (dp_batch_stats * count)()
+    rc = _check(load().dp_batch_policy_iterate(batch, C.byref(opts), C.byref(s), per),
+                allow=(DP_OK, DP_ENOCONV))
+    return rc, s, [per[i].asdict() for i in range(count)]
+
+
+def dp_batch_sweep(batch: int, count: int, mode: int):
+    """One sweep of every transfer; returns (per-transfer residuals, ms)."""
+    r = np.empty(count, np.float64)
+    ms = C.c_double(0)
+    _check(load().dp_batch_sweep(batch, mode, _host_ptr(r, np.float64), C.byref(ms)))
+    return r, ms.value
+
+
+def dp_batch_set_value(batch: int, index: int, V) -> None:
+    V = np.ascontiguousarray(V, np.float64)
+    _check(load().dp_batch_set_value(batch, index, _host_ptr(V, np.float64), len(V)))
+
+
+def dp_batch_get_value(batch: int, index: int, count: int) -> np.ndarray:
+    out = np.empty(count, np.float64)
+    _check(load().dp_batch_get_value(batch, index, _host_ptr(out, np.float64), count))
+    return out
+
+
+def dp_batch_set_policy(batch: int, index: int, codes) -> None:
+    codes = np.ascontiguousarray(codes, np.uint16)
+    _check(load().dp_batch_set_policy(batch, index, _host_ptr(codes, np.uint16), len(codes)))
+
+
+def dp_batch_get_policy(batch: int, index: int, count: int) -> np.ndarray:
+    out = np.empty(count, np.uint16)
+    _check(load().dp_batch_get_policy(batch, index, _host_ptr(out, np.uint16), count))
+    return out
+
+
+class Batch:
+    """Owning wrapper of a dp_batch handle over a list of workloads.Problem."""
+
+    def __init__(self, problems, stream: Optional[int] = 0):
+        self.problems = list(problems)
+        self.count = len(self.problems)
+        self.nodes = [int(np.prod(p.n)) for p in self.problems]
+        self.h = dp_batch_create([desc_from_problem(p, 0) for p in self.problems], stream)
+
+    def close(self):
+        if self.h:
+            dp_batch_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return dp_batch_get_info(self.h)
+
+    def autotune(self):
+        return dp_batch_autotune(self.h)
+
+    def policy_iterate(self, **kw):
+        return dp_batch_policy_iterate(self.h, self.count, make_opts(**kw))
+
+    def sweep(self, mode):
+        return dp_batch_sweep(self.h, self.count, mode)
+
+    def set_value(self, i, V):
+        dp_batch_set_value(self.h, i, V)
+
+    def get_value(self, i):
+        return dp_batch_get_value(self.h, i, self.nodes[i])
+
+    def set_policy(self, i, codes):
+        dp_batch_set_policy(self.h, i, codes)
+
+    def get_policy(self, i):
+        return dp_batch_get_policy(self.h, i, self.nodes[i])
 
 
 # ---- learned warm start --------------------------------------------------------

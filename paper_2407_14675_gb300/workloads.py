@@ -178,13 +178,13 @@ def transfer_start(r0: float = 1.0, m0: float = 1.0, mu: float = 1.0) -> np.ndar
     return np.array([r0, 0.0, math.sqrt(mu / r0), m0])
 
 
-def batch_transfers(count: int = 256, seed: int = 14675) -> List[Problem]:
-    """Heterogeneous batch: per-dimension sizes from {17,21,25,31,41}, thrust
+def batch_transfers(count: int = 256, seed: int = 14675, sizes=(17, 21, 25, 31, 41)) -> List[Problem]:
+    """Heterogeneous batch: per-dimension sizes from `sizes`, thrust
     log-uniform in [1e-4, 2e-3], target radius U[1.02, 1.10], initial radius
     U[0.98, 1.02]; box r in [r0 - 0.05, r_T + 0.10], v_r, v_t, m as config 0;
     32 angles with golden refinement, FP32, dt 0.05, beta 0.999."""
     rng = np.random.default_rng(seed)
-    sizes = np.array([17, 21, 25, 31, 41])
+    sizes = np.array(sizes)
     out = []
     for _ in range(count):
         n = tuple(int(s) for s in rng.choice(sizes, size=4))
@@ -196,3 +196,14 @@ def batch_transfers(count: int = 256, seed: int = 14675) -> List[Problem]:
                            accel=a, dt=0.05, n_angles=32, refine=1, precision=FP32,
                            target_c=c, target_w=w, tol=1e-6, n_eval=20))
     return out
+
+
+def mlp_init_params(seed: int = 14675, sizes=(4, 256, 256, 256, 3)):
+    """Initial weights of the warm-start network: per layer [W, b] with W of
+    shape (fan_out, fan_in) and every entry uniform in +-1/sqrt(fan_in)."""
+    rng = np.random.default_rng(seed)
+    params = []
+    for fi, fo in zip(sizes[:-1], sizes[1:]):
+        bound = 1.0 / math.sqrt(fi)
+        params.append([rng.uniform(-bound, bound, size=(fo, fi)), rng.uniform(-bound, bound, size=fo)])
+    return params

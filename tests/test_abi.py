@@ -29,7 +29,7 @@ def test_header_declares_the_boundary():
     names = _declared()
     for n in ["dp_grid_create", "dp_grid_destroy", "dp_value_iterate", "dp_policy_iterate",
               "dp_feedback_control", "dp_simulate_closed_loop", "dp_get_value", "dp_get_policy",
-              "dp_last_error"]:
+              "dp_last_error", "dp_batch_create", "dp_batch_policy_iterate", "dp_batch_autotune"]:
         assert n in names
 
 
@@ -49,7 +49,7 @@ def test_struct_layouts_match_header():
     from paper_2407_14675_gb300 import dp
     src = open(os.path.join(ROOT, "include", "dp.h")).read()
     for struct in (dp.dp_grid_desc, dp.dp_solve_opts, dp.dp_solve_stats, dp.dp_grid_info, dp.dp_mlp_train_opts,
-                   dp.dp_mlp_train_stats):
+                   dp.dp_mlp_train_stats, dp.dp_batch_stats):
         name = struct.__name__
         body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), src, flags=re.S).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)

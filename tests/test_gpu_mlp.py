@@ -21,7 +21,7 @@ def _states(p, n, seed):
 
 def test_forward_matches_fp64_reference(dp):
     p = W.config1()
-    params = mlp.init_params(seed=3)
+    params = W.mlp_init_params(seed=3)
     X = _states(p, 1000, 4)                  # not a multiple of the 128-row tile
     flat = dp.flatten_params(params)
     with dp.Mlp(p.lo, p.hi, batch_capacity=4096) as net:
@@ -35,7 +35,7 @@ def test_forward_matches_fp64_reference(dp):
 
 def test_gradients_match_fp64_reference(dp):
     p = W.config1()
-    params = mlp.init_params(seed=5)
+    params = W.mlp_init_params(seed=5)
     X = _states(p, 1024, 6)
     rng = np.random.default_rng(7)
     T = rng.uniform(-1, 1, size=(1024, 3))
@@ -64,7 +64,7 @@ def test_training_fits_a_solved_grid_and_warm_starts_policy_iteration(dp):
         V_cold = cold.get_value()
         M = cold.info["penalty_M"]
         with dp.Mlp(p.lo, p.hi, batch_capacity=4096) as net:
-            dp.dp_mlp_set_params(net.h, dp.flatten_params(mlp.init_params(seed=11)))
+            dp.dp_mlp_set_params(net.h, dp.flatten_params(W.mlp_init_params(seed=11)))
             st = dp.dp_mlp_train_grid(net.h, cold.h, epochs=8, batch=4096, lr=1e-3)
             assert st.last_epoch_loss < st.first_epoch_loss / 3, st.asdict()
             with dp.Grid(p) as warm:

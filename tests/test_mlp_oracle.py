@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import mlp
+from paper_2407_14675_gb300 import workloads as W
 
 
 def test_gelu_values_and_derivative():
@@ -23,7 +24,7 @@ def test_gelu_values_and_derivative():
 @pytest.mark.parametrize("sizes", [(4, 5, 6, 7, 3), (4, 256, 256, 256, 3)])
 def test_backward_matches_central_differences(sizes):
     rng = np.random.default_rng(3)
-    params = mlp.init_params(seed=5, sizes=sizes)
+    params = W.mlp_init_params(seed=5, sizes=sizes)
     X = rng.uniform(-1, 1, size=(6, 4))
     T = rng.uniform(-1, 1, size=(6, 3))
     Y, cache = mlp.forward(params, X)
@@ -46,7 +47,7 @@ def test_backward_matches_central_differences(sizes):
 
 
 def test_output_layer_is_linear_and_shapes():
-    params = mlp.init_params(seed=1)
+    params = W.mlp_init_params(seed=1)
     X = np.zeros((3, 4))
     Y, cache = mlp.forward(params, X)
     assert Y.shape == (3, 3)
