@@ -281,7 +281,7 @@ def warm_start_leg(args, dp, W, torch, g1, p1):
     states on the warm-started solution."""
     p2 = W.config2()
     out = {"grid": "121^4 box, energy band [%.4f, %.4f]" % (p2.energy_lo, p2.energy_hi)}
-    with dp.Mlp(p1.lo, p1.hi, batch_capacity=4096) as net:
+    with dp.Mlp(p1.lo, p1.hi, batch_capacity=65536) as net:
         dp.dp_mlp_set_params(net.h, dp.flatten_params(W.mlp_init_params()))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -293,15 +293,23 @@ def warm_start_leg(args, dp, W, torch, g1, p1):
         out["train"] = tr
         with dp.Grid(p2, stream=int(torch.cuda.current_stream().cuda_stream)) as g2:
             out["nodes_active"] = g2.info["n_active"]
+            V_cold = None
             for start in ("cold", "warm"):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 ws_ms = 0.0
                 if start == "warm":
                     ws_ms = dp.dp_warm_start(net.h, g2.h)
+                    t_ws = time.perf_counter() - t0
+                    err = np.abs(g2.get_value() - V_cold) / g2.info["penalty_M"]
+                    out["warm_start_error"] = {"max_over_M": float(err.max()), "rms_over_M":
+                                               float(np.sqrt(np.mean(err ** 2)))}
+                    t0 = time.perf_counter() - t_ws   # the host copy for the error is not timed
                 rc, s2 = g2.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=p2.n_eval, polish=1,
                                            warm=int(start == "warm"))
                 torch.cuda.synchronize()
+                if start == "cold":
+                    V_cold = g2.get_value()
                 out[start] = {"seconds": time.perf_counter() - t0, "converged": bool(s2.converged),
                               "residual": s2.residual, "warm_start_ms": ws_ms,
                               "sweeps_improve": s2.sweeps_improve, "sweeps_eval": s2.sweeps_eval,

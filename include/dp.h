@@ -109,7 +109,8 @@ typedef struct dp_solve_opts {
     double  switch_tol;    /* FP32 -> FP64 switch when the improvement residual is
                               below this (<= 0: 16 FP32 epsilons of M, automatic);
                               the switch also happens after 3 improvements without
-                              a 0.1 % gain over the best FP32 residual              */
+                              a 0.1 % gain over the best FP32 residual when it is
+                              below 64 times that tolerance, or after 30 anywhere   */
     int32_t time_kernels;  /* 1: time every sweep with CUDA events (small overhead) */
     double* history;       /* nullable host array: the residual of every stopping
                               test (VI: every sweep; PI: every improvement sweep),
@@ -257,8 +258,9 @@ int dp_mlp_gradients(dp_mlp* mlp, const double* states, const float* targets, in
  * the grid's resident value and policy.  stats nullable. */
 int dp_mlp_train_grid(dp_mlp* mlp, dp_grid* grid, const dp_mlp_train_opts* opts, dp_mlp_train_stats* stats);
 /* Writes V = M clamp(V/M-hat, 0, 1) (0 on target nodes) and the policy code of
- * atan2(sin-hat, cos-hat) at every stored node of a grid.  *ms (nullable):
- * GPU time. */
+ * atan2(sin-hat, cos-hat) at every stored node of a grid, in the grid's
+ * storage precision (an FP32 grid that held FP64 values after a polish goes
+ * back to FP32 values).  *ms (nullable): GPU time. */
 int dp_warm_start(dp_mlp* mlp, dp_grid* grid, double* ms);
 
 /* ---- batched transfers ----

@@ -41,6 +41,8 @@ int fail(int code, const char* fmt, ...)
 
 constexpr int kRing = 8192;        // residual slots (power of two)
 constexpr int kMaxChunk = 2048;    // sweeps enqueued between host checks (< kRing / 2)
+constexpr double kStallZone = 64.0; // "near the FP32 floor": below this multiple of the switch tolerance
+constexpr int kStallFar = 30;       // improvements without gain that switch anywhere
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 }  // namespace
@@ -1009,10 +1011,13 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
             if ((rc = reset_ctl(g))) return rc;
             continue;
         }
-        // FP32 -> FP64 switch once the FP32 residual is small or stalls
+        // FP32 -> FP64 switch once the FP32 residual is small, or stalls: 3
+        // improvements without gain near the FP32 floor, 30 far above it (a
+        // short stall there is the transient of a warm start, which FP64
+        // values would not shorten)
         if (g->fp32 && !mix && o->polish) {
             if (res < best * 0.999) { best = res; stall = 0; } else ++stall;
-            if (res < switch_tol || stall >= 3) {
+            if (res < switch_tol || (stall >= 3 && res < kStallZone * switch_tol) || stall >= kStallFar) {
                 advance(g, t);
                 t = 0;
                 if ((rc = ensure_fp64(g))) return rc;

@@ -277,14 +277,15 @@ __device__ void ctl_update(BState& s, const BParams& p, double M, int stage)
             s.evals = p.n_eval > 0;
             s.full_next = !p.walk;
             if (s.phase == kPh32 && p.polish) {
+                // the switch rule of dp_policy_iterate
+                const double sw = p.switch_tol > 0 ? p.switch_tol : 16.0 * 1.1920928955078125e-07 * M;
                 if (res < s.best * 0.999) {
                     s.best = res;
                     s.stall = 0;
                 } else {
                     ++s.stall;
                 }
-                const double sw = p.switch_tol > 0 ? p.switch_tol : 16.0 * 1.1920928955078125e-07 * M;
-                if (res < sw || s.stall >= 3) s.switch_pending = 1;
+                if (res < sw || (s.stall >= 3 && res < 64.0 * sw) || s.stall >= 30) s.switch_pending = 1;
             }
             if (s.imp32 + s.imp64 >= p.max_outer) s.finish = 1;
         }

@@ -704,7 +704,9 @@ int dp_warm_start(dp_mlp* m, dp_grid* grid, double* ms_out)
             nullptr);
         MCK(cudaGetLastError());
         if ((rc = forward(m, cnt, false, nullptr, 0.0f))) return rc;
-        if (gv.fp32 && !gv.V64)
+        // the value goes to the storage-precision buffer (an FP32 grid holding
+        // FP64 values after a polish returns to its FP32 values)
+        if (gv.fp32)
             warm_write_kernel<float><<<(cnt + 255) / 256, 256, 0, m->st>>>(g, m->y, s0, cnt, gv.M, (float*)gv.V,
                                                                          gv.code);
         else

@@ -70,10 +70,19 @@ def test_training_fits_a_solved_grid_and_warm_starts_policy_iteration(dp):
             with dp.Grid(p) as warm:
                 dp.dp_warm_start(net.h, warm.h)
                 V0 = warm.get_value()
+                C0 = warm.get_policy()
                 fit = np.abs(V0 - V_cold).max() / M
                 rc, st_warm = warm.policy_iterate(tol=1e-6, max_sweeps=4000, n_eval=20, polish=1, warm=1)
                 assert st_warm.converged
                 V_warm = warm.get_value()
+            # the cold grid holds FP64 values after its polished solve: a warm
+            # start into it writes the same FP32 values as into a fresh grid
+            assert st_cold.switch_outer >= 0
+            dp.dp_warm_start(net.h, cold.h)
+            assert cold.info["n_active"] == len(V0)
+            np.testing.assert_array_equal(cold.get_value(), V0)
+            np.testing.assert_array_equal(cold.get_policy(), C0)
+    assert np.isfinite(V0).all() and V0.min() >= 0 and V0.max() <= float(np.float32(M))   # FP32 storage
     assert np.abs(V_warm - V_cold).max() <= 1e-4 * M
     print("fit %.3g, improvements cold %d warm %d" % (
         fit, st_cold.sweeps_improve + st_cold.sweeps_improve_fp64,
