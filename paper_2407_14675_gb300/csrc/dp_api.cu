@@ -43,6 +43,7 @@ constexpr int kRing = 8192;        // residual slots (power of two)
 constexpr int kMaxChunk = 2048;    // sweeps enqueued between host checks (< kRing / 2)
 constexpr double kStallZone = 64.0; // "near the FP32 floor": below this multiple of the switch tolerance
 constexpr int kStallFar = 30;       // improvements without gain that switch anywhere
+constexpr int kMaxConfirms = 3;     // full-table confirmations of an FP32 -> FP64 switch
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 }  // namespace
@@ -933,8 +934,8 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
     double switch_tol = o->switch_tol > 0 ? o->switch_tol : 16.0 * 1.1920928955078125e-07 * g->M;
     long long outer = 0, t = 0;    // outer iterations and sweeps of the current phase
     double res = INFINITY, best = INFINITY;
-    int stall = 0;
-    bool conv = false, first_full = !o->warm;
+    int stall = 0, confirms = 0;
+    bool conv = false, first_full = !o->warm, switch_confirming = false;
     long long hist_n = 0;
     S.switch_outer = -1;
     auto record = [&](long long t0, long long n_imp) {
@@ -1014,10 +1015,23 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
         // FP32 -> FP64 switch once the FP32 residual is small, or stalls: 3
         // improvements without gain near the FP32 floor, 30 far above it (a
         // short stall there is the transient of a warm start, which FP64
-        // values would not shorten)
+        // values would not shorten).  A switch decided after a walk is first
+        // confirmed by a full-table FP32 improvement: walks that settled in
+        // local minima of the table are caught while sweeps are still cheap.
         if (g->fp32 && !mix && o->polish) {
             if (res < best * 0.999) { best = res; stall = 0; } else ++stall;
-            if (res < switch_tol || (stall >= 3 && res < kStallZone * switch_tol) || stall >= kStallFar) {
+            bool want = res < switch_tol || (stall >= 3 && res < kStallZone * switch_tol) || stall >= kStallFar;
+            if (switch_confirming) {
+                // the confirming full table moved V: stay in FP32, stall count anew
+                switch_confirming = false;
+                if (!want) { best = res; stall = 0; }
+            } else if (want && last_was_walk && confirms < kMaxConfirms) {
+                ++confirms;
+                switch_confirming = true;
+                first_full = true;
+                want = false;
+            }
+            if (want) {
                 advance(g, t);
                 t = 0;
                 if ((rc = ensure_fp64(g))) return rc;

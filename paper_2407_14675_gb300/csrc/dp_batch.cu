@@ -45,7 +45,8 @@ using namespace dpk;
 
 namespace {
 
-enum { kLWiden = 0, kLImp32 = 1, kLImp64 = 2, kLEval = 3, kLists = 4 };
+// work lists: widen, improvements by (values, full table or walk), evaluations
+enum { kLWiden = 0, kLImp32Full = 1, kLImp32Walk = 2, kLImp64Full = 3, kLImp64Walk = 4, kLEval = 5, kLists = 6 };
 enum { kPh32 = 0, kPh64 = 1, kPhDone = 2 };
 enum {
     kStBegin = 0,      // start of a solve
@@ -75,7 +76,10 @@ struct BState {
     int finish;                    // the transfer ends with this step
     int switch_pending;            // switch to FP64 values after this step
     int widen;                     // the next step starts by widening V into FP64
-    int stall, nonfinite, converged, pad;
+    int stall, nonfinite, converged;
+    int confirms;                  // full-table confirmations of the FP64 switch so far
+    int confirming;                // this step's improvement confirms a switch
+    int pad;
 };
 
 struct BParams {
@@ -91,7 +95,7 @@ struct BArgs {
     const long long* off;          // first node of each transfer in the shared buffers
     BState* st;
     int* prefix;                   // kLists lists of count + 1 item offsets
-    float* V32[2];
+    float* V32[2];                 // indexed by a runtime bit only through pick()
     double* V64[2];
     uint16_t* code;
     unsigned long long* feet_lo;
@@ -100,6 +104,14 @@ struct BArgs {
     int count;
     int item_eval, item_imp;       // nodes per work item
 };
+
+// One of two buffers by a runtime bit, without indexing the parameter array
+// (a dynamic index would copy the arguments to local memory).
+template <typename T>
+__device__ __forceinline__ T* pick(T* const (&p)[2], int bit)
+{
+    return (bit & 1) ? p[1] : p[0];
+}
 
 __device__ __forceinline__ void load_geo(Geo<float>& dst, const Geo<float>* src)
 {
@@ -131,22 +143,27 @@ __global__ void __launch_bounds__(kBlock) batch_widen_kernel(const BArgs a)
         const int first = (it - pre[t]) * a.item_eval;
         const int end = min(first + a.item_eval, a.geo[t].n_nodes);
         const BState& S = a.st[t];
-        const float* src = a.V32[S.cur] + a.off[t];
-        double* dst = a.V64[S.cur64] + a.off[t];
+        const float* src = pick(a.V32, S.cur) + a.off[t];
+        double* dst = pick(a.V64, S.cur64) + a.off[t];
         for (int j = first + threadIdx.x; j < end; j += kBlock) dst[j] = (double)src[j];
     }
 }
 
 // Improvement sweeps (§3, Eq. (14)): S = float for FP32 values, double for
-// the FP64-value polish (which also writes the first increment).
-template <typename S, int DYN>
-__global__ void __launch_bounds__(kBlock) batch_improve_kernel(const BArgs a)
+// the FP64-value polish (which also writes the first increment); full table
+// or walk as MODE (one kernel each, so each keeps its own register budget).
+// The geometry sits in shared memory here, not in the parameter bank, so the
+// compiler holds more of it in registers: the bound keeps 3 blocks per SM for
+// the FP32 kernels (80 registers, no spills) and 2 for the FP64-value ones.
+template <typename S, int DYN, int MODE>
+__global__ void __launch_bounds__(kBlock, std::is_same<S, double>::value ? 2 : 3) batch_improve_kernel(const BArgs a)
 {
     constexpr bool k64 = std::is_same<S, double>::value;
     __shared__ Geo<float> s_g;
     __shared__ int s_code[kMaxAngles + 1];
     __shared__ float2 s_sc[kMaxAngles];
-    const int list = k64 ? kLImp64 : kLImp32;
+    const int list = k64 ? (MODE == kImproveFull ? kLImp64Full : kLImp64Walk)
+                         : (MODE == kImproveFull ? kLImp32Full : kLImp32Walk);
     const int* pre = a.prefix + list * (a.count + 1);
     const int total = pre[a.count];
     int cur_t = -1;
@@ -171,21 +188,15 @@ __global__ void __launch_bounds__(kBlock) batch_improve_kernel(const BArgs a)
         S* Vout;
         float* inc = nullptr;
         if constexpr (k64) {
-            Vin = a.V64[st.cur64] + o;
-            Vout = a.V64[st.cur64 ^ 1] + o;
+            Vin = pick(a.V64, st.cur64) + o;
+            Vout = pick(a.V64, st.cur64 ^ 1) + o;
             inc = a.V32[0] + o;
         } else {
-            Vin = a.V32[st.cur] + o;
-            Vout = a.V32[st.cur ^ 1] + o;
+            Vin = pick(a.V32, st.cur) + o;
+            Vout = pick(a.V32, st.cur ^ 1) + o;
         }
-        if (st.full_next)
-            sweep_nodes<float, S, kImproveFull, false, DYN>(s_g, T, Vin, Vout, a.code + o, a.feet_lo + o,
-                                                            a.feet_hi + o, inc, nullptr, nullptr, 0,
-                                                            first + threadIdx.x, end, kBlock, resid, bad);
-        else
-            sweep_nodes<float, S, kImproveWalk, false, DYN>(s_g, T, Vin, Vout, a.code + o, a.feet_lo + o,
-                                                            a.feet_hi + o, inc, nullptr, nullptr, 0,
-                                                            first + threadIdx.x, end, kBlock, resid, bad);
+        sweep_nodes<float, S, MODE, false, DYN>(s_g, T, Vin, Vout, a.code + o, a.feet_lo + o, a.feet_hi + o, inc,
+                                                nullptr, nullptr, 0, first + threadIdx.x, end, kBlock, resid, bad);
         block_fold(resid, bad, &st.res_bits, &st.nonfinite);
     }
 }
@@ -194,7 +205,7 @@ __global__ void __launch_bounds__(kBlock) batch_improve_kernel(const BArgs a)
 // FP32 transfers blend at their frozen feet (FEET) or recompute them; FP64
 // transfers sweep increments.  e = -1 is a stand-alone sweep of V[cur].
 template <int DYN, bool FEET>
-__global__ void __launch_bounds__(kBlock) batch_eval_kernel(const BArgs a, int e, int n_eval)
+__global__ void __launch_bounds__(kBlock, 5) batch_eval_kernel(const BArgs a, int e, int n_eval)
 {
     __shared__ Geo<float> s_g;
     const int* pre = a.prefix + kLEval * (a.count + 1);
@@ -216,8 +227,8 @@ __global__ void __launch_bounds__(kBlock) batch_eval_kernel(const BArgs a, int e
         float resid = 0.0f;
         bool bad = false;
         if (st.phase == kPh32 || !FEET) {
-            const float* Vin = a.V32[(st.cur + 1 + e) & 1] + o;
-            float* Vout = a.V32[(st.cur + 2 + e) & 1] + o;
+            const float* Vin = pick(a.V32, st.cur + 1 + e) + o;
+            float* Vout = pick(a.V32, st.cur + 2 + e) + o;
             if constexpr (FEET)
                 sweep_nodes<float, float, kEvalFeet, false, DYN>(s_g, T, Vin, Vout, a.code + o, a.feet_lo + o,
                                                                  a.feet_hi + o, nullptr, nullptr, nullptr, 0,
@@ -228,9 +239,9 @@ __global__ void __launch_bounds__(kBlock) batch_eval_kernel(const BArgs a, int e
                                                              end, kBlock, resid, bad);
         } else if constexpr (FEET) {
             const int flags = (e == 0 ? 1 : 0) | (e == n_eval - 1 ? 2 : 0);
-            sweep_nodes<float, float, kIncr, false, DYN>(s_g, T, a.V32[e & 1] + o, a.V32[(e + 1) & 1] + o,
+            sweep_nodes<float, float, kIncr, false, DYN>(s_g, T, pick(a.V32, e) + o, pick(a.V32, e + 1) + o,
                                                          a.code + o, a.feet_lo + o, a.feet_hi + o, nullptr,
-                                                         a.acc + o, a.V64[st.cur64 ^ 1] + o, flags,
+                                                         a.acc + o, pick(a.V64, st.cur64 ^ 1) + o, flags,
                                                          first + threadIdx.x, end, kBlock, resid, bad);
         }
         block_fold(resid, bad, &st.res_bits, &st.nonfinite);
@@ -249,6 +260,7 @@ __device__ void ctl_update(BState& s, const BParams& p, double M, int stage)
         s.full_next = !p.warm || !p.walk;
         s.evals = s.finish = s.switch_pending = s.widen = 0;
         s.stall = s.nonfinite = s.converged = 0;
+        s.confirms = s.confirming = 0;
         s.res = s.best = CUDART_INF;
         s.res_bits = 0;
         s.imp32 = s.eval32 = s.imp64 = s.eval64 = 0;
@@ -285,7 +297,20 @@ __device__ void ctl_update(BState& s, const BParams& p, double M, int stage)
                 } else {
                     ++s.stall;
                 }
-                if (res < sw || (s.stall >= 3 && res < 64.0 * sw) || s.stall >= 30) s.switch_pending = 1;
+                bool want = res < sw || (s.stall >= 3 && res < 64.0 * sw) || s.stall >= 30;
+                if (s.confirming) {
+                    s.confirming = 0;
+                    if (!want) {
+                        s.best = res;
+                        s.stall = 0;
+                    }
+                } else if (want && p.walk && !full && s.confirms < 3) {
+                    ++s.confirms;            // confirm by a full table first
+                    s.confirming = 1;
+                    s.full_next = 1;
+                    want = false;
+                }
+                if (want) s.switch_pending = 1;
             }
             if (s.imp32 + s.imp64 >= p.max_outer) s.finish = 1;
         }
@@ -357,7 +382,7 @@ __global__ void __launch_bounds__(kCtlThreads) batch_ctl_kernel(const BArgs a, B
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int base = 0; base < a.count; base += kCtlThreads) {
         const int t = base + threadIdx.x;
-        int c[kLists + 1] = {0, 0, 0, 0, 0};
+        int c[kLists + 1] = {0, 0, 0, 0, 0, 0, 0};
         if (t < a.count) {
             BState s = a.st[t];
             ctl_update(s, P, a.geo[t].M64, stage);
@@ -365,8 +390,10 @@ __global__ void __launch_bounds__(kCtlThreads) batch_ctl_kernel(const BArgs a, B
             const int n = a.geo[t].n_nodes;
             const int ne = (n + a.item_eval - 1) / a.item_eval, ni = (n + a.item_imp - 1) / a.item_imp;
             c[kLWiden] = (s.phase == kPh64 && s.widen) ? ne : 0;
-            c[kLImp32] = s.phase == kPh32 ? ni : 0;
-            c[kLImp64] = s.phase == kPh64 ? ni : 0;
+            c[kLImp32Full] = (s.phase == kPh32 && s.full_next) ? ni : 0;
+            c[kLImp32Walk] = (s.phase == kPh32 && !s.full_next) ? ni : 0;
+            c[kLImp64Full] = (s.phase == kPh64 && s.full_next) ? ni : 0;
+            c[kLImp64Walk] = (s.phase == kPh64 && !s.full_next) ? ni : 0;
             c[kLEval] = (s.phase != kPhDone && s.evals) ? ne : 0;
             c[kLists] = s.phase != kPhDone;
         }
@@ -467,7 +494,8 @@ struct dp_batch {
     BState* h_st = nullptr;        // pinned mirror of d_st
     BParams* h_par = nullptr;      // pinned
     int item_eval = 8192, item_imp = 8192;
-    int blocks_widen = 0, blocks_imp32 = 0, blocks_imp64 = 0, blocks_eval = 0, blocks_eval_nf = 0;
+    int blocks_widen = 0, blocks_imp32f = 0, blocks_imp32w = 0, blocks_imp64f = 0, blocks_imp64w = 0;
+    int blocks_eval = 0, blocks_eval_nf = 0;
     cudaGraphExec_t exec = nullptr;
     int graph_n_eval = -1, graph_item_eval = 0, graph_item_imp = 0;
     long long graph_launches = 0;
@@ -537,17 +565,20 @@ cudaError_t launch_ctl(const dp_batch* b, int stage)
 }
 
 template <int DYN>
-cudaError_t launch_improve(const dp_batch* b, bool fp64)
+cudaError_t launch_improve(const dp_batch* b, bool fp64, bool full)
 {
     const BArgs a = args_of(b);
-    if (fp64) batch_improve_kernel<double, DYN><<<b->blocks_imp64, kBlock, 0, b->st>>>(a);
-    else batch_improve_kernel<float, DYN><<<b->blocks_imp32, kBlock, 0, b->st>>>(a);
+    if (fp64 && full) batch_improve_kernel<double, DYN, kImproveFull><<<b->blocks_imp64f, kBlock, 0, b->st>>>(a);
+    else if (fp64) batch_improve_kernel<double, DYN, kImproveWalk><<<b->blocks_imp64w, kBlock, 0, b->st>>>(a);
+    else if (full) batch_improve_kernel<float, DYN, kImproveFull><<<b->blocks_imp32f, kBlock, 0, b->st>>>(a);
+    else batch_improve_kernel<float, DYN, kImproveWalk><<<b->blocks_imp32w, kBlock, 0, b->st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_improve(const dp_batch* b, bool fp64)
+cudaError_t launch_improve(const dp_batch* b, bool fp64, bool full)
 {
-    return b->dyn == DP_DYN_ORBIT ? launch_improve<kDynOrbit>(b, fp64) : launch_improve<kDynUnitSpeed>(b, fp64);
+    return b->dyn == DP_DYN_ORBIT ? launch_improve<kDynOrbit>(b, fp64, full)
+                                  : launch_improve<kDynUnitSpeed>(b, fp64, full);
 }
 
 template <int DYN>
@@ -577,13 +608,13 @@ cudaError_t enqueue_step(const dp_batch* b, int n_eval, long long* launches)
 {
     cudaError_t e;
     if ((e = launch_widen(b)) != cudaSuccess) return e;
-    if ((e = launch_improve(b, false)) != cudaSuccess) return e;
-    if ((e = launch_improve(b, true)) != cudaSuccess) return e;
+    for (int k = 0; k < 4; ++k)
+        if ((e = launch_improve(b, k >= 2, (k & 1) == 0)) != cudaSuccess) return e;
     if ((e = launch_ctl(b, kStAfterImp)) != cudaSuccess) return e;
     for (int k = 0; k < n_eval; ++k)
         if ((e = launch_eval(b, k, n_eval, true)) != cudaSuccess) return e;
     if ((e = launch_ctl(b, kStEnd)) != cudaSuccess) return e;
-    *launches += 5 + n_eval;
+    *launches += 7 + n_eval;
     return cudaSuccess;
 }
 
@@ -681,7 +712,8 @@ int manual_sweep(dp_batch* b, int32_t mode, double* ms)
         BCK(cudaEventCreate(&e1));
         BCK(cudaEventRecord(e0, b->st));
     }
-    cudaError_t e = stage == kStManEval ? launch_eval(b, -1, 0, b->feet_valid) : launch_improve(b, false);
+    cudaError_t e = stage == kStManEval ? launch_eval(b, -1, 0, b->feet_valid)
+                                        : launch_improve(b, false, stage == kStManImpFull);
     if (ms) cudaEventRecord(e1, b->st);
     if (e == cudaSuccess) e = launch_ctl(b, kStManEnd);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
@@ -829,13 +861,21 @@ int dp_batch_create(const dp_grid_desc* descs, int32_t count, void* stream, dp_b
 
     bool bad = false;
     if (b->dyn == DP_DYN_ORBIT) {
-        bad = occupancy_blocks(batch_improve_kernel<float, kDynOrbit>, b->sm_count, &b->blocks_imp32) ||
-              occupancy_blocks(batch_improve_kernel<double, kDynOrbit>, b->sm_count, &b->blocks_imp64) ||
+        bad = occupancy_blocks(batch_improve_kernel<float, kDynOrbit, kImproveFull>, b->sm_count, &b->blocks_imp32f) ||
+              occupancy_blocks(batch_improve_kernel<float, kDynOrbit, kImproveWalk>, b->sm_count, &b->blocks_imp32w) ||
+              occupancy_blocks(batch_improve_kernel<double, kDynOrbit, kImproveFull>, b->sm_count, &b->blocks_imp64f) ||
+              occupancy_blocks(batch_improve_kernel<double, kDynOrbit, kImproveWalk>, b->sm_count, &b->blocks_imp64w) ||
               occupancy_blocks(batch_eval_kernel<kDynOrbit, true>, b->sm_count, &b->blocks_eval) ||
               occupancy_blocks(batch_eval_kernel<kDynOrbit, false>, b->sm_count, &b->blocks_eval_nf);
     } else {
-        bad = occupancy_blocks(batch_improve_kernel<float, kDynUnitSpeed>, b->sm_count, &b->blocks_imp32) ||
-              occupancy_blocks(batch_improve_kernel<double, kDynUnitSpeed>, b->sm_count, &b->blocks_imp64) ||
+        bad = occupancy_blocks(batch_improve_kernel<float, kDynUnitSpeed, kImproveFull>, b->sm_count,
+                               &b->blocks_imp32f) ||
+              occupancy_blocks(batch_improve_kernel<float, kDynUnitSpeed, kImproveWalk>, b->sm_count,
+                               &b->blocks_imp32w) ||
+              occupancy_blocks(batch_improve_kernel<double, kDynUnitSpeed, kImproveFull>, b->sm_count,
+                               &b->blocks_imp64f) ||
+              occupancy_blocks(batch_improve_kernel<double, kDynUnitSpeed, kImproveWalk>, b->sm_count,
+                               &b->blocks_imp64w) ||
               occupancy_blocks(batch_eval_kernel<kDynUnitSpeed, true>, b->sm_count, &b->blocks_eval) ||
               occupancy_blocks(batch_eval_kernel<kDynUnitSpeed, false>, b->sm_count, &b->blocks_eval_nf);
     }

@@ -186,21 +186,26 @@ __device__ __forceinline__ void heun_cells(const Geo<G>& g, const StepP<G>& sp, 
 // A foot exactly on an upper face uses the last cell with t = 1.  Returns
 // true when the foot is outside the box (strictly) or not finite.
 template <typename G>
+__device__ __forceinline__ bool foot_dim(int n, int i, G u, int& c, G& t)
+{
+    G fl = floor(u);
+    t = u - fl;
+    c = i + (int)fl;
+    bool out = !(t >= (G)0);
+    if ((unsigned)c > (unsigned)(n - 2)) {   // outside, or on the upper face
+        out = out || c != n - 1 || t > (G)0;
+        c = n - 2;
+        t = (G)1;
+    }
+    return out;
+}
+
+template <typename G>
 __device__ __forceinline__ bool foot_cell(const Geo<G>& g, const int i[4], const G u[4], int c[4], G t[4])
 {
     bool out = false;
 #pragma unroll
-    for (int d = 0; d < 4; ++d) {
-        G fl = floor(u[d]);
-        t[d] = u[d] - fl;
-        c[d] = i[d] + (int)fl;
-        out = out || !(t[d] >= (G)0);
-        if ((unsigned)c[d] > (unsigned)(g.n[d] - 2)) {   // outside, or on the upper face
-            out = out || c[d] != g.n[d] - 1 || t[d] > (G)0;
-            c[d] = g.n[d] - 2;
-            t[d] = (G)1;
-        }
-    }
+    for (int d = 0; d < 4; ++d) out = foot_dim(g.n[d], i[d], u[d], c[d], t[d]) || out;
     return out;
 }
 
@@ -438,7 +443,12 @@ struct NodeEval {
 // costs the Heun step and the blend, with no memory access.  With the default
 // blend type the results are bit-identical to NodeEval; BLEND = float with
 // FP64 values blends the FP64 corner differences V_c - V_j rounded to FP32.
-template <typename G, typename S, bool REDUCED, int DYN, typename BLEND = typename BlendType<G, S>::type>
+//
+// The mass displacement does not depend on the control, so the mass
+// coordinate of the foot is found once per state (reset(), after vj, u0 and
+// the dynamics are set).  OFF = false: the state is a grid node (u0 = 0).
+template <typename G, typename S, bool REDUCED, int DYN, typename BLEND = typename BlendType<G, S>::type,
+          bool OFF = true>
 struct CachedEval {
     typedef BLEND R;
     const Geo<G>* g;
@@ -448,11 +458,20 @@ struct CachedEval {
     G u0[4];
     S vj;
     NodeDyn<G> nd;
-    int cc[4];        // cached cell; cc[0] = -1: none
+    int cc[3];        // cached cell in (r, v_r, v_t); cc[0] = -1: none
     bool cout;        // the cached cell has a corner outside the node set
     Corners<R> K;
+    R pen;            // M - vj
+    int cm;           // mass cell and fraction of every foot of this state
+    G tm;
+    bool outm;
 
-    __device__ __forceinline__ void reset() { cc[0] = -1; }
+    __device__ __forceinline__ void reset()
+    {
+        cc[0] = -1;
+        pen = (R)((S)g->M64 - vj);
+        outm = foot_dim(g->n[3], i[3], OFF ? sp.um + u0[3] : sp.um, cm, tm);
+    }
 
     __device__ __forceinline__ R at_code(int code)
     {
@@ -466,15 +485,22 @@ struct CachedEval {
         G u[4], t[4];
         int cl[4];
         heun_cells<G, DYN>(*g, sp, nd, s, c, u);
+        if (OFF) {
 #pragma unroll
-        for (int d = 0; d < 4; ++d) u[d] += u0[d];
-        if (foot_cell(*g, i, u, cl, t)) return (R)((S)g->M64 - vj);
-        if (cl[0] != cc[0] || cl[1] != cc[1] || cl[2] != cc[2] || cl[3] != cc[3]) {
+            for (int d = 0; d < 3; ++d) u[d] += u0[d];
+        }
+        bool out = outm;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) out = foot_dim(g->n[d], i[d], u[d], cl[d], t[d]) || out;
+        if (out) return pen;
+        cl[3] = cm;
+        t[3] = tm;
+        if (cl[0] != cc[0] || cl[1] != cc[1] || cl[2] != cc[2]) {
             cout = load_corners<R, G, S, REDUCED>(*g, V, cl, vj, K);
 #pragma unroll
-            for (int d = 0; d < 4; ++d) cc[d] = cl[d];
+            for (int d = 0; d < 3; ++d) cc[d] = cl[d];
         }
-        if (cout) return (R)((S)g->M64 - vj);
+        if (cout) return pen;
         const R tr[4] = {(R)t[0], (R)t[1], (R)t[2], (R)t[3]};
         return K.blend(tr);
     }

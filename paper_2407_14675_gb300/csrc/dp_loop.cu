@@ -76,9 +76,9 @@ loop_kernel(const __grid_constant__ Geo<G> g, const __grid_constant__ LoopLaunch
             ev.u0[d] = (G)(sd - fl);
         }
         ev.nd = node_dyn<G, DYN>(g, ev.sp, x);
-        ev.reset();
         // compensation reference: the plain interpolated value at angle 0
         ev.vj = (S)0;
+        ev.reset();
         ev.vj = (S)ev.at_code(0);
         ev.reset();          // cached corners are differences to the old vj
 

@@ -206,7 +206,7 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
         // 1e-9 of a cell's value spread, far below the FP32 geometry's own
         // noise), and the chosen code is then re-evaluated in FP64
         typedef typename std::conditional<kPolish, float, typename BlendType<G, S>::type>::type SearchR;
-        typedef typename std::conditional<kSearch, CachedEval<G, S, REDUCED, DYN, SearchR>,
+        typedef typename std::conditional<kSearch, CachedEval<G, S, REDUCED, DYN, SearchR, false>,
                                           NodeEval<G, S, REDUCED, DYN>>::type Eval;
         for (int j = j0; j < end; j += stride) {
             const S vj = Vin[j];
@@ -303,8 +303,14 @@ __device__ __forceinline__ void block_fold(S resid, bool bad, unsigned long long
     }
 }
 
+// Frozen-feet sweeps are bound by gather latency: more resident warps keep
+// more gathers in flight, so they are compiled for 6 blocks per SM (40
+// registers, no spills; 8 blocks would spill).
+template <int MODE>
+constexpr int min_blocks() { return (MODE == kEvalFeet || MODE == kIncr) ? 6 : 1; }
+
 template <typename G, typename S, int MODE, bool REDUCED, int DYN>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, min_blocks<MODE>())
 sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __restrict__ Vout,
              uint16_t* __restrict__ code, unsigned long long* __restrict__ feet_lo, unsigned* __restrict__ feet_hi,
              float* __restrict__ inc, float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
