@@ -174,6 +174,29 @@ def oracle_step_rate(p, seconds_target=12.0, seed=2407):
     return updates / wall, {"nodes": n_imp, "reps": reps, "seconds": wall, "updates": updates}
 
 
+def _oracle_worker(task):
+    """One process of the all-cores oracle baseline (spawned): the single
+    thread measurement on its own seeded node sample, for a fixed time."""
+    seed, seconds = task
+    from paper_2407_14675_gb300 import workloads as W
+    rate, info = oracle_step_rate(W.config1(), seconds_target=seconds, seed=seed)
+    return info["updates"], info["seconds"]
+
+
+def oracle_parallel_rate(seconds_target=10.0, procs=None):
+    """The oracle on every host core: one spawned process per core, each on
+    its own sample of the same step mix.  Aggregate node-updates / the
+    slowest process's time."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        res = pool.map(_oracle_worker, [(2407 + 97 * k, seconds_target) for k in range(procs)])
+    updates = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    return updates / wall, {"procs": procs, "seconds": wall, "updates": updates}
+
+
 def run_reference(args, world, rank):
     from paper_2407_14675_gb300 import workloads as W
     if rank != 0:
@@ -212,6 +235,36 @@ def _config(p):
 
 
 # ------------------------------------------------------------------ GPU arm --
+
+def extra_legs(args, dp, W, torch, g1, p1):
+    """FP64 value iteration on the 17^4 grid to 1e-8, and the walk against
+    full tabulation in every improvement on the 61^4 cold solve (the paper
+    reports about +20 % total time for exhaustive search)."""
+    out = {}
+    p0 = W.config0()
+    st = int(torch.cuda.current_stream().cuda_stream)
+    with dp.Grid(p0, stream=st) as g0:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, s0 = g0.value_iterate(tol=1e-8, max_sweeps=40000)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        out["vi_fp64_17x4"] = {"seconds": secs, "converged": bool(s0.converged), "sweeps": s0.sweeps_vi,
+                               "residual": s0.residual, "node_updates_per_s": s0.node_updates / secs}
+    res = {}
+    for walk in (1, 0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, s1 = g1.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=p1.n_eval, polish=1, warm=0,
+                                   walk=walk)
+        torch.cuda.synchronize()
+        res["walk" if walk else "full_table"] = {
+            "seconds": time.perf_counter() - t0, "converged": bool(s1.converged),
+            "improvements": s1.sweeps_improve + s1.sweeps_improve_fp64}
+    res["full_over_walk"] = res["full_table"]["seconds"] / max(res["walk"]["seconds"], 1e-9)
+    out["walk_vs_full_61x4"] = res
+    return out
+
 
 def batch_leg(args, dp, W, torch):
     """Batched transfers: the 256-transfer batch solved to 1e-6 in one set of
@@ -417,6 +470,7 @@ def run_ours(args, world, rank, local):
                  "residual_trace": {int(k): float(h[k]) for k in marks if 0 <= k < len(h)},
                  "start": "cold (V = 0, full tabulation first)"}
     warm = warm_start_leg(args, dp, W, torch, g, p) if (args.warm_start and args.solve and rank == 0) else None
+    extra = extra_legs(args, dp, W, torch, g, p) if (args.extra and rank == 0) else None
     g.close()
     batch = batch_leg(args, dp, W, torch) if (args.batch and rank == 0) else None
 
@@ -439,6 +493,8 @@ def run_ours(args, world, rank, local):
     imp_ms = ms_imp / max(n_imp, 1)
 
     cpu_rate, cpu_info = oracle_step_rate(p, seconds_target=args.cpu_seconds) if args.cpu_seconds > 0 else (None, {})
+    par_rate, par_info = (oracle_parallel_rate(args.cpu_seconds / 2) if (args.cpu_seconds > 0 and args.cpu_parallel)
+                          else (None, {}))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -457,9 +513,14 @@ def run_ours(args, world, rank, local):
             "sample": "%d sampled nodes of the 61^4 grid x (1 walk improvement + %d evaluations), %d reps, "
                       "%.1f s FP64 single thread" % (cpu_info["nodes"], p.n_eval, cpu_info["reps"],
                                                       cpu_info["seconds"])},
+        "cpu_baseline_all_cores": None if par_rate is None else {
+            "value": par_rate, "unit": UNIT, "cores": par_info["procs"], "kind": "oracle",
+            "sample": "one spawned oracle process per core, each on its own 2,000-node sample of the 61^4 step "
+                      "mix, %.1f s" % par_info["seconds"]},
         "time_to_tol": solve,
         "warm_start": warm,
         "batch": batch,
+        "other_solves": extra,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -480,6 +541,8 @@ def main():
     ap.add_argument("--warm-start", type=int, default=1, help="train the network, compare cold/warm 121^4 solves")
     ap.add_argument("--mlp-epochs", type=int, default=2)
     ap.add_argument("--batch", type=int, default=1, help="time the 256-transfer batch")
+    ap.add_argument("--extra", type=int, default=1, help="17^4 FP64 VI; walk vs full tabulation")
+    ap.add_argument("--cpu-parallel", type=int, default=1, help="also time the oracle on every host core")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-fp64-sample", type=int, default=4)
     args = ap.parse_args()

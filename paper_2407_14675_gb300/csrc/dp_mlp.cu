@@ -53,8 +53,8 @@ constexpr int kH = 256;                       // hidden width
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kH * 4, kOffW2 = kOffB1 + kH, kOffB2 = kOffW2 + kH * kH;
 constexpr int kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH * kH, kOffW4 = kOffB3 + kH, kOffB4 = kOffW4 + 3 * kH;
 constexpr int kParams = kOffB4 + 3;           // 133,635
-constexpr int kTileM = 128, kKC = 64;
-constexpr int kGemmSmem = 80 * 1024;          // 48 KB of tiles; 80 KB keeps <= 2 CTAs (TMEM 2 x 256) per SM
+constexpr int kTileM = 128, kTileN = 128, kKC = 256;
+constexpr int kGemmSmem = (kTileM + kTileN) * kKC * 2;   // 128 KB: a whole 256-wide K slice of A and B
 constexpr int kWaitPolls = 1 << 22;
 constexpr float kInvSqrt2 = 0.70710678118654752f, kInvSqrt2Pi = 0.39894228040143268f;
 
@@ -66,9 +66,12 @@ __device__ __forceinline__ float gelu_grad(float z)
 
 enum { kEpiFwd = 0, kEpiBwd = 1, kEpiAtomic = 2 };
 
-// C[128 x 256 tile] = A[rows, K range] * B[256, K range]^T on tcgen05.
+// C[128 x 128 tile] = A[rows, K range] * B[256, K range]^T on tcgen05.
 //   A: bf16 [*, lda] row-major (K contiguous); B: bf16 [256, ldb] row-major.
-//   Tile rows start at 128 blockIdx.x; K range [k_per_cta blockIdx.y, +k_per_cta).
+//   Tile rows start at 128 blockIdx.x, columns at 128 blockIdx.y; K range
+//   [k_per_cta blockIdx.z, +k_per_cta), staged 256 at a time: every thread
+//   issues its 16-byte loads of the whole slice at once, then one thread
+//   issues the 16 MMAs (K = 16 each) and commits them to an mbarrier.
 //   kEpiFwd:    z = acc + bias -> zout (optional, FP32), h = GELU(z) -> hout (bf16)
 //   kEpiBwd:    dz = acc * GELU'(zin) -> hout (bf16)
 //   kEpiAtomic: cacc += acc (FP32, split-K weight gradients)
@@ -79,43 +82,55 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
                 bf16* __restrict__ hout, float* __restrict__ cacc, int* __restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sA = smem;                       // 128 x 64 bf16 = 16 KB
-    unsigned char* sB = smem + kTileM * kKC * 2;    // 256 x 64 bf16 = 32 KB
+    unsigned char* sA = smem;                        // 128 x 256 bf16 = 64 KB
+    unsigned char* sB = smem + kTileM * kKC * 2;     // 128 x 256 bf16 = 64 KB
     __shared__ unsigned tmem_slot;
     __shared__ __align__(8) unsigned long long mbar;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == 0) tmem_alloc(&tmem_slot, kH);
+    if (warp == 0) tmem_alloc(&tmem_slot, kTileN);
     if (tid == 0) mbar_init(&mbar);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const unsigned tmem = tmem_slot;
     const size_t row0 = (size_t)blockIdx.x * kTileM;
-    const int kbeg = blockIdx.y * k_per_cta;
-    constexpr unsigned idesc = umma_idesc_bf16(kTileM, kH);
+    const int n0 = blockIdx.y * kTileN;
+    const int kbeg = blockIdx.z * k_per_cta;
+    constexpr unsigned idesc = umma_idesc_bf16(kTileM, kTileN);
+    constexpr int kGroups = kKC / 8;                 // 16-byte groups per row of a slice
 
     int phase = 0;
     bool ok = true;
     for (int k0 = kbeg; k0 < kbeg + k_per_cta; k0 += kKC) {
-        // core-matrix staging: (row, kb) -> ((row / 8) * 8 + kb) * 128 + (row % 8) * 16
-        for (int v = tid; v < kTileM * (kKC / 8); v += 128) {
-            const int row = v >> 3, kb = v & 7;
-            const int4 val = *(const int4*)(A + (row0 + row) * (size_t)lda + k0 + kb * 8);
-            *(int4*)(sA + ((row >> 3) * 8 + kb) * 128 + (row & 7) * 16) = val;
+        // core-matrix staging: (row, kb) -> ((row / 8) * kGroups + kb) * 128 + (row % 8) * 16.
+        // A warp takes 8 rows x 4 consecutive 16-byte groups: 64 contiguous bytes
+        // of each row in global memory, 512 contiguous bytes (no bank conflict)
+        // in shared memory.
+        int4 va[kTileM * kGroups / 128], vb[kTileN * kGroups / 128];
+#pragma unroll
+        for (int q = 0; q < kTileM * kGroups / 128; ++q) {
+            const int v = tid + 128 * q, grp = v >> 5, ln = v & 31;
+            const int row = (grp / (kGroups / 4)) * 8 + (ln & 7), kb = (grp % (kGroups / 4)) * 4 + (ln >> 3);
+            va[q] = *(const int4*)(A + (row0 + row) * (size_t)lda + k0 + kb * 8);
         }
-        for (int v = tid; v < kH * (kKC / 8); v += 128) {
-            const int row = v >> 3, kb = v & 7;
-            const int4 val = *(const int4*)(B + (size_t)row * ldb + k0 + kb * 8);
-            *(int4*)(sB + ((row >> 3) * 8 + kb) * 128 + (row & 7) * 16) = val;
+#pragma unroll
+        for (int q = 0; q < kTileN * kGroups / 128; ++q) {
+            const int v = tid + 128 * q, grp = v >> 5, ln = v & 31;
+            const int row = (grp / (kGroups / 4)) * 8 + (ln & 7), kb = (grp % (kGroups / 4)) * 4 + (ln >> 3);
+            vb[q] = *(const int4*)(B + (size_t)(n0 + row) * ldb + k0 + kb * 8);
         }
+#pragma unroll
+        for (int q = 0; q < kTileM * kGroups / 128; ++q) *(int4*)(sA + (size_t)(tid + 128 * q) * 16) = va[q];
+#pragma unroll
+        for (int q = 0; q < kTileN * kGroups / 128; ++q) *(int4*)(sB + (size_t)(tid + 128 * q) * 16) = vb[q];
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {
             fence_after_sync();
 #pragma unroll
             for (int s = 0; s < kKC / 16; ++s) {
-                const unsigned long long ad = umma_desc(smem_u32(sA) + s * 256, 128, (kKC / 8) * 128);
-                const unsigned long long bd = umma_desc(smem_u32(sB) + s * 256, 128, (kKC / 8) * 128);
+                const unsigned long long ad = umma_desc(smem_u32(sA) + s * 256, 128, kGroups * 128);
+                const unsigned long long bd = umma_desc(smem_u32(sB) + s * 256, 128, kGroups * 128);
                 umma_bf16(tmem, ad, bd, idesc, (k0 > kbeg || s > 0) ? 1u : 0u);
             }
             umma_commit(&mbar);
@@ -131,27 +146,46 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
     fence_after_sync();
     if (ok) {
         const size_t r = row0 + warp * 32 + lane;   // TMEM lane = tile row
-        for (int c0 = 0; c0 < kH; c0 += 16) {
+        for (int c0 = 0; c0 < kTileN; c0 += 16) {
             float v[16];
             tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + c0, v);
+            const size_t off = r * kH + n0 + c0;     // 16 consecutive columns, 64-byte aligned
+            if (EPI == kEpiAtomic) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int c = c0 + q;
-                if (EPI == kEpiFwd) {
-                    const float z = v[q] + bias[c];
-                    if (zout) zout[r * kH + c] = z;
-                    hout[r * kH + c] = __float2bfloat16(gelu(z));
-                } else if (EPI == kEpiBwd) {
-                    hout[r * kH + c] = __float2bfloat16(v[q] * gelu_grad(zin[r * kH + c]));
-                } else {
-                    atomicAdd(&cacc[r * kH + c], v[q]);
+                for (int q = 0; q < 16; ++q) atomicAdd(&cacc[off + q], v[q]);
+                continue;
+            }
+            float z[16];
+            if (EPI == kEpiFwd) {
+#pragma unroll
+                for (int q = 0; q < 16; q += 4) {
+                    const float4 b = *(const float4*)(bias + n0 + c0 + q);
+                    z[q] = v[q] + b.x; z[q + 1] = v[q + 1] + b.y; z[q + 2] = v[q + 2] + b.z; z[q + 3] = v[q + 3] + b.w;
+                    if (zout) *(float4*)(zout + off + q) = make_float4(z[q], z[q + 1], z[q + 2], z[q + 3]);
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) z[q] = gelu(z[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; q += 4) {
+                    const float4 zi = *(const float4*)(zin + off + q);
+                    z[q] = v[q] * gelu_grad(zi.x); z[q + 1] = v[q + 1] * gelu_grad(zi.y);
+                    z[q + 2] = v[q + 2] * gelu_grad(zi.z); z[q + 3] = v[q + 3] * gelu_grad(zi.w);
                 }
             }
+            unsigned pk[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(z[2 * q], z[2 * q + 1]);
+                pk[q] = *(const unsigned*)&h2;
+            }
+            *(uint4*)(hout + off) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *(uint4*)(hout + off + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
         }
     }
     fence_before_sync();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kH);
+    if (warp == 0) tmem_dealloc(tmem, kTileN);
 }
 
 // Inputs (normalised to [-1, 1]^4) and targets (V / M, cos, sin) of nodes
@@ -421,7 +455,7 @@ cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int 
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid(rows / kTileM, k_split);
+    dim3 grid(rows / kTileM, kH / kTileN, k_split);
     mlp_gemm_kernel<EPI><<<grid, 128, kGemmSmem, m->st>>>(A, lda, B, ldb, k_total / k_split, bias, zout, zin, hout,
                                                            cacc, m->err);
     return cudaGetLastError();
@@ -466,7 +500,7 @@ int backward(dp_mlp* m, int count)
     transpose_kernel<<<tg, tb, 0, m->st>>>(m->dz3, rows, m->T1);
     transpose_kernel<<<tg, tb, 0, m->st>>>(m->h2, rows, m->T2);
     MCK(cudaGetLastError());
-    MCK(gemm<kEpiAtomic>(m, m->T1, rows, m->T2, rows, kH, rows, rows / 512, nullptr, nullptr, nullptr, nullptr,
+    MCK(gemm<kEpiAtomic>(m, m->T1, rows, m->T2, rows, kH, rows, rows / kKC, nullptr, nullptr, nullptr, nullptr,
                          m->G + kOffW3));
     feat_reduce_kernel<<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz3, nullptr, 0, rows, chunk, nullptr,
                                                                        m->G + kOffB3);
@@ -476,7 +510,7 @@ int backward(dp_mlp* m, int count)
     transpose_kernel<<<tg, tb, 0, m->st>>>(m->dz2, rows, m->T1);
     transpose_kernel<<<tg, tb, 0, m->st>>>(m->h1, rows, m->T2);
     MCK(cudaGetLastError());
-    MCK(gemm<kEpiAtomic>(m, m->T1, rows, m->T2, rows, kH, rows, rows / 512, nullptr, nullptr, nullptr, nullptr,
+    MCK(gemm<kEpiAtomic>(m, m->T1, rows, m->T2, rows, kH, rows, rows / kKC, nullptr, nullptr, nullptr, nullptr,
                          m->G + kOffW2));
     feat_reduce_kernel<<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz2, nullptr, 0, rows, chunk, nullptr,
                                                                        m->G + kOffB2);

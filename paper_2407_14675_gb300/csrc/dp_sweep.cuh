@@ -151,22 +151,23 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
     (void)kSearch;
     if constexpr (MODE == kEvalFeet || MODE == kIncr) {
         // frozen feet: gather-bound, so the next node's foot and value are
-        // fetched while this node's corners are in flight
+        // fetched while this node's corners are in flight.  The feet are read
+        // once per sweep: evict-first loads keep L1 and L2 for the gathered V.
         const bool first = incr_flags & 1, last = incr_flags & 2;
         int j = j0;
         FootWord w_next{0ull, 0u};
         S v_next = (S)0;
         if (j < end) {
-            w_next.lo = feet_lo[j];
-            w_next.hi = feet_hi[j];
+            w_next.lo = __ldcs(&feet_lo[j]);
+            w_next.hi = __ldcs(&feet_hi[j]);
             v_next = Vin[j];
         }
         for (; j < end; j += stride) {
             const FootWord w = w_next;
             const S vj = v_next;
             if (j + stride < end) {
-                w_next.lo = feet_lo[j + stride];
-                w_next.hi = feet_hi[j + stride];
+                w_next.lo = __ldcs(&feet_lo[j + stride]);
+                w_next.hi = __ldcs(&feet_hi[j + stride]);
                 v_next = Vin[j + stride];
             }
             const int kind = (int)((w.hi >> 16) & 3u);
