@@ -109,24 +109,31 @@ def _dist():
     return world, rank, local
 
 
-def _reduce_max(x, world):
+def _reduce(x, world, op):
+    """All-reduce of one float over the ranks (NCCL on GPUs, gloo on CPU)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op={"max": dist.ReduceOp.MAX, "sum": dist.ReduceOp.SUM}[op])
     return float(t.item())
+
+
+def _reduce_max(x, world):
+    return _reduce(x, world, "max")
 
 
 def _reduce_sum(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, "sum")
+
+
+def aggregate_replicas(updates, ms, world):
+    """Whole-job throughput of independent replicas: every rank's node updates
+    over the slowest rank's time.  Returns (value, slowest ms)."""
+    ms_max = _reduce_max(ms, world)
+    return _reduce_sum(float(updates), world) / (ms_max / 1e3), ms_max
 
 
 def _barrier(world):
@@ -418,10 +425,8 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
     _barrier(world)
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    ms_max = _reduce_max(ms, world)
     updates = sum(s.node_updates for s in stats)
-    total_updates = _reduce_sum(float(updates), world)
-    value = total_updates / (ms_max / 1e3)
+    value, ms_max = aggregate_replicas(updates, ms, world)
     ms_eval = sum(s.ms_eval for s in stats)
     n_eval = sum(s.sweeps_eval for s in stats)
     ms_imp = sum(s.ms_improve for s in stats)
