@@ -18,6 +18,8 @@ from .build import build_oracle
 
 VI, IMPROVE_FULL, IMPROVE_WALK, EVAL = 0, 1, 2, 3
 NCODES = 65536
+CODE_OFF = 65535   # thrust off (grids with the off control)
+OFF = float("nan")  # the off control as an "angle" argument
 
 _lib = None
 
@@ -42,6 +44,13 @@ class _Problem(C.Structure):
         ("reduced", C.c_int),
         ("e_lo", C.c_double),
         ("e_hi", C.c_double),
+        ("off_control", C.c_int),
+        ("cost_alpha", C.c_double),
+        ("cost_beta", C.c_double),
+        ("cost_gamma", C.c_double),
+        ("a_bar", C.c_double),
+        ("e_bar", C.c_double),
+        ("omega_bar", C.c_double),
     ]
 
 
@@ -61,6 +70,8 @@ def lib():
             "orc_build_masks": (C.c_long, [P, _u8, _u8]),
             "orc_in_target": (C.c_int, [P, _dp]),
             "orc_energy": (C.c_double, [P, _dp]),
+            "orc_elements": (None, [P, _dp, _dp, _dp, _dp]),
+            "orc_running_cost": (C.c_double, [P, _dp, C.c_int]),
             "orc_dynamics": (None, [P, _dp, C.c_double, _dp]),
             "orc_heun_displacement": (None, [P, _dp, C.c_double, C.c_double, _dp]),
             "orc_rk4_step": (None, [P, _dp, C.c_double, C.c_double, _dp]),
@@ -104,6 +115,9 @@ def problem(p) -> _Problem:
     s.tgt_w[:] = list(p.target_w)
     s.K, s.refine, s.refine_tol = p.n_angles, p.refine, p.refine_tol
     s.reduced, s.e_lo, s.e_hi = p.reduced, p.energy_lo, p.energy_hi
+    s.off_control = getattr(p, "off_control", 0)
+    s.cost_alpha, s.cost_beta, s.cost_gamma = (getattr(p, k, 0.0) for k in ("cost_alpha", "cost_beta", "cost_gamma"))
+    s.a_bar, s.e_bar, s.omega_bar = (getattr(p, k, 0.0) for k in ("a_bar", "e_bar", "omega_bar"))
     return s
 
 
@@ -141,6 +155,17 @@ class Oracle:
     def energy(self, x):
         x = np.ascontiguousarray(x, np.float64)
         return lib().orc_energy(C.byref(self.s), _ptr(x, _dp))
+
+    def elements(self, x):
+        """(a, e cos omega, e sin omega) of a polar state."""
+        x = np.ascontiguousarray(x, np.float64)
+        a, ex, ey = C.c_double(0), C.c_double(0), C.c_double(0)
+        lib().orc_elements(C.byref(self.s), _ptr(x, _dp), C.byref(a), C.byref(ex), C.byref(ey))
+        return a.value, ex.value, ey.value
+
+    def running_cost(self, x, thrust_on=True):
+        x = np.ascontiguousarray(x, np.float64)
+        return lib().orc_running_cost(C.byref(self.s), _ptr(x, _dp), int(thrust_on))
 
     def in_target(self, x):
         x = np.ascontiguousarray(x, np.float64)

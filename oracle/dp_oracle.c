@@ -29,7 +29,12 @@
  *     (in its discrete form, the Fibonacci search, on the 16-bit angle lattice);
  *   - the approximate optimal feedback Eq. (15) and its fourth-order
  *     Runge-Kutta closed loop (§3 "Computation of the approximate optimal
- *     solution").
+ *     solution");
+ *   - the paper's own Example 1 setting (§4): the polar system with the angle
+ *     theta kept as a periodic coordinate and no mass, the running cost of
+ *     Eq. (11) in polar form (semi-major axis by the vis-viva relation, the
+ *     eccentricity components e cos(omega), e sin(omega) from the
+ *     eccentricity vector), and a thrust-off control besides the angles.
  *
  * Parity unpinned: the paper prints no value function, policy or trajectory
  * value (its figures are not available); the pins of this oracle are closed
@@ -43,7 +48,8 @@
 #define ORC_NCODES 65536
 #define ORC_PI 3.14159265358979323846
 
-enum { ORC_DYN_ORBIT = 0, ORC_DYN_UNIT_SPEED = 1 };
+enum { ORC_DYN_ORBIT = 0, ORC_DYN_UNIT_SPEED = 1, ORC_DYN_POLAR = 2 };
+#define ORC_CODE_OFF 65535   /* policy code of the thrust-off control (grids with off_control) */
 enum { ORC_VI = 0, ORC_IMPROVE_FULL = 1, ORC_IMPROVE_WALK = 2, ORC_EVAL = 3 };
 
 typedef struct orc_problem {
@@ -58,6 +64,11 @@ typedef struct orc_problem {
     double refine_tol;   /* rad */
     int reduced;         /* energy-band node set */
     double e_lo, e_hi;
+    /* Example 1 (ORC_DYN_POLAR): state (rho, v_rho, v_theta, theta), theta
+     * periodic with n[3] nodes over 2 pi; running cost of Eq. (11) */
+    int off_control;     /* 1: a thrust-off control besides the angles */
+    double cost_alpha, cost_beta, cost_gamma;   /* weights of |u|, (a - a_bar)^2, eccentricity */
+    double a_bar, e_bar, omega_bar;             /* target orbit */
 } orc_problem;
 
 /* ------------------------------------------------------------------ grid -- */
@@ -65,6 +76,12 @@ typedef struct orc_problem {
 static double spacing(const orc_problem* p, int d)
 {
     return (p->hi[d] - p->lo[d]) / (double)(p->n[d] - 1);
+}
+
+/* The last coordinate is periodic (the orbital angle) in Example 1. */
+static int periodic(const orc_problem* p, int d)
+{
+    return p->dynamics == ORC_DYN_POLAR && d == 3;
 }
 
 long orc_node_count(const orc_problem* p)
@@ -105,6 +122,36 @@ double orc_energy(const orc_problem* p, const double x[4])
     return 0.5 * (x[1] * x[1] + x[2] * x[2]) - p->mu / x[0];
 }
 
+/* Orbital elements of a polar state (rho, v_rho, v_theta, theta) (§3 "Grid and
+ * polar coordinates"): semi-major axis by the vis-viva relation
+ * a = mu rho / (2 mu - rho v^2), and the eccentricity vector
+ * e = ((v^2 - mu/rho) r - (r . v) v) / mu, whose radial and transverse
+ * components are rho v_theta^2 / mu - 1 and -rho v_rho v_theta / mu; rotated by
+ * theta they give e cos(omega) and e sin(omega). */
+void orc_elements(const orc_problem* p, const double x[4], double* a, double* ex, double* ey)
+{
+    double r = x[0], vr = x[1], vt = x[2], th = x[3];
+    double v2 = vr * vr + vt * vt;
+    *a = p->mu * r / (2.0 * p->mu - r * v2);
+    double er = r * vt * vt / p->mu - 1.0;
+    double et = -r * vr * vt / p->mu;
+    *ex = er * cos(th) - et * sin(th);
+    *ey = er * sin(th) + et * cos(th);
+}
+
+/* Running cost l(x, u) of Eq. (11) in polar form: alpha |u| + beta (a - a_bar)^2
+ * + gamma ((e cos w - e_bar cos w_bar)^2 + (e sin w - e_bar sin w_bar)^2);
+ * |u| = thrust acceleration (0 when off).  Minimum time (l = 1) otherwise. */
+double orc_running_cost(const orc_problem* p, const double x[4], int thrust_on)
+{
+    if (p->dynamics != ORC_DYN_POLAR) return 1.0;
+    double a, ex, ey;
+    orc_elements(p, x, &a, &ex, &ey);
+    double dx = ex - p->e_bar * cos(p->omega_bar), dy = ey - p->e_bar * sin(p->omega_bar);
+    return p->cost_alpha * (thrust_on ? p->accel : 0.0) + p->cost_beta * (a - p->a_bar) * (a - p->a_bar) +
+           p->cost_gamma * (dx * dx + dy * dy);
+}
+
 /* Reduced grid: keep the node iff its energy lies in [e_lo, e_hi]. */
 static int node_active(const orc_problem* p, const double x[4])
 {
@@ -132,10 +179,20 @@ long orc_build_masks(const orc_problem* p, unsigned char* active, unsigned char*
 /* -------------------------------------------------------------- dynamics -- */
 
 /* Right-hand side b(x, alpha).  Orbit: r' = v_r, v_r' = v_t^2/r - mu/r^2 +
- * (a/m) sin alpha, v_t' = -v_r v_t / r + (a/m) cos alpha, m' = -a/c. */
+ * (a/m) sin alpha, v_t' = -v_r v_t / r + (a/m) cos alpha, m' = -a/c.
+ * Polar (Example 1): the same with thrust acceleration a (no mass) and the
+ * angle theta' = v_t / r as last coordinate; alpha = NAN is thrust off. */
 void orc_dynamics(const orc_problem* p, const double x[4], double alpha, double f[4])
 {
-    if (p->dynamics == ORC_DYN_ORBIT) {
+    if (p->dynamics == ORC_DYN_POLAR) {
+        double r = x[0], vr = x[1], vt = x[2];
+        double u = isnan(alpha) ? 0.0 : p->accel;
+        double sa = isnan(alpha) ? 0.0 : sin(alpha), ca = isnan(alpha) ? 0.0 : cos(alpha);
+        f[0] = vr;
+        f[1] = vt * vt / r - p->mu / (r * r) + u * sa;
+        f[2] = -vr * vt / r + u * ca;
+        f[3] = vt / r;
+    } else if (p->dynamics == ORC_DYN_ORBIT) {
         double r = x[0], vr = x[1], vt = x[2], m = x[3];
         double am = p->accel / m;
         f[0] = vr;
@@ -192,6 +249,15 @@ int orc_interp(const orc_problem* p, const double* V, const unsigned char* activ
     int cell[4];
     double t[4];
     for (int d = 0; d < 4; ++d) {
+        if (periodic(p, d)) {
+            /* the angle wraps: cells run from node n-1 back to node 0 */
+            if (!isfinite(s[d])) return 0;
+            double f = floor(s[d]);
+            t[d] = s[d] - f;
+            long c = (long)f % p->n[d];
+            cell[d] = (int)(c < 0 ? c + p->n[d] : c);
+            continue;
+        }
         if (!(s[d] >= 0.0 && s[d] <= (double)(p->n[d] - 1))) return 0;
         int c = (int)floor(s[d]);
         if (c > p->n[d] - 2) c = p->n[d] - 2;
@@ -205,6 +271,7 @@ int orc_interp(const orc_problem* p, const double* V, const unsigned char* activ
         for (int d = 0; d < 4; ++d) {
             int bit = (b >> (3 - d)) & 1;
             idx[d] = cell[d] + bit;
+            if (periodic(p, d) && idx[d] == p->n[d]) idx[d] = 0;
             w *= bit ? t[d] : 1.0 - t[d];
         }
         long j = flat_index(p, idx);
@@ -224,6 +291,13 @@ static double code_angle(long code)
     return 2.0 * ORC_PI * (double)c / (double)ORC_NCODES;
 }
 
+/* Control of a policy code: the angle, or NAN for thrust off. */
+static double code_control(const orc_problem* p, long code)
+{
+    if (p->off_control && code == ORC_CODE_OFF) return NAN;
+    return code_angle(code);
+}
+
 /* Code of the k-th tabulated angle 2 pi k / K on the 16-bit lattice. */
 static long table_code(int K, long k)
 {
@@ -236,8 +310,8 @@ static int nearest_table_index(int K, long code)
     return (int)(((code * K + ORC_NCODES / 2) / ORC_NCODES) % K);
 }
 
-/* Term of Eq. (10) at grid node idx for control angle alpha:
- * dt * l + beta * I[V](x_j + dt Phi(x_j, alpha)), l = 1. */
+/* Term of Eq. (10) at grid node idx for control alpha (NAN: thrust off):
+ * dt * l(x_j, alpha) + beta * I[V](x_j + dt Phi(x_j, alpha)). */
 double orc_q_node(const orc_problem* p, const double* V, const unsigned char* active,
                   const int idx[4], double alpha)
 {
@@ -246,7 +320,7 @@ double orc_q_node(const orc_problem* p, const double* V, const unsigned char* ac
     orc_heun_displacement(p, x, alpha, p->dt, delta);
     for (int d = 0; d < 4; ++d) s[d] = idx[d] + delta[d] / spacing(p, d);
     if (!orc_interp(p, V, active, s, &I)) I = p->M;
-    return p->dt + p->beta * I;
+    return p->dt * orc_running_cost(p, x, !isnan(alpha)) + p->beta * I;
 }
 
 /* Foot of the one-step map from grid node idx in grid units (test helper:
@@ -268,7 +342,7 @@ double orc_q_state(const orc_problem* p, const double* V, const unsigned char* a
     orc_heun_displacement(p, y, alpha, tau, delta);
     for (int d = 0; d < 4; ++d) s[d] = (y[d] + delta[d] - p->lo[d]) / spacing(p, d);
     if (!orc_interp(p, V, active, s, &I)) I = p->M;
-    return tau + pow(p->beta, tau / p->dt) * I;
+    return tau * orc_running_cost(p, y, !isnan(alpha)) + pow(p->beta, tau / p->dt) * I;
 }
 
 typedef struct {
@@ -284,7 +358,7 @@ typedef struct {
 static double q_of_code(q_ctx* c, long code)
 {
     c->evals++;
-    double a = code_angle(code);
+    double a = code_control(c->p, code);
     if (c->idx) return orc_q_node(c->p, c->V, c->active, c->idx, a);
     return orc_q_state(c->p, c->V, c->active, c->y, a, c->tau);
 }
@@ -321,6 +395,17 @@ static int walk_table(q_ctx* c, int k0, double* qbest)
     return k;
 }
 
+/* A refinement point that the search may not evaluate: beyond the upper
+ * tabulated neighbour, or (grids with the off control) the lattice code that
+ * stands for thrust off. */
+static int excluded(const q_ctx* c, long ck, long x, long hi_off)
+{
+    if (x >= hi_off) return 1;
+    long w = (ck + x) % ORC_NCODES;
+    if (w < 0) w += ORC_NCODES;
+    return c->p->off_control && w == ORC_CODE_OFF;
+}
+
 /* Golden-section refinement in its discrete form (Fibonacci search) on the
  * 16-bit angle lattice, inside the bracket formed by the two tabulated
  * neighbours of the tabulated minimiser k.  The interval is extended to a
@@ -345,8 +430,8 @@ static long fibonacci_refine(q_ctx* c, int k, double qk, double* qbest)
     const double step_rad = 2.0 * ORC_PI / ORC_NCODES;
     long a = lo_off;
     long x1 = a + F[n - 2], x2 = a + F[n - 1];
-    double f1 = (x1 >= hi_off) ? INFINITY : q_of_code(c, ck + x1);
-    double f2 = (x2 >= hi_off) ? INFINITY : q_of_code(c, ck + x2);
+    double f1 = excluded(c, ck, x1, hi_off) ? INFINITY : q_of_code(c, ck + x1);
+    double f2 = excluded(c, ck, x2, hi_off) ? INFINITY : q_of_code(c, ck + x2);
     if (f1 < qb) { qb = f1; best = ck + x1; }
     if (f2 < qb) { qb = f2; best = ck + x2; }
     /* interval [a, a + F[kk]] holds the points a + F[kk-2] and a + F[kk-1] */
@@ -354,13 +439,13 @@ static long fibonacci_refine(q_ctx* c, int k, double qk, double* qbest)
         if (f1 <= f2) {          /* keep [a, x2] */
             x2 = x1; f2 = f1;
             x1 = a + F[kk - 3];
-            f1 = (x1 >= hi_off) ? INFINITY : q_of_code(c, ck + x1);
+            f1 = excluded(c, ck, x1, hi_off) ? INFINITY : q_of_code(c, ck + x1);
             if (f1 < qb) { qb = f1; best = ck + x1; }
         } else {                 /* keep [x1, a + F[kk]] */
             a = x1;
             x1 = x2; f1 = f2;
             x2 = a + F[kk - 2];
-            f2 = (x2 >= hi_off) ? INFINITY : q_of_code(c, ck + x2);
+            f2 = excluded(c, ck, x2, hi_off) ? INFINITY : q_of_code(c, ck + x2);
             if (f2 < qb) { qb = f2; best = ck + x2; }
         }
     }
@@ -388,10 +473,18 @@ long orc_bellman_node(const orc_problem* p, const double* V, const unsigned char
         return c.evals;
     }
     int k;
-    if (mode == ORC_IMPROVE_WALK) k = walk_table(&c, nearest_table_index(p->K, code_in), &q);
+    /* a node whose previous control was off has no angle to walk from: it
+     * tabulates in full */
+    int walk = mode == ORC_IMPROVE_WALK && !(p->off_control && code_in == ORC_CODE_OFF);
+    if (walk) k = walk_table(&c, nearest_table_index(p->K, code_in), &q);
     else k = enumerate_table(&c, &q);
     long code = table_code(p->K, k) % ORC_NCODES;
     if (mode != ORC_VI && p->refine) code = fibonacci_refine(&c, k, q, &q);
+    if (p->off_control) {
+        /* thrust off is one more control; it wins a tie */
+        double q_off = q_of_code(&c, ORC_CODE_OFF);
+        if (q_off <= q) { q = q_off; code = ORC_CODE_OFF; }
+    }
     *v_out = q;
     *code_out = (unsigned)code;
     return c.evals;
@@ -440,7 +533,7 @@ void orc_q_nodes(const orc_problem* p, const double* V, const unsigned char* act
     for (long i = 0; i < count; ++i) {
         int idx[4];
         node_index(p, nodes[i], idx);
-        q_out[i] = orc_q_node(p, V, active, idx, code_angle(codes[i]));
+        q_out[i] = orc_q_node(p, V, active, idx, code_control(p, codes[i]));
     }
 }
 
@@ -508,6 +601,10 @@ void orc_feedback(const orc_problem* p, const double* V, const unsigned char* ac
         int k = enumerate_table(&c, &q);
         long code = table_code(p->K, k) % ORC_NCODES;
         if (p->refine) code = fibonacci_refine(&c, k, q, &q);
+        if (p->off_control) {
+            double q_off = q_of_code(&c, ORC_CODE_OFF);
+            if (q_off <= q) { q = q_off; code = ORC_CODE_OFF; }
+        }
         code_out[i] = (uint16_t)code;
         if (q_out) q_out[i] = q;
     }
@@ -529,7 +626,7 @@ void orc_simulate(const orc_problem* p, const double* V, const unsigned char* ac
         for (long s = 0; s < steps; ++s) {
             uint16_t code;
             orc_feedback(p, V, active, y, 1, tau, &code, NULL);
-            orc_rk4_step(p, y, code_angle(code), h, z);
+            orc_rk4_step(p, y, code_control(p, code), h, z);
             memcpy(y, z, sizeof y);
             if (orc_in_target(p, y)) { t_arrive[i] = (s + 1) * h; break; }
         }

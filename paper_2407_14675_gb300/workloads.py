@@ -22,6 +22,7 @@ import numpy as np
 
 DYN_ORBIT = 0        # (r, v_r, v_t, m) planar orbit dynamics with mass flow
 DYN_UNIT_SPEED = 1   # test dynamics x' = (cos a, sin a, 0, 0)
+DYN_POLAR = 2        # (rho, v_rho, v_theta, theta), theta periodic, no mass (the paper's Example 1)
 
 FP64 = 0
 FP32 = 1
@@ -49,6 +50,14 @@ class Problem:
     energy_lo: float = 0.0
     energy_hi: float = 0.0
     precision: int = FP64
+    # Example 1 (DYN_POLAR): thrust-off control and the running cost of Eq. (11)
+    off_control: int = 0
+    cost_alpha: float = 0.0
+    cost_beta: float = 0.0
+    cost_gamma: float = 0.0
+    a_bar: float = 0.0
+    e_bar: float = 0.0
+    omega_bar: float = 0.0
     # solver settings (not part of the grid)
     tol: float = 1e-8
     n_eval: int = 20
@@ -91,6 +100,42 @@ def config2(n: int = 121) -> Problem:
     """121^4 box reduced to the energy band, config-1 dynamics."""
     e_lo, e_hi = energy_band(1.0, 1.05)
     return config1(n).replace(reduced=1, energy_lo=e_lo, energy_hi=e_hi)
+
+
+MU_EARTH = 398600.4418   # km^3 / s^2
+
+
+def example1(n=(110, 30, 30, 30), accel: float = 5e-7) -> Problem:
+    """The paper's Example 1 (§4): target orbit a = 7000 km, e = 0.001, argument
+    of perigee 0; thrust acceleration 5e-7 km/s^2; cost weights alpha = 2.04e-8,
+    beta = 2.31e-2, gamma = 1.5; lambda = 1e-3 (discount exp(-lambda dt));
+    dt = 10 s; rho in [6930, 7070] km, v_rho in [-0.01, 0.01] km/s, v_theta in
+    [7.526, 7.566] km/s, theta in [0, 2 pi) periodic; 72 angles + thrust off.
+    State order (rho, v_rho, v_theta, theta); n gives the nodes in that order
+    (the paper's 110 x 30 x 30 x 30).  No target set (V > 0 everywhere); M is
+    twice the cost of the worst box node held forever."""
+    nt = n[3]
+    dt, lam = 10.0, 1e-3
+    beta = math.exp(-lam * dt)
+    lo = (6930.0, -0.01, 7.526, 0.0)
+    hi = (7070.0, 0.01, 7.566, 2.0 * math.pi * (nt - 1) / nt)
+    a_bar, e_bar = 7000.0, 0.001
+    # worst cost on the box: |a - a_bar| at the vis-viva extremes
+    def a_of(r, v):
+        return MU_EARTH * r / (2.0 * MU_EARTH - r * v * v)
+    vmax = math.hypot(0.01, 7.566)
+    worst = max(abs(a_of(r, v) - a_bar) for r in (6930.0, 7070.0) for v in (7.526, vmax))
+    M = 2.0 * dt * (2.31e-2 * worst ** 2 + 1.5 * 0.25) / (1.0 - beta)
+    return Problem(n=tuple(n), lo=lo, hi=hi, dynamics=DYN_POLAR, mu=MU_EARTH, accel=accel, exhaust_c=1.0,
+                   dt=dt, beta=beta, penalty_M=M, target_c=(-1.0, 0.0, 0.0, 0.0), target_w=(1e-9, 0.0, 0.0, 0.0),
+                   n_angles=72, refine=1, refine_tol=1e-4, precision=FP64, tol=1e-7, n_eval=20,
+                   off_control=1, cost_alpha=2.04e-8, cost_beta=2.31e-2, cost_gamma=1.5,
+                   a_bar=a_bar, e_bar=e_bar, omega_bar=0.0)
+
+
+def example1_start(r0: float = 6978.0) -> np.ndarray:
+    """Circular orbit of radius r0 km at theta = 0 (the paper's start)."""
+    return np.array([r0, 0.0, math.sqrt(MU_EARTH / r0), 0.0])
 
 
 def unit_speed_1d(n: int = 17, beta: float = 0.95, target_node: int = 8) -> Problem:

@@ -412,3 +412,91 @@ def test_closed_loop_1d_arrival_time():
     ta, xf = o.simulate(V, x0, tau=p.dt, h=p.dt, t_max=2.0)
     assert ta == pytest.approx([8 * p.dt, 8 * p.dt, 5 * p.dt], abs=1e-12)
     assert xf[:, 0] == pytest.approx([1.5, 1.5, 1.5], abs=1e-12)
+
+
+# ------------------------------------------ the paper's Example 1 (§4) --
+
+def _ellipse_state(mu, a, e, omega, nu):
+    """Textbook Kepler orbit: state at true anomaly nu of the orbit (a, e,
+    argument of perigee omega), in the polar form (rho, v_rho, v_theta, theta)."""
+    p_ = a * (1.0 - e * e)
+    rho = p_ / (1.0 + e * math.cos(nu))
+    k = math.sqrt(mu / p_)
+    return np.array([rho, k * e * math.sin(nu), k * (1.0 + e * math.cos(nu)), omega + nu])
+
+
+def test_example1_orbital_elements_match_kepler_orbits():
+    p = W.example1(n=(5, 3, 3, 4))
+    o = oracle.Oracle(p)
+    for a, e, w in ((7000.0, 0.0, 0.0), (7000.0, 0.001, 0.0), (6990.0, 0.004, 1.3), (7040.0, 0.02, -2.5)):
+        for nu in (0.0, 0.7, 2.0, math.pi, 4.4):
+            x = _ellipse_state(W.MU_EARTH, a, e, w, nu)
+            ga, ex, ey = o.elements(x)
+            assert ga == pytest.approx(a, rel=1e-12)
+            assert ex == pytest.approx(e * math.cos(w), abs=1e-12)
+            assert ey == pytest.approx(e * math.sin(w), abs=1e-12)
+
+
+def test_example1_cost_vanishes_on_the_target_orbit():
+    # Eq. (11): on the target orbit only the control term remains
+    p = W.example1(n=(5, 3, 3, 4))
+    o = oracle.Oracle(p)
+    for nu in np.linspace(0.0, 2 * math.pi, 9):
+        x = _ellipse_state(W.MU_EARTH, p.a_bar, p.e_bar, p.omega_bar, nu)
+        assert abs(o.running_cost(x, thrust_on=False)) < 1e-12
+        assert o.running_cost(x, thrust_on=True) == pytest.approx(p.cost_alpha * p.accel, abs=1e-12)
+    # off the target: beta (a - a_bar)^2 + gamma e^2 on a circular orbit
+    x = W.example1_start(6980.0)
+    assert o.running_cost(x, False) == pytest.approx(p.cost_beta * 20.0 ** 2 + p.cost_gamma * p.e_bar ** 2,
+                                                     rel=1e-9)
+
+
+def test_example1_dynamics_identities():
+    p = W.example1(n=(5, 3, 3, 4))
+    o = oracle.Oracle(p)
+    x = W.example1_start(7000.0)
+    f = o.dynamics(x, oracle.OFF)   # circular orbit, thrust off: at rest but the angle
+    assert np.abs(f[:3]).max() < 1e-15 and f[3] == pytest.approx(x[2] / x[0], rel=1e-15)
+    y = np.array([6990.0, 0.004, 7.55, 1.1])
+    for alpha in (0.0, 0.9, 2.5, 4.0):
+        f = o.dynamics(y, alpha)
+        u = p.accel
+        dE = y[1] * f[1] + y[2] * f[2] + W.MU_EARTH / y[0] ** 2 * f[0]   # d/dt (v^2/2 - mu/rho)
+        assert dE == pytest.approx(u * (y[1] * math.sin(alpha) + y[2] * math.cos(alpha)), rel=1e-9, abs=1e-18)
+        dh = f[0] * y[2] + y[0] * f[2]                                  # d/dt (rho v_theta)
+        assert dh == pytest.approx(y[0] * u * math.cos(alpha), rel=1e-9, abs=1e-15)
+
+
+def test_example1_angle_interpolates_periodically():
+    # V = (multilinear in rho, v_rho, v_theta) x (a value per angle node): the
+    # Q1 interpolation is exact, and the cell past the last node reaches node 0
+    p = W.example1(n=(4, 3, 3, 6))
+    o = oracle.Oracle(p)
+    rng = np.random.default_rng(4)
+    g = rng.uniform(1, 2, 6)
+    c = rng.uniform(-1, 1, 4)
+    i0, i1, i2, i3 = np.meshgrid(*[np.arange(k) for k in p.n], indexing="ij")
+    lin = c[0] + c[1] * i0 + c[2] * i1 * i2 + c[3] * i0 * i1 * i2
+    V = (lin * g[i3]).reshape(-1)
+    s = np.array([1.3, 0.4, 1.7, 5.25])      # between angle node 5 and node 0
+    l = c[0] + c[1] * 1.3 + c[2] * 0.4 * 1.7 + c[3] * 1.3 * 0.4 * 1.7
+    assert o.interp(V, s) == pytest.approx(l * (0.75 * g[5] + 0.25 * g[0]), rel=1e-13)
+    for k in (-2, 1, 3):
+        assert o.interp(V, s + np.array([0, 0, 0, 6.0 * k])) == pytest.approx(o.interp(V, s), rel=1e-13)
+
+
+def test_example1_thrust_off_wins_where_thrust_only_costs():
+    # V constant inside the box: every control lands on the same value, so
+    # the control term alpha |u| decides and the improvement switches off
+    p = W.example1(n=(6, 4, 4, 6))
+    o = oracle.Oracle(p)
+    V = np.full(o.N, 5.0)
+    Vn, codes, res, ev = o.sweep(V, mode=oracle.IMPROVE_FULL, codes=np.zeros(o.N, np.uint16))
+    idx = np.array(np.unravel_index(np.arange(o.N), p.n)).T
+    interior = (idx[:, 0] > 0) & (idx[:, 0] < p.n[0] - 1) & (idx[:, 1] > 0) & (idx[:, 1] < p.n[1] - 1) & \
+               (idx[:, 2] > 0) & (idx[:, 2] < p.n[2] - 1)
+    assert interior.any()
+    assert (codes[interior] == oracle.CODE_OFF).all()
+    for j in np.flatnonzero(interior)[:5]:
+        x = np.array(p.lo) + idx[j] * (np.array(p.hi) - np.array(p.lo)) / (np.array(p.n) - 1)
+        assert Vn[j] == pytest.approx(p.dt * o.running_cost(x, False) + p.beta * 5.0, rel=1e-14)
