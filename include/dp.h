@@ -62,6 +62,13 @@ extern "C" {
 #define DP_DYN_ORBIT      0  /* planar orbit (r, v_r, v_t, m), §3 polar dynamics   */
 #define DP_DYN_UNIT_SPEED 1  /* test dynamics x' = (cos a, sin a, 0, 0); components
                                 below 1e-12 in magnitude are taken as exact zeros  */
+#define DP_DYN_POLAR      2  /* the paper's Example 1 (§4): state (rho, v_rho,
+                                v_theta, theta), the polar system of §3 with thrust
+                                acceleration `accel` and no mass; theta periodic
+                                (n[3] nodes over 2 pi: hi[3] = lo[3] + 2 pi
+                                (n[3]-1)/n[3]); running cost of Eq. (11); FP64 only */
+
+#define DP_CODE_OFF 65535    /* policy code of the thrust-off control (off_control) */
 
 #define DP_SWEEP_VI           0  /* Eq. (12): min over the tabulated angles        */
 #define DP_SWEEP_IMPROVE_FULL 1  /* Eq. (14): full tabulation (+ refinement)       */
@@ -92,6 +99,13 @@ typedef struct dp_grid_desc {
     double  energy_lo, energy_hi; /* specific energy (v_r^2 + v_t^2)/2 - mu/r band   */
     int32_t precision;     /* DP_FP64 or DP_FP32                                     */
     void*   stream;        /* cudaStream_t for all work of this grid (may be NULL)   */
+    /* DP_DYN_POLAR only (ignored otherwise): */
+    int32_t off_control;   /* 1: thrust off (DP_CODE_OFF) is a control besides the
+                              angles; it wins a tie                                  */
+    double  cost_alpha, cost_beta, cost_gamma; /* Eq. (11): alpha |u| + beta (a - a_bar)^2
+                              + gamma |(e cos w, e sin w) - (e_bar cos w_bar, ...)|^2 */
+    double  a_bar, e_bar, omega_bar;           /* target orbit: semi-major axis (length
+                              unit of the box), eccentricity, argument of perigee  */
 } dp_grid_desc;
 
 /* Solver options. */
@@ -194,8 +208,10 @@ int dp_policy_iterate(dp_grid* grid, const dp_solve_opts* opts, dp_solve_stats* 
 
 /* Approximate optimal feedback, §3 Eq. (15), at n arbitrary states
  * (host, n x 4 row-major) with step tau > 0: full tabulation then refinement
- * (when desc.refine) of tau + beta^(tau/dt) I[V](y + tau Phi(y, alpha)).
- * alpha_out (n, rad in [0, 2 pi)) required, q_out (n) nullable. */
+ * (when desc.refine) of tau l(y, alpha) + beta^(tau/dt) I[V](y + tau Phi(y, alpha))
+ * (l = 1, or Eq. (11) for DP_DYN_POLAR, where the thrust-off control is also
+ * compared).  alpha_out (n, rad in [0, 2 pi); NaN = thrust off) required,
+ * q_out (n) nullable. */
 int dp_feedback_control(const dp_grid* grid, const double* states, int32_t n, double tau,
                         double* alpha_out, double* q_out);
 

@@ -129,8 +129,22 @@ int validate(const dp_grid_desc* d)
         box *= d->n[k];
     }
     if (box > 2147483647LL) return fail(DP_EINVAL, "box of %lld nodes exceeds 2^31 - 1", box);
-    if (d->dynamics != DP_DYN_ORBIT && d->dynamics != DP_DYN_UNIT_SPEED)
+    if (d->dynamics != DP_DYN_ORBIT && d->dynamics != DP_DYN_UNIT_SPEED && d->dynamics != DP_DYN_POLAR)
         return fail(DP_EINVAL, "unknown dynamics %d", d->dynamics);
+    if (d->dynamics == DP_DYN_POLAR) {
+        if (d->precision != DP_FP64) return fail(DP_EINVAL, "polar dynamics need DP_FP64");
+        if (d->reduced) return fail(DP_EINVAL, "polar dynamics take full-box grids");
+        if (!(d->mu > 0) || !(d->accel >= 0) || !(d->lo[0] > 0))
+            return fail(DP_EINVAL, "polar dynamics need mu > 0, accel >= 0 and rho > 0 on the box");
+        double r2 = d->lo[0] + d->dt * std::fmin(d->lo[1], 0.0);
+        if (!(r2 > 0)) return fail(DP_EINVAL, "Heun predictor leaves rho > 0");
+        const double period = (d->hi[3] - d->lo[3]) * d->n[3] / (double)(d->n[3] - 1);
+        if (!(std::fabs(period - kTwoPi) <= 1e-9 * kTwoPi))
+            return fail(DP_EINVAL, "the angle axis must cover 2 pi: hi[3] = lo[3] + 2 pi (n[3] - 1) / n[3]");
+        if (!(d->cost_alpha >= 0) || !(d->cost_beta >= 0) || !(d->cost_gamma >= 0) || !(d->a_bar > 0) ||
+            !(d->e_bar >= 0) || !std::isfinite(d->omega_bar))
+            return fail(DP_EINVAL, "cost weights must be >= 0, a_bar > 0, e_bar >= 0");
+    }
     if (!(d->dt > 0) || !std::isfinite(d->dt)) return fail(DP_EINVAL, "dt must be > 0");
     if (!(d->beta > 0 && d->beta < 1)) return fail(DP_EINVAL, "beta must lie in (0, 1)");
     if (d->n_angles < 2 || d->n_angles > kMaxAngles) return fail(DP_EINVAL, "n_angles must lie in [2, 1024]");
@@ -193,6 +207,14 @@ void fill_geo(const dp_grid* gr, Geo<G>& g)
         g.foot_tm = um - fl;
     }
     g.dyn = d.dynamics;
+    const bool polar = d.dynamics == DP_DYN_POLAR;
+    g.off = polar && d.off_control;
+    g.cost_b = polar ? d.cost_beta : 0.0;
+    g.cost_g = polar ? d.cost_gamma : 0.0;
+    g.a_bar = d.a_bar;
+    g.ex_bar = d.e_bar * std::cos(d.omega_bar);
+    g.ey_bar = d.e_bar * std::sin(d.omega_bar);
+    g.thrust_cost = polar ? d.dt * d.cost_alpha * d.accel : 0.0;   // dt alpha |u| of a thrust control
     g.K = d.n_angles;
     g.refine = d.refine;
     double tc = d.refine ? std::floor(d.refine_tol / (kTwoPi / kCodes)) : 0.0;

@@ -27,7 +27,8 @@ constexpr int kMaxFib = 30;
 constexpr int kMaxAngles = 1024;   // tabulated angles per grid (shared-memory table)
 
 enum { kVI = 0, kImproveFull = 1, kImproveWalk = 2, kEval = 3, kEvalFeet = 4, kIncr = 5 };
-enum { kDynOrbit = 0, kDynUnitSpeed = 1 };
+enum { kDynOrbit = 0, kDynUnitSpeed = 1, kDynPolar = 2 };
+constexpr int kCodeOff = 65535;     // policy code of the thrust-off control
 
 // Fibonacci numbers F[1] = F[2] = 1 (index 0 unused).
 __constant__ int kFib[kMaxFib] = {0, 1, 1, 2, 3, 5, 8, 13, 21, 34, 55, 89, 144, 233, 377, 610, 987,
@@ -69,6 +70,11 @@ struct Geo {
     const unsigned* lines;     // per compact (r, v_r, v_t) line: i_r | i_vr<<10 | i_vt<<20
     const typename V2<G>::type* tab_hi;   // (sin, cos) of 2 pi (c >> 8) 256 / 65536
     const typename V2<G>::type* tab_lo;   // (sin, cos) of 2 pi (c & 255) / 65536
+    // polar dynamics (the paper's Example 1): running cost of Eq. (11)
+    int off;                   // thrust off (kCodeOff) is a control
+    double cost_b, cost_g;     // weights of (a - a_bar)^2 and of the eccentricity term
+    double a_bar, ex_bar, ey_bar;
+    double thrust_cost;        // dt alpha |u| of every thrust control
 };
 
 template <typename G> __device__ __forceinline__ G ginf();
@@ -132,6 +138,7 @@ struct NodeDyn {
     G am, am2;       // a/m at x and at the predictor (m' does not depend on alpha)
     G d1vr, d1vt;    // drift of v_r, v_t at x
     G ir2, muir2sq;  // 1/r and mu/r^2 at the predictor (r' = v_r does not depend on alpha)
+    G ir;            // 1/r at x (polar: the angle rate v_t / r)
 };
 
 template <typename G, int DYN>
@@ -140,16 +147,22 @@ __device__ __forceinline__ NodeDyn<G> node_dyn(const Geo<G>& g, const StepP<G>& 
     NodeDyn<G> n;
     n.vr = x[1];
     n.vt = x[2];
-    if (DYN == kDynOrbit) {
+    if (DYN == kDynOrbit || DYN == kDynPolar) {
         G ir = grcp(x[0]);
-        n.am = g.accel * grcp(x[3]);
+        n.ir = ir;
         n.d1vr = n.vt * n.vt * ir - g.mu * ir * ir;
         n.d1vt = -n.vr * n.vt * ir;
         G r2 = x[0] + sp.dt * n.vr;
-        G m2 = x[3] + sp.dt * g.mdot;
         n.ir2 = grcp(r2);
         n.muir2sq = g.mu * n.ir2 * n.ir2;
-        n.am2 = g.accel * grcp(m2);
+        if (DYN == kDynOrbit) {
+            G m2 = x[3] + sp.dt * g.mdot;
+            n.am = g.accel * grcp(x[3]);
+            n.am2 = g.accel * grcp(m2);
+        } else {
+            n.am = g.accel;   // no mass: the thrust acceleration is fixed
+            n.am2 = g.accel;
+        }
     }
     return n;
 }
@@ -160,7 +173,7 @@ template <typename G, int DYN>
 __device__ __forceinline__ void heun_cells(const Geo<G>& g, const StepP<G>& sp, const NodeDyn<G>& n,
                                            G s, G c, G u[4])
 {
-    if (DYN == kDynOrbit) {
+    if (DYN == kDynOrbit || DYN == kDynPolar) {
         G k1vr = n.d1vr + n.am * s;
         G k1vt = n.d1vt + n.am * c;
         G vr2 = n.vr + sp.dt * k1vr;
@@ -170,7 +183,8 @@ __device__ __forceinline__ void heun_cells(const Geo<G>& g, const StepP<G>& sp, 
         u[0] = sp.hdt * (n.vr + vr2) * g.ih[0];
         u[1] = sp.hdt * (k1vr + k2vr) * g.ih[1];
         u[2] = sp.hdt * (k1vt + k2vt) * g.ih[2];
-        u[3] = sp.um;
+        if (DYN == kDynOrbit) u[3] = sp.um;
+        else u[3] = sp.hdt * (n.vt * n.ir + vt2 * n.ir2) * g.ih[3];   // angle: theta' = v_t / r
     } else {
         // test dynamics: unit speed in the (x0, x1) plane, tiny components zeroed
         G cc = fabs(c) < (G)1e-12 ? (G)0 : c;
@@ -200,13 +214,34 @@ __device__ __forceinline__ bool foot_dim(int n, int i, G u, int& c, G& t)
     return out;
 }
 
+// The periodic angle coordinate: the cell index wraps, nothing is outside.
 template <typename G>
+__device__ __forceinline__ bool foot_dim_periodic(int n, int i, G u, int& c, G& t)
+{
+    G fl = floor(u);
+    t = u - fl;
+    int cc = (i + (int)fl) % n;
+    c = cc < 0 ? cc + n : cc;
+    return !(t >= (G)0);
+}
+
+template <typename G, bool PER3 = false>
 __device__ __forceinline__ bool foot_cell(const Geo<G>& g, const int i[4], const G u[4], int c[4], G t[4])
 {
     bool out = false;
 #pragma unroll
-    for (int d = 0; d < 4; ++d) out = foot_dim(g.n[d], i[d], u[d], c[d], t[d]) || out;
+    for (int d = 0; d < 3; ++d) out = foot_dim(g.n[d], i[d], u[d], c[d], t[d]) || out;
+    if (PER3) out = foot_dim_periodic(g.n[3], i[3], u[3], c[3], t[3]) || out;
+    else out = foot_dim(g.n[3], i[3], u[3], c[3], t[3]) || out;
     return out;
+}
+
+// Offset from the lower to the upper corner in the last coordinate (the
+// periodic angle wraps from node n-1 to node 0).
+template <typename G, bool PER3>
+__device__ __forceinline__ int up3(const Geo<G>& g, int c3)
+{
+    return (PER3 && c3 == g.n[3] - 1) ? 1 - g.n[3] : 1;
 }
 
 __device__ __forceinline__ unsigned long long pack2(float lo, float hi)
@@ -317,13 +352,14 @@ __device__ __forceinline__ bool cell_rows(const Geo<G>& g, const int c[4], int b
 // Loads the 16 corners given the index of corner (c_vt, c_m) in each of the
 // four (r, v_r) rows (n_m: stride of v_t).
 template <typename G, typename S>
-__device__ __forceinline__ void load_rows(const S* __restrict__ V, const int base[4], int n_m, S vj, Corners<G>& K)
+__device__ __forceinline__ void load_rows(const S* __restrict__ V, const int base[4], int n_m, S vj, Corners<G>& K,
+                                          int up = 1)
 {
     G a[8], d[8];
 #pragma unroll
     for (int rb = 0; rb < 4; ++rb) {
         const S* p = V + base[rb];
-        S v00 = __ldg(p), v01 = __ldg(p + 1), v10 = __ldg(p + n_m), v11 = __ldg(p + n_m + 1);
+        S v00 = __ldg(p), v01 = __ldg(p + up), v10 = __ldg(p + n_m), v11 = __ldg(p + n_m + up);
         a[2 * rb] = (G)(v00 - vj);
         d[2 * rb] = (G)(v01 - vj) - a[2 * rb];
         a[2 * rb + 1] = (G)(v10 - vj);
@@ -340,13 +376,13 @@ struct BlendType {
     typedef typename std::conditional<std::is_same<S, double>::value, double, G>::type type;
 };
 
-template <typename R, typename G, typename S, bool REDUCED>
+template <typename R, typename G, typename S, bool REDUCED, bool PER3 = false>
 __device__ __forceinline__ bool load_corners(const Geo<G>& g, const S* __restrict__ V, const int c[4], S vj,
                                              Corners<R>& K)
 {
     int base[4];
     if (cell_rows<G, REDUCED>(g, c, base)) return true;
-    load_rows<R, S>(V, base, g.n_m, vj, K);
+    load_rows<R, S>(V, base, g.n_m, vj, K, up3<G, PER3>(g, c[3]));
     return false;
 }
 
@@ -394,7 +430,7 @@ __device__ __forceinline__ FootWord encode_foot(const int i[4], const int c[4], 
 
 // Q1 interpolation at the foot i + u (grid units), returned as the difference
 // D = I[V] - vj; M - vj when the foot is outside the box or the node set.
-template <typename G, typename S, bool REDUCED>
+template <typename G, typename S, bool REDUCED, bool PER3 = false>
 __device__ __forceinline__ typename BlendType<G, S>::type interp_delta(const Geo<G>& g, const S* __restrict__ V,
                                                                        const int i[4], const G u[4], S vj)
 {
@@ -402,7 +438,8 @@ __device__ __forceinline__ typename BlendType<G, S>::type interp_delta(const Geo
     int c[4];
     G t[4];
     Corners<R> K;
-    if (foot_cell(g, i, u, c, t) || load_corners<R, G, S, REDUCED>(g, V, c, vj, K)) return (R)((S)g.M64 - vj);
+    if (foot_cell<G, PER3>(g, i, u, c, t) || load_corners<R, G, S, REDUCED, PER3>(g, V, c, vj, K))
+        return (R)((S)g.M64 - vj);
     const R tr[4] = {(R)t[0], (R)t[1], (R)t[2], (R)t[3]};
     return K.blend(tr);
 }
@@ -426,7 +463,7 @@ struct NodeEval {
         heun_cells<G, DYN>(*g, sp, nd, s, c, u);
 #pragma unroll
         for (int d = 0; d < 4; ++d) u[d] += u0[d];
-        return interp_delta<G, S, REDUCED>(*g, V, i, u, vj);
+        return interp_delta<G, S, REDUCED, DYN == kDynPolar>(*g, V, i, u, vj);
     }
 
     __device__ __forceinline__ R at_code(int code)
@@ -470,7 +507,8 @@ struct CachedEval {
     {
         cc[0] = -1;
         pen = (R)((S)g->M64 - vj);
-        outm = foot_dim(g->n[3], i[3], OFF ? sp.um + u0[3] : sp.um, cm, tm);
+        if (DYN != kDynPolar) outm = foot_dim(g->n[3], i[3], OFF ? sp.um + u0[3] : sp.um, cm, tm);
+        else outm = false;
     }
 
     __device__ __forceinline__ R at_code(int code)
@@ -492,13 +530,20 @@ struct CachedEval {
         bool out = outm;
 #pragma unroll
         for (int d = 0; d < 3; ++d) out = foot_dim(g->n[d], i[d], u[d], cl[d], t[d]) || out;
+        if (DYN == kDynPolar) {
+            // the angle moves with the control: its cell is found every time
+            out = foot_dim_periodic(g->n[3], i[3], OFF ? u[3] + u0[3] : u[3], cl[3], t[3]) || out;
+        }
         if (out) return pen;
-        cl[3] = cm;
-        t[3] = tm;
-        if (cl[0] != cc[0] || cl[1] != cc[1] || cl[2] != cc[2]) {
-            cout = load_corners<R, G, S, REDUCED>(*g, V, cl, vj, K);
+        if (DYN != kDynPolar) {
+            cl[3] = cm;
+            t[3] = tm;
+        }
+        if (cl[0] != cc[0] || cl[1] != cc[1] || cl[2] != cc[2] || (DYN == kDynPolar && cl[3] != cm)) {
+            cout = load_corners<R, G, S, REDUCED, DYN == kDynPolar>(*g, V, cl, vj, K);
 #pragma unroll
             for (int d = 0; d < 3; ++d) cc[d] = cl[d];
+            if (DYN == kDynPolar) cm = cl[3];
         }
         if (cout) return pen;
         const R tr[4] = {(R)t[0], (R)t[1], (R)t[2], (R)t[3]};
@@ -529,6 +574,7 @@ struct Table {
     const int* code;
     const typename V2<G>::type* sc;
     int K;
+    int off = 0;     // the lattice code kCodeOff stands for thrust off
 };
 
 template <typename G>
@@ -623,8 +669,8 @@ __device__ __forceinline__ int fibonacci_refine(E& ev, const Table<G>& T, int n0
     R qb = Dk;
     int a = lo_off;
     int x1 = a + kFib[n - 2], x2 = a + kFib[n - 1];
-    R f1 = (x1 >= hi_off) ? ginf<R>() : ev.at_code(ck + x1);
-    R f2 = (x2 >= hi_off) ? ginf<R>() : ev.at_code(ck + x2);
+    R f1 = (x1 >= hi_off || (T.off && wrap_code(ck + x1) == kCodeOff)) ? ginf<R>() : ev.at_code(ck + x1);
+    R f2 = (x2 >= hi_off || (T.off && wrap_code(ck + x2) == kCodeOff)) ? ginf<R>() : ev.at_code(ck + x2);
     if (f1 < qb) { qb = f1; best = ck + x1; }
     if (f2 < qb) { qb = f2; best = ck + x2; }
     for (int kk = n; kk > 4 && kFib[kk] > fib_stop; --kk) {
@@ -642,7 +688,8 @@ __device__ __forceinline__ int fibonacci_refine(E& ev, const Table<G>& T, int n0
             x2 = a + kFib[kk - 2];
             xn = x2;
         }
-        const R fn = (xn >= hi_off) ? ginf<R>() : ev.at_code(ck + xn);
+        const bool skip = xn >= hi_off || (T.off && wrap_code(ck + xn) == kCodeOff);
+        const R fn = skip ? ginf<R>() : ev.at_code(ck + xn);
         if (left) f1 = fn;
         else f2 = fn;
         if (fn < qb) { qb = fn; best = ck + xn; }

@@ -9,6 +9,7 @@
 // classical RK4 step of the dynamics (FP64 state) and repeats until the state
 // enters the target or the step budget ends.
 #include "dp_host.h"
+#include "dp_sweep.cuh"
 
 namespace dpk {
 
@@ -22,6 +23,12 @@ __device__ __forceinline__ void dyn64(const double y[4], double s, double c, dou
         f[1] = y[2] * y[2] / y[0] - mu / (y[0] * y[0]) + am * s;
         f[2] = -y[1] * y[2] / y[0] + am * c;
         f[3] = mdot;
+    } else if (DYN == kDynPolar) {
+        // thrust off: s = c = 0
+        f[0] = y[1];
+        f[1] = y[2] * y[2] / y[0] - mu / (y[0] * y[0]) + accel * s;
+        f[2] = -y[1] * y[2] / y[0] + accel * c;
+        f[3] = y[2] / y[0];
     } else {
         f[0] = fabs(c) < 1e-12 ? 0.0 : c;
         f[1] = fabs(s) < 1e-12 ? 0.0 : s;
@@ -44,7 +51,7 @@ loop_kernel(const __grid_constant__ Geo<G> g, const __grid_constant__ LoopLaunch
     __shared__ typename V2<G>::type s_sc[kMaxAngles];
     build_table(g, s_code, s_sc);
     __syncthreads();
-    const Table<G> T{s_code, s_sc, g.K};
+    const Table<G> T{s_code, s_sc, g.K, g.off};
 
     const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -66,10 +73,17 @@ loop_kernel(const __grid_constant__ Geo<G> g, const __grid_constant__ LoopLaunch
     for (long long step = 0; step < steps; ++step) {
         // --- feedback at y (Eq. (15)) ---
         G x[4];
+        double yw[4];
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
-            x[d] = (G)y[d];
-            double sd = (y[d] - (double)g.lo[d]) / (double)g.h[d];
+            yw[d] = y[d];
+            if (DYN == kDynPolar && d == 3) {
+                // the orbital angle keeps growing along a trajectory: wrap it
+                const double per = (double)g.h[3] * g.n[3], lo3 = (double)g.lo[3];
+                yw[d] = lo3 + (y[d] - lo3) - per * floor((y[d] - lo3) / per);
+            }
+            x[d] = (G)yw[d];
+            double sd = (yw[d] - (double)g.lo[d]) / (double)g.h[d];
             double fl = floor(sd);
             fl = fmin(fmax(fl, -4.0), (double)g.n[d] + 4.0);   // keep the index finite
             ev.i[d] = (int)fl;
@@ -97,15 +111,33 @@ loop_kernel(const __grid_constant__ Geo<G> g, const __grid_constant__ LoopLaunch
         }
         int code = T.code[kb] & (kCodes - 1);
         if (g.refine) code = fibonacci_refine(ev, T, g.fib_n0, g.fib_stop, kb, Db, Db);
+        // running cost over tau (polar: Eq. (11); otherwise minimum time) and
+        // the thrust-off control, which wins a tie
+        double cost = a.tau, q = 0.0;
+        if (DYN == kDynPolar) {
+            const double lx = a.tau * state_cost_x(g, yw);
+            cost = lx + a.tau * (g.thrust_cost / g.dt64);
+            q = cost + a.beta_tau * ((double)ev.vj + (double)Db);
+            if (g.off) {
+                const double q_off = lx + a.beta_tau * ((double)ev.vj + (double)ev.at_sc((G)0, (G)0));
+                if (q_off <= q) {
+                    q = q_off;
+                    code = kCodeOff;
+                }
+            }
+        } else {
+            q = cost + a.beta_tau * ((double)ev.vj + (double)Db);
+        }
+        const bool off = g.off && code == kCodeOff;
 
         double2 hi = a.tab_hi64[code >> 8], lo = a.tab_lo64[code & 255];
-        double s = hi.x * lo.y + hi.y * lo.x;
-        double c = hi.y * lo.y - hi.x * lo.x;
+        double s = off ? 0.0 : hi.x * lo.y + hi.y * lo.x;
+        double c = off ? 0.0 : hi.y * lo.y - hi.x * lo.x;
 
         if (a.steps == 0) {
             if (lane == 0) {
-                a.alpha[w] = 6.283185307179586476925286766559 * (double)code / (double)kCodes;
-                if (a.q) a.q[w] = a.tau + a.beta_tau * ((double)ev.vj + (double)Db);
+                a.alpha[w] = off ? CUDART_NAN : 6.283185307179586476925286766559 * (double)code / (double)kCodes;
+                if (a.q) a.q[w] = q;
             }
             return;
         }
@@ -146,6 +178,9 @@ static cudaError_t launch_loop_t(const LoopLaunch<G, S>& L)
     if (L.dyn == kDynUnitSpeed) {
         if (L.reduced) return cudaErrorInvalidValue;
         loop_kernel<G, S, false, kDynUnitSpeed><<<(unsigned)blocks, threads, 0, L.stream>>>(L.g, L);
+    } else if (L.dyn == kDynPolar) {
+        if (L.reduced || !std::is_same<G, double>::value) return cudaErrorInvalidValue;
+        loop_kernel<G, S, false, kDynPolar><<<(unsigned)blocks, threads, 0, L.stream>>>(L.g, L);
     } else if (L.reduced) {
         loop_kernel<G, S, true, kDynOrbit><<<(unsigned)blocks, threads, 0, L.stream>>>(L.g, L);
     } else {

@@ -52,6 +52,31 @@ __device__ __forceinline__ double bellman_value(const Geo<float>& g, double vj, 
     return g.dt64 + g.beta64 * (vj + D);
 }
 
+// State part of the running cost of Eq. (11) (polar dynamics, FP64):
+// beta (a - a_bar)^2 + gamma |(e cos w, e sin w) - target|^2, with a from the
+// vis-viva relation and (e cos w, e sin w) from the eccentricity vector, whose
+// radial and transverse components are r v_t^2 / mu - 1 and -r v_r v_t / mu.
+template <typename G>
+__device__ __forceinline__ double state_cost_x(const Geo<G>& g, const double x[4])
+{
+    const double r = x[0], vr = x[1], vt = x[2], mu = (double)g.mu;
+    double sn, cs;
+    sincos(x[3], &sn, &cs);
+    const double a = mu * r / (2.0 * mu - r * (vr * vr + vt * vt));
+    const double er = r * vt * vt / mu - 1.0, et = -r * vr * vt / mu;
+    const double dx = er * cs - et * sn - g.ex_bar, dy = er * sn + et * cs - g.ey_bar, da = a - g.a_bar;
+    return g.cost_b * da * da + g.cost_g * (dx * dx + dy * dy);
+}
+
+template <typename G>
+__device__ __forceinline__ double state_cost(const Geo<G>& g, const int i[4])
+{
+    double x[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) x[d] = (double)(g.lo[d] + (G)i[d] * g.h[d]);
+    return state_cost_x(g, x);
+}
+
 template <typename S>
 __device__ __forceinline__ S warp_max(S v)
 {
@@ -216,7 +241,42 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
             (void)vnew64;
             Eval ev;
             decode_node(g, j, ev.i);
-            if (!in_target(g, ev.i)) {
+            if constexpr (DYN == kDynPolar) {
+                // the paper's Example 1: running cost of Eq. (11) and the
+                // thrust-off control, which wins a tie (FP64 grids only)
+                if (!in_target(g, ev.i)) {
+                    setup_node<G, S, DYN>(ev, g, Vin, vj);
+                    const double lrun = g.dt64 * state_cost(g, ev.i);
+                    double q;
+                    if constexpr (MODE == kEval) {
+                        const int c0 = code[j];
+                        if (g.off && c0 == kCodeOff) q = lrun + g.beta64 * ((double)vj + (double)ev.at_sc((G)0, (G)0));
+                        else q = lrun + g.thrust_cost + g.beta64 * ((double)vj + (double)ev.at_code(c0));
+                    } else {
+                        ev.reset();
+                        typename Eval::R D;
+                        int k;
+                        const int c_old = MODE == kImproveWalk ? (int)code[j] : 0;
+                        // a node whose previous control was off has no angle to walk from
+                        if (MODE == kImproveWalk && !(g.off && c_old == kCodeOff))
+                            k = walk_table(ev, T, nearest_index(g.K, c_old), D);
+                        else
+                            k = enumerate_table(ev, T, D);
+                        int c = T.code[k] & (kCodes - 1);
+                        if (MODE != kVI && g.refine) c = fibonacci_refine(ev, T, g.fib_n0, g.fib_stop, k, D, D);
+                        q = lrun + g.thrust_cost + g.beta64 * ((double)vj + (double)D);
+                        if (g.off) {
+                            const double q_off = lrun + g.beta64 * ((double)vj + (double)ev.at_sc((G)0, (G)0));
+                            if (q_off <= q) {
+                                q = q_off;
+                                c = kCodeOff;
+                            }
+                        }
+                        if (MODE != kVI) code[j] = (uint16_t)c;
+                    }
+                    vnew = (S)q;
+                }
+            } else if (!in_target(g, ev.i)) {
                 setup_node<G, S, DYN>(ev, g, Vin, vj);
                 typename Eval::R D;
                 if constexpr (MODE == kEval) {
@@ -338,7 +398,7 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
         build_table(g, s_code, s_sc);
         __syncthreads();
     }
-    const Table<G> T{s_code, s_sc, g.K};
+    const Table<G> T{s_code, s_sc, g.K, g.off};
 
     S resid = (S)0;
     bool bad = false;

@@ -5,6 +5,7 @@ namespace dpk {
 
 cudaError_t launch_sweep(const SweepLaunch<float, float>& L)
 {
+    if (L.dyn == kDynPolar) return cudaErrorInvalidValue;   // polar grids are FP64
     if (L.dyn == kDynUnitSpeed) {
         if (L.reduced) return cudaErrorInvalidValue;
         return launch_mode<float, float, kDynUnitSpeed, false>(L);

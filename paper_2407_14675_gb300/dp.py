@@ -18,7 +18,8 @@ from . import workloads as W
 
 DP_OK, DP_EINVAL, DP_ENOMEM, DP_ECUDA, DP_ENOCONV, DP_ETIMEOUT, DP_ENONFINITE = range(7)
 DP_FP64, DP_FP32 = 0, 1
-DP_DYN_ORBIT, DP_DYN_UNIT_SPEED = 0, 1
+DP_DYN_ORBIT, DP_DYN_UNIT_SPEED, DP_DYN_POLAR = 0, 1, 2
+DP_CODE_OFF = 65535
 DP_SWEEP_VI, DP_SWEEP_IMPROVE_FULL, DP_SWEEP_IMPROVE_WALK, DP_SWEEP_EVAL = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -47,6 +48,13 @@ class dp_grid_desc(C.Structure):
         ("energy_hi", C.c_double),
         ("precision", C.c_int32),
         ("stream", C.c_void_p),
+        ("off_control", C.c_int32),
+        ("cost_alpha", C.c_double),
+        ("cost_beta", C.c_double),
+        ("cost_gamma", C.c_double),
+        ("a_bar", C.c_double),
+        ("e_bar", C.c_double),
+        ("omega_bar", C.c_double),
     ]
 
 
@@ -256,6 +264,9 @@ def desc_from_problem(p: "W.Problem", stream: Optional[int] = None) -> dp_grid_d
     d.reduced, d.energy_lo, d.energy_hi = p.reduced, p.energy_lo, p.energy_hi
     d.precision = p.precision
     d.stream = current_stream() if stream is None else stream
+    d.off_control = getattr(p, "off_control", 0)
+    d.cost_alpha, d.cost_beta, d.cost_gamma = p.cost_alpha, p.cost_beta, p.cost_gamma
+    d.a_bar, d.e_bar, d.omega_bar = p.a_bar, p.e_bar, p.omega_bar
     return d
 
 

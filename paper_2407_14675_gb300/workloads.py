@@ -112,20 +112,19 @@ def example1(n=(110, 30, 30, 30), accel: float = 5e-7) -> Problem:
     dt = 10 s; rho in [6930, 7070] km, v_rho in [-0.01, 0.01] km/s, v_theta in
     [7.526, 7.566] km/s, theta in [0, 2 pi) periodic; 72 angles + thrust off.
     State order (rho, v_rho, v_theta, theta); n gives the nodes in that order
-    (the paper's 110 x 30 x 30 x 30).  No target set (V > 0 everywhere); M is
-    twice the cost of the worst box node held forever."""
+    (the paper's 110 x 30 x 30 x 30).  No target set (V > 0 everywhere)."""
     nt = n[3]
     dt, lam = 10.0, 1e-3
     beta = math.exp(-lam * dt)
     lo = (6930.0, -0.01, 7.526, 0.0)
     hi = (7070.0, 0.01, 7.566, 2.0 * math.pi * (nt - 1) / nt)
     a_bar, e_bar = 7000.0, 0.001
-    # worst cost on the box: |a - a_bar| at the vis-viva extremes
-    def a_of(r, v):
-        return MU_EARTH * r / (2.0 * MU_EARTH - r * v * v)
-    vmax = math.hypot(0.01, 7.566)
-    worst = max(abs(a_of(r, v) - a_bar) for r in (6930.0, 7070.0) for v in (7.526, vmax))
-    M = 2.0 * dt * (2.31e-2 * worst ** 2 + 1.5 * 0.25) / (1.0 - beta)
+    # M: the discounted cost of staying forever on the worst circular orbit of
+    # the box (rho at a bound, e = 0).  Larger values (the worst box corner,
+    # a - a_bar ~ 180 km) spread the penalty of the velocity bounds into the
+    # interior through the interpolation and stall the closed loop.
+    worst = max(abs(lo[0] - a_bar), abs(hi[0] - a_bar))
+    M = dt * (2.31e-2 * worst ** 2 + 1.5 * e_bar ** 2) / (1.0 - beta)
     return Problem(n=tuple(n), lo=lo, hi=hi, dynamics=DYN_POLAR, mu=MU_EARTH, accel=accel, exhaust_c=1.0,
                    dt=dt, beta=beta, penalty_M=M, target_c=(-1.0, 0.0, 0.0, 0.0), target_w=(1e-9, 0.0, 0.0, 0.0),
                    n_angles=72, refine=1, refine_tol=1e-4, precision=FP64, tol=1e-7, n_eval=20,
