@@ -88,6 +88,9 @@ def lib():
             "orc_feedback": (None, [P, _dp, _u8, _dp, C.c_long, C.c_double, _u16, _dp]),
             "orc_simulate": (None, [P, _dp, _u8, _dp, C.c_long, C.c_double, C.c_double, C.c_double,
                                     _dp, _dp]),
+            "orc_simulate_drag": (None, [P, _dp, _u8, _dp, C.c_long, C.c_double, C.c_double, C.c_double,
+                                         C.c_double, _dp, _dp]),
+            "orc_dynamics_drag": (None, [P, _dp, C.c_double, C.c_double, _dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -260,7 +263,7 @@ class Oracle:
                            _ptr(codes, _u16), _ptr(q, _dp))
         return codes, q
 
-    def simulate(self, V, x0, tau=None, h=None, t_max=200.0):
+    def simulate(self, V, x0, tau=None, h=None, t_max=200.0, drag=0.0):
         V = np.ascontiguousarray(V, np.float64)
         x0 = np.ascontiguousarray(x0, np.float64).reshape(-1, 4)
         n = len(x0)
@@ -268,9 +271,15 @@ class Oracle:
         h = tau if h is None else h
         ta = np.zeros(n)
         xf = np.zeros((n, 4))
-        lib().orc_simulate(C.byref(self.s), _ptr(V, _dp), _ptr(self.active, _u8), _ptr(x0, _dp), n, tau, h, t_max,
-                           _ptr(ta, _dp), _ptr(xf, _dp))
+        lib().orc_simulate_drag(C.byref(self.s), _ptr(V, _dp), _ptr(self.active, _u8), _ptr(x0, _dp), n, tau, h,
+                                t_max, drag, _ptr(ta, _dp), _ptr(xf, _dp))
         return ta, xf
+
+    def dynamics_drag(self, x, alpha, drag):
+        x = np.ascontiguousarray(x, np.float64)
+        f = np.zeros(4)
+        lib().orc_dynamics_drag(C.byref(self.s), _ptr(x, _dp), alpha, drag, _ptr(f, _dp))
+        return f
 
 
 def code_angle(code):

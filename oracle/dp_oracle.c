@@ -34,7 +34,10 @@
  *     theta kept as a periodic coordinate and no mass, the running cost of
  *     Eq. (11) in polar form (semi-major axis by the vis-viva relation, the
  *     eccentricity components e cos(omega), e sin(omega) from the
- *     eccentricity vector), and a thrust-off control besides the angles.
+ *     eccentricity vector), and a thrust-off control besides the angles;
+ *   - Example 2 (§4): the closed loop of the same feedback on a "real"
+ *     system with aerodynamic drag, whose components are printed as
+ *     -C v_rho^2 and -C v_theta^2 with C = C_D S rho_D / (2 m).
  *
  * Parity unpinned: the paper prints no value function, policy or trajectory
  * value (its figures are not available); the pins of this oracle are closed
@@ -224,18 +227,37 @@ void orc_heun_displacement(const orc_problem* p, const double x[4], double alpha
     for (int d = 0; d < 4; ++d) delta[d] = 0.5 * h * (k1[d] + k2[d]);
 }
 
+/* The "real" system of Example 2: the model plus aerodynamic drag with the
+ * printed components -C v_rho^2 (radial) and -C v_theta^2 (transverse);
+ * polar dynamics only (drag_c = 0 gives the model). */
+void orc_dynamics_drag(const orc_problem* p, const double x[4], double alpha, double drag_c, double f[4])
+{
+    orc_dynamics(p, x, alpha, f);
+    if (p->dynamics == ORC_DYN_POLAR && drag_c != 0.0) {
+        f[1] -= drag_c * x[1] * x[1];
+        f[2] -= drag_c * x[2] * x[2];
+    }
+}
+
+/* Classical fourth-order Runge-Kutta step of the true dynamics (with drag). */
+static void rk4_step_drag(const orc_problem* p, const double x[4], double alpha, double h, double drag_c,
+                          double out[4])
+{
+    double k1[4], k2[4], k3[4], k4[4], y[4];
+    orc_dynamics_drag(p, x, alpha, drag_c, k1);
+    for (int d = 0; d < 4; ++d) y[d] = x[d] + 0.5 * h * k1[d];
+    orc_dynamics_drag(p, y, alpha, drag_c, k2);
+    for (int d = 0; d < 4; ++d) y[d] = x[d] + 0.5 * h * k2[d];
+    orc_dynamics_drag(p, y, alpha, drag_c, k3);
+    for (int d = 0; d < 4; ++d) y[d] = x[d] + h * k3[d];
+    orc_dynamics_drag(p, y, alpha, drag_c, k4);
+    for (int d = 0; d < 4; ++d) out[d] = x[d] + h / 6.0 * (k1[d] + 2.0 * k2[d] + 2.0 * k3[d] + k4[d]);
+}
+
 /* Classical fourth-order Runge-Kutta step of the true dynamics. */
 void orc_rk4_step(const orc_problem* p, const double x[4], double alpha, double h, double out[4])
 {
-    double k1[4], k2[4], k3[4], k4[4], y[4];
-    orc_dynamics(p, x, alpha, k1);
-    for (int d = 0; d < 4; ++d) y[d] = x[d] + 0.5 * h * k1[d];
-    orc_dynamics(p, y, alpha, k2);
-    for (int d = 0; d < 4; ++d) y[d] = x[d] + 0.5 * h * k2[d];
-    orc_dynamics(p, y, alpha, k3);
-    for (int d = 0; d < 4; ++d) y[d] = x[d] + h * k3[d];
-    orc_dynamics(p, y, alpha, k4);
-    for (int d = 0; d < 4; ++d) out[d] = x[d] + h / 6.0 * (k1[d] + 2.0 * k2[d] + 2.0 * k3[d] + k4[d]);
+    rk4_step_drag(p, x, alpha, h, 0.0, out);
 }
 
 /* --------------------------------------------------------- interpolation -- */
@@ -614,9 +636,21 @@ void orc_feedback(const orc_problem* p, const double* V, const unsigned char* ac
  * the step) and the true dynamics advance by one RK4 step.  Arrival is the
  * end of the first step inside the target; t_arrive = -1 if none before
  * t_max. */
+void orc_simulate_drag(const orc_problem* p, const double* V, const unsigned char* active,
+                       const double* x0, long n, double tau, double h, double t_max, double drag_c,
+                       double* t_arrive, double* x_final);
+
 void orc_simulate(const orc_problem* p, const double* V, const unsigned char* active,
                   const double* x0, long n, double tau, double h, double t_max,
                   double* t_arrive, double* x_final)
+{
+    orc_simulate_drag(p, V, active, x0, n, tau, h, t_max, 0.0, t_arrive, x_final);
+}
+
+/* The same closed loop on the "real" system with drag (Example 2). */
+void orc_simulate_drag(const orc_problem* p, const double* V, const unsigned char* active,
+                       const double* x0, long n, double tau, double h, double t_max, double drag_c,
+                       double* t_arrive, double* x_final)
 {
     long steps = (long)ceil(t_max / h - 1e-9);
     for (long i = 0; i < n; ++i) {
@@ -626,7 +660,7 @@ void orc_simulate(const orc_problem* p, const double* V, const unsigned char* ac
         for (long s = 0; s < steps; ++s) {
             uint16_t code;
             orc_feedback(p, V, active, y, 1, tau, &code, NULL);
-            orc_rk4_step(p, y, code_control(p, code), h, z);
+            rk4_step_drag(p, y, code_control(p, code), h, drag_c, z);
             memcpy(y, z, sizeof y);
             if (orc_in_target(p, y)) { t_arrive[i] = (s + 1) * h; break; }
         }

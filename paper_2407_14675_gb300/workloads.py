@@ -132,6 +132,14 @@ def example1(n=(110, 30, 30, 30), accel: float = 5e-7) -> Problem:
                    a_bar=a_bar, e_bar=e_bar, omega_bar=0.0)
 
 
+def example2_drag(cd: float = 2.2, area_m2: float = 2.25, mass_kg: float = 350.0,
+                  density_kg_m3: float = 8.09e-14) -> float:
+    """Drag coefficient C of the paper's Example 2 (§4), C = C_D S rho_D / (2 m),
+    in 1/km so that -C v^2 is in km/s^2 with v in km/s."""
+    c_per_m = cd * area_m2 * density_kg_m3 / (2.0 * mass_kg)
+    return c_per_m * 1000.0
+
+
 def example1_start(r0: float = 6978.0) -> np.ndarray:
     """Circular orbit of radius r0 km at theta = 0 (the paper's start)."""
     return np.array([r0, 0.0, math.sqrt(MU_EARTH / r0), 0.0])

@@ -500,3 +500,22 @@ def test_example1_thrust_off_wins_where_thrust_only_costs():
     for j in np.flatnonzero(interior)[:5]:
         x = np.array(p.lo) + idx[j] * (np.array(p.hi) - np.array(p.lo)) / (np.array(p.n) - 1)
         assert Vn[j] == pytest.approx(p.dt * o.running_cost(x, False) + p.beta * 5.0, rel=1e-14)
+
+
+def test_example2_drag_coefficient_and_deceleration():
+    # C = C_D S rho_D / (2 m) with the paper's constants, in 1/km
+    C = W.example2_drag()
+    assert C == pytest.approx(2.2 * 2.25 * 8.09e-14 / 700.0 * 1000.0, rel=1e-15)
+    assert C == pytest.approx(5.721e-13, rel=1e-3)
+    p = W.example1(n=(5, 3, 3, 4))
+    o = oracle.Oracle(p)
+    y = np.array([6990.0, 0.004, 7.55, 1.1])
+    f0 = o.dynamics(y, oracle.OFF)
+    f = o.dynamics_drag(y, oracle.OFF, C)
+    # the printed components: -C v_rho^2 and -C v_theta^2; the energy then
+    # falls at C (v_rho^3 + v_theta^3)
+    assert f[1] - f0[1] == pytest.approx(-C * y[1] ** 2, rel=1e-6)
+    assert f[2] - f0[2] == pytest.approx(-C * y[2] ** 2, rel=1e-6)
+    dE = y[1] * (f[1] - f0[1]) + y[2] * (f[2] - f0[2])
+    assert dE == pytest.approx(-C * (y[1] ** 3 + y[2] ** 3), rel=1e-6)
+    assert (o.dynamics_drag(y, 0.3, 0.0) == o.dynamics(y, 0.3)).all()
