@@ -287,7 +287,8 @@ def example1_leg(args, dp, W, torch):
     of Eq. (11), 72 angles + thrust off, FP64 policy iteration to 1e-7; then
     the closed loop from the circular orbit at 6978 km for 1e6 s, sampled
     every 2,000 s: when the semi-major axis comes within 1 km of 7000 km,
-    when the thrust switches off for good, and the final orbit."""
+    when the thrust switches off for good, and the final orbit; and the same
+    on the system with drag of Example 2."""
     p = W.example1()
     out = {"grid": list(p.n), "nodes": p.nodes, "dt_s": p.dt, "tol": p.tol}
     st = int(torch.cuda.current_stream().cuda_stream)
@@ -300,26 +301,30 @@ def example1_leg(args, dp, W, torch):
         out["solve"] = {"seconds": secs, "converged": bool(s.converged), "residual": s.residual,
                         "improvements": s.sweeps_improve, "evaluations": s.sweeps_eval,
                         "node_updates_per_s": s.node_updates / secs}
-        y = W.example1_start(6978.0)[None, :]
-        chunk, horizon = 2000.0, 1.0e6
-        t, t_near, t_last_on = 0.0, None, None
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        while t < horizon:
-            alpha, _ = g.feedback(y, p.dt)
-            if not np.isnan(alpha[0]):
-                t_last_on = t
-            ta, y = g.simulate(y, p.dt, p.dt, chunk)
-            t += chunk
+        for name, drag in (("closed_loop", 0.0), ("closed_loop_with_drag", W.example2_drag())):
+            # Example 2 of §4: the same feedback flown on a system with drag
+            y = W.example1_start(6978.0)[None, :]
+            chunk, horizon = 2000.0, 1.0e6
+            t, t_near, t_last_on, worst_after = 0.0, None, None, 0.0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            while t < horizon:
+                alpha, _ = g.feedback(y, p.dt)
+                if not np.isnan(alpha[0]):
+                    t_last_on = t
+                ta, y = g.simulate(y, p.dt, p.dt, chunk, drag=drag)
+                t += chunk
+                a, e = _kepler_a_e(y[0], p.mu)
+                if t_near is None and abs(a - p.a_bar) < 1.0:
+                    t_near = t
+                if t_near is not None:
+                    worst_after = max(worst_after, abs(a - p.a_bar))
             a, e = _kepler_a_e(y[0], p.mu)
-            if t_near is None and abs(a - p.a_bar) < 1.0:
-                t_near = t
-        a, e = _kepler_a_e(y[0], p.mu)
-        out["closed_loop"] = {"seconds": time.perf_counter() - t0, "horizon_s": horizon,
-                              "time_a_within_1km_s": t_near, "last_thrust_on_s": t_last_on,
-                              "final_a_err_km": a - p.a_bar, "final_e": e,
-                              "paper": "target neighbourhood after ~1e5 s, thrust off after ~5e5 s, "
-                                       "radius error ~1e-2 km (CPU Matlab: ~18 min for the value function)"}
+            out[name] = {"seconds": time.perf_counter() - t0, "horizon_s": horizon, "drag_c_per_km": drag,
+                         "time_a_within_1km_s": t_near, "last_thrust_on_s": t_last_on,
+                         "max_a_err_after_km": worst_after, "final_a_err_km": a - p.a_bar, "final_e": e}
+        out["paper"] = ("target neighbourhood after ~1e5 s, thrust off after ~5e5 s, radius error ~1e-2 km; "
+                        "with drag, later adjustment manoeuvres (CPU Matlab: ~18 min for the value function)")
     return out
 
 

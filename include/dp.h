@@ -220,6 +220,13 @@ int dp_feedback_control(const dp_grid* grid, const double* states, int32_t n, do
  * h_rk4 and held over one classical RK4 step of the dynamics, until the state
  * enters the target (t_arrive = end of that step) or t_max (t_arrive = -1).
  * x0 and x_final are n x 4 row-major host arrays. */
+/* The same closed loop on a perturbed "real" system (§4 Example 2): the
+ * feedback comes from the grid's model, while the RK4 steps add aerodynamic
+ * drag with the printed components -drag_c v_rho^2 and -drag_c v_theta^2
+ * (drag_c = C_D S rho_D / (2 m) in 1/length unit; DP_DYN_POLAR grids only;
+ * drag_c = 0 is dp_simulate_closed_loop). */
+int dp_simulate_closed_loop_drag(const dp_grid* grid, const double* x0, int32_t n, double tau, double h_rk4,
+                                 double t_max, double drag_c, double* t_arrive, double* x_final);
 int dp_simulate_closed_loop(const dp_grid* grid, const double* x0, int32_t n, double tau,
                             double h_rk4, double t_max, double* t_arrive, double* x_final);
 

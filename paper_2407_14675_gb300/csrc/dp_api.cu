@@ -462,9 +462,10 @@ namespace {
 
 template <typename G, typename S>
 int run_loop(dp_grid* g, const Geo<G>& geo, const S* V, const double* x0, int n, double tau, double h,
-                    long long steps, double* alpha, double* q, double* t_arrive, double* x_final)
+                    long long steps, double drag, double* alpha, double* q, double* t_arrive, double* x_final)
 {
     LoopLaunch<G, S> L;
+    L.drag = drag;
     L.g = geo;
     L.V = V;
     L.x0 = x0;
@@ -494,7 +495,7 @@ int run_loop(dp_grid* g, const Geo<G>& geo, const S* V, const double* x0, int n,
     return DP_OK;
 }
 
-int loop_common(const dp_grid* cg, const double* states, int n, double tau, double h, double t_max,
+int loop_common(const dp_grid* cg, const double* states, int n, double tau, double h, double t_max, double drag,
                        double* alpha_out, double* q_out, double* t_arrive, double* x_final)
 {
     dp_grid* g = const_cast<dp_grid*>(cg);
@@ -516,15 +517,16 @@ int loop_common(const dp_grid* cg, const double* states, int n, double tau, doub
     if (e == cudaSuccess) {
         switch (store_of(g)) {
         case kStoreF64:
-            rc = run_loop<double, double>(g, g->g64, (const double*)g->V[g->cur], d_x0, n, tau, h, steps, d_a, d_q,
-                                          d_a, d_xf);
+            rc = run_loop<double, double>(g, g->g64, (const double*)g->V[g->cur], d_x0, n, tau, h, steps, drag,
+                                          d_a, d_q, d_a, d_xf);
             break;
         case kStoreF32:
-            rc = run_loop<float, float>(g, g->g32, (const float*)g->V[g->cur], d_x0, n, tau, h, steps, d_a, d_q, d_a,
-                                        d_xf);
+            rc = run_loop<float, float>(g, g->g32, (const float*)g->V[g->cur], d_x0, n, tau, h, steps, drag, d_a,
+                                        d_q, d_a, d_xf);
             break;
         default:
-            rc = run_loop<float, double>(g, g->g32, g->V64[g->cur64], d_x0, n, tau, h, steps, d_a, d_q, d_a, d_xf);
+            rc = run_loop<float, double>(g, g->g32, g->V64[g->cur64], d_x0, n, tau, h, steps, drag, d_a, d_q, d_a,
+                                         d_xf);
         }
         if (rc == DP_OK) {
             if (t_arrive) {
@@ -1089,7 +1091,7 @@ int dp_feedback_control(const dp_grid* g, const double* states, int32_t n, doubl
     if (!g || (n > 0 && (!states || !alpha_out))) return fail(DP_EINVAL, "NULL argument");
     if (n < 0 || !(tau > 0) || !std::isfinite(tau)) return fail(DP_EINVAL, "bad n or tau");
     if (n == 0) return DP_OK;
-    return loop_common(g, states, n, tau, tau, 0.0, alpha_out, q_out, nullptr, nullptr);
+    return loop_common(g, states, n, tau, tau, 0.0, 0.0, alpha_out, q_out, nullptr, nullptr);
 }
 
 int dp_simulate_closed_loop(const dp_grid* g, const double* x0, int32_t n, double tau, double h_rk4, double t_max,
@@ -1099,7 +1101,19 @@ int dp_simulate_closed_loop(const dp_grid* g, const double* x0, int32_t n, doubl
     if (n < 0 || !(tau > 0) || !(h_rk4 > 0) || !(t_max > 0) || !std::isfinite(t_max))
         return fail(DP_EINVAL, "bad n, tau, h_rk4 or t_max");
     if (n == 0) return DP_OK;
-    return loop_common(g, x0, n, tau, h_rk4, t_max, nullptr, nullptr, t_arrive, x_final);
+    return loop_common(g, x0, n, tau, h_rk4, t_max, 0.0, nullptr, nullptr, t_arrive, x_final);
+}
+
+int dp_simulate_closed_loop_drag(const dp_grid* g, const double* x0, int32_t n, double tau, double h_rk4,
+                                 double t_max, double drag_c, double* t_arrive, double* x_final)
+{
+    if (!g || (n > 0 && (!x0 || !t_arrive || !x_final))) return fail(DP_EINVAL, "NULL argument");
+    if (n < 0 || !(tau > 0) || !(h_rk4 > 0) || !(t_max > 0) || !std::isfinite(t_max))
+        return fail(DP_EINVAL, "bad n, tau, h_rk4 or t_max");
+    if (!(drag_c >= 0) || !std::isfinite(drag_c)) return fail(DP_EINVAL, "drag_c must be finite and >= 0");
+    if (drag_c > 0 && g->d.dynamics != DP_DYN_POLAR) return fail(DP_EINVAL, "drag needs DP_DYN_POLAR grids");
+    if (n == 0) return DP_OK;
+    return loop_common(g, x0, n, tau, h_rk4, t_max, drag_c, nullptr, nullptr, t_arrive, x_final);
 }
 
 }  // extern "C"

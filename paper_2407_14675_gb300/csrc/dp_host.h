@@ -50,6 +50,7 @@ struct LoopLaunch {
     long long steps;
     double tgt_c[4], tgt_w[4];
     double mu, accel, mdot, lo_m;
+    double drag;             // closed loop: drag coefficient C of the simulated system (polar)
     const double2* tab_hi64;
     const double2* tab_lo64;
     double* alpha;           // n (feedback)

@@ -15,7 +15,7 @@ namespace dpk {
 
 template <int DYN>
 __device__ __forceinline__ void dyn64(const double y[4], double s, double c, double mu, double accel,
-                                      double mdot, double f[4])
+                                      double mdot, double drag, double f[4])
 {
     if (DYN == kDynOrbit) {
         double am = accel / y[3];
@@ -24,10 +24,11 @@ __device__ __forceinline__ void dyn64(const double y[4], double s, double c, dou
         f[2] = -y[1] * y[2] / y[0] + am * c;
         f[3] = mdot;
     } else if (DYN == kDynPolar) {
-        // thrust off: s = c = 0
+        // thrust off: s = c = 0; drag of the simulated system (Example 2 of
+        // §4) with the printed components -C v_rho^2 and -C v_theta^2
         f[0] = y[1];
-        f[1] = y[2] * y[2] / y[0] - mu / (y[0] * y[0]) + accel * s;
-        f[2] = -y[1] * y[2] / y[0] + accel * c;
+        f[1] = y[2] * y[2] / y[0] - mu / (y[0] * y[0]) + accel * s - drag * y[1] * y[1];
+        f[2] = -y[1] * y[2] / y[0] + accel * c - drag * y[2] * y[2];
         f[3] = y[2] / y[0];
     } else {
         f[0] = fabs(c) < 1e-12 ? 0.0 : c;
@@ -144,16 +145,16 @@ loop_kernel(const __grid_constant__ Geo<G> g, const __grid_constant__ LoopLaunch
 
         // --- one RK4 step of the dynamics with the angle held ---
         double k1[4], k2[4], k3[4], k4[4], z[4];
-        dyn64<DYN>(y, s, c, a.mu, a.accel, a.mdot, k1);
+        dyn64<DYN>(y, s, c, a.mu, a.accel, a.mdot, a.drag, k1);
 #pragma unroll
         for (int d = 0; d < 4; ++d) z[d] = y[d] + 0.5 * a.h * k1[d];
-        dyn64<DYN>(z, s, c, a.mu, a.accel, a.mdot, k2);
+        dyn64<DYN>(z, s, c, a.mu, a.accel, a.mdot, a.drag, k2);
 #pragma unroll
         for (int d = 0; d < 4; ++d) z[d] = y[d] + 0.5 * a.h * k2[d];
-        dyn64<DYN>(z, s, c, a.mu, a.accel, a.mdot, k3);
+        dyn64<DYN>(z, s, c, a.mu, a.accel, a.mdot, a.drag, k3);
 #pragma unroll
         for (int d = 0; d < 4; ++d) z[d] = y[d] + a.h * k3[d];
-        dyn64<DYN>(z, s, c, a.mu, a.accel, a.mdot, k4);
+        dyn64<DYN>(z, s, c, a.mu, a.accel, a.mdot, a.drag, k4);
 #pragma unroll
         for (int d = 0; d < 4; ++d) y[d] = y[d] + a.h / 6.0 * (k1[d] + 2.0 * k2[d] + 2.0 * k3[d] + k4[d]);
 

@@ -184,6 +184,8 @@ def load(path: Optional[str] = None):
         "dp_policy_iterate": [_P, C.POINTER(dp_solve_opts), C.POINTER(dp_solve_stats)],
         "dp_feedback_control": [_P, _P, C.c_int32, C.c_double, _P, _P],
         "dp_simulate_closed_loop": [_P, _P, C.c_int32, C.c_double, C.c_double, C.c_double, _P, _P],
+        "dp_simulate_closed_loop_drag": [_P, _P, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, _P,
+                                         _P],
         "dp_bellman_sweep_noalloc": [C.POINTER(dp_grid_desc), C.c_int32, _P, _P, _P, _dp],
         "dp_mlp_create": [_P, _P, C.c_int32, _P, C.POINTER(_P)],
         "dp_mlp_destroy": [_P],
@@ -362,6 +364,16 @@ def dp_feedback_control(grid: int, states, tau: float):
     return alpha, q
 
 
+def dp_simulate_closed_loop_drag(grid: int, x0, tau: float, h_rk4: float, t_max: float, drag_c: float):
+    x = np.ascontiguousarray(x0, np.float64).reshape(-1, 4)
+    n = len(x)
+    ta = np.empty(n)
+    xf = np.empty((n, 4))
+    _check(load().dp_simulate_closed_loop_drag(grid, _host_ptr(x, np.float64), n, tau, h_rk4, t_max, drag_c,
+                                               _host_ptr(ta, np.float64), _host_ptr(xf, np.float64)))
+    return ta, xf
+
+
 def dp_simulate_closed_loop(grid: int, x0, tau: float, h_rk4: float, t_max: float):
     x = np.ascontiguousarray(x0, np.float64).reshape(-1, 4)
     n = len(x)
@@ -425,7 +437,9 @@ class Grid:
     def feedback(self, states, tau):
         return dp_feedback_control(self.h, states, tau)
 
-    def simulate(self, x0, tau, h_rk4, t_max):
+    def simulate(self, x0, tau, h_rk4, t_max, drag=0.0):
+        if drag:
+            return dp_simulate_closed_loop_drag(self.h, x0, tau, h_rk4, t_max, drag)
         return dp_simulate_closed_loop(self.h, x0, tau, h_rk4, t_max)
 
 
