@@ -31,6 +31,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Bellman node-updates/s; time to ‖ΔV‖∞<1e-6, plain vs NN-warm-started"
+# DRAM bytes (read + written) of one launch of the 61^4 frozen-feet evaluation
+# sweep, from the ncu capture summarised in profiles/sweep_kernels_61x4.md; to
+# be retaken (or set to None) whenever that kernel changes
+EVAL_TRAFFIC_61X4 = 221.605120e6 + 20.989696e6
 UNIT = "node-updates/s"
 L2_BYTES = 129 * 2 ** 20
 
@@ -504,7 +508,7 @@ def run_ours(args, world, rank, local):
         dp.dp_set_policy(g.h, C_view)
         rc, st = g.policy_iterate(tol=0.0, max_sweeps=1, n_eval=p.n_eval, polish=0, warm=1)
         dp.dp_get_value(g.h, g.n, out=V_host.numpy())
-        C_view[:] = dp.dp_get_policy(g.h, g.n)
+        dp.dp_get_policy(g.h, g.n, out=C_view)
         e2e_updates += st.node_updates
     torch.cuda.synchronize()
     e2e_s = _reduce_max(time.perf_counter() - t0, world)
@@ -549,7 +553,9 @@ def run_ours(args, world, rank, local):
     roof = {"bound": "hbm", "kernel": "sweep_kernel<float,float,EVAL> (policy evaluation)",
             "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
-            "traffic": None, "algorithmic_bytes_per_launch": eval_bytes, "avg_launch_ms": eval_ms,
+            "traffic": EVAL_TRAFFIC_61X4, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                                                              "of one launch, profiles/sweep_kernels_61x4.md",
+            "algorithmic_bytes_per_launch": eval_bytes, "avg_launch_ms": eval_ms,
             "share_of_step": ms_eval / max(ms, 1e-9)}
     imp_ms = ms_imp / max(n_imp, 1)
 

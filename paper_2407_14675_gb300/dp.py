@@ -308,8 +308,8 @@ def dp_set_policy(grid: int, codes) -> None:
     _check(load().dp_set_policy(grid, _host_ptr(codes, np.uint16), len(codes)))
 
 
-def dp_get_policy(grid: int, count: int) -> np.ndarray:
-    out = np.empty(count, np.uint16)
+def dp_get_policy(grid: int, count: int, out=None) -> np.ndarray:
+    out = np.empty(count, np.uint16) if out is None else out
     _check(load().dp_get_policy(grid, _host_ptr(out, np.uint16), count))
     return out
 
