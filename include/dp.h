@@ -399,6 +399,17 @@ int dp_batch_get_policy(const dp_batch* batch, int32_t index, uint16_t* host_cod
 int dp_bellman_sweep_noalloc(const dp_grid_desc* desc, int32_t mode, const void* V_in, void* V_out,
                              uint16_t* codes, double* residual);
 
+/* Warm start of grid dst from the solved value and policy of grid src, the
+ * same problem at another resolution or box (no network; the plain baseline
+ * of the learned warm start): at every stored node of dst, V = the Q1
+ * interpolation of src's resident value (dst's M where the node lies outside
+ * src's box or its src cell leaves src's node set; 0 on dst's target) and
+ * the policy code of the nearest src node (0 where that node is not stored).
+ * Written in dst's storage precision; dst then starts with warm = 1.  Both
+ * grids must have the same dynamics and live on one device; src's stream is
+ * synchronised first.  *ms (nullable): GPU time. */
+int dp_warm_start_from_grid(const dp_grid* src, dp_grid* dst, double* ms);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* dp_last_error(void);
 

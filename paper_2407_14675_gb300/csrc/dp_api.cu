@@ -1085,6 +1085,37 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
     return DP_OK;
 }
 
+int dp_warm_start_from_grid(const dp_grid* src, dp_grid* dst, double* ms_out)
+{
+    if (!src || !dst) return fail(DP_EINVAL, "NULL argument");
+    if (src == dst) return fail(DP_EINVAL, "source and destination must differ");
+    if (src->d.dynamics != dst->d.dynamics) return fail(DP_EINVAL, "source and destination need the same dynamics");
+    if (src->device != dst->device) return fail(DP_EINVAL, "source and destination must be on one device");
+    if (cudaSetDevice(dst->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
+    // the source's work must be finished before the destination's stream reads it
+    CK(cudaStreamSynchronize(src->st));
+    const bool src64 = !src->fp32 || src->fp64_values;
+    const void* Vs = (src->fp32 && src->fp64_values) ? (const void*)src->V64[src->cur64] : src->V[src->cur];
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, dst->st));
+    cudaError_t e = launch_prolong(src->g64, Vs, src64 ? 0 : 1, src->code, src->d.reduced,
+                                   src->d.dynamics == DP_DYN_POLAR, dst->g64, dst->V[dst->cur], dst->fp32, dst->code,
+                                   dst->M, dst->st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, dst->st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(e);
+    if (ms_out) *ms_out = ms;
+    dst->fp64_values = false;
+    dst->feet_valid = false;
+    return DP_OK;
+}
+
 int dp_feedback_control(const dp_grid* g, const double* states, int32_t n, double tau, double* alpha_out,
                         double* q_out)
 {

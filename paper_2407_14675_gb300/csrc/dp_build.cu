@@ -185,6 +185,82 @@ cudaError_t launch_widen(const float* src, double* dst, int n, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Warm start of grid gd from the value and policy of grid gs (the same
+// problem at another resolution or box): Q1 interpolation of gs's value at
+// every stored node of gd (Md where the node lies outside gs's box or its gs
+// cell has a corner outside gs's node set), and the policy code of the
+// nearest gs node (0 where that node is not stored).  Target nodes of gd get
+// value 0.  FP64 coordinates and blend; the same strict outside test as the
+// sweeps.
+template <typename S, bool SRC_REDUCED, bool PER3>
+__global__ void prolong_kernel(Geo<double> gs, const S* __restrict__ Vs, const uint16_t* __restrict__ Cs,
+                               Geo<double> gd, void* Vd, int fp32_dst, uint16_t* __restrict__ Cd, double Md)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= gd.n_nodes) return;
+    int id[4];
+    decode_node(gd, j, id);
+    double v = 0.0;
+    uint16_t code = 0;
+    if (!in_target(gd, id)) {
+        double s[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) s[d] = (gd.lo[d] + (double)id[d] * gd.h[d] - gs.lo[d]) / gs.h[d];
+        const int zero[4] = {0, 0, 0, 0};
+        int c[4];
+        double t[4];
+        Corners<double> K;
+        const bool out = foot_cell<double, PER3>(gs, zero, s, c, t) ||
+                         load_corners<double, double, S, SRC_REDUCED, PER3>(gs, Vs, c, (S)0, K);
+        v = out ? Md : K.blend(t);
+        // nearest source node for the policy
+        int nn[4];
+        bool have = true;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            int k = (int)floor(s[d] + 0.5);
+            if (PER3 && d == 3) k = ((k % gs.n[3]) + gs.n[3]) % gs.n[3];
+            nn[d] = min(max(k, 0), gs.n[d] - 1);
+        }
+        long long idx;
+        if (!SRC_REDUCED) {
+            idx = (((long long)nn[0] * gs.n[1] + nn[1]) * gs.n[2] + nn[2]) * gs.n[3] + nn[3];
+        } else {
+            const int4 R = gs.rows[nn[0] * gs.n[1] + nn[1]];
+            have = nn[2] >= R.y && nn[2] < R.y + R.z;
+            idx = have ? (long long)R.x + (long long)(nn[2] - R.y) * gs.n_m + nn[3] : 0;
+        }
+        code = have ? Cs[idx] : (uint16_t)0;
+    }
+    if (fp32_dst) ((float*)Vd)[j] = (float)v;
+    else ((double*)Vd)[j] = v;
+    Cd[j] = code;
+}
+
+template <typename S>
+static cudaError_t launch_prolong_t(const Geo<double>& gs, const S* Vs, const uint16_t* Cs, int src_reduced,
+                                    int periodic, const Geo<double>& gd, void* Vd, int fp32_dst, uint16_t* Cd,
+                                    double Md, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)((gd.n_nodes + 255) / 256);
+    if (periodic)
+        prolong_kernel<S, false, true><<<blocks, 256, 0, st>>>(gs, Vs, Cs, gd, Vd, fp32_dst, Cd, Md);
+    else if (src_reduced)
+        prolong_kernel<S, true, false><<<blocks, 256, 0, st>>>(gs, Vs, Cs, gd, Vd, fp32_dst, Cd, Md);
+    else
+        prolong_kernel<S, false, false><<<blocks, 256, 0, st>>>(gs, Vs, Cs, gd, Vd, fp32_dst, Cd, Md);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(const Geo<double>& gs, const void* Vs, int src_fp32, const uint16_t* Cs, int src_reduced,
+                           int periodic, const Geo<double>& gd, void* Vd, int fp32_dst, uint16_t* Cd, double Md,
+                           cudaStream_t st)
+{
+    if (src_fp32)
+        return launch_prolong_t<float>(gs, (const float*)Vs, Cs, src_reduced, periodic, gd, Vd, fp32_dst, Cd, Md, st);
+    return launch_prolong_t<double>(gs, (const double*)Vs, Cs, src_reduced, periodic, gd, Vd, fp32_dst, Cd, Md, st);
+}
+
 __global__ void box_index_kernel(Geo<double> g, long long* out)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;

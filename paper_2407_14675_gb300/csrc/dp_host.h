@@ -79,5 +79,8 @@ cudaError_t launch_store_value(const double* src, void* dst, int fp32, int n, co
 cudaError_t launch_load_value(const void* src, double* dst, int fp32, int n, cudaStream_t st);
 cudaError_t launch_widen(const float* src, double* dst, int n, cudaStream_t st);
 cudaError_t launch_box_index(const Geo<double>& g, long long* out, cudaStream_t st);
+cudaError_t launch_prolong(const Geo<double>& gs, const void* Vs, int src_fp32, const uint16_t* Cs, int src_reduced,
+                           int periodic, const Geo<double>& gd, void* Vd, int fp32_dst, uint16_t* Cd, double Md,
+                           cudaStream_t st);
 
 }  // namespace dpk

@@ -195,6 +195,7 @@ def load(path: Optional[str] = None):
         "dp_mlp_gradients": [_P, _P, _P, C.c_int32, _P, C.POINTER(C.c_float)],
         "dp_mlp_train_grid": [_P, _P, C.POINTER(dp_mlp_train_opts), C.POINTER(dp_mlp_train_stats)],
         "dp_warm_start": [_P, _P, _dp],
+        "dp_warm_start_from_grid": [_P, _P, _dp],
         "dp_batch_create": [_P, C.c_int32, _P, C.POINTER(_P)],
         "dp_batch_destroy": [_P],
         "dp_batch_get_info": [_P, _P, _P, _P, _P, _P, _P],
@@ -623,6 +624,12 @@ def dp_mlp_train_grid(mlp: int, grid: int, epochs=4, batch=4096, lr=1e-3, seed=1
 def dp_warm_start(mlp: int, grid: int) -> float:
     ms = C.c_double(0)
     _check(load().dp_warm_start(mlp, grid, C.byref(ms)))
+    return ms.value
+
+
+def dp_warm_start_from_grid(src: int, dst: int) -> float:
+    ms = C.c_double(0)
+    _check(load().dp_warm_start_from_grid(src, dst, C.byref(ms)))
     return ms.value
 
 
