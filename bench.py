@@ -32,8 +32,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Bellman node-updates/s; time to ‖ΔV‖∞<1e-6, plain vs NN-warm-started"
 # DRAM bytes (read + written) of one launch of the 61^4 frozen-feet evaluation
-# sweep, from the ncu capture summarised in profiles/sweep_kernels_61x4.md; to
-# be retaken (or set to None) whenever that kernel changes
+# sweep, from one ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum); to be retaken (or set to None) whenever it changes
 EVAL_TRAFFIC_61X4 = 221.605120e6 + 20.989696e6
 UNIT = "node-updates/s"
 L2_BYTES = 129 * 2 ** 20
@@ -551,6 +551,21 @@ def run_ours(args, world, rank, local):
                             "eval_increments": st.ms_eval_fp64},
                  "residual_trace": {int(k): float(h[k]) for k in marks if 0 <= k < len(h)},
                  "start": "cold (V = 0, full tabulation first)"}
+    cascade = None
+    if args.solve and rank == 0:
+        # coarse to fine: the same problem on 31^4 to 1e-6, its solution
+        # interpolated onto the 61^4 grid, then solved there to 1e-6
+        with dp.Grid(W.config1(n=31), stream=int(stream.cuda_stream)) as gc:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, sc = gc.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=p.n_eval, polish=1, warm=0)
+            dp.dp_warm_start_from_grid(gc.h, g.h)
+            rc, sf = g.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=p.n_eval, polish=1, warm=1)
+            torch.cuda.synchronize()
+            cascade = {"seconds": time.perf_counter() - t0, "converged": bool(sc.converged and sf.converged),
+                       "coarse_31x4_improvements": sc.sweeps_improve + sc.sweeps_improve_fp64,
+                       "fine_61x4_improvements": sf.sweeps_improve + sf.sweeps_improve_fp64,
+                       "residual": sf.residual}
     warm = warm_start_leg(args, dp, W, torch, g, p) if (args.warm_start and args.solve and rank == 0) else None
     extra = extra_legs(args, dp, W, torch, g, p) if (args.extra and rank == 0) else None
     g.close()
@@ -572,7 +587,7 @@ def run_ours(args, world, rank, local):
             "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
             "traffic": EVAL_TRAFFIC_61X4, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum "
-                                                              "of one launch, profiles/sweep_kernels_61x4.md",
+                                                              "of one launch of this kernel (sweep-kernel profile)",
             "algorithmic_bytes_per_launch": eval_bytes, "avg_launch_ms": eval_ms,
             "share_of_step": ms_eval / max(ms, 1e-9)}
     imp_ms = ms_imp / max(n_imp, 1)
@@ -603,6 +618,7 @@ def run_ours(args, world, rank, local):
             "sample": "one spawned oracle process per core, each on its own 2,000-node sample of the 61^4 step "
                       "mix, %.1f s" % par_info["seconds"]},
         "time_to_tol": solve,
+        "time_to_tol_coarse_to_fine": cascade,
         "warm_start": warm,
         "batch": batch,
         "other_solves": extra,
