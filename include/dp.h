@@ -77,6 +77,12 @@ extern "C" {
                                     the minimum"                                   */
 #define DP_SWEEP_EVAL         3  /* Eq. (13): one Jacobi sweep at the frozen policy */
 
+/* How policy iteration evaluates a frozen policy (dp_solve_opts.eval_solver). */
+#define DP_EVAL_JACOBI 0     /* n_eval Jacobi sweeps (modified policy iteration)   */
+#define DP_EVAL_GMRES  1     /* the linear system of Eq. (13) by restarted GMRES,
+                                as §3 prescribes after Eq. (14)                    */
+#define DP_GMRES_MAX_RESTART 64
+
 typedef struct dp_grid dp_grid;
 
 /* Grid, dynamics, target and control-set description (§3, §4). */
@@ -130,6 +136,21 @@ typedef struct dp_solve_opts {
                               test (VI: every sweep; PI: every improvement sweep),
                               in order, up to history_capacity entries          */
     int64_t history_capacity;
+    /* Evaluation of the frozen policy in policy iteration (§3 after Eq. (14)):
+     * with the control fixed, Eq. (13) is the sparse linear system
+     * (I - beta W_f) V = b, W_f holding the Q1 weights of each node's foot.
+     * DP_EVAL_GMRES replaces the n_eval Jacobi sweeps by restarted GMRES on it:
+     * each cycle starts from the residual T_f(V) - V of the value the
+     * improvement sweep produced and adds the minimal-residual correction
+     * from an Arnoldi basis of up to gmres_restart vectors. */
+    int32_t eval_solver;   /* DP_EVAL_JACOBI (0) or DP_EVAL_GMRES                     */
+    int32_t gmres_restart; /* Arnoldi steps per cycle, 1..DP_GMRES_MAX_RESTART
+                              (0: 30)                                              */
+    int32_t gmres_cycles;  /* cycles per evaluation (0: 1); cycles after the first
+                              cost one evaluation sweep each for their residual    */
+    int32_t gmres_reorth;  /* 1: classical Gram-Schmidt twice (0: once)            */
+    double  gmres_rtol;    /* a cycle ends early once the 2-norm residual estimate
+                              falls below gmres_rtol times its start (0: 1e-3)     */
 } dp_solve_opts;
 
 /* Solver statistics (filled on DP_OK and on DP_ENOCONV). */
@@ -149,6 +170,10 @@ typedef struct dp_solve_stats {
     int64_t history_count;        /* entries written to opts->history                */
     int64_t switch_outer;         /* PI: improvement sweeps before the FP64 switch
                                      (-1: no switch)                                 */
+    int64_t gmres_cycles;         /* GMRES: cycles run                               */
+    int64_t gmres_matvecs;        /* GMRES: products with I - beta W_f (Arnoldi
+                                     steps); their GPU time is in ms_eval /
+                                     ms_eval_fp64 when time_kernels = 1             */
 } dp_solve_stats;
 
 /* Sizes of a grid. */
@@ -203,8 +228,24 @@ int dp_value_iterate(dp_grid* grid, const dp_solve_opts* opts, dp_solve_stats* s
  * refinement when desc.refine) and opts->n_eval Jacobi evaluation sweeps at
  * the frozen policy, repeated until an improvement sweep moves V by less than
  * opts->tol.  FP32 grids with opts->polish switch to FP64 values once the FP32
- * residual stalls and finish there.  stats nullable. */
+ * residual stalls and finish there.  With opts->eval_solver = DP_EVAL_GMRES
+ * the evaluation is GMRES on the linear system instead of n_eval sweeps (the
+ * paper's policy iteration); the host then checks every improvement sweep.
+ * stats nullable. */
 int dp_policy_iterate(dp_grid* grid, const dp_solve_opts* opts, dp_solve_stats* stats);
+
+/* Policy evaluation, §3 Eq. (13) solved as a linear system: restarted GMRES
+ * on (I - beta W_f) V = b at the resident policy, from the resident V, until
+ * an evaluation sweep moves V by less than opts->tol (sup norm) or after
+ * opts->max_sweeps cycles (DP_ENOCONV).  Each round is one evaluation sweep
+ * (V <- T_f(V), whose change is the stopping test) and one GMRES cycle of
+ * opts->gmres_restart steps; opts->gmres_cycles is ignored.  FP32 grids build
+ * the frozen feet of the policy first when no improvement sweep has stored
+ * them.  The basis takes (gmres_restart + 1) x n_active values of the
+ * storage precision (FP32 grids: FP32) of device memory, allocated on first
+ * use and kept with the grid.  Uses tol, max_sweeps, gmres_*, time_kernels;
+ * stats nullable (sweeps_eval / sweeps_eval_fp64, gmres_*, residual). */
+int dp_policy_evaluate(dp_grid* grid, const dp_solve_opts* opts, dp_solve_stats* stats);
 
 /* Approximate optimal feedback, §3 Eq. (15), at n arbitrary states
  * (host, n x 4 row-major) with step tau > 0: full tabulation then refinement
@@ -340,7 +381,7 @@ int dp_batch_autotune(dp_batch* batch, int32_t* item_eval, int32_t* item_improve
 /* Modified policy iteration of every transfer with the options of
  * dp_policy_iterate (tol, max_sweeps = improvement budget per transfer,
  * n_eval <= 1024, walk, warm, polish, switch_tol; time_kernels and history are
- * ignored).  total (nullable): sums of the sweep counts, node_updates,
+ * ignored; eval_solver must be DP_EVAL_JACOBI).  total (nullable): sums of the sweep counts, node_updates,
  * launches, the largest residual and switch_outer, converged = all converged.
  * per (nullable): count entries.  Returns DP_ENOCONV if some transfer missed
  * the tolerance (statistics valid), DP_ENONFINITE if one produced a non-finite

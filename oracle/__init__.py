@@ -91,6 +91,7 @@ def lib():
             "orc_simulate_drag": (None, [P, _dp, _u8, _dp, C.c_long, C.c_double, C.c_double, C.c_double,
                                          C.c_double, _dp, _dp]),
             "orc_dynamics_drag": (None, [P, _dp, C.c_double, C.c_double, _dp]),
+            "orc_policy_system": (None, [P, _u8, _u8, _u16, _l, _dp, _dp, C.POINTER(C.c_int)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -231,6 +232,33 @@ class Oracle:
         lib().orc_q_nodes(C.byref(self.s), _ptr(V, _dp), _ptr(self.active, _u8), nodes.ctypes.data_as(_l),
                           _ptr(codes, _u16), len(nodes), _ptr(out, _dp))
         return out
+
+    def policy_system(self, codes):
+        """Eq. (13) at a frozen policy as the affine map V -> b + beta W V:
+        returns (W, b) with W a scipy CSR matrix of the Q1 foot weights (rows
+        of target, inactive and outside nodes are empty)."""
+        import scipy.sparse as sp
+        codes = np.ascontiguousarray(codes, np.uint16)
+        idx = np.zeros((self.N, 16), np.int64)
+        w = np.zeros((self.N, 16))
+        b = np.zeros(self.N)
+        cnt = np.zeros(self.N, np.int32)
+        lib().orc_policy_system(C.byref(self.s), _ptr(self.active, _u8), _ptr(self.target, _u8), _ptr(codes, _u16),
+                                idx.ctypes.data_as(_l), _ptr(w, _dp), _ptr(b, _dp),
+                                cnt.ctypes.data_as(C.POINTER(C.c_int)))
+        rows = np.repeat(np.arange(self.N), 16).reshape(self.N, 16)
+        used = cnt[:, None] > np.arange(16)[None, :]
+        W = sp.csr_matrix((w[used], (rows[used], idx[used])), shape=(self.N, self.N))
+        return W, b
+
+    def evaluate_exact(self, codes):
+        """Exact policy evaluation: the solution of (I - beta W) V = b, the
+        linear system of Eq. (13) at a frozen policy, by a sparse direct solve."""
+        import scipy.sparse as sp
+        import scipy.sparse.linalg as spla
+        W, b = self.policy_system(codes)
+        A = (sp.identity(self.N, format="csr") - self.s.beta * W).tocsc()
+        return spla.spsolve(A, b)
 
     def value_iterate(self, V0=None, tol=None, max_sweeps=100000):
         V = np.zeros(self.N) if V0 is None else np.array(V0, np.float64)

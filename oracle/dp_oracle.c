@@ -265,8 +265,12 @@ void orc_rk4_step(const orc_problem* p, const double x[4], double alpha, double 
 /* Q1 interpolation of V at the point s given in grid units (s_d = 0 at lo_d,
  * n_d - 1 at hi_d).  Returns 0 when the point is outside the box (strictly)
  * or a corner of its cell is not in the node set; the caller then uses M. */
-int orc_interp(const orc_problem* p, const double* V, const unsigned char* active,
-               const double s[4], double* out)
+/* Q1 interpolation of §3 (after Eq. (10)) at grid coordinates s: the flat
+ * indices and weights of the 2^4 cell corners, weights the products of
+ * (1 - t_d) or t_d.  Returns 0 when s leaves the box (in a non-periodic
+ * dimension) or a corner is outside the node set (active may be NULL). */
+static int interp_corners(const orc_problem* p, const unsigned char* active, const double s[4], long idx16[16],
+                          double w16[16])
 {
     int cell[4];
     double t[4];
@@ -286,7 +290,6 @@ int orc_interp(const orc_problem* p, const double* V, const unsigned char* activ
         cell[d] = c;
         t[d] = s[d] - c;
     }
-    double acc = 0.0;
     for (int b = 0; b < 16; ++b) {
         int idx[4];
         double w = 1.0;
@@ -298,8 +301,20 @@ int orc_interp(const orc_problem* p, const double* V, const unsigned char* activ
         }
         long j = flat_index(p, idx);
         if (active && !active[j]) return 0;
-        acc += w * V[j];
+        idx16[b] = j;
+        w16[b] = w;
     }
+    return 1;
+}
+
+int orc_interp(const orc_problem* p, const double* V, const unsigned char* active,
+               const double s[4], double* out)
+{
+    long idx[16];
+    double w[16];
+    if (!interp_corners(p, active, s, idx, w)) return 0;
+    double acc = 0.0;
+    for (int b = 0; b < 16; ++b) acc += w[b] * V[idx[b]];
     *out = acc;
     return 1;
 }
@@ -343,6 +358,44 @@ double orc_q_node(const orc_problem* p, const double* V, const unsigned char* ac
     for (int d = 0; d < 4; ++d) s[d] = idx[d] + delta[d] / spacing(p, d);
     if (!orc_interp(p, V, active, s, &I)) I = p->M;
     return p->dt * orc_running_cost(p, x, !isnan(alpha)) + p->beta * I;
+}
+
+/* Row j of the policy-evaluation system, Eq. (13) at a frozen control code:
+ * the update of node j is affine in V,
+ *     V_j = b_j + beta * sum_c w_c V_{idx_c},
+ * with w_c the Q1 weights of the node's foot.  b_j is dt l(x_j, control),
+ * plus beta M when the foot leaves the box or the node set (the row is then
+ * empty).  A target node has V_j = 0 and an inactive node V_j = M: b_j is
+ * that value and the row is empty.  Returns the number of weights (16 or 0). */
+int orc_policy_row(const orc_problem* p, const unsigned char* active, const unsigned char* target, long j,
+                   unsigned code, long idx16[16], double w16[16], double* b)
+{
+    if (!active[j]) { *b = p->M; return 0; }
+    if (target[j]) { *b = 0.0; return 0; }
+    int node[4];
+    double x[4], delta[4], s[4];
+    node_index(p, j, node);
+    node_state(p, node, x);
+    double a = code_control(p, code);
+    orc_heun_displacement(p, x, a, p->dt, delta);
+    for (int d = 0; d < 4; ++d) s[d] = node[d] + delta[d] / spacing(p, d);
+    double run = p->dt * orc_running_cost(p, x, !isnan(a));
+    if (!interp_corners(p, active, s, idx16, w16)) {
+        *b = run + p->beta * p->M;
+        return 0;
+    }
+    *b = run;
+    return 16;
+}
+
+/* Every row of the policy-evaluation system (orc_policy_row): idx and w hold
+ * 16 entries per node (count[j] of them used), b one value per node. */
+void orc_policy_system(const orc_problem* p, const unsigned char* active, const unsigned char* target,
+                       const uint16_t* code, long* idx, double* w, double* b, int* count)
+{
+    long N = orc_node_count(p);
+    for (long j = 0; j < N; ++j)
+        count[j] = orc_policy_row(p, active, target, j, code[j], idx + 16 * j, w + 16 * j, b + j);
 }
 
 /* Foot of the one-step map from grid node idx in grid units (test helper:

@@ -10,6 +10,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -45,6 +46,18 @@ constexpr double kStallZone = 64.0; // "near the FP32 floor": below this multipl
 constexpr int kStallFar = 30;       // improvements without gain that switch anywhere
 constexpr int kMaxConfirms = 3;     // full-table confirmations of an FP32 -> FP64 switch
 constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kGmDefaultRestart = 30;
+constexpr double kGmDefaultRtol = 1e-3;
+constexpr int kGmMaxCycles = 64;
+
+// The end of GmCtl that the host reads back after a cycle.
+struct GmTail {
+    double beta0, rel;
+    int k, done;
+};
+static_assert(offsetof(GmCtl, rel) == offsetof(GmCtl, beta0) + 8 && offsetof(GmCtl, k) == offsetof(GmCtl, beta0) + 16 &&
+                  offsetof(GmCtl, done) == offsetof(GmCtl, beta0) + 20,
+              "GmTail mirrors the tail of GmCtl");
 
 }  // namespace
 
@@ -81,6 +94,16 @@ struct dp_grid {
     Ctl* h_ctl = nullptr;                // pinned
     unsigned long long* h_ring = nullptr;// pinned, kRing
     long long device_bytes = 0;
+    // GMRES policy evaluation (allocated on first use)
+    unsigned char* gm_Q = nullptr;       // (gm_m + 1) x gm_ldq basis values
+    long long gm_ldq = 0;
+    int gm_m = 0;
+    int gm_es = 0;                       // bytes per basis value
+    long long gm_bytes = 0;
+    double* gm_partial = nullptr;        // gm_blocks x kGmLd
+    int gm_blocks = 0;
+    GmCtl* gm_ctl = nullptr;
+    GmTail* h_gm = nullptr;              // pinned, one per cycle of a round
 
     Geo<double> g64;
     Geo<float> g32;
@@ -110,11 +133,12 @@ void free_grid(dp_grid* g)
     if (g->st) cudaStreamSynchronize(g->st);
     void* ps[] = {g->rows, g->lines, g->hi64, g->lo64, g->hi32, g->lo32, g->V[0], g->V[1], g->V64[0],
                   g->V64[1], g->code, g->feet_lo, g->feet_hi, g->acc, g->ctl, g->ring, g->staging,
-                  g->scratch64};
+                  g->scratch64, g->gm_Q, g->gm_partial, g->gm_ctl};
     for (void* p : ps)
         if (p) cudaFree(p);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
     if (g->h_ring) cudaFreeHost(g->h_ring);
+    if (g->h_gm) cudaFreeHost(g->h_gm);
     delete g;
 }
 
@@ -448,6 +472,111 @@ int ensure_fp64(dp_grid* g)
     return DP_OK;
 }
 
+// GMRES options with their defaults filled in.
+struct GmOpts {
+    int m, cycles, reorth;
+    double rtol;
+};
+
+int gm_options(const dp_solve_opts* o, GmOpts& go)
+{
+    if (o->gmres_restart < 0 || o->gmres_restart > kGmMaxRestart)
+        return fail(DP_EINVAL, "gmres_restart %d outside 0..%d", o->gmres_restart, kGmMaxRestart);
+    if (o->gmres_cycles < 0 || o->gmres_cycles > kGmMaxCycles)
+        return fail(DP_EINVAL, "gmres_cycles %d outside 0..%d", o->gmres_cycles, kGmMaxCycles);
+    if (!(o->gmres_rtol >= 0) || !(o->gmres_rtol < 1)) return fail(DP_EINVAL, "gmres_rtol must be in [0, 1)");
+    if (o->gmres_reorth != 0 && o->gmres_reorth != 1) return fail(DP_EINVAL, "gmres_reorth must be 0 or 1");
+    go.m = o->gmres_restart > 0 ? o->gmres_restart : kGmDefaultRestart;
+    go.cycles = o->gmres_cycles > 0 ? o->gmres_cycles : 1;
+    go.reorth = o->gmres_reorth;
+    go.rtol = o->gmres_rtol > 0 ? o->gmres_rtol : kGmDefaultRtol;
+    return DP_OK;
+}
+
+// Basis of m + 1 vectors in the grid's storage precision (FP32 grids keep an
+// FP32 basis after the switch to FP64 values), partial sums and control.
+int ensure_gmres(dp_grid* g, int m)
+{
+    const int es = g->fp32 ? (int)sizeof(float) : (int)sizeof(double);
+    const long long ldq = (g->n_active + 63) / 64 * 64;   // 256-byte aligned vectors
+    if (g->gm_Q && (g->gm_m < m || g->gm_es != es)) {
+        CK(cudaStreamSynchronize(g->st));
+        cudaFree(g->gm_Q);
+        g->device_bytes -= g->gm_bytes;
+        g->gm_Q = nullptr;
+    }
+    int rc;
+    if (!g->gm_Q) {
+        if ((rc = dalloc(g, &g->gm_Q, (size_t)(m + 1) * ldq * es))) return rc;
+        g->gm_m = m;
+        g->gm_es = es;
+        g->gm_ldq = ldq;
+        g->gm_bytes = (long long)(m + 1) * ldq * es;
+    }
+    if (!g->gm_partial) {
+        g->gm_blocks = 8 * g->sm_count;
+        if ((rc = dalloc(g, &g->gm_partial, (size_t)g->gm_blocks * kGmLd))) return rc;
+    }
+    if (!g->gm_ctl) {
+        if ((rc = dalloc(g, &g->gm_ctl, 1))) return rc;
+        CK(cudaMemsetAsync(g->gm_ctl, 0, sizeof(GmCtl), g->st));   // the block counter starts at 0
+    }
+    if (!g->h_gm) CK(cudaMallocHost((void**)&g->h_gm, kGmMaxCycles * sizeof(GmTail)));
+    return DP_OK;
+}
+
+template <typename G, typename VT>
+GmArgs<G, VT> gm_args(const dp_grid* g, const Geo<G>& geo, const GmOpts& go)
+{
+    GmArgs<G, VT> a;
+    a.g = geo;
+    a.g.M = (G)0;           // the products carry no penalty: a foot outside blends to 0
+    a.g.M64 = 0.0;
+    a.Q = (VT*)g->gm_Q;
+    a.ldq = g->gm_ldq;
+    a.m = go.m;
+    a.reorth = go.reorth;
+    a.rtol = go.rtol;
+    a.code = g->code;
+    a.feet_lo = g->feet_lo;
+    a.feet_hi = g->feet_hi;
+    a.partial = g->gm_partial;
+    a.max_blocks = g->gm_blocks;
+    a.gctl = g->gm_ctl;
+    a.ctl = g->ctl;
+    a.dyn = g->d.dynamics;
+    a.reduced = g->d.reduced;
+    a.sm_count = g->sm_count;
+    a.stream = g->st;
+    return a;
+}
+
+// One GMRES cycle on the current value: the previous buffer holds V, the
+// current one T_f(V) (an improvement or evaluation sweep just ran); the
+// current one receives V + e.  The cycle's tail is copied to h_gm[slot].
+cudaError_t enqueue_gmres(dp_grid* g, const GmOpts& go, int slot)
+{
+    cudaError_t e;
+    switch (store_of(g)) {
+    case kStoreF64:
+        e = gm_cycle(gm_args<double, double>(g, g->g64, go), (const double*)g->V[g->cur ^ 1], (double*)g->V[g->cur]);
+        break;
+    case kStoreF32:
+        if (!g->feet_valid) return cudaErrorInvalidValue;
+        e = gm_cycle(gm_args<float, float>(g, g->g32, go), (const float*)g->V[g->cur ^ 1], (float*)g->V[g->cur]);
+        break;
+    default:
+        if (!g->feet_valid) return cudaErrorInvalidValue;
+        e = gm_cycle(gm_args<float, float>(g, g->g32, go), (const double*)g->V64[g->cur64 ^ 1], g->V64[g->cur64]);
+        break;
+    }
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(&g->h_gm[slot], &g->gm_ctl->beta0, sizeof(GmTail), cudaMemcpyDeviceToHost, g->st);
+}
+
+// Launches of one cycle (some exit at once after an early stop).
+long long gmres_launches(const GmOpts& go) { return 2 + (long long)go.m * (go.reorth ? 3 : 2); }
+
 int zero_value(dp_grid* g)
 {
     size_t es = g->fp32 ? sizeof(float) : sizeof(double);
@@ -635,6 +764,133 @@ int describe_full_grid(const dp_grid_desc* desc, Geo<double>* g64, Geo<float>* g
 }
 
 }  // namespace dpk
+
+
+namespace {
+
+// FP32 -> FP64 switch rule of policy iteration, shared by both evaluation
+// solvers: switch once the FP32 improvement residual is small, or stalls: 3
+// improvements without gain near the FP32 floor, 30 far above it (a short
+// stall there is the transient of a warm start, which FP64 values would not
+// shorten).  A switch decided after a walk is first confirmed by a full-table
+// FP32 improvement: walks that settled in local minima of the table are
+// caught while sweeps are still cheap.
+struct SwitchRule {
+    double tol;
+    double best = INFINITY;
+    int stall = 0, confirms = 0;
+    bool confirming = false;
+
+    // Returns 1 to switch, 2 to run a confirming full tabulation next, 0 to go on.
+    int step(double res, bool last_was_walk)
+    {
+        if (res < best * 0.999) { best = res; stall = 0; } else ++stall;
+        bool want = res < tol || (stall >= 3 && res < kStallZone * tol) || stall >= kStallFar;
+        if (confirming) {
+            // the confirming full table moved V: stay in FP32, stall count anew
+            confirming = false;
+            if (!want) { best = res; stall = 0; }
+        } else if (want && last_was_walk && confirms < kMaxConfirms) {
+            ++confirms;
+            confirming = true;
+            return 2;
+        }
+        return want ? 1 : 0;
+    }
+};
+
+int switch_to_fp64(dp_grid* g)
+{
+    int rc;
+    if ((rc = ensure_fp64(g))) return rc;
+    CK(launch_widen((const float*)g->V[g->cur], g->V64[g->cur64], (int)g->n_active, g->st));
+    g->fp64_values = true;
+    return reset_ctl(g);
+}
+
+// Policy iteration with GMRES evaluation (§3, Eq. (13)-(14) with the linear
+// system of the evaluation step solved by GMRES).  Every improvement sweep is
+// checked on the host before the evaluation is enqueued: the solve stops at
+// the first improvement that moves V by less than tol (after a walk, a
+// full-table improvement confirms it).
+int pi_gmres(dp_grid* g, const dp_solve_opts* o, const GmOpts& go, dp_solve_stats& S, SweepTimer& T, double& res,
+             bool& conv, long long& hist_n)
+{
+    int rc;
+    SwitchRule rule;
+    rule.tol = o->switch_tol > 0 ? o->switch_tol : 16.0 * 1.1920928955078125e-07 * g->M;
+    bool first_full = !o->warm;
+    int pending = 0;   // cycles whose tails wait for the next synchronisation
+    auto collect = [&]() {
+        for (int c = 0; c < pending; ++c) {
+            S.gmres_cycles += 1;
+            S.gmres_matvecs += g->h_gm[c].k;
+        }
+        pending = 0;
+    };
+    long long outer = 0;
+    while (outer < o->max_sweeps) {
+        const bool mix = store_of(g) == kStoreMix;
+        const bool full = first_full || !o->walk;
+        first_full = false;
+        if ((rc = clear_ring(g, 0, 1))) return rc;
+        CK(T.begin(mix ? kTImp64 : kTImp));
+        const int mode = full ? DP_SWEEP_IMPROVE_FULL : DP_SWEEP_IMPROVE_WALK;
+        if (mix) CK(enqueue_polish_improve(g, mode, g->cur64, 0, 0, o->tol));
+        else CK(enqueue_sweep(g, mode, 0, 0, o->tol));
+        CK(T.end());
+        S.launches += 1;
+        if ((rc = fetch(g, 0, 1))) return rc;
+        CK(T.collect());
+        collect();
+        res = ring_value(g, 0);
+        if (o->history && hist_n < o->history_capacity) o->history[hist_n] = res;
+        ++hist_n;
+        if (mix) ++S.sweeps_improve_fp64;
+        else ++S.sweeps_improve;
+        ++outer;
+        advance(g, 1);
+        if (g->h_ctl->nonfinite) break;
+        if (res < o->tol) {
+            if (!full) {
+                first_full = true;   // a converged walk is confirmed by a full tabulation
+                continue;
+            }
+            conv = true;
+            break;
+        }
+        if (g->fp32 && !mix && o->polish) {
+            const int act = rule.step(res, !full);
+            if (act == 1) {
+                if ((rc = switch_to_fp64(g))) return rc;
+                S.switch_outer = outer;
+                continue;            // the FP64 phase starts with an improvement
+            }
+            if (act == 2) first_full = true;
+        }
+        for (int c = 0; c < go.cycles; ++c) {
+            CK(T.begin(mix ? kTEval64 : kTEval));
+            if (c > 0) {
+                // the residual of the corrected value needs its image T_f(V)
+                CK(enqueue_sweep(g, DP_SWEEP_EVAL, 0, 0, o->tol));
+                advance(g, 1);
+                if (mix) ++S.sweeps_eval_fp64;
+                else ++S.sweeps_eval;
+                S.launches += 1;
+            }
+            CK(enqueue_gmres(g, go, pending));
+            CK(T.end());
+            ++pending;
+            S.launches += gmres_launches(go);
+        }
+    }
+    CK(cudaStreamSynchronize(g->st));
+    CK(T.collect());
+    collect();
+    return DP_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -942,6 +1198,8 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
 {
     if (!g || !o) return fail(DP_EINVAL, "NULL argument");
     if (o->max_sweeps < 0 || o->n_eval < 0 || !(o->tol >= 0)) return fail(DP_EINVAL, "bad options");
+    if (o->eval_solver != DP_EVAL_JACOBI && o->eval_solver != DP_EVAL_GMRES)
+        return fail(DP_EINVAL, "unknown eval_solver %d", o->eval_solver);
     if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
     double t0 = now_ms();
     dp_solve_stats S;
@@ -950,23 +1208,27 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
     T.on = o->time_kernels != 0;
     T.st = g->st;
     int rc;
+    GmOpts go{};
+    const bool gmres = o->eval_solver == DP_EVAL_GMRES;
+    if (gmres && ((rc = gm_options(o, go)) || (rc = ensure_gmres(g, go.m)))) return rc;
     if (!o->warm && (rc = zero_value(g))) return rc;
     if ((rc = reset_ctl(g))) return rc;
 
     const long long per = 1 + o->n_eval;                 // sweeps per outer iteration
     const long long per_chunk = std::max<long long>(1, kMaxChunk / per / 4);
-    double switch_tol = o->switch_tol > 0 ? o->switch_tol : 16.0 * 1.1920928955078125e-07 * g->M;
+    SwitchRule rule;
+    rule.tol = o->switch_tol > 0 ? o->switch_tol : 16.0 * 1.1920928955078125e-07 * g->M;
     long long outer = 0, t = 0;    // outer iterations and sweeps of the current phase
-    double res = INFINITY, best = INFINITY;
-    int stall = 0, confirms = 0;
-    bool conv = false, first_full = !o->warm, switch_confirming = false;
+    double res = INFINITY;
+    bool conv = false, first_full = !o->warm;
     long long hist_n = 0;
     S.switch_outer = -1;
+    if (gmres && (rc = pi_gmres(g, o, go, S, T, res, conv, hist_n))) return rc;
     auto record = [&](long long t0, long long n_imp) {
         for (long long q = 0; q < n_imp; ++q, ++hist_n)
             if (o->history && hist_n < o->history_capacity) o->history[hist_n] = ring_value(g, t0 + q * per);
     };
-    while (outer < o->max_sweeps) {
+    while (!gmres && outer < o->max_sweeps) {
         const bool mix = store_of(g) == kStoreMix;
         long long n_out = std::min<long long>(per_chunk, o->max_sweeps - outer);
         if (g->fp32 && !mix && o->polish) n_out = 1;     // watch for the FP32 stall each step
@@ -1036,33 +1298,15 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
             if ((rc = reset_ctl(g))) return rc;
             continue;
         }
-        // FP32 -> FP64 switch once the FP32 residual is small, or stalls: 3
-        // improvements without gain near the FP32 floor, 30 far above it (a
-        // short stall there is the transient of a warm start, which FP64
-        // values would not shorten).  A switch decided after a walk is first
-        // confirmed by a full-table FP32 improvement: walks that settled in
-        // local minima of the table are caught while sweeps are still cheap.
+        // FP32 -> FP64 switch (SwitchRule)
         if (g->fp32 && !mix && o->polish) {
-            if (res < best * 0.999) { best = res; stall = 0; } else ++stall;
-            bool want = res < switch_tol || (stall >= 3 && res < kStallZone * switch_tol) || stall >= kStallFar;
-            if (switch_confirming) {
-                // the confirming full table moved V: stay in FP32, stall count anew
-                switch_confirming = false;
-                if (!want) { best = res; stall = 0; }
-            } else if (want && last_was_walk && confirms < kMaxConfirms) {
-                ++confirms;
-                switch_confirming = true;
-                first_full = true;
-                want = false;
-            }
-            if (want) {
+            const int act = rule.step(res, last_was_walk);
+            if (act == 2) first_full = true;
+            if (act == 1) {
                 advance(g, t);
                 t = 0;
-                if ((rc = ensure_fp64(g))) return rc;
-                CK(launch_widen((const float*)g->V[g->cur], g->V64[g->cur64], (int)g->n_active, g->st));
-                g->fp64_values = true;
+                if ((rc = switch_to_fp64(g))) return rc;
                 S.switch_outer = outer;
-                if ((rc = reset_ctl(g))) return rc;
             }
         }
     }
@@ -1070,8 +1314,8 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
     S.history_count = std::min<long long>(hist_n, o->history ? o->history_capacity : 0);
     S.residual = res;
     S.converged = conv && !g->h_ctl->nonfinite;
-    S.node_updates = (S.sweeps_improve + S.sweeps_eval + S.sweeps_improve_fp64 + S.sweeps_eval_fp64) *
-                     updates_per_sweep(g);
+    S.node_updates = (S.sweeps_improve + S.sweeps_eval + S.sweeps_improve_fp64 + S.sweeps_eval_fp64 +
+                      S.gmres_matvecs) * updates_per_sweep(g);
     S.ms_improve = T.ms[kTImp];
     S.ms_eval = T.ms[kTEval];
     S.ms_improve_fp64 = T.ms[kTImp64];
@@ -1081,6 +1325,73 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
     if ((rc = finish_nonfinite(g))) return rc;
     if (!S.converged)
         return fail(DP_ENOCONV, "no convergence within %lld improvement sweeps (residual %g)",
+                    (long long)o->max_sweeps, res);
+    return DP_OK;
+}
+
+int dp_policy_evaluate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
+{
+    if (!g || !o) return fail(DP_EINVAL, "NULL argument");
+    if (o->max_sweeps < 0 || !(o->tol >= 0)) return fail(DP_EINVAL, "bad options");
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
+    const double t0 = now_ms();
+    int rc;
+    GmOpts go{};
+    if ((rc = gm_options(o, go)) || (rc = ensure_gmres(g, go.m))) return rc;
+    dp_solve_stats S;
+    memset(&S, 0, sizeof S);
+    S.switch_outer = -1;
+    SweepTimer T;
+    T.on = o->time_kernels != 0;
+    T.st = g->st;
+    if ((rc = reset_ctl(g))) return rc;
+    const bool mix = store_of(g) == kStoreMix;
+    if (g->fp32 && !g->feet_valid) {
+        CK(launch_feet(g->g32, g->code, g->feet_lo, g->feet_hi, g->d.dynamics, g->d.reduced, g->sm_count, g->st));
+        g->feet_valid = true;
+        S.launches += 1;
+    }
+    double res = INFINITY;
+    bool conv = false;
+    for (long long c = 0;; ++c) {
+        // V <- T_f(V): its change is the stopping test, and the new pair
+        // (V, T_f(V)) starts the next cycle
+        if ((rc = clear_ring(g, 0, 1))) return rc;
+        CK(T.begin(mix ? kTEval64 : kTEval));
+        CK(enqueue_sweep(g, DP_SWEEP_EVAL, 0, 0, o->tol));
+        CK(T.end());
+        S.launches += 1;
+        if ((rc = fetch(g, 0, 1))) return rc;
+        if (c > 0) {
+            S.gmres_cycles += 1;
+            S.gmres_matvecs += g->h_gm[0].k;
+        }
+        advance(g, 1);
+        if (mix) ++S.sweeps_eval_fp64;
+        else ++S.sweeps_eval;
+        res = ring_value(g, 0);
+        if (g->h_ctl->nonfinite) break;
+        if (res < o->tol) {
+            conv = true;
+            break;
+        }
+        if (c >= o->max_sweeps) break;
+        CK(T.begin(mix ? kTEval64 : kTEval));
+        CK(enqueue_gmres(g, go, 0));
+        CK(T.end());
+        S.launches += gmres_launches(go);
+    }
+    CK(T.collect());
+    S.residual = res;
+    S.converged = conv && !g->h_ctl->nonfinite;
+    S.node_updates = (S.sweeps_eval + S.sweeps_eval_fp64 + S.gmres_matvecs) * updates_per_sweep(g);
+    S.ms_eval = T.ms[kTEval];
+    S.ms_eval_fp64 = T.ms[kTEval64];
+    S.ms_wall = now_ms() - t0;
+    if (stats) *stats = S;
+    if ((rc = finish_nonfinite(g))) return rc;
+    if (!S.converged)
+        return fail(DP_ENOCONV, "policy evaluation: no convergence within %lld GMRES cycles (residual %g)",
                     (long long)o->max_sweeps, res);
     return DP_OK;
 }

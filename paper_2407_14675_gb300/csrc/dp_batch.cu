@@ -996,6 +996,7 @@ int dp_batch_policy_iterate(dp_batch* b, const dp_solve_opts* o, dp_solve_stats*
     if (!b || !o) return bfail(DP_EINVAL, "NULL argument");
     if (o->max_sweeps < 1 || o->n_eval < 0 || o->n_eval > 1024 || !(o->tol >= 0))
         return bfail(DP_EINVAL, "bad options (max_sweeps >= 1, 0 <= n_eval <= 1024, tol >= 0)");
+    if (o->eval_solver != DP_EVAL_JACOBI) return bfail(DP_EINVAL, "batched policy iteration evaluates by Jacobi sweeps only");
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(DP_ECUDA, "cudaSetDevice failed");
     const double t0 = now_ms();
     int rc;

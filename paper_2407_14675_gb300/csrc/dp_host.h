@@ -83,4 +83,57 @@ cudaError_t launch_prolong(const Geo<double>& gs, const void* Vs, int src_fp32, 
                            int periodic, const Geo<double>& gd, void* Vd, int fp32_dst, uint16_t* Cd, double Md,
                            cudaStream_t st);
 
+// Policy evaluation by restarted GMRES (§3: with the control frozen, Eq. (13)
+// is the sparse linear system (I - beta W_f) V = b).  One cycle starts from
+// the residual r0 = T_f(V) - V of the current value, builds an m-step Arnoldi
+// basis of A = I - beta W_f (classical Gram-Schmidt, optionally twice), and
+// adds the minimal-residual correction to V.  Basis vectors are stored
+// unnormalised with their scales; the small Hessenberg problem lives on the
+// device and is updated by the last block of each launch.
+constexpr int kGmMaxRestart = 64;
+constexpr int kGmLd = kGmMaxRestart + 2;     // columns of the per-block partial sums
+
+struct GmCtl {
+    double H[kGmMaxRestart + 1][kGmMaxRestart];   // Hessenberg, rotated in place
+    double cs[kGmMaxRestart], sn[kGmMaxRestart];  // Givens rotations
+    double gv[kGmMaxRestart + 1];                 // rotated right-hand side
+    double scale[kGmMaxRestart + 1];              // 1 / ||Q_i|| of the stored vectors
+    double coef[kGmMaxRestart + 1];               // coefficients of raw Q_i for the next update
+    double beta0;                                 // ||r0||_2
+    double rel;                                   // residual estimate / beta0
+    int k;                                        // Arnoldi steps taken in this cycle
+    int done;                                     // the cycle has its correction in coef
+    unsigned counter;                             // blocks finished (last-block reductions)
+    int pad;
+};
+
+template <typename G, typename VT>
+struct GmArgs {
+    Geo<G> g;                        // grid geometry with M = 0 (the linear part has no penalty)
+    VT* Q;                           // (m + 1) vectors of ldq entries
+    long long ldq;
+    int m;                           // Arnoldi steps per cycle (1..kGmMaxRestart)
+    int reorth;                      // 1: Gram-Schmidt twice
+    double rtol;                     // a cycle ends once ||r|| <= rtol ||r0||
+    const uint16_t* code;            // frozen policy
+    const unsigned long long* feet_lo;   // frozen feet (FP32 geometry)
+    const unsigned* feet_hi;
+    double* partial;                 // max_blocks x kGmLd
+    int max_blocks;
+    GmCtl* gctl;
+    Ctl* ctl;                        // the grid's control block (non-finite flag)
+    int dyn;
+    int reduced;
+    int sm_count;
+    cudaStream_t stream;
+};
+
+// One GMRES cycle: reads V_in and V_next = T_f(V_in), writes V_next = V_in + e.
+cudaError_t gm_cycle(const GmArgs<float, float>& a, const float* Vin, float* Vnext);
+cudaError_t gm_cycle(const GmArgs<float, float>& a, const double* Vin, double* Vnext);
+cudaError_t gm_cycle(const GmArgs<double, double>& a, const double* Vin, double* Vnext);
+// Frozen feet of the resident policy (FP32 geometry), as an improvement sweep stores them.
+cudaError_t launch_feet(const Geo<float>& g, const uint16_t* code, unsigned long long* feet_lo, unsigned* feet_hi,
+                        int dyn, int reduced, int sm_count, cudaStream_t st);
+
 }  // namespace dpk

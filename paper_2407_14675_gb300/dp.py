@@ -21,6 +21,8 @@ DP_FP64, DP_FP32 = 0, 1
 DP_DYN_ORBIT, DP_DYN_UNIT_SPEED, DP_DYN_POLAR = 0, 1, 2
 DP_CODE_OFF = 65535
 DP_SWEEP_VI, DP_SWEEP_IMPROVE_FULL, DP_SWEEP_IMPROVE_WALK, DP_SWEEP_EVAL = 0, 1, 2, 3
+DP_EVAL_JACOBI, DP_EVAL_GMRES = 0, 1
+DP_GMRES_MAX_RESTART = 64
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libdp.so")
@@ -70,6 +72,11 @@ class dp_solve_opts(C.Structure):
         ("time_kernels", C.c_int32),
         ("history", C.POINTER(C.c_double)),
         ("history_capacity", C.c_int64),
+        ("eval_solver", C.c_int32),
+        ("gmres_restart", C.c_int32),
+        ("gmres_cycles", C.c_int32),
+        ("gmres_reorth", C.c_int32),
+        ("gmres_rtol", C.c_double),
     ]
 
 
@@ -92,6 +99,8 @@ class dp_solve_stats(C.Structure):
         ("launches", C.c_int64),
         ("history_count", C.c_int64),
         ("switch_outer", C.c_int64),
+        ("gmres_cycles", C.c_int64),
+        ("gmres_matvecs", C.c_int64),
     ]
 
     def asdict(self):
@@ -201,6 +210,7 @@ def load(path: Optional[str] = None):
         "dp_batch_get_info": [_P, _P, _P, _P, _P, _P, _P],
         "dp_batch_set_items": [_P, C.c_int32, C.c_int32],
         "dp_batch_autotune": [_P, _P, _P],
+        "dp_policy_evaluate": [_P, C.POINTER(dp_solve_opts), C.POINTER(dp_solve_stats)],
         "dp_batch_policy_iterate": [_P, C.POINTER(dp_solve_opts), C.POINTER(dp_solve_stats), _P],
         "dp_batch_sweep": [_P, C.c_int32, _P, _dp],
         "dp_batch_set_value": [_P, C.c_int32, _P, C.c_int64],
@@ -331,12 +341,16 @@ def dp_bellman_sweep_noalloc(desc: dp_grid_desc, mode: int, V_in: int, V_out: in
 
 
 def make_opts(tol=1e-6, max_sweeps=100000, n_eval=20, walk=1, warm=0, polish=1, switch_tol=0.0,
-              time_kernels=0, history=None) -> dp_solve_opts:
+              time_kernels=0, history=None, eval_solver=DP_EVAL_JACOBI, gmres_restart=0, gmres_cycles=0,
+              gmres_reorth=0, gmres_rtol=0.0) -> dp_solve_opts:
     """Solver options; history: optional float64 numpy array that receives the
-    residual of every stopping test (kept alive by the caller)."""
+    residual of every stopping test (kept alive by the caller).  eval_solver
+    DP_EVAL_GMRES evaluates each policy by GMRES (gmres_*: 0 = default)."""
     o = dp_solve_opts()
     o.tol, o.max_sweeps, o.n_eval, o.walk, o.warm = tol, max_sweeps, n_eval, walk, warm
     o.polish, o.switch_tol, o.time_kernels = polish, switch_tol, time_kernels
+    o.eval_solver, o.gmres_restart, o.gmres_cycles = eval_solver, gmres_restart, gmres_cycles
+    o.gmres_reorth, o.gmres_rtol = gmres_reorth, gmres_rtol
     if history is not None:
         o.history = history.ctypes.data_as(C.POINTER(C.c_double))
         o.history_capacity = len(history)
@@ -352,6 +366,12 @@ def dp_value_iterate(grid: int, opts: dp_solve_opts):
 def dp_policy_iterate(grid: int, opts: dp_solve_opts):
     s = dp_solve_stats()
     rc = _check(load().dp_policy_iterate(grid, C.byref(opts), C.byref(s)), allow=(DP_OK, DP_ENOCONV))
+    return rc, s
+
+
+def dp_policy_evaluate(grid: int, opts: dp_solve_opts):
+    s = dp_solve_stats()
+    rc = _check(load().dp_policy_evaluate(grid, C.byref(opts), C.byref(s)), allow=(DP_OK, DP_ENOCONV))
     return rc, s
 
 
@@ -434,6 +454,9 @@ class Grid:
 
     def policy_iterate(self, **kw):
         return dp_policy_iterate(self.h, make_opts(**kw))
+
+    def policy_evaluate(self, **kw):
+        return dp_policy_evaluate(self.h, make_opts(**kw))
 
     def feedback(self, states, tau):
         return dp_feedback_control(self.h, states, tau)

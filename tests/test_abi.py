@@ -29,7 +29,8 @@ def test_header_declares_the_boundary():
     names = _declared()
     for n in ["dp_grid_create", "dp_grid_destroy", "dp_value_iterate", "dp_policy_iterate",
               "dp_feedback_control", "dp_simulate_closed_loop", "dp_get_value", "dp_get_policy",
-              "dp_last_error", "dp_batch_create", "dp_batch_policy_iterate", "dp_batch_autotune"]:
+              "dp_last_error", "dp_batch_create", "dp_batch_policy_iterate", "dp_batch_autotune",
+              "dp_policy_evaluate"]:
         assert n in names
 
 

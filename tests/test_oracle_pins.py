@@ -519,3 +519,61 @@ def test_example2_drag_coefficient_and_deceleration():
     dE = y[1] * (f[1] - f0[1]) + y[2] * (f[2] - f0[2])
     assert dE == pytest.approx(-C * (y[1] ** 3 + y[2] ** 3), rel=1e-6)
     assert (o.dynamics_drag(y, 0.3, 0.0) == o.dynamics(y, 0.3)).all()
+
+
+# ------------------------------------------- exact policy evaluation (Eq. 13) --
+
+def test_policy_system_reproduces_the_evaluation_sweep():
+    # the assembled rows are the evaluation sweep written as V -> b + beta W V:
+    # a dropped penalty, a transposed weight or a misplaced discount breaks it
+    for p, seed in [(W.config1(13).replace(n=(9, 9, 9, 9)), 1), (W.config2(13), 2), (W.example1(n=(12, 7, 7, 8)), 3)]:
+        o = oracle.Oracle(p)
+        codes = W.random_codes(p, seed)
+        if p.off_control:
+            codes[::5] = oracle.CODE_OFF
+        V = W.smooth_value(p, seed + 10)
+        Wm, b = o.policy_system(codes)
+        got = b + o.s.beta * (Wm @ V)
+        want = o.sweep(V, mode=oracle.EVAL, codes=codes)[0]
+        act = o.active.astype(bool)
+        assert np.abs(got - want)[act].max() <= 1e-12 * np.abs(want).max()
+        # rows are convex combinations or empty
+        rs = np.asarray(Wm.sum(axis=1)).ravel()
+        assert np.all((np.abs(rs - 1.0) < 1e-12) | (rs == 0.0))
+
+
+def test_exact_evaluation_closed_form_1d():
+    # x' = 1 on a line with dt = h: every foot lands one node to the right.
+    # Left of the target the value is the discounted time to go,
+    # dt (1 - beta^d) / (1 - beta); right of it the trajectory leaves the box
+    # after s = n - 1 - i steps and pays the penalty M one step later.
+    M = 3.0
+    p = W.unit_speed_1d().replace(penalty_M=M)
+    o = oracle.Oracle(p)
+    v = o.evaluate_exact(np.zeros(p.nodes, np.uint16)).reshape(p.n)
+    n, t, dt, beta = p.n[0], 8, p.dt, p.beta
+    for i in range(n):
+        if i < t:
+            want = dt * (1 - beta ** (t - i)) / (1 - beta)
+        elif i == t:
+            want = 0.0
+        else:
+            s = n - 1 - i
+            want = dt * (1 - beta ** s) / (1 - beta) + beta ** s * (dt + beta * M)
+        assert np.allclose(v[i], want, rtol=0, atol=1e-13), (i, v[i, 0, 0, 0], want)
+
+
+def test_exact_evaluation_is_the_fixed_point_of_the_sweep():
+    # the evaluated value is the unique fixed point of the frozen-policy sweep
+    # (a beta-contraction), and Jacobi sweeps approach it at rate beta
+    p = W.config1(13).replace(n=(11, 9, 9, 9))
+    o = oracle.Oracle(p)
+    codes = W.random_codes(p, 5)
+    v = o.evaluate_exact(codes)
+    v1 = o.sweep(v, mode=oracle.EVAL, codes=codes)[0]
+    assert np.abs(v1 - v).max() <= 1e-12 * o.M
+    V = np.zeros(p.nodes)
+    e0 = np.abs(V - v).max()
+    for _ in range(50):
+        V = o.sweep(V, mode=oracle.EVAL, codes=codes)[0]
+    assert np.abs(V - v).max() <= p.beta ** 50 * e0 * (1 + 1e-9)
