@@ -17,6 +17,11 @@
 // block into a partial row, and the last block to finish adds the rows in a
 // fixed order (the result does not depend on block scheduling) and does the
 // O(m) Hessenberg and Givens work on one thread.  No block waits for another.
+//
+// Element-wise work runs in the basis precision VT (FP32 on FP32 grids: the
+// FP64 pipe of this GPU is a small fraction of its FP32 pipe).  Each thread's
+// partial sums cover kGmS products; they are widened to FP64 for the warp,
+// block and grid sums and for the Hessenberg problem.
 #include "dp_sweep.cuh"
 
 namespace dpk {
@@ -126,17 +131,17 @@ gm_start_kernel(const VV* __restrict__ Vin, const VV* __restrict__ Vnext, VT* __
     sums_zero(S);
     const int tiles = (n + kGmTile - 1) / kGmTile;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        double nrm = 0.0;
+        VT nrm = (VT)0;
 #pragma unroll
         for (int s = 0; s < kGmS; ++s) {
             const int j = tile * kGmTile + s * kGmBlock + threadIdx.x;
             if (j < n) {
-                const VT r = (VT)((double)Vnext[j] - (double)Vin[j]);
+                const VT r = (VT)(Vnext[j] - Vin[j]);
                 q0[j] = r;
-                nrm += (double)r * (double)r;
+                nrm += r * r;
             }
         }
-        sums_add(S, 0, nrm);
+        sums_add(S, 0, (double)nrm);
     }
     if (!sums_finish(S, 1, partial, gc, red)) return;
     if (threadIdx.x == 0) {
@@ -165,7 +170,7 @@ gm_arnoldi_kernel(const __grid_constant__ Geo<G> g, VT* __restrict__ Q, long lon
     sums_zero(S);
     const VT* x = Q + (size_t)k * ldq;
     VT* w = Q + (size_t)(k + 1) * ldq;
-    const double sk = gc->scale[k];
+    const VT sk = (VT)gc->scale[k];
     const int n = g.n_nodes;
     const int tiles = (n + kGmTile - 1) / kGmTile;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -176,28 +181,28 @@ gm_arnoldi_kernel(const __grid_constant__ Geo<G> g, VT* __restrict__ Q, long lon
             const int j = j0 + s * kGmBlock;
             wv[s] = (VT)0;
             if (j < n) {
-                double y;
+                VT y;
                 if constexpr (std::is_same<G, float>::value) {
                     // the feet are read once per product: evict-first
                     const FootWord fw{__ldcs(&feet_lo[j]), __ldcs(&feet_hi[j])};
-                    y = (double)apply_a_feet<REDUCED, DYN>(g, x, j, fw, code);
+                    y = apply_a_feet<REDUCED, DYN>(g, x, j, fw, code);
                 } else {
                     y = apply_a_node<REDUCED, DYN>(g, x, j, code);
                 }
-                wv[s] = (VT)(sk * y);
+                wv[s] = sk * y;
                 w[j] = wv[s];
             }
         }
 #pragma unroll 2
         for (int i = 0; i <= k; ++i) {
             const VT* qi = Q + (size_t)i * ldq;
-            double d = 0.0;
+            VT d = (VT)0;
 #pragma unroll
             for (int s = 0; s < kGmS; ++s) {
                 const int j = j0 + s * kGmBlock;
-                if (j < n) d += (double)qi[j] * (double)wv[s];
+                if (j < n) d += qi[j] * wv[s];
             }
-            sums_add(S, i, d);
+            sums_add(S, i, (double)d);
         }
     }
     if (!sums_finish(S, k + 1, partial, gc, red)) return;
@@ -264,54 +269,52 @@ gm_update_kernel(VT* __restrict__ Q, long long ldq, int n, int k, int m, double 
     if (*(volatile int*)&gc->done) return;
     __shared__ BlockSums S;
     __shared__ double red[kGmLd];
-    __shared__ double s_coef[kGmMaxRestart + 1];
-    for (int i = threadIdx.x; i <= k; i += kGmBlock) s_coef[i] = gc->coef[i];
+    __shared__ VT s_coef[kGmMaxRestart + 1];
+    for (int i = threadIdx.x; i <= k; i += kGmBlock) s_coef[i] = (VT)gc->coef[i];
     sums_zero(S);
     VT* w = Q + (size_t)(k + 1) * ldq;
     const int tiles = (n + kGmTile - 1) / kGmTile;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int j0 = tile * kGmTile + threadIdx.x;
-        double wd[kGmS];
+        VT wv[kGmS];
 #pragma unroll
         for (int s = 0; s < kGmS; ++s) {
             const int j = j0 + s * kGmBlock;
-            wd[s] = j < n ? (double)w[j] : 0.0;
+            wv[s] = j < n ? w[j] : (VT)0;
         }
 #pragma unroll 2
         for (int i = 0; i <= k; ++i) {
             const VT* qi = Q + (size_t)i * ldq;
-            const double c = s_coef[i];
+            const VT c = s_coef[i];
 #pragma unroll
             for (int s = 0; s < kGmS; ++s) {
                 const int j = j0 + s * kGmBlock;
-                if (j < n) wd[s] -= c * (double)qi[j];
+                if (j < n) wv[s] -= c * qi[j];
             }
         }
-        VT wv[kGmS];
-        double nrm = 0.0;
+        VT nrm = (VT)0;
 #pragma unroll
         for (int s = 0; s < kGmS; ++s) {
             const int j = j0 + s * kGmBlock;
-            wv[s] = (VT)wd[s];
             if (j < n) {
                 w[j] = wv[s];
-                nrm += (double)wv[s] * (double)wv[s];
+                nrm += wv[s] * wv[s];
             }
         }
         if constexpr (DOTS) {
 #pragma unroll 2
             for (int i = 0; i <= k; ++i) {
                 const VT* qi = Q + (size_t)i * ldq;
-                double d = 0.0;
+                VT d = (VT)0;
 #pragma unroll
                 for (int s = 0; s < kGmS; ++s) {
                     const int j = j0 + s * kGmBlock;
-                    if (j < n) d += (double)qi[j] * (double)wv[s];
+                    if (j < n) d += qi[j] * wv[s];
                 }
-                sums_add(S, i, d);
+                sums_add(S, i, (double)d);
             }
         } else {
-            sums_add(S, 0, nrm);
+            sums_add(S, 0, (double)nrm);
         }
     }
     if (!sums_finish(S, DOTS ? k + 1 : 1, partial, gc, red)) return;
@@ -328,43 +331,41 @@ gm_update_kernel(VT* __restrict__ Q, long long ldq, int n, int k, int m, double 
     }
 }
 
-// V_next = V_in + sum_i coef_i Q_i over the cycle's k columns.
+// V_next = V_in + sum_i coef_i Q_i over the cycle's k columns; the
+// correction is summed in the basis precision and added once to V_in.
 template <typename VV, typename VT>
 __global__ void __launch_bounds__(kGmBlock)
 gm_apply_kernel(const VV* __restrict__ Vin, VV* __restrict__ Vnext, const VT* __restrict__ Q, long long ldq, int n,
                 const GmCtl* __restrict__ gc, Ctl* __restrict__ ctl)
 {
-    __shared__ double s_coef[kGmMaxRestart + 1];
+    __shared__ VT s_coef[kGmMaxRestart + 1];
     const int kk = gc->k;
-    for (int i = threadIdx.x; i < kk; i += kGmBlock) s_coef[i] = gc->coef[i];
+    for (int i = threadIdx.x; i < kk; i += kGmBlock) s_coef[i] = (VT)gc->coef[i];
     __syncthreads();
     bool bad = false;
     const int tiles = (n + kGmTile - 1) / kGmTile;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int j0 = tile * kGmTile + threadIdx.x;
-        double v[kGmS];
+        VT e[kGmS];
 #pragma unroll
-        for (int s = 0; s < kGmS; ++s) {
-            const int j = j0 + s * kGmBlock;
-            v[s] = j < n ? (double)Vin[j] : 0.0;
-        }
+        for (int s = 0; s < kGmS; ++s) e[s] = (VT)0;
 #pragma unroll 2
         for (int i = 0; i < kk; ++i) {
             const VT* qi = Q + (size_t)i * ldq;
-            const double c = s_coef[i];
+            const VT c = s_coef[i];
 #pragma unroll
             for (int s = 0; s < kGmS; ++s) {
                 const int j = j0 + s * kGmBlock;
-                if (j < n) v[s] += c * (double)qi[j];
+                if (j < n) e[s] += c * qi[j];
             }
         }
 #pragma unroll
         for (int s = 0; s < kGmS; ++s) {
             const int j = j0 + s * kGmBlock;
             if (j < n) {
-                const VV o = (VV)v[s];
+                const VV o = Vin[j] + (VV)e[s];
                 Vnext[j] = o;
-                bad = bad || !isfinite((double)o);
+                bad = bad || !isfinite(o);
             }
         }
     }
