@@ -262,6 +262,19 @@ def extra_legs(args, dp, W, torch, g1, p1):
         secs = time.perf_counter() - t0
         out["vi_fp64_17x4"] = {"seconds": secs, "converged": bool(s0.converged), "sweeps": s0.sweeps_vi,
                                "residual": s0.residual, "node_updates_per_s": s0.node_updates / secs}
+        # FP64 policy iteration on the same grid, each policy evaluated by 20
+        # Jacobi sweeps or by GMRES
+        pi = {}
+        for name, kw in (("jacobi20", {"n_eval": 20}),
+                         ("gmres", {"eval_solver": dp.DP_EVAL_GMRES, "gmres_restart": args.gmres_restart_fp64})):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, s0 = g0.policy_iterate(tol=1e-8, max_sweeps=args.solve_max, polish=0, **kw)
+            torch.cuda.synchronize()
+            pi[name] = {"seconds": time.perf_counter() - t0, "converged": bool(s0.converged),
+                        "improvements": s0.sweeps_improve, "evaluation_sweeps": s0.sweeps_eval,
+                        "matvecs": s0.gmres_matvecs}
+        out["pi_fp64_17x4"] = pi
     res = {}
     for walk in (1, 0):
         torch.cuda.synchronize()
@@ -288,11 +301,12 @@ def _kepler_a_e(x, mu):
 
 def example1_leg(args, dp, W, torch):
     """The paper's Example 1 (§4): 110 x 30 x 30 x 30 polar grid, running cost
-    of Eq. (11), 72 angles + thrust off, FP64 policy iteration to 1e-7; then
-    the closed loop from the circular orbit at 6978 km for 1e6 s, sampled
-    every 2,000 s: when the semi-major axis comes within 1 km of 7000 km,
-    when the thrust switches off for good, and the final orbit; and the same
-    on the system with drag of Example 2."""
+    of Eq. (11), 72 angles + thrust off, FP64 policy iteration to 1e-7, with
+    each policy evaluated by GMRES (the paper's method) and, for comparison,
+    by 20 Jacobi sweeps; then the closed loop from the circular orbit at
+    6978 km for 1e6 s, sampled every 2,000 s: when the semi-major axis comes
+    within 1 km of 7000 km, when the thrust switches off for good, and the
+    final orbit; and the same on the system with drag of Example 2."""
     p = W.example1()
     out = {"grid": list(p.n), "nodes": p.nodes, "dt_s": p.dt, "tol": p.tol}
     st = int(torch.cuda.current_stream().cuda_stream)
@@ -302,9 +316,22 @@ def example1_leg(args, dp, W, torch):
         rc, s = g.policy_iterate(tol=p.tol, max_sweeps=args.solve_max, n_eval=p.n_eval, polish=0)
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
+        out["solve_jacobi"] = {"seconds": secs, "converged": bool(s.converged), "residual": s.residual,
+                               "improvements": s.sweeps_improve, "evaluation_sweeps": s.sweeps_eval,
+                               "node_updates_per_s": s.node_updates / secs}
+        v_jacobi = g.get_value()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, s = g.policy_iterate(tol=p.tol, max_sweeps=args.solve_max, polish=0, eval_solver=dp.DP_EVAL_GMRES,
+                                 gmres_restart=args.gmres_restart_fp64)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        v = g.get_value()
         out["solve"] = {"seconds": secs, "converged": bool(s.converged), "residual": s.residual,
-                        "improvements": s.sweeps_improve, "evaluations": s.sweeps_eval,
-                        "node_updates_per_s": s.node_updates / secs}
+                        "evaluation": "GMRES(%d)" % args.gmres_restart_fp64, "improvements": s.sweeps_improve,
+                        "gmres_cycles": s.gmres_cycles, "matvecs": s.gmres_matvecs,
+                        "max_rel_diff_to_jacobi_solution": float(np.abs(v - v_jacobi).max() / np.abs(v_jacobi).max()),
+                        "speedup_over_jacobi": out["solve_jacobi"]["seconds"] / secs}
         for name, drag in (("closed_loop", 0.0), ("closed_loop_with_drag", W.example2_drag())):
             # Example 2 of §4: the same feedback flown on a system with drag
             y = W.example1_start(6978.0)[None, :]
@@ -551,6 +578,19 @@ def run_ours(args, world, rank, local):
                             "eval_increments": st.ms_eval_fp64},
                  "residual_trace": {int(k): float(h[k]) for k in marks if 0 <= k < len(h)},
                  "start": "cold (V = 0, full tabulation first)"}
+    solve_gmres = None
+    if args.solve and rank == 0:
+        # the same cold solve with each policy evaluated by GMRES on FP32 vectors
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = g.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, polish=1, warm=0, time_kernels=1,
+                                  eval_solver=dp.DP_EVAL_GMRES, gmres_restart=args.gmres_restart_fp32)
+        torch.cuda.synchronize()
+        solve_gmres = {"seconds": time.perf_counter() - t0, "converged": bool(st.converged),
+                       "residual": st.residual, "evaluation": "GMRES(%d)" % args.gmres_restart_fp32,
+                       "improvements": st.sweeps_improve + st.sweeps_improve_fp64, "matvecs": st.gmres_matvecs,
+                       "gpu_ms": {"improve": st.ms_improve + st.ms_improve_fp64,
+                                  "gmres": st.ms_eval + st.ms_eval_fp64}}
     cascade = None
     if args.solve and rank == 0:
         # coarse to fine: the same problem on 31^4 to 1e-6, its solution
@@ -619,6 +659,7 @@ def run_ours(args, world, rank, local):
                       "mix, %.1f s" % par_info["seconds"]},
         "time_to_tol": solve,
         "time_to_tol_coarse_to_fine": cascade,
+        "time_to_tol_gmres": solve_gmres,
         "warm_start": warm,
         "batch": batch,
         "other_solves": extra,
@@ -646,6 +687,8 @@ def main():
     ap.add_argument("--extra", type=int, default=1, help="17^4 FP64 VI; walk vs full tabulation")
     ap.add_argument("--cpu-parallel", type=int, default=1, help="also time the oracle on every host core")
     ap.add_argument("--example1", type=int, default=1, help="the paper's Example 1 solve and closed loop")
+    ap.add_argument("--gmres-restart-fp64", type=int, default=60, help="GMRES restart length, FP64 grids")
+    ap.add_argument("--gmres-restart-fp32", type=int, default=20, help="GMRES restart length, 61^4 FP32 grid")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-fp64-sample", type=int, default=4)
     args = ap.parse_args()

@@ -28,7 +28,8 @@ namespace dpk {
 namespace {
 
 constexpr int kGmBlock = 256;
-constexpr int kGmS = 4;                     // nodes per thread and tile
+constexpr int kGmS = 4;                     // nodes per thread and tile (four consecutive
+                                            // nodes per thread in the streaming loops)
 constexpr int kGmTile = kGmBlock * kGmS;
 constexpr int kGmWarps = kGmBlock / 32;
 
@@ -88,6 +89,51 @@ __device__ bool sums_finish(BlockSums& S, int ncol, double* __restrict__ partial
     return true;
 }
 
+// Four consecutive entries j4..j4+3 of a vector (j4 a multiple of 4 and the
+// vector 16-byte aligned: one or two 16-byte accesses); entries at or past n
+// read as 0 and are not written.
+__device__ __forceinline__ void ld4(const float* p, float v[4])
+{
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double v[4])
+{
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float v[4])
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double v[4])
+{
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, int j4, int n, T v[4])
+{
+    if (j4 + 3 < n) {
+        ld4(p + j4, v);
+    } else {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) v[s] = j4 + s < n ? p[j4 + s] : (T)0;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void store4(T* p, int j4, int n, const T v[4])
+{
+    if (j4 + 3 < n) {
+        st4(p + j4, v);
+    } else {
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+            if (j4 + s < n) p[j4 + s] = v[s];
+    }
+}
+
 // (A x)_j = x_j - beta (W_f x)_j from node j's frozen foot (FP32 geometry).
 // A foot outside the box or the node set, and a target node, have no W row.
 template <bool REDUCED, int DYN>
@@ -131,16 +177,18 @@ gm_start_kernel(const VV* __restrict__ Vin, const VV* __restrict__ Vnext, VT* __
     sums_zero(S);
     const int tiles = (n + kGmTile - 1) / kGmTile;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int j4 = tile * kGmTile + kGmS * threadIdx.x;
+        VV a[kGmS], b[kGmS];
+        VT r[kGmS];
+        load4(Vin, j4, n, a);
+        load4(Vnext, j4, n, b);
         VT nrm = (VT)0;
 #pragma unroll
         for (int s = 0; s < kGmS; ++s) {
-            const int j = tile * kGmTile + s * kGmBlock + threadIdx.x;
-            if (j < n) {
-                const VT r = (VT)(Vnext[j] - Vin[j]);
-                q0[j] = r;
-                nrm += r * r;
-            }
+            r[s] = (VT)(b[s] - a[s]);
+            nrm += r[s] * r[s];
         }
+        store4(q0, j4, n, r);
         sums_add(S, 0, (double)nrm);
     }
     if (!sums_finish(S, 1, partial, gc, red)) return;
@@ -167,6 +215,7 @@ gm_arnoldi_kernel(const __grid_constant__ Geo<G> g, VT* __restrict__ Q, long lon
     if (*(volatile int*)&gc->done) return;
     __shared__ BlockSums S;
     __shared__ double red[kGmLd];
+    __shared__ __align__(16) VT s_w[kGmTile];
     sums_zero(S);
     const VT* x = Q + (size_t)k * ldq;
     VT* w = Q + (size_t)(k + 1) * ldq;
@@ -174,34 +223,37 @@ gm_arnoldi_kernel(const __grid_constant__ Geo<G> g, VT* __restrict__ Q, long lon
     const int n = g.n_nodes;
     const int tiles = (n + kGmTile - 1) / kGmTile;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int j0 = tile * kGmTile + threadIdx.x;
-        VT wv[kGmS];
+        // the product, nodes strided by the block so that the feet and the
+        // gathered corners of a warp are adjacent
 #pragma unroll
         for (int s = 0; s < kGmS; ++s) {
-            const int j = j0 + s * kGmBlock;
-            wv[s] = (VT)0;
+            const int j = tile * kGmTile + s * kGmBlock + threadIdx.x;
+            VT y = (VT)0;
             if (j < n) {
-                VT y;
                 if constexpr (std::is_same<G, float>::value) {
                     // the feet are read once per product: evict-first
                     const FootWord fw{__ldcs(&feet_lo[j]), __ldcs(&feet_hi[j])};
-                    y = apply_a_feet<REDUCED, DYN>(g, x, j, fw, code);
+                    y = sk * apply_a_feet<REDUCED, DYN>(g, x, j, fw, code);
                 } else {
-                    y = apply_a_node<REDUCED, DYN>(g, x, j, code);
+                    y = sk * apply_a_node<REDUCED, DYN>(g, x, j, code);
                 }
-                wv[s] = sk * y;
-                w[j] = wv[s];
+                w[j] = y;
             }
+            s_w[s * kGmBlock + threadIdx.x] = y;
         }
-#pragma unroll 2
+        __syncthreads();
+        // the projections, four consecutive nodes per thread (16-byte loads)
+        const int j4 = tile * kGmTile + kGmS * threadIdx.x;
+        VT wv[kGmS];
+        ld4(&s_w[kGmS * threadIdx.x], wv);
+        __syncthreads();
+#pragma unroll 4
         for (int i = 0; i <= k; ++i) {
-            const VT* qi = Q + (size_t)i * ldq;
+            VT q[kGmS];
+            load4(Q + (size_t)i * ldq, j4, n, q);
             VT d = (VT)0;
 #pragma unroll
-            for (int s = 0; s < kGmS; ++s) {
-                const int j = j0 + s * kGmBlock;
-                if (j < n) d += qi[j] * wv[s];
-            }
+            for (int s = 0; s < kGmS; ++s) d += q[s] * wv[s];
             sums_add(S, i, (double)d);
         }
     }
@@ -275,42 +327,29 @@ gm_update_kernel(VT* __restrict__ Q, long long ldq, int n, int k, int m, double 
     VT* w = Q + (size_t)(k + 1) * ldq;
     const int tiles = (n + kGmTile - 1) / kGmTile;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int j0 = tile * kGmTile + threadIdx.x;
+        const int j4 = tile * kGmTile + kGmS * threadIdx.x;
         VT wv[kGmS];
-#pragma unroll
-        for (int s = 0; s < kGmS; ++s) {
-            const int j = j0 + s * kGmBlock;
-            wv[s] = j < n ? w[j] : (VT)0;
-        }
-#pragma unroll 2
+        load4(w, j4, n, wv);
+#pragma unroll 4
         for (int i = 0; i <= k; ++i) {
-            const VT* qi = Q + (size_t)i * ldq;
+            VT q[kGmS];
+            load4(Q + (size_t)i * ldq, j4, n, q);
             const VT c = s_coef[i];
 #pragma unroll
-            for (int s = 0; s < kGmS; ++s) {
-                const int j = j0 + s * kGmBlock;
-                if (j < n) wv[s] -= c * qi[j];
-            }
+            for (int s = 0; s < kGmS; ++s) wv[s] -= c * q[s];
         }
+        store4(w, j4, n, wv);
         VT nrm = (VT)0;
 #pragma unroll
-        for (int s = 0; s < kGmS; ++s) {
-            const int j = j0 + s * kGmBlock;
-            if (j < n) {
-                w[j] = wv[s];
-                nrm += wv[s] * wv[s];
-            }
-        }
+        for (int s = 0; s < kGmS; ++s) nrm += wv[s] * wv[s];
         if constexpr (DOTS) {
-#pragma unroll 2
+#pragma unroll 4
             for (int i = 0; i <= k; ++i) {
-                const VT* qi = Q + (size_t)i * ldq;
+                VT q[kGmS];
+                load4(Q + (size_t)i * ldq, j4, n, q);
                 VT d = (VT)0;
 #pragma unroll
-                for (int s = 0; s < kGmS; ++s) {
-                    const int j = j0 + s * kGmBlock;
-                    if (j < n) d += qi[j] * wv[s];
-                }
+                for (int s = 0; s < kGmS; ++s) d += q[s] * wv[s];
                 sums_add(S, i, (double)d);
             }
         } else {
@@ -345,29 +384,26 @@ gm_apply_kernel(const VV* __restrict__ Vin, VV* __restrict__ Vnext, const VT* __
     bool bad = false;
     const int tiles = (n + kGmTile - 1) / kGmTile;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int j0 = tile * kGmTile + threadIdx.x;
+        const int j4 = tile * kGmTile + kGmS * threadIdx.x;
         VT e[kGmS];
 #pragma unroll
         for (int s = 0; s < kGmS; ++s) e[s] = (VT)0;
-#pragma unroll 2
+#pragma unroll 4
         for (int i = 0; i < kk; ++i) {
-            const VT* qi = Q + (size_t)i * ldq;
+            VT q[kGmS];
+            load4(Q + (size_t)i * ldq, j4, n, q);
             const VT c = s_coef[i];
 #pragma unroll
-            for (int s = 0; s < kGmS; ++s) {
-                const int j = j0 + s * kGmBlock;
-                if (j < n) e[s] += c * qi[j];
-            }
+            for (int s = 0; s < kGmS; ++s) e[s] += c * q[s];
         }
+        VV v[kGmS];
+        load4(Vin, j4, n, v);
 #pragma unroll
         for (int s = 0; s < kGmS; ++s) {
-            const int j = j0 + s * kGmBlock;
-            if (j < n) {
-                const VV o = Vin[j] + (VV)e[s];
-                Vnext[j] = o;
-                bad = bad || !isfinite(o);
-            }
+            v[s] += (VV)e[s];
+            bad = bad || (j4 + s < n && !isfinite(v[s]));
         }
+        store4(Vnext, j4, n, v);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->nonfinite, 1);
 }
