@@ -18,10 +18,11 @@
 // fixed order (the result does not depend on block scheduling) and does the
 // O(m) Hessenberg and Givens work on one thread.  No block waits for another.
 //
-// Element-wise work runs in the basis precision VT (FP32 on FP32 grids: the
-// FP64 pipe of this GPU is a small fraction of its FP32 pipe).  Each thread's
-// partial sums cover kGmS products; they are widened to FP64 for the warp,
-// block and grid sums and for the Hessenberg problem.
+// Element-wise work and the warp reductions run in the basis precision VT
+// (FP32 on FP32 grids: the FP64 pipe of this GPU is a small fraction of its
+// FP32 pipe, and FP64 adds in every lane of the warp trees made the
+// orthogonalisation FP64-bound).  Each warp's total over 128 products is
+// widened to FP64 for the block and grid sums and the Hessenberg problem.
 #include "dp_sweep.cuh"
 
 namespace dpk {
@@ -33,7 +34,8 @@ constexpr int kGmS = 4;                     // nodes per thread and tile (four c
 constexpr int kGmTile = kGmBlock * kGmS;
 constexpr int kGmWarps = kGmBlock / 32;
 
-__device__ __forceinline__ double warp_sum(double v)
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -52,10 +54,13 @@ __device__ __forceinline__ void sums_zero(BlockSums& S)
 }
 
 // Adds the warp's total of v to column c.  Every lane of the warp calls it.
-__device__ __forceinline__ void sums_add(BlockSums& S, int c, double v)
+// The warp tree runs in v's precision (a pairwise sum of 32 per-thread
+// partials); only its total is widened to FP64.
+template <typename T>
+__device__ __forceinline__ void sums_add(BlockSums& S, int c, T v)
 {
     v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0) S.acc[threadIdx.x >> 5][c] += v;
+    if ((threadIdx.x & 31) == 0) S.acc[threadIdx.x >> 5][c] += (double)v;
 }
 
 // Stores the block's columns [0, ncol) in its partial row.  Returns true in
@@ -189,7 +194,7 @@ gm_start_kernel(const VV* __restrict__ Vin, const VV* __restrict__ Vnext, VT* __
             nrm += r[s] * r[s];
         }
         store4(q0, j4, n, r);
-        sums_add(S, 0, (double)nrm);
+        sums_add(S, 0, nrm);
     }
     if (!sums_finish(S, 1, partial, gc, red)) return;
     if (threadIdx.x == 0) {
@@ -254,7 +259,7 @@ gm_arnoldi_kernel(const __grid_constant__ Geo<G> g, VT* __restrict__ Q, long lon
             VT d = (VT)0;
 #pragma unroll
             for (int s = 0; s < kGmS; ++s) d += q[s] * wv[s];
-            sums_add(S, i, (double)d);
+            sums_add(S, i, d);
         }
     }
     if (!sums_finish(S, k + 1, partial, gc, red)) return;
@@ -350,10 +355,10 @@ gm_update_kernel(VT* __restrict__ Q, long long ldq, int n, int k, int m, double 
                 VT d = (VT)0;
 #pragma unroll
                 for (int s = 0; s < kGmS; ++s) d += q[s] * wv[s];
-                sums_add(S, i, (double)d);
+                sums_add(S, i, d);
             }
         } else {
-            sums_add(S, 0, (double)nrm);
+            sums_add(S, 0, nrm);
         }
     }
     if (!sums_finish(S, DOTS ? k + 1 : 1, partial, gc, red)) return;
