@@ -575,7 +575,7 @@ cudaError_t enqueue_gmres(dp_grid* g, const GmOpts& go, int slot)
 }
 
 // Launches of one cycle (some exit at once after an early stop).
-long long gmres_launches(const GmOpts& go) { return 2 + (long long)go.m * (go.reorth ? 3 : 2); }
+long long gmres_launches(const GmOpts& go) { return 2 + (long long)go.m * (go.reorth ? 4 : 3); }
 
 int zero_value(dp_grid* g)
 {

@@ -13,10 +13,13 @@
 //   r0 = T_f(V) - V, Arnoldi on A from r0 (m steps, classical Gram-Schmidt,
 //   optionally twice), y = argmin ||beta0 e1 - H y||, V <- V + Q y.
 // The basis vectors are stored unnormalised, with scale[i] = 1 / ||Q_i||.
-// Every launch walks tiles of kGmTile nodes; its dot products are summed per
-// block into a partial row, and the last block to finish adds the rows in a
-// fixed order (the result does not depend on block scheduling) and does the
-// O(m) Hessenberg and Givens work on one thread.  No block waits for another.
+// An Arnoldi step is three launches: the product (gather-bound, one node per
+// thread at the evaluation sweep's occupancy), the projections, and the
+// update with the norm (both streaming, tiles of kGmTile nodes with 16-byte
+// loads).  A streaming launch sums its dot products per block into a partial
+// row, and the last block to finish adds the rows in a fixed order (the
+// result does not depend on block scheduling) and does the O(m) Hessenberg
+// and Givens work on one thread.  No block waits for another.
 //
 // Element-wise work and the warp reductions run in the basis precision VT
 // (FP32 on FP32 grids: the FP64 pipe of this GPU is a small fraction of its
@@ -209,66 +212,37 @@ gm_start_kernel(const VV* __restrict__ Vin, const VV* __restrict__ Vnext, VT* __
     }
 }
 
-// Arnoldi step k, first half: Q_{k+1} = A q_k (q_k = scale[k] Q_k) and the
-// projections h_ik = <q_i, Q_{k+1}>, i <= k.
+// Arnoldi step k, the product: Q_{k+1} = A q_k (q_k = scale[k] Q_k).  One
+// node per thread, nodes of a warp adjacent, the next node's foot and value
+// fetched while this node's corners are in flight (as in the evaluation
+// sweep); compiled for the sweep's occupancy on FP32 grids.
+template <typename G>
+constexpr int matvec_min_blocks() { return std::is_same<G, float>::value ? 6 : 2; }
+
 template <typename G, typename VT, bool REDUCED, int DYN>
-__global__ void __launch_bounds__(kGmBlock, 4)
-gm_arnoldi_kernel(const __grid_constant__ Geo<G> g, VT* __restrict__ Q, long long ldq, int k,
-                  const uint16_t* __restrict__ code, const unsigned long long* __restrict__ feet_lo,
-                  const unsigned* __restrict__ feet_hi, double* __restrict__ partial, GmCtl* __restrict__ gc)
+__global__ void __launch_bounds__(kGmBlock, matvec_min_blocks<G>())
+gm_matvec_kernel(const __grid_constant__ Geo<G> g, VT* __restrict__ Q, long long ldq, int k,
+                 const uint16_t* __restrict__ code, const unsigned long long* __restrict__ feet_lo,
+                 const unsigned* __restrict__ feet_hi, const GmCtl* __restrict__ gc)
 {
-    if (*(volatile int*)&gc->done) return;
-    __shared__ BlockSums S;
-    __shared__ double red[kGmLd];
-    __shared__ __align__(16) VT s_w[kGmTile];
-    sums_zero(S);
+    if (*(const volatile int*)&gc->done) return;
     const VT* x = Q + (size_t)k * ldq;
     VT* w = Q + (size_t)(k + 1) * ldq;
     const VT sk = (VT)gc->scale[k];
     const int n = g.n_nodes;
-    const int tiles = (n + kGmTile - 1) / kGmTile;
-    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        // the product, nodes strided by the block so that the feet and the
-        // gathered corners of a warp are adjacent
-#pragma unroll
-        for (int s = 0; s < kGmS; ++s) {
-            const int j = tile * kGmTile + s * kGmBlock + threadIdx.x;
-            VT y = (VT)0;
-            if (j < n) {
-                if constexpr (std::is_same<G, float>::value) {
-                    // the feet are read once per product: evict-first
-                    const FootWord fw{__ldcs(&feet_lo[j]), __ldcs(&feet_hi[j])};
-                    y = sk * apply_a_feet<REDUCED, DYN>(g, x, j, fw, code);
-                } else {
-                    y = sk * apply_a_node<REDUCED, DYN>(g, x, j, code);
-                }
-                w[j] = y;
-            }
-            s_w[s * kGmBlock + threadIdx.x] = y;
+    const int stride = gridDim.x * kGmBlock;
+    if constexpr (std::is_same<G, float>::value) {
+        int j = blockIdx.x * kGmBlock + threadIdx.x;
+        FootWord next{0ull, 0u};
+        if (j < n) next = FootWord{__ldcs(&feet_lo[j]), __ldcs(&feet_hi[j])};
+        for (; j < n; j += stride) {
+            const FootWord fw = next;
+            if (j + stride < n) next = FootWord{__ldcs(&feet_lo[j + stride]), __ldcs(&feet_hi[j + stride])};
+            w[j] = sk * apply_a_feet<REDUCED, DYN>(g, x, j, fw, code);
         }
-        __syncthreads();
-        // the projections, four consecutive nodes per thread (16-byte loads)
-        const int j4 = tile * kGmTile + kGmS * threadIdx.x;
-        VT wv[kGmS];
-        ld4(&s_w[kGmS * threadIdx.x], wv);
-        __syncthreads();
-#pragma unroll 4
-        for (int i = 0; i <= k; ++i) {
-            VT q[kGmS];
-            load4(Q + (size_t)i * ldq, j4, n, q);
-            VT d = (VT)0;
-#pragma unroll
-            for (int s = 0; s < kGmS; ++s) d += q[s] * wv[s];
-            sums_add(S, i, d);
-        }
-    }
-    if (!sums_finish(S, k + 1, partial, gc, red)) return;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i <= k; ++i) {
-            const double h = gc->scale[i] * red[i];
-            gc->H[i][k] = h;
-            gc->coef[i] = h * gc->scale[i];
-        }
+    } else {
+        for (int j = blockIdx.x * kGmBlock + threadIdx.x; j < n; j += stride)
+            w[j] = sk * apply_a_node<REDUCED, DYN>(g, x, j, code);
     }
 }
 
@@ -315,10 +289,11 @@ __device__ void finalize_column(GmCtl* gc, int k, int m, double rtol, double nrm
     }
 }
 
-// Arnoldi step k, second half: Q_{k+1} -= sum_i coef_i Q_i.  DOTS: also the
-// projections of the result for a second Gram-Schmidt pass; otherwise the
-// norm that closes the column.
-template <typename VT, bool DOTS>
+// Arnoldi step k, Gram-Schmidt on Q_{k+1}.  SUB: Q_{k+1} -= sum_i coef_i Q_i.
+// DOTS: the projections h_ik = <q_i, Q_{k+1}> of the result, which set column
+// k of H (first pass, !SUB) or correct it (second pass) and become the next
+// coefficients; otherwise the norm that closes the column.
+template <typename VT, bool SUB, bool DOTS>
 __global__ void __launch_bounds__(kGmBlock)
 gm_update_kernel(VT* __restrict__ Q, long long ldq, int n, int k, int m, double rtol, double* __restrict__ partial,
                  GmCtl* __restrict__ gc)
@@ -327,7 +302,8 @@ gm_update_kernel(VT* __restrict__ Q, long long ldq, int n, int k, int m, double 
     __shared__ BlockSums S;
     __shared__ double red[kGmLd];
     __shared__ VT s_coef[kGmMaxRestart + 1];
-    for (int i = threadIdx.x; i <= k; i += kGmBlock) s_coef[i] = (VT)gc->coef[i];
+    if (SUB)
+        for (int i = threadIdx.x; i <= k; i += kGmBlock) s_coef[i] = (VT)gc->coef[i];
     sums_zero(S);
     VT* w = Q + (size_t)(k + 1) * ldq;
     const int tiles = (n + kGmTile - 1) / kGmTile;
@@ -335,15 +311,17 @@ gm_update_kernel(VT* __restrict__ Q, long long ldq, int n, int k, int m, double 
         const int j4 = tile * kGmTile + kGmS * threadIdx.x;
         VT wv[kGmS];
         load4(w, j4, n, wv);
+        if constexpr (SUB) {
 #pragma unroll 4
-        for (int i = 0; i <= k; ++i) {
-            VT q[kGmS];
-            load4(Q + (size_t)i * ldq, j4, n, q);
-            const VT c = s_coef[i];
+            for (int i = 0; i <= k; ++i) {
+                VT q[kGmS];
+                load4(Q + (size_t)i * ldq, j4, n, q);
+                const VT c = s_coef[i];
 #pragma unroll
-            for (int s = 0; s < kGmS; ++s) wv[s] -= c * q[s];
+                for (int s = 0; s < kGmS; ++s) wv[s] -= c * q[s];
+            }
+            store4(w, j4, n, wv);
         }
-        store4(w, j4, n, wv);
         VT nrm = (VT)0;
 #pragma unroll
         for (int s = 0; s < kGmS; ++s) nrm += wv[s] * wv[s];
@@ -366,7 +344,7 @@ gm_update_kernel(VT* __restrict__ Q, long long ldq, int n, int k, int m, double 
         if constexpr (DOTS) {
             for (int i = 0; i <= k; ++i) {
                 const double h = gc->scale[i] * red[i];
-                gc->H[i][k] += h;
+                gc->H[i][k] = SUB ? gc->H[i][k] + h : h;
                 gc->coef[i] = h * gc->scale[i];
             }
         } else {
@@ -453,10 +431,35 @@ int tiled_blocks(K kern, int n, int sm_count, int max_blocks, int& per_sm)
 template <typename G, typename VT, bool REDUCED, int DYN>
 cudaError_t launch_arnoldi(const GmArgs<G, VT>& a, int k)
 {
-    auto kern = gm_arnoldi_kernel<G, VT, REDUCED, DYN>;
+    auto kern = gm_matvec_kernel<G, VT, REDUCED, DYN>;
     static int per_sm = 0;
-    const int b = tiled_blocks(kern, a.g.n_nodes, a.sm_count, a.max_blocks, per_sm);
-    kern<<<b, kGmBlock, 0, a.stream>>>(a.g, a.Q, a.ldq, k, a.code, a.feet_lo, a.feet_hi, a.partial, a.gctl);
+    if (per_sm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGmBlock, 0) != cudaSuccess) per_sm = 1;
+        if (per_sm < 1) per_sm = 1;
+    }
+    const long long need = ((long long)a.g.n_nodes + kGmBlock - 1) / kGmBlock;
+    const long long cap = (long long)per_sm * a.sm_count;
+    const int b = (int)(need < cap ? (need < 1 ? 1 : need) : cap);
+    kern<<<b, kGmBlock, 0, a.stream>>>(a.g, a.Q, a.ldq, k, a.code, a.feet_lo, a.feet_hi, a.gctl);
+    return cudaGetLastError();
+}
+
+template <typename VT, bool SUB, bool DOTS>
+cudaError_t launch_update(const GmArgs<float, VT>& a, int n, int k)
+{
+    auto kern = gm_update_kernel<VT, SUB, DOTS>;
+    static int per_sm = 0;
+    const int b = tiled_blocks(kern, n, a.sm_count, a.max_blocks, per_sm);
+    kern<<<b, kGmBlock, 0, a.stream>>>(a.Q, a.ldq, n, k, a.m, a.rtol, a.partial, a.gctl);
+    return cudaGetLastError();
+}
+template <typename VT, bool SUB, bool DOTS>
+cudaError_t launch_update(const GmArgs<double, VT>& a, int n, int k)
+{
+    auto kern = gm_update_kernel<VT, SUB, DOTS>;
+    static int per_sm = 0;
+    const int b = tiled_blocks(kern, n, a.sm_count, a.max_blocks, per_sm);
+    kern<<<b, kGmBlock, 0, a.stream>>>(a.Q, a.ldq, n, k, a.m, a.rtol, a.partial, a.gctl);
     return cudaGetLastError();
 }
 
@@ -497,18 +500,9 @@ cudaError_t cycle(const GmArgs<G, VT>& a, const VV* Vin, VV* Vnext)
     }
     for (int k = 0; k < a.m; ++k) {
         if ((e = dispatch_arnoldi(a, k)) != cudaSuccess) return e;
-        if (a.reorth) {
-            auto kern = gm_update_kernel<VT, true>;
-            static int per_sm = 0;
-            const int b = tiled_blocks(kern, n, a.sm_count, a.max_blocks, per_sm);
-            kern<<<b, kGmBlock, 0, a.stream>>>(a.Q, a.ldq, n, k, a.m, a.rtol, a.partial, a.gctl);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
-        auto kern = gm_update_kernel<VT, false>;
-        static int per_sm = 0;
-        const int b = tiled_blocks(kern, n, a.sm_count, a.max_blocks, per_sm);
-        kern<<<b, kGmBlock, 0, a.stream>>>(a.Q, a.ldq, n, k, a.m, a.rtol, a.partial, a.gctl);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_update<VT, false, true>(a, n, k)) != cudaSuccess) return e;      // projections
+        if (a.reorth && (e = launch_update<VT, true, true>(a, n, k)) != cudaSuccess) return e;
+        if ((e = launch_update<VT, true, false>(a, n, k)) != cudaSuccess) return e;      // update + norm
     }
     auto kern = gm_apply_kernel<VV, VT>;
     static int per_sm = 0;
