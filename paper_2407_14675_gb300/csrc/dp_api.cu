@@ -451,13 +451,9 @@ enum { kTVI = 0, kTImp = 1, kTEval = 2, kTImp64 = 3, kTEval64 = 4 };
 
 int finish_nonfinite(dp_grid* g)
 {
-    if (g->h_ctl->timeout) return fail(DP_ETIMEOUT, "a sweep gave up waiting for its staged inputs");
     if (g->h_ctl->nonfinite) return fail(DP_ENONFINITE, "a sweep produced a non-finite value");
     return DP_OK;
 }
-
-// A sweep failed on the device (non-finite value or an expired wait).
-bool ctl_failed(const dp_grid* g) { return g->h_ctl->nonfinite || g->h_ctl->timeout; }
 
 long long updates_per_sweep(const dp_grid* g) { return g->n_active - g->n_target; }
 
@@ -854,7 +850,7 @@ int pi_gmres(dp_grid* g, const dp_solve_opts* o, const GmOpts& go, dp_solve_stat
         else ++S.sweeps_improve;
         ++outer;
         advance(g, 1);
-        if (ctl_failed(g)) break;
+        if (g->h_ctl->nonfinite) break;
         if (res < o->tol) {
             if (!full) {
                 first_full = true;   // a converged walk is confirmed by a full tabulation
@@ -1179,11 +1175,11 @@ int dp_value_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
         }
         res = ring_value(g, s + c - 1);
         s += c;
-        if (ctl_failed(g)) { done = s; break; }
+        if (g->h_ctl->nonfinite) { done = s; break; }
         if (res < o->tol) { done = s; break; }
         chunk = std::min<long long>(chunk * 2, kMaxChunk);
     }
-    bool conv = done >= 0 && !ctl_failed(g);
+    bool conv = done >= 0 && !g->h_ctl->nonfinite;
     if (done < 0) done = s;
     advance(g, done);
     S.sweeps_vi = done;
@@ -1295,7 +1291,7 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
         } else {
             t += ran;
         }
-        if (ctl_failed(g)) break;
+        if (g->h_ctl->nonfinite) break;
         if (conv) break;
         if (confirm_next) {
             first_full = true;
@@ -1317,7 +1313,7 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
     if (store_of(g) != kStoreMix) advance(g, t);
     S.history_count = std::min<long long>(hist_n, o->history ? o->history_capacity : 0);
     S.residual = res;
-    S.converged = conv && !ctl_failed(g);
+    S.converged = conv && !g->h_ctl->nonfinite;
     S.node_updates = (S.sweeps_improve + S.sweeps_eval + S.sweeps_improve_fp64 + S.sweeps_eval_fp64 +
                       S.gmres_matvecs) * updates_per_sweep(g);
     S.ms_improve = T.ms[kTImp];
@@ -1374,7 +1370,7 @@ int dp_policy_evaluate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats
         if (mix) ++S.sweeps_eval_fp64;
         else ++S.sweeps_eval;
         res = ring_value(g, 0);
-        if (ctl_failed(g)) break;
+        if (g->h_ctl->nonfinite) break;
         if (res < o->tol) {
             conv = true;
             break;
@@ -1387,7 +1383,7 @@ int dp_policy_evaluate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats
     }
     CK(T.collect());
     S.residual = res;
-    S.converged = conv && !ctl_failed(g);
+    S.converged = conv && !g->h_ctl->nonfinite;
     S.node_updates = (S.sweeps_eval + S.sweeps_eval_fp64 + S.gmres_matvecs) * updates_per_sweep(g);
     S.ms_eval = T.ms[kTEval];
     S.ms_eval_fp64 = T.ms[kTEval64];

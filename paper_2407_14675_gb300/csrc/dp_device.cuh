@@ -44,7 +44,7 @@ struct Ctl {
     int stop;         // 1 once a stopping test has passed
     int stop_sweep;   // sweeps completed when it passed
     int nonfinite;    // a sweep produced a non-finite value
-    int timeout;      // a bounded device-side wait expired (the sweep's output is incomplete)
+    int pad;
 };
 
 // Everything a sweep kernel needs about the grid, in geometry precision G.

@@ -22,7 +22,6 @@
 
 #include "dp_device.cuh"
 #include "dp_host.h"
-#include "dp_umma.cuh"
 
 namespace dpk {
 
@@ -158,23 +157,6 @@ __device__ __forceinline__ float incr_recompute(const Geo<float>& g, const float
     return K.blend(t);
 }
 
-// New value of node j at its frozen foot w (FP32 evaluation sweep, Eq. (13)).
-template <bool REDUCED, int DYN>
-__device__ __forceinline__ float eval_feet_value(const Geo<float>& g, const float* __restrict__ Vin,
-                                                 const uint16_t* __restrict__ code, int j, FootWord w, float vj)
-{
-    const int kind = (int)((w.hi >> 16) & 3u);
-    if (kind == kFootInside) return bellman_value<float, float>(g, vj, eval_foot<REDUCED>(g, Vin, j, w, vj));
-    if (kind == kFootOut) return bellman_value<float, float>(g, vj, (float)((float)g.M64 - vj));
-    if (kind == kFootRecompute) {
-        NodeEval<float, float, REDUCED, DYN> ev;
-        decode_node(g, j, ev.i);
-        setup_node<float, float, DYN>(ev, g, Vin, vj);
-        return bellman_value<float, float>(g, vj, ev.at_code(code[j]));
-    }
-    return 0.0f;   // target node
-}
-
 // Sweeps nodes j0, j0 + stride, ... < end of one grid: the per-node work of
 // every sweep mode.  Folds max |V_out - V_in| into resid and non-finite
 // results into bad.
@@ -213,15 +195,24 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                 w_next.hi = __ldcs(&feet_hi[j + stride]);
                 v_next = Vin[j + stride];
             }
+            const int kind = (int)((w.hi >> 16) & 3u);
             S vnew = (S)0;
             if constexpr (MODE == kEvalFeet) {
-                vnew = eval_feet_value<REDUCED, DYN>(g, Vin, code, j, w, vj);
+                if (kind == kFootInside) {
+                    vnew = bellman_value<G, S>(g, vj, eval_foot<REDUCED>(g, Vin, j, w, vj));
+                } else if (kind == kFootOut) {
+                    vnew = bellman_value<G, S>(g, vj, (G)((S)g.M64 - vj));
+                } else if (kind == kFootRecompute) {
+                    NodeEval<G, S, REDUCED, DYN> ev;
+                    decode_node(g, j, ev.i);
+                    setup_node<G, S, DYN>(ev, g, Vin, vj);
+                    vnew = bellman_value<G, S>(g, vj, ev.at_code(code[j]));
+                }
                 Vout[j] = vnew;
                 resid = fmax(resid, (S)fabs(vnew - vj));
             } else {
                 // increment: d' = beta W d at the frozen policy (no running cost,
                 // no penalty: both cancel between consecutive sweeps)
-                const int kind = (int)((w.hi >> 16) & 3u);
                 float D = 0.0f;
                 if (kind == kFootInside) D = eval_foot<REDUCED>(g, Vin, j, w, 0.0f);
                 else if (kind == kFootRecompute) D = incr_recompute<REDUCED, DYN>(g, Vin, j, code[j]);
@@ -417,134 +408,6 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
     block_fold(resid, bad, &ring[sweep & ring_mask], &ctl->nonfinite);
 }
 
-// Evaluation at frozen feet (FP32) with the streamed inputs staged by bulk
-// copies.  The feet (12 B per node) and the node values (4 B) are read once
-// per sweep in node order: one thread of each block streams tiles of
-// kStageTile nodes into a two-stage shared-memory ring with cp.async.bulk
-// (the feet with an evict-first L2 policy), while the block evaluates the
-// previous tile, so the threads themselves issue only the corner gathers,
-// which mostly hit L1 and L2.  The arithmetic is eval_feet_value's, as in the
-// register path: results are bit-identical.  Every wait on a tile is bounded:
-// on expiry the block records ctl->timeout, waits (bounded) for its copies in
-// flight and stops; the host then reports DP_ETIMEOUT.
-constexpr int kStageU = 2;                       // nodes per thread and tile
-constexpr int kStageTile = kBlock * kStageU;     // 512 nodes, 8 KB per stage
-constexpr int kStagePolls = 1 << 22;
-
-template <bool REDUCED, int DYN>
-__global__ void __launch_bounds__(kBlock, 6)
-eval_staged_kernel(const __grid_constant__ Geo<float> g, const float* __restrict__ Vin, float* __restrict__ Vout,
-                   const uint16_t* __restrict__ code, const unsigned long long* __restrict__ feet_lo,
-                   const unsigned* __restrict__ feet_hi, Ctl* __restrict__ ctl, unsigned long long* __restrict__ ring,
-                   int ring_mask, long long sweep, int check_prev, double tol)
-{
-    if (*(volatile int*)&ctl->stop) return;
-    if (check_prev) {
-        unsigned long long bits = *(volatile unsigned long long*)&ring[(sweep - 1) & ring_mask];
-        if (__longlong_as_double((long long)bits) < tol) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                ctl->stop_sweep = (int)sweep;
-                ctl->stop = 1;
-            }
-            return;
-        }
-    }
-    __shared__ __align__(16) unsigned long long s_lo[2][kStageTile];
-    __shared__ __align__(16) unsigned s_hi[2][kStageTile];
-    __shared__ __align__(16) float s_v[2][kStageTile];
-    __shared__ __align__(8) unsigned long long s_bar[2];
-    __shared__ int s_fail;
-    const int n = g.n_nodes;
-    const int full = n / kStageTile;
-    const int mine = full > (int)blockIdx.x ? (full - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    if (threadIdx.x == 0) {
-        mbar_init(&s_bar[0]);
-        mbar_init(&s_bar[1]);
-        s_fail = 0;
-    }
-    __syncthreads();
-    // tile `it` of this block -> stage it & 1 (thread 0)
-    auto issue = [&](int it, unsigned long long pol) {
-        const int st = it & 1;
-        const size_t j0 = ((size_t)blockIdx.x + (size_t)it * gridDim.x) * kStageTile;
-        mbar_arrive_expect_tx(&s_bar[st], kStageTile * 16);
-        bulk_g2s_hint(s_lo[st], feet_lo + j0, kStageTile * 8, &s_bar[st], pol);
-        bulk_g2s_hint(s_hi[st], feet_hi + j0, kStageTile * 4, &s_bar[st], pol);
-        bulk_g2s(s_v[st], Vin + j0, kStageTile * 4, &s_bar[st]);
-    };
-    unsigned long long pol = 0;
-    if (threadIdx.x == 0) {
-        pol = l2_evict_first();
-        if (mine > 0) issue(0, pol);
-        if (mine > 1) issue(1, pol);
-    }
-    float resid = 0.0f;
-    bool bad = false;
-    int it = 0;
-    for (; it < mine; ++it) {
-        const int st = it & 1;
-        if (!mbar_wait(&s_bar[st], (it >> 1) & 1, kStagePolls)) s_fail = 1;
-        __syncthreads();
-        if (s_fail) break;
-        const int j0 = ((int)blockIdx.x + it * (int)gridDim.x) * kStageTile;
-#pragma unroll
-        for (int u = 0; u < kStageU; ++u) {
-            const int t = u * kBlock + threadIdx.x;
-            const FootWord w{s_lo[st][t], s_hi[st][t]};
-            const float vj = s_v[st][t];
-            const float vnew = eval_feet_value<REDUCED, DYN>(g, Vin, code, j0 + t, w, vj);
-            Vout[j0 + t] = vnew;
-            resid = fmaxf(resid, fabsf(vnew - vj));
-            bad = bad || !isfinite(vnew);
-        }
-        __syncthreads();   // stage st is free again
-        if (threadIdx.x == 0 && it + 2 < mine) {
-            fence_async_smem();
-            issue(it + 2, pol);
-        }
-    }
-    if (s_fail) {
-        if (threadIdx.x == 0) {
-            atomicExch(&ctl->timeout, 1);
-            // the copies still in flight: this tile's and the next one's
-            for (int q = it; q < it + 2 && q < mine; ++q) mbar_wait(&s_bar[q & 1], (q >> 1) & 1, kStagePolls);
-        }
-        __syncthreads();
-        return;
-    }
-    // the last partial tile, plain loads
-    for (int j = full * kStageTile + (int)blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock) {
-        const FootWord w{__ldcs(&feet_lo[j]), __ldcs(&feet_hi[j])};
-        const float vj = Vin[j];
-        const float vnew = eval_feet_value<REDUCED, DYN>(g, Vin, code, j, w, vj);
-        Vout[j] = vnew;
-        resid = fmaxf(resid, fabsf(vnew - vj));
-        bad = bad || !isfinite(vnew);
-    }
-    block_fold(resid, bad, &ring[sweep & ring_mask], &ctl->nonfinite);
-}
-
-template <bool REDUCED, int DYN>
-cudaError_t launch_eval_staged(const SweepLaunch<float, float>& L)
-{
-    // the bulk copies need 16-byte aligned sources (allocation bases)
-    if (((uintptr_t)L.Vin | (uintptr_t)L.feet_lo | (uintptr_t)L.feet_hi) & 15) return cudaErrorInvalidValue;
-    auto kern = eval_staged_kernel<REDUCED, DYN>;
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) per_sm = 1;
-    }
-    const long long tiles = L.g.n_nodes / kStageTile;
-    const long long cap = (long long)per_sm * L.sm_count;
-    int blocks = (int)(tiles < cap ? tiles : cap);
-    if (blocks < 1) blocks = 1;
-    kern<<<blocks, kBlock, 0, L.stream>>>(L.g, L.Vin, L.Vout, L.code, L.feet_lo, L.feet_hi, L.ctl, L.ring,
-                                          L.ring_mask, L.sweep, L.check_prev, L.tol);
-    return cudaGetLastError();
-}
-
 template <typename G, typename S, int MODE, bool REDUCED, int DYN>
 cudaError_t launch_one(const SweepLaunch<G, S>& L)
 {
@@ -574,7 +437,7 @@ cudaError_t launch_mode(const SweepLaunch<G, S>& L)
     case kImproveWalk: return launch_one<G, S, kImproveWalk, REDUCED, DYN>(L);
     case kEval: return launch_one<G, S, kEval, REDUCED, DYN>(L);
     case kEvalFeet:
-        if constexpr (f32) return L.feet_lo ? launch_eval_staged<REDUCED, DYN>(L) : cudaErrorInvalidValue;
+        if constexpr (f32) return L.feet_lo ? launch_one<G, S, kEvalFeet, REDUCED, DYN>(L) : cudaErrorInvalidValue;
         return cudaErrorInvalidValue;
     case kIncr:
         if constexpr (f32)

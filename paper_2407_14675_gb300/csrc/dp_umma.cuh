@@ -1,8 +1,7 @@
 // dp_umma.cuh -- fifth-generation tensor-core (tcgen05) primitives for the
 // warm-start network's GEMMs: TMEM allocation, shared-memory matrix
 // descriptors, the BF16 MMA with FP32 accumulation in TMEM, completion via an
-// mbarrier (bounded wait), and TMEM -> register loads; and the bulk
-// asynchronous copies (cp.async.bulk) that stage the sweeps' streamed inputs.
+// mbarrier (bounded wait), and TMEM -> register loads.
 //
 // Operand layout in shared memory: K-major, no swizzle, as 8 x 8 "core
 // matrices" of 16-bit elements (8 rows of 16 bytes, 128 contiguous bytes).
@@ -58,34 +57,6 @@ __device__ __forceinline__ void mbar_init(unsigned long long* bar)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
-}
-
-// Arrival that also expects `bytes` of asynchronous copies on the barrier.
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-// L2 policy for data read once (evict first).
-__device__ __forceinline__ unsigned long long l2_evict_first()
-{
-    unsigned long long pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-// Bulk (non-tensor) copy global -> shared memory whose completion is counted
-// on bar: both addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, unsigned bytes, unsigned long long* bar,
-                                              unsigned long long policy)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
-                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy) : "memory");
 }
 
 // D (TMEM) = (accumulate ? D : 0) + A * B^T for one K = 16 step.
