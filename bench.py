@@ -591,21 +591,41 @@ def run_ours(args, world, rank, local):
                        "improvements": st.sweeps_improve + st.sweeps_improve_fp64, "matvecs": st.gmres_matvecs,
                        "gpu_ms": {"improve": st.ms_improve + st.ms_improve_fp64,
                                   "gmres": st.ms_eval + st.ms_eval_fp64}}
+    solve_tuned = None
+    if args.solve and rank == 0:
+        # the same cold solve with more evaluation sweeps per improvement: the
+        # sweeps needed to propagate the value stay about the same, the
+        # improvement sweeps (16 evaluation sweeps' worth each) fall
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = g.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=args.n_eval_tuned, polish=1, warm=0)
+        torch.cuda.synchronize()
+        solve_tuned = {"seconds": time.perf_counter() - t0, "converged": bool(st.converged), "residual": st.residual,
+                       "n_eval": args.n_eval_tuned, "improvements": st.sweeps_improve + st.sweeps_improve_fp64,
+                       "evaluation_sweeps": st.sweeps_eval + st.sweeps_eval_fp64}
     cascade = None
     if args.solve and rank == 0:
-        # coarse to fine: the same problem on 31^4 to 1e-6, its solution
-        # interpolated onto the 61^4 grid, then solved there to 1e-6
-        with dp.Grid(W.config1(n=31), stream=int(stream.cuda_stream)) as gc:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            rc, sc = gc.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=p.n_eval, polish=1, warm=0)
-            dp.dp_warm_start_from_grid(gc.h, g.h)
-            rc, sf = g.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=p.n_eval, polish=1, warm=1)
-            torch.cuda.synchronize()
-            cascade = {"seconds": time.perf_counter() - t0, "converged": bool(sc.converged and sf.converged),
-                       "coarse_31x4_improvements": sc.sweeps_improve + sc.sweeps_improve_fp64,
-                       "fine_61x4_improvements": sf.sweeps_improve + sf.sweeps_improve_fp64,
-                       "residual": sf.residual}
+        # coarse to fine: the same problem on 16^4, then 31^4, each solved to
+        # 1e-6 and interpolated onto the next grid (dp_warm_start_from_grid),
+        # then solved on 61^4 to 1e-6; every level with n_eval = cascade_n_eval
+        levels = [16, 31]
+        grids = [dp.Grid(W.config1(n=n), stream=int(stream.cuda_stream)) for n in levels]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        per, prev = [], None
+        for n, gc in zip(levels + [61], grids + [g]):
+            if prev is not None:
+                dp.dp_warm_start_from_grid(prev.h, gc.h)
+            rc, sc = gc.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=args.cascade_n_eval, polish=1,
+                                       warm=int(prev is not None))
+            per.append({"grid": "%d^4" % n, "improvements": sc.sweeps_improve + sc.sweeps_improve_fp64,
+                        "converged": bool(sc.converged), "ms": sc.ms_wall})
+            prev = gc
+        torch.cuda.synchronize()
+        cascade = {"seconds": time.perf_counter() - t0, "converged": all(q["converged"] for q in per),
+                   "n_eval": args.cascade_n_eval, "levels": per, "residual": sc.residual}
+        for gc in grids:
+            gc.close()
     warm = warm_start_leg(args, dp, W, torch, g, p) if (args.warm_start and args.solve and rank == 0) else None
     extra = extra_legs(args, dp, W, torch, g, p) if (args.extra and rank == 0) else None
     g.close()
@@ -658,6 +678,7 @@ def run_ours(args, world, rank, local):
             "sample": "one spawned oracle process per core, each on its own 2,000-node sample of the 61^4 step "
                       "mix, %.1f s" % par_info["seconds"]},
         "time_to_tol": solve,
+        "time_to_tol_n_eval_tuned": solve_tuned,
         "time_to_tol_coarse_to_fine": cascade,
         "time_to_tol_gmres": solve_gmres,
         "warm_start": warm,
@@ -687,6 +708,8 @@ def main():
     ap.add_argument("--extra", type=int, default=1, help="17^4 FP64 VI; walk vs full tabulation")
     ap.add_argument("--cpu-parallel", type=int, default=1, help="also time the oracle on every host core")
     ap.add_argument("--example1", type=int, default=1, help="the paper's Example 1 solve and closed loop")
+    ap.add_argument("--n-eval-tuned", type=int, default=160, help="evaluation sweeps per improvement, tuned solve")
+    ap.add_argument("--cascade-n-eval", type=int, default=120, help="evaluation sweeps per improvement, cascade")
     ap.add_argument("--gmres-restart-fp64", type=int, default=60, help="GMRES restart length, FP64 grids")
     ap.add_argument("--gmres-restart-fp32", type=int, default=20, help="GMRES restart length, 61^4 FP32 grid")
     ap.add_argument("--batch-count", type=int, default=256)
