@@ -423,8 +423,9 @@ def batch_leg(args, dp, W, torch):
 def warm_start_leg(args, dp, W, torch, g1, p1):
     """Learned warm start: train the network on the converged 61^4 solve
     (every stored node), then solve the 121^4 energy-band grid to 1e-6 from
-    V = 0 and from the network's V and policy; closed loop from 1024 seeded
-    states on the warm-started solution."""
+    V = 0, from the network's V and policy, and from the 61^4 solution, with
+    the configured and with the tuned number of evaluation sweeps per
+    improvement; closed loop from 1024 seeded states on the last solution."""
     p2 = W.config2()
     out = {"grid": "121^4 box, energy band [%.4f, %.4f]" % (p2.energy_lo, p2.energy_hi)}
     with dp.Mlp(p1.lo, p1.hi, batch_capacity=65536) as net:
@@ -440,23 +441,30 @@ def warm_start_leg(args, dp, W, torch, g1, p1):
         with dp.Grid(p2, stream=int(torch.cuda.current_stream().cuda_stream)) as g2:
             out["nodes_active"] = g2.info["n_active"]
             V_cold = None
-            for start in ("cold", "warm", "from_61x4_grid"):
+            # each start with the configured 20 evaluation sweeps per improvement,
+            # then again with the tuned count
+            tuned = "_n_eval_%d" % args.n_eval_tuned
+            runs = [(k, p2.n_eval) for k in ("cold", "warm", "from_61x4_grid")]
+            runs += [(k + tuned, args.n_eval_tuned) for k in ("cold", "warm", "from_61x4_grid")]
+            for start, n_eval in runs:
+                kind = start.split("_n_eval")[0]
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 ws_ms = 0.0
-                if start != "cold":
-                    if start == "warm":
+                if kind != "cold":
+                    if kind == "warm":
                         ws_ms = dp.dp_warm_start(net.h, g2.h)
                     else:
                         # the non-learned baseline: Q1 interpolation of the 61^4 solution
                         ws_ms = dp.dp_warm_start_from_grid(g1.h, g2.h)
-                    t_ws = time.perf_counter() - t0
-                    err = np.abs(g2.get_value() - V_cold) / g2.info["penalty_M"]
-                    out[("warm_start_error" if start == "warm" else "from_61x4_grid_error")] = {
-                        "max_over_M": float(err.max()), "rms_over_M": float(np.sqrt(np.mean(err ** 2)))}
-                    t0 = time.perf_counter() - t_ws   # the host copy for the error is not timed
-                rc, s2 = g2.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=p2.n_eval, polish=1,
-                                           warm=int(start != "cold"))
+                    if start == kind:
+                        t_ws = time.perf_counter() - t0
+                        err = np.abs(g2.get_value() - V_cold) / g2.info["penalty_M"]
+                        out[("warm_start_error" if kind == "warm" else "from_61x4_grid_error")] = {
+                            "max_over_M": float(err.max()), "rms_over_M": float(np.sqrt(np.mean(err ** 2)))}
+                        t0 = time.perf_counter() - t_ws   # the host copy for the error is not timed
+                rc, s2 = g2.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=n_eval, polish=1,
+                                           warm=int(kind != "cold"))
                 torch.cuda.synchronize()
                 if start == "cold":
                     V_cold = g2.get_value()
@@ -474,7 +482,7 @@ def warm_start_leg(args, dp, W, torch, g1, p1):
                         "frac_of_hbm": 10.0 * n_upd / (ev_ms / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
                         "walk_ms": sk.ms_improve / max(sk.sweeps_improve, 1)}
                 out[start] = {"seconds": time.perf_counter() - t0, "converged": bool(s2.converged),
-                              "residual": s2.residual, "warm_start_ms": ws_ms,
+                              "residual": s2.residual, "n_eval": n_eval, "warm_start_ms": ws_ms,
                               "sweeps_improve": s2.sweeps_improve, "sweeps_eval": s2.sweeps_eval,
                               "sweeps_improve_fp64": s2.sweeps_improve_fp64,
                               "sweeps_eval_fp64": s2.sweeps_eval_fp64, "node_updates": s2.node_updates}
@@ -488,6 +496,8 @@ def warm_start_leg(args, dp, W, torch, g1, p1):
     c, w, gr = out["cold"], out["warm"], out["from_61x4_grid"]
     out["speedup_wall"] = c["seconds"] / max(w["seconds"], 1e-9)
     out["speedup_wall_grid_start"] = c["seconds"] / max(gr["seconds"], 1e-9)
+    ct, wt = out["cold" + tuned], out["warm" + tuned]
+    out["speedup_wall" + tuned] = ct["seconds"] / max(wt["seconds"], 1e-9)
     return out
 
 
