@@ -260,6 +260,20 @@ class Oracle:
         A = (sp.identity(self.N, format="csr") - self.s.beta * W).tocsc()
         return spla.spsolve(A, b)
 
+    def eval_diag_sweep(self, V, codes):
+        """One Jacobi iteration on the policy-evaluation system (I - beta W) V = b
+        (Eq. (13) at a frozen policy) with each node's own coefficient solved:
+            V'_j = (b_j + beta sum_{c != j} W_jc V_c) / (1 - beta W_jj).
+        The evaluation sweep V' = b + beta W V has the same fixed point.
+        Returns (V', max |V' - V| over the node set)."""
+        Wm, b = self.policy_system(codes)
+        V = np.asarray(V, np.float64)
+        d = Wm.diagonal()
+        beta = self.s.beta
+        Vn = (b + beta * (Wm @ V - d * V)) / (1.0 - beta * d)
+        act = self.active.astype(bool)
+        return Vn, float(np.abs(Vn - V)[act].max())
+
     def value_iterate(self, V0=None, tol=None, max_sweeps=100000):
         V = np.zeros(self.N) if V0 is None else np.array(V0, np.float64)
         res = C.c_double(0)

@@ -577,3 +577,45 @@ def test_exact_evaluation_is_the_fixed_point_of_the_sweep():
     for _ in range(50):
         V = o.sweep(V, mode=oracle.EVAL, codes=codes)[0]
     assert np.abs(V - v).max() <= p.beta ** 50 * e0 * (1 + 1e-9)
+
+
+def test_eval_diag_sweep_closed_form_half_step():
+    # x' = 1 with dt = h / 2: every foot lies half-way to the right neighbour,
+    # so a node's own weight is 1/2 and the other 1/2 sits on node j + 1:
+    # V'_j = (dt + beta V_{j+1} / 2) / (1 - beta / 2)
+    p = W.unit_speed_1d().replace(dt=0.5 / 16)
+    o = oracle.Oracle(p)
+    codes = np.zeros(p.nodes, np.uint16)
+    V = W.smooth_value(p, 31)
+    Vn, _ = o.eval_diag_sweep(V, codes)
+    Vg, Vng = V.reshape(p.n), Vn.reshape(p.n)
+    for i in range(15):
+        if i == 8:
+            assert Vng[i, 0, 0, 0] == 0.0
+            continue
+        want = (p.dt + p.beta * 0.5 * Vg[i + 1]) / (1.0 - 0.5 * p.beta)
+        assert np.allclose(Vng[i], want, rtol=1e-14, atol=0)
+
+
+def test_eval_diag_sweep_has_the_exact_evaluation_as_fixed_point_and_contracts():
+    for p in (W.config1(13).replace(n=(11, 9, 9, 9)), W.example1(n=(12, 7, 7, 8))):
+        o = oracle.Oracle(p)
+        codes = W.random_codes(p, 33)
+        if p.off_control:
+            codes[::5] = oracle.CODE_OFF
+        v = o.evaluate_exact(codes)
+        v1, r = o.eval_diag_sweep(v, codes)
+        assert r <= 1e-12 * np.abs(v).max()
+        # a beta-contraction in the sup norm (row factor beta (1 - w) / (1 - beta w) <= beta)
+        U = W.smooth_value(p, 34) * np.abs(v).max() / o.M
+        X = W.smooth_value(p, 35) * np.abs(v).max() / o.M
+        act = o.active.astype(bool)
+        dU, _ = o.eval_diag_sweep(U, codes)
+        dX, _ = o.eval_diag_sweep(X, codes)
+        assert np.abs(dU - dX)[act].max() <= o.s.beta * np.abs(U - X)[act].max() * (1 + 1e-12)
+        # and it converges no slower than the plain evaluation sweep
+        Vp, Vd = np.zeros(p.nodes), np.zeros(p.nodes)
+        for _ in range(30):
+            Vp = o.sweep(Vp, mode=oracle.EVAL, codes=codes)[0]
+            Vd = o.eval_diag_sweep(Vd, codes)[0]
+        assert np.abs(Vd - v)[act].max() <= np.abs(Vp - v)[act].max() * (1 + 1e-12)
