@@ -76,11 +76,19 @@ extern "C" {
                                     (+ refinement), §3 "Efficient computation of
                                     the minimum"                                   */
 #define DP_SWEEP_EVAL         3  /* Eq. (13): one Jacobi sweep at the frozen policy */
+#define DP_SWEEP_EVAL_DIAG    4  /* Eq. (13) as a linear system: one Jacobi iteration
+                                    with each node's own coefficient solved,
+                                    V'_j = V_j + (T_f(V)_j - V_j) / (1 - beta w_jj),
+                                    w_jj the node's own weight among the Q1
+                                    corners of its foot (same fixed point)     */
 
 /* How policy iteration evaluates a frozen policy (dp_solve_opts.eval_solver). */
 #define DP_EVAL_JACOBI 0     /* n_eval Jacobi sweeps (modified policy iteration)   */
 #define DP_EVAL_GMRES  1     /* the linear system of Eq. (13) by restarted GMRES,
                                 as §3 prescribes after Eq. (14)                    */
+#define DP_EVAL_DIAG   2     /* n_eval DP_SWEEP_EVAL_DIAG iterations: the Jacobi
+                                method proper on that system (the node's own
+                                coefficient solved), same fixed point          */
 #define DP_GMRES_MAX_RESTART 64
 
 typedef struct dp_grid dp_grid;
@@ -143,7 +151,7 @@ typedef struct dp_solve_opts {
      * each cycle starts from the residual T_f(V) - V of the value the
      * improvement sweep produced and adds the minimal-residual correction
      * from an Arnoldi basis of up to gmres_restart vectors. */
-    int32_t eval_solver;   /* DP_EVAL_JACOBI (0) or DP_EVAL_GMRES                     */
+    int32_t eval_solver;   /* DP_EVAL_JACOBI (0), DP_EVAL_GMRES or DP_EVAL_DIAG        */
     int32_t gmres_restart; /* Arnoldi steps per cycle, 1..DP_GMRES_MAX_RESTART
                               (0: 30)                                              */
     int32_t gmres_cycles;  /* cycles per evaluation (0: 1); cycles after the first
@@ -214,7 +222,7 @@ int dp_get_policy(const dp_grid* grid, uint16_t* host_codes, int64_t count);
 
 /* One Jacobi sweep of the scheme on the resident V and policy (mode =
  * DP_SWEEP_*): Eq. (12), (13) or (14).  Improvement modes rewrite the policy;
- * EVAL reads it.  On FP32 grids whose value has moved to FP64 (after a
+ * EVAL and EVAL_DIAG read it.  On FP32 grids whose value has moved to FP64 (after a
  * polish) the sweep runs with FP64 values.  *residual (nullable) receives
  * max_j |V'_j - V_j| over the stored nodes, accumulated in FP64. */
 int dp_bellman_sweep(dp_grid* grid, int32_t mode, double* residual);
@@ -410,7 +418,7 @@ int dp_batch_get_policy(const dp_batch* batch, int32_t index, uint16_t* host_cod
  * extra cudaMalloc can fail or fragment that pool.  dp_grid_create allocates,
  * so such callers cannot hold a grid; this call needs none.
  *
- * It runs the same sweep as dp_bellman_sweep (mode = DP_SWEEP_*) for the
+ * It runs the same sweep as dp_bellman_sweep (mode = DP_SWEEP_VI ... EVAL) for the
  * full-box grid that desc describes (desc->reduced must be 0), on buffers the
  * caller owns, in desc->stream on the current device:
  *   V_in   device, n0 n1 n2 n3 values in box order, double (DP_FP64) or float

@@ -306,6 +306,7 @@ Store store_of(const dp_grid* g)
 cudaError_t enqueue_sweep(dp_grid* g, int mode, long long t, int check_prev, double tol)
 {
     int a = (int)(t & 1);
+    if (mode == DP_SWEEP_EVAL_DIAG && store_of(g) != kStoreF32) mode = kEvalDiag;
     switch (store_of(g)) {
     case kStoreF64: {
         const double* in = (const double*)g->V[(g->cur + a) & 1];
@@ -319,6 +320,7 @@ cudaError_t enqueue_sweep(dp_grid* g, int mode, long long t, int check_prev, dou
         // evaluation sweeps after them read those instead of recomputing
         if (mode == DP_SWEEP_IMPROVE_FULL || mode == DP_SWEEP_IMPROVE_WALK) g->feet_valid = g->feet_lo != nullptr;
         if (mode == DP_SWEEP_EVAL && g->feet_valid) mode = kEvalFeet;
+        if (mode == DP_SWEEP_EVAL_DIAG) mode = g->feet_valid ? kEvalFeetDiag : kEvalDiag;
         return launch_sweep(sweep_launch<float, float>(g, g->g32, in, out, mode, t, check_prev, tol));
     }
     default: {
@@ -344,10 +346,11 @@ cudaError_t enqueue_polish_improve(dp_grid* g, int mode, int c, long long t, int
     return launch_sweep(L);
 }
 
-cudaError_t enqueue_increment(dp_grid* g, int c, int e, int n, long long t, int check_prev, double tol)
+cudaError_t enqueue_increment(dp_grid* g, int c, int e, int n, long long t, int check_prev, double tol, bool diag)
 {
     SweepLaunch<float, float> L = sweep_launch<float, float>(g, g->g32, (const float*)g->V[e & 1],
-                                                             (float*)g->V[(e + 1) & 1], kIncr, t, check_prev, tol);
+                                                             (float*)g->V[(e + 1) & 1], diag ? kIncrDiag : kIncr, t,
+                                                             check_prev, tol);
     L.acc = g->acc;
     L.V64 = g->V64[c];
     L.incr_flags = (e == 0 ? 1 : 0) | (e == n - 1 ? 2 : 0);
@@ -1129,7 +1132,7 @@ int dp_get_policy(const dp_grid* g, uint16_t* host_codes, int64_t count)
 int dp_bellman_sweep(dp_grid* g, int32_t mode, double* residual)
 {
     if (!g) return fail(DP_EINVAL, "grid is NULL");
-    if (mode < DP_SWEEP_VI || mode > DP_SWEEP_EVAL) return fail(DP_EINVAL, "unknown sweep mode %d", mode);
+    if (mode < DP_SWEEP_VI || mode > DP_SWEEP_EVAL_DIAG) return fail(DP_EINVAL, "unknown sweep mode %d", mode);
     if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
     int rc;
     if ((rc = reset_ctl(g)) || (rc = clear_ring(g, 0, 1))) return rc;
@@ -1198,8 +1201,9 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
 {
     if (!g || !o) return fail(DP_EINVAL, "NULL argument");
     if (o->max_sweeps < 0 || o->n_eval < 0 || !(o->tol >= 0)) return fail(DP_EINVAL, "bad options");
-    if (o->eval_solver != DP_EVAL_JACOBI && o->eval_solver != DP_EVAL_GMRES)
+    if (o->eval_solver != DP_EVAL_JACOBI && o->eval_solver != DP_EVAL_GMRES && o->eval_solver != DP_EVAL_DIAG)
         return fail(DP_EINVAL, "unknown eval_solver %d", o->eval_solver);
+    const bool diag = o->eval_solver == DP_EVAL_DIAG;
     if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
     double t0 = now_ms();
     dp_solve_stats S;
@@ -1246,8 +1250,8 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
             CK(T.end());
             for (int e = 0; e < o->n_eval; ++e) {
                 CK(T.begin(mix ? kTEval64 : kTEval));
-                if (mix) CK(enqueue_increment(g, c64 ^ 1, e, o->n_eval, ti + 1 + e, e == 0, o->tol));
-                else CK(enqueue_sweep(g, DP_SWEEP_EVAL, ti + 1 + e, e == 0, o->tol));
+                if (mix) CK(enqueue_increment(g, c64 ^ 1, e, o->n_eval, ti + 1 + e, e == 0, o->tol, diag));
+                else CK(enqueue_sweep(g, diag ? DP_SWEEP_EVAL_DIAG : DP_SWEEP_EVAL, ti + 1 + e, e == 0, o->tol));
                 CK(T.end());
             }
             c64 ^= 1;

@@ -26,7 +26,16 @@ constexpr int kBlock = 256;         // threads per block of the sweep kernels
 constexpr int kMaxFib = 30;
 constexpr int kMaxAngles = 1024;   // tabulated angles per grid (shared-memory table)
 
-enum { kVI = 0, kImproveFull = 1, kImproveWalk = 2, kEval = 3, kEvalFeet = 4, kIncr = 5 };
+enum { kVI = 0, kImproveFull = 1, kImproveWalk = 2, kEval = 3, kEvalFeet = 4, kIncr = 5,
+       kEvalDiag = 6, kEvalFeetDiag = 7, kIncrDiag = 8 };
+// kEval*Diag, kIncrDiag: the evaluation as a Jacobi iteration on the linear
+// system of Eq. (13) with each node's own coefficient solved exactly (the
+// weight w_jj of node j among the Q1 corners of its own foot):
+//   V'_j = V_j + (T_f(V)_j - V_j) / (1 - beta w_jj),
+// which has the fixed point of the plain evaluation sweep.  Where the foot
+// stays in the node's own cell (w_jj near 1: the mass moves ~0.002 cells per
+// step) the plain sweep contracts by beta w_jj ~ 0.997 there; this one does
+// not.
 enum { kDynOrbit = 0, kDynUnitSpeed = 1, kDynPolar = 2 };
 constexpr int kCodeOff = 65535;     // policy code of the thrust-off control
 
@@ -428,6 +437,21 @@ __device__ __forceinline__ FootWord encode_foot(const int i[4], const int c[4], 
     return w;
 }
 
+// Weight of node i among the Q1 corners of cell c with fractions t (0 when i
+// is not a corner of the cell).
+template <typename G, bool PER3>
+__device__ __forceinline__ G self_weight(const Geo<G>& g, const int i[4], const int c[4], const G t[4])
+{
+    G w = (G)1;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        int hi = c[d] + 1;
+        if (PER3 && d == 3 && hi == g.n[3]) hi = 0;
+        w *= i[d] == c[d] ? (G)1 - t[d] : (i[d] == hi ? t[d] : (G)0);
+    }
+    return w;
+}
+
 // Q1 interpolation at the foot i + u (grid units), returned as the difference
 // D = I[V] - vj; M - vj when the foot is outside the box or the node set.
 template <typename G, typename S, bool REDUCED, bool PER3 = false>
@@ -441,6 +465,25 @@ __device__ __forceinline__ typename BlendType<G, S>::type interp_delta(const Geo
     if (foot_cell<G, PER3>(g, i, u, c, t) || load_corners<R, G, S, REDUCED, PER3>(g, V, c, vj, K))
         return (R)((S)g.M64 - vj);
     const R tr[4] = {(R)t[0], (R)t[1], (R)t[2], (R)t[3]};
+    return K.blend(tr);
+}
+
+// The same, also returning the node's own weight among the corners (0 when
+// the foot is outside: that row of the system is empty).
+template <typename G, typename S, bool REDUCED, bool PER3 = false>
+__device__ __forceinline__ typename BlendType<G, S>::type interp_delta_w(const Geo<G>& g, const S* __restrict__ V,
+                                                                         const int i[4], const G u[4], S vj,
+                                                                         typename BlendType<G, S>::type& wself)
+{
+    typedef typename BlendType<G, S>::type R;
+    int c[4];
+    G t[4];
+    Corners<R> K;
+    wself = (R)0;
+    if (foot_cell<G, PER3>(g, i, u, c, t) || load_corners<R, G, S, REDUCED, PER3>(g, V, c, vj, K))
+        return (R)((S)g.M64 - vj);
+    const R tr[4] = {(R)t[0], (R)t[1], (R)t[2], (R)t[3]};
+    wself = (R)self_weight<G, PER3>(g, i, c, t);
     return K.blend(tr);
 }
 
@@ -471,6 +514,23 @@ struct NodeEval {
         G s, c;
         code_sincos(*g, code, s, c);
         return at_sc(s, c);
+    }
+
+    // with the node's own weight among the corners
+    __device__ __forceinline__ R at_sc_w(G s, G c, R& wself)
+    {
+        G u[4];
+        heun_cells<G, DYN>(*g, sp, nd, s, c, u);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) u[d] += u0[d];
+        return interp_delta_w<G, S, REDUCED, DYN == kDynPolar>(*g, V, i, u, vj, wself);
+    }
+
+    __device__ __forceinline__ R at_code_w(int code, R& wself)
+    {
+        G s, c;
+        code_sincos(*g, code, s, c);
+        return at_sc_w(s, c, wself);
     }
 };
 

@@ -139,13 +139,32 @@ __device__ __forceinline__ float eval_foot(const Geo<float>& g, const float* __r
     return K.blend(t);
 }
 
+// Node j's own weight among the corners of its frozen foot (kind inside):
+// per coordinate 1 - t where the cell starts at the node, t where it ends
+// there, 0 otherwise.
+__device__ __forceinline__ float foot_self_weight(const Geo<float>& g, FootWord w)
+{
+    const int dr = (int)((w.hi >> 8) & 3u) - 2;
+    const int dv = (int)((w.hi >> 10) & 15u) - 8;
+    const int dt = (int)((w.hi >> 14) & 3u) - 2;
+    const unsigned q2 = (unsigned)(w.lo >> 48) | ((w.hi & 0xffu) << 16);
+    const float t0 = (float)(unsigned)(w.lo & 0xffffffu) * (1.0f / kFootQ);
+    const float t1 = (float)(unsigned)((w.lo >> 24) & 0xffffffu) * (1.0f / kFootQ);
+    const float t2 = (float)q2 * (1.0f / kFootQ);
+    auto f = [](int off, float t) { return off == 0 ? 1.0f - t : (off == -1 ? t : 0.0f); };
+    return f(dr, t0) * f(dv, t1) * f(dt, t2) * f(g.foot_dm, g.foot_tm);
+}
+
 // Blend of increments d at node j's recomputed foot for a policy code: the
-// foot of an outside or target node carries no increment.
+// foot of an outside or target node carries no increment.  *wself
+// (nullable): node j's own weight among the corners.
 template <bool REDUCED, int DYN>
-__device__ __forceinline__ float incr_recompute(const Geo<float>& g, const float* __restrict__ d, int j, int code)
+__device__ __forceinline__ float incr_recompute(const Geo<float>& g, const float* __restrict__ d, int j, int code,
+                                                float* wself = nullptr)
 {
     NodeEval<float, float, REDUCED, DYN> ev;
     decode_node(g, j, ev.i);
+    if (wself) *wself = 0.0f;
     if (in_target(g, ev.i)) return 0.0f;
     setup_node<float, float, DYN>(ev, g, d, 0.0f);
     float s, c, u[4], t[4];
@@ -154,7 +173,19 @@ __device__ __forceinline__ float incr_recompute(const Geo<float>& g, const float
     heun_cells<float, DYN>(g, ev.sp, ev.nd, s, c, u);
     Corners<float> K;
     if (foot_cell(g, ev.i, u, cl, t) || load_corners<float, float, float, REDUCED>(g, d, cl, 0.0f, K)) return 0.0f;
+    if (wself) *wself = self_weight<float, false>(g, ev.i, cl, t);
     return K.blend(t);
+}
+
+// The diagonal-solved step of the evaluation: V_j + (T_f(V)_j - V_j) / (1 - beta w_jj).
+__device__ __forceinline__ float diag_step(const Geo<float>& g, float vj, float vplain, float ws)
+{
+    return vj + (vplain - vj) / (1.0f - (g.beta_hi + g.beta_lo) * ws);
+}
+template <typename G>
+__device__ __forceinline__ double diag_step(const Geo<G>& g, double vj, double vplain, double ws)
+{
+    return vj + (vplain - vj) / (1.0 - g.beta64 * ws);
 }
 
 // Sweeps nodes j0, j0 + stride, ... < end of one grid: the per-node work of
@@ -174,7 +205,8 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
     constexpr bool kPolish = kGeo32 && std::is_same<S, double>::value;   // FP32 geometry, FP64 values
     (void)T;
     (void)kSearch;
-    if constexpr (MODE == kEvalFeet || MODE == kIncr) {
+    if constexpr (MODE == kEvalFeet || MODE == kIncr || MODE == kEvalFeetDiag || MODE == kIncrDiag) {
+        constexpr bool kDiag = MODE == kEvalFeetDiag || MODE == kIncrDiag;
         // frozen feet: gather-bound, so the next node's foot and value are
         // fetched while this node's corners are in flight.  The feet are read
         // once per sweep: evict-first loads keep L1 and L2 for the gathered V.
@@ -197,26 +229,44 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
             }
             const int kind = (int)((w.hi >> 16) & 3u);
             S vnew = (S)0;
-            if constexpr (MODE == kEvalFeet) {
+            if constexpr (MODE == kEvalFeet || MODE == kEvalFeetDiag) {
+                float ws = 0.0f;
                 if (kind == kFootInside) {
                     vnew = bellman_value<G, S>(g, vj, eval_foot<REDUCED>(g, Vin, j, w, vj));
+                    if constexpr (kDiag) ws = foot_self_weight(g, w);
                 } else if (kind == kFootOut) {
                     vnew = bellman_value<G, S>(g, vj, (G)((S)g.M64 - vj));
                 } else if (kind == kFootRecompute) {
                     NodeEval<G, S, REDUCED, DYN> ev;
                     decode_node(g, j, ev.i);
                     setup_node<G, S, DYN>(ev, g, Vin, vj);
-                    vnew = bellman_value<G, S>(g, vj, ev.at_code(code[j]));
+                    if constexpr (kDiag) vnew = bellman_value<G, S>(g, vj, ev.at_code_w(code[j], ws));
+                    else vnew = bellman_value<G, S>(g, vj, ev.at_code(code[j]));
+                }
+                if constexpr (kDiag) {
+                    if (kind != kFootTarget) vnew = diag_step(g, vj, vnew, ws);
                 }
                 Vout[j] = vnew;
                 resid = fmax(resid, (S)fabs(vnew - vj));
             } else {
                 // increment: d' = beta W d at the frozen policy (no running cost,
-                // no penalty: both cancel between consecutive sweeps)
-                float D = 0.0f;
-                if (kind == kFootInside) D = eval_foot<REDUCED>(g, Vin, j, w, 0.0f);
-                else if (kind == kFootRecompute) D = incr_recompute<REDUCED, DYN>(g, Vin, j, code[j]);
-                vnew = fmaf(g.beta_hi, D, g.beta_lo * D);
+                // no penalty: both cancel between consecutive sweeps).  Diagonal
+                // solved: the first increment after the improvement's plain step
+                // is beta W d scaled by 1 / (1 - beta w_jj), later ones use the
+                // off-diagonal weights only, d' = beta (W d - w_jj d_j) / (1 - beta w_jj)
+                float D = 0.0f, ws = 0.0f;
+                if (kind == kFootInside) {
+                    D = eval_foot<REDUCED>(g, Vin, j, w, 0.0f);
+                    if constexpr (kDiag) ws = foot_self_weight(g, w);
+                } else if (kind == kFootRecompute) {
+                    D = incr_recompute<REDUCED, DYN>(g, Vin, j, code[j], kDiag ? &ws : nullptr);
+                }
+                if constexpr (kDiag) {
+                    const float Dx = first ? D : D - ws * vj;
+                    vnew = fmaf(g.beta_hi, Dx, g.beta_lo * Dx) / (1.0f - (g.beta_hi + g.beta_lo) * ws);
+                } else {
+                    vnew = fmaf(g.beta_hi, D, g.beta_lo * D);
+                }
                 Vout[j] = vnew;
                 const float sum = (first ? 0.0f : acc[j]) + vnew;
                 if (last) V64[j] += (double)sum;
@@ -252,6 +302,14 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                         const int c0 = code[j];
                         if (g.off && c0 == kCodeOff) q = lrun + g.beta64 * ((double)vj + (double)ev.at_sc((G)0, (G)0));
                         else q = lrun + g.thrust_cost + g.beta64 * ((double)vj + (double)ev.at_code(c0));
+                    } else if constexpr (MODE == kEvalDiag) {
+                        const int c0 = code[j];
+                        typename Eval::R ws;
+                        if (g.off && c0 == kCodeOff)
+                            q = lrun + g.beta64 * ((double)vj + (double)ev.at_sc_w((G)0, (G)0, ws));
+                        else
+                            q = lrun + g.thrust_cost + g.beta64 * ((double)vj + (double)ev.at_code_w(c0, ws));
+                        q = diag_step(g, (double)vj, q, (double)ws);
                     } else {
                         ev.reset();
                         typename Eval::R D;
@@ -279,8 +337,12 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
             } else if (!in_target(g, ev.i)) {
                 setup_node<G, S, DYN>(ev, g, Vin, vj);
                 typename Eval::R D;
+                typename Eval::R ws = 0;
+                (void)ws;
                 if constexpr (MODE == kEval) {
                     D = ev.at_code(code[j]);
+                } else if constexpr (MODE == kEvalDiag) {
+                    D = ev.at_code_w(code[j], ws);
                 } else {
                     ev.reset();
                     int k;
@@ -330,6 +392,7 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                 if constexpr (kPolish) vnew = (S)bellman_value(g, (double)vj, (double)D);
                 else vnew = bellman_value<G, S>(g, vj, D);
                 if constexpr (kImprove && kPolish) vnew = (S)vnew64;
+                if constexpr (MODE == kEvalDiag) vnew = (S)diag_step(g, vj, vnew, ws);
             } else if constexpr (kGeo32 && kImprove) {
                 if (feet_lo) {
                     const FootWord w = foot_word_kind(kFootTarget);
@@ -368,7 +431,10 @@ __device__ __forceinline__ void block_fold(S resid, bool bad, unsigned long long
 // more gathers in flight, so they are compiled for 6 blocks per SM (40
 // registers, no spills; 8 blocks would spill).
 template <int MODE>
-constexpr int min_blocks() { return (MODE == kEvalFeet || MODE == kIncr) ? 6 : 1; }
+constexpr int min_blocks()
+{
+    return (MODE == kEvalFeet || MODE == kIncr || MODE == kEvalFeetDiag || MODE == kIncrDiag) ? 6 : 1;
+}
 
 template <typename G, typename S, int MODE, bool REDUCED, int DYN>
 __global__ void __launch_bounds__(kBlock, min_blocks<MODE>())
@@ -442,6 +508,15 @@ cudaError_t launch_mode(const SweepLaunch<G, S>& L)
     case kIncr:
         if constexpr (f32)
             return (L.feet_lo && L.acc && L.V64) ? launch_one<G, S, kIncr, REDUCED, DYN>(L) : cudaErrorInvalidValue;
+        return cudaErrorInvalidValue;
+    case kEvalDiag: return launch_one<G, S, kEvalDiag, REDUCED, DYN>(L);
+    case kEvalFeetDiag:
+        if constexpr (f32) return L.feet_lo ? launch_one<G, S, kEvalFeetDiag, REDUCED, DYN>(L) : cudaErrorInvalidValue;
+        return cudaErrorInvalidValue;
+    case kIncrDiag:
+        if constexpr (f32)
+            return (L.feet_lo && L.acc && L.V64) ? launch_one<G, S, kIncrDiag, REDUCED, DYN>(L)
+                                                 : cudaErrorInvalidValue;
         return cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;

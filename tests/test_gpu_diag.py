@@ -1,0 +1,133 @@
+"""The evaluation as the Jacobi method proper on the linear system of Eq. (13):
+each node's own coefficient solved (DP_SWEEP_EVAL_DIAG, DP_EVAL_DIAG), against
+the oracle's eval_diag_sweep (pinned by the CPU tests) and, for whole solves,
+against the oracle's fixed point, which this iteration shares with the plain
+evaluation sweep.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_14675_gb300 import workloads as W
+from test_gpu_parity import TOL32, TOL64, _check_values
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(name):
+    if name == "config1_11x9x9x9_fp64":
+        return W.config1(13).replace(n=(11, 9, 9, 9), precision=W.FP64)
+    if name == "example1_12x7x7x8":
+        return W.example1(n=(12, 7, 7, 8))
+    if name == "band_13x4_fp64":
+        return W.config2(13).replace(precision=W.FP64)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["config1_11x9x9x9_fp64", "example1_12x7x7x8", "band_13x4_fp64"])
+def test_eval_diag_sweep_matches_oracle_fp64(dp, name):
+    p = _problem(name)
+    o = oracle.Oracle(p)
+    codes = W.random_codes(p, 41)
+    if p.off_control:
+        codes[::6] = oracle.CODE_OFF
+    scale = 1.0 if not p.off_control else 1e-2
+    V = W.smooth_value(p, 42) * scale
+    V[o.target.astype(bool)] = 0.0
+    idx = np.flatnonzero(o.active)
+    want, r_o = o.eval_diag_sweep(V, codes)
+    with dp.Grid(p) as g:
+        g.set_value(V[idx])
+        g.set_policy(codes[idx])
+        r = g.sweep(dp.DP_SWEEP_EVAL_DIAG)
+        v = g.get_value()
+    _check_values(v, want[idx], TOL64, name)
+    assert abs(r - r_o) <= TOL64 * np.abs(want).max()
+
+
+def test_eval_diag_sweep_fp32_frozen_feet_and_recomputed(dp):
+    p = W.config1(n=17)
+    o = oracle.Oracle(p)
+    V0 = W.smooth_value(p, 43)
+    V0[o.target.astype(bool)] = 0.0
+    with dp.Grid(p) as g:
+        # recomputed feet: a policy set from the host has no frozen feet
+        codes = W.random_codes(p, 44)
+        g.set_value(V0)
+        g.set_policy(codes)
+        g.sweep(dp.DP_SWEEP_EVAL_DIAG)
+        v_rec = g.get_value()
+        want, _ = o.eval_diag_sweep(V0, codes)
+        _check_values(v_rec, want, TOL32, "recomputed", o=o, nodes=np.arange(p.nodes), codes=codes)
+        # frozen feet: stored by the improvement sweep
+        g.set_value(V0)
+        g.sweep(dp.DP_SWEEP_IMPROVE_FULL)
+        V1, c1 = g.get_value(), g.get_policy()
+        g.sweep(dp.DP_SWEEP_EVAL_DIAG)
+        v_feet = g.get_value()
+    want, _ = o.eval_diag_sweep(V1, c1)
+    _check_values(v_feet, want, TOL32, "frozen feet", o=o, nodes=np.arange(p.nodes), codes=c1)
+
+
+def test_diag_policy_iteration_fp32_with_polish_matches_oracle(dp):
+    # the problem of the Jacobi polish test; the FP64-value phase runs the
+    # diagonal-solved increments
+    p = W.config1(n=9).replace(beta=0.995, dt=0.1)
+    o = oracle.Oracle(p)
+    out = {}
+    for solver in (dp.DP_EVAL_JACOBI, dp.DP_EVAL_DIAG):
+        with dp.Grid(p) as g:
+            rc, st = g.policy_iterate(tol=1e-6, max_sweeps=5000, n_eval=20, polish=1, eval_solver=solver)
+            assert rc == dp.DP_OK and st.converged and st.residual < 1e-6, st.asdict()
+            out[solver] = (g.get_value(), st)
+    v_gpu, st = out[dp.DP_EVAL_DIAG]
+    assert st.sweeps_improve_fp64 > 0
+    st_j = out[dp.DP_EVAL_JACOBI][1]
+    assert st.sweeps_improve + st.sweeps_improve_fp64 < st_j.sweeps_improve + st_j.sweeps_improve_fp64
+    V, codes, outer, ev, res = o.policy_iterate(tol=1e-9, max_outer=20000, n_eval=20)
+    _check_values(v_gpu, V, TOL32, "diagonal-solved policy iteration, FP32 + polish")
+
+
+def test_diag_policy_iteration_fp64_matches_oracle(dp):
+    p = W.config1(n=9).replace(beta=0.995, dt=0.1, precision=W.FP64)
+    o = oracle.Oracle(p)
+    with dp.Grid(p) as g:
+        rc, st = g.policy_iterate(tol=1e-10, max_sweeps=5000, n_eval=20, eval_solver=dp.DP_EVAL_DIAG)
+        assert rc == dp.DP_OK and st.converged, st.asdict()
+        v_gpu = g.get_value()
+    V, codes, outer, ev, res = o.policy_iterate(tol=1e-12, max_outer=20000, n_eval=20)
+    _check_values(v_gpu, V, 1e-7, "diagonal-solved policy iteration, FP64")
+
+
+def test_diag_policy_iteration_example1_matches_jacobi(dp):
+    p = W.example1(n=(12, 7, 7, 8))
+    o = oracle.Oracle(p)
+    out = {}
+    for solver in (dp.DP_EVAL_JACOBI, dp.DP_EVAL_DIAG):
+        with dp.Grid(p) as g:
+            rc, st = g.policy_iterate(tol=1e-7, max_sweeps=2000, n_eval=20, polish=0, eval_solver=solver)
+            assert rc == dp.DP_OK and st.converged, st.asdict()
+            out[solver] = (g.get_value(), st)
+    v_j, st_j = out[dp.DP_EVAL_JACOBI]
+    v_d, st_d = out[dp.DP_EVAL_DIAG]
+    assert st_d.sweeps_improve <= st_j.sweeps_improve
+    scale = np.abs(v_j).max()
+    assert np.abs(v_d - v_j).max() <= 2e-7 / (1 - p.beta) + 1e-12 * scale
+    v1, _, r, _ = o.sweep(v_d, mode=oracle.IMPROVE_FULL)
+    assert r <= 1e-6 * scale
+
+
+def test_diag_modes_are_rejected_where_unsupported(dp):
+    import torch
+    p = W.config1(n=9)
+    a = torch.zeros(p.nodes, device="cuda", dtype=torch.float32)
+    b = torch.zeros(p.nodes, device="cuda", dtype=torch.float32)
+    c = torch.zeros(p.nodes, device="cuda", dtype=torch.int16)
+    desc = dp.desc_from_problem(p, stream=int(torch.cuda.current_stream().cuda_stream))
+    with pytest.raises(dp.DPError) as e:
+        dp.dp_bellman_sweep_noalloc(desc, dp.DP_SWEEP_EVAL_DIAG, a.data_ptr(), b.data_ptr(), c.data_ptr())
+    assert e.value.code == dp.DP_EINVAL
+    with dp.Grid(p) as g:
+        with pytest.raises(dp.DPError) as e:
+            g.sweep(5)
+        assert e.value.code == dp.DP_EINVAL
