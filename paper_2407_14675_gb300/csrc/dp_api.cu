@@ -319,8 +319,9 @@ cudaError_t enqueue_sweep(dp_grid* g, int mode, long long t, int check_prev, dou
         // improvement sweeps store the frozen feet of the new policy; the
         // evaluation sweeps after them read those instead of recomputing
         if (mode == DP_SWEEP_IMPROVE_FULL || mode == DP_SWEEP_IMPROVE_WALK) g->feet_valid = g->feet_lo != nullptr;
-        if (mode == DP_SWEEP_EVAL && g->feet_valid) mode = kEvalFeet;
+        // (public and internal mode numbers overlap: map each public mode once)
         if (mode == DP_SWEEP_EVAL_DIAG) mode = g->feet_valid ? kEvalFeetDiag : kEvalDiag;
+        else if (mode == DP_SWEEP_EVAL && g->feet_valid) mode = kEvalFeet;
         return launch_sweep(sweep_launch<float, float>(g, g->g32, in, out, mode, t, check_prev, tol));
     }
     default: {
