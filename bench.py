@@ -266,7 +266,8 @@ def extra_legs(args, dp, W, torch, g1, p1):
         # Jacobi sweeps or by GMRES
         pi = {}
         for name, kw in (("jacobi20", {"n_eval": 20}),
-                         ("gmres", {"eval_solver": dp.DP_EVAL_GMRES, "gmres_restart": args.gmres_restart_fp64})):
+                         ("gmres", {"eval_solver": dp.DP_EVAL_GMRES, "gmres_restart": args.gmres_restart_fp64}),
+                         ("diag", {"eval_solver": dp.DP_EVAL_DIAG, "n_eval": args.diag_n_eval})):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             rc, s0 = g0.policy_iterate(tol=1e-8, max_sweeps=args.solve_max, polish=0, **kw)
@@ -302,8 +303,9 @@ def _kepler_a_e(x, mu):
 def example1_leg(args, dp, W, torch):
     """The paper's Example 1 (§4): 110 x 30 x 30 x 30 polar grid, running cost
     of Eq. (11), 72 angles + thrust off, FP64 policy iteration to 1e-7, with
-    each policy evaluated by GMRES (the paper's method) and, for comparison,
-    by 20 Jacobi sweeps; then the closed loop from the circular orbit at
+    each policy evaluated by 20 plain evaluation sweeps, by GMRES (the paper's
+    method) and by diagonal-solved Jacobi iterations; then the closed loop
+    (on the last solution) from the circular orbit at
     6978 km for 1e6 s, sampled every 2,000 s: when the semi-major axis comes
     within 1 km of 7000 km, when the thrust switches off for good, and the
     final orbit; and the same on the system with drag of Example 2."""
@@ -332,6 +334,19 @@ def example1_leg(args, dp, W, torch):
                         "gmres_cycles": s.gmres_cycles, "matvecs": s.gmres_matvecs,
                         "max_rel_diff_to_jacobi_solution": float(np.abs(v - v_jacobi).max() / np.abs(v_jacobi).max()),
                         "speedup_over_jacobi": out["solve_jacobi"]["seconds"] / secs}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, s = g.policy_iterate(tol=p.tol, max_sweeps=args.solve_max, polish=0, eval_solver=dp.DP_EVAL_DIAG,
+                                 n_eval=args.diag_n_eval)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        v = g.get_value()
+        out["solve_diag"] = {"seconds": secs, "converged": bool(s.converged), "residual": s.residual,
+                             "evaluation": "diagonal-solved Jacobi, %d per improvement" % args.diag_n_eval,
+                             "improvements": s.sweeps_improve, "evaluation_sweeps": s.sweeps_eval,
+                             "max_rel_diff_to_jacobi_solution": float(np.abs(v - v_jacobi).max() /
+                                                                      np.abs(v_jacobi).max()),
+                             "speedup_over_jacobi": out["solve_jacobi"]["seconds"] / secs}
         for name, drag in (("closed_loop", 0.0), ("closed_loop_with_drag", W.example2_drag())):
             # Example 2 of §4: the same feedback flown on a system with drag
             y = W.example1_start(6978.0)[None, :]
@@ -424,8 +439,8 @@ def warm_start_leg(args, dp, W, torch, g1, p1):
     """Learned warm start: train the network on the converged 61^4 solve
     (every stored node), then solve the 121^4 energy-band grid to 1e-6 from
     V = 0, from the network's V and policy, and from the 61^4 solution, with
-    the configured and with the tuned number of evaluation sweeps per
-    improvement; closed loop from 1024 seeded states on the last solution."""
+    the configured evaluation sweeps and with the diagonal-solved ones;
+    closed loop from 1024 seeded states on the last solution."""
     p2 = W.config2()
     out = {"grid": "121^4 box, energy band [%.4f, %.4f]" % (p2.energy_lo, p2.energy_hi)}
     with dp.Mlp(p1.lo, p1.hi, batch_capacity=65536) as net:
@@ -442,12 +457,12 @@ def warm_start_leg(args, dp, W, torch, g1, p1):
             out["nodes_active"] = g2.info["n_active"]
             V_cold = None
             # each start with the configured 20 evaluation sweeps per improvement,
-            # then again with the tuned count
-            tuned = "_n_eval_%d" % args.n_eval_tuned
-            runs = [(k, p2.n_eval) for k in ("cold", "warm", "from_61x4_grid")]
-            runs += [(k + tuned, args.n_eval_tuned) for k in ("cold", "warm", "from_61x4_grid")]
-            for start, n_eval in runs:
-                kind = start.split("_n_eval")[0]
+            # then again with the diagonal-solved evaluation
+            tuned = "_diag"
+            runs = [(k, p2.n_eval, dp.DP_EVAL_JACOBI) for k in ("cold", "warm", "from_61x4_grid")]
+            runs += [(k + tuned, args.diag_n_eval, dp.DP_EVAL_DIAG) for k in ("cold", "warm", "from_61x4_grid")]
+            for start, n_eval, solver in runs:
+                kind = start.split("_diag")[0]
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 ws_ms = 0.0
@@ -464,7 +479,7 @@ def warm_start_leg(args, dp, W, torch, g1, p1):
                             "max_over_M": float(err.max()), "rms_over_M": float(np.sqrt(np.mean(err ** 2)))}
                         t0 = time.perf_counter() - t_ws   # the host copy for the error is not timed
                 rc, s2 = g2.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=n_eval, polish=1,
-                                           warm=int(kind != "cold"))
+                                           warm=int(kind != "cold"), eval_solver=solver)
                 torch.cuda.synchronize()
                 if start == "cold":
                     V_cold = g2.get_value()
@@ -482,7 +497,9 @@ def warm_start_leg(args, dp, W, torch, g1, p1):
                         "frac_of_hbm": 10.0 * n_upd / (ev_ms / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
                         "walk_ms": sk.ms_improve / max(sk.sweeps_improve, 1)}
                 out[start] = {"seconds": time.perf_counter() - t0, "converged": bool(s2.converged),
-                              "residual": s2.residual, "n_eval": n_eval, "warm_start_ms": ws_ms,
+                              "residual": s2.residual, "n_eval": n_eval,
+                              "evaluation": "diagonal-solved Jacobi" if solver == dp.DP_EVAL_DIAG else "sweeps",
+                              "warm_start_ms": ws_ms,
                               "sweeps_improve": s2.sweeps_improve, "sweeps_eval": s2.sweeps_eval,
                               "sweeps_improve_fp64": s2.sweeps_improve_fp64,
                               "sweeps_eval_fp64": s2.sweeps_eval_fp64, "node_updates": s2.node_updates}
@@ -613,11 +630,27 @@ def run_ours(args, world, rank, local):
         solve_tuned = {"seconds": time.perf_counter() - t0, "converged": bool(st.converged), "residual": st.residual,
                        "n_eval": args.n_eval_tuned, "improvements": st.sweeps_improve + st.sweeps_improve_fp64,
                        "evaluation_sweeps": st.sweeps_eval + st.sweeps_eval_fp64}
+    solve_diag = None
+    if args.solve and rank == 0:
+        # the same cold solve with each evaluation sweep solving the node's own
+        # coefficient (the Jacobi method proper on the evaluation system)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = g.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=args.diag_n_eval, polish=1, warm=0,
+                                  eval_solver=dp.DP_EVAL_DIAG, time_kernels=1)
+        torch.cuda.synchronize()
+        solve_diag = {"seconds": time.perf_counter() - t0, "converged": bool(st.converged), "residual": st.residual,
+                      "evaluation": "diagonal-solved Jacobi", "n_eval": args.diag_n_eval,
+                      "improvements": st.sweeps_improve + st.sweeps_improve_fp64,
+                      "evaluation_sweeps": st.sweeps_eval + st.sweeps_eval_fp64,
+                      "gpu_ms": {"improve": st.ms_improve, "eval": st.ms_eval, "improve_fp64": st.ms_improve_fp64,
+                                 "eval_increments": st.ms_eval_fp64}}
     cascade = None
     if args.solve and rank == 0:
         # coarse to fine: the same problem on 16^4, then 31^4, each solved to
         # 1e-6 and interpolated onto the next grid (dp_warm_start_from_grid),
-        # then solved on 61^4 to 1e-6; every level with n_eval = cascade_n_eval
+        # then solved on 61^4 to 1e-6; every level with the diagonal-solved
+        # evaluation, n_eval = cascade_n_eval
         levels = [16, 31]
         grids = [dp.Grid(W.config1(n=n), stream=int(stream.cuda_stream)) for n in levels]
         torch.cuda.synchronize()
@@ -627,13 +660,14 @@ def run_ours(args, world, rank, local):
             if prev is not None:
                 dp.dp_warm_start_from_grid(prev.h, gc.h)
             rc, sc = gc.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=args.cascade_n_eval, polish=1,
-                                       warm=int(prev is not None))
+                                       warm=int(prev is not None), eval_solver=dp.DP_EVAL_DIAG)
             per.append({"grid": "%d^4" % n, "improvements": sc.sweeps_improve + sc.sweeps_improve_fp64,
                         "converged": bool(sc.converged), "ms": sc.ms_wall})
             prev = gc
         torch.cuda.synchronize()
         cascade = {"seconds": time.perf_counter() - t0, "converged": all(q["converged"] for q in per),
-                   "n_eval": args.cascade_n_eval, "levels": per, "residual": sc.residual}
+                   "evaluation": "diagonal-solved Jacobi", "n_eval": args.cascade_n_eval, "levels": per,
+                   "residual": sc.residual}
         for gc in grids:
             gc.close()
     warm = warm_start_leg(args, dp, W, torch, g, p) if (args.warm_start and args.solve and rank == 0) else None
@@ -689,6 +723,7 @@ def run_ours(args, world, rank, local):
                       "mix, %.1f s" % par_info["seconds"]},
         "time_to_tol": solve,
         "time_to_tol_n_eval_tuned": solve_tuned,
+        "time_to_tol_diag": solve_diag,
         "time_to_tol_coarse_to_fine": cascade,
         "time_to_tol_gmres": solve_gmres,
         "warm_start": warm,
@@ -719,7 +754,9 @@ def main():
     ap.add_argument("--cpu-parallel", type=int, default=1, help="also time the oracle on every host core")
     ap.add_argument("--example1", type=int, default=1, help="the paper's Example 1 solve and closed loop")
     ap.add_argument("--n-eval-tuned", type=int, default=160, help="evaluation sweeps per improvement, tuned solve")
-    ap.add_argument("--cascade-n-eval", type=int, default=120, help="evaluation sweeps per improvement, cascade")
+    ap.add_argument("--cascade-n-eval", type=int, default=20,
+                    help="diagonal-solved evaluation sweeps per improvement, cascade")
+    ap.add_argument("--diag-n-eval", type=int, default=40, help="diagonal-solved evaluation sweeps per improvement")
     ap.add_argument("--gmres-restart-fp64", type=int, default=60, help="GMRES restart length, FP64 grids")
     ap.add_argument("--gmres-restart-fp32", type=int, default=20, help="GMRES restart length, 61^4 FP32 grid")
     ap.add_argument("--batch-count", type=int, default=256)
