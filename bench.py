@@ -376,7 +376,8 @@ def example1_leg(args, dp, W, torch):
 
 def batch_leg(args, dp, W, torch):
     """Batched transfers: the 256-transfer batch solved to 1e-6 in one set of
-    graph-replayed persistent launches, the evaluation sweep's HBM roofline,
+    graph-replayed persistent launches (plain and diagonal-solved
+    evaluation), the evaluation sweep's HBM roofline,
     and, on a sample of the same transfers, the batched FP32 solve against
     plain FP64 policy iteration of each transfer on its own grid."""
     probs = W.batch_transfers(count=args.batch_count)
@@ -411,6 +412,18 @@ def batch_leg(args, dp, W, torch):
                         "launches": tot.launches, "max_residual": tot.residual,
                         "improvements_per_transfer": {"min": int(imp.min()), "median": float(np.median(imp)),
                                                       "max": int(imp.max())}}
+        # the same solve with the diagonal-solved evaluation
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, tot, per = b.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=args.diag_n_eval, polish=1,
+                                        eval_solver=dp.DP_EVAL_DIAG)
+        secs = time.perf_counter() - t0
+        imp = np.array([q["sweeps_improve"] + q["sweeps_improve_fp64"] for q in per])
+        out["solve_diag"] = {"seconds": secs, "converged": int(sum(q["converged"] for q in per)),
+                             "n_eval": args.diag_n_eval, "max_residual": tot.residual,
+                             "improvements_per_transfer": {"min": int(imp.min()), "median": float(np.median(imp)),
+                                                           "max": int(imp.max())},
+                             "speedup_over_sweeps": out["solve"]["seconds"] / secs}
     # the same transfers, sampled: batched FP32 vs plain FP64 per grid
     pick = [int(i) for i in np.linspace(0, len(probs) - 1, args.batch_fp64_sample)]
     sample = [probs[i] for i in pick]

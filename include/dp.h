@@ -389,7 +389,7 @@ int dp_batch_autotune(dp_batch* batch, int32_t* item_eval, int32_t* item_improve
 /* Modified policy iteration of every transfer with the options of
  * dp_policy_iterate (tol, max_sweeps = improvement budget per transfer,
  * n_eval <= 1024, walk, warm, polish, switch_tol; time_kernels and history are
- * ignored; eval_solver must be DP_EVAL_JACOBI).  total (nullable): sums of the sweep counts, node_updates,
+ * ignored; eval_solver DP_EVAL_JACOBI or DP_EVAL_DIAG).  total (nullable): sums of the sweep counts, node_updates,
  * launches, the largest residual and switch_outer, converged = all converged.
  * per (nullable): count entries.  Returns DP_ENOCONV if some transfer missed
  * the tolerance (statistics valid), DP_ENONFINITE if one produced a non-finite

@@ -204,7 +204,8 @@ __global__ void __launch_bounds__(kBlock, std::is_same<S, double>::value ? 2 : 3
 // Evaluation sweep e of an outer step (§3, Eq. (13)) at the frozen policy:
 // FP32 transfers blend at their frozen feet (FEET) or recompute them; FP64
 // transfers sweep increments.  e = -1 is a stand-alone sweep of V[cur].
-template <int DYN, bool FEET>
+// DIAG: each node's own coefficient solved (the Jacobi method proper).
+template <int DYN, bool FEET, bool DIAG>
 __global__ void __launch_bounds__(kBlock, 5) batch_eval_kernel(const BArgs a, int e, int n_eval)
 {
     __shared__ Geo<float> s_g;
@@ -230,16 +231,16 @@ __global__ void __launch_bounds__(kBlock, 5) batch_eval_kernel(const BArgs a, in
             const float* Vin = pick(a.V32, st.cur + 1 + e) + o;
             float* Vout = pick(a.V32, st.cur + 2 + e) + o;
             if constexpr (FEET)
-                sweep_nodes<float, float, kEvalFeet, false, DYN>(s_g, T, Vin, Vout, a.code + o, a.feet_lo + o,
-                                                                 a.feet_hi + o, nullptr, nullptr, nullptr, 0,
-                                                                 first + threadIdx.x, end, kBlock, resid, bad);
+                sweep_nodes<float, float, DIAG ? kEvalFeetDiag : kEvalFeet, false, DYN>(
+                    s_g, T, Vin, Vout, a.code + o, a.feet_lo + o, a.feet_hi + o, nullptr, nullptr, nullptr, 0,
+                    first + threadIdx.x, end, kBlock, resid, bad);
             else
-                sweep_nodes<float, float, kEval, false, DYN>(s_g, T, Vin, Vout, a.code + o, nullptr, nullptr,
-                                                             nullptr, nullptr, nullptr, 0, first + threadIdx.x,
-                                                             end, kBlock, resid, bad);
+                sweep_nodes<float, float, DIAG ? kEvalDiag : kEval, false, DYN>(
+                    s_g, T, Vin, Vout, a.code + o, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
+                    first + threadIdx.x, end, kBlock, resid, bad);
         } else if constexpr (FEET) {
             const int flags = (e == 0 ? 1 : 0) | (e == n_eval - 1 ? 2 : 0);
-            sweep_nodes<float, float, kIncr, false, DYN>(s_g, T, pick(a.V32, e) + o, pick(a.V32, e + 1) + o,
+            sweep_nodes<float, float, DIAG ? kIncrDiag : kIncr, false, DYN>(s_g, T, pick(a.V32, e) + o, pick(a.V32, e + 1) + o,
                                                          a.code + o, a.feet_lo + o, a.feet_hi + o, nullptr,
                                                          a.acc + o, pick(a.V64, st.cur64 ^ 1) + o, flags,
                                                          first + threadIdx.x, end, kBlock, resid, bad);
@@ -498,6 +499,7 @@ struct dp_batch {
     int blocks_eval = 0, blocks_eval_nf = 0;
     cudaGraphExec_t exec = nullptr;
     int graph_n_eval = -1, graph_item_eval = 0, graph_item_imp = 0;
+    bool graph_diag = false;
     long long graph_launches = 0;
     bool feet_valid = false;
     long long device_bytes = 0;
@@ -582,18 +584,20 @@ cudaError_t launch_improve(const dp_batch* b, bool fp64, bool full)
 }
 
 template <int DYN>
-cudaError_t launch_eval(const dp_batch* b, int e, int n_eval, bool feet)
+cudaError_t launch_eval(const dp_batch* b, int e, int n_eval, bool feet, bool diag)
 {
     const BArgs a = args_of(b);
-    if (feet) batch_eval_kernel<DYN, true><<<b->blocks_eval, kBlock, 0, b->st>>>(a, e, n_eval);
-    else batch_eval_kernel<DYN, false><<<b->blocks_eval_nf, kBlock, 0, b->st>>>(a, e, n_eval);
+    if (feet && diag) batch_eval_kernel<DYN, true, true><<<b->blocks_eval, kBlock, 0, b->st>>>(a, e, n_eval);
+    else if (feet) batch_eval_kernel<DYN, true, false><<<b->blocks_eval, kBlock, 0, b->st>>>(a, e, n_eval);
+    else if (diag) batch_eval_kernel<DYN, false, true><<<b->blocks_eval_nf, kBlock, 0, b->st>>>(a, e, n_eval);
+    else batch_eval_kernel<DYN, false, false><<<b->blocks_eval_nf, kBlock, 0, b->st>>>(a, e, n_eval);
     return cudaGetLastError();
 }
 
-cudaError_t launch_eval(const dp_batch* b, int e, int n_eval, bool feet)
+cudaError_t launch_eval(const dp_batch* b, int e, int n_eval, bool feet, bool diag = false)
 {
-    return b->dyn == DP_DYN_ORBIT ? launch_eval<kDynOrbit>(b, e, n_eval, feet)
-                                  : launch_eval<kDynUnitSpeed>(b, e, n_eval, feet);
+    return b->dyn == DP_DYN_ORBIT ? launch_eval<kDynOrbit>(b, e, n_eval, feet, diag)
+                                  : launch_eval<kDynUnitSpeed>(b, e, n_eval, feet, diag);
 }
 
 cudaError_t launch_widen(const dp_batch* b)
@@ -604,7 +608,7 @@ cudaError_t launch_widen(const dp_batch* b)
 
 // One outer step of every live transfer: widen, improvements, decisions,
 // evaluation sweeps, end-of-step bookkeeping.
-cudaError_t enqueue_step(const dp_batch* b, int n_eval, long long* launches)
+cudaError_t enqueue_step(const dp_batch* b, int n_eval, bool diag, long long* launches)
 {
     cudaError_t e;
     if ((e = launch_widen(b)) != cudaSuccess) return e;
@@ -612,15 +616,15 @@ cudaError_t enqueue_step(const dp_batch* b, int n_eval, long long* launches)
         if ((e = launch_improve(b, k >= 2, (k & 1) == 0)) != cudaSuccess) return e;
     if ((e = launch_ctl(b, kStAfterImp)) != cudaSuccess) return e;
     for (int k = 0; k < n_eval; ++k)
-        if ((e = launch_eval(b, k, n_eval, true)) != cudaSuccess) return e;
+        if ((e = launch_eval(b, k, n_eval, true, diag)) != cudaSuccess) return e;
     if ((e = launch_ctl(b, kStEnd)) != cudaSuccess) return e;
     *launches += 7 + n_eval;
     return cudaSuccess;
 }
 
-int ensure_graph(dp_batch* b, int n_eval)
+int ensure_graph(dp_batch* b, int n_eval, bool diag)
 {
-    if (b->exec && b->graph_n_eval == n_eval && b->graph_item_eval == b->item_eval &&
+    if (b->exec && b->graph_n_eval == n_eval && b->graph_diag == diag && b->graph_item_eval == b->item_eval &&
         b->graph_item_imp == b->item_imp)
         return DP_OK;
     if (b->exec) {
@@ -631,7 +635,7 @@ int ensure_graph(dp_batch* b, int n_eval)
     BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
     long long launches = 0;
     cudaError_t e = cudaSuccess;
-    for (int c = 0; c < kChunksPerGraph && e == cudaSuccess; ++c) e = enqueue_step(b, n_eval, &launches);
+    for (int c = 0; c < kChunksPerGraph && e == cudaSuccess; ++c) e = enqueue_step(b, n_eval, diag, &launches);
     cudaError_t e2 = cudaStreamEndCapture(b->st, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -646,6 +650,7 @@ int ensure_graph(dp_batch* b, int n_eval)
         return bfail(DP_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
     }
     b->graph_n_eval = n_eval;
+    b->graph_diag = diag;
     b->graph_item_eval = b->item_eval;
     b->graph_item_imp = b->item_imp;
     b->graph_launches = launches;
@@ -865,8 +870,8 @@ int dp_batch_create(const dp_grid_desc* descs, int32_t count, void* stream, dp_b
               occupancy_blocks(batch_improve_kernel<float, kDynOrbit, kImproveWalk>, b->sm_count, &b->blocks_imp32w) ||
               occupancy_blocks(batch_improve_kernel<double, kDynOrbit, kImproveFull>, b->sm_count, &b->blocks_imp64f) ||
               occupancy_blocks(batch_improve_kernel<double, kDynOrbit, kImproveWalk>, b->sm_count, &b->blocks_imp64w) ||
-              occupancy_blocks(batch_eval_kernel<kDynOrbit, true>, b->sm_count, &b->blocks_eval) ||
-              occupancy_blocks(batch_eval_kernel<kDynOrbit, false>, b->sm_count, &b->blocks_eval_nf);
+              occupancy_blocks(batch_eval_kernel<kDynOrbit, true, false>, b->sm_count, &b->blocks_eval) ||
+              occupancy_blocks(batch_eval_kernel<kDynOrbit, false, false>, b->sm_count, &b->blocks_eval_nf);
     } else {
         bad = occupancy_blocks(batch_improve_kernel<float, kDynUnitSpeed, kImproveFull>, b->sm_count,
                                &b->blocks_imp32f) ||
@@ -876,8 +881,8 @@ int dp_batch_create(const dp_grid_desc* descs, int32_t count, void* stream, dp_b
                                &b->blocks_imp64f) ||
               occupancy_blocks(batch_improve_kernel<double, kDynUnitSpeed, kImproveWalk>, b->sm_count,
                                &b->blocks_imp64w) ||
-              occupancy_blocks(batch_eval_kernel<kDynUnitSpeed, true>, b->sm_count, &b->blocks_eval) ||
-              occupancy_blocks(batch_eval_kernel<kDynUnitSpeed, false>, b->sm_count, &b->blocks_eval_nf);
+              occupancy_blocks(batch_eval_kernel<kDynUnitSpeed, true, false>, b->sm_count, &b->blocks_eval) ||
+              occupancy_blocks(batch_eval_kernel<kDynUnitSpeed, false, false>, b->sm_count, &b->blocks_eval_nf);
     }
     bad = bad || occupancy_blocks(batch_widen_kernel, b->sm_count, &b->blocks_widen);
     if (bad) return bail(bfail(DP_ECUDA, "occupancy query failed"));
@@ -996,7 +1001,9 @@ int dp_batch_policy_iterate(dp_batch* b, const dp_solve_opts* o, dp_solve_stats*
     if (!b || !o) return bfail(DP_EINVAL, "NULL argument");
     if (o->max_sweeps < 1 || o->n_eval < 0 || o->n_eval > 1024 || !(o->tol >= 0))
         return bfail(DP_EINVAL, "bad options (max_sweeps >= 1, 0 <= n_eval <= 1024, tol >= 0)");
-    if (o->eval_solver != DP_EVAL_JACOBI) return bfail(DP_EINVAL, "batched policy iteration evaluates by Jacobi sweeps only");
+    if (o->eval_solver != DP_EVAL_JACOBI && o->eval_solver != DP_EVAL_DIAG)
+        return bfail(DP_EINVAL, "batched policy iteration evaluates by plain or diagonal-solved sweeps only");
+    const bool diag = o->eval_solver == DP_EVAL_DIAG;
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(DP_ECUDA, "cudaSetDevice failed");
     const double t0 = now_ms();
     int rc;
@@ -1007,7 +1014,7 @@ int dp_batch_policy_iterate(dp_batch* b, const dp_solve_opts* o, dp_solve_stats*
         BCK(cudaMemsetAsync(b->V32[0], 0, sizeof(float) * b->total, b->st));
     }
     if ((rc = set_params(b, o, o->warm ? 1 : 0))) return rc;
-    if ((rc = ensure_graph(b, o->n_eval))) return rc;
+    if ((rc = ensure_graph(b, o->n_eval, diag))) return rc;
     BCK(launch_ctl(b, kStBegin));
     const long long max_replays = o->max_sweeps / kChunksPerGraph + 4;
     long long replays = 0;

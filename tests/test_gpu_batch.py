@@ -47,9 +47,11 @@ def test_batch_sweeps_match_oracle_per_transfer(dp):
                 assert res[i] == pytest.approx(np.abs(v_g - V).max(), rel=1e-6, abs=1e-12)
 
 
-def test_batch_solve_reproduces_single_grid_solves(dp):
+@pytest.mark.parametrize("solver", ["sweeps", "diag"])
+def test_batch_solve_reproduces_single_grid_solves(dp, solver):
     probs = W.batch_transfers(count=6, seed=11, sizes=(9, 11, 13))
-    opts = dict(tol=1e-6, max_sweeps=4000, n_eval=20, polish=1)
+    opts = dict(tol=1e-6, max_sweeps=4000, n_eval=20, polish=1,
+                eval_solver=dp.DP_EVAL_DIAG if solver == "diag" else dp.DP_EVAL_JACOBI)
     with dp.Batch(probs) as b:
         dp.dp_batch_set_items(b.h, 512, 256)
         rc, tot, per = b.policy_iterate(**opts)
