@@ -92,6 +92,7 @@ def lib():
                                          C.c_double, _dp, _dp]),
             "orc_dynamics_drag": (None, [P, _dp, C.c_double, C.c_double, _dp]),
             "orc_policy_system": (None, [P, _u8, _u8, _u16, _l, _dp, _dp, C.POINTER(C.c_int)]),
+            "orc_vi_diag_sweep": (C.c_double, [P, _dp, _dp, _u8, _u8]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -259,6 +260,16 @@ class Oracle:
         W, b = self.policy_system(codes)
         A = (sp.identity(self.N, format="csr") - self.s.beta * W).tocsc()
         return spla.spsolve(A, b)
+
+    def vi_diag_sweep(self, V):
+        """One value-iteration sweep (Eq. (12)) with each node's own coefficient
+        solved: V'_j = min_a (c_a + beta R_a) / (1 - beta w_jj^a).  Minimum time
+        only.  Returns (V', max |V' - V| over the node set)."""
+        V = np.ascontiguousarray(V, np.float64)
+        W = np.empty(self.N)
+        r = lib().orc_vi_diag_sweep(C.byref(self.s), _ptr(V, _dp), _ptr(W, _dp), _ptr(self.active, _u8),
+                                    _ptr(self.target, _u8))
+        return W, r
 
     def eval_diag_sweep(self, V, codes):
         """One Jacobi iteration on the policy-evaluation system (I - beta W) V = b

@@ -630,6 +630,52 @@ long orc_value_iterate(const orc_problem* p, double* V, const unsigned char* act
     return s;
 }
 
+/* Value iteration, Eq. (12), with each node's own coefficient solved: for a
+ * control a the update of node j is V_j = c_a + beta w_jj^a V_j + beta R_a,
+ * w_jj^a the node's own Q1 weight at its foot and R_a the rest of the blend,
+ * and the sweep takes V'_j = min_a (c_a + beta R_a) / (1 - beta w_jj^a) over
+ * the tabulated angles (ties to the lowest index).  A foot outside the box or
+ * the node set gives c_a = dt + beta M.  The affine maps have slopes below 1,
+ * so the fixed point of this sweep is that of Eq. (12).  Minimum time only
+ * (l = 1, no thrust-off control).  Returns max |V' - V| over the node set. */
+double orc_vi_diag_sweep(const orc_problem* p, const double* V_in, double* V_out, const unsigned char* active,
+                         const unsigned char* target)
+{
+    long N = orc_node_count(p);
+    double res = 0.0;
+    for (long j = 0; j < N; ++j) {
+        if (!active[j]) { V_out[j] = p->M; continue; }
+        if (target[j]) { V_out[j] = 0.0; continue; }
+        int node[4];
+        double x[4];
+        node_index(p, j, node);
+        node_state(p, node, x);
+        double best = INFINITY;
+        for (int k = 0; k < p->K; ++k) {
+            double a = code_angle(table_code(p->K, k)), delta[4], sgrid[4], w[16];
+            long idx[16];
+            orc_heun_displacement(p, x, a, p->dt, delta);
+            for (int d = 0; d < 4; ++d) sgrid[d] = node[d] + delta[d] / spacing(p, d);
+            double q;
+            if (!interp_corners(p, active, sgrid, idx, w)) {
+                q = p->dt + p->beta * p->M;
+            } else {
+                double self = 0.0, rest = 0.0;
+                for (int b = 0; b < 16; ++b) {
+                    if (idx[b] == j) self += w[b];
+                    else rest += w[b] * V_in[idx[b]];
+                }
+                q = (p->dt + p->beta * rest) / (1.0 - p->beta * self);
+            }
+            if (q < best) best = q;
+        }
+        V_out[j] = best;
+        double dv = fabs(best - V_in[j]);
+        if (dv > res || isnan(dv)) res = dv;
+    }
+    return res;
+}
+
 /* Modified policy iteration: improvement Eq. (14) (full enumeration first,
  * then walk), n_eval Jacobi sweeps of Eq. (13) at the frozen policy, repeat
  * until an improvement sweep moves V by less than tol.  Returns the number of

@@ -619,3 +619,47 @@ def test_eval_diag_sweep_has_the_exact_evaluation_as_fixed_point_and_contracts()
             Vp = o.sweep(Vp, mode=oracle.EVAL, codes=codes)[0]
             Vd = o.eval_diag_sweep(Vd, codes)[0]
         assert np.abs(Vd - v)[act].max() <= np.abs(Vp - v)[act].max() * (1 + 1e-12)
+
+
+def test_vi_diag_sweep_closed_form_half_step():
+    # x' = cos a with dt = h / 2 and the two angles 0 and pi: the foot lies
+    # half-way to a neighbour, so V'_j = min over the two neighbours of
+    # (dt + beta V_nb / 2) / (1 - beta / 2) (the slice i_vr = 0: an angle of
+    # pi moves v_r by dt sin(pi) > 0, inside the box there)
+    p = W.unit_speed_1d().replace(dt=0.5 / 16)
+    o = oracle.Oracle(p)
+    V = W.smooth_value(p, 36)
+    V[o.target.astype(bool)] = 0.0
+    Vn, _ = o.vi_diag_sweep(V)
+    Vg, Vng = V.reshape(p.n), Vn.reshape(p.n)
+    for i in range(17):
+        if i == 8:
+            continue
+        cands = []
+        for nb in (i - 1, i + 1):
+            if 0 <= nb < 17:
+                cands.append((p.dt + 0.5 * p.beta * Vg[nb, 0]) / (1 - 0.5 * p.beta))
+            else:
+                cands.append(np.full_like(Vg[i, 0], p.dt + p.beta * o.M))
+        want = np.minimum(cands[0], cands[1])
+        assert np.allclose(Vng[i, 0], want, rtol=1e-14, atol=0), i
+
+
+def test_vi_diag_has_the_value_iteration_fixed_point():
+    # the fixed point of Eq. (12) is also that of the diagonal-solved sweep,
+    # which gets there in far fewer sweeps
+    p = W.config0().replace(n=(7, 7, 7, 7), beta=0.99)
+    o = oracle.Oracle(p)
+    V, sweeps, res = o.value_iterate(tol=1e-11, max_sweeps=200000)
+    Vd = np.zeros(p.nodes)
+    n = 0
+    for n in range(1, 200000):
+        Vd, r = o.vi_diag_sweep(Vd)
+        if r < 1e-11:
+            break
+    act = o.active.astype(bool)
+    assert np.abs(Vd - V)[act].max() <= 1e-8 * np.abs(V).max()
+    assert n < sweeps / 3
+    # one sweep at the fixed point moves nothing
+    V1, r1 = o.vi_diag_sweep(V)
+    assert r1 <= 1e-9 * np.abs(V).max()
