@@ -81,6 +81,10 @@ extern "C" {
                                     V'_j = V_j + (T_f(V)_j - V_j) / (1 - beta w_jj),
                                     w_jj the node's own weight among the Q1
                                     corners of its foot (same fixed point)     */
+#define DP_SWEEP_VI_DIAG      5  /* Eq. (12) with each node's own coefficient solved
+                                    inside the minimisation:
+                                    V'_j = min_a (c_a + beta R_a) / (1 - beta w_jj^a)
+                                    (same fixed point; minimum-time dynamics)   */
 
 /* How policy iteration evaluates a frozen policy (dp_solve_opts.eval_solver). */
 #define DP_EVAL_JACOBI 0     /* n_eval Jacobi sweeps (modified policy iteration)   */
@@ -228,7 +232,8 @@ int dp_get_policy(const dp_grid* grid, uint16_t* host_codes, int64_t count);
 int dp_bellman_sweep(dp_grid* grid, int32_t mode, double* residual);
 
 /* Value iteration, §3 Eq. (12): sweeps until the residual < opts->tol or
- * opts->max_sweeps (DP_ENOCONV).  stats nullable. */
+ * opts->max_sweeps (DP_ENOCONV).  opts->eval_solver = DP_EVAL_DIAG runs
+ * DP_SWEEP_VI_DIAG sweeps instead (minimum-time dynamics).  stats nullable. */
 int dp_value_iterate(dp_grid* grid, const dp_solve_opts* opts, dp_solve_stats* stats);
 
 /* Modified policy iteration, §3 Eq. (13)-(14): an improvement sweep (full

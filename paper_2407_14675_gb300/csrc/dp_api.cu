@@ -303,10 +303,33 @@ Store store_of(const dp_grid* g)
 
 // Enqueue sweep number `t` (relative to the solve start, buffers alternate
 // from the current one).
-cudaError_t enqueue_sweep(dp_grid* g, int mode, long long t, int check_prev, double tol)
+// Internal sweep mode of a public DP_SWEEP_* mode for the grid's storage
+// (the two numberings overlap: every public mode is mapped exactly once).
+int internal_mode(const dp_grid* g, int mode)
+{
+    const bool feet = store_of(g) == kStoreF32 && g->feet_valid;
+    switch (mode) {
+    case DP_SWEEP_VI: return kVI;
+    case DP_SWEEP_IMPROVE_FULL: return kImproveFull;
+    case DP_SWEEP_IMPROVE_WALK: return kImproveWalk;
+    case DP_SWEEP_EVAL: return feet ? kEvalFeet : kEval;
+    case DP_SWEEP_EVAL_DIAG: return feet ? kEvalFeetDiag : kEvalDiag;
+    case DP_SWEEP_VI_DIAG: return kVIDiag;
+    }
+    return -1;
+}
+
+// Enqueue sweep number `t` of public mode `pmode` (relative to the solve
+// start, buffers alternate from the current one).
+cudaError_t enqueue_sweep(dp_grid* g, int pmode, long long t, int check_prev, double tol)
 {
     int a = (int)(t & 1);
-    if (mode == DP_SWEEP_EVAL_DIAG && store_of(g) != kStoreF32) mode = kEvalDiag;
+    // improvement sweeps of FP32 grids store the frozen feet of the new
+    // policy; the evaluation sweeps after them read those instead of
+    // recomputing
+    if (store_of(g) == kStoreF32 && (pmode == DP_SWEEP_IMPROVE_FULL || pmode == DP_SWEEP_IMPROVE_WALK))
+        g->feet_valid = g->feet_lo != nullptr;
+    const int mode = internal_mode(g, pmode);
     switch (store_of(g)) {
     case kStoreF64: {
         const double* in = (const double*)g->V[(g->cur + a) & 1];
@@ -316,12 +339,6 @@ cudaError_t enqueue_sweep(dp_grid* g, int mode, long long t, int check_prev, dou
     case kStoreF32: {
         const float* in = (const float*)g->V[(g->cur + a) & 1];
         float* out = (float*)g->V[(g->cur + a + 1) & 1];
-        // improvement sweeps store the frozen feet of the new policy; the
-        // evaluation sweeps after them read those instead of recomputing
-        if (mode == DP_SWEEP_IMPROVE_FULL || mode == DP_SWEEP_IMPROVE_WALK) g->feet_valid = g->feet_lo != nullptr;
-        // (public and internal mode numbers overlap: map each public mode once)
-        if (mode == DP_SWEEP_EVAL_DIAG) mode = g->feet_valid ? kEvalFeetDiag : kEvalDiag;
-        else if (mode == DP_SWEEP_EVAL && g->feet_valid) mode = kEvalFeet;
         return launch_sweep(sweep_launch<float, float>(g, g->g32, in, out, mode, t, check_prev, tol));
     }
     default: {
@@ -1133,7 +1150,9 @@ int dp_get_policy(const dp_grid* g, uint16_t* host_codes, int64_t count)
 int dp_bellman_sweep(dp_grid* g, int32_t mode, double* residual)
 {
     if (!g) return fail(DP_EINVAL, "grid is NULL");
-    if (mode < DP_SWEEP_VI || mode > DP_SWEEP_EVAL_DIAG) return fail(DP_EINVAL, "unknown sweep mode %d", mode);
+    if (mode < DP_SWEEP_VI || mode > DP_SWEEP_VI_DIAG) return fail(DP_EINVAL, "unknown sweep mode %d", mode);
+    if (mode == DP_SWEEP_VI_DIAG && g->d.dynamics == DP_DYN_POLAR)
+        return fail(DP_EINVAL, "DP_SWEEP_VI_DIAG needs the minimum-time dynamics");
     if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
     int rc;
     if ((rc = reset_ctl(g)) || (rc = clear_ring(g, 0, 1))) return rc;
@@ -1148,6 +1167,11 @@ int dp_value_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
 {
     if (!g || !o) return fail(DP_EINVAL, "NULL argument");
     if (o->max_sweeps < 0 || !(o->tol >= 0)) return fail(DP_EINVAL, "bad tol or max_sweeps");
+    if (o->eval_solver != DP_EVAL_JACOBI && o->eval_solver != DP_EVAL_DIAG)
+        return fail(DP_EINVAL, "value iteration: eval_solver must be DP_EVAL_JACOBI or DP_EVAL_DIAG");
+    if (o->eval_solver == DP_EVAL_DIAG && g->d.dynamics == DP_DYN_POLAR)
+        return fail(DP_EINVAL, "the diagonal-solved value iteration needs the minimum-time dynamics");
+    const int vi_mode = o->eval_solver == DP_EVAL_DIAG ? DP_SWEEP_VI_DIAG : DP_SWEEP_VI;
     if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
     double t0 = now_ms();
     dp_solve_stats S;
@@ -1166,7 +1190,7 @@ int dp_value_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
         if ((rc = clear_ring(g, s, c))) return rc;
         for (long long k = 0; k < c; ++k) {
             CK(T.begin(tk));
-            CK(enqueue_sweep(g, DP_SWEEP_VI, s + k, s + k > 0, o->tol));
+            CK(enqueue_sweep(g, vi_mode, s + k, s + k > 0, o->tol));
             CK(T.end());
             S.launches++;
         }

@@ -27,7 +27,7 @@ constexpr int kMaxFib = 30;
 constexpr int kMaxAngles = 1024;   // tabulated angles per grid (shared-memory table)
 
 enum { kVI = 0, kImproveFull = 1, kImproveWalk = 2, kEval = 3, kEvalFeet = 4, kIncr = 5,
-       kEvalDiag = 6, kEvalFeetDiag = 7, kIncrDiag = 8 };
+       kEvalDiag = 6, kEvalFeetDiag = 7, kIncrDiag = 8, kVIDiag = 9 };
 // kEval*Diag, kIncrDiag: the evaluation as a Jacobi iteration on the linear
 // system of Eq. (13) with each node's own coefficient solved exactly (the
 // weight w_jj of node j among the Q1 corners of its own foot):
@@ -35,7 +35,9 @@ enum { kVI = 0, kImproveFull = 1, kImproveWalk = 2, kEval = 3, kEvalFeet = 4, kI
 // which has the fixed point of the plain evaluation sweep.  Where the foot
 // stays in the node's own cell (w_jj near 1: the mass moves ~0.002 cells per
 // step) the plain sweep contracts by beta w_jj ~ 0.997 there; this one does
-// not.
+// not.  kVIDiag: value iteration with the node's own coefficient solved
+// inside the minimisation, min_a (c_a + beta R_a) / (1 - beta w_jj^a) (the
+// fixed point of Eq. (12); minimum-time dynamics).
 enum { kDynOrbit = 0, kDynUnitSpeed = 1, kDynPolar = 2 };
 constexpr int kCodeOff = 65535;     // policy code of the thrust-off control
 
@@ -545,7 +547,7 @@ struct NodeEval {
 // coordinate of the foot is found once per state (reset(), after vj, u0 and
 // the dynamics are set).  OFF = false: the state is a grid node (u0 = 0).
 template <typename G, typename S, bool REDUCED, int DYN, typename BLEND = typename BlendType<G, S>::type,
-          bool OFF = true>
+          bool OFF = true, bool DIAG = false>
 struct CachedEval {
     typedef BLEND R;
     const Geo<G>* g;
@@ -607,7 +609,21 @@ struct CachedEval {
         }
         if (cout) return pen;
         const R tr[4] = {(R)t[0], (R)t[1], (R)t[2], (R)t[3]};
-        return K.blend(tr);
+        const R D = K.blend(tr);
+        if constexpr (DIAG) {
+            // the node's own coefficient solved (grid node, l = 1): return the
+            // difference D~ with dt + beta (vj + D~) = vj + r / (1 - beta w),
+            // r = dt + beta (vj + D) - vj the plain update's change and w the
+            // node's own weight among the corners; D~ = D + w r / (1 - beta w)
+            // orders the controls as the solved values do
+            const R w = (R)self_weight<G, DYN == kDynPolar>(*g, i, cl, t);
+            const R beta = std::is_same<R, double>::value ? (R)g->beta64 : (R)(g->beta_hi + g->beta_lo);
+            const R dt = std::is_same<R, double>::value ? (R)g->dt64 : (R)g->dt;
+            const R vr = (R)vj;
+            const R r = dt + beta * (vr + D) - vr;
+            return D + w * r / ((R)1 - beta * w);
+        }
+        return D;
     }
 
     // Frozen-foot word of this node for a code (FP32 geometry only).

@@ -199,7 +199,8 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                                             float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
                                             int j0, int end, int stride, S& resid, bool& bad)
 {
-    constexpr bool kSearch = MODE == kVI || MODE == kImproveFull || MODE == kImproveWalk;
+    constexpr bool kIsVI = MODE == kVI || MODE == kVIDiag;
+    constexpr bool kSearch = kIsVI || MODE == kImproveFull || MODE == kImproveWalk;
     constexpr bool kImprove = MODE == kImproveFull || MODE == kImproveWalk;
     constexpr bool kGeo32 = std::is_same<G, float>::value;
     constexpr bool kPolish = kGeo32 && std::is_same<S, double>::value;   // FP32 geometry, FP64 values
@@ -282,7 +283,7 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
         // 1e-9 of a cell's value spread, far below the FP32 geometry's own
         // noise), and the chosen code is then re-evaluated in FP64
         typedef typename std::conditional<kPolish, float, typename BlendType<G, S>::type>::type SearchR;
-        typedef typename std::conditional<kSearch, CachedEval<G, S, REDUCED, DYN, SearchR, false>,
+        typedef typename std::conditional<kSearch, CachedEval<G, S, REDUCED, DYN, SearchR, false, MODE == kVIDiag>,
                                           NodeEval<G, S, REDUCED, DYN>>::type Eval;
         for (int j = j0; j < end; j += stride) {
             const S vj = Vin[j];
@@ -321,7 +322,7 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                         else
                             k = enumerate_table(ev, T, D);
                         int c = T.code[k] & (kCodes - 1);
-                        if (MODE != kVI && g.refine) c = fibonacci_refine(ev, T, g.fib_n0, g.fib_stop, k, D, D);
+                        if (!kIsVI && g.refine) c = fibonacci_refine(ev, T, g.fib_n0, g.fib_stop, k, D, D);
                         q = lrun + g.thrust_cost + g.beta64 * ((double)vj + (double)D);
                         if (g.off) {
                             const double q_off = lrun + g.beta64 * ((double)vj + (double)ev.at_sc((G)0, (G)0));
@@ -330,7 +331,7 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                                 c = kCodeOff;
                             }
                         }
-                        if (MODE != kVI) code[j] = (uint16_t)c;
+                        if (!kIsVI) code[j] = (uint16_t)c;
                     }
                     vnew = (S)q;
                 }
@@ -352,7 +353,7 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                     else
                         k = enumerate_table(ev, T, D);
                     int c = T.code[k] & (kCodes - 1);
-                    if (MODE != kVI && g.refine) c = fibonacci_refine(ev, T, g.fib_n0, g.fib_stop, k, D, D);
+                    if (!kIsVI && g.refine) c = fibonacci_refine(ev, T, g.fib_n0, g.fib_stop, k, D, D);
                     if constexpr (kImprove && kPolish) {
                         // FP64 blend of the chosen code.  Both the walk and the
                         // full tabulation keep the node's current code unless the
@@ -380,7 +381,7 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                         }
                         vnew64 = g.dt64 + g.beta64 * ((double)vj + d_new);
                     }
-                    if (MODE != kVI) code[j] = (uint16_t)c;
+                    if (!kIsVI) code[j] = (uint16_t)c;
                     if constexpr (kGeo32 && kImprove) {
                         if (feet_lo) {
                             const FootWord w = ev.foot_of(c);
@@ -444,7 +445,7 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
              Ctl* __restrict__ ctl, unsigned long long* __restrict__ ring, int ring_mask, long long sweep,
              int check_prev, double tol)
 {
-    constexpr bool kSearch = MODE == kVI || MODE == kImproveFull || MODE == kImproveWalk;
+    constexpr bool kSearch = MODE == kVI || MODE == kVIDiag || MODE == kImproveFull || MODE == kImproveWalk;
     if (*(volatile int*)&ctl->stop) return;
     if (check_prev) {
         unsigned long long bits = *(volatile unsigned long long*)&ring[(sweep - 1) & ring_mask];
@@ -510,6 +511,9 @@ cudaError_t launch_mode(const SweepLaunch<G, S>& L)
             return (L.feet_lo && L.acc && L.V64) ? launch_one<G, S, kIncr, REDUCED, DYN>(L) : cudaErrorInvalidValue;
         return cudaErrorInvalidValue;
     case kEvalDiag: return launch_one<G, S, kEvalDiag, REDUCED, DYN>(L);
+    case kVIDiag:
+        if constexpr (DYN != kDynPolar) return launch_one<G, S, kVIDiag, REDUCED, DYN>(L);
+        return cudaErrorInvalidValue;
     case kEvalFeetDiag:
         if constexpr (f32) return L.feet_lo ? launch_one<G, S, kEvalFeetDiag, REDUCED, DYN>(L) : cudaErrorInvalidValue;
         return cudaErrorInvalidValue;

@@ -20,7 +20,8 @@ DP_OK, DP_EINVAL, DP_ENOMEM, DP_ECUDA, DP_ENOCONV, DP_ETIMEOUT, DP_ENONFINITE = 
 DP_FP64, DP_FP32 = 0, 1
 DP_DYN_ORBIT, DP_DYN_UNIT_SPEED, DP_DYN_POLAR = 0, 1, 2
 DP_CODE_OFF = 65535
-DP_SWEEP_VI, DP_SWEEP_IMPROVE_FULL, DP_SWEEP_IMPROVE_WALK, DP_SWEEP_EVAL, DP_SWEEP_EVAL_DIAG = 0, 1, 2, 3, 4
+DP_SWEEP_VI, DP_SWEEP_IMPROVE_FULL, DP_SWEEP_IMPROVE_WALK, DP_SWEEP_EVAL = 0, 1, 2, 3
+DP_SWEEP_EVAL_DIAG, DP_SWEEP_VI_DIAG = 4, 5
 DP_EVAL_JACOBI, DP_EVAL_GMRES, DP_EVAL_DIAG = 0, 1, 2
 DP_GMRES_MAX_RESTART = 64
 

@@ -129,5 +129,43 @@ def test_diag_modes_are_rejected_where_unsupported(dp):
     assert e.value.code == dp.DP_EINVAL
     with dp.Grid(p) as g:
         with pytest.raises(dp.DPError) as e:
-            g.sweep(5)
+            g.sweep(6)
+        assert e.value.code == dp.DP_EINVAL
+
+
+@pytest.mark.parametrize("name", ["config0_17x4", "unit_speed_2d"])
+def test_vi_diag_sweeps_match_oracle_fp64(dp, name):
+    p = W.config0() if name == "config0_17x4" else W.unit_speed_2d(n=13, n_angles=8)
+    o = oracle.Oracle(p)
+    V = W.smooth_value(p, 45)
+    V[o.target.astype(bool)] = 0.0
+    with dp.Grid(p) as g:
+        g.set_value(V)
+        for k in range(3):
+            want, r_o = o.vi_diag_sweep(V)
+            r = g.sweep(dp.DP_SWEEP_VI_DIAG)
+            v = g.get_value()
+            _check_values(v, want, TOL64, "%s sweep %d" % (name, k))
+            assert abs(r - r_o) <= TOL64 * np.abs(want).max()
+            V = want
+
+
+def test_vi_diag_reaches_the_value_iteration_fixed_point(dp):
+    p = W.config0()
+    out = {}
+    for solver in (dp.DP_EVAL_JACOBI, dp.DP_EVAL_DIAG):
+        with dp.Grid(p) as g:
+            rc, st = g.value_iterate(tol=1e-10, max_sweeps=60000, eval_solver=solver)
+            assert rc == dp.DP_OK and st.converged, st.asdict()
+            out[solver] = (g.get_value(), st.sweeps_vi)
+    (v_p, n_p), (v_d, n_d) = out[dp.DP_EVAL_JACOBI], out[dp.DP_EVAL_DIAG]
+    assert n_d < n_p / 3
+    # both within tol / (1 - beta) of the fixed point
+    assert np.abs(v_d - v_p).max() <= 2e-10 / (1 - p.beta)
+    with dp.Grid(W.example1(n=(12, 7, 7, 8))) as g:
+        with pytest.raises(dp.DPError) as e:
+            g.value_iterate(tol=1e-6, max_sweeps=5, eval_solver=dp.DP_EVAL_DIAG)
+        assert e.value.code == dp.DP_EINVAL
+        with pytest.raises(dp.DPError) as e:
+            g.sweep(dp.DP_SWEEP_VI_DIAG)
         assert e.value.code == dp.DP_EINVAL
