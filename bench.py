@@ -262,6 +262,14 @@ def extra_legs(args, dp, W, torch, g1, p1):
         secs = time.perf_counter() - t0
         out["vi_fp64_17x4"] = {"seconds": secs, "converged": bool(s0.converged), "sweeps": s0.sweeps_vi,
                                "residual": s0.residual, "node_updates_per_s": s0.node_updates / secs}
+        # the same with each sweep solving the node's own coefficient
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, s0 = g0.value_iterate(tol=1e-8, max_sweeps=40000, eval_solver=dp.DP_EVAL_DIAG)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        out["vi_diag_fp64_17x4"] = {"seconds": secs, "converged": bool(s0.converged), "sweeps": s0.sweeps_vi,
+                                    "residual": s0.residual, "speedup": out["vi_fp64_17x4"]["seconds"] / secs}
         # FP64 policy iteration on the same grid, each policy evaluated by 20
         # Jacobi sweeps or by GMRES
         pi = {}
