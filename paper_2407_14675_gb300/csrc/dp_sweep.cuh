@@ -178,9 +178,11 @@ __device__ __forceinline__ float incr_recompute(const Geo<float>& g, const float
 }
 
 // The diagonal-solved step of the evaluation: V_j + (T_f(V)_j - V_j) / (1 - beta w_jj).
+// The factor only sets the step length (the fixed point is where the change
+// T_f(V)_j - V_j vanishes), so FP32 uses the fast division.
 __device__ __forceinline__ float diag_step(const Geo<float>& g, float vj, float vplain, float ws)
 {
-    return vj + (vplain - vj) / (1.0f - (g.beta_hi + g.beta_lo) * ws);
+    return vj + __fdividef(vplain - vj, 1.0f - (g.beta_hi + g.beta_lo) * ws);
 }
 template <typename G>
 __device__ __forceinline__ double diag_step(const Geo<G>& g, double vj, double vplain, double ws)
@@ -264,7 +266,7 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                 }
                 if constexpr (kDiag) {
                     const float Dx = first ? D : D - ws * vj;
-                    vnew = fmaf(g.beta_hi, Dx, g.beta_lo * Dx) / (1.0f - (g.beta_hi + g.beta_lo) * ws);
+                    vnew = __fdividef(fmaf(g.beta_hi, Dx, g.beta_lo * Dx), 1.0f - (g.beta_hi + g.beta_lo) * ws);
                 } else {
                     vnew = fmaf(g.beta_hi, D, g.beta_lo * D);
                 }
