@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "dp.h"
@@ -86,6 +87,8 @@ struct dp_grid {
     unsigned long long* feet_lo = nullptr;  // frozen feet of the current policy (FP32 grids)
     unsigned* feet_hi = nullptr;
     bool feet_valid = false;
+    Feet64 f64;                             // frozen feet of FP64 grids
+    bool feet64_valid = false;
     float* acc = nullptr;                   // FP64-value polish: running sum of increments
     Ctl* ctl = nullptr;
     unsigned long long* ring = nullptr;
@@ -133,7 +136,7 @@ void free_grid(dp_grid* g)
     if (g->st) cudaStreamSynchronize(g->st);
     void* ps[] = {g->rows, g->lines, g->hi64, g->lo64, g->hi32, g->lo32, g->V[0], g->V[1], g->V64[0],
                   g->V64[1], g->code, g->feet_lo, g->feet_hi, g->acc, g->ctl, g->ring, g->staging,
-                  g->scratch64, g->gm_Q, g->gm_partial, g->gm_ctl};
+                  g->scratch64, g->gm_Q, g->gm_partial, g->gm_ctl, g->f64.w, g->f64.t, g->f64.c};
     for (void* p : ps)
         if (p) cudaFree(p);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
@@ -278,6 +281,7 @@ SweepLaunch<G, S> sweep_launch(dp_grid* g, const Geo<G>& geo, const S* Vin, S* V
     L.acc = nullptr;
     L.V64 = nullptr;
     L.incr_flags = 0;
+    if constexpr (std::is_same<G, double>::value && std::is_same<S, double>::value) L.f64 = g->f64;
     L.ctl = g->ctl;
     L.ring = g->ring;
     L.ring_mask = kRing - 1;
@@ -308,12 +312,13 @@ Store store_of(const dp_grid* g)
 int internal_mode(const dp_grid* g, int mode)
 {
     const bool feet = store_of(g) == kStoreF32 && g->feet_valid;
+    const bool feet64 = store_of(g) == kStoreF64 && g->feet64_valid;
     switch (mode) {
     case DP_SWEEP_VI: return kVI;
     case DP_SWEEP_IMPROVE_FULL: return kImproveFull;
     case DP_SWEEP_IMPROVE_WALK: return kImproveWalk;
-    case DP_SWEEP_EVAL: return feet ? kEvalFeet : kEval;
-    case DP_SWEEP_EVAL_DIAG: return feet ? kEvalFeetDiag : kEvalDiag;
+    case DP_SWEEP_EVAL: return feet ? kEvalFeet : (feet64 ? kEvalFeet64 : kEval);
+    case DP_SWEEP_EVAL_DIAG: return feet ? kEvalFeetDiag : (feet64 ? kEvalFeet64Diag : kEvalDiag);
     case DP_SWEEP_VI_DIAG: return kVIDiag;
     }
     return -1;
@@ -327,8 +332,10 @@ cudaError_t enqueue_sweep(dp_grid* g, int pmode, long long t, int check_prev, do
     // improvement sweeps of FP32 grids store the frozen feet of the new
     // policy; the evaluation sweeps after them read those instead of
     // recomputing
-    if (store_of(g) == kStoreF32 && (pmode == DP_SWEEP_IMPROVE_FULL || pmode == DP_SWEEP_IMPROVE_WALK))
-        g->feet_valid = g->feet_lo != nullptr;
+    if (pmode == DP_SWEEP_IMPROVE_FULL || pmode == DP_SWEEP_IMPROVE_WALK) {
+        if (store_of(g) == kStoreF32) g->feet_valid = g->feet_lo != nullptr;
+        if (store_of(g) == kStoreF64) g->feet64_valid = g->f64.w != nullptr;
+    }
     const int mode = internal_mode(g, pmode);
     switch (store_of(g)) {
     case kStoreF64: {
@@ -748,6 +755,7 @@ void grid_after_warm_start(dp_grid* g)
 {
     g->fp64_values = false;
     g->feet_valid = false;
+    g->feet64_valid = false;
 }
 
 // Validation and sweep geometry of a full-box grid described by desc, without
@@ -1028,6 +1036,9 @@ int dp_grid_create(const dp_grid_desc* desc, dp_grid** out)
     if ((rc = dalloc(g, &g->code, g->n_active))) return bail(rc);
     if (g->fp32 && ((rc = dalloc(g, &g->feet_lo, g->n_active)) || (rc = dalloc(g, &g->feet_hi, g->n_active))))
         return bail(rc);
+    if (!g->fp32 && ((rc = dalloc(g, &g->f64.w, g->n_active)) || (rc = dalloc(g, &g->f64.t, 2 * g->n_active)) ||
+                     (rc = dalloc(g, &g->f64.c, g->n_active))))
+        return bail(rc);
     if ((rc = dalloc(g, &g->ctl, 1))) return bail(rc);
     if ((rc = dalloc(g, &g->ring, kRing))) return bail(rc);
     if (cudaMemsetAsync(g->code, 0, sizeof(uint16_t) * g->n_active, g->st) != cudaSuccess ||
@@ -1133,6 +1144,7 @@ int dp_set_policy(dp_grid* g, const uint16_t* host_codes, int64_t count)
     if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
     CK(cudaMemcpyAsync(g->code, host_codes, sizeof(uint16_t) * count, cudaMemcpyHostToDevice, g->st));
     g->feet_valid = false;   // the stored feet belong to the previous policy
+    g->feet64_valid = false;
     CK(cudaStreamSynchronize(g->st));
     return DP_OK;
 }
@@ -1453,6 +1465,7 @@ int dp_warm_start_from_grid(const dp_grid* src, dp_grid* dst, double* ms_out)
     if (ms_out) *ms_out = ms;
     dst->fp64_values = false;
     dst->feet_valid = false;
+    dst->feet64_valid = false;
     return DP_OK;
 }
 

@@ -27,7 +27,7 @@ constexpr int kMaxFib = 30;
 constexpr int kMaxAngles = 1024;   // tabulated angles per grid (shared-memory table)
 
 enum { kVI = 0, kImproveFull = 1, kImproveWalk = 2, kEval = 3, kEvalFeet = 4, kIncr = 5,
-       kEvalDiag = 6, kEvalFeetDiag = 7, kIncrDiag = 8, kVIDiag = 9 };
+       kEvalDiag = 6, kEvalFeetDiag = 7, kIncrDiag = 8, kVIDiag = 9, kEvalFeet64 = 10, kEvalFeet64Diag = 11 };
 // kEval*Diag, kIncrDiag: the evaluation as a Jacobi iteration on the linear
 // system of Eq. (13) with each node's own coefficient solved exactly (the
 // weight w_jj of node j among the Q1 corners of its own foot):
@@ -418,6 +418,20 @@ struct FootWord {
     unsigned hi;
 };
 
+// Frozen feet of FP64 grids.  The FP64 evaluation sweep otherwise repeats the
+// FP64 one-step map and, for the paper's Example 1, the running cost of
+// Eq. (11) at every node in every sweep.  Per node: a word with the kind
+// (bits 32-33) and the cell's offsets from the node as int8 (coordinate d in
+// bits 8d..8d+7), the four fractions in FP64 (two double2), and the constant
+// part c_j of the node's update under its control (dt l(x_j, control), the
+// thrust cost included).  Evaluation from them gives the recomputing sweep's
+// results bit for bit.
+struct Feet64 {
+    unsigned long long* w = nullptr;
+    double2* t = nullptr;
+    double* c = nullptr;
+};
+
 __device__ __forceinline__ FootWord foot_word_kind(int kind)
 {
     return FootWord{0ull, (unsigned)kind << 16};
@@ -624,6 +638,27 @@ struct CachedEval {
             return D + w * r / ((R)1 - beta * w);
         }
         return D;
+    }
+
+    // FP64 frozen foot of this node for the control (s, c) (sine and cosine;
+    // 0, 0 for thrust off): returns the word, fractions in t.
+    __device__ __forceinline__ unsigned long long foot64_of(G s, G c, G t[4]) const
+    {
+        G u[4];
+        int cl[4], base[4];
+        heun_cells<G, DYN>(*g, sp, nd, s, c, u);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) u[d] += u0[d];
+        if (foot_cell<G, DYN == kDynPolar>(*g, i, u, cl, t)) return (unsigned long long)kFootOut << 32;
+        if (REDUCED && cell_rows<G, REDUCED>(*g, cl, base)) return (unsigned long long)kFootOut << 32;
+        unsigned long long w = (unsigned long long)kFootInside << 32;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const int off = cl[d] - i[d];
+            if (off < -128 || off > 127) return (unsigned long long)kFootRecompute << 32;
+            w |= (unsigned long long)(unsigned char)(signed char)off << (8 * d);
+        }
+        return w;
     }
 
     // Frozen-foot word of this node for a code (FP32 geometry only).

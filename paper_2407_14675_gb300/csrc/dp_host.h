@@ -27,6 +27,7 @@ struct SweepLaunch {
     long long sweep;            // sweep index within the solve (ring slot)
     int check_prev;             // 1: stop if the previous sweep's residual < tol
     double tol;
+    Feet64 f64;                 // FP64 grids: frozen feet (written by improvements, read by kEvalFeet64*)
     int mode;                   // kVI, kImproveFull, kImproveWalk, kEval
     int dyn;
     int reduced;

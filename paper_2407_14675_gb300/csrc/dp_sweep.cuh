@@ -199,7 +199,8 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                                             unsigned long long* __restrict__ feet_lo,
                                             unsigned* __restrict__ feet_hi, float* __restrict__ inc,
                                             float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
-                                            int j0, int end, int stride, S& resid, bool& bad)
+                                            int j0, int end, int stride, S& resid, bool& bad,
+                                            const Feet64 f64 = Feet64())
 {
     constexpr bool kIsVI = MODE == kVI || MODE == kVIDiag;
     constexpr bool kSearch = kIsVI || MODE == kImproveFull || MODE == kImproveWalk;
@@ -208,7 +209,53 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
     constexpr bool kPolish = kGeo32 && std::is_same<S, double>::value;   // FP32 geometry, FP64 values
     (void)T;
     (void)kSearch;
-    if constexpr (MODE == kEvalFeet || MODE == kIncr || MODE == kEvalFeetDiag || MODE == kIncrDiag) {
+    if constexpr (MODE == kEvalFeet64 || MODE == kEvalFeet64Diag) {
+        // FP64 evaluation from the FP64 frozen feet
+        constexpr bool kDiag = MODE == kEvalFeet64Diag;
+        constexpr bool kPer = DYN == kDynPolar;
+        for (int j = j0; j < end; j += stride) {
+            const S vj = Vin[j];
+            const unsigned long long w = __ldcs(&f64.w[j]);
+            const int kind = (int)((w >> 32) & 3u);
+            S vnew = (S)0;
+            if (kind != kFootTarget) {
+                const double cj = __ldcs(&f64.c[j]);
+                double D, ws = 0.0;
+                if (kind == kFootOut) {
+                    D = g.M64 - (double)vj;
+                } else if (kind == kFootInside) {
+                    int i[4], cl[4];
+                    decode_node(g, j, i);
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) cl[d] = i[d] + (int)(signed char)((w >> (8 * d)) & 0xffu);
+                    if (kPer) cl[3] = cl[3] < 0 ? cl[3] + g.n[3] : (cl[3] >= g.n[3] ? cl[3] - g.n[3] : cl[3]);
+                    const double2 ta = __ldcs(&f64.t[2 * (size_t)j]), tb = __ldcs(&f64.t[2 * (size_t)j + 1]);
+                    const double t[4] = {ta.x, ta.y, tb.x, tb.y};
+                    Corners<double> K;
+                    load_corners<double, G, S, REDUCED, kPer>(g, Vin, cl, vj, K);   // membership checked when stored
+                    D = K.blend(t);
+                    if constexpr (kDiag) ws = self_weight<G, kPer>(g, i, cl, t);
+                } else {
+                    NodeEval<G, S, REDUCED, DYN> ev;
+                    decode_node(g, j, ev.i);
+                    setup_node<G, S, DYN>(ev, g, Vin, vj);
+                    const int c0 = code[j];
+                    typename NodeEval<G, S, REDUCED, DYN>::R wr = 0;
+                    if (kPer && g.off && c0 == kCodeOff)
+                        D = kDiag ? ev.at_sc_w((G)0, (G)0, wr) : ev.at_sc((G)0, (G)0);
+                    else
+                        D = kDiag ? ev.at_code_w(c0, wr) : ev.at_code(c0);
+                    ws = wr;
+                }
+                double q = cj + g.beta64 * ((double)vj + D);
+                if constexpr (kDiag) q = diag_step(g, (double)vj, q, ws);
+                vnew = (S)q;
+            }
+            Vout[j] = vnew;
+            resid = fmax(resid, (S)fabs(vnew - vj));
+            bad = bad || !isfinite(vnew);
+        }
+    } else if constexpr (MODE == kEvalFeet || MODE == kIncr || MODE == kEvalFeetDiag || MODE == kIncrDiag) {
         constexpr bool kDiag = MODE == kEvalFeetDiag || MODE == kIncrDiag;
         // frozen feet: gather-bound, so the next node's foot and value are
         // fetched while this node's corners are in flight.  The feet are read
@@ -334,8 +381,21 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                             }
                         }
                         if (!kIsVI) code[j] = (uint16_t)c;
+                        if constexpr (!kGeo32 && kImprove) {
+                            if (f64.w) {
+                                const bool off = g.off && c == kCodeOff;
+                                G sn = (G)0, cs = (G)0, t[4];
+                                if (!off) code_sincos(g, c, sn, cs);
+                                f64.w[j] = ev.foot64_of(sn, cs, t);
+                                f64.t[2 * (size_t)j] = make_double2((double)t[0], (double)t[1]);
+                                f64.t[2 * (size_t)j + 1] = make_double2((double)t[2], (double)t[3]);
+                                f64.c[j] = off ? lrun : lrun + g.thrust_cost;
+                            }
+                        }
                     }
                     vnew = (S)q;
+                } else if constexpr (!kGeo32 && kImprove) {
+                    if (f64.w) f64.w[j] = (unsigned long long)kFootTarget << 32;
                 }
             } else if (!in_target(g, ev.i)) {
                 setup_node<G, S, DYN>(ev, g, Vin, vj);
@@ -391,6 +451,16 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                             feet_hi[j] = w.hi;
                         }
                     }
+                    if constexpr (!kGeo32 && kImprove) {
+                        if (f64.w) {
+                            G sn, cs, t[4];
+                            code_sincos(g, c, sn, cs);
+                            f64.w[j] = ev.foot64_of(sn, cs, t);
+                            f64.t[2 * (size_t)j] = make_double2((double)t[0], (double)t[1]);
+                            f64.t[2 * (size_t)j + 1] = make_double2((double)t[2], (double)t[3]);
+                            f64.c[j] = g.dt64;
+                        }
+                    }
                 }
                 if constexpr (kPolish) vnew = (S)bellman_value(g, (double)vj, (double)D);
                 else vnew = bellman_value<G, S>(g, vj, D);
@@ -402,6 +472,8 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                     feet_lo[j] = w.lo;
                     feet_hi[j] = w.hi;
                 }
+            } else if constexpr (!kGeo32 && kImprove) {
+                if (f64.w) f64.w[j] = (unsigned long long)kFootTarget << 32;
             }
             if constexpr (kImprove) {
                 if (inc) inc[j] = (float)(vnew - vj);   // first increment of the evaluation sweeps
@@ -436,7 +508,9 @@ __device__ __forceinline__ void block_fold(S resid, bool bad, unsigned long long
 template <int MODE>
 constexpr int min_blocks()
 {
-    return (MODE == kEvalFeet || MODE == kIncr || MODE == kEvalFeetDiag || MODE == kIncrDiag) ? 6 : 1;
+    return (MODE == kEvalFeet || MODE == kIncr || MODE == kEvalFeetDiag || MODE == kIncrDiag) ? 6
+           : (MODE == kEvalFeet64 || MODE == kEvalFeet64Diag)                               ? 4
+                                                                                             : 1;
 }
 
 template <typename G, typename S, int MODE, bool REDUCED, int DYN>
@@ -445,7 +519,7 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
              uint16_t* __restrict__ code, unsigned long long* __restrict__ feet_lo, unsigned* __restrict__ feet_hi,
              float* __restrict__ inc, float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
              Ctl* __restrict__ ctl, unsigned long long* __restrict__ ring, int ring_mask, long long sweep,
-             int check_prev, double tol)
+             int check_prev, double tol, const Feet64 f64)
 {
     constexpr bool kSearch = MODE == kVI || MODE == kVIDiag || MODE == kImproveFull || MODE == kImproveWalk;
     if (*(volatile int*)&ctl->stop) return;
@@ -473,7 +547,7 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
     bool bad = false;
     sweep_nodes<G, S, MODE, REDUCED, DYN>(g, T, Vin, Vout, code, feet_lo, feet_hi, inc, acc, V64, incr_flags,
                                           blockIdx.x * kBlock + threadIdx.x, g.n_nodes, gridDim.x * kBlock,
-                                          resid, bad);
+                                          resid, bad, f64);
     block_fold(resid, bad, &ring[sweep & ring_mask], &ctl->nonfinite);
 }
 
@@ -492,7 +566,8 @@ cudaError_t launch_one(const SweepLaunch<G, S>& L)
     int blocks = (int)(need < cap ? need : cap);
     if (blocks < 1) blocks = 1;
     kern<<<blocks, kBlock, 0, L.stream>>>(L.g, L.Vin, L.Vout, L.code, L.feet_lo, L.feet_hi, L.inc, L.acc, L.V64,
-                                          L.incr_flags, L.ctl, L.ring, L.ring_mask, L.sweep, L.check_prev, L.tol);
+                                          L.incr_flags, L.ctl, L.ring, L.ring_mask, L.sweep, L.check_prev, L.tol,
+                                          L.f64);
     return cudaGetLastError();
 }
 
@@ -515,6 +590,14 @@ cudaError_t launch_mode(const SweepLaunch<G, S>& L)
     case kEvalDiag: return launch_one<G, S, kEvalDiag, REDUCED, DYN>(L);
     case kVIDiag:
         if constexpr (DYN != kDynPolar) return launch_one<G, S, kVIDiag, REDUCED, DYN>(L);
+        return cudaErrorInvalidValue;
+    case kEvalFeet64:
+        if constexpr (std::is_same<G, double>::value && std::is_same<S, double>::value)
+            return L.f64.w ? launch_one<G, S, kEvalFeet64, REDUCED, DYN>(L) : cudaErrorInvalidValue;
+        return cudaErrorInvalidValue;
+    case kEvalFeet64Diag:
+        if constexpr (std::is_same<G, double>::value && std::is_same<S, double>::value)
+            return L.f64.w ? launch_one<G, S, kEvalFeet64Diag, REDUCED, DYN>(L) : cudaErrorInvalidValue;
         return cudaErrorInvalidValue;
     case kEvalFeetDiag:
         if constexpr (f32) return L.feet_lo ? launch_one<G, S, kEvalFeetDiag, REDUCED, DYN>(L) : cudaErrorInvalidValue;

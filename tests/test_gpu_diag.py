@@ -169,3 +169,30 @@ def test_vi_diag_reaches_the_value_iteration_fixed_point(dp):
         with pytest.raises(dp.DPError) as e:
             g.sweep(dp.DP_SWEEP_VI_DIAG)
         assert e.value.code == dp.DP_EINVAL
+
+
+@pytest.mark.parametrize("name", ["config1_11x9x9x9_fp64", "example1_12x7x7x8", "band_13x4_fp64"])
+def test_fp64_frozen_feet_evaluate_bit_for_bit(dp, name):
+    # FP64 grids store the foot of the chosen control in their improvement
+    # sweeps; evaluation from it must equal the recomputing evaluation (a
+    # policy set from the host has no stored feet)
+    p = _problem(name)
+    o = oracle.Oracle(p)
+    scale = 1.0 if not p.off_control else 1e-2
+    V = W.smooth_value(p, 47) * scale
+    V[o.target.astype(bool)] = 0.0
+    idx = np.flatnonzero(o.active)
+    with dp.Grid(p) as g:
+        for mode in (dp.DP_SWEEP_EVAL, dp.DP_SWEEP_EVAL_DIAG):
+            g.set_value(V[idx])
+            g.sweep(dp.DP_SWEEP_IMPROVE_FULL)
+            V1, c1 = g.get_value(), g.get_policy()
+            g.sweep(mode)
+            v_feet = g.get_value()
+            g.set_value(V1)
+            g.set_policy(c1)
+            g.sweep(mode)
+            v_rec = g.get_value()
+            np.testing.assert_array_equal(v_feet, v_rec)
+            if p.off_control:
+                assert (c1 == dp.DP_CODE_OFF).any()
