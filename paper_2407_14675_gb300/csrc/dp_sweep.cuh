@@ -346,7 +346,7 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                 // thrust-off control, which wins a tie (FP64 grids only)
                 if (!in_target(g, ev.i)) {
                     setup_node<G, S, DYN>(ev, g, Vin, vj);
-                    const double lrun = g.dt64 * state_cost(g, ev.i);
+                    const double lrun = __dmul_rn(g.dt64, state_cost(g, ev.i));   // rounded on its own: no contraction with the sums below
                     double q;
                     if constexpr (MODE == kEval) {
                         const int c0 = code[j];
