@@ -568,6 +568,7 @@ GmArgs<G, VT> gm_args(const dp_grid* g, const Geo<G>& geo, const GmOpts& go)
     a.code = g->code;
     a.feet_lo = g->feet_lo;
     a.feet_hi = g->feet_hi;
+    if (g->feet64_valid) a.f64 = g->f64;
     a.partial = g->gm_partial;
     a.max_blocks = g->gm_blocks;
     a.gctl = g->gm_ctl;

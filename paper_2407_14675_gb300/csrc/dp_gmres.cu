@@ -174,6 +174,31 @@ __device__ __forceinline__ double apply_a_node(const Geo<double>& g, const doubl
     return xj - g.beta64 * (xj + D);
 }
 
+// The same from an FP64 frozen foot (offsets word and fractions).
+template <bool REDUCED, int DYN>
+__device__ __forceinline__ double apply_a_feet64(const Geo<double>& g, const double* __restrict__ x, int j,
+                                                 const Feet64& f64, const uint16_t* __restrict__ code)
+{
+    constexpr bool kPer = DYN == kDynPolar;
+    const double xj = x[j];
+    const unsigned long long w = __ldcs(&f64.w[j]);
+    const int kind = (int)((w >> 32) & 3u);
+    if (kind == kFootInside) {
+        int i[4], cl[4];
+        decode_node(g, j, i);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) cl[d] = i[d] + (int)(signed char)((w >> (8 * d)) & 0xffu);
+        if (kPer) cl[3] = cl[3] < 0 ? cl[3] + g.n[3] : (cl[3] >= g.n[3] ? cl[3] - g.n[3] : cl[3]);
+        const double2 ta = __ldcs(&f64.t[2 * (size_t)j]), tb = __ldcs(&f64.t[2 * (size_t)j + 1]);
+        const double t[4] = {ta.x, ta.y, tb.x, tb.y};
+        Corners<double> K;
+        load_corners<double, double, double, REDUCED, kPer>(g, x, cl, 0.0, K);
+        return xj - g.beta64 * K.blend(t);
+    }
+    if (kind == kFootRecompute) return apply_a_node<REDUCED, DYN>(g, x, j, code);
+    return xj;   // outside or target: no W row
+}
+
 // r0 = V_next - V_in into Q_0, and ||r0||.
 template <typename VV, typename VT>
 __global__ void __launch_bounds__(kGmBlock)
@@ -223,7 +248,7 @@ template <typename G, typename VT, bool REDUCED, int DYN>
 __global__ void __launch_bounds__(kGmBlock, matvec_min_blocks<G>())
 gm_matvec_kernel(const __grid_constant__ Geo<G> g, VT* __restrict__ Q, long long ldq, int k,
                  const uint16_t* __restrict__ code, const unsigned long long* __restrict__ feet_lo,
-                 const unsigned* __restrict__ feet_hi, const GmCtl* __restrict__ gc)
+                 const unsigned* __restrict__ feet_hi, const Feet64 f64, const GmCtl* __restrict__ gc)
 {
     if (*(const volatile int*)&gc->done) return;
     const VT* x = Q + (size_t)k * ldq;
@@ -240,6 +265,9 @@ gm_matvec_kernel(const __grid_constant__ Geo<G> g, VT* __restrict__ Q, long long
             if (j + stride < n) next = FootWord{__ldcs(&feet_lo[j + stride]), __ldcs(&feet_hi[j + stride])};
             w[j] = sk * apply_a_feet<REDUCED, DYN>(g, x, j, fw, code);
         }
+    } else if (f64.w) {
+        for (int j = blockIdx.x * kGmBlock + threadIdx.x; j < n; j += stride)
+            w[j] = sk * apply_a_feet64<REDUCED, DYN>(g, x, j, f64, code);
     } else {
         for (int j = blockIdx.x * kGmBlock + threadIdx.x; j < n; j += stride)
             w[j] = sk * apply_a_node<REDUCED, DYN>(g, x, j, code);
@@ -440,7 +468,7 @@ cudaError_t launch_arnoldi(const GmArgs<G, VT>& a, int k)
     const long long need = ((long long)a.g.n_nodes + kGmBlock - 1) / kGmBlock;
     const long long cap = (long long)per_sm * a.sm_count;
     const int b = (int)(need < cap ? (need < 1 ? 1 : need) : cap);
-    kern<<<b, kGmBlock, 0, a.stream>>>(a.g, a.Q, a.ldq, k, a.code, a.feet_lo, a.feet_hi, a.gctl);
+    kern<<<b, kGmBlock, 0, a.stream>>>(a.g, a.Q, a.ldq, k, a.code, a.feet_lo, a.feet_hi, a.f64, a.gctl);
     return cudaGetLastError();
 }
 

@@ -119,6 +119,7 @@ struct GmArgs {
     const uint16_t* code;            // frozen policy
     const unsigned long long* feet_lo;   // frozen feet (FP32 geometry)
     const unsigned* feet_hi;
+    Feet64 f64;                      // FP64 frozen feet (FP64 grids; w == nullptr: recompute)
     double* partial;                 // max_blocks x kGmLd
     int max_blocks;
     GmCtl* gctl;
