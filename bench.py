@@ -34,7 +34,7 @@ METRIC = "Bellman node-updates/s; time to ‖ΔV‖∞<1e-6, plain vs NN-warm-st
 # DRAM bytes (read + written) of one launch of the 61^4 frozen-feet evaluation
 # sweep, from one ncu capture of the current kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum); to be retaken (or set to None) whenever it changes
-EVAL_TRAFFIC_61X4 = 221.605120e6 + 20.989696e6
+EVAL_TRAFFIC_61X4 = 221.585408e6 + 21.070848e6
 UNIT = "node-updates/s"
 L2_BYTES = 129 * 2 ** 20
 
