@@ -69,3 +69,18 @@ def test_invalid_descriptor_is_rejected_without_gpu_work(lib):
     rc = lib.dp_grid_create(C.byref(d), C.byref(h))
     assert rc == dp.DP_EINVAL and not h.value
     assert "beta" in dp.dp_last_error()
+
+
+def test_binding_constants_match_header():
+    # every DP_* number the binding exports equals the header's #define
+    from paper_2407_14675_gb300 import dp
+    src = open(os.path.join(ROOT, "include", "dp.h")).read()
+    defines = dict((k, int(v)) for k, v in re.findall(r"#define\s+(DP_[A-Z0-9_]+)\s+(-?\d+)", src))
+    names = [n for n in dir(dp) if n.startswith("DP_") and isinstance(getattr(dp, n), int)]
+    assert len(names) >= 20
+    for n in names:
+        assert n in defines, n
+        assert getattr(dp, n) == defines[n], n
+    for n in ("DP_EVAL_JACOBI", "DP_EVAL_GMRES", "DP_EVAL_DIAG", "DP_SWEEP_EVAL_DIAG", "DP_SWEEP_VI_DIAG",
+              "DP_GMRES_MAX_RESTART"):
+        assert n in names
