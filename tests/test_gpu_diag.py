@@ -203,3 +203,21 @@ def test_fp64_frozen_feet_evaluate_as_recomputing(dp, name):
                 assert (c1 == dp.DP_CODE_OFF).any()
             else:
                 np.testing.assert_array_equal(v_feet, v_rec)
+
+
+def test_solvers_agree_on_the_fp32_band_grid(dp):
+    # the energy-band (reduced) grid in FP32 with the FP64 polish: plain,
+    # diagonal-solved and GMRES evaluation reach the same fixed point
+    p = W.config2(25)
+    out = {}
+    for name, kw in (("sweeps", dict(n_eval=20)), ("diag", dict(n_eval=20, eval_solver=dp.DP_EVAL_DIAG)),
+                     ("gmres", dict(eval_solver=dp.DP_EVAL_GMRES, gmres_restart=20))):
+        with dp.Grid(p) as g:
+            rc, st = g.policy_iterate(tol=1e-6, max_sweeps=3000, polish=1, **kw)
+            assert rc == dp.DP_OK and st.converged, (name, st.asdict())
+            out[name] = (g.get_value(), st.sweeps_improve + st.sweeps_improve_fp64)
+    v0 = out["sweeps"][0]
+    for name in ("diag", "gmres"):
+        # each is within tol / (1 - beta) of the scheme's fixed point
+        assert np.abs(out[name][0] - v0).max() <= 2e-6 / (1 - p.beta), name
+    assert out["diag"][1] < out["sweeps"][1]
