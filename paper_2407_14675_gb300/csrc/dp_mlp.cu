@@ -231,52 +231,86 @@ __global__ void states_in_kernel(const double* __restrict__ s, int count, double
     x[4 * i + 3] = (float)(2.0 * (s[4 * i + 3] - lo.w) / (hi.w - lo.w) - 1.0);
 }
 
-// Layer 1 (4 -> 256): z1 = W1 x + b1, h1 = GELU(z1); rows >= count are zero.
+// Layer 1 (4 -> 256) with GELU: one thread per sample and 8 consecutive
+// features (16-byte stores of h1), W1 and b1 staged in shared memory.
 __global__ void l1_fwd_kernel(const float* __restrict__ x, const float* __restrict__ P, int count, int rows,
                               float* __restrict__ z1, bf16* __restrict__ h1)
 {
+    __shared__ float sW[kH * 4 + kH];
+    for (int i = threadIdx.x; i < kH * 5; i += blockDim.x) sW[i] = P[kOffW1 + i];   // W1 then b1
+    __syncthreads();
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (long long)rows * kH) return;
-    const int s = (int)(e / kH), o = (int)(e % kH);
-    float z = 0.0f;
-    if (s < count) {
-        const float* W = P + kOffW1 + o * 4;
-        z = P[kOffB1 + o] + W[0] * x[4 * s] + W[1] * x[4 * s + 1] + W[2] * x[4 * s + 2] + W[3] * x[4 * s + 3];
+    if (e >= (long long)rows * (kH / 8)) return;
+    const int s = (int)(e / (kH / 8)), o0 = (int)(e % (kH / 8)) * 8;
+    float4 xs = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (s < count) xs = *reinterpret_cast<const float4*>(x + 4 * (size_t)s);
+    float z[8];
+    unsigned pk[4];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float* W = sW + (o0 + q) * 4;
+        z[q] = s < count ? sW[kH * 4 + o0 + q] + W[0] * xs.x + W[1] * xs.y + W[2] * xs.z + W[3] * xs.w : 0.0f;
     }
-    if (z1) z1[e] = z;
-    h1[e] = __float2bfloat16(s < count ? gelu(z) : 0.0f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(s < count ? gelu(z[2 * q]) : 0.0f,
+                                                        s < count ? gelu(z[2 * q + 1]) : 0.0f);
+        pk[q] = *reinterpret_cast<const unsigned*>(&h2);
+    }
+    *reinterpret_cast<uint4*>(h1 + (size_t)s * kH + o0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    if (z1) {
+        float4* zp = reinterpret_cast<float4*>(z1 + (size_t)s * kH + o0);
+        zp[0] = make_float4(z[0], z[1], z[2], z[3]);
+        zp[1] = make_float4(z[4], z[5], z[6], z[7]);
+    }
 }
 
-// Output layer (256 -> 3), one thread per sample; with targets also the loss
-// gradient dy = 2 (y - t) / (3 B) and the loss sum.
+// Output layer (256 -> 3): one warp per sample, each lane 8 consecutive
+// features (one 16-byte load), the three sums reduced across the warp; with
+// targets also the loss gradient dy = 2 (y - t) / (3 B) and the loss sum.
 __global__ void out_kernel(const bf16* __restrict__ h3, const float* __restrict__ P, const float* __restrict__ t,
                            int count, float inv_n, float* __restrict__ y, float* __restrict__ dy,
                            float* __restrict__ loss)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ float sW[3 * kH + 3];
+    for (int i = threadIdx.x; i < 3 * kH + 3; i += blockDim.x) sW[i] = P[kOffW4 + i];   // W4 then b4
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     float l = 0.0f;
     if (s < count) {
-        float acc[3] = {P[kOffB4], P[kOffB4 + 1], P[kOffB4 + 2]};
-        const bf16* h = h3 + (size_t)s * kH;
-        for (int i = 0; i < kH; ++i) {
-            const float a = __bfloat162float(h[i]);
+        const uint4 v = *reinterpret_cast<const uint4*>(h3 + (size_t)s * kH + lane * 8);
+        const unsigned u[4] = {v.x, v.y, v.z, v.w};
+        float a[8];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) acc[k] += P[kOffW4 + k * kH + i] * a;
+        for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&u[q]);
+            a[2 * q] = __low2float(h2);
+            a[2 * q + 1] = __high2float(h2);
         }
+        float acc[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            if (y) y[3 * s + k] = acc[k];
-            if (t) {
-                const float r = acc[k] - t[3 * s + k];
-                l += r * r;
-                dy[3 * s + k] = 2.0f * r * inv_n;
+            float sum = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) sum += sW[k * kH + lane * 8 + q] * a[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            acc[k] = sum + sW[3 * kH + k];
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (y) y[3 * (size_t)s + k] = acc[k];
+                if (t) {
+                    const float r = acc[k] - t[3 * (size_t)s + k];
+                    l += r * r;
+                    dy[3 * (size_t)s + k] = 2.0f * r * inv_n;
+                }
             }
         }
     }
-    if (loss) {
-        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(loss, l);
-    }
+    if (loss && lane == 0 && l != 0.0f) atomicAdd(loss, l);
 }
 
 // dz3 = (dy W4) * GELU'(z3), one thread per (sample, feature).
@@ -466,15 +500,15 @@ cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int 
 int forward(dp_mlp* m, int count, bool save, const float* targets, float inv_n)
 {
     const int rows = (count + kTileM - 1) / kTileM * kTileM;
-    const long long e = (long long)rows * kH;
-    l1_fwd_kernel<<<(unsigned)((e + 255) / 256), 256, 0, m->st>>>(m->x, m->P, count, rows, save ? m->z1 : nullptr,
-                                                                    m->h1);
+    const long long e8 = (long long)rows * (kH / 8);
+    l1_fwd_kernel<<<(unsigned)((e8 + 255) / 256), 256, 0, m->st>>>(m->x, m->P, count, rows,
+                                                                     save ? m->z1 : nullptr, m->h1);
     MCK(cudaGetLastError());
     MCK(gemm<kEpiFwd>(m, m->h1, kH, m->W2b, kH, rows, kH, 1, m->P + kOffB2, save ? m->z2 : nullptr, nullptr, m->h2,
                       nullptr));
     MCK(gemm<kEpiFwd>(m, m->h2, kH, m->W3b, kH, rows, kH, 1, m->P + kOffB3, save ? m->z3 : nullptr, nullptr, m->h3,
                       nullptr));
-    out_kernel<<<(count + 127) / 128, 128, 0, m->st>>>(m->h3, m->P, targets, count, inv_n, m->y, m->dy,
+    out_kernel<<<(count + 7) / 8, 256, 0, m->st>>>(m->h3, m->P, targets, count, inv_n, m->y, m->dy,
                                                         targets ? m->loss : nullptr);
     MCK(cudaGetLastError());
     return DP_OK;
