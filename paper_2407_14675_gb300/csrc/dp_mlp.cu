@@ -66,12 +66,24 @@ __device__ __forceinline__ float gelu_grad(float z)
 
 enum { kEpiFwd = 0, kEpiBwd = 1, kEpiAtomic = 2 };
 
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned), and the
+// wait for all of this thread's copies.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
 // C[128 x 128 tile] = A[rows, K range] * B[256, K range]^T on tcgen05.
 //   A: bf16 [*, lda] row-major (K contiguous); B: bf16 [256, ldb] row-major.
 //   Tile rows start at 128 blockIdx.x, columns at 128 blockIdx.y; K range
 //   [k_per_cta blockIdx.z, +k_per_cta), staged 256 at a time: every thread
-//   issues its 16-byte loads of the whole slice at once, then one thread
-//   issues the 16 MMAs (K = 16 each) and commits them to an mbarrier.
+//   issues its 16-byte asynchronous copies of the whole slice at once, then
+//   one thread issues the 16 MMAs (K = 16 each) and commits them to an
+//   mbarrier.
 //   kEpiFwd:    z = acc + bias -> zout (optional, FP32), h = GELU(z) -> hout (bf16)
 //   kEpiBwd:    dz = acc * GELU'(zin) -> hout (bf16)
 //   kEpiAtomic: cacc += acc (FP32, split-K weight gradients)
@@ -106,23 +118,21 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
         // A warp takes 8 rows x 4 consecutive 16-byte groups: 64 contiguous bytes
         // of each row in global memory, 512 contiguous bytes (no bank conflict)
         // in shared memory.
-        int4 va[kTileM * kGroups / 128], vb[kTileN * kGroups / 128];
+        // the 16-byte groups go straight to shared memory (cp.async): every
+        // group of the slice is in flight at once, none through registers
 #pragma unroll
         for (int q = 0; q < kTileM * kGroups / 128; ++q) {
             const int v = tid + 128 * q, grp = v >> 5, ln = v & 31;
             const int row = (grp / (kGroups / 4)) * 8 + (ln & 7), kb = (grp % (kGroups / 4)) * 4 + (ln >> 3);
-            va[q] = *(const int4*)(A + (row0 + row) * (size_t)lda + k0 + kb * 8);
+            cp_async16(sA + (size_t)v * 16, A + (row0 + row) * (size_t)lda + k0 + kb * 8);
         }
 #pragma unroll
         for (int q = 0; q < kTileN * kGroups / 128; ++q) {
             const int v = tid + 128 * q, grp = v >> 5, ln = v & 31;
             const int row = (grp / (kGroups / 4)) * 8 + (ln & 7), kb = (grp % (kGroups / 4)) * 4 + (ln >> 3);
-            vb[q] = *(const int4*)(B + (size_t)(n0 + row) * ldb + k0 + kb * 8);
+            cp_async16(sB + (size_t)v * 16, B + (size_t)(n0 + row) * ldb + k0 + kb * 8);
         }
-#pragma unroll
-        for (int q = 0; q < kTileM * kGroups / 128; ++q) *(int4*)(sA + (size_t)(tid + 128 * q) * 16) = va[q];
-#pragma unroll
-        for (int q = 0; q < kTileN * kGroups / 128; ++q) *(int4*)(sB + (size_t)(tid + 128 * q) * 16) = vb[q];
+        cp_async_wait_all();
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {
