@@ -11,6 +11,7 @@
 // backward, split-K atomic accumulation for weight gradients).  The 4-wide
 // input layer, the 3-wide output layer, the reductions and Adam run on the
 // CUDA cores.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -54,7 +55,10 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kH * 4, kOffW2 = kOffB1 + kH, kOffB2
 constexpr int kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH * kH, kOffW4 = kOffB3 + kH, kOffB4 = kOffW4 + 3 * kH;
 constexpr int kParams = kOffB4 + 3;           // 133,635
 constexpr int kTileM = 128, kTileN = 128, kKC = 256;
-constexpr int kGemmSmem = (kTileM + kTileN) * kKC * 2;   // 128 KB: a whole 256-wide K slice of A and B
+// Shared memory of a K slice of A and B: 128 KB for a whole 256-wide slice
+// (one CTA per SM; small batches: every slice at once), 64 KB for 128-wide
+// slices (three CTAs per SM overlap one another's loads and epilogues).
+constexpr int gemm_smem(int kc) { return (kTileM + kTileN) * kc * 2; }
 constexpr int kWaitPolls = 1 << 22;
 constexpr float kInvSqrt2 = 0.70710678118654752f, kInvSqrt2Pi = 0.39894228040143268f;
 
@@ -87,15 +91,15 @@ __device__ __forceinline__ void cp_async_wait_all()
 //   kEpiFwd:    z = acc + bias -> zout (optional, FP32), h = GELU(z) -> hout (bf16)
 //   kEpiBwd:    dz = acc * GELU'(zin) -> hout (bf16)
 //   kEpiAtomic: cacc += acc (FP32, split-K weight gradients)
-template <int EPI>
+template <int EPI, int KC>
 __global__ void __launch_bounds__(128)
 mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb, int k_per_cta,
                 const float* __restrict__ bias, float* __restrict__ zout, const float* __restrict__ zin,
                 bf16* __restrict__ hout, float* __restrict__ cacc, int* __restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sA = smem;                        // 128 x 256 bf16 = 64 KB
-    unsigned char* sB = smem + kTileM * kKC * 2;     // 128 x 256 bf16 = 64 KB
+    unsigned char* sA = smem;                        // 128 x KC bf16
+    unsigned char* sB = smem + kTileM * KC * 2;      // 128 x KC bf16
     __shared__ unsigned tmem_slot;
     __shared__ __align__(8) unsigned long long mbar;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -109,11 +113,11 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
     const int n0 = blockIdx.y * kTileN;
     const int kbeg = blockIdx.z * k_per_cta;
     constexpr unsigned idesc = umma_idesc_bf16(kTileM, kTileN);
-    constexpr int kGroups = kKC / 8;                 // 16-byte groups per row of a slice
+    constexpr int kGroups = KC / 8;                  // 16-byte groups per row of a slice
 
     int phase = 0;
     bool ok = true;
-    for (int k0 = kbeg; k0 < kbeg + k_per_cta; k0 += kKC) {
+    for (int k0 = kbeg; k0 < kbeg + k_per_cta; k0 += KC) {
         // core-matrix staging: (row, kb) -> ((row / 8) * kGroups + kb) * 128 + (row % 8) * 16.
         // A warp takes 8 rows x 4 consecutive 16-byte groups: 64 contiguous bytes
         // of each row in global memory, 512 contiguous bytes (no bank conflict)
@@ -138,7 +142,7 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
         if (tid == 0) {
             fence_after_sync();
 #pragma unroll
-            for (int s = 0; s < kKC / 16; ++s) {
+            for (int s = 0; s < KC / 16; ++s) {
                 const unsigned long long ad = umma_desc(smem_u32(sA) + s * 256, 128, kGroups * 128);
                 const unsigned long long bd = umma_desc(smem_u32(sB) + s * 256, 128, kGroups * 128);
                 umma_bf16(tmem, ad, bd, idesc, (k0 > kbeg || s > 0) ? 1u : 0u);
@@ -249,8 +253,9 @@ __global__ void l1_fwd_kernel(const float* __restrict__ x, const float* __restri
     __shared__ float sW[kH * 4 + kH];
     for (int i = threadIdx.x; i < kH * 5; i += blockDim.x) sW[i] = P[kOffW1 + i];   // W1 then b1
     __syncthreads();
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (long long)rows * (kH / 8)) return;
+    const long long total = (long long)rows * (kH / 8);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
     const int s = (int)(e / (kH / 8)), o0 = (int)(e % (kH / 8)) * 8;
     float4 xs = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (s < count) xs = *reinterpret_cast<const float4*>(x + 4 * (size_t)s);
@@ -272,6 +277,7 @@ __global__ void l1_fwd_kernel(const float* __restrict__ x, const float* __restri
         float4* zp = reinterpret_cast<float4*>(z1 + (size_t)s * kH + o0);
         zp[0] = make_float4(z[0], z[1], z[2], z[3]);
         zp[1] = make_float4(z[4], z[5], z[6], z[7]);
+    }
     }
 }
 
@@ -443,6 +449,7 @@ int fail_cuda(const char* what, cudaError_t e)
 
 struct dp_mlp {
     int device = 0;
+    int sm_count = 1;
     cudaStream_t st = nullptr;
     int cap = 0;                       // activation rows (multiple of 512)
     double lo[4], hi[4];               // input box (normalisation)
@@ -488,21 +495,35 @@ int refresh_bf16(dp_mlp* m)
     return DP_OK;
 }
 
-template <int EPI>
-cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int rows, int k_total, int k_split,
-                 const float* bias, float* zout, const float* zin, bf16* hout, float* cacc)
+template <int EPI, int KC>
+cudaError_t gemm_kc(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int rows, int k_total, int k_split,
+                    const float* bias, float* zout, const float* zin, bf16* hout, float* cacc)
 {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(mlp_gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kGemmSmem);
+        cudaError_t e = cudaFuncSetAttribute(mlp_gemm_kernel<EPI, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             gemm_smem(KC));
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid(rows / kTileM, kH / kTileN, k_split);
-    mlp_gemm_kernel<EPI><<<grid, 128, kGemmSmem, m->st>>>(A, lda, B, ldb, k_total / k_split, bias, zout, zin, hout,
-                                                           cacc, m->err);
+    mlp_gemm_kernel<EPI, KC><<<grid, 128, gemm_smem(KC), m->st>>>(A, lda, B, ldb, k_total / k_split, bias, zout, zin,
+                                                                   hout, cacc, m->err);
     return cudaGetLastError();
+}
+
+// Large batches (inference over a grid) stage K in 128-wide halves so that
+// three CTAs share an SM; small ones (training) stage the whole 256-wide K
+// slice at once; split-K weight gradients take one 256-wide slice per CTA.
+constexpr int kManyRows = 16384;
+
+template <int EPI>
+cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int rows, int k_total, int k_split,
+                 const float* bias, float* zout, const float* zin, bf16* hout, float* cacc)
+{
+    if (EPI != kEpiAtomic && rows >= kManyRows)
+        return gemm_kc<EPI, kKC / 2>(m, A, lda, B, ldb, rows, k_total, k_split, bias, zout, zin, hout, cacc);
+    return gemm_kc<EPI, kKC>(m, A, lda, B, ldb, rows, k_total, k_split, bias, zout, zin, hout, cacc);
 }
 
 // Forward of `count` rows held in m->x (rows padded to a multiple of 128).
@@ -511,8 +532,8 @@ int forward(dp_mlp* m, int count, bool save, const float* targets, float inv_n)
 {
     const int rows = (count + kTileM - 1) / kTileM * kTileM;
     const long long e8 = (long long)rows * (kH / 8);
-    l1_fwd_kernel<<<(unsigned)((e8 + 255) / 256), 256, 0, m->st>>>(m->x, m->P, count, rows,
-                                                                     save ? m->z1 : nullptr, m->h1);
+    const unsigned b1 = (unsigned)std::min<long long>((e8 + 255) / 256, 8LL * m->sm_count);
+    l1_fwd_kernel<<<b1, 256, 0, m->st>>>(m->x, m->P, count, rows, save ? m->z1 : nullptr, m->h1);
     MCK(cudaGetLastError());
     MCK(gemm<kEpiFwd>(m, m->h1, kH, m->W2b, kH, rows, kH, 1, m->P + kOffB2, save ? m->z2 : nullptr, nullptr, m->h2,
                       nullptr));
@@ -593,6 +614,7 @@ int dp_mlp_create(const double* lo, const double* hi, int32_t batch_capacity, vo
     m->cap = batch_capacity;
     for (int d = 0; d < 4; ++d) { m->lo[d] = lo[d]; m->hi[d] = hi[d]; }
     cudaGetDevice(&m->device);
+    cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, m->device);
     const size_t C = (size_t)m->cap, CH = C * kH;
     cudaError_t e = cudaSuccess;
     auto A = [&](auto** p, size_t n) { if (e == cudaSuccess) e = malloc_n(p, n); };
