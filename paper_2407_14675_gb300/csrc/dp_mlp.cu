@@ -245,39 +245,31 @@ __global__ void states_in_kernel(const double* __restrict__ s, int count, double
     x[4 * i + 3] = (float)(2.0 * (s[4 * i + 3] - lo.w) / (hi.w - lo.w) - 1.0);
 }
 
-// Layer 1 (4 -> 256) with GELU: one thread per sample and 8 consecutive
-// features (16-byte stores of h1), W1 and b1 staged in shared memory.
+// Layer 1 (4 -> 256) with GELU: 32 threads per sample, thread `lane` takes
+// the features lane + 32 q (conflict-free reads of the transposed W1 in shared
+// memory, each warp store 64 contiguous bytes).  Rows >= count are zero.
 __global__ void l1_fwd_kernel(const float* __restrict__ x, const float* __restrict__ P, int count, int rows,
                               float* __restrict__ z1, bf16* __restrict__ h1)
 {
-    __shared__ float sW[kH * 4 + kH];
-    for (int i = threadIdx.x; i < kH * 5; i += blockDim.x) sW[i] = P[kOffW1 + i];   // W1 then b1
+    __shared__ float sWt[4 * kH + kH];   // W1 transposed (4 x 256), then b1
+    for (int i = threadIdx.x; i < 4 * kH; i += blockDim.x) sWt[(i & 3) * kH + (i >> 2)] = P[kOffW1 + i];
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) sWt[4 * kH + i] = P[kOffB1 + i];
     __syncthreads();
-    const long long total = (long long)rows * (kH / 8);
+    const long long total = (long long)rows * 32;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(e / (kH / 8)), o0 = (int)(e % (kH / 8)) * 8;
-    float4 xs = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (s < count) xs = *reinterpret_cast<const float4*>(x + 4 * (size_t)s);
-    float z[8];
-    unsigned pk[4];
+        const int s = (int)(e >> 5), lane = (int)(e & 31);
+        float4 xs = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (s < count) xs = *reinterpret_cast<const float4*>(x + 4 * (size_t)s);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const float* W = sW + (o0 + q) * 4;
-        z[q] = s < count ? sW[kH * 4 + o0 + q] + W[0] * xs.x + W[1] * xs.y + W[2] * xs.z + W[3] * xs.w : 0.0f;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(s < count ? gelu(z[2 * q]) : 0.0f,
-                                                        s < count ? gelu(z[2 * q + 1]) : 0.0f);
-        pk[q] = *reinterpret_cast<const unsigned*>(&h2);
-    }
-    *reinterpret_cast<uint4*>(h1 + (size_t)s * kH + o0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    if (z1) {
-        float4* zp = reinterpret_cast<float4*>(z1 + (size_t)s * kH + o0);
-        zp[0] = make_float4(z[0], z[1], z[2], z[3]);
-        zp[1] = make_float4(z[4], z[5], z[6], z[7]);
-    }
+        for (int q = 0; q < kH / 32; ++q) {
+            const int o = lane + 32 * q;
+            const float z = s < count ? sWt[4 * kH + o] + sWt[o] * xs.x + sWt[kH + o] * xs.y +
+                                            sWt[2 * kH + o] * xs.z + sWt[3 * kH + o] * xs.w
+                                      : 0.0f;
+            h1[(size_t)s * kH + o] = __float2bfloat16(s < count ? gelu(z) : 0.0f);
+            if (z1) z1[(size_t)s * kH + o] = z;
+        }
     }
 }
 
@@ -531,7 +523,7 @@ cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int 
 int forward(dp_mlp* m, int count, bool save, const float* targets, float inv_n)
 {
     const int rows = (count + kTileM - 1) / kTileM * kTileM;
-    const long long e8 = (long long)rows * (kH / 8);
+    const long long e8 = (long long)rows * 32;
     const unsigned b1 = (unsigned)std::min<long long>((e8 + 255) / 256, 8LL * m->sm_count);
     l1_fwd_kernel<<<b1, 256, 0, m->st>>>(m->x, m->P, count, rows, save ? m->z1 : nullptr, m->h1);
     MCK(cudaGetLastError());
