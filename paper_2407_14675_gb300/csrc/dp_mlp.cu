@@ -70,6 +70,11 @@ __device__ __forceinline__ float gelu_grad(float z)
 
 enum { kEpiFwd = 0, kEpiBwd = 1, kEpiAtomic = 2 };
 
+// Four doubles by value (the network's input box corners).
+struct Box4 {
+    double x, y, z, w;
+};
+
 // 16-byte asynchronous copy global -> shared (both 16-byte aligned), and the
 // wait for all of this thread's copies.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src)
@@ -210,7 +215,7 @@ template <typename S>
 __global__ void batch_from_grid_kernel(Geo<double> g, const S* __restrict__ V, const uint16_t* __restrict__ code,
                                        const double2* __restrict__ thi, const double2* __restrict__ tlo,
                                        long long n, long long mult, long long offset, long long start, int count,
-                                       double invM, double4 nlo, double4 nhi, float* __restrict__ x,
+                                       double invM, Box4 nlo, Box4 nhi, float* __restrict__ x,
                                        float* __restrict__ t)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -234,7 +239,7 @@ __global__ void batch_from_grid_kernel(Geo<double> g, const S* __restrict__ V, c
 }
 
 // Arbitrary states (device, n x 4 double) normalised to [-1, 1]^4.
-__global__ void states_in_kernel(const double* __restrict__ s, int count, double4 lo, double4 hi,
+__global__ void states_in_kernel(const double* __restrict__ s, int count, Box4 lo, Box4 hi,
                                  float* __restrict__ x)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -664,8 +669,8 @@ int dp_mlp_forward(dp_mlp* m, const double* states, int32_t n, float* out)
 {
     if (!m || (n > 0 && (!states || !out))) return record_error(DP_EINVAL, "NULL argument");
     if (n < 0) return record_error(DP_EINVAL, "n < 0");
-    const double4 lo = make_double4(m->lo[0], m->lo[1], m->lo[2], m->lo[3]);
-    const double4 hi = make_double4(m->hi[0], m->hi[1], m->hi[2], m->hi[3]);
+    const Box4 lo{m->lo[0], m->lo[1], m->lo[2], m->lo[3]};
+    const Box4 hi{m->hi[0], m->hi[1], m->hi[2], m->hi[3]};
     for (int s0 = 0; s0 < n; s0 += m->cap) {
         const int cnt = std::min(m->cap, n - s0);
         MCK(cudaMemcpyAsync(m->states, states + 4 * (size_t)s0, sizeof(double) * 4 * cnt, cudaMemcpyHostToDevice,
@@ -683,8 +688,8 @@ int dp_mlp_gradients(dp_mlp* m, const double* states, const float* targets, int3
 {
     if (!m || !states || !targets || !grads) return record_error(DP_EINVAL, "NULL argument");
     if (n < 512 || n % 512 != 0 || n > m->cap) return record_error(DP_EINVAL, "n must be a multiple of 512 <= capacity");
-    const double4 lo = make_double4(m->lo[0], m->lo[1], m->lo[2], m->lo[3]);
-    const double4 hi = make_double4(m->hi[0], m->hi[1], m->hi[2], m->hi[3]);
+    const Box4 lo{m->lo[0], m->lo[1], m->lo[2], m->lo[3]};
+    const Box4 hi{m->hi[0], m->hi[1], m->hi[2], m->hi[3]};
     MCK(cudaMemcpyAsync(m->states, states, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, m->st));
     MCK(cudaMemcpyAsync(m->t, targets, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->st));
     states_in_kernel<<<(n + 255) / 256, 256, 0, m->st>>>(m->states, n, lo, hi, m->x);
@@ -715,8 +720,8 @@ int dp_mlp_train_grid(dp_mlp* m, dp_grid* grid, const dp_mlp_train_opts* o, dp_m
     MCK(cudaEventRecord(e0, m->st));
     const int B = o->batch;
     const long long steps_per_epoch = n / B;
-    const double4 nlo = make_double4(m->lo[0], m->lo[1], m->lo[2], m->lo[3]);
-    const double4 nhi = make_double4(m->hi[0], m->hi[1], m->hi[2], m->hi[3]);
+    const Box4 nlo{m->lo[0], m->lo[1], m->lo[2], m->lo[3]};
+    const Box4 nhi{m->hi[0], m->hi[1], m->hi[2], m->hi[3]};
     double last_loss = 0.0, first_loss = -1.0;
     unsigned long long rng = o->seed ? o->seed : 14675ull;
     auto next = [&]() {   // splitmix64: seeds of the per-epoch permutation
@@ -787,8 +792,8 @@ int dp_warm_start(dp_mlp* m, dp_grid* grid, double* ms_out)
     MCK(cudaEventRecord(e0, m->st));
     // node coordinates of this grid, normalised to the network's own box
     Geo<double> g = gv.g64;
-    const double4 nlo = make_double4(m->lo[0], m->lo[1], m->lo[2], m->lo[3]);
-    const double4 nhi = make_double4(m->hi[0], m->hi[1], m->hi[2], m->hi[3]);
+    const Box4 nlo{m->lo[0], m->lo[1], m->lo[2], m->lo[3]};
+    const Box4 nhi{m->hi[0], m->hi[1], m->hi[2], m->hi[3]};
     for (long long s0 = 0; s0 < gv.n; s0 += m->cap) {
         const int cnt = (int)std::min<long long>(m->cap, gv.n - s0);
         batch_from_grid_kernel<double><<<(cnt + 255) / 256, 256, 0, m->st>>>(
