@@ -207,6 +207,112 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
     if (warp == 0) tmem_dealloc(tmem, kTileN);
 }
 
+// Forward GEMM of a large batch (inference over a grid), persistent: each
+// CTA takes one 128-column half of the layer (its 128 x 256 slice of the
+// weights stays in shared memory, 64 KB) and walks row tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  The next tile's 128 x 256
+// activations are copied (cp.async) into the second of two 64 KB buffers
+// while the MMAs and the bias + GELU epilogue of the current tile run.
+// Same staging layout, MMAs and epilogue arithmetic as mlp_gemm_kernel<kEpiFwd>.
+constexpr int kPersistSmem = (kTileN + 2 * kTileM) * kKC * 2;   // 192 KB
+
+__global__ void __launch_bounds__(128)
+mlp_fwd_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb, int tiles,
+                          const float* __restrict__ bias, bf16* __restrict__ hout, int* __restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sB = smem;                                  // 128 x 256
+    unsigned char* sA[2] = {smem + kTileN * kKC * 2, smem + (kTileN + kTileM) * kKC * 2};
+    __shared__ unsigned tmem_slot;
+    __shared__ __align__(8) unsigned long long mbar;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tmem_alloc(&tmem_slot, kTileN);
+    if (tid == 0) mbar_init(&mbar);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const unsigned tmem = tmem_slot;
+    const int n0 = blockIdx.y * kTileN;
+    constexpr unsigned idesc = umma_idesc_bf16(kTileM, kTileN);
+    constexpr int kGroups = kKC / 8;
+
+    // (row, kb) -> ((row / 8) * kGroups + kb) * 128 + (row % 8) * 16, a warp
+    // taking 8 rows x 4 consecutive 16-byte groups
+    auto stage = [&](unsigned char* dst, const bf16* src, size_t ld, size_t r0) {
+#pragma unroll 4
+        for (int q = 0; q < kTileM * kGroups / 128; ++q) {
+            const int v = tid + 128 * q, grp = v >> 5, ln = v & 31;
+            const int row = (grp / (kGroups / 4)) * 8 + (ln & 7), kb = (grp % (kGroups / 4)) * 4 + (ln >> 3);
+            cp_async16(dst + (size_t)v * 16, src + (r0 + row) * ld + kb * 8);
+        }
+    };
+    stage(sB, B, (size_t)ldb, (size_t)n0);
+    int t = blockIdx.x;
+    if (t < tiles) stage(sA[0], A, (size_t)lda, (size_t)t * kTileM);
+    cp_async_wait_all();
+    fence_async_smem();
+    __syncthreads();
+
+    int phase = 0, buf = 0;
+    bool ok = true;
+    for (; t < tiles; t += gridDim.x, buf ^= 1) {
+        if (tid == 0) {
+            fence_after_sync();
+#pragma unroll
+            for (int s = 0; s < kKC / 16; ++s) {
+                const unsigned long long ad = umma_desc(smem_u32(sA[buf]) + s * 256, 128, kGroups * 128);
+                const unsigned long long bd = umma_desc(smem_u32(sB) + s * 256, 128, kGroups * 128);
+                umma_bf16(tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
+            }
+            umma_commit(&mbar);
+        }
+        // the next tile's activations, into the other buffer (its last
+        // reader, the previous tile's MMAs, has completed)
+        const int tn = t + gridDim.x;
+        if (tn < tiles) stage(sA[buf ^ 1], A, (size_t)lda, (size_t)tn * kTileM);
+        if (!mbar_wait(&mbar, phase, kWaitPolls)) {
+            ok = false;
+            if (lane == 0) atomicOr(err, 1);
+        }
+        phase ^= 1;
+        fence_after_sync();
+        if (!__syncthreads_and(ok)) {
+            cp_async_wait_all();   // no copy may outlive the CTA
+            break;
+        }
+        const size_t r = (size_t)t * kTileM + warp * 32 + lane;   // TMEM lane = tile row
+        for (int c0 = 0; c0 < kTileN; c0 += 16) {
+            float v[16], z[16];
+            tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + c0, v);
+            const size_t off = r * kH + n0 + c0;
+#pragma unroll
+            for (int q = 0; q < 16; q += 4) {
+                const float4 b = *(const float4*)(bias + n0 + c0 + q);
+                z[q] = v[q] + b.x; z[q + 1] = v[q + 1] + b.y; z[q + 2] = v[q + 2] + b.z; z[q + 3] = v[q + 3] + b.w;
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) z[q] = gelu(z[q]);
+            unsigned pk[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(z[2 * q], z[2 * q + 1]);
+                pk[q] = *(const unsigned*)&h2;
+            }
+            *(uint4*)(hout + off) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *(uint4*)(hout + off + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+        // the epilogue's TMEM reads finish before the next tile's MMAs
+        // overwrite the accumulator; the next activations must have landed
+        cp_async_wait_all();
+        fence_async_smem();
+        fence_before_sync();
+        __syncthreads();
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTileN);
+}
+
 // Inputs (normalised to [-1, 1]^4) and targets (V / M, cos, sin) of nodes
 // idx = (mult * (start + i) + offset) mod n of a grid (a seeded permutation).
 // Without V only the inputs are written.  Inputs are normalised to the
@@ -518,6 +624,20 @@ template <int EPI>
 cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int rows, int k_total, int k_split,
                  const float* bias, float* zout, const float* zin, bf16* hout, float* cacc)
 {
+    if (EPI == kEpiFwd && rows >= kManyRows && !zout && k_total == kKC && k_split == 1) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(mlp_fwd_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 kPersistSmem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        const int tiles = rows / kTileM;
+        const int per_half = std::max(1, std::min(tiles, m->sm_count / 2));
+        dim3 grid(per_half, kH / kTileN);
+        mlp_fwd_persistent_kernel<<<grid, 128, kPersistSmem, m->st>>>(A, lda, B, ldb, tiles, bias, hout, m->err);
+        return cudaGetLastError();
+    }
     if (EPI != kEpiAtomic && rows >= kManyRows)
         return gemm_kc<EPI, kKC / 2>(m, A, lda, B, ldb, rows, k_total, k_split, bias, zout, zin, hout, cacc);
     return gemm_kc<EPI, kKC>(m, A, lda, B, ldb, rows, k_total, k_split, bias, zout, zin, hout, cacc);

@@ -33,6 +33,27 @@ def test_forward_matches_fp64_reference(dp):
     assert np.abs(Y - Yref).max() <= 3e-2 * scale + 1e-3
 
 
+def test_large_batch_forward_equals_small_batches(dp):
+    # 40,000 rows in one call take the persistent large-batch GEMM; 4,096-row
+    # calls the per-tile one.  Same staging layout, MMA order and epilogue:
+    # the outputs are bit-identical, and within the BF16 tolerance of the
+    # FP64 reference
+    p = W.config1()
+    params = W.mlp_init_params(seed=5)
+    X = _states(p, 40000, 6)
+    flat = dp.flatten_params(params)
+    with dp.Mlp(p.lo, p.hi, batch_capacity=65536) as big, dp.Mlp(p.lo, p.hi, batch_capacity=4096) as small:
+        dp.dp_mlp_set_params(big.h, flat)
+        dp.dp_mlp_set_params(small.h, flat)
+        Yb = dp.dp_mlp_forward(big.h, X)
+        Yb2 = dp.dp_mlp_forward(big.h, X)
+        Ys = dp.dp_mlp_forward(small.h, X)
+    np.testing.assert_array_equal(Yb, Ys)
+    np.testing.assert_array_equal(Yb, Yb2)
+    Yref = mlp.forward(params, mlp.normalise_states(X[:2000], p.lo, p.hi))[0]
+    assert np.abs(Yb[:2000] - Yref).max() <= 3e-2 * np.abs(Yref).max() + 1e-3
+
+
 def test_gradients_match_fp64_reference(dp):
     p = W.config1()
     params = W.mlp_init_params(seed=5)
