@@ -214,9 +214,12 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
 // activations are copied (cp.async) into the second of two 64 KB buffers
 // while the MMAs and the bias + GELU epilogue of the current tile run.
 // Same staging layout, MMAs and epilogue arithmetic as mlp_gemm_kernel<kEpiFwd>.
+// Eight warps: two per quarter of the TMEM lanes, each taking half of the
+// columns in the epilogue.
 constexpr int kPersistSmem = (kTileN + 2 * kTileM) * kKC * 2;   // 192 KB
+constexpr int kPersistThreads = 256;
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kPersistThreads)
 mlp_fwd_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb, int tiles,
                           const float* __restrict__ bias, bf16* __restrict__ hout, int* __restrict__ err)
 {
@@ -240,8 +243,8 @@ mlp_fwd_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __res
     // taking 8 rows x 4 consecutive 16-byte groups
     auto stage = [&](unsigned char* dst, const bf16* src, size_t ld, size_t r0) {
 #pragma unroll 4
-        for (int q = 0; q < kTileM * kGroups / 128; ++q) {
-            const int v = tid + 128 * q, grp = v >> 5, ln = v & 31;
+        for (int q = 0; q < kTileM * kGroups / kPersistThreads; ++q) {
+            const int v = tid + kPersistThreads * q, grp = v >> 5, ln = v & 31;
             const int row = (grp / (kGroups / 4)) * 8 + (ln & 7), kb = (grp % (kGroups / 4)) * 4 + (ln >> 3);
             cp_async16(dst + (size_t)v * 16, src + (r0 + row) * ld + kb * 8);
         }
@@ -280,10 +283,11 @@ mlp_fwd_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __res
             cp_async_wait_all();   // no copy may outlive the CTA
             break;
         }
-        const size_t r = (size_t)t * kTileM + warp * 32 + lane;   // TMEM lane = tile row
-        for (int c0 = 0; c0 < kTileN; c0 += 16) {
+        const int quarter = warp & 3, half = warp >> 2;
+        const size_t r = (size_t)t * kTileM + quarter * 32 + lane;   // TMEM lane = tile row
+        for (int c0 = half * (kTileN / 2); c0 < (half + 1) * (kTileN / 2); c0 += 16) {
             float v[16], z[16];
-            tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + c0, v);
+            tmem_ld16(tmem + ((unsigned)(quarter * 32) << 16) + c0, v);
             const size_t off = r * kH + n0 + c0;
 #pragma unroll
             for (int q = 0; q < 16; q += 4) {
@@ -635,7 +639,8 @@ cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int 
         const int tiles = rows / kTileM;
         const int per_half = std::max(1, std::min(tiles, m->sm_count / 2));
         dim3 grid(per_half, kH / kTileN);
-        mlp_fwd_persistent_kernel<<<grid, 128, kPersistSmem, m->st>>>(A, lda, B, ldb, tiles, bias, hout, m->err);
+        mlp_fwd_persistent_kernel<<<grid, kPersistThreads, kPersistSmem, m->st>>>(A, lda, B, ldb, tiles, bias, hout,
+                                                                                  m->err);
         return cudaGetLastError();
     }
     if (EPI != kEpiAtomic && rows >= kManyRows)
