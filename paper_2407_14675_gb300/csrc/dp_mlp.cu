@@ -214,10 +214,11 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
 // activations are copied (cp.async) into the second of two 64 KB buffers
 // while the MMAs and the bias + GELU epilogue of the current tile run.
 // Same staging layout, MMAs and epilogue arithmetic as mlp_gemm_kernel<kEpiFwd>.
-// Eight warps: two per quarter of the TMEM lanes, each taking half of the
-// columns in the epilogue.
+// Sixteen warps: four per quarter of the TMEM lanes, each taking a quarter
+// of the columns in the epilogue.
 constexpr int kPersistSmem = (kTileN + 2 * kTileM) * kKC * 2;   // 192 KB
-constexpr int kPersistThreads = 256;
+constexpr int kPersistThreads = 512;
+constexpr int kPersistParts = kPersistThreads / 128;            // column parts per TMEM lane quarter
 
 __global__ void __launch_bounds__(kPersistThreads)
 mlp_fwd_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb, int tiles,
@@ -283,9 +284,10 @@ mlp_fwd_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __res
             cp_async_wait_all();   // no copy may outlive the CTA
             break;
         }
-        const int quarter = warp & 3, half = warp >> 2;
+        const int quarter = warp & 3, part = warp >> 2;
         const size_t r = (size_t)t * kTileM + quarter * 32 + lane;   // TMEM lane = tile row
-        for (int c0 = half * (kTileN / 2); c0 < (half + 1) * (kTileN / 2); c0 += 16) {
+        constexpr int kCols = kTileN / kPersistParts;
+        for (int c0 = part * kCols; c0 < (part + 1) * kCols; c0 += 16) {
             float v[16], z[16];
             tmem_ld16(tmem + ((unsigned)(quarter * 32) << 16) + c0, v);
             const size_t off = r * kH + n0 + c0;
