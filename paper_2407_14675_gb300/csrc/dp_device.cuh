@@ -307,6 +307,22 @@ template <> struct Corners<double> {
         double h1 = f[2] + t[1] * (f[3] - f[2]);
         return h0 + t[0] * (h1 - h0);
     }
+    // the lerp along m done once for a fixed mass fraction (e0 then holds
+    // it); blend_m_folded(t) equals blend(t) for that fraction
+    __device__ __forceinline__ void fold_m(double t3)
+    {
+#pragma unroll
+        for (int x = 0; x < 8; ++x) e0[x] = e0[x] + t3 * de[x];
+    }
+    __device__ __forceinline__ double blend_m_folded(const double t[4]) const
+    {
+        double f[4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) f[y] = e0[2 * y] + t[2] * (e0[2 * y + 1] - e0[2 * y]);
+        double h0 = f[0] + t[1] * (f[1] - f[0]);
+        double h1 = f[2] + t[1] * (f[3] - f[2]);
+        return h0 + t[0] * (h1 - h0);
+    }
 };
 
 template <> struct Corners<float> {
@@ -331,6 +347,22 @@ template <> struct Corners<float> {
         float h0, h1;
         unpack2(S, h0, h1);
         return h0 + t[0] * (h1 - h0);                                            // along r
+    }
+    __device__ __forceinline__ void fold_m(float t3)
+    {
+        const unsigned long long tt = pack2(t3, t3);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) q0[x] = fma2(qd[x], tt, q0[x]);
+    }
+    __device__ __forceinline__ float blend_m_folded(const float t[4]) const
+    {
+        const unsigned long long t2 = pack2(t[2], t[2]), t1 = pack2(t[1], t[1]);
+        unsigned long long R0 = fma2(sub2(q0[1], q0[0]), t2, q0[0]);
+        unsigned long long R1 = fma2(sub2(q0[3], q0[2]), t2, q0[2]);
+        unsigned long long S = fma2(sub2(R1, R0), t1, R0);
+        float h0, h1;
+        unpack2(S, h0, h1);
+        return h0 + t[0] * (h1 - h0);
     }
 };
 
@@ -361,7 +393,9 @@ __device__ __forceinline__ bool cell_rows(const Geo<G>& g, const int c[4], int b
 }
 
 // Loads the 16 corners given the index of corner (c_vt, c_m) in each of the
-// four (r, v_r) rows (n_m: stride of v_t).
+// four (r, v_r) rows (n_m: stride of v_t).  The lower mass corner enters as
+// its difference to vj, the step to the upper one as v_upper - v_lower
+// (one rounding, in the value type).
 template <typename G, typename S>
 __device__ __forceinline__ void load_rows(const S* __restrict__ V, const int base[4], int n_m, S vj, Corners<G>& K,
                                           int up = 1)
@@ -372,11 +406,38 @@ __device__ __forceinline__ void load_rows(const S* __restrict__ V, const int bas
         const S* p = V + base[rb];
         S v00 = __ldg(p), v01 = __ldg(p + up), v10 = __ldg(p + n_m), v11 = __ldg(p + n_m + up);
         a[2 * rb] = (G)(v00 - vj);
-        d[2 * rb] = (G)(v01 - vj) - a[2 * rb];
+        d[2 * rb] = (G)(v01 - v00);
         a[2 * rb + 1] = (G)(v10 - vj);
-        d[2 * rb + 1] = (G)(v11 - vj) - a[2 * rb + 1];
+        d[2 * rb + 1] = (G)(v11 - v10);
     }
     K.set(a, d);
+}
+
+// FP32 values and blend: the same differences, two per paired instruction,
+// written straight into the pairs (x, x + 4) of Corners<float>: row rb and
+// row rb + 2 of the same v_t corner.
+template <>
+__device__ __forceinline__ void load_rows<float, float>(const float* __restrict__ V, const int base[4], int n_m,
+                                                        float vj, Corners<float>& K, int up)
+{
+    float v00[4], v01[4], v10[4], v11[4];
+#pragma unroll
+    for (int rb = 0; rb < 4; ++rb) {
+        const float* p = V + base[rb];
+        v00[rb] = __ldg(p);
+        v01[rb] = __ldg(p + up);
+        v10[rb] = __ldg(p + n_m);
+        v11[rb] = __ldg(p + n_m + up);
+    }
+    const unsigned long long jj = pack2(vj, vj);
+#pragma unroll
+    for (int rb = 0; rb < 2; ++rb) {
+        const unsigned long long lo0 = pack2(v00[rb], v00[rb + 2]), lo1 = pack2(v10[rb], v10[rb + 2]);
+        K.q0[2 * rb] = sub2(lo0, jj);
+        K.qd[2 * rb] = sub2(pack2(v01[rb], v01[rb + 2]), lo0);
+        K.q0[2 * rb + 1] = sub2(lo1, jj);
+        K.qd[2 * rb + 1] = sub2(pack2(v11[rb], v11[rb + 2]), lo1);
+    }
 }
 
 // Type in which D = I[V] - V_j is blended and compared: FP64 when the values
@@ -621,10 +682,11 @@ struct CachedEval {
 #pragma unroll
             for (int d = 0; d < 3; ++d) cc[d] = cl[d];
             if (DYN == kDynPolar) cm = cl[3];
+            else K.fold_m((R)tm);   // every foot of this state has the same mass fraction
         }
         if (cout) return pen;
         const R tr[4] = {(R)t[0], (R)t[1], (R)t[2], (R)t[3]};
-        const R D = K.blend(tr);
+        const R D = DYN == kDynPolar ? K.blend(tr) : K.blend_m_folded(tr);
         if constexpr (DIAG) {
             // the node's own coefficient solved (grid node, l = 1): return the
             // difference D~ with dt + beta (vj + D~) = vj + r / (1 - beta w),
