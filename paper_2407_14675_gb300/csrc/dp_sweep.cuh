@@ -177,6 +177,23 @@ __device__ __forceinline__ float incr_recompute(const Geo<float>& g, const float
     return K.blend(t);
 }
 
+// The rare nodes whose foot was not stored (kind kFootRecompute) evaluate
+// out of line, so that the registers of the one-step map do not count against
+// the gather loop of the evaluation sweeps: (new value, node's own weight).
+template <bool REDUCED, int DYN, bool DIAG>
+__device__ __noinline__ float2 feet_recompute(const Geo<float>& g, const float* __restrict__ Vin, int j, int c,
+                                              float vj)
+{
+    NodeEval<float, float, REDUCED, DYN> ev;
+    decode_node(g, j, ev.i);
+    setup_node<float, float, DYN>(ev, g, Vin, vj);
+    float ws = 0.0f;
+    float D;
+    if constexpr (DIAG) D = ev.at_code_w(c, ws);
+    else D = ev.at_code(c);
+    return make_float2(bellman_value<float, float>(g, vj, D), ws);
+}
+
 // The diagonal-solved step of the evaluation: V_j + (T_f(V)_j - V_j) / (1 - beta w_jj).
 // The factor only sets the step length (the fixed point is where the change
 // T_f(V)_j - V_j vanishes), so FP32 uses the fast division.
@@ -287,11 +304,9 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                 } else if (kind == kFootOut) {
                     vnew = bellman_value<G, S>(g, vj, (G)((S)g.M64 - vj));
                 } else if (kind == kFootRecompute) {
-                    NodeEval<G, S, REDUCED, DYN> ev;
-                    decode_node(g, j, ev.i);
-                    setup_node<G, S, DYN>(ev, g, Vin, vj);
-                    if constexpr (kDiag) vnew = bellman_value<G, S>(g, vj, ev.at_code_w(code[j], ws));
-                    else vnew = bellman_value<G, S>(g, vj, ev.at_code(code[j]));
+                    const float2 r = feet_recompute<REDUCED, DYN, kDiag>(g, Vin, j, code[j], vj);
+                    vnew = r.x;
+                    ws = r.y;
                 }
                 if constexpr (kDiag) {
                     if (kind != kFootTarget) vnew = diag_step(g, vj, vnew, ws);
@@ -503,14 +518,16 @@ __device__ __forceinline__ void block_fold(S resid, bool bad, unsigned long long
 }
 
 // Frozen-feet sweeps are bound by gather latency: more resident warps keep
-// more gathers in flight, so they are compiled for 6 blocks per SM (40
-// registers, no spills; 8 blocks would spill).
+// more gathers in flight.  The plain evaluation fits 32 registers (8 blocks
+// per SM); the diagonal-solved and increment forms need 40 (6 blocks), and
+// spill at 32.
 template <int MODE>
 constexpr int min_blocks()
 {
-    return (MODE == kEvalFeet || MODE == kIncr || MODE == kEvalFeetDiag || MODE == kIncrDiag) ? 6
-           : (MODE == kEvalFeet64 || MODE == kEvalFeet64Diag)                               ? 4
-                                                                                             : 1;
+    return MODE == kEvalFeet                                                       ? 8
+           : (MODE == kIncr || MODE == kEvalFeetDiag || MODE == kIncrDiag)          ? 6
+           : (MODE == kEvalFeet64 || MODE == kEvalFeet64Diag)                      ? 4
+                                                                                   : 1;
 }
 
 template <typename G, typename S, int MODE, bool REDUCED, int DYN>
