@@ -640,6 +640,15 @@ struct CachedEval {
     int cm;           // mass cell and fraction of every foot of this state
     G tm;
     bool outm;
+    // Orbit dynamics: the Heun displacement in cells as a polynomial in
+    // (s, c) = (sin alpha, cos alpha), expanded once per state.  With the
+    // predictor v_r2 = R0 + R1 s, v_t2 = P0 + P1 c (R1 = P1 = dt a/m):
+    //   u_r  = a0 + b0 s
+    //   u_vr = a1 + b1 s + c (g1 + d1 c)      (v_t2^2 / r2 term)
+    //   u_vt = a2 + b2 s + c (g2 + e2 s)      (v_r2 v_t2 / r2 term)
+    // Seven FMAs per angle instead of the two-stage step, and the terms
+    // that do not depend on the angle are rounded once for all angles.
+    G pa0, pb0, pa1, pb1, pg1, pd1, pa2, pb2, pg2, pe2;
 
     __device__ __forceinline__ void reset()
     {
@@ -647,6 +656,44 @@ struct CachedEval {
         pen = (R)((S)g->M64 - vj);
         if (DYN != kDynPolar) outm = foot_dim(g->n[3], i[3], OFF ? sp.um + u0[3] : sp.um, cm, tm);
         else outm = false;
+        if constexpr (DYN == kDynOrbit) {
+            const G dt = sp.dt;
+            const G R0 = nd.vr + dt * nd.d1vr, P0 = nd.vt + dt * nd.d1vt, R1 = dt * nd.am, P1 = R1;
+            const G h0 = sp.hdt * g->ih[0], h1 = sp.hdt * g->ih[1], h2 = sp.hdt * g->ih[2];
+            const G amm = nd.am + nd.am2;
+            pa0 = h0 * (nd.vr + R0);
+            pb0 = h0 * R1;
+            pa1 = h1 * (nd.d1vr + (P0 * P0 * nd.ir2 - nd.muir2sq));
+            pb1 = h1 * amm;
+            pg1 = h1 * ((G)2 * P0 * P1 * nd.ir2);
+            pd1 = h1 * (P1 * P1 * nd.ir2);
+            pa2 = h2 * (nd.d1vt - R0 * P0 * nd.ir2);
+            pb2 = -h2 * (R1 * P0 * nd.ir2);
+            pg2 = h2 * (amm - R0 * P1 * nd.ir2);
+            pe2 = -h2 * (R1 * P1 * nd.ir2);
+            if (OFF) {
+                pa0 += u0[0];
+                pa1 += u0[1];
+                pa2 += u0[2];
+            }
+        }
+    }
+
+    // displacement of the first three coordinates (u0 included when OFF)
+    __device__ __forceinline__ void displacement(G s, G c, G u[4]) const
+    {
+        if constexpr (DYN == kDynOrbit) {
+            u[0] = pa0 + pb0 * s;
+            u[1] = (pa1 + pb1 * s) + c * (pg1 + pd1 * c);
+            u[2] = (pa2 + pb2 * s) + c * (pg2 + pe2 * s);
+            u[3] = sp.um;
+        } else {
+            heun_cells<G, DYN>(*g, sp, nd, s, c, u);
+            if (OFF) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) u[d] += u0[d];
+            }
+        }
     }
 
     __device__ __forceinline__ R at_code(int code)
@@ -660,11 +707,7 @@ struct CachedEval {
     {
         G u[4], t[4];
         int cl[4];
-        heun_cells<G, DYN>(*g, sp, nd, s, c, u);
-        if (OFF) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) u[d] += u0[d];
-        }
+        displacement(s, c, u);
         bool out = outm;
 #pragma unroll
         for (int d = 0; d < 3; ++d) out = foot_dim(g->n[d], i[d], u[d], cl[d], t[d]) || out;
@@ -724,15 +767,19 @@ struct CachedEval {
         return w;
     }
 
-    // Frozen-foot word of this node for a code (FP32 geometry only).
+    // Frozen-foot word of this node for a code (FP32 geometry only; after
+    // reset(), from the same displacement as the search).
     __device__ __forceinline__ FootWord foot_of(int code) const
     {
         G s, c, u[4], t[4];
         int cl[4], base[4];
         code_sincos(*g, code, s, c);
-        heun_cells<G, DYN>(*g, sp, nd, s, c, u);
+        displacement(s, c, u);
+        if (!OFF) {
 #pragma unroll
-        for (int d = 0; d < 4; ++d) u[d] += u0[d];
+            for (int d = 0; d < 3; ++d) u[d] += u0[d];
+        }
+        u[3] += u0[3];
         if (foot_cell(*g, i, u, cl, t)) return foot_word_kind(kFootOut);
         if (REDUCED && cell_rows<G, REDUCED>(*g, cl, base)) return foot_word_kind(kFootOut);
         return encode_foot(i, cl, t, g->foot_dm, g->foot_tm);
