@@ -143,6 +143,16 @@ struct StepP {
 };
 
 // Control-independent part of the Heun step at a state.
+//
+// Orbit dynamics: with the control held over the step, the predictor is
+// v_r2 = R0 + R1 s, v_t2 = P0 + P1 c (s, c = sin, cos alpha; R1 = P1 = dt a/m),
+// and r2, m2 do not depend on alpha.  So the Heun displacement in cells is a
+// polynomial in (s, c), expanded once per state:
+//   u_r  = a0 + b0 s
+//   u_vr = a1 + b1 s + c (g1 + d1 c)      (from the v_t2^2 / r2 term)
+//   u_vt = a2 + b2 s + c (g2 + e2 s)      (from the v_r2 v_t2 / r2 term)
+// Seven FMAs per control instead of the two-stage step; the terms that do
+// not depend on alpha are rounded once for all controls of the state.
 template <typename G>
 struct NodeDyn {
     G vr, vt;
@@ -150,6 +160,7 @@ struct NodeDyn {
     G d1vr, d1vt;    // drift of v_r, v_t at x
     G ir2, muir2sq;  // 1/r and mu/r^2 at the predictor (r' = v_r does not depend on alpha)
     G ir;            // 1/r at x (polar: the angle rate v_t / r)
+    G a0, b0, a1, b1, g1, d1, a2, b2, g2, e2;   // orbit: the expanded displacement
 };
 
 template <typename G, int DYN>
@@ -170,6 +181,19 @@ __device__ __forceinline__ NodeDyn<G> node_dyn(const Geo<G>& g, const StepP<G>& 
             G m2 = x[3] + sp.dt * g.mdot;
             n.am = g.accel * grcp(x[3]);
             n.am2 = g.accel * grcp(m2);
+            const G R0 = n.vr + sp.dt * n.d1vr, P0 = n.vt + sp.dt * n.d1vt, R1 = sp.dt * n.am, P1 = R1;
+            const G h0 = sp.hdt * g.ih[0], h1 = sp.hdt * g.ih[1], h2 = sp.hdt * g.ih[2];
+            const G amm = n.am + n.am2;
+            n.a0 = h0 * (n.vr + R0);
+            n.b0 = h0 * R1;
+            n.a1 = h1 * (n.d1vr + (P0 * P0 * n.ir2 - n.muir2sq));
+            n.b1 = h1 * amm;
+            n.g1 = h1 * ((G)2 * P0 * P1 * n.ir2);
+            n.d1 = h1 * (P1 * P1 * n.ir2);
+            n.a2 = h2 * (n.d1vt - R0 * P0 * n.ir2);
+            n.b2 = -h2 * (R1 * P0 * n.ir2);
+            n.g2 = h2 * (amm - R0 * P1 * n.ir2);
+            n.e2 = -h2 * (R1 * P1 * n.ir2);
         } else {
             n.am = g.accel;   // no mass: the thrust acceleration is fixed
             n.am2 = g.accel;
@@ -184,7 +208,12 @@ template <typename G, int DYN>
 __device__ __forceinline__ void heun_cells(const Geo<G>& g, const StepP<G>& sp, const NodeDyn<G>& n,
                                            G s, G c, G u[4])
 {
-    if (DYN == kDynOrbit || DYN == kDynPolar) {
+    if (DYN == kDynOrbit) {
+        u[0] = n.a0 + n.b0 * s;
+        u[1] = (n.a1 + n.b1 * s) + c * (n.g1 + n.d1 * c);
+        u[2] = (n.a2 + n.b2 * s) + c * (n.g2 + n.e2 * s);
+        u[3] = sp.um;
+    } else if (DYN == kDynPolar) {
         G k1vr = n.d1vr + n.am * s;
         G k1vt = n.d1vt + n.am * c;
         G vr2 = n.vr + sp.dt * k1vr;
@@ -194,8 +223,7 @@ __device__ __forceinline__ void heun_cells(const Geo<G>& g, const StepP<G>& sp, 
         u[0] = sp.hdt * (n.vr + vr2) * g.ih[0];
         u[1] = sp.hdt * (k1vr + k2vr) * g.ih[1];
         u[2] = sp.hdt * (k1vt + k2vt) * g.ih[2];
-        if (DYN == kDynOrbit) u[3] = sp.um;
-        else u[3] = sp.hdt * (n.vt * n.ir + vt2 * n.ir2) * g.ih[3];   // angle: theta' = v_t / r
+        u[3] = sp.hdt * (n.vt * n.ir + vt2 * n.ir2) * g.ih[3];   // angle: theta' = v_t / r
     } else {
         // test dynamics: unit speed in the (x0, x1) plane, tiny components zeroed
         G cc = fabs(c) < (G)1e-12 ? (G)0 : c;
@@ -640,15 +668,6 @@ struct CachedEval {
     int cm;           // mass cell and fraction of every foot of this state
     G tm;
     bool outm;
-    // Orbit dynamics: the Heun displacement in cells as a polynomial in
-    // (s, c) = (sin alpha, cos alpha), expanded once per state.  With the
-    // predictor v_r2 = R0 + R1 s, v_t2 = P0 + P1 c (R1 = P1 = dt a/m):
-    //   u_r  = a0 + b0 s
-    //   u_vr = a1 + b1 s + c (g1 + d1 c)      (v_t2^2 / r2 term)
-    //   u_vt = a2 + b2 s + c (g2 + e2 s)      (v_r2 v_t2 / r2 term)
-    // Seven FMAs per angle instead of the two-stage step, and the terms
-    // that do not depend on the angle are rounded once for all angles.
-    G pa0, pb0, pa1, pb1, pg1, pd1, pa2, pb2, pg2, pe2;
 
     __device__ __forceinline__ void reset()
     {
@@ -656,44 +675,6 @@ struct CachedEval {
         pen = (R)((S)g->M64 - vj);
         if (DYN != kDynPolar) outm = foot_dim(g->n[3], i[3], OFF ? sp.um + u0[3] : sp.um, cm, tm);
         else outm = false;
-        if constexpr (DYN == kDynOrbit) {
-            const G dt = sp.dt;
-            const G R0 = nd.vr + dt * nd.d1vr, P0 = nd.vt + dt * nd.d1vt, R1 = dt * nd.am, P1 = R1;
-            const G h0 = sp.hdt * g->ih[0], h1 = sp.hdt * g->ih[1], h2 = sp.hdt * g->ih[2];
-            const G amm = nd.am + nd.am2;
-            pa0 = h0 * (nd.vr + R0);
-            pb0 = h0 * R1;
-            pa1 = h1 * (nd.d1vr + (P0 * P0 * nd.ir2 - nd.muir2sq));
-            pb1 = h1 * amm;
-            pg1 = h1 * ((G)2 * P0 * P1 * nd.ir2);
-            pd1 = h1 * (P1 * P1 * nd.ir2);
-            pa2 = h2 * (nd.d1vt - R0 * P0 * nd.ir2);
-            pb2 = -h2 * (R1 * P0 * nd.ir2);
-            pg2 = h2 * (amm - R0 * P1 * nd.ir2);
-            pe2 = -h2 * (R1 * P1 * nd.ir2);
-            if (OFF) {
-                pa0 += u0[0];
-                pa1 += u0[1];
-                pa2 += u0[2];
-            }
-        }
-    }
-
-    // displacement of the first three coordinates (u0 included when OFF)
-    __device__ __forceinline__ void displacement(G s, G c, G u[4]) const
-    {
-        if constexpr (DYN == kDynOrbit) {
-            u[0] = pa0 + pb0 * s;
-            u[1] = (pa1 + pb1 * s) + c * (pg1 + pd1 * c);
-            u[2] = (pa2 + pb2 * s) + c * (pg2 + pe2 * s);
-            u[3] = sp.um;
-        } else {
-            heun_cells<G, DYN>(*g, sp, nd, s, c, u);
-            if (OFF) {
-#pragma unroll
-                for (int d = 0; d < 3; ++d) u[d] += u0[d];
-            }
-        }
     }
 
     __device__ __forceinline__ R at_code(int code)
@@ -707,7 +688,11 @@ struct CachedEval {
     {
         G u[4], t[4];
         int cl[4];
-        displacement(s, c, u);
+        heun_cells<G, DYN>(*g, sp, nd, s, c, u);
+        if (OFF) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) u[d] += u0[d];
+        }
         bool out = outm;
 #pragma unroll
         for (int d = 0; d < 3; ++d) out = foot_dim(g->n[d], i[d], u[d], cl[d], t[d]) || out;
@@ -767,19 +752,15 @@ struct CachedEval {
         return w;
     }
 
-    // Frozen-foot word of this node for a code (FP32 geometry only; after
-    // reset(), from the same displacement as the search).
+    // Frozen-foot word of this node for a code (FP32 geometry only).
     __device__ __forceinline__ FootWord foot_of(int code) const
     {
         G s, c, u[4], t[4];
         int cl[4], base[4];
         code_sincos(*g, code, s, c);
-        displacement(s, c, u);
-        if (!OFF) {
+        heun_cells<G, DYN>(*g, sp, nd, s, c, u);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) u[d] += u0[d];
-        }
-        u[3] += u0[3];
+        for (int d = 0; d < 4; ++d) u[d] += u0[d];
         if (foot_cell(*g, i, u, cl, t)) return foot_word_kind(kFootOut);
         if (REDUCED && cell_rows<G, REDUCED>(*g, cl, base)) return foot_word_kind(kFootOut);
         return encode_foot(i, cl, t, g->foot_dm, g->foot_tm);

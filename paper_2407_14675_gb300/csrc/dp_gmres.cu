@@ -433,7 +433,6 @@ feet_kernel(const __grid_constant__ Geo<float> g, const uint16_t* __restrict__ c
             w = foot_word_kind(kFootTarget);
         } else {
             setup_node<float, float, DYN>(ev, g, (const float*)nullptr, 0.0f);
-            ev.reset();
             w = ev.foot_of(code[j]);
         }
         feet_lo[j] = w.lo;
