@@ -97,6 +97,15 @@ template <> __device__ __forceinline__ double ginf<double>() { return CUDART_INF
 __device__ __forceinline__ float grcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double grcp(double x) { return __drcp_rn(x); }
 
+// Explicitly rounded operations: expressions written with them compile to
+// the same instructions in every kernel (no context-dependent contraction).
+__device__ __forceinline__ float xmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float xadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double xadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float xfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double xfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Code of the k-th tabulated angle 2 pi k / K on the lattice (round half up).
 __device__ __forceinline__ int table_code(int K, int k) { return (k * kCodes + K / 2) / K; }
 
@@ -156,11 +165,13 @@ struct StepP {
 template <typename G>
 struct NodeDyn {
     G vr, vt;
-    G am, am2;       // a/m at x and at the predictor (m' does not depend on alpha)
+    // polar: the two-stage step's parts
+    G am, am2;       // a/m at x and at the predictor
     G d1vr, d1vt;    // drift of v_r, v_t at x
     G ir2, muir2sq;  // 1/r and mu/r^2 at the predictor (r' = v_r does not depend on alpha)
-    G ir;            // 1/r at x (polar: the angle rate v_t / r)
-    G a0, b0, a1, b1, g1, d1, a2, b2, g2, e2;   // orbit: the expanded displacement
+    G ir;            // 1/r at x (the angle rate v_t / r)
+    // orbit: the expanded displacement
+    G a0, b0, a1, b1, g1, d1, a2, b2, g2, e2;
 };
 
 template <typename G, int DYN>
@@ -169,7 +180,31 @@ __device__ __forceinline__ NodeDyn<G> node_dyn(const Geo<G>& g, const StepP<G>& 
     NodeDyn<G> n;
     n.vr = x[1];
     n.vt = x[2];
-    if (DYN == kDynOrbit || DYN == kDynPolar) {
+    if (DYN == kDynOrbit) {
+        // every operation rounded explicitly: the searches, the stored feet and
+        // the recomputing sweeps run this in different kernels and must agree
+        const G ir = grcp(x[0]);
+        const G d1vr = xfma(xmul(n.vt, n.vt), ir, -xmul(g.mu, xmul(ir, ir)));
+        const G d1vt = -xmul(xmul(n.vr, n.vt), ir);
+        const G ir2 = grcp(xfma(sp.dt, n.vr, x[0]));
+        const G muir2sq = xmul(g.mu, xmul(ir2, ir2));
+        const G am = xmul(g.accel, grcp(x[3]));
+        const G am2 = xmul(g.accel, grcp(xfma(sp.dt, g.mdot, x[3])));
+        const G R0 = xfma(sp.dt, d1vr, n.vr), P0 = xfma(sp.dt, d1vt, n.vt), R1 = xmul(sp.dt, am), P1 = R1;
+        const G h0 = xmul(sp.hdt, g.ih[0]), h1 = xmul(sp.hdt, g.ih[1]), h2 = xmul(sp.hdt, g.ih[2]);
+        const G amm = xadd(am, am2);
+        const G q = xmul(P0, ir2), p1r = xmul(P1, ir2);   // P0 / r2, P1 / r2
+        n.a0 = xmul(h0, xadd(n.vr, R0));
+        n.b0 = xmul(h0, R1);
+        n.a1 = xmul(h1, xadd(d1vr, xfma(P0, q, -muir2sq)));
+        n.b1 = xmul(h1, amm);
+        n.g1 = xmul(h1, xmul(xadd(P1, P1), q));
+        n.d1 = xmul(h1, xmul(P1, p1r));
+        n.a2 = xmul(h2, xfma(-R0, q, d1vt));
+        n.b2 = -xmul(h2, xmul(R1, q));
+        n.g2 = xmul(h2, xfma(-R0, p1r, amm));
+        n.e2 = -xmul(h2, xmul(R1, p1r));
+    } else if (DYN == kDynPolar) {
         G ir = grcp(x[0]);
         n.ir = ir;
         n.d1vr = n.vt * n.vt * ir - g.mu * ir * ir;
@@ -177,27 +212,8 @@ __device__ __forceinline__ NodeDyn<G> node_dyn(const Geo<G>& g, const StepP<G>& 
         G r2 = x[0] + sp.dt * n.vr;
         n.ir2 = grcp(r2);
         n.muir2sq = g.mu * n.ir2 * n.ir2;
-        if (DYN == kDynOrbit) {
-            G m2 = x[3] + sp.dt * g.mdot;
-            n.am = g.accel * grcp(x[3]);
-            n.am2 = g.accel * grcp(m2);
-            const G R0 = n.vr + sp.dt * n.d1vr, P0 = n.vt + sp.dt * n.d1vt, R1 = sp.dt * n.am, P1 = R1;
-            const G h0 = sp.hdt * g.ih[0], h1 = sp.hdt * g.ih[1], h2 = sp.hdt * g.ih[2];
-            const G amm = n.am + n.am2;
-            n.a0 = h0 * (n.vr + R0);
-            n.b0 = h0 * R1;
-            n.a1 = h1 * (n.d1vr + (P0 * P0 * n.ir2 - n.muir2sq));
-            n.b1 = h1 * amm;
-            n.g1 = h1 * ((G)2 * P0 * P1 * n.ir2);
-            n.d1 = h1 * (P1 * P1 * n.ir2);
-            n.a2 = h2 * (n.d1vt - R0 * P0 * n.ir2);
-            n.b2 = -h2 * (R1 * P0 * n.ir2);
-            n.g2 = h2 * (amm - R0 * P1 * n.ir2);
-            n.e2 = -h2 * (R1 * P1 * n.ir2);
-        } else {
-            n.am = g.accel;   // no mass: the thrust acceleration is fixed
-            n.am2 = g.accel;
-        }
+        n.am = g.accel;   // no mass: the thrust acceleration is fixed
+        n.am2 = g.accel;
     }
     return n;
 }
@@ -209,9 +225,9 @@ __device__ __forceinline__ void heun_cells(const Geo<G>& g, const StepP<G>& sp, 
                                            G s, G c, G u[4])
 {
     if (DYN == kDynOrbit) {
-        u[0] = n.a0 + n.b0 * s;
-        u[1] = (n.a1 + n.b1 * s) + c * (n.g1 + n.d1 * c);
-        u[2] = (n.a2 + n.b2 * s) + c * (n.g2 + n.e2 * s);
+        u[0] = xfma(n.b0, s, n.a0);
+        u[1] = xfma(c, xfma(n.d1, c, n.g1), xfma(n.b1, s, n.a1));
+        u[2] = xfma(c, xfma(n.e2, s, n.g2), xfma(n.b2, s, n.a2));
         u[3] = sp.um;
     } else if (DYN == kDynPolar) {
         G k1vr = n.d1vr + n.am * s;
