@@ -678,6 +678,7 @@ struct CachedEval {
     S vj;
     NodeDyn<G> nd;
     int cc[3];        // cached cell in (r, v_r, v_t); cc[0] = -1: none
+    G co[3];          // its offset from the node, cc - i
     bool cout;        // the cached cell has a corner outside the node set
     Corners<R> K;
     R pen;            // M - vj
@@ -691,6 +692,13 @@ struct CachedEval {
         pen = (R)((S)g->M64 - vj);
         if (DYN != kDynPolar) outm = foot_dim(g->n[3], i[3], OFF ? sp.um + u0[3] : sp.um, cm, tm);
         else outm = false;
+    }
+
+    // 0 <= t < 1 (false for NaN and -0)
+    static __device__ __forceinline__ bool unit_fraction(float t) { return __float_as_uint(t) < 0x3f800000u; }
+    static __device__ __forceinline__ bool unit_fraction(double t)
+    {
+        return (unsigned long long)__double_as_longlong(t) < 0x3ff0000000000000ull;
     }
 
     __device__ __forceinline__ R at_code(int code)
@@ -709,6 +717,26 @@ struct CachedEval {
 #pragma unroll
             for (int d = 0; d < 3; ++d) u[d] += u0[d];
         }
+        if constexpr (DYN != kDynPolar) {
+            // the usual case: the foot lies in the cached cell, whose fractions
+            // are u - (cell - node) in [0, 1), the same numbers foot_dim gives
+            if (cc[0] >= 0) {
+                bool in = true;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    t[d] = u[d] - co[d];
+                    in = in && unit_fraction(t[d]);
+                }
+                if (in) {
+                    if (cout) return pen;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) cl[d] = cc[d];
+                    cl[3] = cm;
+                    t[3] = tm;
+                    return blend_at(cl, t);
+                }
+            }
+        }
         bool out = outm;
 #pragma unroll
         for (int d = 0; d < 3; ++d) out = foot_dim(g->n[d], i[d], u[d], cl[d], t[d]) || out;
@@ -724,11 +752,20 @@ struct CachedEval {
         if (cl[0] != cc[0] || cl[1] != cc[1] || cl[2] != cc[2] || (DYN == kDynPolar && cl[3] != cm)) {
             cout = load_corners<R, G, S, REDUCED, DYN == kDynPolar>(*g, V, cl, vj, K);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) cc[d] = cl[d];
+            for (int d = 0; d < 3; ++d) {
+                cc[d] = cl[d];
+                co[d] = (G)(cl[d] - i[d]);
+            }
             if (DYN == kDynPolar) cm = cl[3];
             else K.fold_m((R)tm);   // every foot of this state has the same mass fraction
         }
         if (cout) return pen;
+        return blend_at(cl, t);
+    }
+
+    // D at the cached corners for cell cl, fractions t
+    __device__ __forceinline__ R blend_at(const int cl[4], const G t[4]) const
+    {
         const R tr[4] = {(R)t[0], (R)t[1], (R)t[2], (R)t[3]};
         const R D = DYN == kDynPolar ? K.blend(tr) : K.blend_m_folded(tr);
         if constexpr (DIAG) {
