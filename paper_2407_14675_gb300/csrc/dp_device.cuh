@@ -614,6 +614,7 @@ __device__ __forceinline__ typename BlendType<G, S>::type interp_delta_w(const G
 template <typename G, typename S, bool REDUCED, int DYN>
 struct NodeEval {
     typedef typename BlendType<G, S>::type R;
+    static constexpr bool kMayOff = DYN == kDynPolar;   // only these dynamics have the thrust-off code
     const Geo<G>* g;
     const S* __restrict__ V;
     StepP<G> sp;
@@ -670,6 +671,7 @@ template <typename G, typename S, bool REDUCED, int DYN, typename BLEND = typena
           bool OFF = true, bool DIAG = false>
 struct CachedEval {
     typedef BLEND R;
+    static constexpr bool kMayOff = DYN == kDynPolar;   // only these dynamics have the thrust-off code
     const Geo<G>* g;
     const S* __restrict__ V;
     StepP<G> sp;
@@ -924,8 +926,8 @@ __device__ __forceinline__ int fibonacci_refine(E& ev, const Table<G>& T, int n0
     R qb = Dk;
     int a = lo_off;
     int x1 = a + kFib[n - 2], x2 = a + kFib[n - 1];
-    R f1 = (x1 >= hi_off || (T.off && wrap_code(ck + x1) == kCodeOff)) ? ginf<R>() : ev.at_code(ck + x1);
-    R f2 = (x2 >= hi_off || (T.off && wrap_code(ck + x2) == kCodeOff)) ? ginf<R>() : ev.at_code(ck + x2);
+    R f1 = (x1 >= hi_off || (E::kMayOff && T.off && wrap_code(ck + x1) == kCodeOff)) ? ginf<R>() : ev.at_code(ck + x1);
+    R f2 = (x2 >= hi_off || (E::kMayOff && T.off && wrap_code(ck + x2) == kCodeOff)) ? ginf<R>() : ev.at_code(ck + x2);
     if (f1 < qb) { qb = f1; best = ck + x1; }
     if (f2 < qb) { qb = f2; best = ck + x2; }
     for (int kk = n; kk > 4 && kFib[kk] > fib_stop; --kk) {
@@ -943,7 +945,7 @@ __device__ __forceinline__ int fibonacci_refine(E& ev, const Table<G>& T, int n0
             x2 = a + kFib[kk - 2];
             xn = x2;
         }
-        const bool skip = xn >= hi_off || (T.off && wrap_code(ck + xn) == kCodeOff);
+        const bool skip = xn >= hi_off || (E::kMayOff && T.off && wrap_code(ck + xn) == kCodeOff);
         const R fn = skip ? ginf<R>() : ev.at_code(ck + xn);
         if (left) f1 = fn;
         else f2 = fn;
