@@ -437,26 +437,29 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                         // new one is strictly better in FP64 (policy iteration's
                         // rule for termination): otherwise the two searches, which
                         // can stop in different local minima, undo each other
+                        // The FP64 blends interpolate V itself (reference value 0,
+                        // so no corner differences): FP64 keeps its 1e-16 relative
+                        // error on V, and the FP64 pipe does half the work.
                         NodeEval<G, S, REDUCED, DYN> e64;
                         e64.g = ev.g;
                         e64.V = ev.V;
                         e64.sp = ev.sp;
-                        e64.vj = ev.vj;
+                        e64.vj = (S)0;
                         e64.nd = ev.nd;
 #pragma unroll
                         for (int d = 0; d < 4; ++d) {
                             e64.i[d] = ev.i[d];
                             e64.u0[d] = ev.u0[d];
                         }
-                        double d_new = e64.at_code(c);
+                        double q_new = e64.at_code(c);   // I[V] at the foot, M outside
                         if (c != c_old) {
-                            const double d_old = e64.at_code(c_old);
-                            if (!(d_new < d_old)) {
+                            const double q_old = e64.at_code(c_old);
+                            if (!(q_new < q_old)) {
                                 c = c_old;
-                                d_new = d_old;
+                                q_new = q_old;
                             }
                         }
-                        vnew64 = g.dt64 + g.beta64 * ((double)vj + d_new);
+                        vnew64 = g.dt64 + g.beta64 * q_new;
                     }
                     if (!kIsVI) code[j] = (uint16_t)c;
                     if constexpr (kGeo32 && kImprove) {
