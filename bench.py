@@ -32,9 +32,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Bellman node-updates/s; time to ‖ΔV‖∞<1e-6, plain vs NN-warm-started"
 # DRAM bytes (read + written) of one launch of the 61^4 frozen-feet evaluation
-# sweep, from one ncu capture of the current kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum); to be retaken (or set to None) whenever it changes
-EVAL_TRAFFIC_61X4 = 221.585408e6 + 21.070848e6
+# sweep: mean of two launches of one ncu capture of the current kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum); to be retaken (or set to
+# None) whenever it changes
+EVAL_TRAFFIC_61X4 = (221.699328e6 + 23.575040e6 + 221.704448e6 + 20.552960e6) / 2
 UNIT = "node-updates/s"
 L2_BYTES = 129 * 2 ** 20
 
@@ -712,7 +713,7 @@ def run_ours(args, world, rank, local):
             "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
             "traffic": EVAL_TRAFFIC_61X4, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum "
-                                                              "of one launch of this kernel (sweep-kernel profile)",
+                                                              "of this kernel, mean of two launches (sweep-kernel profile)",
             "algorithmic_bytes_per_launch": eval_bytes, "avg_launch_ms": eval_ms,
             "share_of_step": ms_eval / max(ms, 1e-9)}
     imp_ms = ms_imp / max(n_imp, 1)
