@@ -299,8 +299,8 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
             if constexpr (MODE == kEvalFeet || MODE == kEvalFeetDiag) {
                 float ws = 0.0f;
                 if (kind == kFootInside) {
-                    vnew = bellman_value<G, S>(g, vj, eval_foot<REDUCED>(g, Vin, j, w, vj));
                     if constexpr (kDiag) ws = foot_self_weight(g, w);
+                    vnew = bellman_value<G, S>(g, vj, eval_foot<REDUCED>(g, Vin, j, w, vj));
                 } else if (kind == kFootOut) {
                     vnew = bellman_value<G, S>(g, vj, (G)((S)g.M64 - vj));
                 } else if (kind == kFootRecompute) {
