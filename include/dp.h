@@ -139,7 +139,7 @@ typedef struct dp_solve_opts {
     int32_t polish;        /* FP32 grids: 1 = finish with FP64 values once FP32
                               stalls; 0 = stay FP32                                 */
     double  switch_tol;    /* FP32 -> FP64 switch when the improvement residual is
-                              below this (<= 0: 4 FP32 epsilons of M, automatic);
+                              below this (<= 0: 16 FP32 epsilons of M, automatic);
                               the switch also happens after 3 improvements without
                               a 0.1 % gain over the best FP32 residual when it is
                               below 64 times that tolerance, or after 30 anywhere   */

@@ -848,7 +848,7 @@ int pi_gmres(dp_grid* g, const dp_solve_opts* o, const GmOpts& go, dp_solve_stat
 {
     int rc;
     SwitchRule rule;
-    rule.tol = o->switch_tol > 0 ? o->switch_tol : kSwitchEpsilons * kFp32Epsilon * g->M;
+    rule.tol = o->switch_tol > 0 ? o->switch_tol : 16.0 * 1.1920928955078125e-07 * g->M;
     bool first_full = !o->warm;
     int pending = 0;   // cycles whose tails wait for the next synchronisation
     auto collect = [&]() {
@@ -1259,7 +1259,7 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
     const long long per = 1 + o->n_eval;                 // sweeps per outer iteration
     const long long per_chunk = std::max<long long>(1, kMaxChunk / per / 4);
     SwitchRule rule;
-    rule.tol = o->switch_tol > 0 ? o->switch_tol : kSwitchEpsilons * kFp32Epsilon * g->M;
+    rule.tol = o->switch_tol > 0 ? o->switch_tol : 16.0 * 1.1920928955078125e-07 * g->M;
     long long outer = 0, t = 0;    // outer iterations and sweeps of the current phase
     double res = INFINITY;
     bool conv = false, first_full = !o->warm;

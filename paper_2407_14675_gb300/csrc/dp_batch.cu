@@ -291,7 +291,7 @@ __device__ void ctl_update(BState& s, const BParams& p, double M, int stage)
             s.full_next = !p.walk;
             if (s.phase == kPh32 && p.polish) {
                 // the switch rule of dp_policy_iterate
-                const double sw = p.switch_tol > 0 ? p.switch_tol : kSwitchEpsilons * kFp32Epsilon * M;
+                const double sw = p.switch_tol > 0 ? p.switch_tol : 16.0 * 1.1920928955078125e-07 * M;
                 if (res < s.best * 0.999) {
                     s.best = res;
                     s.stall = 0;

@@ -84,15 +84,6 @@ cudaError_t launch_prolong(const Geo<double>& gs, const void* Vs, int src_fp32, 
                            int periodic, const Geo<double>& gd, void* Vd, int fp32_dst, uint16_t* Cd, double Md,
                            cudaStream_t st);
 
-// Automatic FP32 -> FP64-value switch of policy iteration on FP32 grids: the
-// improvement residual below this many FP32 epsilons of the penalty M (values
-// lie in [0, M], so one epsilon of M is about the FP32 rounding of the largest
-// value).  Four: with the orbit step expanded once per state the angle
-// searches add little rounding noise, and the FP32 phase keeps improving to
-// about 1e-5 on the 61^4 and 121^4 grids (M = 20).
-constexpr double kSwitchEpsilons = 4.0;
-constexpr double kFp32Epsilon = 1.1920928955078125e-07;
-
 // Policy evaluation by restarted GMRES (§3: with the control frozen, Eq. (13)
 // is the sparse linear system (I - beta W_f) V = b).  One cycle starts from
 // the residual r0 = T_f(V) - V of the current value, builds an m-step Arnoldi
