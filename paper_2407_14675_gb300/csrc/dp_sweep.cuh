@@ -210,7 +210,7 @@ __device__ __forceinline__ double diag_step(const Geo<G>& g, double vj, double v
 // Sweeps nodes j0, j0 + stride, ... < end of one grid: the per-node work of
 // every sweep mode.  Folds max |V_out - V_in| into resid and non-finite
 // results into bad.
-template <typename G, typename S, int MODE, bool REDUCED, int DYN>
+template <typename G, typename S, int MODE, bool REDUCED, int DYN, bool PREFETCH = true>
 __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, const S* __restrict__ Vin,
                                             S* __restrict__ Vout, uint16_t* __restrict__ code,
                                             unsigned long long* __restrict__ feet_lo,
@@ -274,13 +274,12 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
         }
     } else if constexpr (MODE == kEvalFeet || MODE == kIncr || MODE == kEvalFeetDiag || MODE == kIncrDiag) {
         constexpr bool kDiag = MODE == kEvalFeetDiag || MODE == kIncrDiag;
-        // frozen feet: gather-bound.  The increment sweeps fetch the next
-        // node's foot and value while this node's corners are in flight; the
-        // evaluation sweeps instead fit 32 registers without that prefetch
-        // and hide the latency with 8 blocks per SM (1 % faster on 61^4).  The
-        // feet are read once per sweep: evict-first loads keep L1 and L2 for
-        // the gathered V.
-        constexpr bool kPrefetch = MODE != kEvalFeetDiag && MODE != kEvalFeet;
+        // frozen feet: gather-bound.  With PREFETCH the next node's foot and
+        // value are fetched while this node's corners are in flight; without
+        // it the loop needs fewer registers (more resident blocks instead).
+        // The feet are read once per sweep: evict-first loads keep L1 and L2
+        // for the gathered V.
+        constexpr bool kPrefetch = PREFETCH;
         const bool first = incr_flags & 1, last = incr_flags & 2;
         int j = j0;
         FootWord w_next{0ull, 0u};
@@ -533,19 +532,29 @@ __device__ __forceinline__ void block_fold(S resid, bool bad, unsigned long long
 }
 
 // Frozen-feet sweeps are bound by gather latency: more resident warps keep
-// more gathers in flight.  The evaluation sweeps fit 32 registers (8 blocks
-// per SM); the increment forms need 40 (6 blocks), and spill at 32.
-template <int MODE>
+// more gathers in flight.  On the full box both evaluation forms fit 32
+// registers without the next-node prefetch (8 blocks per SM; 1 % faster than
+// prefetching at 6).  On the reduced grid the plain evaluation keeps the
+// prefetch at 8 blocks and the diagonal-solved one at 6 (both measured best
+// there); the increment forms prefetch at 6 blocks (they spill at 32
+// registers).
+template <int MODE, bool REDUCED>
+__host__ __device__ constexpr bool eval_prefetch()
+{
+    return !((MODE == kEvalFeet || MODE == kEvalFeetDiag) && !REDUCED);
+}
+
+template <int MODE, bool REDUCED>
 constexpr int min_blocks()
 {
-    return (MODE == kEvalFeet || MODE == kEvalFeetDiag)                           ? 8
-           : (MODE == kIncr || MODE == kIncrDiag)                                  ? 6
-           : (MODE == kEvalFeet64 || MODE == kEvalFeet64Diag)                      ? 4
-                                                                                   : 1;
+    return (MODE == kEvalFeet || (MODE == kEvalFeetDiag && !REDUCED))            ? 8
+           : (MODE == kIncr || MODE == kEvalFeetDiag || MODE == kIncrDiag)        ? 6
+           : (MODE == kEvalFeet64 || MODE == kEvalFeet64Diag)                    ? 4
+                                                                                 : 1;
 }
 
 template <typename G, typename S, int MODE, bool REDUCED, int DYN>
-__global__ void __launch_bounds__(kBlock, min_blocks<MODE>())
+__global__ void __launch_bounds__(kBlock, min_blocks<MODE, REDUCED>())
 sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __restrict__ Vout,
              uint16_t* __restrict__ code, unsigned long long* __restrict__ feet_lo, unsigned* __restrict__ feet_hi,
              float* __restrict__ inc, float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
@@ -576,9 +585,9 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
 
     S resid = (S)0;
     bool bad = false;
-    sweep_nodes<G, S, MODE, REDUCED, DYN>(g, T, Vin, Vout, code, feet_lo, feet_hi, inc, acc, V64, incr_flags,
-                                          blockIdx.x * kBlock + threadIdx.x, g.n_nodes, gridDim.x * kBlock,
-                                          resid, bad, f64);
+    sweep_nodes<G, S, MODE, REDUCED, DYN, eval_prefetch<MODE, REDUCED>()>(
+        g, T, Vin, Vout, code, feet_lo, feet_hi, inc, acc, V64, incr_flags, blockIdx.x * kBlock + threadIdx.x,
+        g.n_nodes, gridDim.x * kBlock, resid, bad, f64);
     block_fold(resid, bad, &ring[sweep & ring_mask], &ctl->nonfinite);
 }
 
