@@ -163,6 +163,10 @@ typedef struct dp_solve_opts {
     int32_t gmres_reorth;  /* 1: classical Gram-Schmidt twice (0: once)            */
     double  gmres_rtol;    /* a cycle ends early once the 2-norm residual estimate
                               falls below gmres_rtol times its start (0: 1e-3)     */
+    int32_t n_eval_fp64;   /* PI on FP32 grids with polish: evaluation sweeps per
+                              improvement once the values are FP64 (>= 0; 0:
+                              automatic, max(n_eval, 80), or 0 when n_eval is 0).
+                              Batches ignore it                                    */
 } dp_solve_opts;
 
 /* Solver statistics (filled on DP_OK and on DP_ENOCONV). */

@@ -221,3 +221,28 @@ def test_solvers_agree_on_the_fp32_band_grid(dp):
         # each is within tol / (1 - beta) of the scheme's fixed point
         assert np.abs(out[name][0] - v0).max() <= 2e-6 / (1 - p.beta), name
     assert out["diag"][1] < out["sweeps"][1]
+
+
+def test_fp64_phase_evaluation_count(dp):
+    # n_eval_fp64 sets the evaluation sweeps per improvement once the values
+    # are FP64; every count reaches the same fixed point
+    p = W.config1(n=9).replace(beta=0.995, dt=0.1)
+    out = {}
+    for ne64 in (0, 7, 120):
+        with dp.Grid(p) as g:
+            rc, st = g.policy_iterate(tol=1e-6, max_sweeps=5000, n_eval=20, polish=1,
+                                      eval_solver=dp.DP_EVAL_DIAG, n_eval_fp64=ne64)
+            assert rc == dp.DP_OK and st.converged and st.sweeps_improve_fp64 > 0, st.asdict()
+            out[ne64] = (g.get_value(), st)
+    for ne64 in (7, 120):
+        st = out[ne64][1]
+        # the device stops the queue at the first converged improvement
+        assert st.sweeps_eval_fp64 <= ne64 * st.sweeps_improve_fp64
+        assert st.sweeps_eval_fp64 >= ne64 * (st.sweeps_improve_fp64 - 1)
+        assert np.abs(out[ne64][0] - out[0][0]).max() <= 2e-6 / (1 - p.beta)
+    st0 = out[0][1]
+    assert st0.sweeps_eval_fp64 >= 80 * (st0.sweeps_improve_fp64 - 1)   # automatic: at least 80
+    with dp.Grid(p) as g:
+        with pytest.raises(dp.DPError) as e:
+            g.policy_iterate(tol=1e-6, max_sweeps=5, n_eval=20, n_eval_fp64=-1)
+        assert e.value.code == dp.DP_EINVAL
