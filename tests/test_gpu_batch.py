@@ -60,7 +60,9 @@ def test_batch_solve_reproduces_single_grid_solves(dp, solver):
     assert tot.node_updates > 0 and tot.launches > 0
     for i, p in enumerate(probs):
         with dp.Grid(p) as g:
-            rc, st = g.policy_iterate(**opts)
+            # a batch evaluates n_eval sweeps per improvement in both precision
+            # phases: the single grid is given the same FP64-phase count
+            rc, st = g.policy_iterate(n_eval_fp64=opts["n_eval"], **opts)
             assert st.converged
             V, C = g.get_value(), g.get_policy()
         s = per[i]
