@@ -236,12 +236,14 @@ def test_fp64_phase_evaluation_count(dp):
             out[ne64] = (g.get_value(), st)
     for ne64 in (7, 120):
         st = out[ne64][1]
-        # the device stops the queue at the first converged improvement
+        # the device stops the queue at the first converged improvement: the
+        # converged walk and the full tabulation that confirms it run no
+        # evaluation sweeps
         assert st.sweeps_eval_fp64 <= ne64 * st.sweeps_improve_fp64
-        assert st.sweeps_eval_fp64 >= ne64 * (st.sweeps_improve_fp64 - 1)
+        assert st.sweeps_eval_fp64 >= ne64 * (st.sweeps_improve_fp64 - 2)
         assert np.abs(out[ne64][0] - out[0][0]).max() <= 2e-6 / (1 - p.beta)
     st0 = out[0][1]
-    assert st0.sweeps_eval_fp64 >= 80 * (st0.sweeps_improve_fp64 - 1)   # automatic: at least 80
+    assert st0.sweeps_eval_fp64 >= 80 * (st0.sweeps_improve_fp64 - 2)   # automatic: at least 80
     with dp.Grid(p) as g:
         with pytest.raises(dp.DPError) as e:
             g.policy_iterate(tol=1e-6, max_sweeps=5, n_eval=20, n_eval_fp64=-1)
