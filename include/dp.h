@@ -165,8 +165,9 @@ typedef struct dp_solve_opts {
                               falls below gmres_rtol times its start (0: 1e-3)     */
     int32_t n_eval_fp64;   /* PI on FP32 grids with polish: evaluation sweeps per
                               improvement once the values are FP64 (>= 0; 0:
-                              automatic, max(n_eval, 80), or 0 when n_eval is 0).
-                              Batches ignore it                                    */
+                              automatic, max(n_eval, 80) for DP_EVAL_DIAG and
+                              max(n_eval, 160) for DP_EVAL_JACOBI, 0 when n_eval
+                              is 0).  Batches ignore it and keep n_eval           */
 } dp_solve_opts;
 
 /* Solver statistics (filled on DP_OK and on DP_ENOCONV). */

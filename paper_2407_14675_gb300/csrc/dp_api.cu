@@ -1239,14 +1239,17 @@ int dp_value_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
 // improvement costs about as much as 30 evaluation sweeps (its blends run on
 // the FP64 pipe), and the FP64 phase starts near the fixed point, where the
 // policy changes little: evaluating each policy further pays.  Measured on
-// the 61^4 and 121^4 band grids (diagonal-solved 40 per improvement, plain
-// 20): 80 or more beat the FP32 phase's count, by 4-10 % and 20-25 %.
-constexpr int kFp64PhaseMinEvals = 80;
+// the 61^4 and 121^4 band grids: at least 80 diagonal-solved iterations
+// (from 40) and at least 160 plain sweeps (from 20), which contract far less
+// per sweep, beat the FP32 phase's counts by 4-10 % and 5-25 %.
+constexpr int kFp64PhaseMinDiag = 80;
+constexpr int kFp64PhaseMinSweeps = 160;
 
 static int fp64_phase_evals(const dp_solve_opts* o)
 {
     if (o->n_eval_fp64 > 0) return o->n_eval_fp64;
-    return o->n_eval > 0 ? std::max(o->n_eval, kFp64PhaseMinEvals) : 0;
+    const int lo = o->eval_solver == DP_EVAL_DIAG ? kFp64PhaseMinDiag : kFp64PhaseMinSweeps;
+    return o->n_eval > 0 ? std::max(o->n_eval, lo) : 0;
 }
 
 int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
