@@ -12,7 +12,7 @@ value and policy go up from pinned host memory and come back every step.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 step (there is no reference implementation of this method to run).
 
-Multi-GPU: the grid does not shard in this build ("replicas only"): every rank
+Multi-GPU: the grid does not shard ("replicas only"): every rank
 solves its own copy, value = all ranks' node updates / the slowest rank.
 """
 from __future__ import annotations

@@ -298,8 +298,8 @@ int dp_simulate_closed_loop(const dp_grid* grid, const double* x0, int32_t n, do
  * tensor-core GEMMs (tcgen05).  Training minimises the mean squared error over
  * the three outputs with Adam (beta1 0.9, beta2 0.999, eps 1e-8) on every node
  * of a solved grid; the trained network then initialises V and the policy of
- * another grid for policy iteration (dp_solve_opts.warm = 1).  The sweeps stay
- * the judge: the warm start only changes where policy iteration starts.
+ * another grid for policy iteration (dp_solve_opts.warm = 1).  The sweeps still
+ * decide the result: the warm start only changes where policy iteration starts.
  *
  * Parameter order of the flat FP32 vector (dp_mlp_param_count() floats):
  * W1 (256 x 4, row = output), b1 (256), W2 (256 x 256), b2, W3 (256 x 256), b3,
