@@ -517,15 +517,16 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
 
 // Block-wide max of resid folded into *slot (FP64 bits) and the non-finite
 // flag into *nonfinite.  Every thread of the block calls it.
-template <typename S>
+template <typename S, int BLOCK = kBlock>
 __device__ __forceinline__ void block_fold(S resid, bool bad, unsigned long long* slot, int* nonfinite)
 {
-    __shared__ S red[kBlock / 32];
+    static_assert(BLOCK % 32 == 0 && BLOCK <= 1024, "block of whole warps, at most 32");
+    __shared__ S red[BLOCK / 32];
     resid = warp_max(resid);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = resid;
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(nonfinite, 1);
     if (threadIdx.x < 32) {
-        S r = threadIdx.x < kBlock / 32 ? red[threadIdx.x] : (S)0;
+        S r = threadIdx.x < BLOCK / 32 ? red[threadIdx.x] : (S)0;
         r = warp_max(r);
         if (threadIdx.x == 0) atomicMax(slot, (unsigned long long)__double_as_longlong((double)r));
     }
@@ -533,28 +534,48 @@ __device__ __forceinline__ void block_fold(S resid, bool bad, unsigned long long
 
 // Frozen-feet sweeps are bound by gather latency: more resident warps keep
 // more gathers in flight.  On the full box both evaluation forms fit 32
-// registers without the next-node prefetch (8 blocks per SM; 1 % faster than
-// prefetching at 6).  On the reduced grid the plain evaluation keeps the
-// prefetch at 8 blocks and the diagonal-solved one at 6 (both measured best
-// there); the increment forms prefetch at 6 blocks (they spill at 32
-// registers).
+// registers without the next-node prefetch (64 warps per SM; 1 % faster than
+// prefetching at 48).  On the reduced grid the evaluation forms keep the
+// prefetch (measured best there); so do the increment forms, at 40
+// registers (they spill at 32).
 template <int MODE, bool REDUCED>
 __host__ __device__ constexpr bool eval_prefetch()
 {
     return !((MODE == kEvalFeet || MODE == kEvalFeetDiag) && !REDUCED);
 }
 
+// Block size of the frozen-feet sweeps.  A grid-stride iteration of a block
+// covers that many consecutive nodes, whose corner lines overlap (a node's
+// v_t neighbours lie 61 nodes on, on the 61^4 grid), so larger blocks take
+// more of their gathers from L1: 1024 threads (2 blocks per SM) for the
+// evaluation sweeps, 768 (2 per SM at 40 registers) for the increment sweeps.
+// Same-box A/B on 61^4 against 256-thread blocks: 78.9 against 83.0 us per
+// evaluation sweep, 88.0 against 90.8 us diagonal-solved.  The diagonal-
+// solved sweep of the reduced grid needs 40 registers and keeps 256 (6 per
+// SM).
+template <int MODE, bool REDUCED>
+__host__ __device__ constexpr bool big_blocks()
+{
+    return MODE == kEvalFeet || (MODE == kEvalFeetDiag && !REDUCED) || MODE == kIncr || MODE == kIncrDiag;
+}
+
+template <int MODE, bool REDUCED>
+__host__ __device__ constexpr int sweep_block()
+{
+    return (MODE == kIncr || MODE == kIncrDiag) ? 768 : big_blocks<MODE, REDUCED>() ? 1024 : kBlock;
+}
+
 template <int MODE, bool REDUCED>
 constexpr int min_blocks()
 {
-    return (MODE == kEvalFeet || (MODE == kEvalFeetDiag && !REDUCED))            ? 8
-           : (MODE == kIncr || MODE == kEvalFeetDiag || MODE == kIncrDiag)        ? 6
-           : (MODE == kEvalFeet64 || MODE == kEvalFeet64Diag)                    ? 4
-                                                                                 : 1;
+    return big_blocks<MODE, REDUCED>()                               ? 2
+           : MODE == kEvalFeetDiag                                    ? 6   // reduced grid, 256 threads
+           : (MODE == kEvalFeet64 || MODE == kEvalFeet64Diag)         ? 4
+                                                                      : 1;
 }
 
 template <typename G, typename S, int MODE, bool REDUCED, int DYN>
-__global__ void __launch_bounds__(kBlock, min_blocks<MODE, REDUCED>())
+__global__ void __launch_bounds__(sweep_block<MODE, REDUCED>(), min_blocks<MODE, REDUCED>())
 sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __restrict__ Vout,
              uint16_t* __restrict__ code, unsigned long long* __restrict__ feet_lo, unsigned* __restrict__ feet_hi,
              float* __restrict__ inc, float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
@@ -585,27 +606,29 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
 
     S resid = (S)0;
     bool bad = false;
+    constexpr int B = sweep_block<MODE, REDUCED>();
+    const int j0 = blockIdx.x * B + threadIdx.x, end = g.n_nodes, stride = gridDim.x * B;
     sweep_nodes<G, S, MODE, REDUCED, DYN, eval_prefetch<MODE, REDUCED>()>(
-        g, T, Vin, Vout, code, feet_lo, feet_hi, inc, acc, V64, incr_flags, blockIdx.x * kBlock + threadIdx.x,
-        g.n_nodes, gridDim.x * kBlock, resid, bad, f64);
-    block_fold(resid, bad, &ring[sweep & ring_mask], &ctl->nonfinite);
+        g, T, Vin, Vout, code, feet_lo, feet_hi, inc, acc, V64, incr_flags, j0, end, stride, resid, bad, f64);
+    block_fold<S, B>(resid, bad, &ring[sweep & ring_mask], &ctl->nonfinite);
 }
 
 template <typename G, typename S, int MODE, bool REDUCED, int DYN>
 cudaError_t launch_one(const SweepLaunch<G, S>& L)
 {
     auto kern = sweep_kernel<G, S, MODE, REDUCED, DYN>;
+    constexpr int B = sweep_block<MODE, REDUCED>();
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, B, 0);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
-    long long need = ((long long)L.g.n_nodes + kBlock - 1) / kBlock;
+    long long need = ((long long)L.g.n_nodes + B - 1) / B;
     long long cap = (long long)per_sm * L.sm_count;
     int blocks = (int)(need < cap ? need : cap);
     if (blocks < 1) blocks = 1;
-    kern<<<blocks, kBlock, 0, L.stream>>>(L.g, L.Vin, L.Vout, L.code, L.feet_lo, L.feet_hi, L.inc, L.acc, L.V64,
+    kern<<<blocks, B, 0, L.stream>>>(L.g, L.Vin, L.Vout, L.code, L.feet_lo, L.feet_hi, L.inc, L.acc, L.V64,
                                           L.incr_flags, L.ctl, L.ring, L.ring_mask, L.sweep, L.check_prev, L.tol,
                                           L.f64);
     return cudaGetLastError();
