@@ -35,7 +35,7 @@ METRIC = "Bellman node-updates/s; time to ‖ΔV‖∞<1e-6, plain vs NN-warm-st
 # sweep: mean of two launches of one ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum); to be retaken (or set to
 # None) whenever it changes
-EVAL_TRAFFIC_61X4 = (221.547520e6 + 21.487872e6 + 221.550592e6 + 18.955008e6) / 2
+EVAL_TRAFFIC_61X4 = (221.541120e6 + 23.328256e6 + 221.548288e6 + 20.264448e6) / 2
 UNIT = "node-updates/s"
 L2_BYTES = 129 * 2 ** 20
 
