@@ -548,28 +548,29 @@ __host__ __device__ constexpr bool eval_prefetch()
 // covers that many consecutive nodes, whose corner lines overlap (a node's
 // v_t neighbours lie 61 nodes on, on the 61^4 grid), so larger blocks take
 // more of their gathers from L1: 1024 threads (2 blocks per SM) for the
-// evaluation sweeps, 768 (2 per SM at 40 registers) for the increment sweeps.
-// Same-box A/B on 61^4 against 256-thread blocks: 78.9 against 83.0 us per
-// evaluation sweep, 88.0 against 90.8 us diagonal-solved.  The diagonal-
-// solved sweep of the reduced grid needs 40 registers and keeps 256 (6 per
-// SM).
+// evaluation sweeps, 768 (2 per SM at 40 registers) for the increment sweeps
+// and for the diagonal-solved evaluation of the reduced grid.  Same-box A/B
+// against 256-thread blocks: 78.9 against 83.0 us per evaluation sweep on
+// 61^4, 88.0 against 90.8 us diagonal-solved; 0.40 against 0.45 ms for the
+// diagonal-solved sweep of the 121^4 band grid.
 template <int MODE, bool REDUCED>
 __host__ __device__ constexpr bool big_blocks()
 {
-    return MODE == kEvalFeet || (MODE == kEvalFeetDiag && !REDUCED) || MODE == kIncr || MODE == kIncrDiag;
+    return MODE == kEvalFeet || MODE == kEvalFeetDiag || MODE == kIncr || MODE == kIncrDiag;
 }
 
 template <int MODE, bool REDUCED>
 __host__ __device__ constexpr int sweep_block()
 {
-    return (MODE == kIncr || MODE == kIncrDiag) ? 768 : big_blocks<MODE, REDUCED>() ? 1024 : kBlock;
+    return (MODE == kIncr || MODE == kIncrDiag || (MODE == kEvalFeetDiag && REDUCED)) ? 768
+           : big_blocks<MODE, REDUCED>()                                               ? 1024
+                                                                                       : kBlock;
 }
 
 template <int MODE, bool REDUCED>
 constexpr int min_blocks()
 {
     return big_blocks<MODE, REDUCED>()                               ? 2
-           : MODE == kEvalFeetDiag                                    ? 6   // reduced grid, 256 threads
            : (MODE == kEvalFeet64 || MODE == kEvalFeet64Diag)         ? 4
                                                                       : 1;
 }
