@@ -205,8 +205,13 @@ __global__ void __launch_bounds__(kBlock, std::is_same<S, double>::value ? 2 : 3
 // FP32 transfers blend at their frozen feet (FEET) or recompute them; FP64
 // transfers sweep increments.  e = -1 is a stand-alone sweep of V[cur].
 // DIAG: each node's own coefficient solved (the Jacobi method proper).
+// Evaluation and increment sweeps of a batch run 640-thread blocks (2 per SM
+// at up to 51 registers, the resident warps of 5 blocks of 256): a block's
+// iteration then covers more neighbouring corner lines of its work item.
+constexpr int kBatchEvalBlock = 640;
+
 template <int DYN, bool FEET, bool DIAG>
-__global__ void __launch_bounds__(kBlock, 5) batch_eval_kernel(const BArgs a, int e, int n_eval)
+__global__ void __launch_bounds__(kBatchEvalBlock, 2) batch_eval_kernel(const BArgs a, int e, int n_eval)
 {
     __shared__ Geo<float> s_g;
     const int* pre = a.prefix + kLEval * (a.count + 1);
@@ -233,19 +238,19 @@ __global__ void __launch_bounds__(kBlock, 5) batch_eval_kernel(const BArgs a, in
             if constexpr (FEET)
                 sweep_nodes<float, float, DIAG ? kEvalFeetDiag : kEvalFeet, false, DYN>(
                     s_g, T, Vin, Vout, a.code + o, a.feet_lo + o, a.feet_hi + o, nullptr, nullptr, nullptr, 0,
-                    first + threadIdx.x, end, kBlock, resid, bad);
+                    first + threadIdx.x, end, kBatchEvalBlock, resid, bad);
             else
                 sweep_nodes<float, float, DIAG ? kEvalDiag : kEval, false, DYN>(
                     s_g, T, Vin, Vout, a.code + o, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
-                    first + threadIdx.x, end, kBlock, resid, bad);
+                    first + threadIdx.x, end, kBatchEvalBlock, resid, bad);
         } else if constexpr (FEET) {
             const int flags = (e == 0 ? 1 : 0) | (e == n_eval - 1 ? 2 : 0);
             sweep_nodes<float, float, DIAG ? kIncrDiag : kIncr, false, DYN>(s_g, T, pick(a.V32, e) + o, pick(a.V32, e + 1) + o,
                                                          a.code + o, a.feet_lo + o, a.feet_hi + o, nullptr,
                                                          a.acc + o, pick(a.V64, st.cur64 ^ 1) + o, flags,
-                                                         first + threadIdx.x, end, kBlock, resid, bad);
+                                                         first + threadIdx.x, end, kBatchEvalBlock, resid, bad);
         }
-        block_fold(resid, bad, &st.res_bits, &st.nonfinite);
+        block_fold<float, kBatchEvalBlock>(resid, bad, &st.res_bits, &st.nonfinite);
     }
 }
 
@@ -457,10 +462,10 @@ double now_ms()
 }
 
 template <typename K>
-int occupancy_blocks(K kern, int sm_count, int* out)
+int occupancy_blocks(K kern, int sm_count, int* out, int block = kBlock)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0) != cudaSuccess) return 1;
     *out = std::max(1, per_sm) * sm_count;
     return 0;
 }
@@ -587,10 +592,10 @@ template <int DYN>
 cudaError_t launch_eval(const dp_batch* b, int e, int n_eval, bool feet, bool diag)
 {
     const BArgs a = args_of(b);
-    if (feet && diag) batch_eval_kernel<DYN, true, true><<<b->blocks_eval, kBlock, 0, b->st>>>(a, e, n_eval);
-    else if (feet) batch_eval_kernel<DYN, true, false><<<b->blocks_eval, kBlock, 0, b->st>>>(a, e, n_eval);
-    else if (diag) batch_eval_kernel<DYN, false, true><<<b->blocks_eval_nf, kBlock, 0, b->st>>>(a, e, n_eval);
-    else batch_eval_kernel<DYN, false, false><<<b->blocks_eval_nf, kBlock, 0, b->st>>>(a, e, n_eval);
+    if (feet && diag) batch_eval_kernel<DYN, true, true><<<b->blocks_eval, kBatchEvalBlock, 0, b->st>>>(a, e, n_eval);
+    else if (feet) batch_eval_kernel<DYN, true, false><<<b->blocks_eval, kBatchEvalBlock, 0, b->st>>>(a, e, n_eval);
+    else if (diag) batch_eval_kernel<DYN, false, true><<<b->blocks_eval_nf, kBatchEvalBlock, 0, b->st>>>(a, e, n_eval);
+    else batch_eval_kernel<DYN, false, false><<<b->blocks_eval_nf, kBatchEvalBlock, 0, b->st>>>(a, e, n_eval);
     return cudaGetLastError();
 }
 
@@ -870,8 +875,8 @@ int dp_batch_create(const dp_grid_desc* descs, int32_t count, void* stream, dp_b
               occupancy_blocks(batch_improve_kernel<float, kDynOrbit, kImproveWalk>, b->sm_count, &b->blocks_imp32w) ||
               occupancy_blocks(batch_improve_kernel<double, kDynOrbit, kImproveFull>, b->sm_count, &b->blocks_imp64f) ||
               occupancy_blocks(batch_improve_kernel<double, kDynOrbit, kImproveWalk>, b->sm_count, &b->blocks_imp64w) ||
-              occupancy_blocks(batch_eval_kernel<kDynOrbit, true, false>, b->sm_count, &b->blocks_eval) ||
-              occupancy_blocks(batch_eval_kernel<kDynOrbit, false, false>, b->sm_count, &b->blocks_eval_nf);
+              occupancy_blocks(batch_eval_kernel<kDynOrbit, true, false>, b->sm_count, &b->blocks_eval, kBatchEvalBlock) ||
+              occupancy_blocks(batch_eval_kernel<kDynOrbit, false, false>, b->sm_count, &b->blocks_eval_nf, kBatchEvalBlock);
     } else {
         bad = occupancy_blocks(batch_improve_kernel<float, kDynUnitSpeed, kImproveFull>, b->sm_count,
                                &b->blocks_imp32f) ||
@@ -881,8 +886,8 @@ int dp_batch_create(const dp_grid_desc* descs, int32_t count, void* stream, dp_b
                                &b->blocks_imp64f) ||
               occupancy_blocks(batch_improve_kernel<double, kDynUnitSpeed, kImproveWalk>, b->sm_count,
                                &b->blocks_imp64w) ||
-              occupancy_blocks(batch_eval_kernel<kDynUnitSpeed, true, false>, b->sm_count, &b->blocks_eval) ||
-              occupancy_blocks(batch_eval_kernel<kDynUnitSpeed, false, false>, b->sm_count, &b->blocks_eval_nf);
+              occupancy_blocks(batch_eval_kernel<kDynUnitSpeed, true, false>, b->sm_count, &b->blocks_eval, kBatchEvalBlock) ||
+              occupancy_blocks(batch_eval_kernel<kDynUnitSpeed, false, false>, b->sm_count, &b->blocks_eval_nf, kBatchEvalBlock);
     }
     bad = bad || occupancy_blocks(batch_widen_kernel, b->sm_count, &b->blocks_widen);
     if (bad) return bail(bfail(DP_ECUDA, "occupancy query failed"));
