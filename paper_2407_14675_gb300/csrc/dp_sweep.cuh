@@ -204,7 +204,7 @@ __device__ __forceinline__ float diag_step(const Geo<float>& g, float vj, float 
 template <typename G>
 __device__ __forceinline__ double diag_step(const Geo<G>& g, double vj, double vplain, double ws)
 {
-    return vj + (vplain - vj) / (1.0 - g.beta64 * ws);
+    return vj + (vplain - vj) * recip_newton(1.0 - g.beta64 * ws);
 }
 
 // Sweeps nodes j0, j0 + stride, ... < end of one grid: the per-node work of
@@ -549,7 +549,8 @@ __host__ __device__ constexpr bool eval_prefetch()
 // v_t neighbours lie 61 nodes on, on the 61^4 grid), so larger blocks take
 // more of their gathers from L1: 1024 threads (2 blocks per SM) for the
 // evaluation sweeps, 768 (2 per SM at 40 registers) for the increment sweeps
-// and for the diagonal-solved evaluation of the reduced grid.  Same-box A/B
+// and for the diagonal-solved evaluation of the reduced grid, 1024 (one per SM
+// at 64 registers) for the FP64 evaluation from FP64 feet.  Same-box A/B
 // against 256-thread blocks: 78.9 against 83.0 us per evaluation sweep on
 // 61^4, 88.0 against 90.8 us diagonal-solved; 0.40 against 0.45 ms for the
 // diagonal-solved sweep of the 121^4 band grid.
@@ -563,7 +564,7 @@ template <int MODE, bool REDUCED>
 __host__ __device__ constexpr int sweep_block()
 {
     return (MODE == kIncr || MODE == kIncrDiag || (MODE == kEvalFeetDiag && REDUCED)) ? 768
-           : big_blocks<MODE, REDUCED>()                                               ? 1024
+           : (big_blocks<MODE, REDUCED>() || MODE == kEvalFeet64 || MODE == kEvalFeet64Diag) ? 1024
                                                                                        : kBlock;
 }
 
@@ -571,7 +572,7 @@ template <int MODE, bool REDUCED>
 constexpr int min_blocks()
 {
     return big_blocks<MODE, REDUCED>()                               ? 2
-           : (MODE == kEvalFeet64 || MODE == kEvalFeet64Diag)         ? 4
+           : (MODE == kEvalFeet64 || MODE == kEvalFeet64Diag)         ? 1   // 1024 threads, 64 registers
                                                                       : 1;
 }
 
