@@ -553,31 +553,36 @@ __host__ __device__ constexpr bool eval_prefetch()
 // at 64 registers) for the FP64 evaluation from FP64 feet.  Same-box A/B
 // against 256-thread blocks: 78.9 against 83.0 us per evaluation sweep on
 // 61^4, 88.0 against 90.8 us diagonal-solved; 0.40 against 0.45 ms for the
-// diagonal-solved sweep of the 121^4 band grid.
+// diagonal-solved sweep of the 121^4 band grid.  A grid too small to give
+// every SM a large block (the 17^4 box has 83,521 nodes) runs 256-thread
+// blocks instead (BIG = false).
 template <int MODE, bool REDUCED>
-__host__ __device__ constexpr bool big_blocks()
+__host__ __device__ constexpr int big_block()
 {
-    return MODE == kEvalFeet || MODE == kEvalFeetDiag || MODE == kIncr || MODE == kIncrDiag;
+    return (MODE == kIncr || MODE == kIncrDiag || (MODE == kEvalFeetDiag && REDUCED))  ? 768
+           : (MODE == kEvalFeet || MODE == kEvalFeetDiag || MODE == kEvalFeet64 || MODE == kEvalFeet64Diag) ? 1024
+                                                                                        : kBlock;
 }
 
-template <int MODE, bool REDUCED>
+template <int MODE, bool REDUCED, bool BIG>
 __host__ __device__ constexpr int sweep_block()
 {
-    return (MODE == kIncr || MODE == kIncrDiag || (MODE == kEvalFeetDiag && REDUCED)) ? 768
-           : (big_blocks<MODE, REDUCED>() || MODE == kEvalFeet64 || MODE == kEvalFeet64Diag) ? 1024
-                                                                                       : kBlock;
+    return BIG ? big_block<MODE, REDUCED>() : kBlock;
 }
 
-template <int MODE, bool REDUCED>
+template <int MODE, bool REDUCED, bool BIG>
 constexpr int min_blocks()
 {
-    return big_blocks<MODE, REDUCED>()                               ? 2
-           : (MODE == kEvalFeet64 || MODE == kEvalFeet64Diag)         ? 1   // 1024 threads, 64 registers
-                                                                      : 1;
+    constexpr bool feet64 = MODE == kEvalFeet64 || MODE == kEvalFeet64Diag;
+    if (BIG) return feet64 ? 1 : 2;
+    return ((MODE == kEvalFeet || MODE == kEvalFeetDiag) && !REDUCED)   ? 8
+           : (MODE == kIncr || MODE == kIncrDiag || MODE == kEvalFeetDiag) ? 6
+           : feet64                                                      ? 4
+                                                                         : 1;
 }
 
-template <typename G, typename S, int MODE, bool REDUCED, int DYN>
-__global__ void __launch_bounds__(sweep_block<MODE, REDUCED>(), min_blocks<MODE, REDUCED>())
+template <typename G, typename S, int MODE, bool REDUCED, int DYN, bool BIG>
+__global__ void __launch_bounds__(sweep_block<MODE, REDUCED, BIG>(), min_blocks<MODE, REDUCED, BIG>())
 sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __restrict__ Vout,
              uint16_t* __restrict__ code, unsigned long long* __restrict__ feet_lo, unsigned* __restrict__ feet_hi,
              float* __restrict__ inc, float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
@@ -608,18 +613,18 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
 
     S resid = (S)0;
     bool bad = false;
-    constexpr int B = sweep_block<MODE, REDUCED>();
+    constexpr int B = sweep_block<MODE, REDUCED, BIG>();
     const int j0 = blockIdx.x * B + threadIdx.x, end = g.n_nodes, stride = gridDim.x * B;
     sweep_nodes<G, S, MODE, REDUCED, DYN, eval_prefetch<MODE, REDUCED>()>(
         g, T, Vin, Vout, code, feet_lo, feet_hi, inc, acc, V64, incr_flags, j0, end, stride, resid, bad, f64);
     block_fold<S, B>(resid, bad, &ring[sweep & ring_mask], &ctl->nonfinite);
 }
 
-template <typename G, typename S, int MODE, bool REDUCED, int DYN>
-cudaError_t launch_one(const SweepLaunch<G, S>& L)
+template <typename G, typename S, int MODE, bool REDUCED, int DYN, bool BIG>
+cudaError_t launch_sized(const SweepLaunch<G, S>& L)
 {
-    auto kern = sweep_kernel<G, S, MODE, REDUCED, DYN>;
-    constexpr int B = sweep_block<MODE, REDUCED>();
+    auto kern = sweep_kernel<G, S, MODE, REDUCED, DYN, BIG>;
+    constexpr int B = sweep_block<MODE, REDUCED, BIG>();
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, B, 0);
@@ -631,9 +636,20 @@ cudaError_t launch_one(const SweepLaunch<G, S>& L)
     int blocks = (int)(need < cap ? need : cap);
     if (blocks < 1) blocks = 1;
     kern<<<blocks, B, 0, L.stream>>>(L.g, L.Vin, L.Vout, L.code, L.feet_lo, L.feet_hi, L.inc, L.acc, L.V64,
-                                          L.incr_flags, L.ctl, L.ring, L.ring_mask, L.sweep, L.check_prev, L.tol,
-                                          L.f64);
+                                      L.incr_flags, L.ctl, L.ring, L.ring_mask, L.sweep, L.check_prev, L.tol, L.f64);
     return cudaGetLastError();
+}
+
+template <typename G, typename S, int MODE, bool REDUCED, int DYN>
+cudaError_t launch_one(const SweepLaunch<G, S>& L)
+{
+    constexpr int Bbig = big_block<MODE, REDUCED>();
+    if constexpr (Bbig != kBlock) {
+        // large blocks only where every SM gets one
+        if ((long long)L.g.n_nodes >= (long long)Bbig * L.sm_count)
+            return launch_sized<G, S, MODE, REDUCED, DYN, true>(L);
+    }
+    return launch_sized<G, S, MODE, REDUCED, DYN, false>(L);
 }
 
 template <typename G, typename S, int DYN, bool REDUCED>
