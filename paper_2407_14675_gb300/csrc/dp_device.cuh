@@ -175,17 +175,14 @@ struct StepP {
 //   u_vr = a1 + b1 s + c (g1 + d1 c)      (from the v_t2^2 / r2 term)
 //   u_vt = a2 + b2 s + c (g2 + e2 s)      (from the v_r2 v_t2 / r2 term)
 // Seven FMAs per control instead of the two-stage step; the terms that do
-// not depend on alpha are rounded once for all controls of the state.
+// not depend on alpha are rounded once for all controls of the state.  The
+// polar dynamics (Example 1) are the same with a fixed thrust acceleration
+// (no mass), plus the orbital angle u_theta = a3 + g3 c from theta' = v_t / r.
 template <typename G>
 struct NodeDyn {
     G vr, vt;
-    // polar: the two-stage step's parts
-    G am, am2;       // a/m at x and at the predictor
-    G d1vr, d1vt;    // drift of v_r, v_t at x
-    G ir2, muir2sq;  // 1/r and mu/r^2 at the predictor (r' = v_r does not depend on alpha)
-    G ir;            // 1/r at x (the angle rate v_t / r)
-    // orbit: the expanded displacement
-    G a0, b0, a1, b1, g1, d1, a2, b2, g2, e2;
+    G a0, b0, a1, b1, g1, d1, a2, b2, g2, e2;   // the expanded displacement
+    G a3, g3;                                   // polar: the orbital angle's
 };
 
 template <typename G, int DYN>
@@ -194,7 +191,7 @@ __device__ __forceinline__ NodeDyn<G> node_dyn(const Geo<G>& g, const StepP<G>& 
     NodeDyn<G> n;
     n.vr = x[1];
     n.vt = x[2];
-    if (DYN == kDynOrbit) {
+    if (DYN == kDynOrbit || DYN == kDynPolar) {
         // every operation rounded explicitly: the searches, the stored feet and
         // the recomputing sweeps run this in different kernels and must agree
         const G ir = grcp(x[0]);
@@ -202,8 +199,11 @@ __device__ __forceinline__ NodeDyn<G> node_dyn(const Geo<G>& g, const StepP<G>& 
         const G d1vt = -xmul(xmul(n.vr, n.vt), ir);
         const G ir2 = grcp(xfma(sp.dt, n.vr, x[0]));
         const G muir2sq = xmul(g.mu, xmul(ir2, ir2));
-        const G am = xmul(g.accel, grcp(x[3]));
-        const G am2 = xmul(g.accel, grcp(xfma(sp.dt, g.mdot, x[3])));
+        G am = g.accel, am2 = g.accel;   // polar: no mass, the thrust acceleration is fixed
+        if (DYN == kDynOrbit) {
+            am = xmul(g.accel, grcp(x[3]));
+            am2 = xmul(g.accel, grcp(xfma(sp.dt, g.mdot, x[3])));
+        }
         const G R0 = xfma(sp.dt, d1vr, n.vr), P0 = xfma(sp.dt, d1vt, n.vt), R1 = xmul(sp.dt, am), P1 = R1;
         const G h0 = xmul(sp.hdt, g.ih[0]), h1 = xmul(sp.hdt, g.ih[1]), h2 = xmul(sp.hdt, g.ih[2]);
         const G amm = xadd(am, am2);
@@ -218,16 +218,12 @@ __device__ __forceinline__ NodeDyn<G> node_dyn(const Geo<G>& g, const StepP<G>& 
         n.b2 = -xmul(h2, xmul(R1, q));
         n.g2 = xmul(h2, xfma(-R0, p1r, amm));
         n.e2 = -xmul(h2, xmul(R1, p1r));
-    } else if (DYN == kDynPolar) {
-        G ir = grcp(x[0]);
-        n.ir = ir;
-        n.d1vr = n.vt * n.vt * ir - g.mu * ir * ir;
-        n.d1vt = -n.vr * n.vt * ir;
-        G r2 = x[0] + sp.dt * n.vr;
-        n.ir2 = grcp(r2);
-        n.muir2sq = g.mu * n.ir2 * n.ir2;
-        n.am = g.accel;   // no mass: the thrust acceleration is fixed
-        n.am2 = g.accel;
+        if (DYN == kDynPolar) {
+            // the orbital angle, theta' = v_t / r: u_theta = a3 + g3 c
+            const G h3 = xmul(sp.hdt, g.ih[3]);
+            n.a3 = xmul(h3, xfma(n.vt, ir, q));
+            n.g3 = xmul(h3, p1r);
+        }
     }
     return n;
 }
@@ -238,22 +234,11 @@ template <typename G, int DYN>
 __device__ __forceinline__ void heun_cells(const Geo<G>& g, const StepP<G>& sp, const NodeDyn<G>& n,
                                            G s, G c, G u[4])
 {
-    if (DYN == kDynOrbit) {
+    if (DYN == kDynOrbit || DYN == kDynPolar) {
         u[0] = xfma(n.b0, s, n.a0);
         u[1] = xfma(c, xfma(n.d1, c, n.g1), xfma(n.b1, s, n.a1));
         u[2] = xfma(c, xfma(n.e2, s, n.g2), xfma(n.b2, s, n.a2));
-        u[3] = sp.um;
-    } else if (DYN == kDynPolar) {
-        G k1vr = n.d1vr + n.am * s;
-        G k1vt = n.d1vt + n.am * c;
-        G vr2 = n.vr + sp.dt * k1vr;
-        G vt2 = n.vt + sp.dt * k1vt;
-        G k2vr = vt2 * vt2 * n.ir2 - n.muir2sq + n.am2 * s;
-        G k2vt = -vr2 * vt2 * n.ir2 + n.am2 * c;
-        u[0] = sp.hdt * (n.vr + vr2) * g.ih[0];
-        u[1] = sp.hdt * (k1vr + k2vr) * g.ih[1];
-        u[2] = sp.hdt * (k1vt + k2vt) * g.ih[2];
-        u[3] = sp.hdt * (n.vt * n.ir + vt2 * n.ir2) * g.ih[3];   // angle: theta' = v_t / r
+        u[3] = DYN == kDynOrbit ? sp.um : xfma(n.g3, c, n.a3);
     } else {
         // test dynamics: unit speed in the (x0, x1) plane, tiny components zeroed
         G cc = fabs(c) < (G)1e-12 ? (G)0 : c;

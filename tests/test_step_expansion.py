@@ -66,3 +66,27 @@ def test_expansion_keeps_the_angle_dependence():
     uh = _expanded(x, np.pi / 2, 1.0, accel, -accel, dt)
     u3h = _expanded(x, 3 * np.pi / 2, 1.0, accel, -accel, dt)
     assert (uh[1] - u3h[1]) > 0.9 * dt * accel * 2
+
+
+def test_polar_expansion_with_the_orbital_angle():
+    # the polar dynamics of the paper's Example 1: thrust acceleration fixed
+    # (no mass), and the orbital angle with theta' = v_t / r
+    rng = np.random.default_rng(2407)
+    for _ in range(200):
+        r, vr, vt = rng.uniform(0.95, 1.15), rng.uniform(-0.1, 0.1), rng.uniform(0.85, 1.1)
+        a, accel, dt = rng.uniform(0, 2 * np.pi), 10 ** rng.uniform(-5, -2), rng.uniform(0.005, 0.1)
+        s, c = np.sin(a), np.cos(a)
+
+        def drift(r, vr, vt):
+            return np.array([vr, vt * vt / r - 1.0 / r ** 2 + accel * s, -vr * vt / r + accel * c, vt / r])
+
+        k1 = drift(r, vr, vt)
+        k2 = drift(r + dt * k1[0], vr + dt * k1[1], vt + dt * k1[2])
+        want = 0.5 * dt * (k1 + k2)
+        # the expansion with a / m = a at both stages
+        got3 = _expanded((r, vr, vt, 1.0), a, 1.0, accel, 0.0, dt)
+        ir, ir2 = 1.0 / r, 1.0 / (r + dt * vr)
+        P0, P1 = vt + dt * (-vr * vt * ir), dt * accel
+        a3, g3 = 0.5 * dt * (vt * ir + P0 * ir2), 0.5 * dt * P1 * ir2
+        np.testing.assert_allclose(got3, want[:3], rtol=0, atol=1e-14)
+        np.testing.assert_allclose(a3 + g3 * c, want[3], rtol=0, atol=1e-14)
