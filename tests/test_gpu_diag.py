@@ -248,3 +248,46 @@ def test_fp64_phase_evaluation_count(dp):
         with pytest.raises(dp.DPError) as e:
             g.policy_iterate(tol=1e-6, max_sweeps=5, n_eval=20, n_eval_fp64=-1)
         assert e.value.code == dp.DP_EINVAL
+
+
+def test_large_grid_block_layout_sweeps_match_oracle(dp):
+    # a reduced grid large enough for the large-block layout of the frozen-feet
+    # sweeps (384,580 stored nodes: every SM gets a 1024- or 768-thread
+    # block): one plain and one diagonal-solved evaluation sweep at the feet
+    # an improvement stored, against the oracle
+    p = W.config2(n=35)
+    o = oracle.Oracle(p)
+    idx = np.flatnonzero(o.active)
+    V = W.smooth_value(p, 48)
+    V[o.target.astype(bool)] = 0.0
+    with dp.Grid(p) as g:
+        g.set_value(V[idx])
+        g.sweep(dp.DP_SWEEP_IMPROVE_FULL)
+        V1, c1 = g.get_value(), g.get_policy()
+        g.sweep(dp.DP_SWEEP_EVAL)
+        v_plain = g.get_value()
+        g.set_value(V1)                      # the stored feet stay valid
+        g.sweep(dp.DP_SWEEP_EVAL_DIAG)
+        v_diag = g.get_value()
+    Vf = np.zeros(p.nodes)
+    Vf[idx] = V1
+    cf = np.zeros(p.nodes, np.uint16)
+    cf[idx] = c1
+    want_plain = o.sweep(Vf, mode=oracle.EVAL, codes=cf)[0][idx]
+    want_diag = o.eval_diag_sweep(Vf, cf)[0][idx]
+    _check_values(v_plain, want_plain, TOL32, "plain evaluation", o=o, nodes=idx, codes=c1)
+    _check_values(v_diag, want_diag, TOL32, "diagonal-solved evaluation", o=o, nodes=idx, codes=c1)
+
+
+def test_large_grid_solvers_agree_with_polish(dp):
+    # 25^4 (390,625 nodes): the large-block evaluation and increment sweeps
+    # in both precision phases; plain and diagonal-solved evaluation reach the
+    # same fixed point
+    p = W.config1(n=25)
+    out = {}
+    for name, kw in (("sweeps", dict(n_eval=20)), ("diag", dict(n_eval=20, eval_solver=dp.DP_EVAL_DIAG))):
+        with dp.Grid(p) as g:
+            rc, st = g.policy_iterate(tol=1e-6, max_sweeps=3000, polish=1, **kw)
+            assert rc == dp.DP_OK and st.converged and st.sweeps_improve_fp64 > 0, (name, st.asdict())
+            out[name] = g.get_value()
+    assert np.abs(out["diag"] - out["sweeps"]).max() <= 2e-6 / (1 - p.beta)
