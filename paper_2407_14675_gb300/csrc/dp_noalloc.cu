@@ -13,7 +13,6 @@
 // every GPU that loads the library holds until the process exits.
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "dp.h"
 #include "dp_host.h"
@@ -47,27 +46,34 @@ static __device__ __align__(256) unsigned char dp_noalloc_scratch[kScratchBytes]
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char* g_scratch[kMaxDevices] = {};   // device address of the array, per device
-
-// Set-up, once per device, with that device current: the device address of
-// the scratch array (the host-side symbol is only a stand-in).
-int scratch_address(int dev, unsigned char** out)
+// Device address of the scratch array in the current context.  The lookup
+// runs on every call: it is a host-side query that allocates nothing, and an
+// address kept from an earlier call would belong to a dead context after
+// cudaDeviceReset, or to another context when the caller has made a
+// non-primary driver-API context current.  (Under lazy module loading the
+// first lookup in a context loads the module, which places the array.)
+int scratch_address(unsigned char** out)
 {
-    if (dev < 0 || dev >= kMaxDevices) return record_error(DP_EINVAL, "device index beyond 64");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, dp_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return record_error(DP_ECUDA, "cudaGetSymbolAddress of the no-allocation scratch failed");
-        }
-        g_scratch[dev] = (unsigned char*)p;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, dp_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return record_error(DP_ECUDA, "cudaGetSymbolAddress of the no-allocation scratch failed");
     }
-    *out = g_scratch[dev];
+    *out = (unsigned char*)p;
     return DP_OK;
+}
+
+// Internal sweep mode of the public DP_SWEEP_VI ... DP_SWEEP_EVAL.
+int sweep_mode(int mode)
+{
+    switch (mode) {
+    case DP_SWEEP_VI: return kVI;
+    case DP_SWEEP_IMPROVE_FULL: return kImproveFull;
+    case DP_SWEEP_IMPROVE_WALK: return kImproveWalk;
+    case DP_SWEEP_EVAL: return kEval;
+    }
+    return -1;
 }
 
 int cuda_fail(const char* what, cudaError_t e)
@@ -117,7 +123,8 @@ extern "C" int dp_bellman_sweep_noalloc(const dp_grid_desc* desc, int32_t mode, 
     long long n = 0;
     int rc = describe_full_grid(desc, &g64, &g32, &n);
     if (rc) return rc;
-    if (mode < DP_SWEEP_VI || mode > DP_SWEEP_EVAL) return record_error(DP_EINVAL, "unknown sweep mode");
+    const int kmode = sweep_mode(mode);
+    if (kmode < 0) return record_error(DP_EINVAL, "unknown sweep mode");
     if (!V_in || !V_out || V_in == V_out) return record_error(DP_EINVAL, "V_in and V_out must be distinct device buffers");
     if (mode != DP_SWEEP_VI && !codes) return record_error(DP_EINVAL, "this sweep mode needs the policy buffer");
     const long long rows = (long long)desc->n[0] * desc->n[1];
@@ -131,7 +138,7 @@ extern "C" int dp_bellman_sweep_noalloc(const dp_grid_desc* desc, int32_t mode, 
     if ((e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return cuda_fail("device query", e);
     unsigned char* scr = nullptr;
-    if ((rc = scratch_address(dev, &scr))) return rc;
+    if ((rc = scratch_address(&scr))) return rc;
     cudaStream_t st = (cudaStream_t)desc->stream;
 
     // tables of the node set and the angles, rebuilt in the scratch each call
@@ -158,9 +165,9 @@ extern "C" int dp_bellman_sweep_noalloc(const dp_grid_desc* desc, int32_t mode, 
     g32.tab_hi = (const float2*)(scr + kHi32);
     g32.tab_lo = (const float2*)(scr + kLo32);
     if (desc->precision == DP_FP64)
-        rc = run<double, double>(g64, scr, mode, V_in, V_out, codes, desc->dynamics, st, sm);
+        rc = run<double, double>(g64, scr, kmode, V_in, V_out, codes, desc->dynamics, st, sm);
     else
-        rc = run<float, float>(g32, scr, mode, V_in, V_out, codes, desc->dynamics, st, sm);
+        rc = run<float, float>(g32, scr, kmode, V_in, V_out, codes, desc->dynamics, st, sm);
     if (rc) return rc;
 
     unsigned long long bits = 0;
