@@ -168,6 +168,17 @@ typedef struct dp_solve_opts {
                               automatic, max(n_eval, 80) for DP_EVAL_DIAG and
                               max(n_eval, 160) for DP_EVAL_JACOBI, 0 when n_eval
                               is 0).  Batches ignore it and keep n_eval           */
+    int32_t eval_levels;   /* PI on FP32 grids (DP_EVAL_JACOBI, DP_EVAL_DIAG):
+                              evaluation sweeps run per launch, 1..32 (0:
+                              automatic).  Above 1 a launch runs that many
+                              consecutive Jacobi sweeps as a wavefront over the
+                              nodes, each sweep's chunk starting once the
+                              previous sweep has finished every chunk within
+                              the frozen feet's reach; the values are the same
+                              as one sweep per launch, bit for bit.  Automatic
+                              (0): one sweep per launch.  A launch that gives
+                              up a bounded wait (2 s) makes the call return
+                              DP_ETIMEOUT                                    */
 } dp_solve_opts;
 
 /* Solver statistics (filled on DP_OK and on DP_ENOCONV). */
@@ -448,10 +459,16 @@ int dp_batch_get_policy(const dp_batch* batch, int32_t index, uint16_t* host_cod
  * that overlap on the GPU (two streams, two threads) race on the array and give
  * wrong results: issue them one after another.
  *
- * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  The call itself never calls cudaMalloc,
- * cudaFree or any allocating library routine.
+ * Set-up: make one warm-up call per device at start-up, before the phase in
+ * which the caller may not allocate.  With lazy module loading (the CUDA
+ * default since 12.2) the library's device code, this array included, is
+ * loaded into a context on first use, and that load allocates device memory;
+ * after the warm-up call the array is resident until the context ends.  Every
+ * call looks up the array's device address in the current context
+ * (cudaGetSymbolAddress, a host-side query), so a context re-created after
+ * cudaDeviceReset needs one more warm-up call and nothing else.  Apart from
+ * that first load the call never calls cudaMalloc, cudaFree or any
+ * allocating library routine.
  *
  * Errors: DP_EINVAL (descriptor, mode, NULL or aliased buffers, grid beyond
  * the scratch bound), DP_ECUDA, DP_ENONFINITE (V_out holds a non-finite value). */

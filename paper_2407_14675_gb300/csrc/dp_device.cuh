@@ -55,7 +55,11 @@ struct Ctl {
     int stop;         // 1 once a stopping test has passed
     int stop_sweep;   // sweeps completed when it passed
     int nonfinite;    // a sweep produced a non-finite value
-    int pad;
+    int reach;        // largest |corner index - node index| of the stored frozen feet
+                      //   (improvement sweeps fold it in; the multi-level
+                      //   evaluation orders its chunks by it)
+    int wave_err;     // a multi-level evaluation gave up a bounded wait
+    int pad[3];
 };
 
 // Everything a sweep kernel needs about the grid, in geometry precision G.
@@ -456,21 +460,39 @@ __device__ __forceinline__ void load_rows(const S* __restrict__ V, const int bas
     K.set(a, d);
 }
 
+// Weak global load through L1 (ld.global): for values that other blocks of
+// the same launch write (the multi-level evaluation), where the read-only
+// path (ld.global.nc) may return stale data.  volatile keeps it after the
+// acquire fence and block barrier that make those writes visible.
+__device__ __forceinline__ float ld_coherent(const float* p)
+{
+    float v;
+    asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 // FP32 values and blend: the same differences, two per paired instruction,
 // written straight into the pairs (x, x + 4) of Corners<float>: row rb and
-// row rb + 2 of the same v_t corner.
-template <>
-__device__ __forceinline__ void load_rows<float, float>(const float* __restrict__ V, const int base[4], int n_m,
-                                                        float vj, Corners<float>& K, int up)
+// row rb + 2 of the same v_t corner.  COH: coherent loads (ld_coherent).
+template <bool COH>
+__device__ __forceinline__ void load_rows_f32(const float* __restrict__ V, const int base[4], int n_m, float vj,
+                                              Corners<float>& K, int up = 1)
 {
     float v00[4], v01[4], v10[4], v11[4];
 #pragma unroll
     for (int rb = 0; rb < 4; ++rb) {
         const float* p = V + base[rb];
-        v00[rb] = __ldg(p);
-        v01[rb] = __ldg(p + up);
-        v10[rb] = __ldg(p + n_m);
-        v11[rb] = __ldg(p + n_m + up);
+        if constexpr (COH) {
+            v00[rb] = ld_coherent(p);
+            v01[rb] = ld_coherent(p + up);
+            v10[rb] = ld_coherent(p + n_m);
+            v11[rb] = ld_coherent(p + n_m + up);
+        } else {
+            v00[rb] = __ldg(p);
+            v01[rb] = __ldg(p + up);
+            v10[rb] = __ldg(p + n_m);
+            v11[rb] = __ldg(p + n_m + up);
+        }
     }
     const unsigned long long jj = pack2(vj, vj);
 #pragma unroll
@@ -481,6 +503,13 @@ __device__ __forceinline__ void load_rows<float, float>(const float* __restrict_
         K.q0[2 * rb + 1] = sub2(lo1, jj);
         K.qd[2 * rb + 1] = sub2(pack2(v11[rb], v11[rb + 2]), lo1);
     }
+}
+
+template <>
+__device__ __forceinline__ void load_rows<float, float>(const float* __restrict__ V, const int base[4], int n_m,
+                                                        float vj, Corners<float>& K, int up)
+{
+    load_rows_f32<false>(V, base, n_m, vj, K, up);
 }
 
 // Type in which D = I[V] - V_j is blended and compared: FP64 when the values
@@ -807,8 +836,10 @@ struct CachedEval {
         return w;
     }
 
-    // Frozen-foot word of this node for a code (FP32 geometry only).
-    __device__ __forceinline__ FootWord foot_of(int code) const
+    // Frozen-foot word of this node for a code (FP32 geometry only).  cell
+    // (nullable) receives the foot's cell when it has corners (kinds inside
+    // and recompute).
+    __device__ __forceinline__ FootWord foot_of(int code, int* cell = nullptr) const
     {
         G s, c, u[4], t[4];
         int cl[4], base[4];
@@ -818,6 +849,10 @@ struct CachedEval {
         for (int d = 0; d < 4; ++d) u[d] += u0[d];
         if (foot_cell(*g, i, u, cl, t)) return foot_word_kind(kFootOut);
         if (REDUCED && cell_rows<G, REDUCED>(*g, cl, base)) return foot_word_kind(kFootOut);
+        if (cell) {
+#pragma unroll
+            for (int d = 0; d < 4; ++d) cell[d] = cl[d];
+        }
         return encode_foot(i, cl, t, g->foot_dm, g->foot_tm);
     }
 };

@@ -39,6 +39,45 @@ cudaError_t launch_sweep(const SweepLaunch<double, double>& L);
 cudaError_t launch_sweep(const SweepLaunch<float, float>& L);
 cudaError_t launch_sweep(const SweepLaunch<float, double>& L);
 
+// Several evaluation sweeps of policy iteration in one launch (FP32 grids with
+// frozen feet; dp_wave.cuh): levels 0 .. levels-1 run sweeps sweep ..
+// sweep + levels - 1, level s reading V[(in0 + s) & 1] and writing
+// V[(in0 + s + 1) & 1].
+constexpr int kWaveBlock = 512;
+constexpr int kWaveNodesPerThread = 4;
+constexpr int kWaveChunk = kWaveBlock * kWaveNodesPerThread;   // nodes per work item
+constexpr int kWaveMaxLevels = 32;
+constexpr unsigned long long kWaveTimeoutNs = 2000000000ull;   // 2 s per wait
+
+// Counters of one launch: [0] ticket, then levels x n_chunks completion counts.
+__host__ __device__ constexpr long long wave_sync_ints(int levels, long long n_nodes)
+{
+    return 1 + (long long)levels * ((n_nodes + kWaveChunk - 1) / kWaveChunk);
+}
+
+struct WaveArgs {
+    Geo<float> g;
+    float* V[2];                           // the value buffers (kEval*) or increment buffers (kIncr*)
+    int in0;                               // buffer that level 0 reads
+    const uint16_t* code;
+    const unsigned long long* feet_lo;
+    const unsigned* feet_hi;
+    float* acc;                            // kIncr*: running sum of increments
+    double* V64;                           // kIncr*: FP64 value that receives the sum
+    int e0, ne;                            // kIncr*: chain index of level 0, chain length
+    int levels;
+    int* sync;                             // wave_sync_ints(levels, n_nodes), zeroed
+    Ctl* ctl;
+    unsigned long long* ring;
+    int ring_mask;
+    long long sweep;                       // ring slot of level 0
+    int check_prev;
+    double tol;
+};
+
+// mode: kEvalFeet, kEvalFeetDiag, kIncr or kIncrDiag.  Zeroes a.sync first.
+cudaError_t launch_wave(const WaveArgs& a, int mode, int dyn, int reduced, cudaStream_t st, int sm_count);
+
 // Feedback (steps == 0) or closed loop (steps > 0) over n states.
 template <typename G, typename S>
 struct LoopLaunch {

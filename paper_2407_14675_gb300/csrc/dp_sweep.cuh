@@ -207,6 +207,18 @@ __device__ __forceinline__ double diag_step(const Geo<G>& g, double vj, double v
     return vj + (vplain - vj) * recip_newton(1.0 - g.beta64 * ws);
 }
 
+// Largest distance in stored-node index from node j to a corner of cell cl
+// (the cell's lowest corner, and the highest one plus the v_t and mass steps).
+template <bool REDUCED>
+__device__ __forceinline__ int cell_reach(const Geo<float>& g, int j, const int cl[4])
+{
+    int base[4];
+    cell_rows<float, REDUCED>(g, cl, base);
+    const int lo = min(min(base[0], base[1]), min(base[2], base[3]));
+    const int hi = max(max(base[0], base[1]), max(base[2], base[3])) + g.n_m + 1;
+    return max(j - lo, hi - j);
+}
+
 // Sweeps nodes j0, j0 + stride, ... < end of one grid: the per-node work of
 // every sweep mode.  Folds max |V_out - V_in| into resid and non-finite
 // results into bad.
@@ -217,7 +229,7 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                                             unsigned* __restrict__ feet_hi, float* __restrict__ inc,
                                             float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
                                             int j0, int end, int stride, S& resid, bool& bad,
-                                            const Feet64 f64 = Feet64())
+                                            const Feet64 f64 = Feet64(), int* reach = nullptr)
 {
     constexpr bool kIsVI = MODE == kVI || MODE == kVIDiag;
     constexpr bool kSearch = kIsVI || MODE == kImproveFull || MODE == kImproveWalk;
@@ -475,9 +487,12 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                     if (!kIsVI) code[j] = (uint16_t)c;
                     if constexpr (kGeo32 && kImprove) {
                         if (feet_lo) {
-                            const FootWord w = ev.foot_of(c);
+                            int cl[4];
+                            const FootWord w = ev.foot_of(c, cl);
                             feet_lo[j] = w.lo;
                             feet_hi[j] = w.hi;
+                            if (reach && ((w.hi >> 16) & 3u) != kFootOut)
+                                *reach = max(*reach, cell_reach<REDUCED>(g, j, cl));
                         }
                     }
                     if constexpr (!kGeo32 && kImprove) {
@@ -615,8 +630,16 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
     bool bad = false;
     constexpr int B = sweep_block<MODE, REDUCED, BIG>();
     const int j0 = blockIdx.x * B + threadIdx.x, end = g.n_nodes, stride = gridDim.x * B;
+    constexpr bool kReach = std::is_same<G, float>::value && (MODE == kImproveFull || MODE == kImproveWalk);
+    int reach = 0;
     sweep_nodes<G, S, MODE, REDUCED, DYN, eval_prefetch<MODE, REDUCED>()>(
-        g, T, Vin, Vout, code, feet_lo, feet_hi, inc, acc, V64, incr_flags, j0, end, stride, resid, bad, f64);
+        g, T, Vin, Vout, code, feet_lo, feet_hi, inc, acc, V64, incr_flags, j0, end, stride, resid, bad, f64,
+        kReach ? &reach : nullptr);
+    if constexpr (kReach) {
+        // the stored feet's reach, for the multi-level evaluation that follows
+        reach = __reduce_max_sync(0xffffffffu, (unsigned)reach);
+        if ((threadIdx.x & 31) == 0 && reach > 0) atomicMax(&ctl->reach, reach);
+    }
     block_fold<S, B>(resid, bad, &ring[sweep & ring_mask], &ctl->nonfinite);
 }
 

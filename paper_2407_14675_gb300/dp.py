@@ -79,6 +79,7 @@ class dp_solve_opts(C.Structure):
         ("gmres_reorth", C.c_int32),
         ("gmres_rtol", C.c_double),
         ("n_eval_fp64", C.c_int32),
+        ("eval_levels", C.c_int32),
     ]
 
 
@@ -344,16 +345,18 @@ def dp_bellman_sweep_noalloc(desc: dp_grid_desc, mode: int, V_in: int, V_out: in
 
 def make_opts(tol=1e-6, max_sweeps=100000, n_eval=20, walk=1, warm=0, polish=1, switch_tol=0.0,
               time_kernels=0, history=None, eval_solver=DP_EVAL_JACOBI, gmres_restart=0, gmres_cycles=0,
-              gmres_reorth=0, gmres_rtol=0.0, n_eval_fp64=0) -> dp_solve_opts:
+              gmres_reorth=0, gmres_rtol=0.0, n_eval_fp64=0, eval_levels=0) -> dp_solve_opts:
     """Solver options; history: optional float64 numpy array that receives the
     residual of every stopping test (kept alive by the caller).  eval_solver
-    DP_EVAL_GMRES evaluates each policy by GMRES (gmres_*: 0 = default)."""
+    DP_EVAL_GMRES evaluates each policy by GMRES (gmres_*: 0 = default).
+    eval_levels: evaluation sweeps per launch (0 = automatic, 1 = one)."""
     o = dp_solve_opts()
     o.tol, o.max_sweeps, o.n_eval, o.walk, o.warm = tol, max_sweeps, n_eval, walk, warm
     o.polish, o.switch_tol, o.time_kernels = polish, switch_tol, time_kernels
     o.eval_solver, o.gmres_restart, o.gmres_cycles = eval_solver, gmres_restart, gmres_cycles
     o.gmres_reorth, o.gmres_rtol = gmres_reorth, gmres_rtol
     o.n_eval_fp64 = n_eval_fp64
+    o.eval_levels = eval_levels
     if history is not None:
         o.history = history.ctypes.data_as(C.POINTER(C.c_double))
         o.history_capacity = len(history)
