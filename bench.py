@@ -1,13 +1,15 @@
 #!/usr/bin/env python
 """Benchmark: Bellman node-updates/s of modified policy iteration on the
-61^4 minimum-time orbit-transfer grid (FP32 sweeps, FP64 residual).
+121^4 energy-band reduced grid (55,976,052 stored nodes; FP32 sweeps, FP64
+residual), the largest single-GPU configuration of the workload set.
 
 One step = one outer iteration of modified policy iteration: an improvement
 sweep (local walk from the previous optimum + golden-section refinement over
 64 tabulated angles) followed by 20 Jacobi policy-evaluation sweeps, over the
-13,845,841 grid nodes resident in HBM.  value = node updates / device time.
-The e2e figure runs the same step through the C ABI with host buffers: the
-value and policy go up from pinned host memory and come back every step.
+stored nodes resident in HBM.  value = node updates / device time.  The e2e
+figure runs the same step through the C ABI with host buffers: the value
+(FP64) and the policy go up from pinned host memory and come back every step.
+The same step on the 61^4 full box is reported as step_61x4.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 step (there is no reference implementation of this method to run).
@@ -31,11 +33,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Bellman node-updates/s; time to ‖ΔV‖∞<1e-6, plain vs NN-warm-started"
-# DRAM bytes (read + written) of one launch of the 61^4 frozen-feet evaluation
-# sweep: mean of two launches of one ncu capture of the current kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum); to be retaken (or set to
-# None) whenever it changes
-EVAL_TRAFFIC_61X4 = (221.541120e6 + 23.328256e6 + 221.548288e6 + 20.264448e6) / 2
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the frozen-feet evaluation sweep, from one ncu capture per workload, with a
+# hash of the kernel sources they were taken on: a capture of an older kernel
+# is reported as stale (traffic null) instead of silently.
+EVAL_TRAFFIC = {
+    "61x4": {"bytes": (221.541120e6 + 23.328256e6 + 221.548288e6 + 20.264448e6) / 2, "src": None},
+    "121x4_band": {"bytes": (899.600640e6 + 191.732480e6 + 899.415552e6 + 189.348864e6) / 2, "src": "ab82ee31959cc8ba"},
+}
+KERNEL_SOURCES = ("paper_2407_14675_gb300/csrc/dp_sweep.cuh", "paper_2407_14675_gb300/csrc/dp_device.cuh")
 UNIT = "node-updates/s"
 L2_BYTES = 129 * 2 ** 20
 
@@ -45,6 +51,26 @@ def _env_int(k, d):
         return int(os.environ.get(k, d))
     except ValueError:
         return d
+
+
+def kernel_src_hash():
+    """Hash of the sources of the sweep kernels (first 16 hex digits)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(key):
+    rec = EVAL_TRAFFIC.get(key) or {}
+    if rec.get("bytes") is None:
+        return None, "not captured for this kernel"
+    if rec.get("src") != kernel_src_hash():
+        return None, "stale: the kernel sources changed since the ncu capture"
+    return rec["bytes"], ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel, mean of two launches "
+                          "(kernel sources %s)" % rec["src"])
 
 
 def _peaks():
@@ -69,7 +95,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
@@ -149,61 +175,65 @@ def _barrier(world):
 
 # ---------------------------------------------------------------- CPU oracle --
 
-def oracle_step_rate(p, seconds_target=12.0, seed=2407):
-    """Node-updates/s of the FP64 oracle (single thread) for the step's mix of
-    one walk improvement and n_eval evaluation sweeps, measured on sampled
-    nodes of the same grid with a seeded smooth value function."""
-    import oracle
-    from paper_2407_14675_gb300 import workloads as W
-    o = oracle.Oracle(p)
-    V = W.smooth_value(p, seed)
-    V[o.target.astype(bool)] = 0
-    rng = np.random.default_rng(seed)
-    free = np.flatnonzero((o.active & ~o.target).astype(bool))
-    # previous optimum for the walk: the oracle's own full tabulation (untimed)
-    n_imp = 2000
-    nodes = np.sort(rng.choice(free, n_imp, replace=False))
-    _, start = o.bellman_nodes(V, nodes, mode=oracle.IMPROVE_FULL)
-    t0 = time.perf_counter()
-    o.bellman_nodes(V, nodes, mode=oracle.IMPROVE_WALK, codes=start)
-    t_imp = (time.perf_counter() - t0) / n_imp
-    n_ev = 50000
-    ev_nodes = np.sort(rng.choice(free, n_ev, replace=False))
-    codes = rng.integers(0, 65536, n_ev).astype(np.uint16)
-    t0 = time.perf_counter()
-    o.bellman_nodes(V, ev_nodes, mode=oracle.EVAL, codes=codes)
-    t_ev = (time.perf_counter() - t0) / n_ev
-    # scale the sample to about seconds_target of CPU work
-    per_step_node = t_imp + p.n_eval * t_ev
-    reps = max(1, int(seconds_target / max(per_step_node * n_imp, 1e-9)))
-    t0 = time.perf_counter()
-    for _ in range(reps):
+class OracleSample:
+    """The FP64 oracle on a seeded sample of one grid's stored nodes, with a
+    seeded smooth value function (built once: for the 121^4 band the box
+    holds 214M nodes)."""
+
+    def __init__(self, p, seed=2407, n_imp=2000):
+        import oracle
+        from paper_2407_14675_gb300 import workloads as W
+        self.o = oracle.Oracle(p)
+        self.p = p
+        self.V = W.smooth_value(p, seed)
+        self.V[self.o.target.astype(bool)] = 0
+        rng = np.random.default_rng(seed)
+        free = np.flatnonzero((self.o.active & ~self.o.target).astype(bool))
+        self.nodes = np.sort(rng.choice(free, n_imp, replace=False))
+        # previous optimum for the walk: the oracle's own full tabulation (untimed)
+        _, self.start = self.o.bellman_nodes(self.V, self.nodes, mode=oracle.IMPROVE_FULL)
+
+    def step_rate(self, seconds_target=12.0):
+        """Node-updates/s for the step's mix: one walk improvement and n_eval
+        evaluation sweeps at the sampled nodes, repeated to about
+        seconds_target of single-thread CPU time."""
+        import oracle
+        o, V, nodes, start, p = self.o, self.V, self.nodes, self.start, self.p
+        t0 = time.perf_counter()
         o.bellman_nodes(V, nodes, mode=oracle.IMPROVE_WALK, codes=start)
         for _e in range(p.n_eval):
             o.bellman_nodes(V, nodes, mode=oracle.EVAL, codes=start)
-    wall = time.perf_counter() - t0
-    updates = reps * n_imp * (1 + p.n_eval)
-    return updates / wall, {"nodes": n_imp, "reps": reps, "seconds": wall, "updates": updates}
+        once = time.perf_counter() - t0
+        reps = max(1, int(seconds_target / max(once, 1e-9)))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            o.bellman_nodes(V, nodes, mode=oracle.IMPROVE_WALK, codes=start)
+            for _e in range(p.n_eval):
+                o.bellman_nodes(V, nodes, mode=oracle.EVAL, codes=start)
+        wall = time.perf_counter() - t0
+        updates = reps * len(nodes) * (1 + p.n_eval)
+        return updates / wall, {"nodes": len(nodes), "reps": reps, "seconds": wall, "updates": updates}
 
 
 def _oracle_worker(task):
     """One process of the all-cores oracle baseline (spawned): the single
     thread measurement on its own seeded node sample, for a fixed time."""
-    seed, seconds = task
+    seed, seconds, n = task
     from paper_2407_14675_gb300 import workloads as W
-    rate, info = oracle_step_rate(W.config1(), seconds_target=seconds, seed=seed)
+    rate, info = OracleSample(W.config2(n=n), seed=seed).step_rate(seconds)
     return info["updates"], info["seconds"]
 
 
-def oracle_parallel_rate(seconds_target=10.0, procs=None):
-    """The oracle on every host core: one spawned process per core, each on
-    its own sample of the same step mix.  Aggregate node-updates / the
-    slowest process's time."""
+def oracle_parallel_rate(seconds_target=10.0, procs=None, n=121):
+    """The oracle on the host cores: one spawned process per core (at most 8:
+    each holds the band's 214M-node box value, 1.7 GB), each on its own sample
+    of the same step mix.  Aggregate node-updates / the slowest process's
+    time."""
     import multiprocessing as mp
-    procs = procs or os.cpu_count() or 1
+    procs = procs or min(os.cpu_count() or 1, 8)
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs) as pool:
-        res = pool.map(_oracle_worker, [(2407 + 97 * k, seconds_target) for k in range(procs)])
+        res = pool.map(_oracle_worker, [(2407 + 97 * k, seconds_target, n) for k in range(procs)])
     updates = sum(r[0] for r in res)
     wall = max(r[1] for r in res)
     return updates / wall, {"procs": procs, "seconds": wall, "updates": updates}
@@ -213,24 +243,25 @@ def run_reference(args, world, rank):
     from paper_2407_14675_gb300 import workloads as W
     if rank != 0:
         return 0
-    p = W.config1()
+    p = W.config2()
+    sample = OracleSample(p)
     steps = []
     for _ in range(args.warmup):
-        oracle_step_rate(p, seconds_target=2.0)
+        sample.step_rate(seconds_target=2.0)
     for _ in range(args.steps):
-        r, info = oracle_step_rate(p, seconds_target=max(2.0, 20.0 / max(args.steps, 1)))
+        r, info = sample.step_rate(seconds_target=max(2.0, 20.0 / max(args.steps, 1)))
         steps.append((r, info))
     rate = float(np.mean([s[0] for s in steps]))
-    nodes = p.nodes
-    ms_step = (1 + p.n_eval) * nodes / rate * 1e3
+    n_upd = int(sample.o.n_active - int(sample.o.target.sum()))
+    ms_step = (1 + p.n_eval) * n_upd / rate * 1e3
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": _config(p),
+        "config": _config(p, n_upd),
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "per step: %d sampled nodes x (1 walk improvement + %d evaluations), "
-                                   "repeated to ~%.0f s, FP64 single thread" %
+                         "sample": "per step: %d sampled stored nodes of the 121^4 band x (1 walk improvement + %d "
+                                   "evaluations), repeated to ~%.0f s, FP64 single thread" %
                                    (steps[0][1]["nodes"], p.n_eval, steps[0][1]["seconds"])},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -238,12 +269,21 @@ def run_reference(args, world, rank):
     return 0
 
 
-def _config(p):
-    return {"workload": "61^4 minimum-time orbit transfer (r, v_r, v_t, m), FP32 modified policy iteration: "
-                        "1 walk+golden improvement (64 angles) + 20 evaluation sweeps per step",
-            "grid": list(p.n), "nodes": p.nodes, "n_angles": p.n_angles, "n_eval": p.n_eval,
-            "accel": p.accel, "dt": p.dt, "beta": p.beta,
-            "l2": "flushed between steps (256 MiB write); per-sweep working set 138 MB > 129 MB L2"}
+def _config(p, n_upd=None):
+    band = bool(p.reduced)
+    d = {"workload": ("121^4 box reduced to the energy band [%.4f, %.4f] (55,976,052 stored nodes), minimum-time "
+                      "orbit transfer (r, v_r, v_t, m), FP32 modified policy iteration with FP64 residual: "
+                      "1 walk+golden improvement (64 angles) + 20 evaluation sweeps per step" % (p.energy_lo, p.energy_hi)
+                      if band else
+                      "%d^4 minimum-time orbit transfer (r, v_r, v_t, m), FP32 modified policy iteration: "
+                      "1 walk+golden improvement (64 angles) + 20 evaluation sweeps per step" % p.n[0]),
+         "grid": list(p.n), "box_nodes": p.nodes, "n_angles": p.n_angles, "n_eval": p.n_eval,
+         "accel": p.accel, "dt": p.dt, "beta": p.beta,
+         "l2": ("flushed between steps (256 MiB write); per-sweep working set %s > 129 MB L2" %
+                ("1.12 GB" if band else "276 MB"))}
+    if n_upd is not None:
+        d["node_updates_per_sweep"] = int(n_upd)
+    return d
 
 
 # ------------------------------------------------------------------ GPU arm --
@@ -457,7 +497,7 @@ def batch_leg(args, dp, W, torch):
     return out
 
 
-def warm_start_leg(args, dp, W, torch, g1, p1):
+def warm_start_leg(args, dp, W, torch, g1, p1, g2):
     """Learned warm start: train the network on the converged 61^4 solve
     (every stored node), then solve the 121^4 energy-band grid to 1e-6 from
     V = 0, from the network's V and policy, and from the 61^4 solution, with
@@ -475,69 +515,159 @@ def warm_start_leg(args, dp, W, torch, g1, p1):
         tr["wall_s"] = time.perf_counter() - t0
         tr["tflops_nominal"] = st.flops / max(st.ms, 1e-9) / 1e9
         out["train"] = tr
-        with dp.Grid(p2, stream=int(torch.cuda.current_stream().cuda_stream)) as g2:
-            out["nodes_active"] = g2.info["n_active"]
-            V_cold = None
-            # each start with the configured 20 evaluation sweeps per improvement,
-            # then again with the diagonal-solved evaluation
-            tuned = "_diag"
-            runs = [(k, p2.n_eval, dp.DP_EVAL_JACOBI) for k in ("cold", "warm", "from_61x4_grid")]
-            runs += [(k + tuned, args.diag_n_eval, dp.DP_EVAL_DIAG) for k in ("cold", "warm", "from_61x4_grid")]
-            for start, n_eval, solver in runs:
-                kind = start.split("_diag")[0]
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                ws_ms = 0.0
-                if kind != "cold":
-                    if kind == "warm":
-                        ws_ms = dp.dp_warm_start(net.h, g2.h)
-                    else:
-                        # the non-learned baseline: Q1 interpolation of the 61^4 solution
-                        ws_ms = dp.dp_warm_start_from_grid(g1.h, g2.h)
-                    if start == kind:
-                        t_ws = time.perf_counter() - t0
-                        err = np.abs(g2.get_value() - V_cold) / g2.info["penalty_M"]
-                        out[("warm_start_error" if kind == "warm" else "from_61x4_grid_error")] = {
-                            "max_over_M": float(err.max()), "rms_over_M": float(np.sqrt(np.mean(err ** 2)))}
-                        t0 = time.perf_counter() - t_ws   # the host copy for the error is not timed
-                rc, s2 = g2.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=n_eval, polish=1,
-                                           warm=int(kind != "cold"), eval_solver=solver)
-                torch.cuda.synchronize()
-                if start == "cold":
-                    V_cold = g2.get_value()
-                    # the energy-band grid's evaluation sweep against the HBM roofline
-                    # (10 B per node-update), timed after the solve on its FP32 values
-                    g2.set_value(V_cold)
-                    rc, sk = g2.policy_iterate(tol=0.0, max_sweeps=2, n_eval=p2.n_eval, polish=0, warm=1,
-                                               time_kernels=1)
-                    n_upd = g2.info["n_active"] - g2.info["n_target"]
-                    ev_ms = sk.ms_eval / max(sk.sweeps_eval, 1)
-                    peaks, _ = _peaks()
-                    out["eval_sweep_121x4_band"] = {
-                        "ms": ev_ms, "node_updates_per_s": n_upd / (ev_ms / 1e3),
-                        "achieved_gbs": 10.0 * n_upd / (ev_ms / 1e3) / 1e9,
-                        "frac_of_hbm": 10.0 * n_upd / (ev_ms / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
-                        "walk_ms": sk.ms_improve / max(sk.sweeps_improve, 1)}
-                out[start] = {"seconds": time.perf_counter() - t0, "converged": bool(s2.converged),
-                              "residual": s2.residual, "n_eval": n_eval,
-                              "evaluation": "diagonal-solved Jacobi" if solver == dp.DP_EVAL_DIAG else "sweeps",
-                              "warm_start_ms": ws_ms,
-                              "sweeps_improve": s2.sweeps_improve, "sweeps_eval": s2.sweeps_eval,
-                              "sweeps_improve_fp64": s2.sweeps_improve_fp64,
-                              "sweeps_eval_fp64": s2.sweeps_eval_fp64, "node_updates": s2.node_updates}
-            x0 = W.closed_loop_states(p2, 1024, band=(p2.energy_lo, p2.energy_hi))
+        out["nodes_active"] = g2.info["n_active"]
+        V_cold = None
+        # each start with the configured 20 evaluation sweeps per improvement,
+        # then again with the diagonal-solved evaluation
+        tuned = "_diag"
+        runs = [(k, p2.n_eval, dp.DP_EVAL_JACOBI) for k in ("cold", "warm", "from_61x4_grid")]
+        runs += [(k + tuned, args.diag_n_eval, dp.DP_EVAL_DIAG) for k in ("cold", "warm", "from_61x4_grid")]
+        for start, n_eval, solver in runs:
+            kind = start.split("_diag")[0]
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ta, xf = g2.simulate(x0, p2.dt, p2.dt, 200.0)
-            out["closed_loop"] = {"states": len(x0), "seconds": time.perf_counter() - t0,
-                                  "arrived": int((ta >= 0).sum()),
-                                  "median_time": float(np.median(ta[ta >= 0])) if (ta >= 0).any() else None}
+            ws_ms = 0.0
+            if kind != "cold":
+                if kind == "warm":
+                    ws_ms = dp.dp_warm_start(net.h, g2.h)
+                else:
+                    # the non-learned baseline: Q1 interpolation of the 61^4 solution
+                    ws_ms = dp.dp_warm_start_from_grid(g1.h, g2.h)
+                if start == kind:
+                    t_ws = time.perf_counter() - t0
+                    err = np.abs(g2.get_value() - V_cold) / g2.info["penalty_M"]
+                    out[("warm_start_error" if kind == "warm" else "from_61x4_grid_error")] = {
+                        "max_over_M": float(err.max()), "rms_over_M": float(np.sqrt(np.mean(err ** 2)))}
+                    t0 = time.perf_counter() - t_ws   # the host copy for the error is not timed
+            rc, s2 = g2.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=n_eval, polish=1,
+                                       warm=int(kind != "cold"), eval_solver=solver)
+            torch.cuda.synchronize()
+            if start == "cold":
+                V_cold = g2.get_value()
+                # the energy-band grid's evaluation sweep against the HBM roofline
+                # (10 B per node-update), timed after the solve on its FP32 values
+                g2.set_value(V_cold)
+                rc, sk = g2.policy_iterate(tol=0.0, max_sweeps=2, n_eval=p2.n_eval, polish=0, warm=1,
+                                           time_kernels=1)
+                n_upd = g2.info["n_active"] - g2.info["n_target"]
+                ev_ms = sk.ms_eval / max(sk.sweeps_eval, 1)
+                peaks, _ = _peaks()
+                out["eval_sweep_121x4_band"] = {
+                    "ms": ev_ms, "node_updates_per_s": n_upd / (ev_ms / 1e3),
+                    "achieved_gbs": 10.0 * n_upd / (ev_ms / 1e3) / 1e9,
+                    "frac_of_hbm": 10.0 * n_upd / (ev_ms / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
+                    "walk_ms": sk.ms_improve / max(sk.sweeps_improve, 1)}
+            out[start] = {"seconds": time.perf_counter() - t0, "converged": bool(s2.converged),
+                          "residual": s2.residual, "n_eval": n_eval,
+                          "evaluation": "diagonal-solved Jacobi" if solver == dp.DP_EVAL_DIAG else "sweeps",
+                          "warm_start_ms": ws_ms,
+                          "sweeps_improve": s2.sweeps_improve, "sweeps_eval": s2.sweeps_eval,
+                          "sweeps_improve_fp64": s2.sweeps_improve_fp64,
+                          "sweeps_eval_fp64": s2.sweeps_eval_fp64, "node_updates": s2.node_updates}
+        x0 = W.closed_loop_states(p2, 1024, band=(p2.energy_lo, p2.energy_hi))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ta, xf = g2.simulate(x0, p2.dt, p2.dt, 200.0)
+        out["closed_loop"] = {"states": len(x0), "seconds": time.perf_counter() - t0,
+                              "arrived": int((ta >= 0).sum()),
+                              "median_time": float(np.median(ta[ta >= 0])) if (ta >= 0).any() else None}
     c, w, gr = out["cold"], out["warm"], out["from_61x4_grid"]
     out["speedup_wall"] = c["seconds"] / max(w["seconds"], 1e-9)
     out["speedup_wall_grid_start"] = c["seconds"] / max(gr["seconds"], 1e-9)
     ct, wt = out["cold" + tuned], out["warm" + tuned]
     out["speedup_wall" + tuned] = ct["seconds"] / max(wt["seconds"], 1e-9)
     return out
+
+
+def time_pi_step(dp, torch, g, p, steps, warmup, world, local, flush, clocks=True):
+    """The benchmark step on grid g: a cold start (full tabulation) and 3 outer
+    iterations, `warmup` untimed steps, then `steps` timed steps (1 walk
+    improvement + n_eval evaluation sweeps each) with CUDA events on the grid's
+    stream, an L2 flush before each step outside its events."""
+    stream = torch.cuda.current_stream()
+    g.policy_iterate(tol=0.0, max_sweeps=3, n_eval=p.n_eval, polish=0, warm=0)
+    for _ in range(warmup):
+        g.policy_iterate(tol=0.0, max_sweeps=1, n_eval=p.n_eval, polish=0, warm=1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stats = []
+    _barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local) if clocks else None
+    if clk:
+        clk.__enter__()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        rc, st = g.policy_iterate(tol=0.0, max_sweeps=1, n_eval=p.n_eval, polish=0, warm=1, time_kernels=1)
+        ev[k][1].record(stream)
+        stats.append(st)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__()
+    _barrier(world)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    return {"ms": ms, "updates": sum(s.node_updates for s in stats), "stats": stats,
+            "clocks": clk.summary() if clk else None}
+
+
+def step_roofline(g, p, timed, key):
+    """Roofline of the step's dominant kernel, the frozen-feet evaluation
+    sweep: algorithmic bytes per sweep (V read 4 + policy 2 + V write 4 per
+    node-update) over its CUDA-event time, against the measured HBM copy
+    bandwidth."""
+    stats = timed["stats"]
+    n_upd = g.info["n_active"] - g.info["n_target"]
+    ms_eval = sum(s.ms_eval for s in stats)
+    n_eval = sum(s.sweeps_eval for s in stats)
+    ms_imp = sum(s.ms_improve for s in stats)
+    n_imp = sum(s.sweeps_improve for s in stats)
+    launches_eval = sum(s.launches for s in stats) - n_imp
+    peaks, peak_src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    eval_ms = ms_eval / max(n_eval, 1)
+    eval_bytes = 10.0 * n_upd
+    ach = eval_bytes / (eval_ms / 1e3) / 1e9
+    traffic, tsrc = _traffic(key)
+    roof = {"bound": "hbm", "kernel": "sweep_kernel<float,float,EVAL_FEET,%s> (policy evaluation at the frozen feet)"
+                                      % ("reduced" if p.reduced else "box"),
+            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "peak_source": (peak_src + " (MEASURED_PEAKS.json hbm_gbs, burst copy)") if peak_src == "measured"
+            else peak_src + " (6.8 TB/s)",
+            "traffic": traffic, "traffic_source": tsrc,
+            "algorithmic_bytes_per_sweep": eval_bytes, "avg_sweep_ms": eval_ms,
+            "sweeps_per_launch": n_eval / max(launches_eval, 1),
+            "share_of_step": ms_eval / max(timed["ms"], 1e-9)}
+    imp_ms = ms_imp / max(n_imp, 1)
+    improve = {"avg_launch_ms": imp_ms, "share_of_step": ms_imp / max(timed["ms"], 1e-9),
+               "node_updates_per_s": n_upd / (imp_ms / 1e3)}
+    return roof, improve, n_upd / (eval_ms / 1e3)
+
+
+def e2e_pi_step(dp, torch, g, p, steps, world):
+    """The same step through the C ABI with host buffers: the value (FP64) and
+    the policy go up from pinned host memory before each step and come back
+    after it, inside the timed region."""
+    V_host = torch.empty(g.n, dtype=torch.float64, pin_memory=True)
+    C_host = torch.empty(g.n, dtype=torch.int16, pin_memory=True)
+    C_view = C_host.numpy().view(np.uint16)
+    dp.dp_get_value(g.h, g.n, out=V_host.numpy())
+    C_view[:] = g.get_policy()
+    torch.cuda.synchronize()
+    _barrier(world)
+    t0 = time.perf_counter()
+    updates = 0
+    for _ in range(steps):
+        dp.dp_set_value(g.h, V_host)
+        dp.dp_set_policy(g.h, C_view)
+        rc, st = g.policy_iterate(tol=0.0, max_sweeps=1, n_eval=p.n_eval, polish=0, warm=1)
+        dp.dp_get_value(g.h, g.n, out=V_host.numpy())
+        dp.dp_get_policy(g.h, g.n, out=C_view)
+        updates += st.node_updates
+    torch.cuda.synchronize()
+    secs = _reduce_max(time.perf_counter() - t0, world)
+    return {"value": _reduce_sum(float(updates), world) / secs, "unit": UNIT, "steps": steps,
+            "h2d_bytes_per_step": g.n * (8 + 2), "d2h_bytes_per_step": g.n * (8 + 2)}
 
 
 def run_ours(args, world, rank, local):
@@ -551,63 +681,27 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl")
     build.build()
     dp.load()
-    p = W.config1()
     stream = torch.cuda.current_stream()
-    g = dp.Grid(p, stream=int(stream.cuda_stream))
-    n_upd = g.info["n_active"] - g.info["n_target"]
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
 
-    # prepare a realistic state: cold start (full tabulation) + a few steps
-    g.policy_iterate(tol=0.0, max_sweeps=3, n_eval=p.n_eval, polish=0, warm=0)
-    for _ in range(args.warmup):
-        g.policy_iterate(tol=0.0, max_sweeps=1, n_eval=p.n_eval, polish=0, warm=1)
-    torch.cuda.synchronize()
+    # --- headline: the 121^4 energy-band grid, inputs resident in HBM ---
+    p2 = W.config2()
+    g2 = dp.Grid(p2, stream=int(stream.cuda_stream))
+    timed = time_pi_step(dp, torch, g2, p2, args.steps, args.warmup, world, local, flush)
+    value, ms_max = aggregate_replicas(timed["updates"], timed["ms"], world)
+    roof, improve, eval_rate = step_roofline(g2, p2, timed, "121x4_band")
+    n_upd2 = g2.info["n_active"] - g2.info["n_target"]
+    launches = sum(s.launches for s in timed["stats"])
+    e2e = e2e_pi_step(dp, torch, g2, p2, max(1, min(args.steps, 5)), world)
 
-    # --- timed device-resident steps ---
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stats = []
-    _barrier(world)
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            rc, st = g.policy_iterate(tol=0.0, max_sweeps=1, n_eval=p.n_eval, polish=0, warm=1, time_kernels=1)
-            ev[k][1].record(stream)
-            stats.append(st)
-        torch.cuda.synchronize()
-    _barrier(world)
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    updates = sum(s.node_updates for s in stats)
-    value, ms_max = aggregate_replicas(updates, ms, world)
-    ms_eval = sum(s.ms_eval for s in stats)
-    n_eval = sum(s.sweeps_eval for s in stats)
-    ms_imp = sum(s.ms_improve for s in stats)
-    n_imp = sum(s.sweeps_improve for s in stats)
-    launches = sum(s.launches for s in stats)
-
-    # --- end to end through the C ABI with host buffers ---
-    V_host = torch.empty(g.n, dtype=torch.float64, pin_memory=True)
-    C_host = torch.empty(g.n, dtype=torch.int16, pin_memory=True)
-    C_view = C_host.numpy().view(np.uint16)
-    dp.dp_get_value(g.h, g.n, out=V_host.numpy())
-    C_view[:] = g.get_policy()
-    e2e_steps = max(1, min(args.steps, 5))
-    torch.cuda.synchronize()
-    _barrier(world)
-    t0 = time.perf_counter()
-    e2e_updates = 0
-    for _ in range(e2e_steps):
-        dp.dp_set_value(g.h, V_host)
-        dp.dp_set_policy(g.h, C_view)
-        rc, st = g.policy_iterate(tol=0.0, max_sweeps=1, n_eval=p.n_eval, polish=0, warm=1)
-        dp.dp_get_value(g.h, g.n, out=V_host.numpy())
-        dp.dp_get_policy(g.h, g.n, out=C_view)
-        e2e_updates += st.node_updates
-    torch.cuda.synchronize()
-    e2e_s = _reduce_max(time.perf_counter() - t0, world)
-    e2e_value = _reduce_sum(float(e2e_updates), world) / e2e_s
-
+    # --- the same step on the 61^4 full box ---
+    p = W.config1()
+    g = dp.Grid(p, stream=int(stream.cuda_stream))
+    t1 = time_pi_step(dp, torch, g, p, max(1, min(args.steps, 10)), args.warmup, world, local, flush, clocks=False)
+    roof1, improve1, eval_rate1 = step_roofline(g, p, t1, "61x4")
+    step_61x4 = {"value": t1["updates"] / (t1["ms"] / 1e3), "unit": UNIT, "ms_per_step": t1["ms"] / len(t1["stats"]),
+                 "config": _config(p, g.info["n_active"] - g.info["n_target"]), "roofline": roof1,
+                 "improve_sweep": improve1, "eval_sweep_node_updates_per_s": eval_rate1}
     # --- time to ||dV|| < 1e-6 (plain cold start, FP32 + FP64 polish) ---
     solve = None
     if args.solve:
@@ -692,9 +786,10 @@ def run_ours(args, world, rank, local):
                    "residual": sc.residual}
         for gc in grids:
             gc.close()
-    warm = warm_start_leg(args, dp, W, torch, g, p) if (args.warm_start and args.solve and rank == 0) else None
+    warm = warm_start_leg(args, dp, W, torch, g, p, g2) if (args.warm_start and args.solve and rank == 0) else None
     extra = extra_legs(args, dp, W, torch, g, p) if (args.extra and rank == 0) else None
     g.close()
+    g2.close()
     batch = batch_leg(args, dp, W, torch) if (args.batch and rank == 0) else None
     ex1 = example1_leg(args, dp, W, torch) if (args.example1 and rank == 0) else None
 
@@ -704,45 +799,34 @@ def run_ours(args, world, rank, local):
             dist.destroy_process_group()
         return 0
 
-    peaks, peak_src = _peaks()
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    eval_ms = ms_eval / max(n_eval, 1)
-    eval_bytes = 10.0 * n_upd        # V read 4 B + policy 2 B + V write 4 B per node
-    ach = eval_bytes / (eval_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": "sweep_kernel<float,float,EVAL> (policy evaluation)",
-            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
-            "traffic": EVAL_TRAFFIC_61X4, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum "
-                                                              "of this kernel, mean of two launches (sweep-kernel profile)",
-            "algorithmic_bytes_per_launch": eval_bytes, "avg_launch_ms": eval_ms,
-            "share_of_step": ms_eval / max(ms, 1e-9)}
-    imp_ms = ms_imp / max(n_imp, 1)
-
-    cpu_rate, cpu_info = oracle_step_rate(p, seconds_target=args.cpu_seconds) if args.cpu_seconds > 0 else (None, {})
+    cpu_rate, cpu_info = None, {}
+    if args.cpu_seconds > 0:
+        sample = OracleSample(p2)
+        cpu_rate, cpu_info = sample.step_rate(seconds_target=args.cpu_seconds)
+        del sample
     par_rate, par_info = (oracle_parallel_rate(args.cpu_seconds / 2) if (args.cpu_seconds > 0 and args.cpu_parallel)
                           else (None, {}))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(_config(p), parallelism="replicas" if world > 1 else "single"),
-        "clocks": clk.summary(),
-        "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
-                "h2d_bytes_per_step": g.n * (8 + 2), "d2h_bytes_per_step": g.n * (8 + 2)},
+        "config": dict(_config(p2, n_upd2), parallelism="replicas" if world > 1 else "single"),
+        "clocks": timed["clocks"],
+        "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": roof,
-        "improve_sweep": {"avg_launch_ms": imp_ms, "share_of_step": ms_imp / max(ms, 1e-9),
-                          "node_updates_per_s": n_upd / (imp_ms / 1e3)},
-        "eval_sweep_node_updates_per_s": n_upd / (eval_ms / 1e3),
+        "improve_sweep": improve,
+        "eval_sweep_node_updates_per_s": eval_rate,
         "cpu_baseline": None if cpu_rate is None else {
             "value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d sampled nodes of the 61^4 grid x (1 walk improvement + %d evaluations), %d reps, "
-                      "%.1f s FP64 single thread" % (cpu_info["nodes"], p.n_eval, cpu_info["reps"],
+            "sample": "%d sampled stored nodes of the 121^4 band x (1 walk improvement + %d evaluations), %d reps, "
+                      "%.1f s FP64 single thread" % (cpu_info["nodes"], p2.n_eval, cpu_info["reps"],
                                                       cpu_info["seconds"])},
         "cpu_baseline_all_cores": None if par_rate is None else {
             "value": par_rate, "unit": UNIT, "cores": par_info["procs"], "kind": "oracle",
-            "sample": "one spawned oracle process per core, each on its own 2,000-node sample of the 61^4 step "
-                      "mix, %.1f s" % par_info["seconds"]},
+            "sample": "one spawned oracle process per core (at most 8), each on its own 2,000-node sample of the "
+                      "band step mix, %.1f s" % par_info["seconds"]},
+        "step_61x4": step_61x4,
         "time_to_tol": solve,
         "time_to_tol_n_eval_tuned": solve_tuned,
         "time_to_tol_diag": solve_diag,

@@ -180,7 +180,6 @@ def smooth_value(p: Problem, seed: int) -> np.ndarray:
     control choice a near-tie."""
     rng = np.random.default_rng(seed)
     axes = [np.linspace(0.0, 1.0, k) for k in p.n]
-    g = np.meshgrid(*axes, indexing="ij")
     f = np.zeros(p.n)
     for _ in range(6):
         k = rng.uniform(0.5, 2.5, size=4)
@@ -188,7 +187,10 @@ def smooth_value(p: Problem, seed: int) -> np.ndarray:
         a = rng.uniform(0.2, 1.0)
         term = a
         for d in range(4):
-            term = term * np.cos(np.pi * k[d] * g[d] + ph[d])
+            # one axis at a time, broadcast (no full-size coordinate arrays)
+            shape = [1, 1, 1, 1]
+            shape[d] = p.n[d]
+            term = term * np.cos(np.pi * k[d] * axes[d] + ph[d]).reshape(shape)
         f = f + term
     f = (f - f.min()) / (f.max() - f.min() + 1e-300)
     return (0.05 + 0.9 * f).reshape(-1) * p.M()
