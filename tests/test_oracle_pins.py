@@ -414,6 +414,56 @@ def test_closed_loop_1d_arrival_time():
     assert xf[:, 0] == pytest.approx([1.5, 1.5, 1.5], abs=1e-12)
 
 
+def _unit_1d_closed_form(p, target_node=8):
+    """V of the 1-D unit-speed problem on the full box: dt (1 - beta^n) /
+    (1 - beta), n the grid distance to the target node (dt = h)."""
+    n = np.abs(np.arange(p.n[0]) - target_node)
+    exact = p.dt * (1 - p.beta ** n) / (1 - p.beta)
+    return np.repeat(exact, np.prod(p.n[1:])), n
+
+
+def test_feedback_with_its_own_step_tau_closed_form():
+    # Eq. (15) with a feedback step tau = k dt (the paper takes dt = o(tau)).
+    # In the 1-D unit-speed problem the foot of a node moves k cells, so
+    # towards the target q = tau * 1 + beta^(tau / dt) V(n - k), with V the
+    # closed form.  A discount of beta instead of beta^(tau / dt), or a running
+    # cost dt instead of tau, misses it by O(dt).
+    p = W.unit_speed_1d(beta=0.95)
+    o = oracle.Oracle(p)
+    V, n = _unit_1d_closed_form(p)
+    for k in (2, 3):
+        tau = k * p.dt
+        idx = np.flatnonzero(n >= k)
+        states = np.zeros((len(idx), 4)) + 1.0
+        states[:, 0] = 1.0 + idx * p.dt
+        codes, q = o.feedback(V, states, tau=tau)
+        d = np.abs(idx - 8) - k                       # grid distance after the step
+        v_after = p.dt * (1 - p.beta ** d) / (1 - p.beta)
+        want = tau + p.beta ** k * v_after
+        assert np.abs(q - want).max() < 1e-13, (k, np.abs(q - want).max())
+        assert (codes[idx < 8] == 0).all() and (codes[idx > 8] == 32768).all()
+        # neither the discount of one grid step nor the running cost of one
+        # would do (where the foot is not in the target, V > 0 there)
+        far = d > 0
+        assert np.abs(tau + p.beta * v_after - want)[far].min() > 1e-4
+        assert np.abs(p.dt + p.beta ** k * v_after - want).min() > 1e-4
+
+
+def test_closed_loop_1d_with_unequal_feedback_and_rk4_steps():
+    # The closed loop re-decides the control every RK4 step h and looks ahead
+    # by tau; unit speed is integrated exactly by RK4, so from grid distance n
+    # the state reaches the target after n dt whatever tau and h (h dividing
+    # dt), and the arrival time is counted in steps of h.
+    p = W.unit_speed_1d()
+    o = oracle.Oracle(p)
+    V, _ = _unit_1d_closed_form(p)
+    x0 = np.array([[1.0, 1.0, 1.0, 1.0], [2.0, 1.5, 1.0, 1.0], [1.0 + 3 * p.dt, 1.0, 1.0, 1.0]])
+    for tau, h in ((2 * p.dt, p.dt / 2), (3 * p.dt, p.dt / 3), (p.dt, p.dt / 4), (2 * p.dt, p.dt)):
+        ta, xf = o.simulate(V, x0, tau=tau, h=h, t_max=2.0)
+        assert ta == pytest.approx([8 * p.dt, 8 * p.dt, 5 * p.dt], abs=1e-12), (tau, h, ta)
+        assert xf[:, 0] == pytest.approx([1.5, 1.5, 1.5], abs=1e-12)
+
+
 # ------------------------------------------ the paper's Example 1 (§4) --
 
 def _ellipse_state(mu, a, e, omega, nu):
