@@ -7,6 +7,14 @@ GELU (exact erf form) after the three hidden layers, linear output
 the three outputs.  Plain numpy in float64, one layer at a time; the
 backward pass is pinned by central finite differences in the tests.
 
+forward_bf16 / backward_bf16 are the same network with BF16 rounding (round
+to nearest even) applied where a tensor-core implementation with BF16
+operands and FP32 accumulation rounds: the hidden activations, the weights
+of the two 256 x 256 layers and the back-propagated pre-activation
+gradients.  Everything else stays FP64, so the GPU path differs from them only
+by FP32 accumulation and by isolated one-unit rounding flips, which lets a
+test check its outputs element by element.
+
 Only the test suite uses this module.
 """
 from __future__ import annotations
@@ -74,6 +82,54 @@ def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
             mh = m / (1 - b1 ** t)
             vh = v / (1 - b2 ** t)
             layer[pi] -= lr * mh / (np.sqrt(vh) + eps)
+
+
+def bf16(a):
+    """Round to BF16 (8 significant bits, round to nearest even) through FP32,
+    returned as float64.  Finite inputs of FP32 range only."""
+    x = np.ascontiguousarray(np.asarray(a, np.float64).astype(np.float32))
+    b = x.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16 << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(params, X):
+    """Forward pass with BF16 hidden activations and BF16 weights of layers 2
+    and 3 (inputs, layer 1 and the output layer in full precision).  Returns
+    the output and the per-layer (input, pre-activation) pairs."""
+    a = np.asarray(X, np.float32).astype(np.float64)
+    cache = []
+    last = len(params) - 1
+    for li, (W, b) in enumerate(params):
+        W = np.asarray(W, np.float32).astype(np.float64)
+        b = np.asarray(b, np.float32).astype(np.float64)
+        if 0 < li < last:
+            W = bf16(W)
+        z = a @ W.T + b
+        cache.append((a, z))
+        a = bf16(gelu(z)) if li < last else z
+    return a, cache
+
+
+def backward_bf16(params, cache, Y, T):
+    """Gradients of the mean squared error for forward_bf16: the gradients of
+    the pre-activations of the hidden layers are rounded to BF16 before they
+    are propagated and reduced, and layers 2 and 3 back-propagate through
+    their BF16 weights."""
+    n = Y.size
+    d = 2.0 * (Y - T) / n
+    grads = [None] * len(params)
+    last = len(params) - 1
+    for li in range(last, -1, -1):
+        a_in, z = cache[li]
+        if li < last:
+            d = bf16(d * gelu_grad(z))
+        W = np.asarray(params[li][0], np.float32).astype(np.float64)
+        if 0 < li < last:
+            W = bf16(W)
+        grads[li] = [d.T @ a_in, d.sum(axis=0)]
+        d = d @ W
+    return grads
 
 
 def normalise_states(X, lo, hi):

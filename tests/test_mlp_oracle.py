@@ -71,3 +71,44 @@ def test_normalisation_maps_box_to_unit_cube():
     X = np.array([lo, hi, [(a + b) / 2 for a, b in zip(lo, hi)]])
     N = mlp.normalise_states(X, lo, hi)
     assert np.allclose(N, [[-1] * 4, [1] * 4, [0] * 4], atol=1e-12)
+
+
+def test_bf16_rounding_pins():
+    # values with at most 8 significant bits are exact; round to nearest even
+    # at the midpoint between two BF16 neighbours; relative error <= 2^-8
+    # (half a unit of the 8th significant bit; the FP32 step adds 2^-24)
+    exact = np.array([0.0, 1.0, -1.5, 0.75, 2.0 ** -20, 3.0 * 2 ** 10, 255.0, -1.0 / 128])
+    assert (mlp.bf16(exact) == exact).all()
+    assert mlp.bf16(np.array([1.0 + 2.0 ** -8]))[0] == 1.0                    # tie to even (1.0)
+    assert mlp.bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6    # tie to even (up)
+    assert mlp.bf16(np.array([1.0 + 2.0 ** -8 + 2.0 ** -20]))[0] == 1.0 + 2.0 ** -7
+    x = np.random.default_rng(0).normal(size=10000) * 10.0 ** np.random.default_rng(1).uniform(-6, 6, 10000)
+    r = mlp.bf16(x)
+    assert (np.abs(r - x) <= (2.0 ** -8 + 2.0 ** -24) * np.abs(x)).all()
+    assert (mlp.bf16(r) == r).all()
+
+
+def test_bf16_reference_is_the_fp64_network_with_rounded_operands():
+    # without the roundings (all values already representable) the BF16
+    # reference is the FP64 network; with them it moves by O(2^-8) of scale
+    rng = np.random.default_rng(4)
+    params = W.mlp_init_params(seed=6)
+    X = rng.uniform(-1, 1, size=(64, 4))
+    T = rng.uniform(-1, 1, size=(64, 3))
+    Y, cache = mlp.forward(params, X)
+    Yb, cache_b = mlp.forward_bf16(params, X)
+    scale = np.abs(Y).max()
+    assert 0 < np.abs(Yb - Y).max() <= 2e-2 * scale
+    g = mlp.backward(params, cache, Y, T)
+    gb = mlp.backward_bf16(params, cache_b, Yb, T)
+    for li in range(4):
+        for pi in range(2):
+            rel = np.linalg.norm(gb[li][pi] - g[li][pi]) / np.linalg.norm(g[li][pi])
+            assert rel < 5e-2, (li, pi, rel)
+    # a network whose operands are exactly representable: identical results
+    params_r = [[mlp.bf16(Wt), mlp.bf16(bv)] for Wt, bv in params]
+    Xr = mlp.bf16(X)
+    Y1, c1 = mlp.forward(params_r, Xr)
+    Y2, c2 = mlp.forward_bf16(params_r, Xr)
+    # hidden activations still round, so compare the first layer's pre-activation
+    assert np.array_equal(c1[0][1], c2[0][1])
