@@ -181,6 +181,14 @@ typedef struct dp_solve_opts {
                               DP_ETIMEOUT                                    */
 } dp_solve_opts;
 
+/* Test hook for the bounded waits of the multi-level evaluation
+ * (eval_levels > 1): a launch whose chunk waits longer than ns nanoseconds for
+ * the previous sweep gives up, every block of it returns, and the call
+ * returns DP_ETIMEOUT with the value not valid (a later call starts clean).
+ * ns >= 0 (0: give up at the first unmet dependency), -1 restores the default
+ * of 2 s.  Process-wide. */
+int dp_set_wave_wait_limit(int64_t ns);
+
 /* Solver statistics (filled on DP_OK and on DP_ENOCONV). */
 typedef struct dp_solve_stats {
     int64_t sweeps_vi;
@@ -347,6 +355,20 @@ int dp_mlp_forward(dp_mlp* mlp, const double* states, int32_t n, float* out);
  * capacity) with respect to every parameter, and the loss; no update. */
 int dp_mlp_gradients(dp_mlp* mlp, const double* states, const float* targets, int32_t n, float* grads,
                      float* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step size lr; the step
+ * count and moments carry over from earlier steps and dp_mlp_train_grid)
+ * with a caller-supplied gradient of count = dp_mlp_param_count() entries,
+ * in the flat parameter order of dp_mlp_set_params: for gradients computed
+ * elsewhere (dp_mlp_gradients, or another process).  Synchronises the
+ * network's stream. */
+int dp_mlp_apply_gradients(dp_mlp* mlp, const float* grads, int64_t count, double lr);
+/* Test hook for the bounded wait of the tensor-core GEMMs: the number of
+ * polls of each GEMM's wait for its MMAs before it gives up (polls >= 0; 0
+ * gives up at once), -1 restores the default (2^22).  A GEMM that gives up
+ * sets an error flag, still waits (with the default limit) for the MMAs it
+ * committed, skips its epilogue, frees its TMEM and returns; the call then
+ * returns DP_ETIMEOUT and clears the flag, so the next call runs normally. */
+int dp_mlp_set_wait_limit(dp_mlp* mlp, int32_t polls);
 /* Trains on every stored node of a grid: targets V / M and the (cos, sin) of
  * the grid's resident value and policy.  stats nullable. */
 int dp_mlp_train_grid(dp_mlp* mlp, dp_grid* grid, const dp_mlp_train_opts* opts, dp_mlp_train_stats* stats);

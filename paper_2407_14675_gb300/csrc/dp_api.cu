@@ -397,6 +397,9 @@ int wave_levels(const dp_grid* g, const dp_solve_opts* o)
     return 1;
 }
 
+// Limit of each bounded wait of the multi-level evaluation (test hook).
+unsigned long long g_wave_timeout_ns = kWaveTimeoutNs;
+
 // Levels e0 .. e0 + k - 1 of the n evaluation sweeps after an improvement as
 // one launch; t = sweep index of level 0.  FP32 values: plain or
 // diagonal-solved evaluation at the frozen feet.  FP64 values (mix): the
@@ -423,6 +426,7 @@ cudaError_t enqueue_wave(dp_grid* g, bool mix, bool diag, int c, int e0, int n, 
     a.sweep = t;
     a.check_prev = check_prev;
     a.tol = tol;
+    a.timeout_ns = g_wave_timeout_ns;
     // buffers as enqueue_sweep / enqueue_increment alternate them
     a.in0 = mix ? (e0 & 1) : (int)((g->cur + t) & 1);
     const int mode = mix ? (diag ? kIncrDiag : kIncr) : (diag ? kEvalFeetDiag : kEvalFeet);
@@ -1446,6 +1450,13 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
     if (!S.converged)
         return fail(DP_ENOCONV, "no convergence within %lld improvement sweeps (residual %g)",
                     (long long)o->max_sweeps, res);
+    return DP_OK;
+}
+
+int dp_set_wave_wait_limit(int64_t ns)
+{
+    if (ns < -1) return fail(DP_EINVAL, "bad wait limit");
+    g_wave_timeout_ns = ns >= 0 ? (unsigned long long)ns : kWaveTimeoutNs;
     return DP_OK;
 }
 

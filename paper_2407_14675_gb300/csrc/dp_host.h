@@ -73,6 +73,7 @@ struct WaveArgs {
     long long sweep;                       // ring slot of level 0
     int check_prev;
     double tol;
+    unsigned long long timeout_ns;         // limit of each wait (kWaveTimeoutNs unless a test sets it)
 };
 
 // mode: kEvalFeet, kEvalFeetDiag, kIncr or kIncrDiag.  Zeroes a.sync first.

@@ -100,7 +100,7 @@ template <int EPI, int KC>
 __global__ void __launch_bounds__(128)
 mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb, int k_per_cta,
                 const float* __restrict__ bias, float* __restrict__ zout, const float* __restrict__ zin,
-                bf16* __restrict__ hout, float* __restrict__ cacc, int* __restrict__ err)
+                bf16* __restrict__ hout, float* __restrict__ cacc, int* __restrict__ err, int polls)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                        // 128 x KC bf16
@@ -154,9 +154,12 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
             }
             umma_commit(&mbar);
         }
-        if (!mbar_wait(&mbar, phase, kWaitPolls)) {
+        if (!mbar_wait(&mbar, phase, polls)) {
+            // give up (error flag), but let the committed MMAs finish before
+            // the accumulator is freed and the staging buffers are released
             ok = false;
             if (lane == 0) atomicOr(err, 1);
+            mbar_wait(&mbar, phase, kWaitPolls);
         }
         phase ^= 1;
         __syncthreads();
@@ -222,7 +225,8 @@ constexpr int kPersistParts = kPersistThreads / 128;            // column parts 
 
 __global__ void __launch_bounds__(kPersistThreads)
 mlp_fwd_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb, int tiles,
-                          const float* __restrict__ bias, bf16* __restrict__ hout, int* __restrict__ err)
+                          const float* __restrict__ bias, bf16* __restrict__ hout, int* __restrict__ err,
+                          int polls)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sB = smem;                                  // 128 x 256
@@ -274,9 +278,10 @@ mlp_fwd_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __res
         // reader, the previous tile's MMAs, has completed)
         const int tn = t + gridDim.x;
         if (tn < tiles) stage(sA[buf ^ 1], A, (size_t)lda, (size_t)tn * kTileM);
-        if (!mbar_wait(&mbar, phase, kWaitPolls)) {
+        if (!mbar_wait(&mbar, phase, polls)) {
             ok = false;
             if (lane == 0) atomicOr(err, 1);
+            mbar_wait(&mbar, phase, kWaitPolls);   // the committed MMAs finish first
         }
         phase ^= 1;
         fence_after_sync();
@@ -573,6 +578,7 @@ struct dp_mlp {
     int* err = nullptr;
     float* h_loss = nullptr;           // pinned
     int* h_err = nullptr;
+    int wait_polls = kWaitPolls;       // polls of the first wait for the MMAs (test hook)
 };
 
 namespace {
@@ -617,7 +623,7 @@ cudaError_t gemm_kc(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, i
     }
     dim3 grid(rows / kTileM, kH / kTileN, k_split);
     mlp_gemm_kernel<EPI, KC><<<grid, 128, gemm_smem(KC), m->st>>>(A, lda, B, ldb, k_total / k_split, bias, zout, zin,
-                                                                   hout, cacc, m->err);
+                                                                   hout, cacc, m->err, m->wait_polls);
     return cudaGetLastError();
 }
 
@@ -642,7 +648,7 @@ cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int 
         const int per_half = std::max(1, std::min(tiles, m->sm_count / 2));
         dim3 grid(per_half, kH / kTileN);
         mlp_fwd_persistent_kernel<<<grid, kPersistThreads, kPersistSmem, m->st>>>(A, lda, B, ldb, tiles, bias, hout,
-                                                                                  m->err);
+                                                                                  m->err, m->wait_polls);
         return cudaGetLastError();
     }
     if (EPI != kEpiAtomic && rows >= kManyRows)
@@ -710,11 +716,31 @@ int backward(dp_mlp* m, int count)
     return DP_OK;
 }
 
+// One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the gradient in m->G,
+// then the BF16 copies of the weights.
+int adam_step(dp_mlp* m, double lr)
+{
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    ++m->step;
+    const float bc1 = 1.0f - powf(b1, (float)m->step), bc2 = 1.0f - powf(b2, (float)m->step);
+    adam_kernel<<<(kParams + 255) / 256, 256, 0, m->st>>>(m->P, m->G, m->Am, m->Av, kParams, (float)lr, b1, b2, eps,
+                                                          bc1, bc2);
+    MCK(cudaGetLastError());
+    return refresh_bf16(m);
+}
+
 int check_err(dp_mlp* m)
 {
     MCK(cudaMemcpyAsync(m->h_err, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->st));
     MCK(cudaStreamSynchronize(m->st));
-    if (*m->h_err) return record_error(DP_ETIMEOUT, "a tensor-core GEMM gave up waiting for its MMAs");
+    if (*m->h_err) {
+        // the kernels that gave up drained their MMAs and freed their TMEM:
+        // clear the flag so that the next call starts clean
+        *m->h_err = 0;
+        MCK(cudaMemsetAsync(m->err, 0, sizeof(int), m->st));
+        MCK(cudaStreamSynchronize(m->st));
+        return record_error(DP_ETIMEOUT, "a tensor-core GEMM gave up waiting for its MMAs");
+    }
     return DP_OK;
 }
 
@@ -831,6 +857,25 @@ int dp_mlp_gradients(dp_mlp* m, const double* states, const float* targets, int3
     return DP_OK;
 }
 
+int dp_mlp_apply_gradients(dp_mlp* m, const float* grads, int64_t count, double lr)
+{
+    if (!m || !grads) return record_error(DP_EINVAL, "NULL argument");
+    if (count != kParams) return record_error(DP_EINVAL, "parameter count mismatch");
+    if (!(lr > 0)) return record_error(DP_EINVAL, "lr must be positive");
+    MCK(cudaMemcpyAsync(m->G, grads, sizeof(float) * kParams, cudaMemcpyHostToDevice, m->st));
+    int rc = adam_step(m, lr);
+    if (rc) return rc;
+    MCK(cudaStreamSynchronize(m->st));
+    return DP_OK;
+}
+
+int dp_mlp_set_wait_limit(dp_mlp* m, int32_t polls)
+{
+    if (!m || polls < -1) return record_error(DP_EINVAL, "bad argument");
+    m->wait_polls = polls >= 0 ? polls : kWaitPolls;
+    return DP_OK;
+}
+
 int dp_mlp_train_grid(dp_mlp* m, dp_grid* grid, const dp_mlp_train_opts* o, dp_mlp_train_stats* stats)
 {
     if (!m || !grid || !o) return record_error(DP_EINVAL, "NULL argument");
@@ -859,7 +904,6 @@ int dp_mlp_train_grid(dp_mlp* m, dp_grid* grid, const dp_mlp_train_opts* o, dp_m
         return z ^ (z >> 31);
     };
     auto gcd = [](unsigned long long a, unsigned long long b) { while (b) { unsigned long long t = a % b; a = b; b = t; } return a; };
-    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     for (int ep = 0; ep < o->epochs; ++ep) {
         unsigned long long mult = (next() % (unsigned long long)n) | 1ull;
         while (gcd(mult, (unsigned long long)n) != 1) mult = (mult + 2) % (unsigned long long)n;
@@ -877,12 +921,7 @@ int dp_mlp_train_grid(dp_mlp* m, dp_grid* grid, const dp_mlp_train_opts* o, dp_m
             MCK(cudaGetLastError());
             if ((rc = forward(m, B, true, m->t, 1.0f / (3.0f * B)))) return rc;
             if ((rc = backward(m, B))) return rc;
-            ++m->step;
-            const float bc1 = 1.0f - powf(b1, (float)m->step), bc2 = 1.0f - powf(b2, (float)m->step);
-            adam_kernel<<<(kParams + 255) / 256, 256, 0, m->st>>>(m->P, m->G, m->Am, m->Av, kParams, (float)o->lr, b1,
-                                                                  b2, eps, bc1, bc2);
-            MCK(cudaGetLastError());
-            if ((rc = refresh_bf16(m))) return rc;
+            if ((rc = adam_step(m, o->lr))) return rc;
         }
         MCK(cudaMemcpyAsync(m->h_loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->st));
         if ((rc = check_err(m))) return rc;

@@ -26,7 +26,7 @@
 // resident blocks.  Completion is counted per level and per group of G chunks;
 // a block that finished a chunk publishes it with a fence and an atomic add
 // (release), a block about to start one polls the counters of its range and
-// fences (acquire).  Every wait is bounded (kWaveTimeoutNs): past it the
+// fences (acquire).  Every wait is bounded (kWaveTimeoutNs, 2 s): past it the
 // block sets ctl->wave_err, every other block gives up at its next poll, and
 // the host reports DP_ETIMEOUT.
 #pragma once
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kWaveBlock, 3) wave_kernel(const __grid_consta
                     }
                     const unsigned long long now = global_ns();
                     if (poll == 0) t0 = now;
-                    else if (now - t0 > kWaveTimeoutNs) {
+                    else if (now - t0 > a.timeout_ns) {
                         if (lane == 0) atomicOr(&ctl->wave_err, 1);
                         lev = -2;
                         break;

@@ -206,6 +206,9 @@ def load(path: Optional[str] = None):
         "dp_mlp_forward": [_P, _P, C.c_int32, _P],
         "dp_mlp_gradients": [_P, _P, _P, C.c_int32, _P, C.POINTER(C.c_float)],
         "dp_mlp_train_grid": [_P, _P, C.POINTER(dp_mlp_train_opts), C.POINTER(dp_mlp_train_stats)],
+        "dp_mlp_apply_gradients": [_P, _P, C.c_int64, C.c_double],
+        "dp_set_wave_wait_limit": [C.c_int64],
+        "dp_mlp_set_wait_limit": [_P, C.c_int32],
         "dp_warm_start": [_P, _P, _dp],
         "dp_warm_start_from_grid": [_P, _P, _dp],
         "dp_batch_create": [_P, C.c_int32, _P, C.POINTER(_P)],
@@ -640,6 +643,19 @@ def dp_mlp_gradients(mlp: int, states, targets):
     _check(load().dp_mlp_gradients(mlp, _host_ptr(st, np.float64), _host_ptr(tg, np.float32), len(st),
                                    _host_ptr(g, np.float32), C.byref(loss)))
     return g, loss.value
+
+
+def dp_mlp_apply_gradients(mlp: int, grads, lr=1e-3):
+    g = np.ascontiguousarray(grads, np.float32)
+    _check(load().dp_mlp_apply_gradients(mlp, _host_ptr(g, np.float32), len(g), lr))
+
+
+def dp_set_wave_wait_limit(ns: int):
+    _check(load().dp_set_wave_wait_limit(ns))
+
+
+def dp_mlp_set_wait_limit(mlp: int, polls: int):
+    _check(load().dp_mlp_set_wait_limit(mlp, polls))
 
 
 def dp_mlp_train_grid(mlp: int, grid: int, epochs=4, batch=4096, lr=1e-3, seed=14675):
