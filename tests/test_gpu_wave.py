@@ -77,3 +77,22 @@ def test_multi_level_solve_to_tolerance_matches(dp):
     assert out[0][2] and out[1][2]
     assert out[0][3:] == out[1][3:]
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_multi_level_wait_limit_gives_up_cleanly(dp):
+    """Test hook: with a wait limit of 0 the first unmet dependency makes the
+    launch give up (on 17^4 every chunk of a level depends on every chunk of
+    the previous one, and the blocks waiting for level 1 start while level 0
+    runs): the call returns DP_ETIMEOUT, no block hangs, and with the default
+    limit restored the next solve is bit-identical to one sweep per launch."""
+    p = W.config1(n=17)
+    dp.dp_set_wave_wait_limit(0)
+    try:
+        with dp.Grid(p) as g:
+            with pytest.raises(dp.DPError) as e:
+                g.policy_iterate(tol=0.0, max_sweeps=2, n_eval=20, polish=0, warm=0, eval_levels=20)
+            assert e.value.code == dp.DP_ETIMEOUT
+    finally:
+        dp.dp_set_wave_wait_limit(-1)
+    ref = _solve(dp, p, 1, max_sweeps=3, n_eval=20, polish=0)
+    _same(ref, _solve(dp, p, 20, max_sweeps=3, n_eval=20, polish=0), "after a timeout")
