@@ -279,7 +279,7 @@ def _config(p, n_upd=None):
                       "1 walk+golden improvement (64 angles) + 20 evaluation sweeps per step" % p.n[0]),
          "grid": list(p.n), "box_nodes": p.nodes, "n_angles": p.n_angles, "n_eval": p.n_eval,
          "accel": p.accel, "dt": p.dt, "beta": p.beta,
-         "l2": ("flushed between steps (256 MiB write); per-sweep working set %s > 129 MB L2" %
+         "l2": ("flushed before the timed steps (256 MiB write); every sweep streams %s > 129 MB of L2" %
                 ("1.12 GB" if band else "276 MB"))}
     if n_upd is not None:
         d["node_updates_per_sweep"] = int(n_upd)
@@ -564,6 +564,29 @@ def warm_start_leg(args, dp, W, torch, g1, p1, g2):
                           "sweeps_improve": s2.sweeps_improve, "sweeps_eval": s2.sweeps_eval,
                           "sweeps_improve_fp64": s2.sweeps_improve_fp64,
                           "sweeps_eval_fp64": s2.sweeps_eval_fp64, "node_updates": s2.node_updates}
+        if args.fp64_band:
+            # the plain FP64 GPU solve of the same grid (no network, no FP32
+            # phase), cold, to the same tolerance: with the diagonal-solved
+            # evaluation and, with --fp64-band 2, with plain sweeps too
+            p64 = p2.replace(precision=W.FP64)
+            kinds = [("diag", args.diag_n_eval, dp.DP_EVAL_DIAG)]
+            if args.fp64_band > 1:
+                kinds.append(("sweeps", p2.n_eval, dp.DP_EVAL_JACOBI))
+            with dp.Grid(p64, stream=int(torch.cuda.current_stream().cuda_stream)) as g64:
+                for name, n_eval, solver in kinds:
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    rc, s64 = g64.policy_iterate(tol=1e-6, max_sweeps=args.solve_max, n_eval=n_eval, warm=0,
+                                                 eval_solver=solver)
+                    torch.cuda.synchronize()
+                    out["plain_fp64_" + name] = {
+                        "seconds": time.perf_counter() - t0, "converged": bool(s64.converged),
+                        "residual": s64.residual, "n_eval": n_eval, "improvements": s64.sweeps_improve,
+                        "evaluation_sweeps": s64.sweeps_eval}
+                    if name == "diag":
+                        v64 = g64.get_value()
+                        err = np.abs(v64 - V_cold)
+                        out["plain_fp64_diag"]["max_abs_diff_to_fp32_polish_solve"] = float(err.max())
         x0 = W.closed_loop_states(p2, 1024, band=(p2.energy_lo, p2.energy_hi))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -576,38 +599,49 @@ def warm_start_leg(args, dp, W, torch, g1, p1, g2):
     out["speedup_wall_grid_start"] = c["seconds"] / max(gr["seconds"], 1e-9)
     ct, wt = out["cold" + tuned], out["warm" + tuned]
     out["speedup_wall" + tuned] = ct["seconds"] / max(wt["seconds"], 1e-9)
+    if "plain_fp64_diag" in out:
+        # the learned warm-started FP32 solve (network inference included,
+        # training not) against the plain FP64 GPU solve of the same grid
+        f64 = out["plain_fp64_diag"]
+        cmp_ = {"learned_fp32_diag_seconds": wt["seconds"], "plain_fp64_diag_seconds": f64["seconds"],
+                "speedup_diag": f64["seconds"] / max(wt["seconds"], 1e-9),
+                "learned_fp32_sweeps_seconds": w["seconds"],
+                "training_seconds": out["train"]["wall_s"]}
+        if "plain_fp64_sweeps" in out:
+            cmp_["plain_fp64_sweeps_seconds"] = out["plain_fp64_sweeps"]["seconds"]
+            cmp_["speedup_sweeps"] = out["plain_fp64_sweeps"]["seconds"] / max(w["seconds"], 1e-9)
+        out["learned_fp32_vs_plain_fp64"] = cmp_
     return out
 
 
 def time_pi_step(dp, torch, g, p, steps, warmup, world, local, flush, clocks=True):
     """The benchmark step on grid g: a cold start (full tabulation) and 3 outer
     iterations, `warmup` untimed steps, then `steps` timed steps (1 walk
-    improvement + n_eval evaluation sweeps each) with CUDA events on the grid's
-    stream, an L2 flush before each step outside its events."""
+    improvement + n_eval evaluation sweeps each) as one policy-iteration call
+    of `steps` outer iterations, between CUDA events on the grid's stream.
+    L2 is flushed once before the timed region; between the steps each sweep
+    streams more than L2 holds (1.12 GB on the band grid, 276 MB on 61^4)."""
     stream = torch.cuda.current_stream()
     g.policy_iterate(tol=0.0, max_sweeps=3, n_eval=p.n_eval, polish=0, warm=0)
-    for _ in range(warmup):
-        g.policy_iterate(tol=0.0, max_sweeps=1, n_eval=p.n_eval, polish=0, warm=1)
+    if warmup:
+        g.policy_iterate(tol=0.0, max_sweeps=warmup, n_eval=p.n_eval, polish=0, warm=1)
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    stats = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
     _barrier(world)
     torch.cuda.synchronize()
     clk = ClockSampler(local) if clocks else None
     if clk:
         clk.__enter__()
-    for k in range(steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        rc, st = g.policy_iterate(tol=0.0, max_sweeps=1, n_eval=p.n_eval, polish=0, warm=1, time_kernels=1)
-        ev[k][1].record(stream)
-        stats.append(st)
+    e0.record(stream)
+    rc, st = g.policy_iterate(tol=0.0, max_sweeps=steps, n_eval=p.n_eval, polish=0, warm=1, time_kernels=1)
+    e1.record(stream)
     torch.cuda.synchronize()
     if clk:
         clk.__exit__()
     _barrier(world)
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    return {"ms": ms, "updates": sum(s.node_updates for s in stats), "stats": stats,
+    assert st.sweeps_improve == steps and st.sweeps_eval == steps * p.n_eval, st.asdict()
+    return {"ms": e0.elapsed_time(e1), "updates": st.node_updates, "stats": [st], "steps": steps,
             "clocks": clk.summary() if clk else None}
 
 
@@ -699,7 +733,7 @@ def run_ours(args, world, rank, local):
     g = dp.Grid(p, stream=int(stream.cuda_stream))
     t1 = time_pi_step(dp, torch, g, p, max(1, min(args.steps, 10)), args.warmup, world, local, flush, clocks=False)
     roof1, improve1, eval_rate1 = step_roofline(g, p, t1, "61x4")
-    step_61x4 = {"value": t1["updates"] / (t1["ms"] / 1e3), "unit": UNIT, "ms_per_step": t1["ms"] / len(t1["stats"]),
+    step_61x4 = {"value": t1["updates"] / (t1["ms"] / 1e3), "unit": UNIT, "ms_per_step": t1["ms"] / t1["steps"],
                  "config": _config(p, g.info["n_active"] - g.info["n_target"]), "roofline": roof1,
                  "improve_sweep": improve1, "eval_sweep_node_updates_per_s": eval_rate1}
     # --- time to ||dV|| < 1e-6 (plain cold start, FP32 + FP64 polish) ---
@@ -855,6 +889,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--warm-start", type=int, default=1, help="train the network, compare cold/warm 121^4 solves")
     ap.add_argument("--mlp-epochs", type=int, default=2)
+    ap.add_argument("--fp64-band", type=int, default=1,
+                    help="plain FP64 solve of the band grid: 0 none, 1 diagonal-solved evaluation, 2 also plain sweeps")
     ap.add_argument("--batch", type=int, default=1, help="time the 256-transfer batch")
     ap.add_argument("--extra", type=int, default=1, help="17^4 FP64 VI; walk vs full tabulation")
     ap.add_argument("--cpu-parallel", type=int, default=1, help="also time the oracle on every host core")
