@@ -563,18 +563,20 @@ __host__ __device__ constexpr bool eval_prefetch()
 // covers that many consecutive nodes, whose corner lines overlap (a node's
 // v_t neighbours lie 61 nodes on, on the 61^4 grid), so larger blocks take
 // more of their gathers from L1: 1024 threads (2 blocks per SM) for the
-// evaluation sweeps, 768 (2 per SM at 40 registers) for the increment sweeps
-// and for the diagonal-solved evaluation of the reduced grid, 1024 (one per SM
-// at 64 registers) for the FP64 evaluation from FP64 feet.  Same-box A/B
-// against 256-thread blocks: 78.9 against 83.0 us per evaluation sweep on
-// 61^4, 88.0 against 90.8 us diagonal-solved; 0.40 against 0.45 ms for the
-// diagonal-solved sweep of the 121^4 band grid.  A grid too small to give
+// evaluation sweeps of the full box, 768 (2 per SM at 40 registers) for the
+// increment sweeps and for both evaluation forms of the reduced grid (whose
+// prefetching loop needs the 40 registers: 0.346 against 0.376 ms per plain
+// sweep of the 121^4 band in 1024-thread blocks, 0.387 without the prefetch),
+// 1024 (one per SM at 64 registers) for the FP64 evaluation from FP64 feet.
+// Same-box A/B against 256-thread blocks: 78.9 against 83.0 us per evaluation
+// sweep on 61^4, 88.0 against 90.8 us diagonal-solved; 0.40 against 0.45 ms
+// for the diagonal-solved sweep of the 121^4 band grid.  A grid too small to give
 // every SM a large block (the 17^4 box has 83,521 nodes) runs 256-thread
 // blocks instead (BIG = false).
 template <int MODE, bool REDUCED>
 __host__ __device__ constexpr int big_block()
 {
-    return (MODE == kIncr || MODE == kIncrDiag || (MODE == kEvalFeetDiag && REDUCED))  ? 768
+    return (MODE == kIncr || MODE == kIncrDiag || ((MODE == kEvalFeet || MODE == kEvalFeetDiag) && REDUCED)) ? 768
            : (MODE == kEvalFeet || MODE == kEvalFeetDiag || MODE == kEvalFeet64 || MODE == kEvalFeet64Diag) ? 1024
                                                                                         : kBlock;
 }
@@ -585,11 +587,17 @@ __host__ __device__ constexpr int sweep_block()
     return BIG ? big_block<MODE, REDUCED>() : kBlock;
 }
 
-template <int MODE, bool REDUCED, bool BIG>
+template <typename G, typename S, int MODE, bool REDUCED, bool BIG>
 constexpr int min_blocks()
 {
     constexpr bool feet64 = MODE == kEvalFeet64 || MODE == kEvalFeet64Diag;
     if (BIG) return feet64 ? 1 : 2;
+    // FP32 angle searches: 3 blocks of 256 per SM (80 registers).  Left to
+    // itself the compiler gives the reduced-grid walk 96 registers (2 blocks):
+    // 4.84 against 4.36 ms per sweep on the 121^4 band
+    if (std::is_same<G, float>::value && std::is_same<S, float>::value &&
+        (MODE == kImproveWalk || MODE == kImproveFull))
+        return 3;
     return ((MODE == kEvalFeet || MODE == kEvalFeetDiag) && !REDUCED)   ? 8
            : (MODE == kIncr || MODE == kIncrDiag || MODE == kEvalFeetDiag) ? 6
            : feet64                                                      ? 4
@@ -597,7 +605,7 @@ constexpr int min_blocks()
 }
 
 template <typename G, typename S, int MODE, bool REDUCED, int DYN, bool BIG>
-__global__ void __launch_bounds__(sweep_block<MODE, REDUCED, BIG>(), min_blocks<MODE, REDUCED, BIG>())
+__global__ void __launch_bounds__(sweep_block<MODE, REDUCED, BIG>(), min_blocks<G, S, MODE, REDUCED, BIG>())
 sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __restrict__ Vout,
              uint16_t* __restrict__ code, unsigned long long* __restrict__ feet_lo, unsigned* __restrict__ feet_hi,
              float* __restrict__ inc, float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
