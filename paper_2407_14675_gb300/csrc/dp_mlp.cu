@@ -328,15 +328,29 @@ mlp_fwd_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __res
 // idx = (mult * (start + i) + offset) mod n of a grid (a seeded permutation).
 // Without V only the inputs are written.  Inputs are normalised to the
 // network's box (nlo, nhi).
+// Training-step state in device memory, so that one captured step can be
+// replayed: the epoch's permutation (mult, offset), the first sample of the
+// step, and the Adam step count.
+struct TrainState {
+    long long mult, offset, start;
+    int t;
+    int pad;
+};
+
 template <typename S>
 __global__ void batch_from_grid_kernel(Geo<double> g, const S* __restrict__ V, const uint16_t* __restrict__ code,
                                        const double2* __restrict__ thi, const double2* __restrict__ tlo,
                                        long long n, long long mult, long long offset, long long start, int count,
                                        double invM, Box4 nlo, Box4 nhi, float* __restrict__ x,
-                                       float* __restrict__ t)
+                                       float* __restrict__ t, const TrainState* __restrict__ ts = nullptr)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
+    if (ts) {
+        mult = ts->mult;
+        offset = ts->offset;
+        start = ts->start;
+    }
     const long long j = (long long)(((unsigned long long)mult * (unsigned long long)(start + i) +
                                      (unsigned long long)offset) % (unsigned long long)n);
     int id[4];
@@ -503,17 +517,36 @@ __global__ void transpose_kernel(const bf16* __restrict__ src, int rows, bf16* _
 
 // Adam on the FP32 master parameters, then the BF16 copies of W2, W3 and
 // their transposes used by the tensor-core GEMMs.
+// The step count t (1 for the first step) comes from device memory; the
+// bias corrections are 1 - beta^t.
 __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
-                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float bc1, float bc2)
+                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps,
+                            const TrainState* __restrict__ ts)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const float tf = (float)ts->t;
+    const float bc1 = 1.0f - powf(b1, tf), bc2 = 1.0f - powf(b2, tf);
     const float g = G[i];
     const float mi = b1 * m[i] + (1.0f - b1) * g;
     const float vi = b2 * v[i] + (1.0f - b2) * g * g;
     m[i] = mi;
     v[i] = vi;
     P[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+// End of a replayed training step: the next step's first sample and the
+// next Adam step count.
+__global__ void train_advance_kernel(TrainState* ts, int batch)
+{
+    ts->start += batch;
+    ts->t += 1;
+}
+
+// Sets the Adam step count (eager steps outside a replayed graph).
+__global__ void set_step_kernel(TrainState* ts, int t)
+{
+    ts->t = t;
 }
 
 __global__ void bf16_weights_kernel(const float* __restrict__ P, bf16* __restrict__ W2, bf16* __restrict__ W3,
@@ -579,6 +612,10 @@ struct dp_mlp {
     float* h_loss = nullptr;           // pinned
     int* h_err = nullptr;
     int wait_polls = kWaitPolls;       // polls of the first wait for the MMAs (test hook)
+    TrainState* ts = nullptr;          // training-step state (device)
+    TrainState* h_ts = nullptr;        // pinned staging of its per-epoch values
+    cudaStream_t cst = nullptr;        // private stream: training steps are captured and replayed there
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 namespace {
@@ -594,6 +631,11 @@ void free_mlp(dp_mlp* m)
         if (p) cudaFree(p);
     if (m->h_loss) cudaFreeHost(m->h_loss);
     if (m->h_err) cudaFreeHost(m->h_err);
+    if (m->ts) cudaFree(m->ts);
+    if (m->h_ts) cudaFreeHost(m->h_ts);
+    if (m->ev_in) cudaEventDestroy(m->ev_in);
+    if (m->ev_out) cudaEventDestroy(m->ev_out);
+    if (m->cst) cudaStreamDestroy(m->cst);
     delete m;
 }
 
@@ -716,17 +758,23 @@ int backward(dp_mlp* m, int count)
     return DP_OK;
 }
 
-// One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the gradient in m->G,
-// then the BF16 copies of the weights.
-int adam_step(dp_mlp* m, double lr)
+// Adam (beta1 0.9, beta2 0.999, eps 1e-8) with the gradient in m->G and the
+// step count in m->ts, then the BF16 copies of the weights.
+int adam_launch(dp_mlp* m, double lr)
 {
-    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    ++m->step;
-    const float bc1 = 1.0f - powf(b1, (float)m->step), bc2 = 1.0f - powf(b2, (float)m->step);
-    adam_kernel<<<(kParams + 255) / 256, 256, 0, m->st>>>(m->P, m->G, m->Am, m->Av, kParams, (float)lr, b1, b2, eps,
-                                                          bc1, bc2);
+    adam_kernel<<<(kParams + 255) / 256, 256, 0, m->st>>>(m->P, m->G, m->Am, m->Av, kParams, (float)lr, 0.9f, 0.999f,
+                                                          1e-8f, m->ts);
     MCK(cudaGetLastError());
     return refresh_bf16(m);
+}
+
+// One Adam step with the gradient in m->G (the next step count).
+int adam_step(dp_mlp* m, double lr)
+{
+    ++m->step;
+    set_step_kernel<<<1, 1, 0, m->st>>>(m->ts, (int)m->step);
+    MCK(cudaGetLastError());
+    return adam_launch(m, lr);
 }
 
 int check_err(dp_mlp* m)
@@ -742,6 +790,120 @@ int check_err(dp_mlp* m)
         return record_error(DP_ETIMEOUT, "a tensor-core GEMM gave up waiting for its MMAs");
     }
     return DP_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// One training step on a batch of the grid's nodes, everything on m->st:
+// the batch of samples start .. start + B - 1 of the epoch's permutation (from
+// m->ts), forward, backward, Adam with step count m->ts->t, then the next
+// step's start and count.  Replayable: no argument changes between steps.
+int train_step(dp_mlp* m, const GridView& gv, int B, Box4 nlo, Box4 nhi, double lr)
+{
+    const double invM = 1.0 / gv.M;
+    if (gv.fp32 && !gv.V64)
+        batch_from_grid_kernel<float><<<(B + 255) / 256, 256, 0, m->st>>>(
+            gv.g64, (const float*)gv.V, gv.code, gv.tab_hi64, gv.tab_lo64, gv.n, 0, 0, 0, B, invM, nlo, nhi, m->x,
+            m->t, m->ts);
+    else
+        batch_from_grid_kernel<double><<<(B + 255) / 256, 256, 0, m->st>>>(
+            gv.g64, gv.V64 ? gv.V64 : (const double*)gv.V, gv.code, gv.tab_hi64, gv.tab_lo64, gv.n, 0, 0, 0, B, invM,
+            nlo, nhi, m->x, m->t, m->ts);
+    MCK(cudaGetLastError());
+    int rc;
+    if ((rc = forward(m, B, true, m->t, 1.0f / (3.0f * B)))) return rc;
+    if ((rc = backward(m, B))) return rc;
+    if ((rc = adam_launch(m, lr))) return rc;
+    train_advance_kernel<<<1, 1, 0, m->st>>>(m->ts, B);
+    MCK(cudaGetLastError());
+    return DP_OK;
+}
+
+// The epochs of dp_mlp_train_grid.  The first step runs as launched (it also
+// sets the kernels' attributes); the next one is captured as a CUDA graph
+// and every later step replays it, which removes the host's ~20 launches
+// per step.
+int train_grid_steps(dp_mlp* m, const GridView& gv, const dp_mlp_train_opts* o, dp_mlp_train_stats* stats)
+{
+    const long long n = gv.n;
+    const int B = o->batch;
+    const long long steps_per_epoch = n / B;
+    const Box4 nlo{m->lo[0], m->lo[1], m->lo[2], m->lo[3]};
+    const Box4 nhi{m->hi[0], m->hi[1], m->hi[2], m->hi[3]};
+    double last_loss = 0.0, first_loss = -1.0;
+    unsigned long long rng = o->seed ? o->seed : 14675ull;
+    auto next = [&]() {   // splitmix64: seeds of the per-epoch permutation
+        rng += 0x9E3779B97F4A7C15ull;
+        unsigned long long z = rng;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto gcd = [](unsigned long long a, unsigned long long b) { while (b) { unsigned long long t = a % b; a = b; b = t; } return a; };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto done = [&](int rc) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return rc;
+    };
+    int rc;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess ||
+        (e = cudaEventRecord(e0, m->st)) != cudaSuccess)
+        return done(fail_cuda("training events", e));
+    for (int ep = 0; ep < o->epochs; ++ep) {
+        unsigned long long mult = (next() % (unsigned long long)n) | 1ull;
+        while (gcd(mult, (unsigned long long)n) != 1) mult = (mult + 2) % (unsigned long long)n;
+        const unsigned long long off = next() % (unsigned long long)n;
+        // the previous epoch's copy from h_ts has completed (check_err synchronised)
+        *m->h_ts = TrainState{(long long)mult, (long long)off, 0, (int)(m->step + 1), 0};
+        if ((e = cudaMemcpyAsync(m->ts, m->h_ts, sizeof(TrainState), cudaMemcpyHostToDevice, m->st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(m->loss, 0, sizeof(float), m->st)) != cudaSuccess)
+            return done(fail_cuda("training state", e));
+        for (long long s = 0; s < steps_per_epoch; ++s) {
+            if (exec) {
+                if ((e = cudaGraphLaunch(exec, m->st)) != cudaSuccess) return done(fail_cuda("graph launch", e));
+            } else if (ep == 0 && s == 0) {
+                if ((rc = train_step(m, gv, B, nlo, nhi, o->lr))) return done(rc);
+            } else {
+                if ((e = cudaStreamBeginCapture(m->st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                    return done(fail_cuda("stream capture", e));
+                const int rs = train_step(m, gv, B, nlo, nhi, o->lr);
+                e = cudaStreamEndCapture(m->st, &graph);
+                if (rs) return done(rs);
+                if (e != cudaSuccess) return done(fail_cuda("stream capture", e));
+                if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess ||
+                    (e = cudaGraphLaunch(exec, m->st)) != cudaSuccess)
+                    return done(fail_cuda("training graph", e));
+            }
+        }
+        m->step += steps_per_epoch;
+        if ((e = cudaMemcpyAsync(m->h_loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->st)) != cudaSuccess)
+            return done(fail_cuda("loss read-back", e));
+        if ((rc = check_err(m))) return done(rc);
+        last_loss = *m->h_loss / (3.0 * B * (double)steps_per_epoch);
+        if (first_loss < 0) first_loss = last_loss;
+    }
+    if ((e = cudaEventRecord(e1, m->st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess)
+        return done(fail_cuda("training events", e));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (stats) {
+        stats->epochs = o->epochs;
+        stats->steps = steps_per_epoch * o->epochs;
+        stats->samples = (int64_t)B * steps_per_epoch * o->epochs;
+        stats->first_epoch_loss = first_loss;
+        stats->last_epoch_loss = last_loss;
+        stats->ms = ms;
+        stats->flops = 3.0 * 2.0 * 132864.0 * (double)stats->samples;   // forward + 2x backward
+    }
+    return done(DP_OK);
 }
 
 }  // namespace
@@ -775,8 +937,13 @@ int dp_mlp_create(const double* lo, const double* hi, int32_t batch_capacity, vo
     A(&m->h1, CH); A(&m->h2, CH); A(&m->h3, CH); A(&m->dz1, CH); A(&m->dz2, CH); A(&m->dz3, CH);
     A(&m->T1, CH); A(&m->T2, CH);
     A(&m->states, C * 4); A(&m->loss, 1); A(&m->err, 1);
+    A(&m->ts, 1);
     if (e == cudaSuccess) e = cudaMallocHost(&m->h_loss, sizeof(float));
     if (e == cudaSuccess) e = cudaMallocHost(&m->h_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&m->h_ts, sizeof(TrainState));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->cst, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_mlp(m);
@@ -884,65 +1051,19 @@ int dp_mlp_train_grid(dp_mlp* m, dp_grid* grid, const dp_mlp_train_opts* o, dp_m
     GridView gv;
     int rc = grid_view(grid, &gv);
     if (rc) return rc;
-    const long long n = gv.n;
-    if (n < o->batch) return record_error(DP_EINVAL, "grid smaller than one batch");
-    cudaEvent_t e0, e1;
-    MCK(cudaEventCreate(&e0));
-    MCK(cudaEventCreate(&e1));
-    MCK(cudaEventRecord(e0, m->st));
-    const int B = o->batch;
-    const long long steps_per_epoch = n / B;
-    const Box4 nlo{m->lo[0], m->lo[1], m->lo[2], m->lo[3]};
-    const Box4 nhi{m->hi[0], m->hi[1], m->hi[2], m->hi[3]};
-    double last_loss = 0.0, first_loss = -1.0;
-    unsigned long long rng = o->seed ? o->seed : 14675ull;
-    auto next = [&]() {   // splitmix64: seeds of the per-epoch permutation
-        rng += 0x9E3779B97F4A7C15ull;
-        unsigned long long z = rng;
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        return z ^ (z >> 31);
-    };
-    auto gcd = [](unsigned long long a, unsigned long long b) { while (b) { unsigned long long t = a % b; a = b; b = t; } return a; };
-    for (int ep = 0; ep < o->epochs; ++ep) {
-        unsigned long long mult = (next() % (unsigned long long)n) | 1ull;
-        while (gcd(mult, (unsigned long long)n) != 1) mult = (mult + 2) % (unsigned long long)n;
-        const unsigned long long off = next() % (unsigned long long)n;
-        MCK(cudaMemsetAsync(m->loss, 0, sizeof(float), m->st));
-        for (long long s = 0; s < steps_per_epoch; ++s) {
-            if (gv.fp32 && !gv.V64)
-                batch_from_grid_kernel<float><<<(B + 255) / 256, 256, 0, m->st>>>(
-                    gv.g64, (const float*)gv.V, gv.code, gv.tab_hi64, gv.tab_lo64, n, (long long)mult, (long long)off,
-                    s * B, B, 1.0 / gv.M, nlo, nhi, m->x, m->t);
-            else
-                batch_from_grid_kernel<double><<<(B + 255) / 256, 256, 0, m->st>>>(
-                    gv.g64, gv.V64 ? gv.V64 : (const double*)gv.V, gv.code, gv.tab_hi64, gv.tab_lo64, n,
-                    (long long)mult, (long long)off, s * B, B, 1.0 / gv.M, nlo, nhi, m->x, m->t);
-            MCK(cudaGetLastError());
-            if ((rc = forward(m, B, true, m->t, 1.0f / (3.0f * B)))) return rc;
-            if ((rc = backward(m, B))) return rc;
-            if ((rc = adam_step(m, o->lr))) return rc;
-        }
-        MCK(cudaMemcpyAsync(m->h_loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->st));
-        if ((rc = check_err(m))) return rc;
-        last_loss = *m->h_loss / (3.0 * B * (double)steps_per_epoch);
-        if (first_loss < 0) first_loss = last_loss;
-    }
-    MCK(cudaEventRecord(e1, m->st));
-    MCK(cudaEventSynchronize(e1));
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (stats) {
-        stats->epochs = o->epochs;
-        stats->steps = steps_per_epoch * o->epochs;
-        stats->samples = (int64_t)B * steps_per_epoch * o->epochs;
-        stats->first_epoch_loss = first_loss;
-        stats->last_epoch_loss = last_loss;
-        stats->ms = ms;
-        stats->flops = 3.0 * 2.0 * 132864.0 * (double)stats->samples;   // forward + 2x backward
-    }
+    if (gv.n < o->batch) return record_error(DP_EINVAL, "grid smaller than one batch");
+    // the steps run on the network's private stream, ordered after the
+    // caller's stream and before its later work
+    cudaStream_t user = m->st;
+    MCK(cudaEventRecord(m->ev_in, user));
+    MCK(cudaStreamWaitEvent(m->cst, m->ev_in, 0));
+    m->st = m->cst;
+    rc = train_grid_steps(m, gv, o, stats);
+    m->st = user;
+    cudaError_t e = cudaEventRecord(m->ev_out, m->cst);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, m->ev_out, 0);
+    if (rc) return rc;
+    MCK(e);
     return DP_OK;
 }
 

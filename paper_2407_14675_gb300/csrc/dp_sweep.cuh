@@ -547,27 +547,30 @@ __device__ __forceinline__ void block_fold(S resid, bool bad, unsigned long long
     }
 }
 
-// Frozen-feet sweeps are bound by gather latency: more resident warps keep
-// more gathers in flight.  On the full box both evaluation forms fit 32
-// registers without the next-node prefetch (64 warps per SM; 1 % faster than
-// prefetching at 48).  On the reduced grid the evaluation forms keep the
-// prefetch (measured best there); so do the increment forms, at 40
-// registers (they spill at 32).
+// Frozen-feet sweeps are bound by the bytes and gathers each thread keeps in
+// flight.  The plain evaluation prefetches the next node's foot and value
+// (40 registers, 768-thread blocks): on the full box 76.7 against 79.0 us per
+// 61^4 sweep without it at 32 registers.  The diagonal-solved evaluation of
+// the full box fits 32 registers without the prefetch (64 warps per SM); on
+// the reduced grid it keeps the prefetch, as do the increment forms (they
+// spill at 32 registers).
 template <int MODE, bool REDUCED>
 __host__ __device__ constexpr bool eval_prefetch()
 {
-    return !((MODE == kEvalFeet || MODE == kEvalFeetDiag) && !REDUCED);
+    return !(MODE == kEvalFeetDiag && !REDUCED);
 }
 
 // Block size of the frozen-feet sweeps.  A grid-stride iteration of a block
 // covers that many consecutive nodes, whose corner lines overlap (a node's
 // v_t neighbours lie 61 nodes on, on the 61^4 grid), so larger blocks take
-// more of their gathers from L1: 1024 threads (2 blocks per SM) for the
-// evaluation sweeps of the full box, 768 (2 per SM at 40 registers) for the
-// increment sweeps and for both evaluation forms of the reduced grid (whose
-// prefetching loop needs the 40 registers: 0.346 against 0.376 ms per plain
-// sweep of the 121^4 band in 1024-thread blocks, 0.387 without the prefetch),
-// 1024 (one per SM at 64 registers) for the FP64 evaluation from FP64 feet.
+// more of their gathers from L1: 768 threads (2 blocks per SM at 40
+// registers) for the plain evaluation, the increment sweeps and the
+// diagonal-solved evaluation of the reduced grid (the prefetching loop needs
+// the 40 registers: 0.346 against 0.376 ms per plain sweep of the 121^4 band
+// in 1024-thread blocks, 0.387 without the prefetch; 640-, 384x4- and
+// 512x4-thread blocks 0.354-0.381), 1024 (2 per SM, 32 registers) for the
+// diagonal-solved evaluation of the full box, 1024 (one per SM at 64
+// registers) for the FP64 evaluation from FP64 feet.
 // Same-box A/B against 256-thread blocks: 78.9 against 83.0 us per evaluation
 // sweep on 61^4, 88.0 against 90.8 us diagonal-solved; 0.40 against 0.45 ms
 // for the diagonal-solved sweep of the 121^4 band grid.  A grid too small to give
@@ -576,7 +579,7 @@ __host__ __device__ constexpr bool eval_prefetch()
 template <int MODE, bool REDUCED>
 __host__ __device__ constexpr int big_block()
 {
-    return (MODE == kIncr || MODE == kIncrDiag || ((MODE == kEvalFeet || MODE == kEvalFeetDiag) && REDUCED)) ? 768
+    return (MODE == kIncr || MODE == kIncrDiag || MODE == kEvalFeet || (MODE == kEvalFeetDiag && REDUCED)) ? 768
            : (MODE == kEvalFeet || MODE == kEvalFeetDiag || MODE == kEvalFeet64 || MODE == kEvalFeet64Diag) ? 1024
                                                                                         : kBlock;
 }
