@@ -248,6 +248,28 @@ int dp_get_value(const dp_grid* grid, double* host_V, int64_t count);
 int dp_set_policy(dp_grid* grid, const uint16_t* host_codes, int64_t count);
 int dp_get_policy(const dp_grid* grid, uint16_t* host_codes, int64_t count);
 
+/* Frozen feet (FP32 grids).  An improvement sweep stores, per node, the cell
+ * and fractions of the foot of its new control (the semi-Lagrangian step of
+ * §3 after Eq. (10)), and the evaluation sweeps that follow (Eq. (13)) read
+ * them instead of repeating the step.  With FP32 values a foot is one 8-byte
+ * word (18-bit fractions) or a word pair (24-bit fractions, 12 bytes); with
+ * FP64 values always the pair.  DP_SWEEP_EVAL reads either; DP_SWEEP_EVAL_DIAG
+ * reads the pair (its step divides by 1 - beta w_jj, which the 18-bit
+ * fractions do not resolve where w_jj is near 1) and otherwise recomputes the
+ * feet, exactly as for a policy set from the host.
+ *   DP_FOOT_AUTO (default): dp_policy_iterate stores the pair for
+ *     DP_EVAL_DIAG and 8-byte words otherwise; dp_bellman_sweep stores
+ *     8-byte words.
+ *   DP_FOOT_WORD8 / DP_FOOT_PAIR: every FP32-value improvement stores that
+ *     format.
+ * The format changes a result by the fraction quantisation only (at most
+ * 3 * 2^-19 of a cell's value spread per evaluation sweep with 8-byte words).
+ * Returns DP_EINVAL for another format. */
+#define DP_FOOT_AUTO  0
+#define DP_FOOT_WORD8 1
+#define DP_FOOT_PAIR  2
+int dp_set_foot_format(dp_grid* grid, int32_t format);
+
 /* One Jacobi sweep of the scheme on the resident V and policy (mode =
  * DP_SWEEP_*): Eq. (12), (13) or (14).  Improvement modes rewrite the policy;
  * EVAL and EVAL_DIAG read it.  On FP32 grids whose value has moved to FP64 (after a
@@ -390,7 +412,9 @@ int dp_warm_start(dp_mlp* mlp, dp_grid* grid, double* ms);
  * sequence as dp_policy_iterate on a grid of its own.
  *
  * Device memory per node: 2 x 4 (FP32 V) + 2 x 8 (FP64 V) + 2 (policy) + 12
- * (frozen foot) + 4 (increment sum) = 42 bytes, plus the line tables.
+ * (frozen foot: an 8-byte word in the FP32-value phase of plain evaluation,
+ * the word pair otherwise) + 4 (increment sum) = 42 bytes, plus the line
+ * tables.
  * Node and value order inside a transfer: box order, as for a grid. */
 typedef struct dp_batch dp_batch;
 

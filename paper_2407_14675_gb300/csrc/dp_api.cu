@@ -87,6 +87,9 @@ struct dp_grid {
     unsigned long long* feet_lo = nullptr;  // frozen feet of the current policy (FP32 grids)
     unsigned* feet_hi = nullptr;
     bool feet_valid = false;
+    bool feet8 = false;                     // they are 8-byte words (stored with FP32 values)
+    bool store_feet8 = true;                // what the next FP32-value improvements store
+    int foot_format = DP_FOOT_AUTO;         // dp_set_foot_format
     Feet64 f64;                             // frozen feet of FP64 grids
     bool feet64_valid = false;
     float* acc = nullptr;                   // FP64-value polish: running sum of increments
@@ -291,6 +294,7 @@ SweepLaunch<G, S> sweep_launch(dp_grid* g, const Geo<G>& geo, const S* Vin, S* V
     L.check_prev = check_prev;
     L.tol = tol;
     L.mode = mode;
+    L.feet8 = g->store_feet8 ? 1 : 0;
     L.dyn = g->d.dynamics;
     L.reduced = g->d.reduced;
     L.stream = g->st;
@@ -313,14 +317,16 @@ Store store_of(const dp_grid* g)
 // (the two numberings overlap: every public mode is mapped exactly once).
 int internal_mode(const dp_grid* g, int mode)
 {
+    // with FP32 values the plain evaluation reads either foot format, the
+    // diagonal-solved one only the word pairs (8-byte feet are recomputed)
     const bool feet = store_of(g) == kStoreF32 && g->feet_valid;
     const bool feet64 = store_of(g) == kStoreF64 && g->feet64_valid;
     switch (mode) {
     case DP_SWEEP_VI: return kVI;
     case DP_SWEEP_IMPROVE_FULL: return kImproveFull;
     case DP_SWEEP_IMPROVE_WALK: return kImproveWalk;
-    case DP_SWEEP_EVAL: return feet ? kEvalFeet : (feet64 ? kEvalFeet64 : kEval);
-    case DP_SWEEP_EVAL_DIAG: return feet ? kEvalFeetDiag : (feet64 ? kEvalFeet64Diag : kEvalDiag);
+    case DP_SWEEP_EVAL: return feet ? (g->feet8 ? kEvalFeet8 : kEvalFeet) : (feet64 ? kEvalFeet64 : kEval);
+    case DP_SWEEP_EVAL_DIAG: return (feet && !g->feet8) ? kEvalFeetDiag : (feet64 ? kEvalFeet64Diag : kEvalDiag);
     case DP_SWEEP_VI_DIAG: return kVIDiag;
     }
     return -1;
@@ -335,7 +341,10 @@ cudaError_t enqueue_sweep(dp_grid* g, int pmode, long long t, int check_prev, do
     // policy; the evaluation sweeps after them read those instead of
     // recomputing
     if (pmode == DP_SWEEP_IMPROVE_FULL || pmode == DP_SWEEP_IMPROVE_WALK) {
-        if (store_of(g) == kStoreF32) g->feet_valid = g->feet_lo != nullptr;
+        if (store_of(g) == kStoreF32) {
+            g->feet_valid = g->feet_lo != nullptr;
+            g->feet8 = g->store_feet8;
+        }
         if (store_of(g) == kStoreF64) g->feet64_valid = g->f64.w != nullptr;
     }
     const int mode = internal_mode(g, pmode);
@@ -370,11 +379,14 @@ cudaError_t enqueue_polish_improve(dp_grid* g, int mode, int c, long long t, int
         sweep_launch<float, double>(g, g->g32, g->V64[c], g->V64[c ^ 1], mode, t, check_prev, tol);
     L.inc = (float*)g->V[0];
     g->feet_valid = g->feet_lo != nullptr;
+    g->feet8 = false;   // the FP64-value phase stores the 24-bit word pair
     return launch_sweep(L);
 }
 
 cudaError_t enqueue_increment(dp_grid* g, int c, int e, int n, long long t, int check_prev, double tol, bool diag)
 {
+    // the increments read the word pairs of the FP64-value improvement
+    if (!g->feet_valid || g->feet8) return cudaErrorInvalidValue;
     SweepLaunch<float, float> L = sweep_launch<float, float>(g, g->g32, (const float*)g->V[e & 1],
                                                              (float*)g->V[(e + 1) & 1], diag ? kIncrDiag : kIncr, t,
                                                              check_prev, tol);
@@ -407,6 +419,8 @@ unsigned long long g_wave_timeout_ns = kWaveTimeoutNs;
 cudaError_t enqueue_wave(dp_grid* g, bool mix, bool diag, int c, int e0, int n, int k, long long t, int check_prev,
                          double tol)
 {
+    // diagonal-solved and increment levels read the word pairs
+    if (!g->feet_valid || (g->feet8 && (mix || diag))) return cudaErrorInvalidValue;
     WaveArgs a;
     a.g = g->g32;
     a.V[0] = (float*)g->V[0];
@@ -429,7 +443,7 @@ cudaError_t enqueue_wave(dp_grid* g, bool mix, bool diag, int c, int e0, int n, 
     a.timeout_ns = g_wave_timeout_ns;
     // buffers as enqueue_sweep / enqueue_increment alternate them
     a.in0 = mix ? (e0 & 1) : (int)((g->cur + t) & 1);
-    const int mode = mix ? (diag ? kIncrDiag : kIncr) : (diag ? kEvalFeetDiag : kEvalFeet);
+    const int mode = mix ? (diag ? kIncrDiag : kIncr) : (diag ? kEvalFeetDiag : (g->feet8 ? kEvalFeet8 : kEvalFeet));
     return launch_wave(a, mode, g->d.dynamics, g->d.reduced, g->st, g->sm_count);
 }
 
@@ -618,7 +632,7 @@ GmArgs<G, VT> gm_args(const dp_grid* g, const Geo<G>& geo, const GmOpts& go)
     a.rtol = go.rtol;
     a.code = g->code;
     a.feet_lo = g->feet_lo;
-    a.feet_hi = g->feet_hi;
+    a.feet_hi = g->feet8 ? nullptr : g->feet_hi;   // nullptr: 8-byte feet
     if (g->feet64_valid) a.f64 = g->f64;
     a.partial = g->gm_partial;
     a.max_blocks = g->gm_blocks;
@@ -1221,6 +1235,7 @@ int dp_bellman_sweep(dp_grid* g, int32_t mode, double* residual)
     if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
     int rc;
     if ((rc = reset_ctl(g)) || (rc = clear_ring(g, 0, 1))) return rc;
+    g->store_feet8 = g->foot_format != DP_FOOT_PAIR;
     CK(enqueue_sweep(g, mode, 0, 0, 0.0));
     if ((rc = fetch(g, 0, 1))) return rc;
     advance(g, 1);
@@ -1312,6 +1327,10 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
     if (o->eval_solver != DP_EVAL_JACOBI && o->eval_solver != DP_EVAL_GMRES && o->eval_solver != DP_EVAL_DIAG)
         return fail(DP_EINVAL, "unknown eval_solver %d", o->eval_solver);
     const bool diag = o->eval_solver == DP_EVAL_DIAG;
+    // the feet its FP32-value improvements store: 8-byte words where the
+    // plain evaluation (or GMRES) reads them, word pairs for the
+    // diagonal-solved evaluation
+    g->store_feet8 = g->foot_format == DP_FOOT_AUTO ? !diag : g->foot_format == DP_FOOT_WORD8;
     if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
     double t0 = now_ms();
     dp_solve_stats S;
@@ -1453,6 +1472,16 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
     return DP_OK;
 }
 
+int dp_set_foot_format(dp_grid* g, int32_t format)
+{
+    if (!g) return fail(DP_EINVAL, "grid is NULL");
+    if (format != DP_FOOT_AUTO && format != DP_FOOT_WORD8 && format != DP_FOOT_PAIR)
+        return fail(DP_EINVAL, "unknown foot format %d", format);
+    g->foot_format = format;
+    g->store_feet8 = format != DP_FOOT_PAIR;
+    return DP_OK;
+}
+
 int dp_set_wave_wait_limit(int64_t ns)
 {
     if (ns < -1) return fail(DP_EINVAL, "bad wait limit");
@@ -1478,8 +1507,12 @@ int dp_policy_evaluate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats
     if ((rc = reset_ctl(g))) return rc;
     const bool mix = store_of(g) == kStoreMix;
     if (g->fp32 && !g->feet_valid) {
-        CK(launch_feet(g->g32, g->code, g->feet_lo, g->feet_hi, g->d.dynamics, g->d.reduced, g->sm_count, g->st));
+        // 8-byte feet with FP32 values (the evaluation kernels read them too),
+        // word pairs with FP64 values
+        CK(launch_feet(g->g32, g->code, g->feet_lo, mix ? g->feet_hi : nullptr, g->d.dynamics, g->d.reduced,
+                       g->sm_count, g->st));
         g->feet_valid = true;
+        g->feet8 = !mix;
         S.launches += 1;
     }
     double res = INFINITY;

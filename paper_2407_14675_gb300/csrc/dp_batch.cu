@@ -103,6 +103,8 @@ struct BArgs {
     float* acc;
     int count;
     int item_eval, item_imp;       // nodes per work item
+    int feet8;                     // FP32-value improvements store, and the plain evaluation
+                                   //   reads, 8-byte feet (1) or the word pairs (0)
 };
 
 // One of two buffers by a runtime bit, without indexing the parameter array
@@ -196,7 +198,8 @@ __global__ void __launch_bounds__(kBlock, std::is_same<S, double>::value ? 2 : 3
             Vout = pick(a.V32, st.cur ^ 1) + o;
         }
         sweep_nodes<float, S, MODE, false, DYN>(s_g, T, Vin, Vout, a.code + o, a.feet_lo + o, a.feet_hi + o, inc,
-                                                nullptr, nullptr, 0, first + threadIdx.x, end, kBlock, resid, bad);
+                                                nullptr, nullptr, 0, first + threadIdx.x, end, kBlock, resid, bad,
+                                                Feet64(), nullptr, a.feet8 != 0);
         block_fold(resid, bad, &st.res_bits, &st.nonfinite);
     }
 }
@@ -235,10 +238,19 @@ __global__ void __launch_bounds__(kBatchEvalBlock, 2) batch_eval_kernel(const BA
         if (st.phase == kPh32 || !FEET) {
             const float* Vin = pick(a.V32, st.cur + 1 + e) + o;
             float* Vout = pick(a.V32, st.cur + 2 + e) + o;
-            if constexpr (FEET)
-                sweep_nodes<float, float, DIAG ? kEvalFeetDiag : kEvalFeet, false, DYN>(
+            if constexpr (FEET && DIAG)
+                sweep_nodes<float, float, kEvalFeetDiag, false, DYN>(
                     s_g, T, Vin, Vout, a.code + o, a.feet_lo + o, a.feet_hi + o, nullptr, nullptr, nullptr, 0,
                     first + threadIdx.x, end, kBatchEvalBlock, resid, bad);
+            else if constexpr (FEET)
+                if (a.feet8)
+                    sweep_nodes<float, float, kEvalFeet8, false, DYN>(
+                        s_g, T, Vin, Vout, a.code + o, a.feet_lo + o, nullptr, nullptr, nullptr, nullptr, 0,
+                        first + threadIdx.x, end, kBatchEvalBlock, resid, bad);
+                else
+                    sweep_nodes<float, float, kEvalFeet, false, DYN>(
+                        s_g, T, Vin, Vout, a.code + o, a.feet_lo + o, a.feet_hi + o, nullptr, nullptr, nullptr, 0,
+                        first + threadIdx.x, end, kBatchEvalBlock, resid, bad);
             else
                 sweep_nodes<float, float, DIAG ? kEvalDiag : kEval, false, DYN>(
                     s_g, T, Vin, Vout, a.code + o, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
@@ -507,6 +519,7 @@ struct dp_batch {
     bool graph_diag = false;
     long long graph_launches = 0;
     bool feet_valid = false;
+    bool feet8 = true;             // format of the feet FP32-value improvements store (and stored last)
     long long device_bytes = 0;
 };
 
@@ -562,6 +575,7 @@ BArgs args_of(const dp_batch* b)
     a.count = b->count;
     a.item_eval = b->item_eval;
     a.item_imp = b->item_imp;
+    a.feet8 = b->feet8 ? 1 : 0;
     return a;
 }
 
@@ -715,6 +729,9 @@ int manual_sweep(dp_batch* b, int32_t mode, double* ms)
 {
     int stage = mode == DP_SWEEP_IMPROVE_FULL ? kStManImpFull : mode == DP_SWEEP_IMPROVE_WALK ? kStManImpWalk
                                                                                                 : kStManEval;
+    // a stand-alone improvement stores 8-byte feet; a stand-alone evaluation
+    // reads the format stored last
+    if (stage != kStManEval) b->feet8 = true;
     BCK(launch_ctl(b, stage));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ms) {
@@ -1010,6 +1027,9 @@ int dp_batch_policy_iterate(dp_batch* b, const dp_solve_opts* o, dp_solve_stats*
         return bfail(DP_EINVAL, "batched policy iteration evaluates by plain or diagonal-solved sweeps only");
     const bool diag = o->eval_solver == DP_EVAL_DIAG;
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(DP_ECUDA, "cudaSetDevice failed");
+    // 8-byte feet for the plain evaluation, word pairs for the
+    // diagonal-solved one (the graph of a solver captures its format)
+    b->feet8 = !diag;
     const double t0 = now_ms();
     int rc;
     if ((rc = pull_state(b))) return rc;
@@ -1031,7 +1051,12 @@ int dp_batch_policy_iterate(dp_batch* b, const dp_solve_opts* o, dp_solve_stats*
         if (b->h_par->active == 0 || replays >= max_replays) break;
     }
     if ((rc = pull_state(b))) return rc;
+    // a transfer whose last improvement ran with FP64 values stored 24-bit
+    // word pairs; stand-alone evaluation sweeps read 8-byte feet, so the
+    // stored feet serve them only if no transfer switched
     b->feet_valid = true;
+    for (int t = 0; t < b->count; ++t)
+        if (b->h_st[t].switch_outer >= 0) b->feet_valid = false;
 
     dp_solve_stats S;
     memset(&S, 0, sizeof S);

@@ -27,7 +27,9 @@ constexpr int kMaxFib = 30;
 constexpr int kMaxAngles = 1024;   // tabulated angles per grid (shared-memory table)
 
 enum { kVI = 0, kImproveFull = 1, kImproveWalk = 2, kEval = 3, kEvalFeet = 4, kIncr = 5,
-       kEvalDiag = 6, kEvalFeetDiag = 7, kIncrDiag = 8, kVIDiag = 9, kEvalFeet64 = 10, kEvalFeet64Diag = 11 };
+       kEvalDiag = 6, kEvalFeetDiag = 7, kIncrDiag = 8, kVIDiag = 9, kEvalFeet64 = 10, kEvalFeet64Diag = 11,
+       kEvalFeet8 = 12 };
+// kEvalFeet8: kEvalFeet at 8-byte frozen feet (kEvalFeet: at the word pairs).
 // kEval*Diag, kIncrDiag: the evaluation as a Jacobi iteration on the linear
 // system of Eq. (13) with each node's own coefficient solved exactly (the
 // weight w_jj of node j among the Q1 corners of its own foot):
@@ -532,7 +534,8 @@ __device__ __forceinline__ bool load_corners(const Geo<G>& g, const S* __restric
 
 // Frozen foot of a node under a fixed policy (FP32 geometry).  Policy
 // evaluation sweeps repeat the same foot ~20 times, so the improvement sweep
-// stores it (12 bytes) and the evaluation sweep only gathers and blends:
+// stores it and the evaluation sweep only gathers and blends.  With FP64
+// values (12 bytes in two arrays):
 //   lo (64 bits): t_r bits 0-23, t_vr bits 24-47, low 16 bits of t_vt 48-63
 //   hi (32 bits): high 8 bits of t_vt 0-7, cell offset from the node in r
 //                 (-2..1) bits 8-9, v_r (-8..7) bits 10-13, v_t (-2..1) bits
@@ -545,6 +548,15 @@ __device__ __forceinline__ bool load_corners(const Geo<G>& g, const S* __restric
 // upper mass face, is marked "recompute").
 enum { kFootInside = 0, kFootOut = 1, kFootTarget = 2, kFootRecompute = 3 };
 constexpr float kFootQ = 16777215.0f;   // 2^24 - 1
+
+// The FP32-value phase stores the same foot in one 8-byte word (no second
+// array to stream): fractions t_r bits 0-17, t_vr 18-35, t_vt 36-53 as 18-bit
+// fixed point q / (2^18 - 1); cell offsets r (-2..1) bits 54-55, v_r (-8..7)
+// 56-59, v_t (-2..1) 60-61; kind bits 62-63.  The quantisation step, 3.8e-6
+// of a cell, is about the rounding of the FP32 one-step map itself for
+// displacements of a few cells (v_r); the FP64-value phase, whose values
+// converge far below FP32 resolution, keeps the 24-bit word pair.
+constexpr float kFoot8Q = 262143.0f;    // 2^18 - 1
 
 struct FootWord {
     unsigned long long lo;
@@ -569,6 +581,23 @@ struct Feet64 {
 __device__ __forceinline__ FootWord foot_word_kind(int kind)
 {
     return FootWord{0ull, (unsigned)kind << 16};
+}
+
+__device__ __forceinline__ unsigned long long foot8_kind(int kind) { return (unsigned long long)kind << 62; }
+__device__ __forceinline__ int foot8_kind_of(unsigned long long w) { return (int)(w >> 62); }
+
+// Encodes cell c and fractions t of a foot from node i in the 8-byte word.
+__device__ __forceinline__ unsigned long long encode_foot8(const int i[4], const int c[4], const float t[4], int dm,
+                                                           float tm)
+{
+    const int dr = c[0] - i[0], dv = c[1] - i[1], dt = c[2] - i[2];
+    if (dr < -2 || dr > 1 || dv < -8 || dv > 7 || dt < -2 || dt > 1 || c[3] - i[3] != dm || t[3] != tm)
+        return foot8_kind(kFootRecompute);
+    const unsigned long long q0 = __float2uint_rn(t[0] * kFoot8Q);
+    const unsigned long long q1 = __float2uint_rn(t[1] * kFoot8Q);
+    const unsigned long long q2 = __float2uint_rn(t[2] * kFoot8Q);
+    return q0 | (q1 << 18) | (q2 << 36) | ((unsigned long long)(dr + 2) << 54) |
+           ((unsigned long long)(dv + 8) << 56) | ((unsigned long long)(dt + 2) << 60);
 }
 
 // Encodes cell c and fractions t of a foot from node i; dm, tm: the grid's
@@ -836,24 +865,47 @@ struct CachedEval {
         return w;
     }
 
-    // Frozen-foot word of this node for a code (FP32 geometry only).  cell
-    // (nullable) receives the foot's cell when it has corners (kinds inside
-    // and recompute).
-    __device__ __forceinline__ FootWord foot_of(int code, int* cell = nullptr) const
+    // Cell cl and fractions t of this node's foot for a code (FP32 geometry
+    // only); false when the foot is outside the box or the node set.
+    __device__ __forceinline__ bool foot_at(int code, int cl[4], G t[4]) const
     {
-        G s, c, u[4], t[4];
-        int cl[4], base[4];
+        G s, c, u[4];
+        int base[4];
         code_sincos(*g, code, s, c);
         heun_cells<G, DYN>(*g, sp, nd, s, c, u);
 #pragma unroll
         for (int d = 0; d < 4; ++d) u[d] += u0[d];
-        if (foot_cell(*g, i, u, cl, t)) return foot_word_kind(kFootOut);
-        if (REDUCED && cell_rows<G, REDUCED>(*g, cl, base)) return foot_word_kind(kFootOut);
+        if (foot_cell(*g, i, u, cl, t)) return false;
+        if (REDUCED && cell_rows<G, REDUCED>(*g, cl, base)) return false;
+        return true;
+    }
+
+    // Frozen-foot word pair of this node for a code (FP32 geometry only).
+    // cell (nullable) receives the foot's cell when it has corners (kinds
+    // inside and recompute).
+    __device__ __forceinline__ FootWord foot_of(int code, int* cell = nullptr) const
+    {
+        G t[4];
+        int cl[4];
+        if (!foot_at(code, cl, t)) return foot_word_kind(kFootOut);
         if (cell) {
 #pragma unroll
             for (int d = 0; d < 4; ++d) cell[d] = cl[d];
         }
         return encode_foot(i, cl, t, g->foot_dm, g->foot_tm);
+    }
+
+    // The same foot as one 8-byte word.
+    __device__ __forceinline__ unsigned long long foot8_of(int code, int* cell = nullptr) const
+    {
+        G t[4];
+        int cl[4];
+        if (!foot_at(code, cl, t)) return foot8_kind(kFootOut);
+        if (cell) {
+#pragma unroll
+            for (int d = 0; d < 4; ++d) cell[d] = cl[d];
+        }
+        return encode_foot8(i, cl, t, g->foot_dm, g->foot_tm);
     }
 };
 

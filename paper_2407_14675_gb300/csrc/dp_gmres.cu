@@ -144,12 +144,12 @@ __device__ __forceinline__ void store4(T* p, int j4, int n, const T v[4])
 
 // (A x)_j = x_j - beta (W_f x)_j from node j's frozen foot (FP32 geometry).
 // A foot outside the box or the node set, and a target node, have no W row.
-template <bool REDUCED, int DYN>
-__device__ __forceinline__ float apply_a_feet(const Geo<float>& g, const float* __restrict__ x, int j, FootWord w,
+template <bool REDUCED, int DYN, typename W>
+__device__ __forceinline__ float apply_a_feet(const Geo<float>& g, const float* __restrict__ x, int j, W w,
                                               const uint16_t* __restrict__ code)
 {
     const float xj = x[j];
-    const int kind = (int)((w.hi >> 16) & 3u);
+    const int kind = foot_kind(w);
     float D = 0.0f;
     if (kind == kFootInside) D = eval_foot<REDUCED>(g, x, j, w, 0.0f);
     else if (kind == kFootRecompute) D = incr_recompute<REDUCED, DYN>(g, x, j, code[j]);
@@ -258,12 +258,24 @@ gm_matvec_kernel(const __grid_constant__ Geo<G> g, VT* __restrict__ Q, long long
     const int stride = gridDim.x * kGmBlock;
     if constexpr (std::is_same<G, float>::value) {
         int j = blockIdx.x * kGmBlock + threadIdx.x;
-        FootWord next{0ull, 0u};
-        if (j < n) next = FootWord{__ldcs(&feet_lo[j]), __ldcs(&feet_hi[j])};
-        for (; j < n; j += stride) {
-            const FootWord fw = next;
-            if (j + stride < n) next = FootWord{__ldcs(&feet_lo[j + stride]), __ldcs(&feet_hi[j + stride])};
-            w[j] = sk * apply_a_feet<REDUCED, DYN>(g, x, j, fw, code);
+        if (feet_hi) {
+            // the word pair of the FP64-value phase
+            FootWord next{0ull, 0u};
+            if (j < n) next = FootWord{__ldcs(&feet_lo[j]), __ldcs(&feet_hi[j])};
+            for (; j < n; j += stride) {
+                const FootWord fw = next;
+                if (j + stride < n) next = FootWord{__ldcs(&feet_lo[j + stride]), __ldcs(&feet_hi[j + stride])};
+                w[j] = sk * apply_a_feet<REDUCED, DYN>(g, x, j, fw, code);
+            }
+        } else {
+            // 8-byte feet of the FP32-value phase
+            unsigned long long next = 0ull;
+            if (j < n) next = __ldcs(&feet_lo[j]);
+            for (; j < n; j += stride) {
+                const unsigned long long fw = next;
+                if (j + stride < n) next = __ldcs(&feet_lo[j + stride]);
+                w[j] = sk * apply_a_feet<REDUCED, DYN>(g, x, j, fw, code);
+            }
         }
     } else if (f64.w) {
         for (int j = blockIdx.x * kGmBlock + threadIdx.x; j < n; j += stride)
@@ -419,7 +431,9 @@ gm_apply_kernel(const VV* __restrict__ Vin, VV* __restrict__ Vnext, const VT* __
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->nonfinite, 1);
 }
 
-// Frozen feet of the resident policy, the words an improvement sweep stores.
+// Frozen feet of the resident policy, the words an improvement sweep stores:
+// the word pair when feet_hi is given (FP64-value phase), else the 8-byte
+// word (FP32-value phase).
 template <bool REDUCED, int DYN>
 __global__ void __launch_bounds__(kGmBlock)
 feet_kernel(const __grid_constant__ Geo<float> g, const uint16_t* __restrict__ code,
@@ -428,15 +442,15 @@ feet_kernel(const __grid_constant__ Geo<float> g, const uint16_t* __restrict__ c
     for (int j = blockIdx.x * kGmBlock + threadIdx.x; j < g.n_nodes; j += gridDim.x * kGmBlock) {
         CachedEval<float, float, REDUCED, DYN, float, false> ev;
         decode_node(g, j, ev.i);
-        FootWord w;
-        if (in_target(g, ev.i)) {
-            w = foot_word_kind(kFootTarget);
+        const bool target = in_target(g, ev.i);
+        if (!target) setup_node<float, float, DYN>(ev, g, (const float*)nullptr, 0.0f);
+        if (feet_hi) {
+            const FootWord w = target ? foot_word_kind(kFootTarget) : ev.foot_of(code[j]);
+            feet_lo[j] = w.lo;
+            feet_hi[j] = w.hi;
         } else {
-            setup_node<float, float, DYN>(ev, g, (const float*)nullptr, 0.0f);
-            w = ev.foot_of(code[j]);
+            feet_lo[j] = target ? foot8_kind(kFootTarget) : ev.foot8_of(code[j]);
         }
-        feet_lo[j] = w.lo;
-        feet_hi[j] = w.hi;
     }
 }
 
@@ -516,7 +530,7 @@ template <typename G, typename VT, typename VV>
 cudaError_t cycle(const GmArgs<G, VT>& a, const VV* Vin, VV* Vnext)
 {
     if (a.m < 1 || a.m > kGmMaxRestart || !a.Q || !a.partial || !a.gctl) return cudaErrorInvalidValue;
-    if (std::is_same<G, float>::value && (!a.feet_lo || !a.feet_hi)) return cudaErrorInvalidValue;
+    if (std::is_same<G, float>::value && !a.feet_lo) return cudaErrorInvalidValue;
     const int n = a.g.n_nodes;
     cudaError_t e;
     {

@@ -28,6 +28,7 @@ struct SweepLaunch {
     int check_prev;             // 1: stop if the previous sweep's residual < tol
     double tol;
     Feet64 f64;                 // FP64 grids: frozen feet (written by improvements, read by kEvalFeet64*)
+    int feet8 = 1;              // improvements with FP32 values: 1 stores 8-byte feet, 0 the word pair
     int mode;                   // kVI, kImproveFull, kImproveWalk, kEval
     int dyn;
     int reduced;
@@ -76,7 +77,7 @@ struct WaveArgs {
     unsigned long long timeout_ns;         // limit of each wait (kWaveTimeoutNs unless a test sets it)
 };
 
-// mode: kEvalFeet, kEvalFeetDiag, kIncr or kIncrDiag.  Zeroes a.sync first.
+// mode: kEvalFeet, kEvalFeet8, kEvalFeetDiag, kIncr or kIncrDiag.  Zeroes a.sync first.
 cudaError_t launch_wave(const WaveArgs& a, int mode, int dyn, int reduced, cudaStream_t st, int sm_count);
 
 // Feedback (steps == 0) or closed loop (steps > 0) over n states.
@@ -158,7 +159,7 @@ struct GmArgs {
     double rtol;                     // a cycle ends once ||r|| <= rtol ||r0||
     const uint16_t* code;            // frozen policy
     const unsigned long long* feet_lo;   // frozen feet (FP32 geometry)
-    const unsigned* feet_hi;
+    const unsigned* feet_hi;         // nullptr: 8-byte feet (FP32-value phase)
     Feet64 f64;                      // FP64 frozen feet (FP64 grids; w == nullptr: recompute)
     double* partial;                 // max_blocks x kGmLd
     int max_blocks;
@@ -174,7 +175,8 @@ struct GmArgs {
 cudaError_t gm_cycle(const GmArgs<float, float>& a, const float* Vin, float* Vnext);
 cudaError_t gm_cycle(const GmArgs<float, float>& a, const double* Vin, double* Vnext);
 cudaError_t gm_cycle(const GmArgs<double, double>& a, const double* Vin, double* Vnext);
-// Frozen feet of the resident policy (FP32 geometry), as an improvement sweep stores them.
+// Frozen feet of the resident policy (FP32 geometry), as an improvement sweep
+// stores them: the word pair, or the 8-byte word when feet_hi is nullptr.
 cudaError_t launch_feet(const Geo<float>& g, const uint16_t* code, unsigned long long* feet_lo, unsigned* feet_hi,
                         int dyn, int reduced, int sm_count, cudaStream_t st);
 

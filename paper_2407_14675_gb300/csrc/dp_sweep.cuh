@@ -11,9 +11,9 @@
 // without touching V, so a queue of sweeps ends at the first converged one.
 //
 // Improvement sweeps with FP32 geometry also store each node's frozen foot
-// (cell offsets and fractions of the chosen control, 12 bytes).  The
-// evaluation sweeps that follow read it (kEvalFeet) and only gather and
-// blend.  With FP64 values the evaluation sweeps run on increments instead
+// (cell offsets and fractions of the chosen control: 8 bytes with FP32
+// values, 12 with FP64 values).  The evaluation sweeps that follow read it
+// (kEvalFeet) and only gather and blend.  With FP64 values the evaluation sweeps run on increments instead
 // (kIncr): V_{k+1} - V_k = beta W (V_k - V_{k-1}) at a frozen policy, so the
 // increments are swept in FP32 and summed into the FP64 value once.
 #pragma once
@@ -103,21 +103,11 @@ __device__ __forceinline__ void setup_node(E& ev, const Geo<G>& g, const S* __re
     ev.nd = node_dyn<G, DYN>(g, ev.sp, x);
 }
 
-// Blend at a frozen foot of kind kFootInside: D = I[V] - vj.
+// Corner rows of node j's frozen-foot cell (offsets dr, dv, dt from the node;
+// the mass offset is the grid's): base[] as cell_rows gives them.
 template <bool REDUCED>
-__device__ __forceinline__ float eval_foot(const Geo<float>& g, const float* __restrict__ V, int j, FootWord w,
-                                           float vj)
+__device__ __forceinline__ void foot_rows(const Geo<float>& g, int j, int dr, int dv, int dt, int base[4])
 {
-    const int dr = (int)((w.hi >> 8) & 3u) - 2;
-    const int dv = (int)((w.hi >> 10) & 15u) - 8;
-    const int dt = (int)((w.hi >> 14) & 3u) - 2;
-    const unsigned q2 = (unsigned)(w.lo >> 48) | ((w.hi & 0xffu) << 16);
-    float t[4];
-    t[0] = (float)(unsigned)(w.lo & 0xffffffu) * (1.0f / kFootQ);
-    t[1] = (float)(unsigned)((w.lo >> 24) & 0xffffffu) * (1.0f / kFootQ);
-    t[2] = (float)q2 * (1.0f / kFootQ);
-    t[3] = g.foot_tm;
-    int base[4];
     if (!REDUCED) {
         // full box: the cell's corner index is the node's own index plus offsets
         const int b0 = j + dr * g.stride[0] + dv * g.stride[1] + dt * g.stride[2] + g.foot_dm;
@@ -134,25 +124,67 @@ __device__ __forceinline__ float eval_foot(const Geo<float>& g, const float* __r
         c[3] = i[3] + g.foot_dm;
         cell_rows<float, true>(g, c, base);   // membership was checked when the foot was stored
     }
+}
+
+// A decoded frozen foot of kind kFootInside: cell offsets and fractions.
+struct FootCell {
+    int dr, dv, dt;
+    float t[4];
+};
+
+__device__ __forceinline__ FootCell foot_cell_of(const Geo<float>& g, FootWord w)
+{
+    FootCell f;
+    f.dr = (int)((w.hi >> 8) & 3u) - 2;
+    f.dv = (int)((w.hi >> 10) & 15u) - 8;
+    f.dt = (int)((w.hi >> 14) & 3u) - 2;
+    const unsigned q2 = (unsigned)(w.lo >> 48) | ((w.hi & 0xffu) << 16);
+    f.t[0] = (float)(unsigned)(w.lo & 0xffffffu) * (1.0f / kFootQ);
+    f.t[1] = (float)(unsigned)((w.lo >> 24) & 0xffffffu) * (1.0f / kFootQ);
+    f.t[2] = (float)q2 * (1.0f / kFootQ);
+    f.t[3] = g.foot_tm;
+    return f;
+}
+
+__device__ __forceinline__ FootCell foot_cell_of(const Geo<float>& g, unsigned long long w)
+{
+    FootCell f;
+    f.dr = (int)((w >> 54) & 3u) - 2;
+    f.dv = (int)((w >> 56) & 15u) - 8;
+    f.dt = (int)((w >> 60) & 3u) - 2;
+    f.t[0] = (float)(unsigned)(w & 0x3ffffu) * (1.0f / kFoot8Q);
+    f.t[1] = (float)(unsigned)((w >> 18) & 0x3ffffu) * (1.0f / kFoot8Q);
+    f.t[2] = (float)(unsigned)((w >> 36) & 0x3ffffu) * (1.0f / kFoot8Q);
+    f.t[3] = g.foot_tm;
+    return f;
+}
+
+// Kind of a stored foot, either format.
+__device__ __forceinline__ int foot_kind(FootWord w) { return (int)((w.hi >> 16) & 3u); }
+__device__ __forceinline__ int foot_kind(unsigned long long w) { return foot8_kind_of(w); }
+
+// Blend at a frozen foot of kind kFootInside: D = I[V] - vj.  W: the word
+// pair (FootWord) or the 8-byte word.
+template <bool REDUCED, typename W>
+__device__ __forceinline__ float eval_foot(const Geo<float>& g, const float* __restrict__ V, int j, W w, float vj)
+{
+    const FootCell f = foot_cell_of(g, w);
+    int base[4];
+    foot_rows<REDUCED>(g, j, f.dr, f.dv, f.dt, base);
     Corners<float> K;
     load_rows<float, float>(V, base, g.n_m, vj, K);
-    return K.blend(t);
+    return K.blend(f.t);
 }
 
 // Node j's own weight among the corners of its frozen foot (kind inside):
 // per coordinate 1 - t where the cell starts at the node, t where it ends
 // there, 0 otherwise.
-__device__ __forceinline__ float foot_self_weight(const Geo<float>& g, FootWord w)
+template <typename W>
+__device__ __forceinline__ float foot_self_weight(const Geo<float>& g, W w)
 {
-    const int dr = (int)((w.hi >> 8) & 3u) - 2;
-    const int dv = (int)((w.hi >> 10) & 15u) - 8;
-    const int dt = (int)((w.hi >> 14) & 3u) - 2;
-    const unsigned q2 = (unsigned)(w.lo >> 48) | ((w.hi & 0xffu) << 16);
-    const float t0 = (float)(unsigned)(w.lo & 0xffffffu) * (1.0f / kFootQ);
-    const float t1 = (float)(unsigned)((w.lo >> 24) & 0xffffffu) * (1.0f / kFootQ);
-    const float t2 = (float)q2 * (1.0f / kFootQ);
-    auto f = [](int off, float t) { return off == 0 ? 1.0f - t : (off == -1 ? t : 0.0f); };
-    return f(dr, t0) * f(dv, t1) * f(dt, t2) * f(g.foot_dm, g.foot_tm);
+    const FootCell f = foot_cell_of(g, w);
+    auto wt = [](int off, float t) { return off == 0 ? 1.0f - t : (off == -1 ? t : 0.0f); };
+    return wt(f.dr, f.t[0]) * wt(f.dv, f.t[1]) * wt(f.dt, f.t[2]) * wt(g.foot_dm, g.foot_tm);
 }
 
 // Blend of increments d at node j's recomputed foot for a policy code: the
@@ -229,7 +261,8 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                                             unsigned* __restrict__ feet_hi, float* __restrict__ inc,
                                             float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
                                             int j0, int end, int stride, S& resid, bool& bad,
-                                            const Feet64 f64 = Feet64(), int* reach = nullptr)
+                                            const Feet64 f64 = Feet64(), int* reach = nullptr,
+                                            bool feet8 = true)
 {
     constexpr bool kIsVI = MODE == kVI || MODE == kVIDiag;
     constexpr bool kSearch = kIsVI || MODE == kImproveFull || MODE == kImproveWalk;
@@ -284,7 +317,8 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
             resid = fmax(resid, (S)fabs(vnew - vj));
             bad = bad || !isfinite(vnew);
         }
-    } else if constexpr (MODE == kEvalFeet || MODE == kIncr || MODE == kEvalFeetDiag || MODE == kIncrDiag) {
+    } else if constexpr (MODE == kEvalFeet || MODE == kEvalFeet8 || MODE == kIncr || MODE == kEvalFeetDiag ||
+                         MODE == kIncrDiag) {
         constexpr bool kDiag = MODE == kEvalFeetDiag || MODE == kIncrDiag;
         // frozen feet: gather-bound.  With PREFETCH the next node's foot and
         // value are fetched while this node's corners are in flight; without
@@ -292,34 +326,39 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
         // The feet are read once per sweep: evict-first loads keep L1 and L2
         // for the gathered V.
         constexpr bool kPrefetch = PREFETCH;
+        // kEvalFeet8 reads one 8-byte word per node, the other modes the
+        // 24-bit word pair
+        constexpr bool kF8 = MODE == kEvalFeet8;
+        typedef typename std::conditional<kF8, unsigned long long, FootWord>::type FW;
+        auto load_foot = [&](int k) -> FW {
+            if constexpr (kF8) return __ldcs(&feet_lo[k]);
+            else return FootWord{__ldcs(&feet_lo[k]), __ldcs(&feet_hi[k])};
+        };
         const bool first = incr_flags & 1, last = incr_flags & 2;
         int j = j0;
-        FootWord w_next{0ull, 0u};
+        FW w_next{};
         S v_next = (S)0;
         if (kPrefetch && j < end) {
-            w_next.lo = __ldcs(&feet_lo[j]);
-            w_next.hi = __ldcs(&feet_hi[j]);
+            w_next = load_foot(j);
             v_next = Vin[j];
         }
         for (; j < end; j += stride) {
-            FootWord w;
+            FW w;
             S vj;
             if constexpr (kPrefetch) {
                 w = w_next;
                 vj = v_next;
                 if (j + stride < end) {
-                    w_next.lo = __ldcs(&feet_lo[j + stride]);
-                    w_next.hi = __ldcs(&feet_hi[j + stride]);
+                    w_next = load_foot(j + stride);
                     v_next = Vin[j + stride];
                 }
             } else {
-                w.lo = __ldcs(&feet_lo[j]);
-                w.hi = __ldcs(&feet_hi[j]);
+                w = load_foot(j);
                 vj = Vin[j];
             }
-            const int kind = (int)((w.hi >> 16) & 3u);
+            const int kind = foot_kind(w);
             S vnew = (S)0;
-            if constexpr (MODE == kEvalFeet || MODE == kEvalFeetDiag) {
+            if constexpr (MODE == kEvalFeet || MODE == kEvalFeet8 || MODE == kEvalFeetDiag) {
                 float ws = 0.0f;
                 if (kind == kFootInside) {
                     if constexpr (kDiag) ws = foot_self_weight(g, w);
@@ -487,12 +526,21 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                     if (!kIsVI) code[j] = (uint16_t)c;
                     if constexpr (kGeo32 && kImprove) {
                         if (feet_lo) {
+                            // 8-byte feet for the plain evaluation of FP32
+                            // values (feet8), else the 24-bit word pair
                             int cl[4];
-                            const FootWord w = ev.foot_of(c, cl);
-                            feet_lo[j] = w.lo;
-                            feet_hi[j] = w.hi;
-                            if (reach && ((w.hi >> 16) & 3u) != kFootOut)
-                                *reach = max(*reach, cell_reach<REDUCED>(g, j, cl));
+                            int kind;
+                            if (!kPolish && feet8) {
+                                const unsigned long long w = ev.foot8_of(c, cl);
+                                feet_lo[j] = w;
+                                kind = foot_kind(w);
+                            } else {
+                                const FootWord w = ev.foot_of(c, cl);
+                                feet_lo[j] = w.lo;
+                                feet_hi[j] = w.hi;
+                                kind = foot_kind(w);
+                            }
+                            if (reach && kind != kFootOut) *reach = max(*reach, cell_reach<REDUCED>(g, j, cl));
                         }
                     }
                     if constexpr (!kGeo32 && kImprove) {
@@ -512,9 +560,13 @@ __device__ __forceinline__ void sweep_nodes(const Geo<G>& g, const Table<G>& T, 
                 if constexpr (MODE == kEvalDiag) vnew = (S)diag_step(g, vj, vnew, ws);
             } else if constexpr (kGeo32 && kImprove) {
                 if (feet_lo) {
-                    const FootWord w = foot_word_kind(kFootTarget);
-                    feet_lo[j] = w.lo;
-                    feet_hi[j] = w.hi;
+                    if (!kPolish && feet8) {
+                        feet_lo[j] = foot8_kind(kFootTarget);
+                    } else {
+                        const FootWord w = foot_word_kind(kFootTarget);
+                        feet_lo[j] = w.lo;
+                        feet_hi[j] = w.hi;
+                    }
                 }
             } else if constexpr (!kGeo32 && kImprove) {
                 if (f64.w) f64.w[j] = (unsigned long long)kFootTarget << 32;
@@ -579,8 +631,10 @@ __host__ __device__ constexpr bool eval_prefetch()
 template <int MODE, bool REDUCED>
 __host__ __device__ constexpr int big_block()
 {
-    return (MODE == kIncr || MODE == kIncrDiag || MODE == kEvalFeet || (MODE == kEvalFeetDiag && REDUCED)) ? 768
-           : (MODE == kEvalFeet || MODE == kEvalFeetDiag || MODE == kEvalFeet64 || MODE == kEvalFeet64Diag) ? 1024
+    return (MODE == kIncr || MODE == kIncrDiag || MODE == kEvalFeet || MODE == kEvalFeet8 ||
+            (MODE == kEvalFeetDiag && REDUCED))
+               ? 768
+           : (MODE == kEvalFeetDiag || MODE == kEvalFeet64 || MODE == kEvalFeet64Diag) ? 1024
                                                                                         : kBlock;
 }
 
@@ -601,7 +655,7 @@ constexpr int min_blocks()
     if (std::is_same<G, float>::value && std::is_same<S, float>::value &&
         (MODE == kImproveWalk || MODE == kImproveFull))
         return 3;
-    return ((MODE == kEvalFeet || MODE == kEvalFeetDiag) && !REDUCED)   ? 8
+    return ((MODE == kEvalFeet || MODE == kEvalFeet8 || MODE == kEvalFeetDiag) && !REDUCED) ? 8
            : (MODE == kIncr || MODE == kIncrDiag || MODE == kEvalFeetDiag) ? 6
            : feet64                                                      ? 4
                                                                          : 1;
@@ -613,7 +667,7 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
              uint16_t* __restrict__ code, unsigned long long* __restrict__ feet_lo, unsigned* __restrict__ feet_hi,
              float* __restrict__ inc, float* __restrict__ acc, double* __restrict__ V64, int incr_flags,
              Ctl* __restrict__ ctl, unsigned long long* __restrict__ ring, int ring_mask, long long sweep,
-             int check_prev, double tol, const Feet64 f64)
+             int check_prev, double tol, const Feet64 f64, int feet8)
 {
     constexpr bool kSearch = MODE == kVI || MODE == kVIDiag || MODE == kImproveFull || MODE == kImproveWalk;
     if (*(volatile int*)&ctl->stop) return;
@@ -645,7 +699,7 @@ sweep_kernel(const __grid_constant__ Geo<G> g, const S* __restrict__ Vin, S* __r
     int reach = 0;
     sweep_nodes<G, S, MODE, REDUCED, DYN, eval_prefetch<MODE, REDUCED>()>(
         g, T, Vin, Vout, code, feet_lo, feet_hi, inc, acc, V64, incr_flags, j0, end, stride, resid, bad, f64,
-        kReach ? &reach : nullptr);
+        kReach ? &reach : nullptr, feet8 != 0);
     if constexpr (kReach) {
         // the stored feet's reach, for the multi-level evaluation that follows
         reach = __reduce_max_sync(0xffffffffu, (unsigned)reach);
@@ -670,7 +724,8 @@ cudaError_t launch_sized(const SweepLaunch<G, S>& L)
     int blocks = (int)(need < cap ? need : cap);
     if (blocks < 1) blocks = 1;
     kern<<<blocks, B, 0, L.stream>>>(L.g, L.Vin, L.Vout, L.code, L.feet_lo, L.feet_hi, L.inc, L.acc, L.V64,
-                                      L.incr_flags, L.ctl, L.ring, L.ring_mask, L.sweep, L.check_prev, L.tol, L.f64);
+                                      L.incr_flags, L.ctl, L.ring, L.ring_mask, L.sweep, L.check_prev, L.tol, L.f64,
+                                      L.feet8);
     return cudaGetLastError();
 }
 
@@ -697,6 +752,9 @@ cudaError_t launch_mode(const SweepLaunch<G, S>& L)
     case kEval: return launch_one<G, S, kEval, REDUCED, DYN>(L);
     case kEvalFeet:
         if constexpr (f32) return L.feet_lo ? launch_one<G, S, kEvalFeet, REDUCED, DYN>(L) : cudaErrorInvalidValue;
+        return cudaErrorInvalidValue;
+    case kEvalFeet8:
+        if constexpr (f32) return L.feet_lo ? launch_one<G, S, kEvalFeet8, REDUCED, DYN>(L) : cudaErrorInvalidValue;
         return cudaErrorInvalidValue;
     case kIncr:
         if constexpr (f32)

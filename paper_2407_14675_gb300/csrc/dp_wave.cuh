@@ -91,38 +91,16 @@ __device__ __forceinline__ int ld_volatile(const int* p)
 
 // Blend at a frozen foot of kind kFootInside with coherent corner loads (the
 // values were written by other blocks of this launch): eval_foot's
-// arithmetic.
-template <bool REDUCED>
-__device__ __forceinline__ float eval_foot_coherent(const Geo<float>& g, const float* V, int j, FootWord w, float vj)
+// arithmetic, either foot format.
+template <bool REDUCED, typename W>
+__device__ __forceinline__ float eval_foot_coherent(const Geo<float>& g, const float* V, int j, W w, float vj)
 {
-    const int dr = (int)((w.hi >> 8) & 3u) - 2;
-    const int dv = (int)((w.hi >> 10) & 15u) - 8;
-    const int dt = (int)((w.hi >> 14) & 3u) - 2;
-    const unsigned q2 = (unsigned)(w.lo >> 48) | ((w.hi & 0xffu) << 16);
-    float t[4];
-    t[0] = (float)(unsigned)(w.lo & 0xffffffu) * (1.0f / kFootQ);
-    t[1] = (float)(unsigned)((w.lo >> 24) & 0xffffffu) * (1.0f / kFootQ);
-    t[2] = (float)q2 * (1.0f / kFootQ);
-    t[3] = g.foot_tm;
+    const FootCell f = foot_cell_of(g, w);
     int base[4];
-    if (!REDUCED) {
-        const int b0 = j + dr * g.stride[0] + dv * g.stride[1] + dt * g.stride[2] + g.foot_dm;
-        base[0] = b0;
-        base[1] = b0 + g.stride[1];
-        base[2] = b0 + g.stride[0];
-        base[3] = b0 + g.stride[0] + g.stride[1];
-    } else {
-        int i[4], c[4];
-        decode_node(g, j, i);
-        c[0] = i[0] + dr;
-        c[1] = i[1] + dv;
-        c[2] = i[2] + dt;
-        c[3] = i[3] + g.foot_dm;
-        cell_rows<float, true>(g, c, base);
-    }
+    foot_rows<REDUCED>(g, j, f.dr, f.dv, f.dt, base);
     Corners<float> K;
     load_rows_f32<true>(V, base, g.n_m, vj, K);
-    return K.blend(t);
+    return K.blend(f.t);
 }
 
 // Q1 interpolation at node j's foot for a policy code, coherent loads:
@@ -262,10 +240,13 @@ __global__ void __launch_bounds__(kWaveBlock, 3) wave_kernel(const __grid_consta
         bool bad = false;
 #pragma unroll 1
         for (int j = c * kWaveChunk + threadIdx.x; j < j_end; j += kWaveBlock) {
-            FootWord w;
-            w.lo = __ldcs(&a.feet_lo[j]);
-            w.hi = __ldcs(&a.feet_hi[j]);
-            const int kind = (int)((w.hi >> 16) & 3u);
+            // plain evaluation: 8-byte feet; diagonal-solved evaluation and
+            // increments: the word pair
+            constexpr bool kF8 = MODE == kEvalFeet8;
+            typename std::conditional<kF8, unsigned long long, FootWord>::type w;
+            if constexpr (kF8) w = __ldcs(&a.feet_lo[j]);
+            else w = FootWord{__ldcs(&a.feet_lo[j]), __ldcs(&a.feet_hi[j])};
+            const int kind = foot_kind(w);
             float vnew = 0.0f;
             if constexpr (!kInc) {
                 const float vj = ld_coherent(Vin + j);
@@ -352,6 +333,7 @@ cudaError_t launch_wave_dyn(const WaveArgs& a, int mode, cudaStream_t st, int sm
 {
     switch (mode) {
     case kEvalFeet: return launch_wave_mode<kEvalFeet, REDUCED, DYN>(a, st, sm_count);
+    case kEvalFeet8: return launch_wave_mode<kEvalFeet8, REDUCED, DYN>(a, st, sm_count);
     case kEvalFeetDiag: return launch_wave_mode<kEvalFeetDiag, REDUCED, DYN>(a, st, sm_count);
     case kIncr: return launch_wave_mode<kIncr, REDUCED, DYN>(a, st, sm_count);
     case kIncrDiag: return launch_wave_mode<kIncrDiag, REDUCED, DYN>(a, st, sm_count);

@@ -22,6 +22,7 @@ DP_DYN_ORBIT, DP_DYN_UNIT_SPEED, DP_DYN_POLAR = 0, 1, 2
 DP_CODE_OFF = 65535
 DP_SWEEP_VI, DP_SWEEP_IMPROVE_FULL, DP_SWEEP_IMPROVE_WALK, DP_SWEEP_EVAL = 0, 1, 2, 3
 DP_SWEEP_EVAL_DIAG, DP_SWEEP_VI_DIAG = 4, 5
+DP_FOOT_AUTO, DP_FOOT_WORD8, DP_FOOT_PAIR = 0, 1, 2
 DP_EVAL_JACOBI, DP_EVAL_GMRES, DP_EVAL_DIAG = 0, 1, 2
 DP_GMRES_MAX_RESTART = 64
 
@@ -208,6 +209,7 @@ def load(path: Optional[str] = None):
         "dp_mlp_train_grid": [_P, _P, C.POINTER(dp_mlp_train_opts), C.POINTER(dp_mlp_train_stats)],
         "dp_mlp_apply_gradients": [_P, _P, C.c_int64, C.c_double],
         "dp_set_wave_wait_limit": [C.c_int64],
+        "dp_set_foot_format": [_P, C.c_int32],
         "dp_mlp_set_wait_limit": [_P, C.c_int32],
         "dp_warm_start": [_P, _P, _dp],
         "dp_warm_start_from_grid": [_P, _P, _dp],
@@ -458,6 +460,9 @@ class Grid:
     def sweep(self, mode):
         return dp_bellman_sweep(self.h, mode)
 
+    def set_foot_format(self, fmt):
+        dp_set_foot_format(self.h, fmt)
+
     def value_iterate(self, **kw):
         return dp_value_iterate(self.h, make_opts(**kw))
 
@@ -652,6 +657,10 @@ def dp_mlp_apply_gradients(mlp: int, grads, lr=1e-3):
 
 def dp_set_wave_wait_limit(ns: int):
     _check(load().dp_set_wave_wait_limit(ns))
+
+
+def dp_set_foot_format(h, fmt: int):
+    _check(load().dp_set_foot_format(h, fmt))
 
 
 def dp_mlp_set_wait_limit(mlp: int, polls: int):

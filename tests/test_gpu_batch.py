@@ -141,3 +141,30 @@ def test_batch_autotune_and_errors(dp):
         with pytest.raises(dp.DPError) as e:
             dp.Batch([probs[1], bad_p])
         assert e.value.code == dp.DP_EINVAL and "transfer 1" in str(e.value)
+
+
+@pytest.mark.parametrize("solver,polish", [("diag", 0), ("sweeps", 1)])
+def test_batch_standalone_evaluation_after_a_solve(dp, solver, polish):
+    # the frozen feet a batched solve leaves behind: word pairs after a
+    # diagonal-solved solve (FP32 values), word pairs of the FP64-value phase
+    # after a polished one (switch at the first improvement); a stand-alone
+    # evaluation sweep afterwards reads or recomputes them and matches the
+    # oracle transfer by transfer
+    probs = W.batch_transfers(count=3, seed=7, sizes=(9, 11))
+    ors = [oracle.Oracle(p) for p in probs]
+    kw = dict(tol=1e-6, max_sweeps=40, n_eval=10, polish=polish)
+    if solver == "diag":
+        kw["eval_solver"] = dp.DP_EVAL_DIAG
+    if polish:
+        kw["switch_tol"] = 100.0
+    with dp.Batch(probs) as b:
+        rc, tot, per = b.policy_iterate(**kw)
+        if polish:
+            assert all(s["switch_outer"] >= 0 for s in per)
+        before = [(b.get_value(i), b.get_policy(i)) for i in range(b.count)]
+        b.sweep(dp.DP_SWEEP_EVAL)
+        for i, (p, o) in enumerate(zip(probs, ors)):
+            V, codes = before[i]
+            v_o = o.sweep(V, mode=oracle.EVAL, codes=codes)[0]
+            _check_values(b.get_value(i), v_o, TOL32, "transfer %d" % i, o=o, nodes=np.arange(p.nodes),
+                          codes=codes)

@@ -51,6 +51,8 @@ def test_eval_diag_sweep_fp32_frozen_feet_and_recomputed(dp):
     V0 = W.smooth_value(p, 43)
     V0[o.target.astype(bool)] = 0.0
     with dp.Grid(p) as g:
+        # the diagonal-solved evaluation reads the 24-bit word pairs
+        g.set_foot_format(dp.DP_FOOT_PAIR)
         # recomputed feet: a policy set from the host has no frozen feet
         codes = W.random_codes(p, 44)
         g.set_value(V0)
@@ -250,17 +252,21 @@ def test_fp64_phase_evaluation_count(dp):
         assert e.value.code == dp.DP_EINVAL
 
 
-def test_large_grid_block_layout_sweeps_match_oracle(dp):
+@pytest.mark.parametrize("fmt", ["word8", "pair"])
+def test_large_grid_block_layout_sweeps_match_oracle(dp, fmt):
     # a reduced grid large enough for the large-block layout of the frozen-feet
     # sweeps (384,580 stored nodes: every SM gets a 1024- or 768-thread
     # block): one plain and one diagonal-solved evaluation sweep at the feet
-    # an improvement stored, against the oracle
+    # an improvement stored (8-byte words: the plain sweep reads them, the
+    # diagonal-solved one recomputes; word pairs: both read them), against
+    # the oracle
     p = W.config2(n=35)
     o = oracle.Oracle(p)
     idx = np.flatnonzero(o.active)
     V = W.smooth_value(p, 48)
     V[o.target.astype(bool)] = 0.0
     with dp.Grid(p) as g:
+        g.set_foot_format(dp.DP_FOOT_WORD8 if fmt == "word8" else dp.DP_FOOT_PAIR)
         g.set_value(V[idx])
         g.sweep(dp.DP_SWEEP_IMPROVE_FULL)
         V1, c1 = g.get_value(), g.get_policy()

@@ -506,16 +506,20 @@ def test_errors(dp):
 
 # ------------------------------------------------------------ frozen feet --
 
+@pytest.mark.parametrize("fmt", ["word8", "pair"])
 @pytest.mark.parametrize("p", [W.config1(n=25), W.config2(n=31)], ids=["full", "reduced"])
-def test_frozen_feet_match_recomputed_evaluation(dp, p):
+def test_frozen_feet_match_recomputed_evaluation(dp, p, fmt):
     # After an improvement sweep the evaluation sweeps read each node's stored
-    # foot (24-bit cell fractions) instead of recomputing the Heun step; the
-    # result must match the recomputing sweep (the same codes set again, which
-    # invalidates the stored feet) to the fraction quantisation (< 1e-5 M).
+    # foot (an 8-byte word with 18-bit cell fractions, or the word pair with
+    # 24-bit ones) instead of recomputing the Heun step; the result must match
+    # the recomputing sweep (the same codes set again, which invalidates the
+    # stored feet) to the fraction quantisation: at most 3 * 2^-19 of a cell's
+    # value spread per sweep, far below 1e-5 M.
     # GPU against GPU: both forms are checked against the oracle elsewhere.
     V = W.smooth_value(p, 81)
     o = oracle.Oracle(p)
     with dp.Grid(p) as g:
+        g.set_foot_format(dp.DP_FOOT_WORD8 if fmt == "word8" else dp.DP_FOOT_PAIR)
         idx = g.active_index()
         g.set_value(V[idx])
         g.sweep(dp.DP_SWEEP_IMPROVE_FULL)
@@ -527,3 +531,35 @@ def test_frozen_feet_match_recomputed_evaluation(dp, p):
         g.sweep(dp.DP_SWEEP_EVAL)                 # recomputed
         v_full = g.get_value()
     assert np.abs(v_feet - v_full).max() <= 1e-5 * o.M
+
+
+def test_feet_of_the_fp64_value_phase_are_not_read_as_fp32_feet(dp, small1):
+    # An FP64-value improvement stores each foot as the 24-bit word pair, an
+    # FP32-value improvement of a plain-evaluation solve as one 8-byte word.
+    # A grid returned to FP32 values after the FP64 phase (set_value) still
+    # holds the word pairs: its evaluation sweep must read them as pairs, and
+    # after the next FP32 improvement read the 8-byte words; both against the
+    # oracle.  An unknown format is refused.
+    p, o = small1
+    with dp.Grid(p) as g:
+        with pytest.raises(dp.DPError) as e:
+            g.set_foot_format(3)
+        assert e.value.code == dp.DP_EINVAL
+        rc, st = g.policy_iterate(tol=0.0, max_sweeps=3, n_eval=5, n_eval_fp64=5, polish=1, switch_tol=100.0,
+                                  warm=0)
+        assert st.switch_outer >= 0 and dp.dp_grid_get_info(g.h)["fp64_values"]
+        V, codes = g.get_value(), g.get_policy()
+        g.set_value(V)                            # FP32 values, the word pairs still stored
+        g.sweep(dp.DP_SWEEP_EVAL)
+        v_eval = g.get_value()
+        g.set_value(V)
+        g.sweep(dp.DP_SWEEP_IMPROVE_WALK)         # stores 8-byte feet
+        V1, c1 = g.get_value(), g.get_policy()
+        g.sweep(dp.DP_SWEEP_EVAL)
+        v_eval1 = g.get_value()
+    V32 = V.astype(np.float32).astype(np.float64)
+    V32[o.target.astype(bool)] = 0
+    want = o.sweep(V32, mode=oracle.EVAL, codes=codes)[0]
+    _check_values(v_eval, want, TOL32, "evaluation after the FP64 phase", o=o, nodes=np.arange(o.N), codes=codes)
+    want1 = o.sweep(V1, mode=oracle.EVAL, codes=c1)[0]
+    _check_values(v_eval1, want1, TOL32, "evaluation at 8-byte feet", o=o, nodes=np.arange(o.N), codes=c1)
