@@ -38,8 +38,8 @@ METRIC = "Bellman node-updates/s; time to ‖ΔV‖∞<1e-6, plain vs NN-warm-st
 # hash of the kernel sources they were taken on: a capture of an older kernel
 # is reported as stale (traffic null) instead of silently.
 EVAL_TRAFFIC = {
-    "61x4": {"bytes": (221.549824e6 + 18.479104e6 + 221.556992e6 + 15.677952e6) / 2, "src": "0362e0033161fe3f"},
-    "121x4_band": {"bytes": (911.792896e6 + 192.553728e6 + 910.852608e6 + 189.142528e6) / 2, "src": "0362e0033161fe3f"},
+    "61x4": {"bytes": (166.166272e6 + 17.993216e6 + 166.171648e6 + 15.406080e6) / 2, "src": "19c3a7e18fcc9498"},
+    "121x4_band": {"bytes": (688.096512e6 + 191.919360e6 + 688.418560e6 + 188.714752e6) / 2, "src": "19c3a7e18fcc9498"},
 }
 KERNEL_SOURCES = ("paper_2407_14675_gb300/csrc/dp_sweep.cuh", "paper_2407_14675_gb300/csrc/dp_device.cuh")
 UNIT = "node-updates/s"
@@ -663,7 +663,7 @@ def step_roofline(g, p, timed, key):
     eval_bytes = 10.0 * n_upd
     ach = eval_bytes / (eval_ms / 1e3) / 1e9
     traffic, tsrc = _traffic(key)
-    roof = {"bound": "hbm", "kernel": "sweep_kernel<float,float,EVAL_FEET,%s> (policy evaluation at the frozen feet)"
+    roof = {"bound": "hbm", "kernel": "sweep_kernel<float,float,EVAL_FEET8,%s> (policy evaluation at the 8-byte frozen feet)"
                                       % ("reduced" if p.reduced else "box"),
             "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "peak_source": (peak_src + " (MEASURED_PEAKS.json hbm_gbs, burst copy)") if peak_src == "measured"

@@ -1359,6 +1359,11 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
     };
     while (!gmres && outer < o->max_sweeps) {
         const bool mix = store_of(g) == kStoreMix;
+        // the FP32 phase of a polished solve stores the word pairs once its
+        // residual nears the switch: the FP64 phase then starts from the
+        // evaluation fixed point of the 24-bit fractions
+        if (g->foot_format == DP_FOOT_AUTO && !diag && g->fp32 && !mix && o->polish)
+            g->store_feet8 = !(res < kFoot8Zone * rule.tol);
         // evaluation sweeps per improvement in this phase, sweeps per outer iteration
         const int ne = mix ? fp64_phase_evals(o) : o->n_eval;
         const long long per = 1 + ne;

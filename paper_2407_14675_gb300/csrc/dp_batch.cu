@@ -79,7 +79,8 @@ struct BState {
     int stall, nonfinite, converged;
     int confirms;                  // full-table confirmations of the FP64 switch so far
     int confirming;                // this step's improvement confirms a switch
-    int pad;
+    int feet8;                     // FP32-value improvements store, and plain evaluations
+                                   //   read, 8-byte feet (1) or word pairs (0)
 };
 
 struct BParams {
@@ -87,7 +88,8 @@ struct BParams {
     long long max_outer;
     int n_eval, polish, walk, warm;
     int active;                    // transfers not finished (written by the control kernel)
-    int pad;
+    int feet8;                     // 1: plain evaluation (8-byte feet until the residual nears
+                                   //   the switch, as dp_policy_iterate), 0: word pairs
 };
 
 struct BArgs {
@@ -103,8 +105,6 @@ struct BArgs {
     float* acc;
     int count;
     int item_eval, item_imp;       // nodes per work item
-    int feet8;                     // FP32-value improvements store, and the plain evaluation
-                                   //   reads, 8-byte feet (1) or the word pairs (0)
 };
 
 // One of two buffers by a runtime bit, without indexing the parameter array
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kBlock, std::is_same<S, double>::value ? 2 : 3
         }
         sweep_nodes<float, S, MODE, false, DYN>(s_g, T, Vin, Vout, a.code + o, a.feet_lo + o, a.feet_hi + o, inc,
                                                 nullptr, nullptr, 0, first + threadIdx.x, end, kBlock, resid, bad,
-                                                Feet64(), nullptr, a.feet8 != 0);
+                                                Feet64(), nullptr, st.feet8 != 0);
         block_fold(resid, bad, &st.res_bits, &st.nonfinite);
     }
 }
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kBatchEvalBlock, 2) batch_eval_kernel(const BA
                     s_g, T, Vin, Vout, a.code + o, a.feet_lo + o, a.feet_hi + o, nullptr, nullptr, nullptr, 0,
                     first + threadIdx.x, end, kBatchEvalBlock, resid, bad);
             else if constexpr (FEET)
-                if (a.feet8)
+                if (st.feet8)
                     sweep_nodes<float, float, kEvalFeet8, false, DYN>(
                         s_g, T, Vin, Vout, a.code + o, a.feet_lo + o, nullptr, nullptr, nullptr, nullptr, 0,
                         first + threadIdx.x, end, kBatchEvalBlock, resid, bad);
@@ -283,6 +283,7 @@ __device__ void ctl_update(BState& s, const BParams& p, double M, int stage)
         s.res_bits = 0;
         s.imp32 = s.eval32 = s.imp64 = s.eval64 = 0;
         s.switch_outer = -1;
+        s.feet8 = p.feet8;
         break;
     case kStAfterImp: {
         if (s.phase == kPhDone) break;
@@ -353,12 +354,19 @@ __device__ void ctl_update(BState& s, const BParams& p, double M, int stage)
             s.widen = 1;
             s.phase = kPh64;
             s.switch_outer = s.imp32;
+        } else if (s.phase == kPh32 && p.polish) {
+            // the foot format of dp_policy_iterate's next step
+            const double sw = p.switch_tol > 0 ? p.switch_tol : 16.0 * 1.1920928955078125e-07 * M;
+            s.feet8 = p.feet8 && !(s.res < kFoot8Zone * sw);
         }
         break;
     }
     case kStManImpFull:
     case kStManImpWalk:
     case kStManEval:
+        // a stand-alone improvement stores 8-byte feet; a stand-alone
+        // evaluation reads the format stored last
+        if (stage != kStManEval) s.feet8 = 1;
         s.phase = kPh32;
         s.full_next = stage == kStManImpFull;
         s.evals = stage == kStManEval;
@@ -519,7 +527,6 @@ struct dp_batch {
     bool graph_diag = false;
     long long graph_launches = 0;
     bool feet_valid = false;
-    bool feet8 = true;             // format of the feet FP32-value improvements store (and stored last)
     long long device_bytes = 0;
 };
 
@@ -575,7 +582,6 @@ BArgs args_of(const dp_batch* b)
     a.count = b->count;
     a.item_eval = b->item_eval;
     a.item_imp = b->item_imp;
-    a.feet8 = b->feet8 ? 1 : 0;
     return a;
 }
 
@@ -719,6 +725,7 @@ int set_params(dp_batch* b, const dp_solve_opts* o, int warm)
     P.polish = o ? o->polish : 0;
     P.walk = o ? o->walk : 0;
     P.warm = warm;
+    P.feet8 = o ? (o->eval_solver != DP_EVAL_DIAG) : 1;
     BCK(cudaMemcpyAsync(b->d_par, b->h_par, sizeof(BParams), cudaMemcpyHostToDevice, b->st));
     return DP_OK;
 }
@@ -729,9 +736,6 @@ int manual_sweep(dp_batch* b, int32_t mode, double* ms)
 {
     int stage = mode == DP_SWEEP_IMPROVE_FULL ? kStManImpFull : mode == DP_SWEEP_IMPROVE_WALK ? kStManImpWalk
                                                                                                 : kStManEval;
-    // a stand-alone improvement stores 8-byte feet; a stand-alone evaluation
-    // reads the format stored last
-    if (stage != kStManEval) b->feet8 = true;
     BCK(launch_ctl(b, stage));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ms) {
@@ -1027,9 +1031,6 @@ int dp_batch_policy_iterate(dp_batch* b, const dp_solve_opts* o, dp_solve_stats*
         return bfail(DP_EINVAL, "batched policy iteration evaluates by plain or diagonal-solved sweeps only");
     const bool diag = o->eval_solver == DP_EVAL_DIAG;
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(DP_ECUDA, "cudaSetDevice failed");
-    // 8-byte feet for the plain evaluation, word pairs for the
-    // diagonal-solved one (the graph of a solver captures its format)
-    b->feet8 = !diag;
     const double t0 = now_ms();
     int rc;
     if ((rc = pull_state(b))) return rc;

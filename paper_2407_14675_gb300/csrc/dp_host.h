@@ -175,6 +175,12 @@ struct GmArgs {
 cudaError_t gm_cycle(const GmArgs<float, float>& a, const float* Vin, float* Vnext);
 cudaError_t gm_cycle(const GmArgs<float, float>& a, const double* Vin, double* Vnext);
 cudaError_t gm_cycle(const GmArgs<double, double>& a, const double* Vin, double* Vnext);
+// Residuals, in units of the FP32 -> FP64 switch tolerance, below which the
+// FP32 phase of a polished solve (plain evaluation) stores word pairs instead
+// of 8-byte feet, so that the FP64 phase starts from the evaluation fixed
+// point of the 24-bit fractions.
+constexpr double kFoot8Zone = 16.0;
+
 // Frozen feet of the resident policy (FP32 geometry), as an improvement sweep
 // stores them: the word pair, or the 8-byte word when feet_hi is nullptr.
 cudaError_t launch_feet(const Geo<float>& g, const uint16_t* code, unsigned long long* feet_lo, unsigned* feet_hi,
