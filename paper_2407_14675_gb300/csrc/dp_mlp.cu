@@ -68,6 +68,19 @@ __device__ __forceinline__ float gelu_grad(float z)
     return 0.5f * (1.0f + erff(z * kInvSqrt2)) + z * kInvSqrt2Pi * expf(-0.5f * z * z);
 }
 
+// 8 consecutive BF16 values (one 16-byte load) as floats.
+__device__ __forceinline__ void load_row8(const bf16* p, float a[8])
+{
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    const unsigned u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&u[q]);
+        a[2 * q] = __low2float(h2);
+        a[2 * q + 1] = __high2float(h2);
+    }
+}
+
 enum { kEpiFwd = 0, kEpiBwd = 1, kEpiAtomic = 2 };
 
 // Four doubles by value (the network's input box corners).
@@ -173,8 +186,10 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
             tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + c0, v);
             const size_t off = r * kH + n0 + c0;     // 16 consecutive columns, 64-byte aligned
             if (EPI == kEpiAtomic) {
+                // four 16-byte reductions (the row's 16 columns are 64-byte aligned)
 #pragma unroll
-                for (int q = 0; q < 16; ++q) atomicAdd(&cacc[off + q], v[q]);
+                for (int q = 0; q < 16; q += 4)
+                    atomicAdd(reinterpret_cast<float4*>(cacc + off + q), make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]));
                 continue;
             }
             float z[16];
@@ -410,29 +425,52 @@ __global__ void l1_fwd_kernel(const float* __restrict__ x, const float* __restri
 }
 
 // Output layer (256 -> 3): one warp per sample, each lane 8 consecutive
-// features (one 16-byte load), the three sums reduced across the warp; with
-// targets also the loss gradient dy = 2 (y - t) / (3 B) and the loss sum.
-__global__ void out_kernel(const bf16* __restrict__ h3, const float* __restrict__ P, const float* __restrict__ t,
-                           int count, float inv_n, float* __restrict__ y, float* __restrict__ dy,
-                           float* __restrict__ loss)
+// features (one 16-byte load), the three sums reduced across the warp.
+__global__ void out_kernel(const bf16* __restrict__ h3, const float* __restrict__ P, int count,
+                           float* __restrict__ y)
 {
     __shared__ float sW[3 * kH + 3];
     for (int i = threadIdx.x; i < 3 * kH + 3; i += blockDim.x) sW[i] = P[kOffW4 + i];   // W4 then b4
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    float l = 0.0f;
-    if (s < count) {
-        const uint4 v = *reinterpret_cast<const uint4*>(h3 + (size_t)s * kH + lane * 8);
-        const unsigned u[4] = {v.x, v.y, v.z, v.w};
-        float a[8];
+    if (s >= count) return;
+    float a[8];
+    load_row8(h3 + (size_t)s * kH + lane * 8, a);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&u[q]);
-            a[2 * q] = __low2float(h2);
-            a[2 * q + 1] = __high2float(h2);
-        }
-        float acc[3];
+    for (int k = 0; k < 3; ++k) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) sum += sW[k * kH + lane * 8 + q] * a[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) y[3 * (size_t)s + k] = sum + sW[3 * kH + k];
+    }
+}
+
+// The output layer of a training step with the first part of its backward
+// pass, one warp per sample (grid-stride over the samples): y = W4 h3 + b4,
+// the loss gradient dy = 2 (y - t) / (3 B), the loss sum, the output layer's
+// gradients dW4 += dy h3^T and db4 += dy (per-lane partial sums, reduced in
+// shared memory and added to G once per block), and
+// dz3 = (dy W4) * GELU'(z3) for the lane's 8 features.
+__global__ void __launch_bounds__(256) out_train_kernel(const bf16* __restrict__ h3, const float* __restrict__ P,
+                                                        const float* __restrict__ t, const float* __restrict__ z3,
+                                                        int count, float inv_n, bf16* __restrict__ dz3,
+                                                        float* __restrict__ G, float* __restrict__ loss)
+{
+    __shared__ float sW[3 * kH + 3];
+    __shared__ float sdW[3 * kH + 4];   // dW4, db4, loss
+    for (int i = threadIdx.x; i < 3 * kH + 3; i += blockDim.x) sW[i] = P[kOffW4 + i];
+    for (int i = threadIdx.x; i < 3 * kH + 4; i += blockDim.x) sdW[i] = 0.0f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
+    float w[3][8] = {}, b[3] = {}, l = 0.0f;
+    for (int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); s < count; s += warps) {
+        float a[8];
+        load_row8(h3 + (size_t)s * kH + lane * 8, a);
+        float dy[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             float sum = 0.0f;
@@ -440,69 +478,76 @@ __global__ void out_kernel(const bf16* __restrict__ h3, const float* __restrict_
             for (int q = 0; q < 8; ++q) sum += sW[k * kH + lane * 8 + q] * a[q];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            acc[k] = sum + sW[3 * kH + k];
-        }
-        if (lane == 0) {
+            const float r = (sum + sW[3 * kH + k]) - t[3 * (size_t)s + k];
+            l += r * r;
+            dy[k] = 2.0f * r * inv_n;
+            b[k] += dy[k];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (y) y[3 * (size_t)s + k] = acc[k];
-                if (t) {
-                    const float r = acc[k] - t[3 * (size_t)s + k];
-                    l += r * r;
-                    dy[3 * (size_t)s + k] = 2.0f * r * inv_n;
-                }
-            }
+            for (int q = 0; q < 8; ++q) w[k][q] += dy[k] * a[q];
         }
+        const float4* zp = reinterpret_cast<const float4*>(z3 + (size_t)s * kH + lane * 8);
+        const float4 z0 = zp[0], z1 = zp[1];
+        const float z[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+        unsigned u[4];
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+            const int i = lane * 8 + q;
+            const float g0 = dy[0] * sW[i] + dy[1] * sW[kH + i] + dy[2] * sW[2 * kH + i];
+            const float g1 = dy[0] * sW[i + 1] + dy[1] * sW[kH + i + 1] + dy[2] * sW[2 * kH + i + 1];
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(g0 * gelu_grad(z[q]), g1 * gelu_grad(z[q + 1]));
+            u[q / 2] = *reinterpret_cast<const unsigned*>(&h2);
+        }
+        *reinterpret_cast<uint4*>(dz3 + (size_t)s * kH + lane * 8) = make_uint4(u[0], u[1], u[2], u[3]);
     }
-    if (loss && lane == 0 && l != 0.0f) atomicAdd(loss, l);
-}
-
-// dz3 = (dy W4) * GELU'(z3), one thread per (sample, feature).
-__global__ void dz3_kernel(const float* __restrict__ dy, const float* __restrict__ P, const float* __restrict__ z3,
-                           int rows, bf16* __restrict__ dz3)
-{
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (long long)rows * kH) return;
-    const int s = (int)(e / kH), i = (int)(e % kH);
-    const float g = dy[3 * s] * P[kOffW4 + i] + dy[3 * s + 1] * P[kOffW4 + kH + i] + dy[3 * s + 2] * P[kOffW4 + 2 * kH + i];
-    dz3[e] = __float2bfloat16(g * gelu_grad(z3[e]));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) atomicAdd(&sdW[k * kH + lane * 8 + q], w[k][q]);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) atomicAdd(&sdW[3 * kH + k], b[k]);
+        atomicAdd(&sdW[3 * kH + 3], l);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * kH; i += blockDim.x) atomicAdd(&G[kOffW4 + i], sdW[i]);
+    if (threadIdx.x < 3) atomicAdd(&G[kOffB4 + threadIdx.x], sdW[3 * kH + threadIdx.x]);
+    if (threadIdx.x == 3 && loss) atomicAdd(loss, sdW[3 * kH + 3]);
 }
 
 // Per-feature reductions over a chunk of samples (thread = feature):
-//   db[o] += sum_s dz[s][o];  with X > 0 also dW[o][d] += sum_s dz[s][o] x[s][d]
-__global__ void feat_reduce_kernel(const bf16* __restrict__ dz, const float* __restrict__ x, int X, int rows,
-                                   int chunk, float* __restrict__ dW, float* __restrict__ db)
+//   db[o] += sum_s dz[s][o];  with X = 4 also dW[o][d] += sum_s dz[s][o] x[s][d]
+// X (0 or 4) is a template argument so that the accumulators stay in
+// registers.
+template <int X>
+__global__ void feat_reduce_kernel(const bf16* __restrict__ dz, const float* __restrict__ x, int rows, int chunk,
+                                   float* __restrict__ dW, float* __restrict__ db)
 {
+    __shared__ float4 sx[X == 4 ? 256 : 1];   // the chunk's inputs (chunk <= 256)
     const int o = threadIdx.x;   // 256 threads
     const int s0 = blockIdx.x * chunk, s1 = min(rows, s0 + chunk);
-    float b = 0.0f, w[4] = {0, 0, 0, 0};
+    if constexpr (X == 4) {
+        if (s0 + o < s1) sx[o] = reinterpret_cast<const float4*>(x)[s0 + o];
+        __syncthreads();
+    }
+    float b = 0.0f, w[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 8
     for (int s = s0; s < s1; ++s) {
         const float g = __bfloat162float(dz[(size_t)s * kH + o]);
         b += g;
-        for (int d = 0; d < X; ++d) w[d] += g * x[(size_t)s * X + d];
-    }
-    atomicAdd(&db[o], b);
-    for (int d = 0; d < X; ++d) atomicAdd(&dW[o * X + d], w[d]);
-}
-
-// Output-layer gradients: dW4[k][i] += sum_s dy[s][k] h3[s][i]; db4[k] += sum_s dy[s][k].
-__global__ void out_wgrad_kernel(const float* __restrict__ dy, const bf16* __restrict__ h3, int rows, int chunk,
-                                 float* __restrict__ dW4, float* __restrict__ db4)
-{
-    const int i = threadIdx.x;   // 256 threads
-    const int s0 = blockIdx.x * chunk, s1 = min(rows, s0 + chunk);
-    float w[3] = {0, 0, 0}, b[3] = {0, 0, 0};
-    for (int s = s0; s < s1; ++s) {
-        const float a = __bfloat162float(h3[(size_t)s * kH + i]);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            w[k] += dy[3 * s + k] * a;
-            b[k] += dy[3 * s + k];
+        if constexpr (X == 4) {
+            const float4 xs = sx[s - s0];
+            w[0] += g * xs.x;
+            w[1] += g * xs.y;
+            w[2] += g * xs.z;
+            w[3] += g * xs.w;
         }
     }
+    atomicAdd(&db[o], b);
+    if constexpr (X == 4) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) atomicAdd(&dW4[k * kH + i], w[k]);
-    if (i < 3) atomicAdd(&db4[i], b[i]);
+        for (int d = 0; d < 4; ++d) atomicAdd(&dW[o * 4 + d], w[d]);
+    }
 }
 
 // bf16 [rows][256] -> [256][rows] (32 x 32 tiles).
@@ -603,7 +648,7 @@ struct dp_mlp {
     long long step = 0;
     float *P = nullptr, *G = nullptr, *Am = nullptr, *Av = nullptr;
     bf16 *W2b = nullptr, *W3b = nullptr, *W2T = nullptr, *W3T = nullptr;
-    float *x = nullptr, *t = nullptr, *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *y = nullptr, *dy = nullptr;
+    float *x = nullptr, *t = nullptr, *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *y = nullptr;
     bf16 *h1 = nullptr, *h2 = nullptr, *h3 = nullptr, *dz1 = nullptr, *dz2 = nullptr, *dz3 = nullptr;
     bf16 *T1 = nullptr, *T2 = nullptr;
     double* states = nullptr;
@@ -626,7 +671,7 @@ void free_mlp(dp_mlp* m)
     cudaSetDevice(m->device);
     if (m->st) cudaStreamSynchronize(m->st);
     void* ps[] = {m->P, m->G, m->Am, m->Av, m->W2b, m->W3b, m->W2T, m->W3T, m->x, m->t, m->z1, m->z2, m->z3, m->y,
-                  m->dy, m->h1, m->h2, m->h3, m->dz1, m->dz2, m->dz3, m->T1, m->T2, m->states, m->loss, m->err};
+                  m->h1, m->h2, m->h3, m->dz1, m->dz2, m->dz3, m->T1, m->T2, m->states, m->loss, m->err};
     for (void* p : ps)
         if (p) cudaFree(p);
     if (m->h_loss) cudaFreeHost(m->h_loss);
@@ -698,9 +743,10 @@ cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int 
     return gemm_kc<EPI, kKC>(m, A, lda, B, ldb, rows, k_total, k_split, bias, zout, zin, hout, cacc);
 }
 
-// Forward of `count` rows held in m->x (rows padded to a multiple of 128).
-// save: keep z1..z3 for a backward pass.
-int forward(dp_mlp* m, int count, bool save, const float* targets, float inv_n)
+// Hidden layers of the forward pass of `count` rows held in m->x (rows
+// padded to a multiple of 128), through h3.  save: keep z1..z3 for a
+// backward pass.
+int forward_hidden(dp_mlp* m, int count, bool save)
 {
     const int rows = (count + kTileM - 1) / kTileM * kTileM;
     const long long e8 = (long long)rows * 32;
@@ -711,26 +757,32 @@ int forward(dp_mlp* m, int count, bool save, const float* targets, float inv_n)
                       nullptr));
     MCK(gemm<kEpiFwd>(m, m->h2, kH, m->W3b, kH, rows, kH, 1, m->P + kOffB3, save ? m->z3 : nullptr, nullptr, m->h3,
                       nullptr));
-    out_kernel<<<(count + 7) / 8, 256, 0, m->st>>>(m->h3, m->P, targets, count, inv_n, m->y, m->dy,
-                                                        targets ? m->loss : nullptr);
+    return DP_OK;
+}
+
+// Forward of `count` rows into m->y.
+int forward(dp_mlp* m, int count)
+{
+    int rc;
+    if ((rc = forward_hidden(m, count, false))) return rc;
+    out_kernel<<<(count + 7) / 8, 256, 0, m->st>>>(m->h3, m->P, count, m->y);
     MCK(cudaGetLastError());
     return DP_OK;
 }
 
 // Gradients of the mean squared error over a batch of `count` rows (count a
-// multiple of 512) into m->G; m->x / m->t hold the batch.
-int backward(dp_mlp* m, int count)
+// multiple of 512; m->x / m->t hold the batch) into m->G, the loss sum added
+// to m->loss.  The output layer and its backward pass run in one kernel.
+int forward_backward(dp_mlp* m, int count, float inv_n)
 {
     const int rows = count;
-    const long long e = (long long)rows * kH;
-    const unsigned eb = (unsigned)((e + 255) / 256);
     MCK(cudaMemsetAsync(m->G, 0, sizeof(float) * kParams, m->st));
-    dz3_kernel<<<eb, 256, 0, m->st>>>(m->dy, m->P, m->z3, rows, m->dz3);
+    int rc;
+    if ((rc = forward_hidden(m, count, true))) return rc;
+    const int ob = (int)std::min<long long>((count + 7) / 8, 2LL * m->sm_count);
+    out_train_kernel<<<ob, 256, 0, m->st>>>(m->h3, m->P, m->t, m->z3, count, inv_n, m->dz3, m->G, m->loss);
     MCK(cudaGetLastError());
-    const int chunk = 256;
-    out_wgrad_kernel<<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dy, m->h3, rows, chunk, m->G + kOffW4,
-                                                                     m->G + kOffB4);
-    MCK(cudaGetLastError());
+    const int chunk = 64;   // rows per block of the batch reductions (<= 256): 256 blocks at 16,384 rows
     // layer 3: dz2 = (dz3 W3) * GELU'(z2); dW3 = dz3^T h2; db3 = sum dz3
     MCK(gemm<kEpiBwd>(m, m->dz3, kH, m->W3T, kH, rows, kH, 1, nullptr, nullptr, m->z2, m->dz2, nullptr));
     dim3 tb(32, 8), tg(kH / 32, rows / 32);
@@ -739,8 +791,8 @@ int backward(dp_mlp* m, int count)
     MCK(cudaGetLastError());
     MCK(gemm<kEpiAtomic>(m, m->T1, rows, m->T2, rows, kH, rows, rows / kKC, nullptr, nullptr, nullptr, nullptr,
                          m->G + kOffW3));
-    feat_reduce_kernel<<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz3, nullptr, 0, rows, chunk, nullptr,
-                                                                       m->G + kOffB3);
+    feat_reduce_kernel<0><<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz3, nullptr, rows, chunk, nullptr,
+                                                                          m->G + kOffB3);
     MCK(cudaGetLastError());
     // layer 2: dz1 = (dz2 W2) * GELU'(z1); dW2 = dz2^T h1; db2 = sum dz2
     MCK(gemm<kEpiBwd>(m, m->dz2, kH, m->W2T, kH, rows, kH, 1, nullptr, nullptr, m->z1, m->dz1, nullptr));
@@ -749,11 +801,11 @@ int backward(dp_mlp* m, int count)
     MCK(cudaGetLastError());
     MCK(gemm<kEpiAtomic>(m, m->T1, rows, m->T2, rows, kH, rows, rows / kKC, nullptr, nullptr, nullptr, nullptr,
                          m->G + kOffW2));
-    feat_reduce_kernel<<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz2, nullptr, 0, rows, chunk, nullptr,
-                                                                       m->G + kOffB2);
+    feat_reduce_kernel<0><<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz2, nullptr, rows, chunk, nullptr,
+                                                                          m->G + kOffB2);
     // layer 1: dW1 = dz1^T x, db1 = sum dz1
-    feat_reduce_kernel<<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz1, m->x, 4, rows, chunk, m->G + kOffW1,
-                                                                       m->G + kOffB1);
+    feat_reduce_kernel<4><<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz1, m->x, rows, chunk, m->G + kOffW1,
+                                                                          m->G + kOffB1);
     MCK(cudaGetLastError());
     return DP_OK;
 }
@@ -813,8 +865,7 @@ int train_step(dp_mlp* m, const GridView& gv, int B, Box4 nlo, Box4 nhi, double 
             nlo, nhi, m->x, m->t, m->ts);
     MCK(cudaGetLastError());
     int rc;
-    if ((rc = forward(m, B, true, m->t, 1.0f / (3.0f * B)))) return rc;
-    if ((rc = backward(m, B))) return rc;
+    if ((rc = forward_backward(m, B, 1.0f / (3.0f * B)))) return rc;
     if ((rc = adam_launch(m, lr))) return rc;
     train_advance_kernel<<<1, 1, 0, m->st>>>(m->ts, B);
     MCK(cudaGetLastError());
@@ -932,7 +983,7 @@ int dp_mlp_create(const double* lo, const double* hi, int32_t batch_capacity, vo
     auto A = [&](auto** p, size_t n) { if (e == cudaSuccess) e = malloc_n(p, n); };
     A(&m->P, kParams); A(&m->G, kParams); A(&m->Am, kParams); A(&m->Av, kParams);
     A(&m->W2b, kH * kH); A(&m->W3b, kH * kH); A(&m->W2T, kH * kH); A(&m->W3T, kH * kH);
-    A(&m->x, C * 4); A(&m->t, C * 3); A(&m->y, C * 3); A(&m->dy, C * 3);
+    A(&m->x, C * 4); A(&m->t, C * 3); A(&m->y, C * 3);
     A(&m->z1, CH); A(&m->z2, CH); A(&m->z3, CH);
     A(&m->h1, CH); A(&m->h2, CH); A(&m->h3, CH); A(&m->dz1, CH); A(&m->dz2, CH); A(&m->dz3, CH);
     A(&m->T1, CH); A(&m->T2, CH);
@@ -997,7 +1048,7 @@ int dp_mlp_forward(dp_mlp* m, const double* states, int32_t n, float* out)
                             m->st));
         states_in_kernel<<<(cnt + 255) / 256, 256, 0, m->st>>>(m->states, cnt, lo, hi, m->x);
         MCK(cudaGetLastError());
-        int rc = forward(m, cnt, false, nullptr, 0.0f);
+        int rc = forward(m, cnt);
         if (rc) return rc;
         MCK(cudaMemcpyAsync(out + 3 * (size_t)s0, m->y, sizeof(float) * 3 * cnt, cudaMemcpyDeviceToHost, m->st));
     }
@@ -1014,9 +1065,8 @@ int dp_mlp_gradients(dp_mlp* m, const double* states, const float* targets, int3
     MCK(cudaMemcpyAsync(m->t, targets, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->st));
     states_in_kernel<<<(n + 255) / 256, 256, 0, m->st>>>(m->states, n, lo, hi, m->x);
     MCK(cudaMemsetAsync(m->loss, 0, sizeof(float), m->st));
-    int rc = forward(m, n, true, m->t, 1.0f / (3.0f * n));
+    int rc = forward_backward(m, n, 1.0f / (3.0f * n));
     if (rc) return rc;
-    if ((rc = backward(m, n))) return rc;
     MCK(cudaMemcpyAsync(grads, m->G, sizeof(float) * kParams, cudaMemcpyDeviceToHost, m->st));
     MCK(cudaMemcpyAsync(m->h_loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->st));
     if ((rc = check_err(m))) return rc;
@@ -1087,7 +1137,7 @@ int dp_warm_start(dp_mlp* m, dp_grid* grid, double* ms_out)
             g, (const double*)nullptr, gv.code, gv.tab_hi64, gv.tab_lo64, gv.n, 1, 0, s0, cnt, 0.0, nlo, nhi, m->x,
             nullptr);
         MCK(cudaGetLastError());
-        if ((rc = forward(m, cnt, false, nullptr, 0.0f))) return rc;
+        if ((rc = forward(m, cnt))) return rc;
         // the value goes to the storage-precision buffer (an FP32 grid holding
         // FP64 values after a polish returns to its FP32 values)
         if (gv.fp32)
