@@ -59,6 +59,13 @@ constexpr int kTileM = 128, kTileN = 128, kKC = 256;
 // (one CTA per SM; small batches: every slice at once), 64 KB for 128-wide
 // slices (three CTAs per SM overlap one another's loads and epilogues).
 constexpr int gemm_smem(int kc) { return (kTileM + kTileN) * kc * 2; }
+// MN-major operands (kEpiAtomicMN) get 32 KB more: the MMAs of a 256-wide
+// slice then read inside the allocation for either assignment of its
+// descriptors' two byte offsets (2048 along K, 128 along MN), at most
+// 92,416 bytes past an operand's start.
+constexpr int kMNPad = 32768;
+template <int EPI, int KC>
+constexpr int gemm_smem_of() { return gemm_smem(KC) + (EPI == 3 ? kMNPad : 0); }
 constexpr int kWaitPolls = 1 << 22;
 constexpr float kInvSqrt2 = 0.70710678118654752f, kInvSqrt2Pi = 0.39894228040143268f;
 
@@ -81,7 +88,7 @@ __device__ __forceinline__ void load_row8(const bf16* p, float a[8])
     }
 }
 
-enum { kEpiFwd = 0, kEpiBwd = 1, kEpiAtomic = 2 };
+enum { kEpiFwd = 0, kEpiBwd = 1, kEpiAtomic = 2, kEpiAtomicMN = 3 };
 
 // Four doubles by value (the network's input box corners).
 struct Box4 {
@@ -109,6 +116,13 @@ __device__ __forceinline__ void cp_async_wait_all()
 //   kEpiFwd:    z = acc + bias -> zout (optional, FP32), h = GELU(z) -> hout (bf16)
 //   kEpiBwd:    dz = acc * GELU'(zin) -> hout (bf16)
 //   kEpiAtomic: cacc += acc (FP32, split-K weight gradients)
+//   kEpiAtomicMN: the same with both operands MN-major: A[K range, 128
+//     blockIdx.x + i] and B[K range, 128 blockIdx.y + j] row-major with the
+//     tile's rows / columns contiguous (a weight gradient dz^T h straight
+//     from the activations, no transposed copies).  Core matrix (K block kb,
+//     MN block mb) holds 8 K-rows of 8 contiguous MN elements at byte
+//     (kb * 16 + mb) * 128: 128 bytes to the next MN block, 2048 to the next
+//     K block.
 template <int EPI, int KC>
 __global__ void __launch_bounds__(128)
 mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb, int k_per_cta,
@@ -130,7 +144,8 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
     const size_t row0 = (size_t)blockIdx.x * kTileM;
     const int n0 = blockIdx.y * kTileN;
     const int kbeg = blockIdx.z * k_per_cta;
-    constexpr unsigned idesc = umma_idesc_bf16(kTileM, kTileN);
+    constexpr bool kMN = EPI == kEpiAtomicMN;
+    constexpr unsigned idesc = umma_idesc_bf16(kTileM, kTileN) | (kMN ? (1u << 15) | (1u << 16) : 0u);
     constexpr int kGroups = KC / 8;                  // 16-byte groups per row of a slice
 
     int phase = 0;
@@ -142,17 +157,34 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
         // in shared memory.
         // the 16-byte groups go straight to shared memory (cp.async): every
         // group of the slice is in flight at once, none through registers
+        if constexpr (kMN) {
+            // a warp takes 8 K-rows x 4 consecutive MN blocks: 64 contiguous
+            // bytes of each row in global memory, 512 in shared memory
 #pragma unroll
-        for (int q = 0; q < kTileM * kGroups / 128; ++q) {
-            const int v = tid + 128 * q, grp = v >> 5, ln = v & 31;
-            const int row = (grp / (kGroups / 4)) * 8 + (ln & 7), kb = (grp % (kGroups / 4)) * 4 + (ln >> 3);
-            cp_async16(sA + (size_t)v * 16, A + (row0 + row) * (size_t)lda + k0 + kb * 8);
-        }
+            for (int q = 0; q < kTileM * kGroups / 128; ++q) {
+                const int v = tid + 128 * q, grp = v >> 5, ln = v & 31;
+                const int kr = (grp >> 2) * 8 + (ln & 7), mb = (grp & 3) * 4 + (ln >> 3);
+                cp_async16(sA + (size_t)v * 16, A + (size_t)(k0 + kr) * lda + row0 + mb * 8);
+            }
 #pragma unroll
-        for (int q = 0; q < kTileN * kGroups / 128; ++q) {
-            const int v = tid + 128 * q, grp = v >> 5, ln = v & 31;
-            const int row = (grp / (kGroups / 4)) * 8 + (ln & 7), kb = (grp % (kGroups / 4)) * 4 + (ln >> 3);
-            cp_async16(sB + (size_t)v * 16, B + (size_t)(n0 + row) * ldb + k0 + kb * 8);
+            for (int q = 0; q < kTileN * kGroups / 128; ++q) {
+                const int v = tid + 128 * q, grp = v >> 5, ln = v & 31;
+                const int kr = (grp >> 2) * 8 + (ln & 7), mb = (grp & 3) * 4 + (ln >> 3);
+                cp_async16(sB + (size_t)v * 16, B + (size_t)(k0 + kr) * ldb + n0 + mb * 8);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < kTileM * kGroups / 128; ++q) {
+                const int v = tid + 128 * q, grp = v >> 5, ln = v & 31;
+                const int row = (grp / (kGroups / 4)) * 8 + (ln & 7), kb = (grp % (kGroups / 4)) * 4 + (ln >> 3);
+                cp_async16(sA + (size_t)v * 16, A + (row0 + row) * (size_t)lda + k0 + kb * 8);
+            }
+#pragma unroll
+            for (int q = 0; q < kTileN * kGroups / 128; ++q) {
+                const int v = tid + 128 * q, grp = v >> 5, ln = v & 31;
+                const int row = (grp / (kGroups / 4)) * 8 + (ln & 7), kb = (grp % (kGroups / 4)) * 4 + (ln >> 3);
+                cp_async16(sB + (size_t)v * 16, B + (size_t)(n0 + row) * ldb + k0 + kb * 8);
+            }
         }
         cp_async_wait_all();
         fence_async_smem();
@@ -161,8 +193,11 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
             fence_after_sync();
 #pragma unroll
             for (int s = 0; s < KC / 16; ++s) {
-                const unsigned long long ad = umma_desc(smem_u32(sA) + s * 256, 128, kGroups * 128);
-                const unsigned long long bd = umma_desc(smem_u32(sB) + s * 256, 128, kGroups * 128);
+                // K step s: two K blocks (K-major: 256 bytes on; MN-major: 4096)
+                const unsigned long long ad =
+                    kMN ? umma_desc(smem_u32(sA) + s * 4096, 2048, 128) : umma_desc(smem_u32(sA) + s * 256, 128, kGroups * 128);
+                const unsigned long long bd =
+                    kMN ? umma_desc(smem_u32(sB) + s * 4096, 2048, 128) : umma_desc(smem_u32(sB) + s * 256, 128, kGroups * 128);
                 umma_bf16(tmem, ad, bd, idesc, (k0 > kbeg || s > 0) ? 1u : 0u);
             }
             umma_commit(&mbar);
@@ -185,7 +220,7 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
             float v[16];
             tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + c0, v);
             const size_t off = r * kH + n0 + c0;     // 16 consecutive columns, 64-byte aligned
-            if (EPI == kEpiAtomic) {
+            if (EPI == kEpiAtomic || EPI == kEpiAtomicMN) {
                 // four 16-byte reductions (the row's 16 columns are 64-byte aligned)
 #pragma unroll
                 for (int q = 0; q < 16; q += 4)
@@ -550,16 +585,6 @@ __global__ void feat_reduce_kernel(const bf16* __restrict__ dz, const float* __r
     }
 }
 
-// bf16 [rows][256] -> [256][rows] (32 x 32 tiles).
-__global__ void transpose_kernel(const bf16* __restrict__ src, int rows, bf16* __restrict__ dst)
-{
-    __shared__ bf16 tile[32][33];
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += 8) tile[k][threadIdx.x] = src[(size_t)(r0 + k) * kH + c0 + threadIdx.x];
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += 8) dst[(size_t)(c0 + k) * rows + r0 + threadIdx.x] = tile[threadIdx.x][k];
-}
-
 // Adam on the FP32 master parameters, then the BF16 copies of W2, W3 and
 // their transposes used by the tensor-core GEMMs.
 // The step count t (1 for the first step) comes from device memory; the
@@ -650,7 +675,6 @@ struct dp_mlp {
     bf16 *W2b = nullptr, *W3b = nullptr, *W2T = nullptr, *W3T = nullptr;
     float *x = nullptr, *t = nullptr, *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *y = nullptr;
     bf16 *h1 = nullptr, *h2 = nullptr, *h3 = nullptr, *dz1 = nullptr, *dz2 = nullptr, *dz3 = nullptr;
-    bf16 *T1 = nullptr, *T2 = nullptr;
     double* states = nullptr;
     float* loss = nullptr;
     int* err = nullptr;
@@ -671,7 +695,7 @@ void free_mlp(dp_mlp* m)
     cudaSetDevice(m->device);
     if (m->st) cudaStreamSynchronize(m->st);
     void* ps[] = {m->P, m->G, m->Am, m->Av, m->W2b, m->W3b, m->W2T, m->W3T, m->x, m->t, m->z1, m->z2, m->z3, m->y,
-                  m->h1, m->h2, m->h3, m->dz1, m->dz2, m->dz3, m->T1, m->T2, m->states, m->loss, m->err};
+                  m->h1, m->h2, m->h3, m->dz1, m->dz2, m->dz3, m->states, m->loss, m->err};
     for (void* p : ps)
         if (p) cudaFree(p);
     if (m->h_loss) cudaFreeHost(m->h_loss);
@@ -704,12 +728,12 @@ cudaError_t gemm_kc(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, i
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(mlp_gemm_kernel<EPI, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             gemm_smem(KC));
+                                             gemm_smem_of<EPI, KC>());
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid(rows / kTileM, kH / kTileN, k_split);
-    mlp_gemm_kernel<EPI, KC><<<grid, 128, gemm_smem(KC), m->st>>>(A, lda, B, ldb, k_total / k_split, bias, zout, zin,
+    mlp_gemm_kernel<EPI, KC><<<grid, 128, gemm_smem_of<EPI, KC>(), m->st>>>(A, lda, B, ldb, k_total / k_split, bias, zout, zin,
                                                                    hout, cacc, m->err, m->wait_polls);
     return cudaGetLastError();
 }
@@ -738,7 +762,7 @@ cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int 
                                                                                   m->err, m->wait_polls);
         return cudaGetLastError();
     }
-    if (EPI != kEpiAtomic && rows >= kManyRows)
+    if (EPI != kEpiAtomic && EPI != kEpiAtomicMN && rows >= kManyRows)
         return gemm_kc<EPI, kKC / 2>(m, A, lda, B, ldb, rows, k_total, k_split, bias, zout, zin, hout, cacc);
     return gemm_kc<EPI, kKC>(m, A, lda, B, ldb, rows, k_total, k_split, bias, zout, zin, hout, cacc);
 }
@@ -785,22 +809,15 @@ int forward_backward(dp_mlp* m, int count, float inv_n)
     const int chunk = 64;   // rows per block of the batch reductions (<= 256): 256 blocks at 16,384 rows
     // layer 3: dz2 = (dz3 W3) * GELU'(z2); dW3 = dz3^T h2; db3 = sum dz3
     MCK(gemm<kEpiBwd>(m, m->dz3, kH, m->W3T, kH, rows, kH, 1, nullptr, nullptr, m->z2, m->dz2, nullptr));
-    dim3 tb(32, 8), tg(kH / 32, rows / 32);
-    transpose_kernel<<<tg, tb, 0, m->st>>>(m->dz3, rows, m->T1);
-    transpose_kernel<<<tg, tb, 0, m->st>>>(m->h2, rows, m->T2);
-    MCK(cudaGetLastError());
-    MCK(gemm<kEpiAtomic>(m, m->T1, rows, m->T2, rows, kH, rows, rows / kKC, nullptr, nullptr, nullptr, nullptr,
-                         m->G + kOffW3));
+    MCK(gemm<kEpiAtomicMN>(m, m->dz3, kH, m->h2, kH, kH, rows, rows / kKC, nullptr, nullptr, nullptr, nullptr,
+                           m->G + kOffW3));
     feat_reduce_kernel<0><<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz3, nullptr, rows, chunk, nullptr,
                                                                           m->G + kOffB3);
     MCK(cudaGetLastError());
     // layer 2: dz1 = (dz2 W2) * GELU'(z1); dW2 = dz2^T h1; db2 = sum dz2
     MCK(gemm<kEpiBwd>(m, m->dz2, kH, m->W2T, kH, rows, kH, 1, nullptr, nullptr, m->z1, m->dz1, nullptr));
-    transpose_kernel<<<tg, tb, 0, m->st>>>(m->dz2, rows, m->T1);
-    transpose_kernel<<<tg, tb, 0, m->st>>>(m->h1, rows, m->T2);
-    MCK(cudaGetLastError());
-    MCK(gemm<kEpiAtomic>(m, m->T1, rows, m->T2, rows, kH, rows, rows / kKC, nullptr, nullptr, nullptr, nullptr,
-                         m->G + kOffW2));
+    MCK(gemm<kEpiAtomicMN>(m, m->dz2, kH, m->h1, kH, kH, rows, rows / kKC, nullptr, nullptr, nullptr, nullptr,
+                           m->G + kOffW2));
     feat_reduce_kernel<0><<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz2, nullptr, rows, chunk, nullptr,
                                                                           m->G + kOffB2);
     // layer 1: dW1 = dz1^T x, db1 = sum dz1
@@ -986,7 +1003,6 @@ int dp_mlp_create(const double* lo, const double* hi, int32_t batch_capacity, vo
     A(&m->x, C * 4); A(&m->t, C * 3); A(&m->y, C * 3);
     A(&m->z1, CH); A(&m->z2, CH); A(&m->z3, CH);
     A(&m->h1, CH); A(&m->h2, CH); A(&m->h3, CH); A(&m->dz1, CH); A(&m->dz2, CH); A(&m->dz3, CH);
-    A(&m->T1, CH); A(&m->T2, CH);
     A(&m->states, C * 4); A(&m->loss, 1); A(&m->err, 1);
     A(&m->ts, 1);
     if (e == cudaSuccess) e = cudaMallocHost(&m->h_loss, sizeof(float));

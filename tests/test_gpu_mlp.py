@@ -135,6 +135,25 @@ def test_gradients_match_bf16_reference(dp):
             assert rel < TOL_G, (li, pi, rel)
     for pi in range(2):
         assert np.linalg.norm(wrong[pi] - gref[1][pi]) / np.linalg.norm(gref[1][pi]) > 10 * TOL_G
+    # weight gradients element by element: dW = dz^T a summed in FP32 over BF16
+    # operands, so each entry is within 2^-6 sum_s |dz_si| |a_sj| of the
+    # reference (a BF16 rounding flip of either operand is 2^-8 of its term);
+    # a transposed or misplaced operand lies orders of magnitude outside
+    d = 2.0 * (Yb - T32) / n
+    for li in range(3, -1, -1):
+        a_in, z = cache[li]
+        if li < 3:
+            d = mlp.bf16(d * mlp.gelu_grad(z))
+        E = np.abs(d).T @ np.abs(a_in)
+        ratio = np.abs(got[li][0] - gref[li][0]) / (E + 1e-30)
+        assert ratio.max() <= 2.0 ** -6, (li, float(ratio.max()))
+        if li in (1, 2):
+            # planted: the 256 x 256 gradient transposed fails the same bound
+            assert (np.abs(got[li][0].T - gref[li][0]) / (E + 1e-30)).max() > 1.0
+        Wt = np.asarray(pr[li][0], np.float32).astype(np.float64)
+        if 0 < li < 3:
+            Wt = mlp.bf16(Wt)
+        d = d @ Wt
 
 
 def test_adam_matches_fp64_reference_from_the_same_gradients(dp):
