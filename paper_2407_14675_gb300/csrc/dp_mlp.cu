@@ -260,23 +260,25 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
     if (warp == 0) tmem_dealloc(tmem, kTileN);
 }
 
-// Forward GEMM of a large batch (inference over a grid), persistent: each
-// CTA takes one 128-column half of the layer (its 128 x 256 slice of the
-// weights stays in shared memory, 64 KB) and walks row tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...  The next tile's 128 x 256
-// activations are copied (cp.async) into the second of two 64 KB buffers
-// while the MMAs and the bias + GELU epilogue of the current tile run.
-// Same staging layout, MMAs and epilogue arithmetic as mlp_gemm_kernel<kEpiFwd>.
+// GEMM of a large batch (inference over a grid, and the training steps'
+// hidden layers), persistent: each CTA takes one 128-column half of the
+// layer (its 128 x 256 slice of the weights stays in shared memory, 64 KB)
+// and walks row tiles blockIdx.x, blockIdx.x + gridDim.x, ...  The next
+// tile's 128 x 256 activations are copied (cp.async) into the second of two
+// 64 KB buffers while the MMAs and the epilogue of the current tile run.
+// Same staging layout, MMAs and epilogue arithmetic as mlp_gemm_kernel<EPI>
+// (kEpiFwd with optional zout, or kEpiBwd).
 // Sixteen warps: four per quarter of the TMEM lanes, each taking a quarter
 // of the columns in the epilogue.
 constexpr int kPersistSmem = (kTileN + 2 * kTileM) * kKC * 2;   // 192 KB
 constexpr int kPersistThreads = 512;
 constexpr int kPersistParts = kPersistThreads / 128;            // column parts per TMEM lane quarter
 
+template <int EPI>
 __global__ void __launch_bounds__(kPersistThreads)
-mlp_fwd_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb, int tiles,
-                          const float* __restrict__ bias, bf16* __restrict__ hout, int* __restrict__ err,
-                          int polls)
+mlp_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb, int tiles,
+                      const float* __restrict__ bias, float* __restrict__ zout, const float* __restrict__ zin,
+                      bf16* __restrict__ hout, int* __restrict__ err, int polls)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sB = smem;                                  // 128 x 256
@@ -346,13 +348,23 @@ mlp_fwd_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __res
             float v[16], z[16];
             tmem_ld16(tmem + ((unsigned)(quarter * 32) << 16) + c0, v);
             const size_t off = r * kH + n0 + c0;
+            if (EPI == kEpiFwd) {
 #pragma unroll
-            for (int q = 0; q < 16; q += 4) {
-                const float4 b = *(const float4*)(bias + n0 + c0 + q);
-                z[q] = v[q] + b.x; z[q + 1] = v[q + 1] + b.y; z[q + 2] = v[q + 2] + b.z; z[q + 3] = v[q + 3] + b.w;
+                for (int q = 0; q < 16; q += 4) {
+                    const float4 b = *(const float4*)(bias + n0 + c0 + q);
+                    z[q] = v[q] + b.x; z[q + 1] = v[q + 1] + b.y; z[q + 2] = v[q + 2] + b.z; z[q + 3] = v[q + 3] + b.w;
+                    if (zout) *(float4*)(zout + off + q) = make_float4(z[q], z[q + 1], z[q + 2], z[q + 3]);
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) z[q] = gelu(z[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; q += 4) {
+                    const float4 zi = *(const float4*)(zin + off + q);
+                    z[q] = v[q] * gelu_grad(zi.x); z[q + 1] = v[q + 1] * gelu_grad(zi.y);
+                    z[q + 2] = v[q + 2] * gelu_grad(zi.z); z[q + 3] = v[q + 3] * gelu_grad(zi.w);
+                }
             }
-#pragma unroll
-            for (int q = 0; q < 16; ++q) z[q] = gelu(z[q]);
             unsigned pk[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -747,10 +759,10 @@ template <int EPI>
 cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int rows, int k_total, int k_split,
                  const float* bias, float* zout, const float* zin, bf16* hout, float* cacc)
 {
-    if (EPI == kEpiFwd && rows >= kManyRows && !zout && k_total == kKC && k_split == 1) {
+    if ((EPI == kEpiFwd || EPI == kEpiBwd) && rows >= kManyRows && k_total == kKC && k_split == 1) {
         static bool attr = false;
         if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(mlp_fwd_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaError_t e = cudaFuncSetAttribute(mlp_persistent_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  kPersistSmem);
             if (e != cudaSuccess) return e;
             attr = true;
@@ -758,8 +770,8 @@ cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int 
         const int tiles = rows / kTileM;
         const int per_half = std::max(1, std::min(tiles, m->sm_count / 2));
         dim3 grid(per_half, kH / kTileN);
-        mlp_fwd_persistent_kernel<<<grid, kPersistThreads, kPersistSmem, m->st>>>(A, lda, B, ldb, tiles, bias, hout,
-                                                                                  m->err, m->wait_polls);
+        mlp_persistent_kernel<EPI><<<grid, kPersistThreads, kPersistSmem, m->st>>>(A, lda, B, ldb, tiles, bias, zout,
+                                                                                   zin, hout, m->err, m->wait_polls);
         return cudaGetLastError();
     }
     if (EPI != kEpiAtomic && EPI != kEpiAtomicMN && rows >= kManyRows)

@@ -97,14 +97,18 @@ def test_large_batch_forward_equals_small_batches(dp):
     _check_forward(Yb[:4000], dp.unflatten_params(flat), X[:4000], p)
 
 
-def test_gradients_match_bf16_reference(dp):
+@pytest.mark.parametrize("n", [1024, 16384])
+def test_gradients_match_bf16_reference(dp, n):
+    # 16,384 rows: the hidden layers' GEMMs run the persistent, pipelined
+    # kernel of large batches (forward with the saved pre-activations, and
+    # the GELU' backward), 1,024 rows the one-tile-per-CTA kernel
     p = W.config1()
     params = W.mlp_init_params(seed=5)
-    X = _states(p, 1024, 6)
+    X = _states(p, n, 6)
     rng = np.random.default_rng(7)
-    T = rng.uniform(-1, 1, size=(1024, 3))
+    T = rng.uniform(-1, 1, size=(n, 3))
     flat = dp.flatten_params(params)
-    with dp.Mlp(p.lo, p.hi, batch_capacity=4096) as net:
+    with dp.Mlp(p.lo, p.hi, batch_capacity=max(4096, n)) as net:
         dp.dp_mlp_set_params(net.h, flat)
         g, loss = dp.dp_mlp_gradients(net.h, X, T)
     pr = dp.unflatten_params(flat)
@@ -115,8 +119,8 @@ def test_gradients_match_bf16_reference(dp):
     assert loss == pytest.approx(mlp.loss(Yb, T32), rel=1e-3)
     got = dp.unflatten_params(g)
     # planted: GELU' of layer 2 skipped (the first layer's gradients change)
-    n = Yb.size
-    d = 2.0 * (Yb - T32) / n
+    n_out = Yb.size
+    d = 2.0 * (Yb - T32) / n_out
     wrong = None
     for li in range(3, -1, -1):
         a_in, z = cache[li]
@@ -139,7 +143,7 @@ def test_gradients_match_bf16_reference(dp):
     # operands, so each entry is within 2^-6 sum_s |dz_si| |a_sj| of the
     # reference (a BF16 rounding flip of either operand is 2^-8 of its term);
     # a transposed or misplaced operand lies orders of magnitude outside
-    d = 2.0 * (Yb - T32) / n
+    d = 2.0 * (Yb - T32) / n_out
     for li in range(3, -1, -1):
         a_in, z = cache[li]
         if li < 3:
