@@ -505,7 +505,7 @@ def warm_start_leg(args, dp, W, torch, g1, p1, g2):
     closed loop from 1024 seeded states on the last solution."""
     p2 = W.config2()
     out = {"grid": "121^4 box, energy band [%.4f, %.4f]" % (p2.energy_lo, p2.energy_hi)}
-    with dp.Mlp(p1.lo, p1.hi, batch_capacity=65536) as net:
+    with dp.Mlp(p1.lo, p1.hi, batch_capacity=262144) as net:
         dp.dp_mlp_set_params(net.h, dp.flatten_params(W.mlp_init_params()))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
