@@ -225,12 +225,17 @@ def _oracle_worker(task):
 
 
 def oracle_parallel_rate(seconds_target=10.0, procs=None, n=121):
-    """The oracle on the host cores: one spawned process per core (at most 8:
-    each holds the band's 214M-node box value, 1.7 GB), each on its own sample
-    of the same step mix.  Aggregate node-updates / the slowest process's
-    time."""
+    """The oracle on the host cores: one spawned process per core (each holds
+    the band's 214M-node box value, 1.7 GB, so at most one per 3 GB of free
+    host memory), each on its own sample of the same step mix.  Aggregate
+    node-updates / the slowest process's time."""
     import multiprocessing as mp
-    procs = procs or min(os.cpu_count() or 1, 8)
+    if not procs:
+        try:
+            free_gb = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") / 2 ** 30
+        except (ValueError, OSError, AttributeError):
+            free_gb = 24.0
+        procs = max(1, min(os.cpu_count() or 1, 64, int(free_gb // 3)))
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs) as pool:
         res = pool.map(_oracle_worker, [(2407 + 97 * k, seconds_target, n) for k in range(procs)])
@@ -679,29 +684,37 @@ def step_roofline(g, p, timed, key):
 
 
 def e2e_pi_step(dp, torch, g, p, steps, world):
-    """The same step through the C ABI with host buffers: the value (FP64) and
-    the policy go up from pinned host memory before each step and come back
-    after it, inside the timed region."""
-    V_host = torch.empty(g.n, dtype=torch.float64, pin_memory=True)
+    """The same step through the C ABI with host buffers: the value and the
+    policy go up from pinned host memory before each step and come back
+    after it, inside the timed region.  The value travels in the grid's
+    storage precision (FP32 for the FP32 grids, dp_set_value_f32 /
+    dp_get_value_f32; FP64 otherwise)."""
+    from paper_2407_14675_gb300 import workloads as W
+    f32 = p.precision == W.FP32
+    V_host = torch.empty(g.n, dtype=torch.float32 if f32 else torch.float64, pin_memory=True)
     C_host = torch.empty(g.n, dtype=torch.int16, pin_memory=True)
     C_view = C_host.numpy().view(np.uint16)
-    dp.dp_get_value(g.h, g.n, out=V_host.numpy())
+    set_v = dp.dp_set_value_f32 if f32 else dp.dp_set_value
+    get_v = dp.dp_get_value_f32 if f32 else dp.dp_get_value
+    get_v(g.h, g.n, out=V_host.numpy())
     C_view[:] = g.get_policy()
     torch.cuda.synchronize()
     _barrier(world)
     t0 = time.perf_counter()
     updates = 0
     for _ in range(steps):
-        dp.dp_set_value(g.h, V_host)
+        set_v(g.h, V_host)
         dp.dp_set_policy(g.h, C_view)
         rc, st = g.policy_iterate(tol=0.0, max_sweeps=1, n_eval=p.n_eval, polish=0, warm=1)
-        dp.dp_get_value(g.h, g.n, out=V_host.numpy())
+        get_v(g.h, g.n, out=V_host.numpy())
         dp.dp_get_policy(g.h, g.n, out=C_view)
         updates += st.node_updates
     torch.cuda.synchronize()
     secs = _reduce_max(time.perf_counter() - t0, world)
+    vb = V_host.element_size()
     return {"value": _reduce_sum(float(updates), world) / secs, "unit": UNIT, "steps": steps,
-            "h2d_bytes_per_step": g.n * (8 + 2), "d2h_bytes_per_step": g.n * (8 + 2)}
+            "value_transfer": "FP32" if f32 else "FP64",
+            "h2d_bytes_per_step": g.n * (vb + 2), "d2h_bytes_per_step": g.n * (vb + 2)}
 
 
 def run_ours(args, world, rank, local):

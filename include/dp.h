@@ -243,6 +243,15 @@ int dp_get_active_index(const dp_grid* grid, int64_t* box_index, int64_t count);
  * storage precision of the grid (FP32 grids round to nearest). */
 int dp_set_value(dp_grid* grid, const double* host_V, int64_t count);
 int dp_get_value(const dp_grid* grid, double* host_V, int64_t count);
+/* The same with FP32 host values: half the bytes over the host link for FP32
+ * grids, whose stored values they are exactly (dp_get_value_f32 copies them
+ * without conversion; dp_set_value_f32 stores them unchanged).  On FP64
+ * grids, and on FP32 grids whose values have moved to FP64 (after a polish),
+ * dp_get_value_f32 rounds to nearest and dp_set_value_f32 widens exactly and
+ * returns the grid to FP32 values, as dp_set_value does.  Same errors as the
+ * FP64 calls. */
+int dp_set_value_f32(dp_grid* grid, const float* host_V, int64_t count);
+int dp_get_value_f32(const dp_grid* grid, float* host_V, int64_t count);
 
 /* Copy the policy (16-bit angle codes) in / out, compact order. */
 int dp_set_policy(dp_grid* grid, const uint16_t* host_codes, int64_t count);

@@ -1204,6 +1204,43 @@ int dp_get_value(const dp_grid* cg, double* host_V, int64_t count)
     return DP_OK;
 }
 
+int dp_set_value_f32(dp_grid* g, const float* host_V, int64_t count)
+{
+    if (!g || !host_V) return fail(DP_EINVAL, "NULL argument");
+    if (count != g->n_active) return fail(DP_EINVAL, "count %lld != stored nodes %lld", (long long)count, g->n_active);
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
+    int rc = ensure_staging(g);   // room for count doubles, so for count floats
+    if (rc) return rc;
+    float* staging = (float*)g->staging;
+    CK(cudaMemcpyAsync(staging, host_V, sizeof(float) * count, cudaMemcpyHostToDevice, g->st));
+    CK(launch_store_value(staging, g->V[g->cur], g->fp32, (int)count, g->g64, &g->ctl->nonfinite, g->st));
+    CK(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    if (g->h_ctl->nonfinite) return fail(DP_ENONFINITE, "V holds a non-finite value; the resident V is unchanged");
+    g->fp64_values = false;
+    return DP_OK;
+}
+
+int dp_get_value_f32(const dp_grid* cg, float* host_V, int64_t count)
+{
+    dp_grid* g = const_cast<dp_grid*>(cg);
+    if (!g || !host_V) return fail(DP_EINVAL, "NULL argument");
+    if (count != g->n_active) return fail(DP_EINVAL, "count %lld != stored nodes %lld", (long long)count, g->n_active);
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(DP_ECUDA, "cudaSetDevice failed");
+    if (g->fp32 && !g->fp64_values) {
+        // the stored values themselves
+        CK(cudaMemcpyAsync(host_V, g->V[g->cur], sizeof(float) * count, cudaMemcpyDeviceToHost, g->st));
+    } else {
+        int rc = ensure_staging(g);
+        if (rc) return rc;
+        const void* src = g->fp32 ? (const void*)g->V64[g->cur64] : (const void*)g->V[g->cur];
+        CK(launch_load_value(src, (float*)g->staging, 0, (int)count, g->st));   // FP64 rounded to FP32
+        CK(cudaMemcpyAsync(host_V, g->staging, sizeof(float) * count, cudaMemcpyDeviceToHost, g->st));
+    }
+    CK(cudaStreamSynchronize(g->st));
+    return DP_OK;
+}
+
 int dp_set_policy(dp_grid* g, const uint16_t* host_codes, int64_t count)
 {
     if (!g || !host_codes) return fail(DP_EINVAL, "NULL argument");

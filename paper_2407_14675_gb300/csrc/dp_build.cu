@@ -130,46 +130,69 @@ cudaError_t launch_lines(const int4* rows, unsigned* lines, int n0, int n1, int 
     return cudaGetLastError();
 }
 
-// Host values (FP64, compact order) into storage precision; target nodes 0.
-// A first pass flags non-finite input; the store pass then leaves V untouched.
-__global__ void check_finite_kernel(const double* src, int n, int* bad)
+// Host values (FP64 or FP32, compact order) into storage precision; target
+// nodes 0.  A first pass flags non-finite input; the store pass then leaves V
+// untouched.
+template <typename H>
+__global__ void check_finite_kernel(const H* src, int n, int* bad)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n && !isfinite(src[j])) atomicOr(bad, 1);
 }
 
-__global__ void store_value_kernel(const double* src, void* dst, int fp32, Geo<double> g, const int* bad)
+template <typename H>
+__global__ void store_value_kernel(const H* src, void* dst, int fp32, Geo<double> g, const int* bad)
 {
     if (*bad) return;
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= g.n_nodes) return;
     int i[4];
     decode_node(g, j, i);
-    double v = in_target(g, i) ? 0.0 : src[j];
-    if (fp32) ((float*)dst)[j] = (float)v;
-    else ((double*)dst)[j] = v;
+    const bool t = in_target(g, i);
+    if (fp32) ((float*)dst)[j] = t ? 0.0f : (float)src[j];
+    else ((double*)dst)[j] = t ? 0.0 : (double)src[j];
+}
+
+template <typename H>
+cudaError_t store_value(const H* src, void* dst, int fp32, int n, const Geo<double>& g, int* bad, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    check_finite_kernel<H><<<(n + 255) / 256, 256, 0, st>>>(src, n, bad);
+    store_value_kernel<H><<<(n + 255) / 256, 256, 0, st>>>(src, dst, fp32, g, bad);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_store_value(const double* src, void* dst, int fp32, int n, const Geo<double>& g, int* bad,
                                cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
-    check_finite_kernel<<<(n + 255) / 256, 256, 0, st>>>(src, n, bad);
-    store_value_kernel<<<(n + 255) / 256, 256, 0, st>>>(src, dst, fp32, g, bad);
-    return cudaGetLastError();
+    return store_value(src, dst, fp32, n, g, bad, st);
 }
 
-__global__ void load_value_kernel(const void* src, double* dst, int fp32, int n)
+cudaError_t launch_store_value(const float* src, void* dst, int fp32, int n, const Geo<double>& g, int* bad,
+                               cudaStream_t st)
+{
+    return store_value(src, dst, fp32, n, g, bad, st);
+}
+
+// Stored values (FP32 or FP64) into a staging buffer of type H.
+template <typename H>
+__global__ void load_value_kernel(const void* src, H* dst, int fp32, int n)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    dst[j] = fp32 ? (double)((const float*)src)[j] : ((const double*)src)[j];
+    dst[j] = fp32 ? (H)((const float*)src)[j] : (H)((const double*)src)[j];
 }
 
 cudaError_t launch_load_value(const void* src, double* dst, int fp32, int n, cudaStream_t st)
 {
-    load_value_kernel<<<(n + 255) / 256, 256, 0, st>>>(src, dst, fp32, n);
+    load_value_kernel<double><<<(n + 255) / 256, 256, 0, st>>>(src, dst, fp32, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_value(const void* src, float* dst, int fp32, int n, cudaStream_t st)
+{
+    load_value_kernel<float><<<(n + 255) / 256, 256, 0, st>>>(src, dst, fp32, n);
     return cudaGetLastError();
 }
 

@@ -118,7 +118,10 @@ cudaError_t launch_lines(const int4* rows, unsigned* lines, int n0, int n1, int 
                          cudaStream_t st);
 cudaError_t launch_store_value(const double* src, void* dst, int fp32, int n, const Geo<double>& g, int* bad,
                                cudaStream_t st);
+cudaError_t launch_store_value(const float* src, void* dst, int fp32, int n, const Geo<double>& g, int* bad,
+                               cudaStream_t st);
 cudaError_t launch_load_value(const void* src, double* dst, int fp32, int n, cudaStream_t st);
+cudaError_t launch_load_value(const void* src, float* dst, int fp32, int n, cudaStream_t st);
 cudaError_t launch_widen(const float* src, double* dst, int n, cudaStream_t st);
 cudaError_t launch_box_index(const Geo<double>& g, long long* out, cudaStream_t st);
 cudaError_t launch_prolong(const Geo<double>& gs, const void* Vs, int src_fp32, const uint16_t* Cs, int src_reduced,

@@ -190,6 +190,8 @@ def load(path: Optional[str] = None):
         "dp_get_active_index": [_P, _P, C.c_int64],
         "dp_set_value": [_P, _P, C.c_int64],
         "dp_get_value": [_P, _P, C.c_int64],
+        "dp_set_value_f32": [_P, _P, C.c_int64],
+        "dp_get_value_f32": [_P, _P, C.c_int64],
         "dp_set_policy": [_P, _P, C.c_int64],
         "dp_get_policy": [_P, _P, C.c_int64],
         "dp_bellman_sweep": [_P, C.c_int32, _dp],
@@ -257,6 +259,8 @@ def _host_ptr(a, dtype):
     # torch tensor on the host
     if getattr(a, "is_cuda", False):
         raise TypeError("host buffer expected")
+    if not a.is_contiguous() or a.element_size() != np.dtype(dtype).itemsize:
+        raise TypeError("expected a contiguous host tensor of %d-byte elements" % np.dtype(dtype).itemsize)
     return C.c_void_p(a.data_ptr())
 
 
@@ -320,6 +324,16 @@ def dp_set_value(grid: int, V) -> None:
 def dp_get_value(grid: int, count: int, out=None):
     out = np.empty(count, np.float64) if out is None else out
     _check(load().dp_get_value(grid, _host_ptr(out, np.float64), count))
+    return out
+
+
+def dp_set_value_f32(grid: int, V) -> None:
+    _check(load().dp_set_value_f32(grid, _host_ptr(V, np.float32), len(V)))
+
+
+def dp_get_value_f32(grid: int, count: int, out=None):
+    out = np.empty(count, np.float32) if out is None else out
+    _check(load().dp_get_value_f32(grid, _host_ptr(out, np.float32), count))
     return out
 
 

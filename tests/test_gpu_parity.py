@@ -122,6 +122,46 @@ def test_set_get_roundtrip_and_target_zero(dp):
     assert (back[~t] == V[~t]).all()
 
 
+@pytest.mark.parametrize("prec", [W.FP32, W.FP64], ids=["fp32", "fp64"])
+def test_fp32_value_transfers(dp, prec):
+    # dp_set_value_f32 / dp_get_value_f32: the stored FP32 values exactly on
+    # FP32 grids, widened / rounded on FP64 grids; targets forced to 0,
+    # non-finite input refused with the resident V unchanged
+    p = W.config2(n=21).replace(precision=prec)
+    with dp.Grid(p) as g:
+        idx = g.active_index()
+        o = oracle.Oracle(p)
+        t = o.target.astype(bool)[idx]
+        V = W.random_value(p, 2)[idx].astype(np.float32)
+        dp.dp_set_value_f32(g.h, V)
+        back64 = g.get_value()
+        back32 = dp.dp_get_value_f32(g.h, g.n)
+        assert (back64[t] == 0).all() and (back32[t] == 0).all()
+        assert np.array_equal(back64[~t], V[~t].astype(np.float64))
+        assert np.array_equal(back32[~t], V[~t])
+        # the FP64 call and the FP32 call agree on what the grid holds
+        g.set_value(W.random_value(p, 3)[idx])
+        assert np.array_equal(dp.dp_get_value_f32(g.h, g.n), g.get_value().astype(np.float32))
+        before = g.get_value()
+        bad = V.copy()
+        bad[len(bad) // 2] = np.nan
+        with pytest.raises(dp.DPError) as e:
+            dp.dp_set_value_f32(g.h, bad)
+        assert e.value.code == dp.DP_ENONFINITE
+        assert np.array_equal(g.get_value(), before)
+        with pytest.raises(TypeError):
+            dp.dp_set_value_f32(g.h, V.astype(np.float64))
+
+
+def test_fp32_value_transfer_after_the_fp64_phase(dp):
+    # after a polish the values are FP64: dp_get_value_f32 rounds them
+    p = W.config1(n=17)
+    with dp.Grid(p) as g:
+        g.policy_iterate(tol=1e-6, max_sweeps=400, n_eval=20, polish=1, switch_tol=100.0)
+        assert dp.dp_grid_get_info(g.h)["fp64_values"]
+        assert np.array_equal(dp.dp_get_value_f32(g.h, g.n), g.get_value().astype(np.float32))
+
+
 # -------------------------------------------------- closed-form dynamics --
 
 @pytest.mark.parametrize("precision", [W.FP64, W.FP32])
