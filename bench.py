@@ -871,7 +871,8 @@ def run_ours(args, world, rank, local):
                                                       cpu_info["seconds"])},
         "cpu_baseline_all_cores": None if par_rate is None else {
             "value": par_rate, "unit": UNIT, "cores": par_info["procs"], "kind": "oracle",
-            "sample": "one spawned oracle process per core (at most 8), each on its own 2,000-node sample of the "
+            "sample": "one spawned oracle process per core (at most one per 3 GB of free host memory), each on its "
+                      "own 2,000-node sample of the "
                       "band step mix, %.1f s" % par_info["seconds"]},
         "step_61x4": step_61x4,
         "time_to_tol": solve,
