@@ -59,13 +59,13 @@ constexpr int kTileM = 128, kTileN = 128, kKC = 256;
 // (one CTA per SM; small batches: every slice at once), 64 KB for 128-wide
 // slices (three CTAs per SM overlap one another's loads and epilogues).
 constexpr int gemm_smem(int kc) { return (kTileM + kTileN) * kc * 2; }
-// MN-major operands (kEpiAtomicMN) get 32 KB more: the MMAs of a 256-wide
+// MN-major operands (kEpiSplitMN) get 32 KB more: the MMAs of a 256-wide
 // slice then read inside the allocation for either assignment of its
 // descriptors' two byte offsets (2048 along K, 128 along MN), at most
 // 92,416 bytes past an operand's start.
 constexpr int kMNPad = 32768;
 template <int EPI, int KC>
-constexpr int gemm_smem_of() { return gemm_smem(KC) + (EPI == 3 ? kMNPad : 0); }
+constexpr int gemm_smem_of() { return gemm_smem(KC) + (EPI == 3 /* kEpiSplitMN */ ? kMNPad : 0); }
 constexpr int kWaitPolls = 1 << 22;
 constexpr float kInvSqrt2 = 0.70710678118654752f, kInvSqrt2Pi = 0.39894228040143268f;
 
@@ -88,7 +88,7 @@ __device__ __forceinline__ void load_row8(const bf16* p, float a[8])
     }
 }
 
-enum { kEpiFwd = 0, kEpiBwd = 1, kEpiAtomic = 2, kEpiAtomicMN = 3 };
+enum { kEpiFwd = 0, kEpiBwd = 1, kEpiAtomic = 2, kEpiSplitMN = 3 };
 
 // Four doubles by value (the network's input box corners).
 struct Box4 {
@@ -116,10 +116,12 @@ __device__ __forceinline__ void cp_async_wait_all()
 //   kEpiFwd:    z = acc + bias -> zout (optional, FP32), h = GELU(z) -> hout (bf16)
 //   kEpiBwd:    dz = acc * GELU'(zin) -> hout (bf16)
 //   kEpiAtomic: cacc += acc (FP32, split-K weight gradients)
-//   kEpiAtomicMN: the same with both operands MN-major: A[K range, 128
-//     blockIdx.x + i] and B[K range, 128 blockIdx.y + j] row-major with the
-//     tile's rows / columns contiguous (a weight gradient dz^T h straight
-//     from the activations, no transposed copies).  Core matrix (K block kb,
+//   kEpiSplitMN: both operands MN-major, A[K range, 128 blockIdx.x + i] and
+//     B[K range, 128 blockIdx.y + j] row-major with the tile's rows / columns
+//     contiguous (a weight gradient dz^T h straight from the activations, no
+//     transposed copies); the tile is stored, not added, at split blockIdx.z
+//     of cacc (256 x 256 floats per split), for a reduction in a fixed
+//     order.  Core matrix (K block kb,
 //     MN block mb) holds 8 K-rows of 8 contiguous MN elements at byte
 //     (kb * 16 + mb) * 128: 128 bytes to the next MN block, 2048 to the next
 //     K block.
@@ -144,7 +146,7 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
     const size_t row0 = (size_t)blockIdx.x * kTileM;
     const int n0 = blockIdx.y * kTileN;
     const int kbeg = blockIdx.z * k_per_cta;
-    constexpr bool kMN = EPI == kEpiAtomicMN;
+    constexpr bool kMN = EPI == kEpiSplitMN;
     constexpr unsigned idesc = umma_idesc_bf16(kTileM, kTileN) | (kMN ? (1u << 15) | (1u << 16) : 0u);
     constexpr int kGroups = KC / 8;                  // 16-byte groups per row of a slice
 
@@ -220,11 +222,18 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
             float v[16];
             tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + c0, v);
             const size_t off = r * kH + n0 + c0;     // 16 consecutive columns, 64-byte aligned
-            if (EPI == kEpiAtomic || EPI == kEpiAtomicMN) {
+            if (EPI == kEpiAtomic) {
                 // four 16-byte reductions (the row's 16 columns are 64-byte aligned)
 #pragma unroll
                 for (int q = 0; q < 16; q += 4)
                     atomicAdd(reinterpret_cast<float4*>(cacc + off + q), make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]));
+                continue;
+            }
+            if (EPI == kEpiSplitMN) {
+                float* dst = cacc + (size_t)blockIdx.z * kH * kH + off;
+#pragma unroll
+                for (int q = 0; q < 16; q += 4)
+                    *reinterpret_cast<float4*>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
                 continue;
             }
             float z[16];
@@ -498,20 +507,21 @@ __global__ void out_kernel(const bf16* __restrict__ h3, const float* __restrict_
 // The output layer of a training step with the first part of its backward
 // pass, one warp per sample (grid-stride over the samples): y = W4 h3 + b4,
 // the loss gradient dy = 2 (y - t) / (3 B), the loss sum, the output layer's
-// gradients dW4 += dy h3^T and db4 += dy (per-lane partial sums, reduced in
-// shared memory and added to G once per block), and
-// dz3 = (dy W4) * GELU'(z3) for the lane's 8 features.
+// gradients dW4 = dy h3^T and db4 = sum dy, and dz3 = (dy W4) * GELU'(z3) for
+// the lane's 8 features.  Each lane sums its samples in order, the block
+// sums its warps in order, and the block's sums (dW4, db4, loss: kOutPart
+// floats) go to part[blockIdx.x] for a reduction in a fixed order.
+constexpr int kOutPart = 3 * kH + 4;
 __global__ void __launch_bounds__(256) out_train_kernel(const bf16* __restrict__ h3, const float* __restrict__ P,
                                                         const float* __restrict__ t, const float* __restrict__ z3,
                                                         int count, float inv_n, bf16* __restrict__ dz3,
-                                                        float* __restrict__ G, float* __restrict__ loss)
+                                                        float* __restrict__ part)
 {
     __shared__ float sW[3 * kH + 3];
-    __shared__ float sdW[3 * kH + 4];   // dW4, db4, loss
+    __shared__ float sP[8][kOutPart];   // per warp: dW4, db4, loss
     for (int i = threadIdx.x; i < 3 * kH + 3; i += blockDim.x) sW[i] = P[kOffW4 + i];
-    for (int i = threadIdx.x; i < 3 * kH + 4; i += blockDim.x) sdW[i] = 0.0f;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int warps = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
     float w[3][8] = {}, b[3] = {}, l = 0.0f;
     for (int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); s < count; s += warps) {
@@ -549,52 +559,76 @@ __global__ void __launch_bounds__(256) out_train_kernel(const bf16* __restrict__
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) atomicAdd(&sdW[k * kH + lane * 8 + q], w[k][q]);
+        for (int q = 0; q < 8; ++q) sP[warp][k * kH + lane * 8 + q] = w[k][q];
     }
     if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) atomicAdd(&sdW[3 * kH + k], b[k]);
-        atomicAdd(&sdW[3 * kH + 3], l);
+        for (int k = 0; k < 3; ++k) sP[warp][3 * kH + k] = b[k];
+        sP[warp][3 * kH + 3] = l;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 3 * kH; i += blockDim.x) atomicAdd(&G[kOffW4 + i], sdW[i]);
-    if (threadIdx.x < 3) atomicAdd(&G[kOffB4 + threadIdx.x], sdW[3 * kH + threadIdx.x]);
-    if (threadIdx.x == 3 && loss) atomicAdd(loss, sdW[3 * kH + 3]);
+    for (int i = threadIdx.x; i < kOutPart; i += blockDim.x) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc += sP[k][i];
+        part[(size_t)blockIdx.x * kOutPart + i] = acc;
+    }
 }
 
-// Per-feature reductions over a chunk of samples (thread = feature):
-//   db[o] += sum_s dz[s][o];  with X = 4 also dW[o][d] += sum_s dz[s][o] x[s][d]
-// X (0 or 4) is a template argument so that the accumulators stay in
-// registers.
+// out[i] (+)= sum_k part[k * stride + i] for i < len, k in order: the
+// fixed-order reduction of per-block partial sums (accumulate: add to out
+// instead of storing).
+__global__ void sum_partials_kernel(const float* __restrict__ part, int n_part, int stride, int len,
+                                    float* __restrict__ out, int accumulate)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    float acc = 0.0f;
+    for (int k = 0; k < n_part; ++k) acc += part[(size_t)k * stride + i];
+    out[i] = accumulate ? out[i] + acc : acc;
+}
+
+// Per-feature reductions over a chunk of samples (thread = feature), in
+// sample order:  db[o] = sum_s dz[s][o];  with X = 4 also
+// dW[o][d] = sum_s dz[s][o] x[s][d].  Block b writes its sums to
+// part[b][0 .. 4 X + ... ): dW (256 X values, feature-major) then db (256),
+// for a reduction in a fixed order.  X (0 or 4) is a template argument so
+// that the accumulators stay in registers; the inputs x of each 256-sample
+// slice of the chunk are staged in shared memory.
 template <int X>
 __global__ void feat_reduce_kernel(const bf16* __restrict__ dz, const float* __restrict__ x, int rows, int chunk,
-                                   float* __restrict__ dW, float* __restrict__ db)
+                                   float* __restrict__ part)
 {
-    __shared__ float4 sx[X == 4 ? 256 : 1];   // the chunk's inputs (chunk <= 256)
+    __shared__ float4 sx[X == 4 ? 256 : 1];
     const int o = threadIdx.x;   // 256 threads
     const int s0 = blockIdx.x * chunk, s1 = min(rows, s0 + chunk);
-    if constexpr (X == 4) {
-        if (s0 + o < s1) sx[o] = reinterpret_cast<const float4*>(x)[s0 + o];
-        __syncthreads();
-    }
     float b = 0.0f, w[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 8
-    for (int s = s0; s < s1; ++s) {
-        const float g = __bfloat162float(dz[(size_t)s * kH + o]);
-        b += g;
+    for (int sb = s0; sb < s1; sb += 256) {
+        const int se = min(s1, sb + 256);
         if constexpr (X == 4) {
-            const float4 xs = sx[s - s0];
-            w[0] += g * xs.x;
-            w[1] += g * xs.y;
-            w[2] += g * xs.z;
-            w[3] += g * xs.w;
+            __syncthreads();
+            if (sb + o < se) sx[o] = reinterpret_cast<const float4*>(x)[sb + o];
+            __syncthreads();
+        }
+#pragma unroll 8
+        for (int s = sb; s < se; ++s) {
+            const float g = __bfloat162float(dz[(size_t)s * kH + o]);
+            b += g;
+            if constexpr (X == 4) {
+                const float4 xs = sx[s - sb];
+                w[0] += g * xs.x;
+                w[1] += g * xs.y;
+                w[2] += g * xs.z;
+                w[3] += g * xs.w;
+            }
         }
     }
-    atomicAdd(&db[o], b);
+    float* pb = part + (size_t)blockIdx.x * (kH * X + kH);
     if constexpr (X == 4) {
 #pragma unroll
-        for (int d = 0; d < 4; ++d) atomicAdd(&dW[o * 4 + d], w[d]);
+        for (int d = 0; d < 4; ++d) pb[o * 4 + d] = w[d];
     }
+    pb[kH * X + o] = b;
 }
 
 // Adam on the FP32 master parameters, then the BF16 copies of W2, W3 and
@@ -689,6 +723,7 @@ struct dp_mlp {
     bf16 *h1 = nullptr, *h2 = nullptr, *h3 = nullptr, *dz1 = nullptr, *dz2 = nullptr, *dz3 = nullptr;
     double* states = nullptr;
     float* loss = nullptr;
+    float* part = nullptr;             // partial sums of the backward pass (kPartFloats)
     int* err = nullptr;
     float* h_loss = nullptr;           // pinned
     int* h_err = nullptr;
@@ -707,7 +742,7 @@ void free_mlp(dp_mlp* m)
     cudaSetDevice(m->device);
     if (m->st) cudaStreamSynchronize(m->st);
     void* ps[] = {m->P, m->G, m->Am, m->Av, m->W2b, m->W3b, m->W2T, m->W3T, m->x, m->t, m->z1, m->z2, m->z3, m->y,
-                  m->h1, m->h2, m->h3, m->dz1, m->dz2, m->dz3, m->states, m->loss, m->err};
+                  m->h1, m->h2, m->h3, m->dz1, m->dz2, m->dz3, m->states, m->loss, m->part, m->err};
     for (void* p : ps)
         if (p) cudaFree(p);
     if (m->h_loss) cudaFreeHost(m->h_loss);
@@ -755,6 +790,14 @@ cudaError_t gemm_kc(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, i
 // slice at once; split-K weight gradients take one 256-wide slice per CTA.
 constexpr int kManyRows = 16384;
 
+// Partial sums of the backward pass (one buffer, reused by each reduction in
+// turn): split-K tiles of a weight gradient, the output layer's per-block
+// sums, the feature reductions' per-block sums.  Split-K 32: 246 us per
+// training step of 16,384 rows (64: 255, 16: 265, 8: 307; float atomics in
+// no fixed order: 217).
+constexpr int kSplitMax = 32, kOutBlocks = 1024, kRedBlocks = 256;
+constexpr size_t kPartFloats = (size_t)kSplitMax * kH * kH;   // >= kOutBlocks * kOutPart, kRedBlocks * 5 * kH
+
 template <int EPI>
 cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int rows, int k_total, int k_split,
                  const float* bias, float* zout, const float* zin, bf16* hout, float* cacc)
@@ -774,7 +817,7 @@ cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int 
                                                                                    zin, hout, m->err, m->wait_polls);
         return cudaGetLastError();
     }
-    if (EPI != kEpiAtomic && EPI != kEpiAtomicMN && rows >= kManyRows)
+    if (EPI != kEpiAtomic && EPI != kEpiSplitMN && rows >= kManyRows)
         return gemm_kc<EPI, kKC / 2>(m, A, lda, B, ldb, rows, k_total, k_split, bias, zout, zin, hout, cacc);
     return gemm_kc<EPI, kKC>(m, A, lda, B, ldb, rows, k_total, k_split, bias, zout, zin, hout, cacc);
 }
@@ -812,30 +855,43 @@ int forward(dp_mlp* m, int count)
 int forward_backward(dp_mlp* m, int count, float inv_n)
 {
     const int rows = count;
-    MCK(cudaMemsetAsync(m->G, 0, sizeof(float) * kParams, m->st));
     int rc;
     if ((rc = forward_hidden(m, count, true))) return rc;
-    const int ob = (int)std::min<long long>((count + 7) / 8, 2LL * m->sm_count);
-    out_train_kernel<<<ob, 256, 0, m->st>>>(m->h3, m->P, m->t, m->z3, count, inv_n, m->dz3, m->G, m->loss);
+    // every gradient sum goes through per-block partial sums and a reduction
+    // in a fixed order, so that a training run is reproducible bit for bit
+    auto reduce = [&](const float* part, int n_part, int stride, int len, float* out, int accumulate) {
+        sum_partials_kernel<<<(len + 255) / 256, 256, 0, m->st>>>(part, n_part, stride, len, out, accumulate);
+        return cudaGetLastError();
+    };
+    const int ob = (int)std::min<long long>(std::min<long long>((count + 7) / 8, 2LL * m->sm_count), kOutBlocks);
+    out_train_kernel<<<ob, 256, 0, m->st>>>(m->h3, m->P, m->t, m->z3, count, inv_n, m->dz3, m->part);
     MCK(cudaGetLastError());
-    const int chunk = 64;   // rows per block of the batch reductions (<= 256): 256 blocks at 16,384 rows
+    MCK(reduce(m->part, ob, kOutPart, 3 * kH + 3, m->G + kOffW4, 0));           // dW4, db4
+    MCK(reduce(m->part + 3 * kH + 3, ob, kOutPart, 1, m->loss, 1));             // the loss sum, accumulated
+    // rows per block of the feature reductions: at most kRedBlocks blocks
+    const int chunk = std::max(64, (rows + kRedBlocks - 1) / kRedBlocks);
+    const int nb = (rows + chunk - 1) / chunk;
+    // split-K of the weight-gradient GEMMs: a divisor of rows / 256, at most kSplitMax
+    int ks = std::min(rows / kKC, kSplitMax);
+    while ((rows / kKC) % ks) --ks;
     // layer 3: dz2 = (dz3 W3) * GELU'(z2); dW3 = dz3^T h2; db3 = sum dz3
     MCK(gemm<kEpiBwd>(m, m->dz3, kH, m->W3T, kH, rows, kH, 1, nullptr, nullptr, m->z2, m->dz2, nullptr));
-    MCK(gemm<kEpiAtomicMN>(m, m->dz3, kH, m->h2, kH, kH, rows, rows / kKC, nullptr, nullptr, nullptr, nullptr,
-                           m->G + kOffW3));
-    feat_reduce_kernel<0><<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz3, nullptr, rows, chunk, nullptr,
-                                                                          m->G + kOffB3);
+    MCK(gemm<kEpiSplitMN>(m, m->dz3, kH, m->h2, kH, kH, rows, ks, nullptr, nullptr, nullptr, nullptr, m->part));
+    MCK(reduce(m->part, ks, kH * kH, kH * kH, m->G + kOffW3, 0));
+    feat_reduce_kernel<0><<<nb, 256, 0, m->st>>>(m->dz3, nullptr, rows, chunk, m->part);
     MCK(cudaGetLastError());
+    MCK(reduce(m->part, nb, kH, kH, m->G + kOffB3, 0));
     // layer 2: dz1 = (dz2 W2) * GELU'(z1); dW2 = dz2^T h1; db2 = sum dz2
     MCK(gemm<kEpiBwd>(m, m->dz2, kH, m->W2T, kH, rows, kH, 1, nullptr, nullptr, m->z1, m->dz1, nullptr));
-    MCK(gemm<kEpiAtomicMN>(m, m->dz2, kH, m->h1, kH, kH, rows, rows / kKC, nullptr, nullptr, nullptr, nullptr,
-                           m->G + kOffW2));
-    feat_reduce_kernel<0><<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz2, nullptr, rows, chunk, nullptr,
-                                                                          m->G + kOffB2);
-    // layer 1: dW1 = dz1^T x, db1 = sum dz1
-    feat_reduce_kernel<4><<<(rows + chunk - 1) / chunk, 256, 0, m->st>>>(m->dz1, m->x, rows, chunk, m->G + kOffW1,
-                                                                          m->G + kOffB1);
+    MCK(gemm<kEpiSplitMN>(m, m->dz2, kH, m->h1, kH, kH, rows, ks, nullptr, nullptr, nullptr, nullptr, m->part));
+    MCK(reduce(m->part, ks, kH * kH, kH * kH, m->G + kOffW2, 0));
+    feat_reduce_kernel<0><<<nb, 256, 0, m->st>>>(m->dz2, nullptr, rows, chunk, m->part);
     MCK(cudaGetLastError());
+    MCK(reduce(m->part, nb, kH, kH, m->G + kOffB2, 0));
+    // layer 1: dW1 = dz1^T x, db1 = sum dz1 (contiguous in G)
+    feat_reduce_kernel<4><<<nb, 256, 0, m->st>>>(m->dz1, m->x, rows, chunk, m->part);
+    MCK(cudaGetLastError());
+    MCK(reduce(m->part, nb, kH * 4 + kH, kH * 4 + kH, m->G + kOffW1, 0));
     return DP_OK;
 }
 
@@ -1015,7 +1071,7 @@ int dp_mlp_create(const double* lo, const double* hi, int32_t batch_capacity, vo
     A(&m->x, C * 4); A(&m->t, C * 3); A(&m->y, C * 3);
     A(&m->z1, CH); A(&m->z2, CH); A(&m->z3, CH);
     A(&m->h1, CH); A(&m->h2, CH); A(&m->h3, CH); A(&m->dz1, CH); A(&m->dz2, CH); A(&m->dz3, CH);
-    A(&m->states, C * 4); A(&m->loss, 1); A(&m->err, 1);
+    A(&m->states, C * 4); A(&m->loss, 1); A(&m->err, 1); A(&m->part, kPartFloats);
     A(&m->ts, 1);
     if (e == cudaSuccess) e = cudaMallocHost(&m->h_loss, sizeof(float));
     if (e == cudaSuccess) e = cudaMallocHost(&m->h_err, sizeof(int));

@@ -260,3 +260,28 @@ def test_training_fits_a_solved_grid_and_warm_starts_policy_iteration(dp):
     print("fit %.3g, improvements cold %d warm %d, sweeps cold %d warm %d" % (
         fit, imp_cold, imp_warm, all_cold, all_warm))
     assert imp_warm < imp_cold and all_warm < all_cold
+
+
+def test_training_and_gradients_are_reproducible(dp):
+    # every gradient sum is reduced through per-block partial sums in a fixed
+    # order (no float atomics): the same gradients twice, and two trainings
+    # from the same parameters on the same grid end with bit-identical
+    # parameters and losses
+    p = W.config1(n=13)
+    X = _states(p, 16384, 8)
+    T = np.random.default_rng(9).uniform(-1, 1, size=(16384, 3))
+    with dp.Mlp(p.lo, p.hi, batch_capacity=16384) as net:
+        dp.dp_mlp_set_params(net.h, dp.flatten_params(W.mlp_init_params(seed=3)))
+        g1, l1 = dp.dp_mlp_gradients(net.h, X, T)
+        g2, l2 = dp.dp_mlp_gradients(net.h, X, T)
+    assert np.array_equal(g1, g2) and l1 == l2
+    with dp.Grid(p) as g:
+        g.policy_iterate(tol=1e-5, max_sweeps=2000, n_eval=20, polish=0)
+        outs = []
+        for _ in range(2):
+            with dp.Mlp(p.lo, p.hi, batch_capacity=16384) as net:
+                dp.dp_mlp_set_params(net.h, dp.flatten_params(W.mlp_init_params()))
+                st = dp.dp_mlp_train_grid(net.h, g.h, epochs=2, batch=4096, lr=1e-3)
+                outs.append((dp.dp_mlp_get_params(net.h), st.last_epoch_loss))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
