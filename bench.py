@@ -514,7 +514,7 @@ def warm_start_leg(args, dp, W, torch, g1, p1, g2):
         dp.dp_mlp_set_params(net.h, dp.flatten_params(W.mlp_init_params()))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st = dp.dp_mlp_train_grid(net.h, g1.h, epochs=args.mlp_epochs, batch=16384, lr=4e-3)
+        st = dp.dp_mlp_train_grid(net.h, g1.h, epochs=args.mlp_epochs, batch=16384, lr=4e-3, lr_final=1e-3)
         torch.cuda.synchronize()
         tr = st.asdict()
         tr["wall_s"] = time.perf_counter() - t0

@@ -361,6 +361,8 @@ typedef struct dp_mlp_train_opts {
     int32_t  batch;        /* samples per step, multiple of 512, <= capacity        */
     double   lr;           /* Adam step size                                        */
     uint64_t seed;         /* permutation seeds (0: 14675)                          */
+    double   lr_final;     /* > 0: step size of the last epoch, reached geometrically
+                              from lr epoch by epoch; 0: lr throughout           */
 } dp_mlp_train_opts;
 
 typedef struct dp_mlp_train_stats {

@@ -405,7 +405,7 @@ mlp_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restric
 struct TrainState {
     long long mult, offset, start;
     int t;
-    int pad;
+    float lr;        // > 0: the epoch's Adam step size (replaces the kernel argument)
 };
 
 template <typename S>
@@ -642,6 +642,7 @@ __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float tf = (float)ts->t;
+    if (ts->lr > 0.0f) lr = ts->lr;
     const float bc1 = 1.0f - powf(b1, tf), bc2 = 1.0f - powf(b2, tf);
     const float g = G[i];
     const float mi = b1 * m[i] + (1.0f - b1) * g;
@@ -663,6 +664,7 @@ __global__ void train_advance_kernel(TrainState* ts, int batch)
 __global__ void set_step_kernel(TrainState* ts, int t)
 {
     ts->t = t;
+    ts->lr = 0.0f;   // the step size of the call
 }
 
 __global__ void bf16_weights_kernel(const float* __restrict__ P, bf16* __restrict__ W2, bf16* __restrict__ W3,
@@ -998,7 +1000,10 @@ int train_grid_steps(dp_mlp* m, const GridView& gv, const dp_mlp_train_opts* o, 
         while (gcd(mult, (unsigned long long)n) != 1) mult = (mult + 2) % (unsigned long long)n;
         const unsigned long long off = next() % (unsigned long long)n;
         // the previous epoch's copy from h_ts has completed (check_err synchronised)
-        *m->h_ts = TrainState{(long long)mult, (long long)off, 0, (int)(m->step + 1), 0};
+        // the epoch's step size: geometric from lr to lr_final over the epochs
+        double lr_ep = o->lr;
+        if (o->lr_final > 0 && o->epochs > 1) lr_ep = o->lr * pow(o->lr_final / o->lr, (double)ep / (o->epochs - 1));
+        *m->h_ts = TrainState{(long long)mult, (long long)off, 0, (int)(m->step + 1), (float)lr_ep};
         if ((e = cudaMemcpyAsync(m->ts, m->h_ts, sizeof(TrainState), cudaMemcpyHostToDevice, m->st)) != cudaSuccess ||
             (e = cudaMemsetAsync(m->loss, 0, sizeof(float), m->st)) != cudaSuccess)
             return done(fail_cuda("training state", e));
@@ -1180,7 +1185,8 @@ int dp_mlp_set_wait_limit(dp_mlp* m, int32_t polls)
 int dp_mlp_train_grid(dp_mlp* m, dp_grid* grid, const dp_mlp_train_opts* o, dp_mlp_train_stats* stats)
 {
     if (!m || !grid || !o) return record_error(DP_EINVAL, "NULL argument");
-    if (o->batch < 512 || o->batch % 512 != 0 || o->batch > m->cap || o->epochs < 0 || !(o->lr > 0))
+    if (o->batch < 512 || o->batch % 512 != 0 || o->batch > m->cap || o->epochs < 0 || !(o->lr > 0) ||
+        !(o->lr_final >= 0))
         return record_error(DP_EINVAL, "bad training options");
     GridView gv;
     int rc = grid_view(grid, &gv);

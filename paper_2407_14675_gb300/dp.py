@@ -128,6 +128,7 @@ class dp_mlp_train_opts(C.Structure):
         ("batch", C.c_int32),
         ("lr", C.c_double),
         ("seed", C.c_uint64),
+        ("lr_final", C.c_double),
     ]
 
 
@@ -681,9 +682,9 @@ def dp_mlp_set_wait_limit(mlp: int, polls: int):
     _check(load().dp_mlp_set_wait_limit(mlp, polls))
 
 
-def dp_mlp_train_grid(mlp: int, grid: int, epochs=4, batch=4096, lr=1e-3, seed=14675):
+def dp_mlp_train_grid(mlp: int, grid: int, epochs=4, batch=4096, lr=1e-3, seed=14675, lr_final=0.0):
     o = dp_mlp_train_opts()
-    o.epochs, o.batch, o.lr, o.seed = epochs, batch, lr, seed
+    o.epochs, o.batch, o.lr, o.seed, o.lr_final = epochs, batch, lr, seed, lr_final
     s = dp_mlp_train_stats()
     _check(load().dp_mlp_train_grid(mlp, grid, C.byref(o), C.byref(s)))
     return s
