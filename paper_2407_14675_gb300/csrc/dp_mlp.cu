@@ -588,6 +588,21 @@ __global__ void sum_partials_kernel(const float* __restrict__ part, int n_part, 
     out[i] = accumulate ? out[i] + acc : acc;
 }
 
+// The same for short outputs with many partials, one warp per output: lane l
+// sums partials l, l + 32, ... in order, then a fixed shuffle tree combines
+// the lanes (deterministic as well).
+__global__ void sum_partials_warp_kernel(const float* __restrict__ part, int n_part, int stride, int len,
+                                         float* __restrict__ out, int accumulate)
+{
+    const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (i >= len) return;
+    float acc = 0.0f;
+    for (int k = lane; k < n_part; k += 32) acc += part[(size_t)k * stride + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[i] = accumulate ? out[i] + acc : acc;
+}
+
 // Per-feature reductions over a chunk of samples (thread = feature), in
 // sample order:  db[o] = sum_s dz[s][o];  with X = 4 also
 // dW[o][d] = sum_s dz[s][o] x[s][d].  Block b writes its sums to
@@ -794,9 +809,9 @@ constexpr int kManyRows = 16384;
 
 // Partial sums of the backward pass (one buffer, reused by each reduction in
 // turn): split-K tiles of a weight gradient, the output layer's per-block
-// sums, the feature reductions' per-block sums.  Split-K 32: 246 us per
-// training step of 16,384 rows (64: 255, 16: 265, 8: 307; float atomics in
-// no fixed order: 217).
+// sums, the feature reductions' per-block sums.  Split-K 32 for the weight
+// gradients (fewer splits serialise the K loop of each CTA, more write more
+// partial tiles).
 constexpr int kSplitMax = 32, kOutBlocks = 1024, kRedBlocks = 256;
 constexpr size_t kPartFloats = (size_t)kSplitMax * kH * kH;   // >= kOutBlocks * kOutPart, kRedBlocks * 5 * kH
 
@@ -862,7 +877,10 @@ int forward_backward(dp_mlp* m, int count, float inv_n)
     // every gradient sum goes through per-block partial sums and a reduction
     // in a fixed order, so that a training run is reproducible bit for bit
     auto reduce = [&](const float* part, int n_part, int stride, int len, float* out, int accumulate) {
-        sum_partials_kernel<<<(len + 255) / 256, 256, 0, m->st>>>(part, n_part, stride, len, out, accumulate);
+        if (len <= 8192)   // short outputs: a warp per output
+            sum_partials_warp_kernel<<<(len + 7) / 8, 256, 0, m->st>>>(part, n_part, stride, len, out, accumulate);
+        else
+            sum_partials_kernel<<<(len + 255) / 256, 256, 0, m->st>>>(part, n_part, stride, len, out, accumulate);
         return cudaGetLastError();
     };
     const int ob = (int)std::min<long long>(std::min<long long>((count + 7) / 8, 2LL * m->sm_count), kOutBlocks);
