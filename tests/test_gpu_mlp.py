@@ -285,3 +285,23 @@ def test_training_and_gradients_are_reproducible(dp):
                 outs.append((dp.dp_mlp_get_params(net.h), st.last_epoch_loss))
     assert np.array_equal(outs[0][0], outs[1][0])
     assert outs[0][1] == outs[1][1]
+
+
+def test_gradients_of_a_large_batch_are_the_mean_of_its_slices(dp):
+    # 131,072 rows: the feature reductions take 512 rows per block in
+    # 256-row slices and the weight gradients 32 splits of 4,096 rows; the
+    # gradient of the mean squared error is the mean of the eight 16,384-row
+    # slices' gradients up to FP32 rounding
+    p = W.config1()
+    n, k = 131072, 8
+    X = _states(p, n, 12)
+    T = np.random.default_rng(13).uniform(-1, 1, size=(n, 3))
+    with dp.Mlp(p.lo, p.hi, batch_capacity=n) as net:
+        dp.dp_mlp_set_params(net.h, dp.flatten_params(W.mlp_init_params(seed=4)))
+        g_all, l_all = dp.dp_mlp_gradients(net.h, X, T)
+        m = n // k
+        parts = [dp.dp_mlp_gradients(net.h, X[i * m:(i + 1) * m], T[i * m:(i + 1) * m]) for i in range(k)]
+    g_mean = np.mean([g for g, _ in parts], axis=0)
+    l_mean = np.mean([l for _, l in parts])
+    assert np.linalg.norm(g_all - g_mean) <= 1e-5 * np.linalg.norm(g_mean)
+    assert abs(l_all - l_mean) <= 1e-5 * l_mean
