@@ -294,14 +294,16 @@ mlp_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restric
     unsigned char* sA[2] = {smem + kTileN * kKC * 2, smem + (kTileN + kTileM) * kKC * 2};
     __shared__ unsigned tmem_slot;
     __shared__ __align__(8) unsigned long long mbar;
+    __shared__ float sBias[kTileN];                              // this CTA's 128 biases
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n0 = blockIdx.y * kTileN;
+    if (EPI == kEpiFwd && tid < kTileN) sBias[tid] = bias[n0 + tid];
     if (warp == 0) tmem_alloc(&tmem_slot, kTileN);
     if (tid == 0) mbar_init(&mbar);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const unsigned tmem = tmem_slot;
-    const int n0 = blockIdx.y * kTileN;
     constexpr unsigned idesc = umma_idesc_bf16(kTileM, kTileN);
     constexpr int kGroups = kKC / 8;
 
@@ -352,36 +354,43 @@ mlp_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restric
         }
         const int quarter = warp & 3, part = warp >> 2;
         const size_t r = (size_t)t * kTileM + quarter * 32 + lane;   // TMEM lane = tile row
-        constexpr int kCols = kTileN / kPersistParts;
-        for (int c0 = part * kCols; c0 < (part + 1) * kCols; c0 += 16) {
-            float v[16], z[16];
-            tmem_ld16(tmem + ((unsigned)(quarter * 32) << 16) + c0, v);
-            const size_t off = r * kH + n0 + c0;
-            if (EPI == kEpiFwd) {
+        constexpr int kCols = kTileN / kPersistParts;                // 32: one TMEM load, one wait
+        static_assert(kCols == 32, "one 32-column TMEM load per thread");
+        const int c0 = part * kCols;
+        const size_t off = r * kH + n0 + c0;
+        float v[32], z[32];
+        if (EPI == kEpiFwd) {
+            tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + c0, v);
 #pragma unroll
-                for (int q = 0; q < 16; q += 4) {
-                    const float4 b = *(const float4*)(bias + n0 + c0 + q);
-                    z[q] = v[q] + b.x; z[q + 1] = v[q + 1] + b.y; z[q + 2] = v[q + 2] + b.z; z[q + 3] = v[q + 3] + b.w;
-                    if (zout) *(float4*)(zout + off + q) = make_float4(z[q], z[q + 1], z[q + 2], z[q + 3]);
-                }
-#pragma unroll
-                for (int q = 0; q < 16; ++q) z[q] = gelu(z[q]);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 16; q += 4) {
-                    const float4 zi = *(const float4*)(zin + off + q);
-                    z[q] = v[q] * gelu_grad(zi.x); z[q + 1] = v[q + 1] * gelu_grad(zi.y);
-                    z[q + 2] = v[q + 2] * gelu_grad(zi.z); z[q + 3] = v[q + 3] * gelu_grad(zi.w);
-                }
+            for (int q = 0; q < 32; q += 4) {
+                z[q] = v[q] + sBias[c0 + q]; z[q + 1] = v[q + 1] + sBias[c0 + q + 1];
+                z[q + 2] = v[q + 2] + sBias[c0 + q + 2]; z[q + 3] = v[q + 3] + sBias[c0 + q + 3];
+                if (zout) *(float4*)(zout + off + q) = make_float4(z[q], z[q + 1], z[q + 2], z[q + 3]);
             }
+#pragma unroll
+            for (int q = 0; q < 32; ++q) z[q] = gelu(z[q]);
+        } else {
+            // the pre-activations are loaded before the accumulator's wait
+            float4 zi[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) zi[q] = *(const float4*)(zin + off + 4 * q);
+            tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + c0, v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                z[4 * q] = v[4 * q] * gelu_grad(zi[q].x); z[4 * q + 1] = v[4 * q + 1] * gelu_grad(zi[q].y);
+                z[4 * q + 2] = v[4 * q + 2] * gelu_grad(zi[q].z); z[4 * q + 3] = v[4 * q + 3] * gelu_grad(zi[q].w);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 32; h += 16) {
             unsigned pk[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const __nv_bfloat162 h2 = __floats2bfloat162_rn(z[2 * q], z[2 * q + 1]);
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(z[h + 2 * q], z[h + 2 * q + 1]);
                 pk[q] = *(const unsigned*)&h2;
             }
-            *(uint4*)(hout + off) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            *(uint4*)(hout + off + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            *(uint4*)(hout + off + h) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *(uint4*)(hout + off + h + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
         }
         // the epilogue's TMEM reads finish before the next tile's MMAs
         // overwrite the accumulator; the next activations must have landed
