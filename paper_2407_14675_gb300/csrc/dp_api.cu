@@ -1421,7 +1421,10 @@ int dp_policy_iterate(dp_grid* g, const dp_solve_opts* o, dp_solve_stats* stats)
             CK(T.end());
             // the evaluation sweeps, `levels` per launch where the frozen feet
             // are stored (mix: the improvement stores them too)
-            const int levels = (mix || g->feet_valid) && g->fp32 ? wave_levels(g, o) : 1;
+            // (the multi-level diagonal-solved evaluation reads word pairs:
+            // 8-byte feet are evaluated one sweep per launch, recomputed)
+            const int levels =
+                (mix || g->feet_valid) && g->fp32 && !(g->feet8 && diag && !mix) ? wave_levels(g, o) : 1;
             for (int e = 0; e < ne;) {
                 const int k = std::min(levels, ne - e);
                 CK(T.begin(mix ? kTEval64 : kTEval));

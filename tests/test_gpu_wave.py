@@ -96,3 +96,21 @@ def test_multi_level_wait_limit_gives_up_cleanly(dp):
         dp.dp_set_wave_wait_limit(-1)
     ref = _solve(dp, p, 1, max_sweeps=3, n_eval=20, polish=0)
     _same(ref, _solve(dp, p, 20, max_sweeps=3, n_eval=20, polish=0), "after a timeout")
+
+
+def test_multi_level_with_each_foot_format(dp):
+    """dp_set_foot_format: with 8-byte feet forced, the diagonal-solved
+    evaluation recomputes the feet one sweep per launch (whatever
+    eval_levels asks), with word pairs forced the plain evaluation's levels
+    read the pairs; each equals the same solve one sweep per launch."""
+    p = W.config2(n=41)
+    for fmt, solver in ((dp.DP_FOOT_WORD8, dp.DP_EVAL_DIAG), (dp.DP_FOOT_PAIR, dp.DP_EVAL_JACOBI)):
+        out = []
+        for levels in (1, 6):
+            hist = np.zeros(64)
+            with dp.Grid(p) as g:
+                g.set_foot_format(fmt)
+                rc, st = g.policy_iterate(tol=0.0, max_sweeps=3, n_eval=12, polish=0, warm=0, eval_levels=levels,
+                                          eval_solver=solver, history=hist)
+                out.append((g.get_value(), g.get_policy(), hist[:st.history_count].copy(), st))
+        _same(out[0], out[1], (fmt, solver))
