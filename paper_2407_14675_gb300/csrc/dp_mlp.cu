@@ -277,10 +277,12 @@ mlp_gemm_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
 // 64 KB buffers while the MMAs and the epilogue of the current tile run.
 // Same staging layout, MMAs and epilogue arithmetic as mlp_gemm_kernel<EPI>
 // (kEpiFwd with optional zout, or kEpiBwd).
-// Sixteen warps: four per quarter of the TMEM lanes, each taking a quarter
-// of the columns in the epilogue.
+// Thirty-two warps: eight per quarter of the TMEM lanes, each taking 16 of
+// the tile's 128 columns in the epilogue (with 16 warps of 32 columns each,
+// fewer warps hide the activation's latency: about 1 % slower training and 2 %
+// slower inference).
 constexpr int kPersistSmem = (kTileN + 2 * kTileM) * kKC * 2;   // 192 KB
-constexpr int kPersistThreads = 512;
+constexpr int kPersistThreads = 1024;
 constexpr int kPersistParts = kPersistThreads / 128;            // column parts per TMEM lane quarter
 
 template <int EPI>
@@ -352,45 +354,57 @@ mlp_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restric
             cp_async_wait_all();   // no copy may outlive the CTA
             break;
         }
+        // Each warp takes a 32-row x kCols-column block of the accumulator
+        // (TMEM lane = tile row, so the load gives lane l row l).  The block
+        // passes through shared memory -- the current tile's activation
+        // buffer, whose last reader, the MMAs, has completed -- so that in
+        // step k lane l holds row kRps k + l / kLpr and the four columns from
+        // 4 (l % kLpr): the global loads and stores then cover whole row
+        // segments instead of one 16-byte piece of 32 rows.  The 16-byte
+        // chunks of a row are XOR-swizzled so that both passes are free of
+        // bank conflicts.
         const int quarter = warp & 3, part = warp >> 2;
-        const size_t r = (size_t)t * kTileM + quarter * 32 + lane;   // TMEM lane = tile row
-        constexpr int kCols = kTileN / kPersistParts;                // 32: one TMEM load, one wait
-        static_assert(kCols == 32, "one 32-column TMEM load per thread");
-        const int c0 = part * kCols;
-        const size_t off = r * kH + n0 + c0;
-        float v[32], z[32];
-        if (EPI == kEpiFwd) {
-            tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + c0, v);
-#pragma unroll
-            for (int q = 0; q < 32; q += 4) {
-                z[q] = v[q] + sBias[c0 + q]; z[q + 1] = v[q + 1] + sBias[c0 + q + 1];
-                z[q + 2] = v[q + 2] + sBias[c0 + q + 2]; z[q + 3] = v[q + 3] + sBias[c0 + q + 3];
-                if (zout) *(float4*)(zout + off + q) = make_float4(z[q], z[q + 1], z[q + 2], z[q + 3]);
-            }
-#pragma unroll
-            for (int q = 0; q < 32; ++q) z[q] = gelu(z[q]);
-        } else {
+        constexpr int kCols = kTileN / kPersistParts;   // columns per warp: one TMEM load, one wait
+        constexpr int kLpr = kCols / 4;                 // lanes per row (16-byte chunks of a row)
+        constexpr int kRps = 32 / kLpr;                 // rows per step
+        static_assert(kCols == 16 || kCols == 32, "one 16- or 32-column TMEM load per thread");
+        static_assert(kPersistThreads / 32 * 32 * kCols * 4 <= kTileM * kKC * 2, "scratch fits the A buffer");
+        const int c0 = part * kCols, rr = lane / kLpr, cc = lane % kLpr;
+        float* S = (float*)sA[buf] + warp * 32 * kCols;
+        const size_t g0 = ((size_t)t * kTileM + quarter * 32 + rr) * kH + n0 + c0 + 4 * cc;
+        auto goff = [&](int k) { return g0 + (size_t)(kRps * k) * kH; };
+        auto sw = [](int row, int c) { return row * kCols + ((c ^ ((row / (8 / kLpr)) % kLpr)) << 2); };
+        float4 zi[kLpr];
+        if (EPI == kEpiBwd) {
             // the pre-activations are loaded before the accumulator's wait
-            float4 zi[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) zi[q] = *(const float4*)(zin + off + 4 * q);
-            tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + c0, v);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                z[4 * q] = v[4 * q] * gelu_grad(zi[q].x); z[4 * q + 1] = v[4 * q + 1] * gelu_grad(zi[q].y);
-                z[4 * q + 2] = v[4 * q + 2] * gelu_grad(zi[q].z); z[4 * q + 3] = v[4 * q + 3] * gelu_grad(zi[q].w);
-            }
+            for (int k = 0; k < kLpr; ++k) zi[k] = *(const float4*)(zin + goff(k));
         }
+        {
+            float v[kCols];
+            const unsigned ta = tmem + ((unsigned)(quarter * 32) << 16) + c0;
+            if constexpr (kCols == 32) tmem_ld32(ta, v);
+            else tmem_ld16(ta, v);
 #pragma unroll
-        for (int h = 0; h < 32; h += 16) {
-            unsigned pk[8];
+            for (int c = 0; c < kLpr; ++c)
+                *(float4*)(S + sw(lane, c)) = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+        }
+        __syncwarp();
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const __nv_bfloat162 h2 = __floats2bfloat162_rn(z[h + 2 * q], z[h + 2 * q + 1]);
-                pk[q] = *(const unsigned*)&h2;
+        for (int k = 0; k < kLpr; ++k) {
+            const float4 a = *(const float4*)(S + sw(kRps * k + rr, cc));
+            float y[4];
+            if (EPI == kEpiFwd) {
+                const float4 z = make_float4(a.x + sBias[c0 + 4 * cc], a.y + sBias[c0 + 4 * cc + 1],
+                                             a.z + sBias[c0 + 4 * cc + 2], a.w + sBias[c0 + 4 * cc + 3]);
+                if (zout) *(float4*)(zout + goff(k)) = z;
+                y[0] = gelu(z.x); y[1] = gelu(z.y); y[2] = gelu(z.z); y[3] = gelu(z.w);
+            } else {
+                y[0] = a.x * gelu_grad(zi[k].x); y[1] = a.y * gelu_grad(zi[k].y);
+                y[2] = a.z * gelu_grad(zi[k].z); y[3] = a.w * gelu_grad(zi[k].w);
             }
-            *(uint4*)(hout + off + h) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            *(uint4*)(hout + off + h + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            const __nv_bfloat162 p0 = __floats2bfloat162_rn(y[0], y[1]), p1 = __floats2bfloat162_rn(y[2], y[3]);
+            *(uint2*)(hout + goff(k)) = make_uint2(*(const unsigned*)&p0, *(const unsigned*)&p1);
         }
         // the epilogue's TMEM reads finish before the next tile's MMAs
         // overwrite the accumulator; the next activations must have landed
