@@ -285,18 +285,31 @@ constexpr int kPersistSmem = (kTileN + 2 * kTileM) * kKC * 2;   // 192 KB
 constexpr int kPersistThreads = 1024;
 constexpr int kPersistParts = kPersistThreads / 128;            // column parts per TMEM lane quarter
 
-template <int EPI>
+//
+// RED (backward only) adds the sums over each row tile that the next
+// gradients need, so that no separate pass re-reads dz: RED = 1 the column
+// sums of dz (a bias gradient), RED = 5 also the sums of dz times each of the
+// four inputs xin (rows x 4, the first layer's weight gradient).  Tile t's
+// sums go to red[t * RED * 256 ..]: for RED = 5 the 4 x 256 weight-gradient
+// entries (feature-major) then the 256 bias-gradient entries, the layout of
+// W1, b1 in the parameter vector.  A warp sums its 32 rows in order (its
+// lanes' rows, then a fixed shuffle tree), the CTA its four row quarters in
+// order; the tiles are summed afterwards in a fixed order.
+template <int EPI, int RED = 0>
 __global__ void __launch_bounds__(kPersistThreads)
 mlp_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb, int tiles,
                       const float* __restrict__ bias, float* __restrict__ zout, const float* __restrict__ zin,
-                      bf16* __restrict__ hout, int* __restrict__ err, int polls)
+                      bf16* __restrict__ hout, const float* __restrict__ xin, float* __restrict__ red,
+                      int* __restrict__ err, int polls)
 {
+    static_assert(RED == 0 || (EPI == kEpiBwd && (RED == 1 || RED == 5)), "tile sums of the backward pass");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sB = smem;                                  // 128 x 256
     unsigned char* sA[2] = {smem + kTileN * kKC * 2, smem + (kTileN + kTileM) * kKC * 2};
     __shared__ unsigned tmem_slot;
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ float sBias[kTileN];                              // this CTA's 128 biases
+    __shared__ float sRed[4][RED > 0 ? RED * kTileN : 1];        // per row quarter: the tile sums
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n0 = blockIdx.y * kTileN;
     if (EPI == kEpiFwd && tid < kTileN) sBias[tid] = bias[n0 + tid];
@@ -374,6 +387,7 @@ mlp_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restric
         const size_t g0 = ((size_t)t * kTileM + quarter * 32 + rr) * kH + n0 + c0 + 4 * cc;
         auto goff = [&](int k) { return g0 + (size_t)(kRps * k) * kH; };
         auto sw = [](int row, int c) { return row * kCols + ((c ^ ((row / (8 / kLpr)) % kLpr)) << 2); };
+        float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f}, cw[4][4] = {};   // RED: column sums, times x
         float4 zi[kLpr];
         if (EPI == kEpiBwd) {
             // the pre-activations are loaded before the accumulator's wait
@@ -402,9 +416,50 @@ mlp_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restric
             } else {
                 y[0] = a.x * gelu_grad(zi[k].x); y[1] = a.y * gelu_grad(zi[k].y);
                 y[2] = a.z * gelu_grad(zi[k].z); y[3] = a.w * gelu_grad(zi[k].w);
+                if (RED > 0) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) cs[i] += y[i];
+                }
+                if (RED == 5) {
+                    const float4 xk = *(const float4*)(xin + 4 * ((size_t)t * kTileM + quarter * 32 + kRps * k + rr));
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        cw[i][0] += y[i] * xk.x; cw[i][1] += y[i] * xk.y;
+                        cw[i][2] += y[i] * xk.z; cw[i][3] += y[i] * xk.w;
+                    }
+                }
             }
-            const __nv_bfloat162 p0 = __floats2bfloat162_rn(y[0], y[1]), p1 = __floats2bfloat162_rn(y[2], y[3]);
-            *(uint2*)(hout + goff(k)) = make_uint2(*(const unsigned*)&p0, *(const unsigned*)&p1);
+            if (RED != 5) {
+                const __nv_bfloat162 p0 = __floats2bfloat162_rn(y[0], y[1]), p1 = __floats2bfloat162_rn(y[2], y[3]);
+                *(uint2*)(hout + goff(k)) = make_uint2(*(const unsigned*)&p0, *(const unsigned*)&p1);
+            }
+        }
+        if (RED > 0) {
+            // lanes with the same columns (equal lane % kLpr) hold the other rows
+#pragma unroll
+            for (int o = kLpr; o < 32; o <<= 1) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    cs[i] += __shfl_xor_sync(0xffffffffu, cs[i], o);
+                    if (RED == 5) {
+#pragma unroll
+                        for (int d = 0; d < 4; ++d) cw[i][d] += __shfl_xor_sync(0xffffffffu, cw[i][d], o);
+                    }
+                }
+            }
+            if (rr == 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int col = c0 + 4 * cc + i;
+                    if (RED == 5) {
+#pragma unroll
+                        for (int d = 0; d < 4; ++d) sRed[quarter][col * 4 + d] = cw[i][d];
+                        sRed[quarter][4 * kTileN + col] = cs[i];
+                    } else {
+                        sRed[quarter][col] = cs[i];
+                    }
+                }
+            }
         }
         // the epilogue's TMEM reads finish before the next tile's MMAs
         // overwrite the accumulator; the next activations must have landed
@@ -412,6 +467,17 @@ mlp_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restric
         fence_async_smem();
         fence_before_sync();
         __syncthreads();
+        if (RED > 0) {
+            // the four row quarters in order (read before the next tile's
+            // epilogue, which follows the next block-wide barrier, writes sRed)
+            float* rt = red + (size_t)t * (RED * kH);
+            for (int i = tid; i < RED * kTileN; i += kPersistThreads) {
+                const float v = ((sRed[0][i] + sRed[1][i]) + sRed[2][i]) + sRed[3][i];
+                const size_t gi = RED == 5 ? (i < 4 * kTileN ? (size_t)n0 * 4 + i : (size_t)4 * kH + n0 + (i - 4 * kTileN))
+                                           : (size_t)n0 + i;
+                rt[gi] = v;
+            }
+        }
     }
     fence_before_sync();
     __syncthreads();
@@ -531,22 +597,24 @@ __global__ void out_kernel(const bf16* __restrict__ h3, const float* __restrict_
 // pass, one warp per sample (grid-stride over the samples): y = W4 h3 + b4,
 // the loss gradient dy = 2 (y - t) / (3 B), the loss sum, the output layer's
 // gradients dW4 = dy h3^T and db4 = sum dy, and dz3 = (dy W4) * GELU'(z3) for
-// the lane's 8 features.  Each lane sums its samples in order, the block
-// sums its warps in order, and the block's sums (dW4, db4, loss: kOutPart
-// floats) go to part[blockIdx.x] for a reduction in a fixed order.
-constexpr int kOutPart = 3 * kH + 4;
+// the lane's 8 features with its sum db3 (FP32, before the BF16 rounding of
+// dz3).  Each lane sums its samples in order, the block sums its warps in
+// order, and the block's sums go to part[blockIdx.x] for a reduction in a
+// fixed order: db3, dW4, db4 (laid out as b3, W4, b4 are in the parameter
+// vector), then the loss.
+constexpr int kOutPart = 4 * kH + 4;
 __global__ void __launch_bounds__(256) out_train_kernel(const bf16* __restrict__ h3, const float* __restrict__ P,
                                                         const float* __restrict__ t, const float* __restrict__ z3,
                                                         int count, float inv_n, bf16* __restrict__ dz3,
                                                         float* __restrict__ part)
 {
     __shared__ float sW[3 * kH + 3];
-    __shared__ float sP[8][kOutPart];   // per warp: dW4, db4, loss
+    __shared__ float sP[8][kOutPart];   // per warp: db3, dW4, db4, loss
     for (int i = threadIdx.x; i < 3 * kH + 3; i += blockDim.x) sW[i] = P[kOffW4 + i];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int warps = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
-    float w[3][8] = {}, b[3] = {}, l = 0.0f;
+    float w[3][8] = {}, b[3] = {}, d3[8] = {}, l = 0.0f;
     for (int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); s < count; s += warps) {
         float a[8];
         load_row8(h3 + (size_t)s * kH + lane * 8, a);
@@ -574,20 +642,25 @@ __global__ void __launch_bounds__(256) out_train_kernel(const bf16* __restrict__
             const int i = lane * 8 + q;
             const float g0 = dy[0] * sW[i] + dy[1] * sW[kH + i] + dy[2] * sW[2 * kH + i];
             const float g1 = dy[0] * sW[i + 1] + dy[1] * sW[kH + i + 1] + dy[2] * sW[2 * kH + i + 1];
-            const __nv_bfloat162 h2 = __floats2bfloat162_rn(g0 * gelu_grad(z[q]), g1 * gelu_grad(z[q + 1]));
+            const float e0 = g0 * gelu_grad(z[q]), e1 = g1 * gelu_grad(z[q + 1]);
+            d3[q] += e0;
+            d3[q + 1] += e1;
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(e0, e1);
             u[q / 2] = *reinterpret_cast<const unsigned*>(&h2);
         }
         *reinterpret_cast<uint4*>(dz3 + (size_t)s * kH + lane * 8) = make_uint4(u[0], u[1], u[2], u[3]);
     }
 #pragma unroll
+    for (int q = 0; q < 8; ++q) sP[warp][lane * 8 + q] = d3[q];
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) sP[warp][k * kH + lane * 8 + q] = w[k][q];
+        for (int q = 0; q < 8; ++q) sP[warp][kH + k * kH + lane * 8 + q] = w[k][q];
     }
     if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) sP[warp][3 * kH + k] = b[k];
-        sP[warp][3 * kH + 3] = l;
+        for (int k = 0; k < 3; ++k) sP[warp][4 * kH + k] = b[k];
+        sP[warp][4 * kH + 3] = l;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kOutPart; i += blockDim.x) {
@@ -669,13 +742,14 @@ __global__ void feat_reduce_kernel(const bf16* __restrict__ dz, const float* __r
     pb[kH * X + o] = b;
 }
 
-// Adam on the FP32 master parameters, then the BF16 copies of W2, W3 and
-// their transposes used by the tensor-core GEMMs.
+// Adam on the FP32 master parameters, writing the BF16 copies of W2, W3 and
+// their transposes used by the tensor-core GEMMs as it goes.
 // The step count t (1 for the first step) comes from device memory; the
 // bias corrections are 1 - beta^t.
 __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
                             float* __restrict__ v, int n, float lr, float b1, float b2, float eps,
-                            const TrainState* __restrict__ ts)
+                            const TrainState* __restrict__ ts, bf16* __restrict__ W2, bf16* __restrict__ W3,
+                            bf16* __restrict__ W2T, bf16* __restrict__ W3T)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -687,7 +761,14 @@ __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, 
     const float vi = b2 * v[i] + (1.0f - b2) * g * g;
     m[i] = mi;
     v[i] = vi;
-    P[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    const float p = P[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    P[i] = p;
+    const bool w2 = i >= kOffW2 && i < kOffW2 + kH * kH, w3 = i >= kOffW3 && i < kOffW3 + kH * kH;
+    if (w2 || w3) {
+        const int e = i - (w2 ? kOffW2 : kOffW3), o = e / kH, c = e % kH;
+        (w2 ? W2 : W3)[e] = __float2bfloat16(p);
+        (w2 ? W2T : W3T)[c * kH + o] = __float2bfloat16(p);
+    }
 }
 
 // End of a replayed training step: the next step's first sample and the
@@ -764,6 +845,7 @@ struct dp_mlp {
     double* states = nullptr;
     float* loss = nullptr;
     float* part = nullptr;             // partial sums of the backward pass (kPartFloats)
+    float* red = nullptr;              // per-row-tile sums of the fused backward GEMMs (cap / 128 x 5 x 256)
     int* err = nullptr;
     float* h_loss = nullptr;           // pinned
     int* h_err = nullptr;
@@ -782,7 +864,7 @@ void free_mlp(dp_mlp* m)
     cudaSetDevice(m->device);
     if (m->st) cudaStreamSynchronize(m->st);
     void* ps[] = {m->P, m->G, m->Am, m->Av, m->W2b, m->W3b, m->W2T, m->W3T, m->x, m->t, m->z1, m->z2, m->z3, m->y,
-                  m->h1, m->h2, m->h3, m->dz1, m->dz2, m->dz3, m->states, m->loss, m->part, m->err};
+                  m->h1, m->h2, m->h3, m->dz1, m->dz2, m->dz3, m->states, m->loss, m->part, m->red, m->err};
     for (void* p : ps)
         if (p) cudaFree(p);
     if (m->h_loss) cudaFreeHost(m->h_loss);
@@ -838,25 +920,33 @@ constexpr int kManyRows = 16384;
 constexpr int kSplitMax = 32, kOutBlocks = 1024, kRedBlocks = 256;
 constexpr size_t kPartFloats = (size_t)kSplitMax * kH * kH;   // >= kOutBlocks * kOutPart, kRedBlocks * 5 * kH
 
+// The persistent kernel over rows (a multiple of 128, at least kManyRows) with
+// K = 256; RED > 0 (backward): the per-tile sums into red.
+template <int EPI, int RED = 0>
+cudaError_t persistent(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int rows, const float* bias,
+                       float* zout, const float* zin, bf16* hout, const float* xin = nullptr, float* red = nullptr)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(mlp_persistent_kernel<EPI, RED>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int tiles = rows / kTileM;
+    const int per_half = std::max(1, std::min(tiles, m->sm_count / 2));
+    dim3 grid(per_half, kH / kTileN);
+    mlp_persistent_kernel<EPI, RED><<<grid, kPersistThreads, kPersistSmem, m->st>>>(
+        A, lda, B, ldb, tiles, bias, zout, zin, hout, xin, red, m->err, m->wait_polls);
+    return cudaGetLastError();
+}
+
 template <int EPI>
 cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int rows, int k_total, int k_split,
                  const float* bias, float* zout, const float* zin, bf16* hout, float* cacc)
 {
-    if ((EPI == kEpiFwd || EPI == kEpiBwd) && rows >= kManyRows && k_total == kKC && k_split == 1) {
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(mlp_persistent_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 kPersistSmem);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        const int tiles = rows / kTileM;
-        const int per_half = std::max(1, std::min(tiles, m->sm_count / 2));
-        dim3 grid(per_half, kH / kTileN);
-        mlp_persistent_kernel<EPI><<<grid, kPersistThreads, kPersistSmem, m->st>>>(A, lda, B, ldb, tiles, bias, zout,
-                                                                                   zin, hout, m->err, m->wait_polls);
-        return cudaGetLastError();
-    }
+    if ((EPI == kEpiFwd || EPI == kEpiBwd) && rows >= kManyRows && k_total == kKC && k_split == 1)
+        return persistent<EPI>(m, A, lda, B, ldb, rows, bias, zout, zin, hout);
     if (EPI != kEpiAtomic && EPI != kEpiSplitMN && rows >= kManyRows)
         return gemm_kc<EPI, kKC / 2>(m, A, lda, B, ldb, rows, k_total, k_split, bias, zout, zin, hout, cacc);
     return gemm_kc<EPI, kKC>(m, A, lda, B, ldb, rows, k_total, k_split, bias, zout, zin, hout, cacc);
@@ -909,21 +999,37 @@ int forward_backward(dp_mlp* m, int count, float inv_n)
     const int ob = (int)std::min<long long>(std::min<long long>((count + 7) / 8, 2LL * m->sm_count), kOutBlocks);
     out_train_kernel<<<ob, 256, 0, m->st>>>(m->h3, m->P, m->t, m->z3, count, inv_n, m->dz3, m->part);
     MCK(cudaGetLastError());
-    MCK(reduce(m->part, ob, kOutPart, 3 * kH + 3, m->G + kOffW4, 0));           // dW4, db4
-    MCK(reduce(m->part + 3 * kH + 3, ob, kOutPart, 1, m->loss, 1));             // the loss sum, accumulated
-    // rows per block of the feature reductions: at most kRedBlocks blocks
-    const int chunk = std::max(64, (rows + kRedBlocks - 1) / kRedBlocks);
-    const int nb = (rows + chunk - 1) / chunk;
+    MCK(reduce(m->part, ob, kOutPart, 4 * kH + 3, m->G + kOffB3, 0));          // db3, dW4, db4
+    MCK(reduce(m->part + 4 * kH + 3, ob, kOutPart, 1, m->loss, 1));             // the loss sum, accumulated
     // split-K of the weight-gradient GEMMs: a divisor of rows / 256, at most kSplitMax
     int ks = std::min(rows / kKC, kSplitMax);
     while ((rows / kKC) % ks) --ks;
-    // layer 3: dz2 = (dz3 W3) * GELU'(z2); dW3 = dz3^T h2; db3 = sum dz3
+    if (rows >= kManyRows) {
+        // persistent backward GEMMs with the bias and first-layer gradients
+        // summed per row tile in their epilogues (dz1 is never stored)
+        const int tiles = rows / kTileM;
+        // layer 3: dz2 = (dz3 W3) * GELU'(z2) with db2; dW3 = dz3^T h2
+        MCK((persistent<kEpiBwd, 1>(m, m->dz3, kH, m->W3T, kH, rows, nullptr, nullptr, m->z2, m->dz2, nullptr,
+                                    m->red)));
+        MCK(gemm<kEpiSplitMN>(m, m->dz3, kH, m->h2, kH, kH, rows, ks, nullptr, nullptr, nullptr, nullptr, m->part));
+        MCK(reduce(m->part, ks, kH * kH, kH * kH, m->G + kOffW3, 0));
+        MCK(reduce(m->red, tiles, kH, kH, m->G + kOffB2, 0));
+        // layer 2: dz1 = (dz2 W2) * GELU'(z1) summed into dW1 = dz1^T x and
+        // db1; dW2 = dz2^T h1
+        MCK((persistent<kEpiBwd, 5>(m, m->dz2, kH, m->W2T, kH, rows, nullptr, nullptr, m->z1, nullptr, m->x,
+                                    m->red)));
+        MCK(gemm<kEpiSplitMN>(m, m->dz2, kH, m->h1, kH, kH, rows, ks, nullptr, nullptr, nullptr, nullptr, m->part));
+        MCK(reduce(m->part, ks, kH * kH, kH * kH, m->G + kOffW2, 0));
+        MCK(reduce(m->red, tiles, 5 * kH, 5 * kH, m->G + kOffW1, 0));
+        return DP_OK;
+    }
+    // rows per block of the feature reductions: at most kRedBlocks blocks
+    const int chunk = std::max(64, (rows + kRedBlocks - 1) / kRedBlocks);
+    const int nb = (rows + chunk - 1) / chunk;
+    // layer 3: dz2 = (dz3 W3) * GELU'(z2); dW3 = dz3^T h2
     MCK(gemm<kEpiBwd>(m, m->dz3, kH, m->W3T, kH, rows, kH, 1, nullptr, nullptr, m->z2, m->dz2, nullptr));
     MCK(gemm<kEpiSplitMN>(m, m->dz3, kH, m->h2, kH, kH, rows, ks, nullptr, nullptr, nullptr, nullptr, m->part));
     MCK(reduce(m->part, ks, kH * kH, kH * kH, m->G + kOffW3, 0));
-    feat_reduce_kernel<0><<<nb, 256, 0, m->st>>>(m->dz3, nullptr, rows, chunk, m->part);
-    MCK(cudaGetLastError());
-    MCK(reduce(m->part, nb, kH, kH, m->G + kOffB3, 0));
     // layer 2: dz1 = (dz2 W2) * GELU'(z1); dW2 = dz2^T h1; db2 = sum dz2
     MCK(gemm<kEpiBwd>(m, m->dz2, kH, m->W2T, kH, rows, kH, 1, nullptr, nullptr, m->z1, m->dz1, nullptr));
     MCK(gemm<kEpiSplitMN>(m, m->dz2, kH, m->h1, kH, kH, rows, ks, nullptr, nullptr, nullptr, nullptr, m->part));
@@ -943,9 +1049,9 @@ int forward_backward(dp_mlp* m, int count, float inv_n)
 int adam_launch(dp_mlp* m, double lr)
 {
     adam_kernel<<<(kParams + 255) / 256, 256, 0, m->st>>>(m->P, m->G, m->Am, m->Av, kParams, (float)lr, 0.9f, 0.999f,
-                                                          1e-8f, m->ts);
+                                                          1e-8f, m->ts, m->W2b, m->W3b, m->W2T, m->W3T);
     MCK(cudaGetLastError());
-    return refresh_bf16(m);
+    return DP_OK;
 }
 
 // One Adam step with the gradient in m->G (the next step count).
@@ -1118,6 +1224,7 @@ int dp_mlp_create(const double* lo, const double* hi, int32_t batch_capacity, vo
     A(&m->z1, CH); A(&m->z2, CH); A(&m->z3, CH);
     A(&m->h1, CH); A(&m->h2, CH); A(&m->h3, CH); A(&m->dz1, CH); A(&m->dz2, CH); A(&m->dz3, CH);
     A(&m->states, C * 4); A(&m->loss, 1); A(&m->err, 1); A(&m->part, kPartFloats);
+    A(&m->red, C / kTileM * 5 * kH);
     A(&m->ts, 1);
     if (e == cudaSuccess) e = cudaMallocHost(&m->h_loss, sizeof(float));
     if (e == cudaSuccess) e = cudaMallocHost(&m->h_err, sizeof(int));
