@@ -671,32 +671,42 @@ __global__ void __launch_bounds__(256) out_train_kernel(const bf16* __restrict__
     }
 }
 
-// out[i] (+)= sum_k part[k * stride + i] for i < len, k in order: the
-// fixed-order reduction of per-block partial sums (accumulate: add to out
-// instead of storing).
-__global__ void sum_partials_kernel(const float* __restrict__ part, int n_part, int stride, int len,
-                                    float* __restrict__ out, int accumulate)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= len) return;
-    float acc = 0.0f;
-    for (int k = 0; k < n_part; ++k) acc += part[(size_t)k * stride + i];
-    out[i] = accumulate ? out[i] + acc : acc;
-}
+// Fixed-order reductions of per-block partial sums: out[i] (+)= sum over k
+// of part[k * stride + i], i < len (accumulate: add to out instead of
+// storing).  Long outputs take a thread per output, which sums k in order;
+// short outputs with many partials a warp per output, lane l summing
+// partials l, l + 32, ... in order before a fixed shuffle tree combines the
+// lanes.  Two such reductions run in one launch: blocks [0, a.blocks) take
+// segment a, the rest segment b (b.blocks = 0: none).
+struct RedSeg {
+    const float* part;
+    int n_part, stride, len;
+    float* out;
+    int accumulate;
+    int warp;     // 1: a warp per output (8 per block), 0: a thread per output
+    int blocks;
+};
 
-// The same for short outputs with many partials, one warp per output: lane l
-// sums partials l, l + 32, ... in order, then a fixed shuffle tree combines
-// the lanes (deterministic as well).
-__global__ void sum_partials_warp_kernel(const float* __restrict__ part, int n_part, int stride, int len,
-                                         float* __restrict__ out, int accumulate)
+__global__ void sum_segments_kernel(RedSeg a, RedSeg b)
 {
-    const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (i >= len) return;
-    float acc = 0.0f;
-    for (int k = lane; k < n_part; k += 32) acc += part[(size_t)k * stride + i];
+    const bool first = (int)blockIdx.x < a.blocks;
+    const RedSeg& r = first ? a : b;
+    const int blk = first ? (int)blockIdx.x : (int)blockIdx.x - a.blocks;
+    if (r.warp) {
+        const int i = (int)((blk * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+        if (i >= r.len) return;
+        float acc = 0.0f;
+        for (int k = lane; k < r.n_part; k += 32) acc += r.part[(size_t)k * r.stride + i];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) out[i] = accumulate ? out[i] + acc : acc;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) r.out[i] = r.accumulate ? r.out[i] + acc : acc;
+    } else {
+        const int i = blk * blockDim.x + threadIdx.x;
+        if (i >= r.len) return;
+        float acc = 0.0f;
+        for (int k = 0; k < r.n_part; ++k) acc += r.part[(size_t)k * r.stride + i];
+        r.out[i] = r.accumulate ? r.out[i] + acc : acc;
+    }
 }
 
 // Per-feature reductions over a chunk of samples (thread = feature), in
@@ -745,38 +755,46 @@ __global__ void feat_reduce_kernel(const bf16* __restrict__ dz, const float* __r
 // Adam on the FP32 master parameters, writing the BF16 copies of W2, W3 and
 // their transposes used by the tensor-core GEMMs as it goes.
 // The step count t (1 for the first step) comes from device memory; the
-// bias corrections are 1 - beta^t.
+// bias corrections are 1 - beta^t.  advance > 0 (a replayed training step):
+// the last block to finish moves the step on -- the next step's first
+// sample start += advance and t += 1 -- once every block has read t and the
+// step size; *arrive counts the finished blocks and is back at 0 afterwards.
 __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
                             float* __restrict__ v, int n, float lr, float b1, float b2, float eps,
-                            const TrainState* __restrict__ ts, bf16* __restrict__ W2, bf16* __restrict__ W3,
-                            bf16* __restrict__ W2T, bf16* __restrict__ W3T)
+                            TrainState* __restrict__ ts, bf16* __restrict__ W2, bf16* __restrict__ W3,
+                            bf16* __restrict__ W2T, bf16* __restrict__ W3T, unsigned* __restrict__ arrive,
+                            int advance)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float tf = (float)ts->t;
-    if (ts->lr > 0.0f) lr = ts->lr;
-    const float bc1 = 1.0f - powf(b1, tf), bc2 = 1.0f - powf(b2, tf);
-    const float g = G[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * g;
-    const float vi = b2 * v[i] + (1.0f - b2) * g * g;
-    m[i] = mi;
-    v[i] = vi;
-    const float p = P[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-    P[i] = p;
-    const bool w2 = i >= kOffW2 && i < kOffW2 + kH * kH, w3 = i >= kOffW3 && i < kOffW3 + kH * kH;
-    if (w2 || w3) {
-        const int e = i - (w2 ? kOffW2 : kOffW3), o = e / kH, c = e % kH;
-        (w2 ? W2 : W3)[e] = __float2bfloat16(p);
-        (w2 ? W2T : W3T)[c * kH + o] = __float2bfloat16(p);
+    if (i < n) {
+        const float tf = (float)ts->t;
+        if (ts->lr > 0.0f) lr = ts->lr;
+        const float bc1 = 1.0f - powf(b1, tf), bc2 = 1.0f - powf(b2, tf);
+        const float g = G[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * g;
+        const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        const float p = P[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        P[i] = p;
+        const bool w2 = i >= kOffW2 && i < kOffW2 + kH * kH, w3 = i >= kOffW3 && i < kOffW3 + kH * kH;
+        if (w2 || w3) {
+            const int e = i - (w2 ? kOffW2 : kOffW3), o = e / kH, c = e % kH;
+            (w2 ? W2 : W3)[e] = __float2bfloat16(p);
+            (w2 ? W2T : W3T)[c * kH + o] = __float2bfloat16(p);
+        }
     }
-}
-
-// End of a replayed training step: the next step's first sample and the
-// next Adam step count.
-__global__ void train_advance_kernel(TrainState* ts, int batch)
-{
-    ts->start += batch;
-    ts->t += 1;
+    if (advance > 0) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(arrive, 1u) == gridDim.x - 1) {
+                ts->start += advance;
+                ts->t += 1;
+                *arrive = 0u;
+            }
+        }
+    }
 }
 
 // Sets the Adam step count (eager steps outside a replayed graph).
@@ -846,6 +864,7 @@ struct dp_mlp {
     float* loss = nullptr;
     float* part = nullptr;             // partial sums of the backward pass (kPartFloats)
     float* red = nullptr;              // per-row-tile sums of the fused backward GEMMs (cap / 128 x 5 x 256)
+    unsigned* arrive = nullptr;        // blocks of the Adam kernel that have finished (0 between launches)
     int* err = nullptr;
     float* h_loss = nullptr;           // pinned
     int* h_err = nullptr;
@@ -864,7 +883,7 @@ void free_mlp(dp_mlp* m)
     cudaSetDevice(m->device);
     if (m->st) cudaStreamSynchronize(m->st);
     void* ps[] = {m->P, m->G, m->Am, m->Av, m->W2b, m->W3b, m->W2T, m->W3T, m->x, m->t, m->z1, m->z2, m->z3, m->y,
-                  m->h1, m->h2, m->h3, m->dz1, m->dz2, m->dz3, m->states, m->loss, m->part, m->red, m->err};
+                  m->h1, m->h2, m->h3, m->dz1, m->dz2, m->dz3, m->states, m->loss, m->part, m->red, m->arrive, m->err};
     for (void* p : ps)
         if (p) cudaFree(p);
     if (m->h_loss) cudaFreeHost(m->h_loss);
@@ -989,18 +1008,23 @@ int forward_backward(dp_mlp* m, int count, float inv_n)
     if ((rc = forward_hidden(m, count, true))) return rc;
     // every gradient sum goes through per-block partial sums and a reduction
     // in a fixed order, so that a training run is reproducible bit for bit
-    auto reduce = [&](const float* part, int n_part, int stride, int len, float* out, int accumulate) {
-        if (len <= 8192)   // short outputs: a warp per output
-            sum_partials_warp_kernel<<<(len + 7) / 8, 256, 0, m->st>>>(part, n_part, stride, len, out, accumulate);
-        else
-            sum_partials_kernel<<<(len + 255) / 256, 256, 0, m->st>>>(part, n_part, stride, len, out, accumulate);
+    auto seg = [](const float* part, int n_part, int stride, int len, float* out, int accumulate) {
+        RedSeg r{part, n_part, stride, len, out, accumulate, len <= 8192 ? 1 : 0, 0};   // short: a warp each
+        r.blocks = r.warp ? (len + 7) / 8 : (len + 255) / 256;
+        return r;
+    };
+    auto reduce2 = [&](const RedSeg& a, const RedSeg& b) {   // both in one launch
+        sum_segments_kernel<<<a.blocks + b.blocks, 256, 0, m->st>>>(a, b);
         return cudaGetLastError();
+    };
+    auto reduce = [&](const float* part, int n_part, int stride, int len, float* out, int accumulate) {
+        return reduce2(seg(part, n_part, stride, len, out, accumulate), RedSeg{});
     };
     const int ob = (int)std::min<long long>(std::min<long long>((count + 7) / 8, 2LL * m->sm_count), kOutBlocks);
     out_train_kernel<<<ob, 256, 0, m->st>>>(m->h3, m->P, m->t, m->z3, count, inv_n, m->dz3, m->part);
     MCK(cudaGetLastError());
-    MCK(reduce(m->part, ob, kOutPart, 4 * kH + 3, m->G + kOffB3, 0));          // db3, dW4, db4
-    MCK(reduce(m->part + 4 * kH + 3, ob, kOutPart, 1, m->loss, 1));             // the loss sum, accumulated
+    MCK(reduce2(seg(m->part, ob, kOutPart, 4 * kH + 3, m->G + kOffB3, 0),      // db3, dW4, db4
+                seg(m->part + 4 * kH + 3, ob, kOutPart, 1, m->loss, 1)));       // the loss sum, accumulated
     // split-K of the weight-gradient GEMMs: a divisor of rows / 256, at most kSplitMax
     int ks = std::min(rows / kKC, kSplitMax);
     while ((rows / kKC) % ks) --ks;
@@ -1012,15 +1036,14 @@ int forward_backward(dp_mlp* m, int count, float inv_n)
         MCK((persistent<kEpiBwd, 1>(m, m->dz3, kH, m->W3T, kH, rows, nullptr, nullptr, m->z2, m->dz2, nullptr,
                                     m->red)));
         MCK(gemm<kEpiSplitMN>(m, m->dz3, kH, m->h2, kH, kH, rows, ks, nullptr, nullptr, nullptr, nullptr, m->part));
-        MCK(reduce(m->part, ks, kH * kH, kH * kH, m->G + kOffW3, 0));
-        MCK(reduce(m->red, tiles, kH, kH, m->G + kOffB2, 0));
+        MCK(reduce2(seg(m->part, ks, kH * kH, kH * kH, m->G + kOffW3, 0), seg(m->red, tiles, kH, kH, m->G + kOffB2, 0)));
         // layer 2: dz1 = (dz2 W2) * GELU'(z1) summed into dW1 = dz1^T x and
         // db1; dW2 = dz2^T h1
         MCK((persistent<kEpiBwd, 5>(m, m->dz2, kH, m->W2T, kH, rows, nullptr, nullptr, m->z1, nullptr, m->x,
                                     m->red)));
         MCK(gemm<kEpiSplitMN>(m, m->dz2, kH, m->h1, kH, kH, rows, ks, nullptr, nullptr, nullptr, nullptr, m->part));
-        MCK(reduce(m->part, ks, kH * kH, kH * kH, m->G + kOffW2, 0));
-        MCK(reduce(m->red, tiles, 5 * kH, 5 * kH, m->G + kOffW1, 0));
+        MCK(reduce2(seg(m->part, ks, kH * kH, kH * kH, m->G + kOffW2, 0),
+                    seg(m->red, tiles, 5 * kH, 5 * kH, m->G + kOffW1, 0)));
         return DP_OK;
     }
     // rows per block of the feature reductions: at most kRedBlocks blocks
@@ -1046,10 +1069,11 @@ int forward_backward(dp_mlp* m, int count, float inv_n)
 
 // Adam (beta1 0.9, beta2 0.999, eps 1e-8) with the gradient in m->G and the
 // step count in m->ts, then the BF16 copies of the weights.
-int adam_launch(dp_mlp* m, double lr)
+int adam_launch(dp_mlp* m, double lr, int advance = 0)
 {
     adam_kernel<<<(kParams + 255) / 256, 256, 0, m->st>>>(m->P, m->G, m->Am, m->Av, kParams, (float)lr, 0.9f, 0.999f,
-                                                          1e-8f, m->ts, m->W2b, m->W3b, m->W2T, m->W3T);
+                                                          1e-8f, m->ts, m->W2b, m->W3b, m->W2T, m->W3T, m->arrive,
+                                                          advance);
     MCK(cudaGetLastError());
     return DP_OK;
 }
@@ -1100,10 +1124,7 @@ int train_step(dp_mlp* m, const GridView& gv, int B, Box4 nlo, Box4 nhi, double 
     MCK(cudaGetLastError());
     int rc;
     if ((rc = forward_backward(m, B, 1.0f / (3.0f * B)))) return rc;
-    if ((rc = adam_launch(m, lr))) return rc;
-    train_advance_kernel<<<1, 1, 0, m->st>>>(m->ts, B);
-    MCK(cudaGetLastError());
-    return DP_OK;
+    return adam_launch(m, lr, B);   // with the next step's start and count
 }
 
 // The epochs of dp_mlp_train_grid.  The first step runs as launched (it also
@@ -1224,7 +1245,7 @@ int dp_mlp_create(const double* lo, const double* hi, int32_t batch_capacity, vo
     A(&m->z1, CH); A(&m->z2, CH); A(&m->z3, CH);
     A(&m->h1, CH); A(&m->h2, CH); A(&m->h3, CH); A(&m->dz1, CH); A(&m->dz2, CH); A(&m->dz3, CH);
     A(&m->states, C * 4); A(&m->loss, 1); A(&m->err, 1); A(&m->part, kPartFloats);
-    A(&m->red, C / kTileM * 5 * kH);
+    A(&m->red, C / kTileM * 5 * kH); A(&m->arrive, 1);
     A(&m->ts, 1);
     if (e == cudaSuccess) e = cudaMallocHost(&m->h_loss, sizeof(float));
     if (e == cudaSuccess) e = cudaMallocHost(&m->h_err, sizeof(int));
@@ -1240,6 +1261,7 @@ int dp_mlp_create(const double* lo, const double* hi, int32_t batch_capacity, vo
     cudaMemsetAsync(m->Am, 0, sizeof(float) * kParams, m->st);
     cudaMemsetAsync(m->Av, 0, sizeof(float) * kParams, m->st);
     cudaMemsetAsync(m->err, 0, sizeof(int), m->st);
+    cudaMemsetAsync(m->arrive, 0, sizeof(unsigned), m->st);
     *out = m;
     return DP_OK;
 }
