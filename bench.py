@@ -38,8 +38,8 @@ METRIC = "Bellman node-updates/s; time to ‖ΔV‖∞<1e-6, plain vs NN-warm-st
 # hash of the kernel sources they were taken on: a capture of an older kernel
 # is reported as stale (traffic null) instead of silently.
 EVAL_TRAFFIC = {
-    "61x4": {"bytes": (166.166272e6 + 17.993216e6 + 166.171648e6 + 15.406080e6) / 2, "src": "19c3a7e18fcc9498"},
-    "121x4_band": {"bytes": (688.096512e6 + 191.919360e6 + 688.418560e6 + 188.714752e6) / 2, "src": "19c3a7e18fcc9498"},
+    "61x4": {"bytes": (166.166528e6 + 18.204672e6 + 166.231552e6 + 14.960896e6) / 2, "src": "75c6a83c8a18675f"},
+    "121x4_band": {"bytes": (678.591232e6 + 191.108608e6 + 677.034496e6 + 187.774976e6) / 2, "src": "75c6a83c8a18675f"},
 }
 KERNEL_SOURCES = ("paper_2407_14675_gb300/csrc/dp_sweep.cuh", "paper_2407_14675_gb300/csrc/dp_device.cuh")
 UNIT = "node-updates/s"

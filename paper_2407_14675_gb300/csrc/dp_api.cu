@@ -75,6 +75,7 @@ struct dp_grid {
     int tlo[4], thi[4];
 
     int4* rows = nullptr;
+    int* row_org = nullptr;
     unsigned* lines = nullptr;
     double2 *hi64 = nullptr, *lo64 = nullptr;
     float2 *hi32 = nullptr, *lo32 = nullptr;
@@ -138,7 +139,7 @@ void free_grid(dp_grid* g)
     if (!g) return;
     cudaSetDevice(g->device);
     if (g->st) cudaStreamSynchronize(g->st);
-    void* ps[] = {g->rows, g->lines, g->hi64, g->lo64, g->hi32, g->lo32, g->V[0], g->V[1], g->V64[0],
+    void* ps[] = {g->rows, g->row_org, g->lines, g->hi64, g->lo64, g->hi32, g->lo32, g->V[0], g->V[1], g->V64[0],
                   g->V64[1], g->code, g->feet_lo, g->feet_hi, g->acc, g->ctl, g->ring, g->staging,
                   g->scratch64, g->gm_Q, g->gm_partial, g->gm_ctl, g->f64.w, g->f64.t, g->f64.c,
                   g->wave_sync};
@@ -268,6 +269,7 @@ void fill_geo(const dp_grid* gr, Geo<G>& g)
     g.magic_m = ((1ULL << 40) + (unsigned long long)d.n[3] - 1) / (unsigned long long)d.n[3];
     g.n_nodes = (int)gr->n_active;
     g.rows = gr->rows;
+    g.row_org = gr->row_org;
     g.lines = gr->lines;
 }
 
@@ -1032,7 +1034,7 @@ int dp_grid_create(const dp_grid_desc* desc, dp_grid** out)
     }
 
     // node set
-    if ((rc = dalloc(g, &g->rows, g->n_rows))) return bail(rc);
+    if ((rc = dalloc(g, &g->rows, g->n_rows)) || (rc = dalloc(g, &g->row_org, g->n_rows))) return bail(rc);
     int* d_err = nullptr;
     long long* d_total = nullptr;
     if ((rc = dalloc(g, &d_err, 1))) return bail(rc);
@@ -1048,7 +1050,7 @@ int dp_grid_create(const dp_grid_desc* desc, dp_grid** out)
     if ((e = cudaMemsetAsync(d_err, 0, sizeof(int), g->st)) != cudaSuccess ||
         (e = launch_rows(g->rows, d_err, d.n[0], d.n[1], d.n[2], d.n[3], d.lo, g->h, d.mu, d.reduced, d.energy_lo,
                          d.energy_hi, g->st)) != cudaSuccess ||
-        (e = launch_row_offsets(g->rows, g->n_rows, d.n[3], d_total, g->st)) != cudaSuccess ||
+        (e = launch_row_offsets(g->rows, g->n_rows, d.n[3], d_total, g->st, g->row_org)) != cudaSuccess ||
         (e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, g->st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(&h_total, d_total, sizeof(long long), cudaMemcpyDeviceToHost, g->st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(g->st)) != cudaSuccess) {

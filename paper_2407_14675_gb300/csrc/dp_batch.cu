@@ -868,10 +868,12 @@ int dp_batch_create(const dp_grid_desc* descs, int32_t count, void* stream, dp_b
     for (int t = 0; t < count; ++t) {
         b->g32[t].lines = b->lines + line_off[t];
         b->g32[t].rows = nullptr;
+        b->g32[t].row_org = nullptr;
         b->g32[t].tab_hi = b->hi32;
         b->g32[t].tab_lo = b->lo32;
         b->g64[t].lines = b->lines + line_off[t];
         b->g64[t].rows = nullptr;
+        b->g64[t].row_org = nullptr;
         b->g64[t].tab_hi = b->hi64;
         b->g64[t].tab_lo = b->lo64;
     }

@@ -79,8 +79,9 @@ cudaError_t launch_rows(int4* rows, int* err, int n0, int n1, int n2, int n3, co
 }
 
 // Exclusive prefix sum of len * n_m over rows (one block, chunked): the
-// compact index of each row's first node.  total receives the node count.
-__global__ void row_offsets_kernel(int4* rows, int n_rows, int n_m, long long* total)
+// compact index of each row's first node.  total receives the node count;
+// org (nullable) each row's origin, first index - lo_vt * n_m.
+__global__ void row_offsets_kernel(int4* rows, int n_rows, int n_m, long long* total, int* org)
 {
     __shared__ long long part[1024];
     const int T = blockDim.x, t = threadIdx.x;
@@ -99,14 +100,15 @@ __global__ void row_offsets_kernel(int4* rows, int n_rows, int n_m, long long* t
     long long run = part[t] - s;
     for (int r = a; r < b; ++r) {
         rows[r].x = (int)run;
+        if (org) org[r] = (int)(run - (long long)rows[r].y * n_m);
         run += (long long)rows[r].z * n_m;
     }
     if (t == T - 1) *total = part[t];
 }
 
-cudaError_t launch_row_offsets(int4* rows, int n_rows, int n_m, long long* total, cudaStream_t st)
+cudaError_t launch_row_offsets(int4* rows, int n_rows, int n_m, long long* total, cudaStream_t st, int* org)
 {
-    row_offsets_kernel<<<1, 1024, 0, st>>>(rows, n_rows, n_m, total);
+    row_offsets_kernel<<<1, 1024, 0, st>>>(rows, n_rows, n_m, total, org);
     return cudaGetLastError();
 }
 

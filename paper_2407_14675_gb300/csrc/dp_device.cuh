@@ -84,6 +84,8 @@ struct Geo {
     unsigned long long magic_m;    // ceil(2^40 / n_m): j / n_m for j < 2^40 / (n_m - 1)
     int n_nodes;               // stored nodes
     const int4* rows;          // per (i_r, i_vr): {first compact index, lo_vt, len, 0}
+    const int* row_org;        // reduced grids, per (i_r, i_vr): first compact index - lo_vt * n_m, the
+                               //   index (v_t = 0, m = 0) would have (4 bytes a row for the feet's lookups)
     const unsigned* lines;     // per compact (r, v_r, v_t) line: i_r | i_vr<<10 | i_vt<<20
     const typename V2<G>::type* tab_hi;   // (sin, cos) of 2 pi (c >> 8) 256 / 65536
     const typename V2<G>::type* tab_lo;   // (sin, cos) of 2 pi (c & 255) / 65536

@@ -113,7 +113,8 @@ cudaError_t launch_trig_tables(double2* hi64, double2* lo64, float2* hi32, float
 cudaError_t launch_rows(int4* rows, int* err, int n0, int n1, int n2, int n3, const double* lo,
                         const double* h, double mu, int reduced, double e_lo, double e_hi,
                         cudaStream_t st);
-cudaError_t launch_row_offsets(int4* rows, int n_rows, int n_m, long long* total, cudaStream_t st);
+cudaError_t launch_row_offsets(int4* rows, int n_rows, int n_m, long long* total, cudaStream_t st,
+                               int* org = nullptr);
 cudaError_t launch_lines(const int4* rows, unsigned* lines, int n0, int n1, int n2, int n_m,
                          cudaStream_t st);
 cudaError_t launch_store_value(const double* src, void* dst, int fp32, int n, const Geo<double>& g, int* bad,

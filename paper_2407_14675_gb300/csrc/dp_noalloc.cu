@@ -159,6 +159,7 @@ extern "C" int dp_bellman_sweep_noalloc(const dp_grid_desc* desc, int32_t mode, 
         return cuda_fail("scratch reset", e);
 
     g64.rows = g32.rows = d_rows;
+    g64.row_org = g32.row_org = nullptr;   // no frozen feet here
     g64.lines = g32.lines = d_lines;
     g64.tab_hi = (const double2*)(scr + kHi64);
     g64.tab_lo = (const double2*)(scr + kLo64);

@@ -116,13 +116,16 @@ __device__ __forceinline__ void foot_rows(const Geo<float>& g, int j, int dr, in
         base[2] = b0 + g.stride[0];
         base[3] = b0 + g.stride[0] + g.stride[1];
     } else {
-        int i[4], c[4];
+        // the four (r, v_r) rows' origins: membership was checked when the
+        // foot was stored, so the row lengths are not needed
+        int i[4];
         decode_node(g, j, i);
-        c[0] = i[0] + dr;
-        c[1] = i[1] + dv;
-        c[2] = i[2] + dt;
-        c[3] = i[3] + g.foot_dm;
-        cell_rows<float, true>(g, c, base);   // membership was checked when the foot was stored
+        const int row = (i[0] + dr) * g.n[1] + i[1] + dv;
+        const int off = (i[2] + dt) * g.n_m + i[3] + g.foot_dm;
+        base[0] = __ldg(&g.row_org[row]) + off;
+        base[1] = __ldg(&g.row_org[row + 1]) + off;
+        base[2] = __ldg(&g.row_org[row + g.n[1]]) + off;
+        base[3] = __ldg(&g.row_org[row + g.n[1] + 1]) + off;
     }
 }
 
