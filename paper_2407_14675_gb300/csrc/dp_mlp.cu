@@ -964,8 +964,10 @@ template <int EPI>
 cudaError_t gemm(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int rows, int k_total, int k_split,
                  const float* bias, float* zout, const float* zin, bf16* hout, float* cacc)
 {
-    if ((EPI == kEpiFwd || EPI == kEpiBwd) && rows >= kManyRows && k_total == kKC && k_split == 1)
-        return persistent<EPI>(m, A, lda, B, ldb, rows, bias, zout, zin, hout);
+    if constexpr (EPI == kEpiFwd || EPI == kEpiBwd) {
+        if (rows >= kManyRows && k_total == kKC && k_split == 1)
+            return persistent<EPI>(m, A, lda, B, ldb, rows, bias, zout, zin, hout);
+    }
     if (EPI != kEpiAtomic && EPI != kEpiSplitMN && rows >= kManyRows)
         return gemm_kc<EPI, kKC / 2>(m, A, lda, B, ldb, rows, k_total, k_split, bias, zout, zin, hout, cacc);
     return gemm_kc<EPI, kKC>(m, A, lda, B, ldb, rows, k_total, k_split, bias, zout, zin, hout, cacc);
