@@ -709,7 +709,9 @@ __global__ void sum_segments_kernel(RedSeg a, RedSeg b)
     }
 }
 
-// Per-feature reductions over a chunk of samples (thread = feature), in
+// Per-feature reductions over a chunk of samples (thread = feature), for
+// batches below kManyRows rows (larger ones are summed per tile in the
+// persistent backward GEMM's epilogue), in
 // sample order:  db[o] = sum_s dz[s][o];  with X = 4 also
 // dW[o][d] = sum_s dz[s][o] x[s][d].  Block b writes its sums to
 // part[b][0 .. 4 X + ... ): dW (256 X values, feature-major) then db (256),
@@ -933,9 +935,10 @@ constexpr int kManyRows = 16384;
 
 // Partial sums of the backward pass (one buffer, reused by each reduction in
 // turn): split-K tiles of a weight gradient, the output layer's per-block
-// sums, the feature reductions' per-block sums.  Split-K 32 for the weight
-// gradients (fewer splits serialise the K loop of each CTA, more write more
-// partial tiles).
+// sums, and below kManyRows rows the feature reductions' per-block sums (the
+// persistent backward GEMMs write their per-tile sums to dp_mlp::red
+// instead).  Split-K 32 for the weight gradients (fewer splits serialise the
+// K loop of each CTA, more write more partial tiles).
 constexpr int kSplitMax = 32, kOutBlocks = 1024, kRedBlocks = 256;
 constexpr size_t kPartFloats = (size_t)kSplitMax * kH * kH;   // >= kOutBlocks * kOutPart, kRedBlocks * 5 * kH
 
@@ -1131,7 +1134,7 @@ int train_step(dp_mlp* m, const GridView& gv, int B, Box4 nlo, Box4 nhi, double 
 
 // The epochs of dp_mlp_train_grid.  The first step runs as launched (it also
 // sets the kernels' attributes); the next one is captured as a CUDA graph
-// and every later step replays it, which removes the host's ~20 launches
+// and every later step replays it, which removes the host's 13 launches
 // per step.
 int train_grid_steps(dp_mlp* m, const GridView& gv, const dp_mlp_train_opts* o, dp_mlp_train_stats* stats)
 {
