@@ -601,7 +601,7 @@ void orc_bellman_nodes(const orc_problem* p, const double* V, const unsigned cha
     }
 }
 
-/* q at a list of (node, code) pairs: used to judge near-tie decisions. */
+/* q at a list of (node, code) pairs: used to check near-tie decisions. */
 void orc_q_nodes(const orc_problem* p, const double* V, const unsigned char* active,
                  const long* nodes, const uint16_t* codes, long count, double* q_out)
 {

@@ -3,7 +3,7 @@
 // cos alpha*, sin alpha*) samples of a solved grid, then evaluated on every
 // node of another grid to initialise V and the policy of policy iteration.
 // Not part of the paper: the network only supplies the starting point, and
-// the Bellman sweeps remain the judge of the result.
+// the Bellman sweeps alone decide the result.
 //
 // The two 256 x 256 layers (98.6 % of the FLOPs) run on the fifth-generation
 // tensor cores: tcgen05.mma kind::f16, BF16 operands staged in shared memory,
