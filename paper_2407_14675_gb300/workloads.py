@@ -102,7 +102,7 @@ def config2(n: int = 121) -> Problem:
     return config1(n).replace(reduced=1, energy_lo=e_lo, energy_hi=e_hi)
 
 
-MU_EARTH = 398600.4418   # km^3 / s^2
+MU_EARTH = 398600.4   # km^3 / s^2, the Earth's gravitational parameter as the paper prints it (§2.1)
 
 
 def example1(n=(110, 30, 30, 30), accel: float = 5e-7) -> Problem:
