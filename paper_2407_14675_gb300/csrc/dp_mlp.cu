@@ -12,6 +12,7 @@
 // input layer, the 3-wide output layer, the reductions and Adam run on the
 // CUDA cores.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -911,17 +912,31 @@ int refresh_bf16(dp_mlp* m)
     return DP_OK;
 }
 
+// A kernel's dynamic shared-memory limit, raised once per device (function
+// attributes hold per device, so a process that drives several GPUs raises
+// it on each).
+constexpr int kMaxDevices = 64;
+
+template <typename K>
+cudaError_t raise_smem_limit(K kernel, int bytes, std::atomic<bool> (&done)[kMaxDevices])
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done[dev].store(true, std::memory_order_release);
+    return e;
+}
+
 template <int EPI, int KC>
 cudaError_t gemm_kc(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int rows, int k_total, int k_split,
                     const float* bias, float* zout, const float* zin, bf16* hout, float* cacc)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(mlp_gemm_kernel<EPI, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             gemm_smem_of<EPI, KC>());
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<bool> attr[kMaxDevices];
+    cudaError_t e = raise_smem_limit(mlp_gemm_kernel<EPI, KC>, gemm_smem_of<EPI, KC>(), attr);
+    if (e != cudaSuccess) return e;
     dim3 grid(rows / kTileM, kH / kTileN, k_split);
     mlp_gemm_kernel<EPI, KC><<<grid, 128, gemm_smem_of<EPI, KC>(), m->st>>>(A, lda, B, ldb, k_total / k_split, bias, zout, zin,
                                                                    hout, cacc, m->err, m->wait_polls);
@@ -948,13 +963,9 @@ template <int EPI, int RED = 0>
 cudaError_t persistent(dp_mlp* m, const bf16* A, int lda, const bf16* B, int ldb, int rows, const float* bias,
                        float* zout, const float* zin, bf16* hout, const float* xin = nullptr, float* red = nullptr)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(mlp_persistent_kernel<EPI, RED>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<bool> attr[kMaxDevices];
+    cudaError_t e = raise_smem_limit(mlp_persistent_kernel<EPI, RED>, kPersistSmem, attr);
+    if (e != cudaSuccess) return e;
     const int tiles = rows / kTileM;
     const int per_half = std::max(1, std::min(tiles, m->sm_count / 2));
     dim3 grid(per_half, kH / kTileN);
