@@ -501,6 +501,24 @@ def test_example1_cost_vanishes_on_the_target_orbit():
                                                      rel=1e-9)
 
 
+def test_example1_cost_eccentricity_vector_term():
+    # Eq. (11) with a = a_bar: only gamma |e_vec - e_bar_vec|^2 remains (thrust
+    # off), where e_vec = e (cos omega, sin omega).  Orbits of the same
+    # eccentricity but another argument of perigee cost more than the target's
+    # own, which a scalar (e - e_bar)^2 would miss.
+    p = W.example1(n=(5, 3, 3, 4))
+    o = oracle.Oracle(p)
+    ebx, eby = p.e_bar * math.cos(p.omega_bar), p.e_bar * math.sin(p.omega_bar)
+    for e, w in ((0.003, 1.0), (0.001, math.pi / 2), (0.001, math.pi), (0.0025, -2.2)):
+        want = p.cost_gamma * ((e * math.cos(w) - ebx) ** 2 + (e * math.sin(w) - eby) ** 2)
+        for nu in (0.3, 2.5, 5.1):
+            x = _ellipse_state(W.MU_EARTH, p.a_bar, e, w, nu)
+            assert o.running_cost(x, thrust_on=False) == pytest.approx(want, rel=1e-7, abs=1e-18)
+    # same eccentricity as the target, perigee turned by pi: |e_vec - e_bar_vec| = 2 e_bar
+    x = _ellipse_state(W.MU_EARTH, p.a_bar, p.e_bar, p.omega_bar + math.pi, 1.1)
+    assert o.running_cost(x, thrust_on=False) == pytest.approx(p.cost_gamma * (2 * p.e_bar) ** 2, rel=1e-7)
+
+
 def test_example1_dynamics_identities():
     p = W.example1(n=(5, 3, 3, 4))
     o = oracle.Oracle(p)
