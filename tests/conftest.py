@@ -11,6 +11,7 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the compiled library")
     config.addinivalue_line("markers", "slow: long CPU test")
+    config.addinivalue_line("markers", "mutation: plants a mistake in a copy of the oracle (opt-in)")
 
 
 @pytest.fixture(scope="session")

@@ -246,6 +246,72 @@ def test_2d_euclidean_limit():
     assert errs[2] < 0.1
 
 
+def test_ties_keep_the_lowest_tabulated_angle():
+    # V = 0 on an interior where every foot stays inside: every control gives
+    # q = dt exactly.  The enumeration keeps the lowest index (code 0), the
+    # refinement keeps the tabulated point when nothing is strictly lower, and
+    # the value is dt.
+    for refine in (0, 1):
+        p = W.unit_speed_2d(n=9, n_angles=8).replace(refine=refine, refine_tol=1e-4)
+        o = oracle.Oracle(p)
+        V = np.zeros(o.N)
+        Vn, codes, res, ev = o.sweep(V, mode=oracle.IMPROVE_FULL, codes=np.full(o.N, 999, np.uint16))
+        idx = np.array(np.unravel_index(np.arange(o.N), p.n)).T
+        inner = (idx[:, 0] > 0) & (idx[:, 0] < p.n[0] - 1) & (idx[:, 1] > 0) & (idx[:, 1] < p.n[1] - 1)
+        inner &= ~o.target.astype(bool)
+        assert inner.sum() > 20
+        assert (codes[inner] == 0).all(), refine
+        assert np.allclose(Vn[inner], p.dt, rtol=0, atol=1e-15)
+
+
+def test_sweep_residual_is_the_sup_norm_of_the_change():
+    # from a value above the fixed point the sweep lowers V: the residual is
+    # still max |V' - V| over the node set, not a signed difference
+    for p in (W.unit_speed_2d(), W.config0().replace(n=(7, 7, 7, 7))):
+        o = oracle.Oracle(p)
+        act = o.active.astype(bool)
+        for V in (np.full(o.N, 0.9 * p.penalty_M if p.penalty_M > 0 else 0.9 * p.dt / (1 - p.beta)),
+                  W.random_value(p, 5)):
+            Vn, _, r, _ = o.sweep(V, mode=oracle.VI)
+            assert r == np.abs(Vn - V)[act].max()
+            assert r > 0
+
+
+def test_policy_iteration_starts_with_a_full_tabulation():
+    # the first improvement of policy iteration enumerates every tabulated
+    # control (the walk only follows); from a random policy it equals the
+    # full-table improvement sweep, not the walk from that policy
+    p = W.config0().replace(n=(9, 9, 9, 9), refine=1)
+    o = oracle.Oracle(p)
+    V0 = W.random_value(p, 8)
+    codes0 = W.random_codes(p, 9)
+    V1, c1, outer, ev, res = o.policy_iterate(V0=V0, codes0=codes0, max_outer=1, n_eval=0, walk=True)
+    Vf, cf, _, _ = o.sweep(V0, mode=oracle.IMPROVE_FULL, codes=codes0)
+    Vw, cw, _, _ = o.sweep(V0, mode=oracle.IMPROVE_WALK, codes=codes0)
+    assert outer == 1
+    assert (c1 == cf).all() and (V1 == Vf).all()
+    assert (cw != cf).any()      # the walk from a random policy differs
+
+
+def test_tabulated_angles_are_the_nearest_lattice_codes():
+    # alpha_k = 2 pi k / K on the 16-bit lattice, rounded to the nearest code:
+    # with K = 72 (the paper's 5 degree table) 910.22 codes per step, so
+    # rounding and truncation differ for four k of every nine
+    p = W.example1(n=(8, 6, 6, 9)).replace(refine=0)
+    o = oracle.Oracle(p)
+    V = W.random_value(p, 4, hi=p.penalty_M)
+    _, codes, _, _ = o.sweep(V, mode=oracle.IMPROVE_FULL, codes=np.zeros(o.N, np.uint16))
+    act = o.active.astype(bool) & ~o.target.astype(bool)
+    on = codes[act][codes[act] != oracle.CODE_OFF].astype(np.int64)
+    assert on.size > 50
+    k = np.rint(on * p.n_angles / 65536.0).astype(np.int64) % p.n_angles
+    nearest = (k * 65536 + p.n_angles // 2) // p.n_angles
+    assert (on == nearest).all()
+    assert (np.abs(on - k * 65536.0 / p.n_angles) <= 0.5).all()
+    # the sample reaches indices where the two roundings differ
+    assert np.isin(k % 9, (3, 4, 7, 8)).any()
+
+
 @pytest.mark.slow
 def test_vi_and_pi_reach_the_same_fixed_point():
     # Eq. (12) and Eq. (13)-(14) solve the same fixed-point problem; the
@@ -519,6 +585,17 @@ def test_example1_cost_eccentricity_vector_term():
     assert o.running_cost(x, thrust_on=False) == pytest.approx(p.cost_gamma * (2 * p.e_bar) ** 2, rel=1e-7)
 
 
+def test_energy_is_the_vis_viva_energy_on_kepler_orbits():
+    # the specific energy v^2/2 - mu/r that selects the band (§3) equals
+    # -mu / (2a) everywhere on a Kepler ellipse, radial speed included
+    p = W.config2(n=9)
+    o = oracle.Oracle(p)
+    for a, e in ((1.0, 0.0), (1.02, 0.05), (0.97, 0.2)):
+        for nu in (0.4, 1.9, 3.6, 5.5):
+            x = _ellipse_state(1.0, a, e, 0.0, nu)
+            assert o.energy(np.array([x[0], x[1], x[2], 1.0])) == pytest.approx(-1.0 / (2.0 * a), rel=1e-13)
+
+
 def test_example1_dynamics_identities():
     p = W.example1(n=(5, 3, 3, 4))
     o = oracle.Oracle(p)
@@ -582,10 +659,17 @@ def test_example2_drag_coefficient_and_deceleration():
     f = o.dynamics_drag(y, oracle.OFF, C)
     # the printed components: -C v_rho^2 and -C v_theta^2; the energy then
     # falls at C (v_rho^3 + v_theta^3)
-    assert f[1] - f0[1] == pytest.approx(-C * y[1] ** 2, rel=1e-6)
-    assert f[2] - f0[2] == pytest.approx(-C * y[2] ** 2, rel=1e-6)
+    # (no absolute tolerance: the radial term is about 1e-17 km/s^2, next to
+    # f0[1] of about 3e-6, so its difference carries ~4e-5 relative rounding)
+    assert f[1] - f0[1] == pytest.approx(-C * y[1] ** 2, rel=1e-3, abs=0.0)
+    assert f[2] - f0[2] == pytest.approx(-C * y[2] ** 2, rel=1e-6, abs=0.0)
     dE = y[1] * (f[1] - f0[1]) + y[2] * (f[2] - f0[2])
-    assert dE == pytest.approx(-C * (y[1] ** 3 + y[2] ** 3), rel=1e-6)
+    assert dE == pytest.approx(-C * (y[1] ** 3 + y[2] ** 3), rel=1e-6, abs=0.0)
+    # an outward or inward radial speed both lose to the radial drag
+    for vr in (0.006, -0.006):
+        z = np.array([6990.0, vr, 7.55, 1.1])
+        dz = o.dynamics_drag(z, oracle.OFF, C)[1] - o.dynamics(z, oracle.OFF)[1]
+        assert dz < 0.0 and dz == pytest.approx(-C * vr * vr, rel=1e-3, abs=0.0)
     assert (o.dynamics_drag(y, 0.3, 0.0) == o.dynamics(y, 0.3)).all()
 
 
