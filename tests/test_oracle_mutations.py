@@ -74,6 +74,19 @@ MUTATIONS = [
  ("mlp.py", "adam v uses g", "v = state[\"v\"][li][pi] = b2 * state[\"v\"][li][pi] + (1 - b2) * g * g", "v = state[\"v\"][li][pi] = b2 * state[\"v\"][li][pi] + (1 - b2) * abs(g)"),
  ("mlp.py", "loss sum not mean", "return float(np.mean((Y - T) ** 2))", "return float(np.sum((Y - T) ** 2))"),
  ("mlp.py", "bias grad mean", "grads[li] = [d.T @ a_in, d.sum(axis=0)]", "grads[li] = [d.T @ a_in, d.mean(axis=0)]"),
+ ("dp_oracle.c", "spacing over n", "return (p->hi[d] - p->lo[d]) / (double)(p->n[d] - 1);", "return (p->hi[d] - p->lo[d]) / (double)(p->n[d]);"),
+ ("dp_oracle.c", "theta not periodic", "return p->dynamics == ORC_DYN_POLAR && d == 3;", "return 0;"),
+ ("dp_oracle.c", "feedback off loses ties", "            if (q_off <= q) { q = q_off; code = ORC_CODE_OFF; }\n        }\n        code_out[i]", "            if (q_off < q) { q = q_off; code = ORC_CODE_OFF; }\n        }\n        code_out[i]"),
+ ("dp_oracle.c", "feedback without refinement", "        if (p->refine) code = fibonacci_refine(&c, k, q, &q);\n        if (p->off_control) {\n            double q_off", "        if (0) code = fibonacci_refine(&c, k, q, &q);\n        if (p->off_control) {\n            double q_off"),
+ ("dp_oracle.c", "closed loop ignores thrust off", "rk4_step_drag(p, y, code_control(p, code), h, drag_c, z);", "rk4_step_drag(p, y, code_angle(code), h, drag_c, z);"),
+ ("dp_oracle.c", "one evaluation sweep short", "for (int e = 0; e < n_eval; ++e) {", "for (int e = 1; e < n_eval; ++e) {"),
+ ("dp_oracle.c", "vi diag penalty without dt", "q = p->dt + p->beta * p->M;", "q = p->beta * p->M;"),
+ ("dp_oracle.c", "vi diag self weight ignored", "if (idx[b] == j) self += w[b];", "if (0) self += w[b];"),
+ ("dp_oracle.c", "policy row target value", "if (target[j]) { *b = 0.0; return 0; }", "if (target[j]) { *b = p->dt; return 0; }"),
+ ("dp_oracle.c", "VI stops one sweep late", "        ++s;\n        if (res < tol) break;", "        ++s;\n        if (res < 0.5 * tol) break;"),
+ ("dp_oracle.c", "eval mode re-searches", "    if (mode == ORC_EVAL) {\n        *v_out = q_of_code(&c, code_in);", "    if (mode == ORC_EVAL) {\n        *v_out = q_of_code(&c, table_code(p->K, nearest_table_index(p->K, code_in)));"),
+ ("mlp.py", "gelu grad drops z pdf", "return cdf + z * pdf", "return cdf"),
+ ("mlp.py", "forward no bias", "        z = a @ W.T + b\n", "        z = a @ W.T\n"),
 ]
 
 

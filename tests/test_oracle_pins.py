@@ -647,6 +647,77 @@ def test_example1_thrust_off_wins_where_thrust_only_costs():
         assert Vn[j] == pytest.approx(p.dt * o.running_cost(x, False) + p.beta * 5.0, rel=1e-14)
 
 
+def test_thrust_off_wins_exact_ties_in_improvement_and_feedback():
+    # with no control cost (alpha = 0) and V = 0 (every Q1 blend exactly 0,
+    # whatever the weights), thrust and thrust off give exactly the same q at
+    # nodes whose feet stay inside; the off control wins the tie in the
+    # improvement sweep and in the feedback of Eq. (15) alike
+    p = W.example1(n=(6, 4, 4, 6)).replace(cost_alpha=0.0)
+    o = oracle.Oracle(p)
+    V = np.zeros(o.N)
+    _, codes, _, _ = o.sweep(V, mode=oracle.IMPROVE_FULL, codes=np.zeros(o.N, np.uint16))
+    idx = np.array(np.unravel_index(np.arange(o.N), p.n)).T
+    interior = (idx[:, 0] > 0) & (idx[:, 0] < p.n[0] - 1) & (idx[:, 1] > 0) & (idx[:, 1] < p.n[1] - 1) & \
+               (idx[:, 2] > 0) & (idx[:, 2] < p.n[2] - 1)
+    assert interior.sum() >= 8
+    assert (codes[interior] == oracle.CODE_OFF).all()
+    h = (np.array(p.hi) - np.array(p.lo)) / (np.array(p.n) - 1)
+    states = np.array(p.lo) + idx[interior] * h
+    fc, _ = o.feedback(V, states)
+    assert (fc == oracle.CODE_OFF).all()
+
+
+def test_closed_loop_coasts_where_the_feedback_switches_off():
+    # V constant: the control term alone decides, the feedback switches the
+    # thrust off, and the closed loop must follow the unforced RK4 steps
+    p = W.example1(n=(6, 4, 4, 6))
+    o = oracle.Oracle(p)
+    V = np.full(o.N, 5.0)
+    x0 = np.array([7000.0, 0.001, 7.546, 0.4])
+    fc, _ = o.feedback(V, x0[None, :])
+    assert fc[0] == oracle.CODE_OFF
+    steps, h = 4, p.dt
+    ta, xf = o.simulate(V, x0[None, :], t_max=steps * h)
+    x = x0.copy()
+    for _ in range(steps):
+        x = o.rk4(x, oracle.OFF, h)
+    assert ta[0] == -1.0
+    assert np.array_equal(xf[0], x)
+
+
+def test_policy_iteration_is_improvement_then_n_eval_evaluations():
+    # the loop of modified policy iteration: a full-table improvement, n_eval
+    # evaluation sweeps at the frozen policy, a walk improvement, n_eval more
+    p = W.config0().replace(n=(7, 7, 7, 7))
+    o = oracle.Oracle(p)
+    V0 = W.random_value(p, 12)
+    c0 = W.random_codes(p, 13)
+    V, c, outer, evs, res = o.policy_iterate(V0=V0, codes0=c0, tol=0.0, max_outer=2, n_eval=3, walk=True)
+    assert outer == 2 and evs == 6
+    U, cu, _, _ = o.sweep(V0, mode=oracle.IMPROVE_FULL, codes=c0)
+    for _ in range(3):
+        U = o.sweep(U, mode=oracle.EVAL, codes=cu)[0]
+    U, cu, _, _ = o.sweep(U, mode=oracle.IMPROVE_WALK, codes=cu)
+    for _ in range(3):
+        U = o.sweep(U, mode=oracle.EVAL, codes=cu)[0]
+    assert np.array_equal(V, U) and np.array_equal(c, cu)
+
+
+def test_value_iteration_stops_at_the_first_sweep_below_tol():
+    # config 0 converges geometrically (its residual falls by about beta per
+    # sweep, never to an exact zero), so the first sweep below tol is unique
+    p = W.config0().replace(n=(7, 7, 7, 7))
+    o = oracle.Oracle(p)
+    for tol in (1e-2, 1e-3):
+        V, s, res = o.value_iterate(tol=tol, max_sweeps=10000)
+        U = np.zeros(o.N)
+        k, r = 0, np.inf
+        while r >= tol:
+            U, _, r, _ = o.sweep(U, mode=oracle.VI)
+            k += 1
+        assert s == k and res == r and np.array_equal(V, U)
+
+
 def test_example2_drag_coefficient_and_deceleration():
     # C = C_D S rho_D / (2 m) with the paper's constants, in 1/km
     C = W.example2_drag()
