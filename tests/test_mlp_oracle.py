@@ -112,3 +112,41 @@ def test_bf16_reference_is_the_fp64_network_with_rounded_operands():
     Y2, c2 = mlp.forward_bf16(params_r, Xr)
     # hidden activations still round, so compare the first layer's pre-activation
     assert np.array_equal(c1[0][1], c2[0][1])
+
+
+def test_bf16_reference_rounds_exactly_the_documented_operands():
+    # which operands the BF16-faithful reference rounds: the hidden activations
+    # (inputs of layers 2-4), the weights of layers 2 and 3, and the hidden
+    # pre-activation gradients; not the inputs, W1, W4 or the biases
+    rng = np.random.default_rng(11)
+    params = W.mlp_init_params(seed=12)
+    X = rng.uniform(-1, 1, size=(16, 4))
+    T = rng.uniform(-1, 1, size=(16, 3))
+    Y, cache = mlp.forward_bf16(params, X)
+    for li in (1, 2, 3):
+        a_in = cache[li][0]
+        assert np.array_equal(mlp.bf16(a_in), a_in), li
+    assert not np.array_equal(mlp.bf16(cache[0][0]), cache[0][0])       # inputs stay FP32
+
+    def with_rounded(layers):
+        return [[mlp.bf16(Wt) if li in layers else Wt, bv] for li, (Wt, bv) in enumerate(params)]
+
+    # pre-rounding W2 and W3 changes nothing, forward or backward
+    Y23, c23 = mlp.forward_bf16(with_rounded((1, 2)), X)
+    assert np.array_equal(Y23, Y)
+    g = mlp.backward_bf16(params, cache, Y, T)
+    g23 = mlp.backward_bf16(with_rounded((1, 2)), c23, Y23, T)
+    for li in range(4):
+        for pi in range(2):
+            assert np.array_equal(g23[li][pi], g[li][pi]), (li, pi)
+    # pre-rounding W1 or W4 does change the output: they are used as they are
+    for li in (0, 3):
+        assert not np.array_equal(mlp.forward_bf16(with_rounded((li,)), X)[0], Y), li
+    # one sample: the hidden layers' bias gradients are the rounded
+    # pre-activation gradients themselves
+    Y1, c1 = mlp.forward_bf16(params, X[:1])
+    g1 = mlp.backward_bf16(params, c1, Y1, T[:1])
+    for li in (0, 1, 2):
+        db = g1[li][1]
+        assert np.array_equal(mlp.bf16(db), db), li
+    assert not np.array_equal(mlp.bf16(g1[3][1]), g1[3][1])              # the output layer's is not rounded

@@ -87,6 +87,10 @@ MUTATIONS = [
  ("dp_oracle.c", "eval mode re-searches", "    if (mode == ORC_EVAL) {\n        *v_out = q_of_code(&c, code_in);", "    if (mode == ORC_EVAL) {\n        *v_out = q_of_code(&c, table_code(p->K, nearest_table_index(p->K, code_in)));"),
  ("mlp.py", "gelu grad drops z pdf", "return cdf + z * pdf", "return cdf"),
  ("mlp.py", "forward no bias", "        z = a @ W.T + b\n", "        z = a @ W.T\n"),
+ ("mlp.py", "bf16 activation not rounded", "        a = bf16(gelu(z)) if li < last else z", "        a = gelu(z) if li < last else z"),
+ ("mlp.py", "bf16 W1 rounded too", "        if 0 < li < last:\n            W = bf16(W)\n        z = a @ W.T + b", "        if li < last:\n            W = bf16(W)\n        z = a @ W.T + b"),
+ ("mlp.py", "bf16 dz not rounded", "            d = bf16(d * gelu_grad(z))", "            d = d * gelu_grad(z)"),
+ ("mlp.py", "bf16 backward unrounded W", "        if 0 < li < last:\n            W = bf16(W)\n        grads[li]", "        if False:\n            W = bf16(W)\n        grads[li]"),
 ]
 
 
