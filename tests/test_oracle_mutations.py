@@ -16,7 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 pytestmark = pytest.mark.mutation
 
-# (file, what the mistake is, the text it replaces, the mistaken text)
+# (file in oracle/, what the mistake is, the text it replaces, the mistaken text)
 MUTATIONS = [
  ("dp_oracle.c", "orbit centrifugal sign", "f[1] = vt * vt / r - p->mu / (r * r) + am * sin(alpha);", "f[1] = -vt * vt / r - p->mu / (r * r) + am * sin(alpha);"),
  ("dp_oracle.c", "orbit gravity 1/r^3", "- p->mu / (r * r) + am * sin(alpha);", "- p->mu / (r * r * r) + am * sin(alpha);"),
@@ -91,6 +91,9 @@ MUTATIONS = [
  ("mlp.py", "bf16 W1 rounded too", "        if 0 < li < last:\n            W = bf16(W)\n        z = a @ W.T + b", "        if li < last:\n            W = bf16(W)\n        z = a @ W.T + b"),
  ("mlp.py", "bf16 dz not rounded", "            d = bf16(d * gelu_grad(z))", "            d = d * gelu_grad(z)"),
  ("mlp.py", "bf16 backward unrounded W", "        if 0 < li < last:\n            W = bf16(W)\n        grads[li]", "        if False:\n            W = bf16(W)\n        grads[li]"),
+ ("__init__.py", "eval diag drops beta in the factor", "Vn = (b + beta * (Wm @ V - d * V)) / (1.0 - beta * d)", "Vn = (b + beta * (Wm @ V - d * V)) / (1.0 - d)"),
+ ("__init__.py", "exact evaluation without beta", "A = (sp.identity(self.N, format=\"csr\") - self.s.beta * W).tocsc()", "A = (sp.identity(self.N, format=\"csr\") - W).tocsc()"),
+ ("__init__.py", "policy system transposed", "W = sp.csr_matrix((w[used], (rows[used], idx[used])), shape=(self.N, self.N))", "W = sp.csr_matrix((w[used], (idx[used], rows[used])), shape=(self.N, self.N))"),
 ]
 
 
