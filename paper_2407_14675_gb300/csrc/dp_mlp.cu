@@ -286,16 +286,16 @@ constexpr int kPersistSmem = (kTileN + 2 * kTileM) * kKC * 2;   // 192 KB
 constexpr int kPersistThreads = 1024;
 constexpr int kPersistParts = kPersistThreads / 128;            // column parts per TMEM lane quarter
 
-//
 // RED (backward only) adds the sums over each row tile that the next
 // gradients need, so that no separate pass re-reads dz: RED = 1 the column
 // sums of dz (a bias gradient), RED = 5 also the sums of dz times each of the
-// four inputs xin (rows x 4, the first layer's weight gradient).  Tile t's
-// sums go to red[t * RED * 256 ..]: for RED = 5 the 4 x 256 weight-gradient
-// entries (feature-major) then the 256 bias-gradient entries, the layout of
-// W1, b1 in the parameter vector.  A warp sums its 32 rows in order (its
-// lanes' rows, then a fixed shuffle tree), the CTA its four row quarters in
-// order; the tiles are summed afterwards in a fixed order.
+// four inputs xin (rows x 4, the first layer's weight gradient), both from
+// the FP32 values before dz is rounded to BF16.  Tile t's sums go to
+// red[t * RED * 256 ..]: for RED = 5 the 4 x 256 weight-gradient entries
+// (feature-major) then the 256 bias-gradient entries, the layout of W1, b1
+// in the parameter vector.  Each lane sums its rows in order, a fixed
+// shuffle tree combines the lanes of a warp, the CTA adds its four row
+// quarters in order, and the tiles are summed afterwards in a fixed order.
 template <int EPI, int RED = 0>
 __global__ void __launch_bounds__(kPersistThreads)
 mlp_persistent_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb, int tiles,
