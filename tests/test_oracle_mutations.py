@@ -94,6 +94,10 @@ MUTATIONS = [
  ("__init__.py", "eval diag drops beta in the factor", "Vn = (b + beta * (Wm @ V - d * V)) / (1.0 - beta * d)", "Vn = (b + beta * (Wm @ V - d * V)) / (1.0 - d)"),
  ("__init__.py", "exact evaluation without beta", "A = (sp.identity(self.N, format=\"csr\") - self.s.beta * W).tocsc()", "A = (sp.identity(self.N, format=\"csr\") - W).tocsc()"),
  ("__init__.py", "policy system transposed", "W = sp.csr_matrix((w[used], (rows[used], idx[used])), shape=(self.N, self.N))", "W = sp.csr_matrix((w[used], (idx[used], rows[used])), shape=(self.N, self.N))"),
+ ("dp_oracle.c", "angle seam clamped", "if (periodic(p, d) && idx[d] == p->n[d]) idx[d] = 0;", "if (periodic(p, d) && idx[d] == p->n[d]) idx[d] = p->n[d] - 1;"),
+ ("dp_oracle.c", "walk start truncated", "return (int)(((code * K + ORC_NCODES / 2) / ORC_NCODES) % K);", "return (int)(((code * K) / ORC_NCODES) % K);"),
+ ("dp_oracle.c", "target counts zero-width dims", "if (p->tgt_w[d] > 0.0 && !(fabs(x[d] - p->tgt_c[d]) < p->tgt_w[d])) return 0;", "if (p->tgt_w[d] >= 0.0 && !(fabs(x[d] - p->tgt_c[d]) < p->tgt_w[d])) return 0;"),
+ ("dp_oracle.c", "periodic fraction reversed", "            t[d] = s[d] - f;", "            t[d] = 1.0 - (s[d] - f);"),
 ]
 
 

@@ -264,6 +264,22 @@ def test_ties_keep_the_lowest_tabulated_angle():
         assert np.allclose(Vn[inner], p.dt, rtol=0, atol=1e-15)
 
 
+def test_walk_starts_at_the_nearest_tabulated_angle():
+    # with q flat (V = 0, every foot inside) the walk never moves, so it
+    # returns its starting index: the table index nearest to the previous
+    # code, also for codes just below or just above a table point
+    p = W.unit_speed_2d(n=9, n_angles=8).replace(refine=0)
+    o = oracle.Oracle(p)
+    step = 65536 // 8
+    idx = np.array(np.unravel_index(np.arange(o.N), p.n)).T
+    inner = (idx[:, 0] > 0) & (idx[:, 0] < p.n[0] - 1) & (idx[:, 1] > 0) & (idx[:, 1] < p.n[1] - 1)
+    inner &= ~o.target.astype(bool)
+    for prev, want in ((3 * step - 1, 3), (3 * step - step // 2 + 1, 3), (3 * step + step // 2 - 1, 3),
+                       (5 * step + 7, 5), (65535 - 3, 0)):
+        _, codes, _, _ = o.sweep(np.zeros(o.N), mode=oracle.IMPROVE_WALK, codes=np.full(o.N, prev, np.uint16))
+        assert (codes[inner] == want * step).all(), (prev, want)
+
+
 def test_sweep_residual_is_the_sup_norm_of_the_change():
     # from a value above the fixed point the sweep lowers V: the residual is
     # still max |V' - V| over the node set, not a signed difference
