@@ -1,5 +1,5 @@
 """Mutation check of the oracle's pins (opt-in: DP_ORACLE_MUTATIONS=1; about
-ten minutes).  Each case plants one plausible mistake -- a dropped term, a
+fifteen minutes).  Each case plants one plausible mistake -- a dropped term, a
 wrong sign or index, a swapped operand, a tie rule turned round -- in a copy of
 oracle/ in a temporary directory, builds that copy, and runs the CPU suite
 against it (the copy first on the import path).  Every case must make some
