@@ -3,6 +3,8 @@
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -84,3 +86,22 @@ def test_binding_constants_match_header():
     for n in ("DP_EVAL_JACOBI", "DP_EVAL_GMRES", "DP_EVAL_DIAG", "DP_SWEEP_EVAL_DIAG", "DP_SWEEP_VI_DIAG",
               "DP_GMRES_MAX_RESTART"):
         assert n in names
+
+
+def test_network_parameter_layout_matches_the_library(lib):
+    # the flat FP32 vector of dp.h: W1 (256 x 4, row = output), b1, W2, b2, W3,
+    # b3, W4 (3 x 256), b4 -- the library's count, the binding's flattening and
+    # the reference network's shapes agree, and flattening round-trips
+    from paper_2407_14675_gb300 import dp, workloads as W
+    params = W.mlp_init_params(seed=3)
+    shapes = [(W_.shape, b.shape) for W_, b in params]
+    assert shapes == [((256, 4), (256,)), ((256, 256), (256,)), ((256, 256), (256,)), ((3, 256), (3,))]
+    flat = dp.flatten_params(params)
+    assert flat.dtype == np.float32
+    assert lib.dp_mlp_param_count() == flat.size == 4 * 256 + 256 + 2 * (256 * 256 + 256) + 3 * 256 + 3
+    back = dp.unflatten_params(flat)
+    for (W0, b0), (W1, b1) in zip(params, back):
+        assert np.array_equal(np.float32(W0), W1) and np.array_equal(np.float32(b0), b1)
+    # the offsets dp.h implies: b1 right after W1, W4 right after b3
+    assert np.array_equal(flat[1024:1280], np.float32(params[0][1]))
+    assert np.array_equal(flat[-3 - 768:-3].reshape(3, 256), np.float32(params[3][0]))
